@@ -1,0 +1,607 @@
+/*
+ * srp_oracle.c -- FP64 CPU oracle of the solar-radiation-pressure (SRP)
+ * ray-grid estimator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this code.  The product library
+ * (the CUDA path) shares no code, header, table or constant with it.
+ *
+ * What it computes (paper, Sec. 3.2):
+ *   force  F(w,theta) = integral over the surface M(theta) of the force
+ *                       field f(x,w,theta)                     (Eq. Force/F)
+ *   torque tau(w,theta) = integral over M of (x - x_COM) x f   (Eq. torque)
+ * with the light-to-force map l2f (Sec. 3.2): photons arriving along the
+ * travel direction d transfer their momentum; reflected photons carry
+ * momentum away along w_out.  The estimator is a grid of parallel rays
+ * over the bounding sphere (the "ray-grid" family of Sec. 2.1 / Table
+ * "Methods"), with closest hits found by testing every ray against EVERY
+ * triangle (the paper's own brute-force intersection, Sec. 3.2,
+ * "Estimation").  No acceleration structure is used.
+ *
+ * Steps, in order, per ray i of sun direction s of design index D:
+ *  1. Philox4x32-10 (Salmon et al., SC'11) with counter (i, s, D, k) and key
+ *     (seed_lo, seed_hi); uniform u(x) = (x >> 8) * 2^-24.
+ *  2. Orthonormal basis (u,v) of the travel direction d = -e by the
+ *     branchless construction of Duff et al. 2017.
+ *  3. Grid over the square of side 2R centred on the mesh's AABB centre c,
+ *     R = max |vertex - c|: pixel (px,py) with jitter (xi1,xi2) (or 0.5),
+ *     origin o = c + (-R+(px+xi1)dx) u + (-R+(py+xi2)dy) v - 2R d,
+ *     per-ray momentum weight w0 = P dx dy.
+ *  4. Closest hit over all triangles, watertight ray/triangle test of Woop,
+ *     Benthin and Wald (JCGT 2013), FP64.  Ties on t go to the smaller
+ *     triangle index.  Bounce rays skip their source triangle and hits with
+ *     t <= 1e-6 R.
+ *  5. At hit k (normal flipped to face the ray, cos = -n.d):
+ *       k == K:  deposit w [(1-rs) d - (2 rs cos + 2/3 rd) n]   (expected
+ *                value of the reflection, the per-plate law)
+ *       k <  K:  branch with fixed probability 1/2 (xi_b = u(x0)):
+ *                specular r = d - 2(d.n)n,        w' = 2 w rs
+ *                diffuse  cosine-weighted about n, w' = 2 w rd
+ *                deposit w d - w' d'; continue with (x, d', w')
+ *     torque deposit (x - COM) x deposit.  Rays that miss deposit nothing.
+ *  6. Sums in FP64 in ray order k.  Uncertainty: each pixel is one
+ *     stratum with one sample, so the variance of the total is estimated by
+ *     collapsing neighbouring strata in pairs (k = 2j, 2j+1) (Cochran,
+ *     "Sampling Techniques", collapsed strata): var = sum_j (y_2j - y_2j+1)^2,
+ *     plus y^2 of an unpaired last ray; sigma = sqrt(var) per component.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* 1. Philox4x32-10, from its published definition (Salmon et al. 2011) */
+/* ------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+static void rng4(uint64_t seed, uint32_t i, uint32_t s, uint32_t dsg, uint32_t k, double u[4])
+{
+    uint32_t ctr[4] = {i, s, dsg, k};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    or_philox4x32_10(ctr, key, o);
+    for (int j = 0; j < 4; ++j) u[j] = u24(o[j]);
+}
+
+/* ------------------------------------------------------------------ */
+/* small vector helpers                                                */
+/* ------------------------------------------------------------------ */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double a[3], const double b[3], double o[3])
+{
+    double x = a[1] * b[2] - a[2] * b[1];
+    double y = a[2] * b[0] - a[0] * b[2];
+    double z = a[0] * b[1] - a[1] * b[0];
+    o[0] = x; o[1] = y; o[2] = z;
+}
+
+/* 2. Duff, Burgess, Christensen, Hery, Kensler, Liani, Villemin (2017):
+ *    branchless ONB for a unit vector n; (b1, b2, n) right-handed. */
+void or_onb(const double n[3], double b1[3], double b2[3])
+{
+    double sign = n[2] >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sign + n[2]);
+    double b = n[0] * n[1] * a;
+    b1[0] = 1.0 + sign * n[0] * n[0] * a; b1[1] = sign * b; b1[2] = -sign * n[0];
+    b2[0] = b; b2[1] = sign + n[1] * n[1] * a; b2[2] = -n[1];
+}
+
+/* ------------------------------------------------------------------ */
+/* 4. Watertight ray/triangle intersection (Woop, Benthin, Wald 2013)  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double o[3], d[3];
+    int kx, ky, kz;
+    double Sx, Sy, Sz;
+} wray;
+
+static void wray_setup(wray* r, const double o[3], const double d[3])
+{
+    for (int j = 0; j < 3; ++j) { r->o[j] = o[j]; r->d[j] = d[j]; }
+    int kz = 0;
+    double ax = fabs(d[0]), ay = fabs(d[1]), az = fabs(d[2]);
+    if (ay > ax && ay >= az) kz = 1;
+    else if (az > ax && az > ay) kz = 2;
+    int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
+    if (d[kz] < 0.0) { int t = kx; kx = ky; ky = t; }
+    r->kx = kx; r->ky = ky; r->kz = kz;
+    r->Sx = d[kx] / d[kz]; r->Sy = d[ky] / d[kz]; r->Sz = 1.0 / d[kz];
+}
+
+/* Returns 1 and the ray parameter t when the ray hits the triangle. */
+static int wray_hit(const wray* r, const double* p0, const double* p1, const double* p2, double* t_out)
+{
+    double A[3], B[3], C[3];
+    for (int j = 0; j < 3; ++j) { A[j] = p0[j] - r->o[j]; B[j] = p1[j] - r->o[j]; C[j] = p2[j] - r->o[j]; }
+    const int kx = r->kx, ky = r->ky, kz = r->kz;
+    double Ax = A[kx] - r->Sx * A[kz], Ay = A[ky] - r->Sy * A[kz];
+    double Bx = B[kx] - r->Sx * B[kz], By = B[ky] - r->Sy * B[kz];
+    double Cx = C[kx] - r->Sx * C[kz], Cy = C[ky] - r->Sy * C[kz];
+    double U = Cx * By - Cy * Bx;
+    double V = Ax * Cy - Ay * Cx;
+    double W = Bx * Ay - By * Ax;
+    if ((U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0)) return 0;
+    double det = U + V + W;
+    if (det == 0.0) return 0;
+    double Az = r->Sz * A[kz], Bz = r->Sz * B[kz], Cz = r->Sz * C[kz];
+    double T = U * Az + V * Bz + W * Cz;
+    *t_out = T / det;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* scene                                                              */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int T;
+    const double* tv;      /* [T][9] vertex positions (double)          */
+    const double* tn;      /* [T][3] unit geometric normal (e1 x e2)    */
+    const int32_t* group;  /* [T]                                        */
+    const double* rho;     /* [G][2]                                     */
+    double c[3], R;        /* grid centre (AABB centre) and radius       */
+    double com[3];
+    double P;
+    int nx, ny, K, jitter;
+    uint64_t seed;
+    uint32_t dsg;          /* design index used in the RNG counter       */
+} scene_t;
+
+/* Closest hit by brute force: smallest t > tmin, ties -> smaller index. */
+static int closest(const scene_t* sc, const wray* r, double tmin, int skip, double* t_best)
+{
+    int best = -1;
+    double tb = INFINITY;
+    for (int f = 0; f < sc->T; ++f) {
+        if (f == skip) continue;
+        const double* v = sc->tv + 9 * (size_t)f;
+        double t;
+        if (!wray_hit(r, v, v + 3, v + 6, &t)) continue;
+        if (!(t > tmin)) continue;
+        if (t < tb) { tb = t; best = f; }
+    }
+    *t_best = tb;
+    return best;
+}
+
+/* Per-path record, used by the gradient. */
+typedef struct {
+    int m;              /* number of hits (segments that hit)            */
+    int f[8];           /* hit triangle                                   */
+    int br[8];          /* 0 specular, 1 diffuse (k < K only)            */
+    double w[9];        /* weight arriving at hit k                      */
+    double x[8][3];     /* hit point                                     */
+    double d[8][3];     /* arriving direction                            */
+    double n[8][3];     /* facing normal                                 */
+    double cs[8];       /* cos = -n.d                                    */
+    double dout[8][3];  /* outgoing direction (k < K)                    */
+} path_t;
+
+static void grid_ray(const scene_t* sc, const double e[3], uint64_t i, uint32_t s,
+                     double o[3], double d[3], double* w0)
+{
+    for (int j = 0; j < 3; ++j) d[j] = -e[j];
+    double bu[3], bv[3];
+    or_onb(d, bu, bv);
+    uint32_t px = (uint32_t)(i % (uint64_t)sc->nx), py = (uint32_t)(i / (uint64_t)sc->nx);
+    double xi1 = 0.5, xi2 = 0.5;
+    if (sc->jitter) {
+        double u[4];
+        rng4(sc->seed, (uint32_t)i, s, sc->dsg, 0, u);
+        xi1 = u[0]; xi2 = u[1];
+    }
+    double dx = 2.0 * sc->R / sc->nx, dy = 2.0 * sc->R / sc->ny;
+    double a = -sc->R + ((double)px + xi1) * dx;
+    double b = -sc->R + ((double)py + xi2) * dy;
+    for (int j = 0; j < 3; ++j) o[j] = sc->c[j] + a * bu[j] + b * bv[j] - 2.0 * sc->R * d[j];
+    *w0 = sc->P * dx * dy;
+}
+
+/* Trace one ray path; accumulate force/torque (6) into acc; fill path. */
+static void trace_path(const scene_t* sc, const double e[3], uint64_t i, uint32_t s,
+                       double acc[6], path_t* pth)
+{
+    double o[3], d[3], w;
+    grid_ray(sc, e, i, s, o, d, &w);
+    int src = -1;
+    double tmin = 0.0;
+    pth->m = 0;
+    for (int k = 1; k <= sc->K; ++k) {
+        wray r;
+        wray_setup(&r, o, d);
+        double t;
+        int f = closest(sc, &r, tmin, src, &t);
+        if (f < 0) break;
+        int h = k - 1;
+        pth->m = k;
+        pth->f[h] = f;
+        pth->w[h] = w;
+        double x[3], n[3];
+        for (int j = 0; j < 3; ++j) x[j] = o[j] + t * d[j];
+        const double* ng = sc->tn + 3 * (size_t)f;
+        double sgn = dot3(ng, d) > 0.0 ? -1.0 : 1.0;
+        for (int j = 0; j < 3; ++j) n[j] = sgn * ng[j];
+        double cs = -dot3(n, d);
+        const double rs = sc->rho[2 * sc->group[f]], rd = sc->rho[2 * sc->group[f] + 1];
+        for (int j = 0; j < 3; ++j) { pth->x[h][j] = x[j]; pth->d[h][j] = d[j]; pth->n[h][j] = n[j]; }
+        pth->cs[h] = cs;
+        double dp[3], arm[3], tq[3];
+        for (int j = 0; j < 3; ++j) arm[j] = x[j] - sc->com[j];
+        if (k == sc->K) {
+            double cn = 2.0 * rs * cs + (2.0 / 3.0) * rd;
+            for (int j = 0; j < 3; ++j) dp[j] = w * ((1.0 - rs) * d[j] - cn * n[j]);
+            cross3(arm, dp, tq);
+            for (int j = 0; j < 3; ++j) { acc[j] += dp[j]; acc[3 + j] += tq[j]; }
+            break;
+        }
+        double u[4];
+        rng4(sc->seed, (uint32_t)i, s, sc->dsg, (uint32_t)k, u);
+        double dout[3], wout;
+        if (u[0] < 0.5) {
+            for (int j = 0; j < 3; ++j) dout[j] = d[j] + 2.0 * cs * n[j];
+            wout = 2.0 * w * rs;
+            pth->br[h] = 0;
+        } else {
+            double b1[3], b2[3];
+            or_onb(n, b1, b2);
+            double rr = sqrt(u[1]), phi = 2.0 * M_PI * u[2];
+            double lx = rr * cos(phi), ly = rr * sin(phi), lz = sqrt(fmax(0.0, 1.0 - u[1]));
+            for (int j = 0; j < 3; ++j) dout[j] = lx * b1[j] + ly * b2[j] + lz * n[j];
+            wout = 2.0 * w * rd;
+            pth->br[h] = 1;
+        }
+        for (int j = 0; j < 3; ++j) { dp[j] = w * d[j] - wout * dout[j]; pth->dout[h][j] = dout[j]; }
+        cross3(arm, dp, tq);
+        for (int j = 0; j < 3; ++j) { acc[j] += dp[j]; acc[3 + j] += tq[j]; }
+        pth->w[h + 1] = wout;
+        for (int j = 0; j < 3; ++j) { o[j] = x[j]; d[j] = dout[j]; }
+        w = wout;
+        src = f;
+        tmin = 1e-6 * sc->R;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Reverse-mode gradient of one path's contribution L = sum_k q_k.dp_k */
+/* (rho part: exact along the fixed path; hinge part: K == 1, hit      */
+/* point held fixed on its facet, see or_force_grad).                  */
+/* ------------------------------------------------------------------ */
+static void path_grad(const scene_t* sc, const path_t* p, const double gF[3], const double gT[3],
+                      double* d_rho /*[G][2]*/)
+{
+    if (p->m == 0) return;
+    double wbar_next = 0.0;  /* adjoint of w_{h+1} */
+    for (int h = p->m - 1; h >= 0; --h) {
+        const int f = p->f[h];
+        const int g = sc->group[f];
+        const double rs = sc->rho[2 * g], rd = sc->rho[2 * g + 1];
+        double arm[3], q[3];
+        for (int j = 0; j < 3; ++j) arm[j] = p->x[h][j] - sc->com[j];
+        cross3(gT, arm, q);
+        for (int j = 0; j < 3; ++j) q[j] += gF[j];
+        const double w = p->w[h];
+        double wbar;
+        if (h + 1 == sc->K) {
+            /* closed-form deposit w[(1-rs)d - (2 rs c + 2/3 rd) n] */
+            double qd = dot3(q, p->d[h]), qn = dot3(q, p->n[h]);
+            double cs = p->cs[h];
+            d_rho[2 * g] += w * (-qd - 2.0 * cs * qn);
+            d_rho[2 * g + 1] += w * (-(2.0 / 3.0) * qn);
+            wbar = (1.0 - rs) * qd - (2.0 * rs * cs + (2.0 / 3.0) * rd) * qn;
+        } else {
+            /* deposit w d - w' d'; w' = 2 w rho_branch */
+            double wbar_out = wbar_next - dot3(q, p->dout[h]);
+            wbar = dot3(q, p->d[h]);
+            double rb = p->br[h] == 0 ? rs : rd;
+            d_rho[2 * g + p->br[h]] += wbar_out * 2.0 * w;
+            wbar += wbar_out * 2.0 * rb;
+        }
+        wbar_next = wbar;
+    }
+}
+
+/* Hinge derivative of a K=1 hit: the ray's surface element is carried
+ * rigidly by the facet, so the ray's contribution is (w/c0) c(a) q.G(n(a)). */
+static double hinge_term(const scene_t* sc, const path_t* p, const double gF[3], const double gT[3],
+                         const double axis_p[3], const double axis_a[3])
+{
+    const int f = p->f[0];
+    const int g = sc->group[f];
+    const double rs = sc->rho[2 * g], rd = sc->rho[2 * g + 1];
+    const double* x = p->x[0];
+    const double* n = p->n[0];
+    const double* d = p->d[0];
+    const double c = p->cs[0];
+    double arm[3], q[3], Gv[3], dn[3], dx[3], rel[3], dq[3], dG[3];
+    for (int j = 0; j < 3; ++j) { arm[j] = x[j] - sc->com[j]; rel[j] = x[j] - axis_p[j]; }
+    cross3(gT, arm, q);
+    for (int j = 0; j < 3; ++j) q[j] += gF[j];
+    const double cn = 2.0 * rs * c + (2.0 / 3.0) * rd;
+    for (int j = 0; j < 3; ++j) Gv[j] = (1.0 - rs) * d[j] - cn * n[j];
+    cross3(axis_a, n, dn);        /* dn/da */
+    cross3(axis_a, rel, dx);      /* dx/da */
+    const double dc = -dot3(dn, d);
+    cross3(gT, dx, dq);           /* dq/da */
+    for (int j = 0; j < 3; ++j) dG[j] = -2.0 * rs * dc * n[j] - cn * dn[j];
+    const double dphi = dc * dot3(q, Gv) + c * (dot3(dq, Gv) + dot3(q, dG));
+    return (p->w[0] / c) * dphi;
+}
+
+/* ------------------------------------------------------------------ */
+/* threaded driver                                                    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const scene_t* sc;
+    const double* sun;     /* [S][3] */
+    int S;
+    int64_t off, stride, n;
+    int64_t chunk;         /* rays per job (even) */
+    int64_t nchunk;
+    uint32_t sun_base;
+    double* part;          /* [S][nchunk][12]: sums (6), squared pair diffs (6) */
+    /* gradient */
+    const double* up;      /* [S][6] or NULL */
+    const double* hp;      /* [H][6] hinge axes */
+    const int32_t* thinge; /* [T] */
+    int H, G;
+    double* grad_rho;      /* per-thread [G][2] */
+    double* grad_h;        /* per-thread [H] */
+    int64_t job0, job1;    /* jobs = s*nchunk + c */
+} work_t;
+
+static void* worker(void* arg)
+{
+    work_t* wk = (work_t*)arg;
+    const scene_t* sc = wk->sc;
+    path_t p;
+    for (int64_t job = wk->job0; job < wk->job1; ++job) {
+        int s = (int)(job / wk->nchunk);
+        int64_t c = job % wk->nchunk;
+        const double* e = wk->sun + 3 * (size_t)s;
+        double acc[6] = {0, 0, 0, 0, 0, 0}, sq[6] = {0, 0, 0, 0, 0, 0}, pend[6] = {0, 0, 0, 0, 0, 0};
+        int64_t k0 = c * wk->chunk, k1 = k0 + wk->chunk < wk->n ? k0 + wk->chunk : wk->n;
+        for (int64_t k = k0; k < k1; ++k) {
+            uint64_t i = (uint64_t)(wk->off + k * wk->stride);
+            double y[6] = {0, 0, 0, 0, 0, 0};
+            trace_path(sc, e, i, wk->sun_base + (uint32_t)s, y, &p);
+            for (int j = 0; j < 6; ++j) acc[j] += y[j];
+            if ((k & 1) == 0) {
+                for (int j = 0; j < 6; ++j) pend[j] = y[j];
+                if (k + 1 == wk->n) for (int j = 0; j < 6; ++j) sq[j] += y[j] * y[j];
+            } else {
+                for (int j = 0; j < 6; ++j) { double q = y[j] - pend[j]; sq[j] += q * q; }
+            }
+            if (wk->up) {
+                const double* g6 = wk->up + 6 * (size_t)s;
+                path_grad(sc, &p, g6, g6 + 3, wk->grad_rho);
+                if (wk->H > 0 && sc->K == 1 && p.m == 1) {
+                    int hh = wk->thinge[p.f[0]];
+                    if (hh >= 0)
+                        wk->grad_h[hh] += hinge_term(sc, &p, g6, g6 + 3, wk->hp + 6 * hh, wk->hp + 6 * hh + 3);
+                }
+            }
+        }
+        double* dst = wk->part + 12 * ((size_t)s * wk->nchunk + c);
+        for (int j = 0; j < 6; ++j) { dst[j] = acc[j]; dst[6 + j] = sq[j]; }
+    }
+    return NULL;
+}
+
+static void build_scene(scene_t* sc, double* tv, double* tn, const float* verts, int V,
+                        const int32_t* tris, int T)
+{
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < V; ++v)
+        for (int j = 0; j < 3; ++j) {
+            double x = verts[3 * v + j];
+            if (x < lo[j]) lo[j] = x;
+            if (x > hi[j]) hi[j] = x;
+        }
+    for (int j = 0; j < 3; ++j) sc->c[j] = 0.5 * (lo[j] + hi[j]);
+    double R2 = 0.0;
+    for (int v = 0; v < V; ++v) {
+        double r2 = 0.0;
+        for (int j = 0; j < 3; ++j) { double q = verts[3 * v + j] - sc->c[j]; r2 += q * q; }
+        if (r2 > R2) R2 = r2;
+    }
+    sc->R = sqrt(R2);
+    for (int f = 0; f < T; ++f) {
+        for (int c = 0; c < 3; ++c)
+            for (int j = 0; j < 3; ++j) tv[9 * f + 3 * c + j] = verts[3 * tris[3 * f + c] + j];
+        double e1[3], e2[3], nn[3];
+        for (int j = 0; j < 3; ++j) { e1[j] = tv[9 * f + 3 + j] - tv[9 * f + j]; e2[j] = tv[9 * f + 6 + j] - tv[9 * f + j]; }
+        cross3(e1, e2, nn);
+        double l = sqrt(dot3(nn, nn));
+        for (int j = 0; j < 3; ++j) tn[3 * f + j] = l > 0.0 ? nn[j] / l : 0.0;
+    }
+    sc->T = T;
+    sc->tv = tv;
+    sc->tn = tn;
+}
+
+/* Grid parameters (centre c, radius R) as the oracle defines them. */
+void or_grid(const float* verts, int V, double c_out[3], double* R_out)
+{
+    int32_t tri0[3] = {0, 0, 0};
+    double tv[9], tn[3];
+    scene_t sc;
+    memset(&sc, 0, sizeof sc);
+    build_scene(&sc, tv, tn, verts, V, tri0, V > 0 ? 1 : 0);
+    for (int j = 0; j < 3; ++j) c_out[j] = sc.c[j];
+    *R_out = sc.R;
+}
+
+/*
+ * Force/torque of one design for S sun directions.
+ *   verts [V][3] f32, tris [T][3], group [T], rho [G][2] (f64),
+ *   sun [S][3] unit vectors toward the sun, com [3].
+ *   Ray subset: k = 0..n-1 traces grid ray i = off + k*stride
+ *   (n = 0: the full grid, off = 0, stride = 1).
+ *   out_ft [S][6] (F, tau), out_sigma [S][6] or NULL.
+ *   Gradient (optional, up != NULL): upstream dL/d(F,tau) [S][6];
+ *   d_rho [G][2] and d_hinge [H] are ADDED to.  Hinges need K == 1.
+ */
+int or_force(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
+             const double* rho, int G, const double* sun, int S, const double* com,
+             int nx, int ny, int K, int jitter, uint64_t seed, double P,
+             int64_t off, int64_t stride, int64_t n, uint32_t sun_base, uint32_t dsg,
+             int threads, double* out_ft, double* out_sigma,
+             const double* up, const int32_t* thinge, const double* hinge_axes, int H,
+             double* d_rho, double* d_hinge)
+{
+    if (T < 0 || V < 0 || S < 0 || nx <= 0 || ny <= 0 || K < 1 || K > 8) return 1;
+    if (n <= 0) { off = 0; stride = 1; n = (int64_t)nx * ny; }
+    if (threads <= 0) threads = 1;
+    double* tv = (double*)malloc(sizeof(double) * 9 * (size_t)(T > 0 ? T : 1));
+    double* tn = (double*)malloc(sizeof(double) * 3 * (size_t)(T > 0 ? T : 1));
+    scene_t sc;
+    memset(&sc, 0, sizeof sc);
+    build_scene(&sc, tv, tn, verts, V, tris, T);
+    sc.group = group; sc.rho = rho;
+    for (int j = 0; j < 3; ++j) sc.com[j] = com[j];
+    sc.P = P; sc.nx = nx; sc.ny = ny; sc.K = K; sc.jitter = jitter; sc.seed = seed; sc.dsg = dsg;
+    const int64_t chunk = 4096;
+    const int64_t nchunk = (n + chunk - 1) / chunk;
+    double* part = (double*)calloc((size_t)S * nchunk * 12 + 1, sizeof(double));
+    int64_t jobs = (int64_t)S * nchunk;
+    if (threads > jobs) threads = jobs > 0 ? (int)jobs : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * threads);
+    work_t* wk = (work_t*)calloc(threads, sizeof(work_t));
+    double* gr = up ? (double*)calloc((size_t)threads * (2 * G + H + 1), sizeof(double)) : NULL;
+    for (int t = 0; t < threads; ++t) {
+        wk[t].sc = &sc; wk[t].sun = sun; wk[t].S = S;
+        wk[t].off = off; wk[t].stride = stride; wk[t].n = n;
+        wk[t].chunk = chunk; wk[t].nchunk = nchunk;
+        wk[t].sun_base = sun_base; wk[t].part = part;
+        wk[t].up = up; wk[t].hp = hinge_axes; wk[t].thinge = thinge; wk[t].H = H; wk[t].G = G;
+        if (gr) { wk[t].grad_rho = gr + (size_t)t * (2 * G + H + 1); wk[t].grad_h = wk[t].grad_rho + 2 * G; }
+        wk[t].job0 = jobs * t / threads;
+        wk[t].job1 = jobs * (t + 1) / threads;
+    }
+    for (int t = 1; t < threads; ++t) pthread_create(&th[t], NULL, worker, &wk[t]);
+    worker(&wk[0]);
+    for (int t = 1; t < threads; ++t) pthread_join(th[t], NULL);
+    for (int s = 0; s < S; ++s) {
+        double tot[12] = {0};
+        for (int64_t c = 0; c < nchunk; ++c)
+            for (int j = 0; j < 12; ++j) tot[j] += part[12 * ((size_t)s * nchunk + c) + j];
+        if (out_ft) for (int j = 0; j < 6; ++j) out_ft[6 * s + j] = tot[j];
+        if (out_sigma) for (int j = 0; j < 6; ++j) out_sigma[6 * s + j] = sqrt(tot[6 + j]);
+    }
+    if (gr) {
+        for (int t = 0; t < threads; ++t) {
+            for (int q = 0; q < 2 * G; ++q) d_rho[q] += wk[t].grad_rho[q];
+            for (int h = 0; h < H; ++h) d_hinge[h] += wk[t].grad_h[h];
+        }
+    }
+    free(gr); free(wk); free(th); free(part); free(tv); free(tn);
+    return 0;
+}
+
+/*
+ * Finite-difference companion of the hinge gradient: the SAME estimator
+ * with each K=1 hit carried rigidly by its facet, re-evaluated at hinge
+ * angle offsets +-h by rotating (x, n) about the hinge axis, without
+ * re-tracing.  Returns the central difference of L = sum_s up_s.(F_s,tau_s)
+ * in d_hinge[H].  Single-threaded; for small test cases.
+ */
+static void rotate(const double a[3], double ang, const double v[3], double o[3])
+{
+    double c = cos(ang), s = sin(ang), axv[3];
+    cross3(a, v, axv);
+    double ad = dot3(a, v);
+    for (int j = 0; j < 3; ++j) o[j] = v[j] * c + axv[j] * s + a[j] * ad * (1.0 - c);
+}
+
+int or_hinge_fd_fixed_hits(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
+                           const double* rho, int G, const double* sun, int S, const double* com,
+                           int nx, int ny, int jitter, uint64_t seed, double P,
+                           const double* up, const int32_t* thinge, const double* hinge_axes, int H,
+                           double hstep, double* d_hinge)
+{
+    (void)G;
+    double* tv = (double*)malloc(sizeof(double) * 9 * (size_t)(T > 0 ? T : 1));
+    double* tn = (double*)malloc(sizeof(double) * 3 * (size_t)(T > 0 ? T : 1));
+    scene_t sc;
+    memset(&sc, 0, sizeof sc);
+    build_scene(&sc, tv, tn, verts, V, tris, T);
+    sc.group = group; sc.rho = rho;
+    for (int j = 0; j < 3; ++j) sc.com[j] = com[j];
+    sc.P = P; sc.nx = nx; sc.ny = ny; sc.K = 1; sc.jitter = jitter; sc.seed = seed; sc.dsg = 0;
+    for (int h = 0; h < H; ++h) d_hinge[h] = 0.0;
+    path_t p;
+    int64_t n = (int64_t)nx * ny;
+    for (int s = 0; s < S; ++s) {
+        const double* e = sun + 3 * s;
+        const double* gF = up + 6 * s;
+        const double* gT = up + 6 * s + 3;
+        for (int64_t i = 0; i < n; ++i) {
+            double acc[6] = {0};
+            trace_path(&sc, e, (uint64_t)i, (uint32_t)s, acc, &p);
+            if (p.m != 1) continue;
+            int hh = thinge[p.f[0]];
+            if (hh < 0) continue;
+            const double* ap = hinge_axes + 6 * hh;
+            const double* aa = ap + 3;
+            const int g = group[p.f[0]];
+            const double rs = rho[2 * g], rd = rho[2 * g + 1];
+            double val[2];
+            for (int sg = 0; sg < 2; ++sg) {
+                double ang = sg == 0 ? hstep : -hstep;
+                double rel[3], xr[3], nr[3], arm[3], q[3], dp[3];
+                for (int j = 0; j < 3; ++j) rel[j] = p.x[0][j] - ap[j];
+                rotate(aa, ang, rel, xr);
+                rotate(aa, ang, p.n[0], nr);
+                for (int j = 0; j < 3; ++j) { xr[j] += ap[j]; arm[j] = xr[j] - com[j]; }
+                double c = -dot3(nr, p.d[0]);
+                double wa = p.w[0] / p.cs[0] * c;
+                double cn = 2.0 * rs * c + (2.0 / 3.0) * rd;
+                for (int j = 0; j < 3; ++j) dp[j] = wa * ((1.0 - rs) * p.d[0][j] - cn * nr[j]);
+                cross3(gT, arm, q);
+                for (int j = 0; j < 3; ++j) q[j] += gF[j];
+                val[sg] = dot3(q, dp);
+            }
+            d_hinge[hh] += (val[0] - val[1]) / (2.0 * hstep);
+        }
+    }
+    free(tv); free(tn);
+    return 0;
+}
+
+/* Single-ray debug query: hit triangle of the primary ray (or -1) and t. */
+int or_primary_hit(const float* verts, int V, const int32_t* tris, int T, const double* sun,
+                   int nx, int ny, int jitter, uint64_t seed, uint32_t sun_idx, uint32_t dsg,
+                   int64_t i, double* t_out)
+{
+    double* tv = (double*)malloc(sizeof(double) * 9 * (size_t)(T > 0 ? T : 1));
+    double* tn = (double*)malloc(sizeof(double) * 3 * (size_t)(T > 0 ? T : 1));
+    scene_t sc;
+    memset(&sc, 0, sizeof sc);
+    build_scene(&sc, tv, tn, verts, V, tris, T);
+    sc.nx = nx; sc.ny = ny; sc.jitter = jitter; sc.seed = seed; sc.dsg = dsg; sc.P = 1.0;
+    double o[3], d[3], w;
+    grid_ray(&sc, sun, (uint64_t)i, sun_idx, o, d, &w);
+    wray r;
+    wray_setup(&r, o, d);
+    int f = closest(&sc, &r, 0.0, -1, t_out);
+    free(tv); free(tn);
+    return f;
+}

@@ -1,0 +1,257 @@
+"""Pins of the FP64 oracle against facts fixed outside it: published test
+vectors, closed forms of the radiation-pressure integrals (Sec. 2.1 box-wing
+and cannonball models; Sec. 3.2 force and torque integrals), exact counts and
+symmetry/linearity invariants.  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _stat_ok(a, b, sa, sb, k=4.0, floor=1e-12):
+    """|a-b| <= k*sqrt(sa^2+sb^2) per component (plus a round-off floor)."""
+    tol = k * np.sqrt(np.asarray(sa) ** 2 + np.asarray(sb) ** 2) + floor
+    return np.all(np.abs(np.asarray(a) - np.asarray(b)) <= tol), np.abs(np.asarray(a) - np.asarray(b)) / (tol)
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+# ---------------------------------------------------------------- ONB
+def test_onb_orthonormal_right_handed():
+    rng = np.random.default_rng(3)
+    ns = list(rng.normal(size=(200, 3))) + [[0, 0, 1.0], [0, 0, -1.0], [1e-9, 0, -1.0], [1, 0, 0]]
+    for n in ns:
+        n = np.asarray(n, float) / np.linalg.norm(n)
+        b1, b2 = oracle.onb(n)
+        M = np.stack([b1, b2, n])
+        assert np.allclose(M @ M.T, np.eye(3), atol=1e-12)
+        assert np.allclose(np.cross(b1, b2), n, atol=1e-12)
+
+
+# ---------------------------------------------------------------- plate
+def _centre_count(R, nx, half):
+    """Number of pixel-centre rays of the 2R grid inside |coord| < half."""
+    dx = 2 * R / nx
+    c = -R + (np.arange(nx) + 0.5) * dx
+    return int(np.sum(np.abs(c) < half))
+
+
+@pytest.mark.parametrize("rs,rd", [(0.0, 0.0), (1.0, 0.0), (0.0, 1.0), (0.3, 0.2)])
+def test_plate_facing_sun_exact(rs, rd):
+    """Plate normal to the sun, pixel centres (no jitter): every deposit is
+    the per-plate law, so F = P a count [(1-rs) d - (2 rs + 2/3 rd) n]
+    with count the pixel centres inside the plate (exact, FP64)."""
+    p = W.flat_plate((2.0, 1.0), 2)
+    rho = np.array([[rs, rd]])
+    e = np.array([0, 0, 1.0])
+    nx = 200
+    ft, _ = oracle.force(p.verts, p.tris, p.group, rho, e, np.zeros(3), nx=nx, jitter=0, K=1)
+    c, R = oracle.grid(p.verts)
+    cnt = _centre_count(R, nx, 1.0) * _centre_count(R, nx, 0.5)
+    a = (2 * R / nx) ** 2
+    d = -e
+    n = e  # facing normal
+    F = a * cnt * ((1 - rs) * d - (2 * rs + 2 / 3 * rd) * n)
+    assert np.allclose(ft[0, :3], F, rtol=1e-12, atol=1e-15)
+    # centred plate, symmetric pixel centres: torque zero to round-off
+    assert np.all(np.abs(ft[0, 3:]) < 1e-12)
+
+
+def test_plate_absorber_forms():
+    """The benchmark spec's absorbed / specular / diffuse plate forms at cos = 1."""
+    p = W.flat_plate((2.0, 1.0), 2)
+    A = 2.0
+    e = np.array([0, 0, 1.0]); d = -e; n = e
+    for (rs, rd), F in [((0, 0), A * d), ((1, 0), -2 * A * n + 0 * d), ((0, 1), A * (d - 2 / 3 * n))]:
+        got = oracle.facet_law(p.verts, p.tris, p.group, np.array([[rs, rd]]), e, np.zeros(3))
+        assert np.allclose(got[:3], F, atol=1e-12)
+
+
+@pytest.mark.parametrize("theta_deg", [20.0, 55.0])
+def test_tilted_plate_statistical(theta_deg):
+    """Tilted plate with stratified jitter: estimator agrees with
+    P A cos [(1-rs) d - (2 rs cos + 2/3 rd) n] within 4 sigma."""
+    p = W.flat_plate((2.0, 1.0), 2)
+    rho = np.array([[0.25, 0.35]])
+    th = math.radians(theta_deg)
+    e = np.array([math.sin(th), 0.3 * math.sin(th), math.cos(th)])
+    e /= np.linalg.norm(e)
+    ft, sg = oracle.force(p.verts, p.tris, p.group, rho, e, np.zeros(3), nx=256, K=1, seed=11)
+    ref = oracle.facet_law(p.verts, p.tris, p.group, rho, e, np.zeros(3))
+    ok, r = _stat_ok(ft[0, :3], ref[:3], sg[0, :3], 0)
+    assert ok, r
+
+
+# ---------------------------------------------------------------- convex bodies
+def test_box_per_facet_law_and_bounce_invariance():
+    """Convex box: K=1 matches the per-facet law (4 sigma); K=3 agrees with
+    K=1 in expectation (reflected rays never re-hit a convex body)."""
+    bv, bt = W.axis_box((0.1, -0.2, 0.3), (0.5, 0.7, 1.1), 0)
+    verts = bv.astype(np.float32); tris = bt.astype(np.int32)
+    group = np.arange(12, dtype=np.int32) // 2
+    rho = W.random_reflectances(6, seed=4)
+    e = np.array([0.3, -0.5, 0.8]); e /= np.linalg.norm(e)
+    com = np.array([0.0, 0.1, 0.0])
+    f1, s1 = oracle.force(verts, tris, group, rho, e, com, nx=256, K=1, seed=1)
+    f3, s3 = oracle.force(verts, tris, group, rho, e, com, nx=256, K=3, seed=2)
+    ref = oracle.facet_law(verts, tris, group, rho, e, com)
+    ok, r = _stat_ok(f1[0], ref, s1[0], 0)
+    assert ok, r
+    ok, r = _stat_ok(f3[0], f1[0], s3[0], s1[0])
+    assert ok, r
+
+
+def test_icosphere_cannonball():
+    """Icosphere -> sphere: per-facet law converges to the cannonball force
+    P pi R^2 (1 + 4 rd/9) d (specular adds nothing on a sphere), torque 0;
+    the MC estimate agrees with the facet law."""
+    e = np.array([0.2, 0.4, -0.9]); e /= np.linalg.norm(e)
+    rs, rd = 0.3, 0.4
+    rho = np.array([[rs, rd]])
+    errs, terrs = [], []
+    for s in (1, 2, 3):
+        m = W.icosphere(s)
+        F = oracle.facet_law(m.verts, m.tris, m.group, rho, e, np.zeros(3))
+        ball = math.pi * (1 + 4 * rd / 9) * (-e)
+        errs.append(np.linalg.norm(F[:3] - ball) / np.linalg.norm(ball))
+        terrs.append(np.linalg.norm(F[3:]) / np.linalg.norm(ball))
+    assert errs[2] < 0.02 and errs[1] < 0.6 * errs[0] and errs[2] < 0.6 * errs[1], errs
+    assert terrs[2] < 1e-3 and terrs[2] < terrs[0], terrs
+    m = W.icosphere(2)
+    ft, sg = oracle.force(m.verts, m.tris, m.group, rho, e, np.zeros(3), nx=192, K=1, seed=5)
+    ref = oracle.facet_law(m.verts, m.tris, m.group, rho, e, np.zeros(3))
+    ok, r = _stat_ok(ft[0], ref, sg[0], 0)
+    assert ok, r
+
+
+def test_all_absorber_counts_hits():
+    """All-absorber body: F = P a (number of rays hitting) d, so F/(P a) is an
+    integer vector multiple of d."""
+    m = W.box_wing()
+    rho = np.zeros((64, 2))
+    e = W.SUN_C1
+    nx = 128
+    ft, _ = oracle.force(m.verts, m.tris, m.group, rho, e, np.zeros(3), nx=nx, K=1, seed=3)
+    c, R = oracle.grid(m.verts)
+    a = (2 * R / nx) ** 2
+    cnt = -ft[0, :3] / e / a
+    assert np.allclose(cnt, cnt[0], rtol=1e-9)
+    assert abs(cnt[0] - round(cnt[0])) < 1e-6 and cnt[0] > 100
+
+
+def test_v_groove_retroreflector_multibounce():
+    """90-degree mirror V-groove lit along its bisector: every entering ray is
+    reflected twice and leaves reversed, so the expected force is
+    2 P A_aperture d.  Exercises the sampled-branch bounce path (K=3)."""
+    L, a = 1.0, 1.0
+    s = a / math.sqrt(2)
+    # walls through the x axis (groove axis), opening toward +z
+    v = np.array([[-L / 2, 0, 0], [L / 2, 0, 0], [L / 2, s, s], [-L / 2, s, s],
+                  [-L / 2, -s, s], [L / 2, -s, s]], dtype=np.float32)
+    t = np.array([[0, 1, 2], [0, 2, 3], [0, 4, 5], [0, 5, 1]], dtype=np.int32)
+    g = np.zeros(4, np.int32)
+    rho = np.array([[1.0, 0.0]])
+    e = np.array([0, 0, 1.0])
+    ft, sg = oracle.force(v, t, g, rho, e, np.zeros(3), nx=256, K=3, seed=9)
+    ap = L * 2 * s
+    ref = 2 * ap * (-e)
+    ok, r = _stat_ok(ft[0, :3], ref, sg[0, :3], 0, k=4.0, floor=3e-3 * np.linalg.norm(ref))
+    assert ok, (ft[0, :3], ref, sg[0, :3])
+    # K=2 closes the second hit with the expected reflection: same mean
+    f2, s2 = oracle.force(v, t, g, rho, e, np.zeros(3), nx=256, K=2, seed=10)
+    ok, r = _stat_ok(f2[0, :3], ref, s2[0, :3], 0, k=4.0, floor=3e-3 * np.linalg.norm(ref))
+    assert ok, (f2[0, :3], ref)
+
+
+def test_boxwing_mirror_symmetry():
+    """Box-wing with one material and the sun in the x-z plane is mirror
+    symmetric in y: F_y, tau_x, tau_z vanish (4 sigma)."""
+    m = W.box_wing()
+    rho = np.tile(np.array([[0.2, 0.3]], np.float32), (64, 1))
+    e = np.array([0.4, 0.0, 0.9]); e /= np.linalg.norm(e)
+    ft, sg = oracle.force(m.verts, m.tris, m.group, rho, e, np.zeros(3), nx=256, K=3, seed=21)
+    for j in (1, 3, 5):
+        assert abs(ft[0, j]) <= 4 * sg[0, j] + 1e-9 * np.linalg.norm(ft[0, :3]), (j, ft[0], sg[0])
+
+
+def test_rotation_equivariance():
+    """Rotating the mesh and the sun together rotates F and tau (4 sigma)."""
+    m = W.box_wing()
+    rho = W.random_reflectances(64, seed=0)
+    e = W.SUN_C1
+    Rm = oracle.rotation(np.array([1.0, 1.0, 0.0]) / math.sqrt(2), 0.7)
+    v2 = (m.verts.astype(np.float64) @ Rm.T).astype(np.float32)
+    f1, s1 = oracle.force(m.verts, m.tris, m.group, rho, e, np.zeros(3), nx=256, K=2, seed=1)
+    f2, s2 = oracle.force(v2, m.tris, m.group, rho, Rm @ e, np.zeros(3), nx=256, K=2, seed=2)
+    rot = np.concatenate([Rm @ f1[0, :3], Rm @ f1[0, 3:]])
+    srot = np.concatenate([np.abs(Rm) @ s1[0, :3], np.abs(Rm) @ s1[0, 3:]])
+    ok, r = _stat_ok(f2[0], rot, s2[0], srot)
+    assert ok, r
+
+
+def test_mc_convergence_rate():
+    """Error of the sampled-bounce estimate falls like N^-1/2: log-log slope
+    of the RMS error over seeds vs the ray count in [-0.6, -0.4]."""
+    L, a = 1.0, 1.0
+    s = a / math.sqrt(2)
+    v = np.array([[-L / 2, 0, 0], [L / 2, 0, 0], [L / 2, s, s], [-L / 2, s, s],
+                  [-L / 2, -s, s], [L / 2, -s, s]], dtype=np.float32)
+    t = np.array([[0, 1, 2], [0, 2, 3], [0, 4, 5], [0, 5, 1]], dtype=np.int32)
+    g = np.zeros(4, np.int32)
+    rho = np.array([[0.4, 0.5]])
+    e = np.array([0.1, 0.2, 1.0]); e /= np.linalg.norm(e)
+    ref, _ = oracle.force(v, t, g, rho, e, np.zeros(3), nx=1024, K=3, seed=1000)
+    ns, errs = [], []
+    for nx in (32, 64, 128, 256):
+        err = []
+        for sd in range(12):
+            f, _ = oracle.force(v, t, g, rho, e, np.zeros(3), nx=nx, K=3, seed=sd)
+            err.append(np.sum((f[0, :3] - ref[0, :3]) ** 2))
+        ns.append(nx * nx); errs.append(math.sqrt(np.mean(err)))
+    slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert -0.6 <= slope <= -0.4, (slope, errs)
+
+
+def test_sigma_matches_seed_spread():
+    """The collapsed-strata sigma is consistent with the spread of the
+    estimate over independent seeds (it may only over-estimate mildly)."""
+    m = W.box_wing()
+    rho = W.random_reflectances(64, seed=0)
+    fs, ss = [], []
+    for sd in range(16):
+        f, s = oracle.force(m.verts, m.tris, m.group, rho, W.SUN_C1, np.zeros(3), nx=96, K=3, seed=100 + sd)
+        fs.append(f[0]); ss.append(s[0])
+    spread = np.std(np.asarray(fs), axis=0, ddof=1)
+    sig = np.mean(np.asarray(ss), axis=0)
+    ratio = sig[:3] / spread[:3]
+    assert np.all((ratio > 0.6) & (ratio < 2.5)), ratio
+
+
+# ---------------------------------------------------------------- reductions
+def test_ray_subset_consistent():
+    """A ray subset (offset, stride) traced in four parts sums to the full
+    grid; thread count does not change the result."""
+    m = W.box_wing()
+    rho = W.random_reflectances(64, seed=0)
+    nx = 64
+    f, s = oracle.force(m.verts, m.tris, m.group, rho, W.SUN_C1, np.zeros(3), nx=nx, K=3)
+    f1, s1 = oracle.force(m.verts, m.tris, m.group, rho, W.SUN_C1, np.zeros(3), nx=nx, K=3, threads=1)
+    assert np.array_equal(f, f1) and np.array_equal(s, s1)
+    parts = [oracle.force(m.verts, m.tris, m.group, rho, W.SUN_C1, np.zeros(3), nx=nx, K=3,
+                          ray_offset=o, ray_stride=4, ray_count=nx * nx // 4)[0] for o in range(4)]
+    assert np.allclose(sum(parts), f, rtol=1e-12, atol=1e-15)
