@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark of the SRP ray-grid tracer on GB300.
+
+Workload (one "step"): the ~50k-triangle procedural satellite (bus, two
+panels, 47,360-triangle paraboloid dish, 200 random boxes; 64 material
+groups, rho ~ U[0,0.5]), 4096 Fibonacci sun directions x a 2048 x 2048
+parallel-ray grid (4,194,304 primary rays per direction), up to 3 bounces,
+FP32 per ray with FP64 sums: one srp_force call = 17.2 G primary rays.
+Metric: primary rays per second (all bounces of each ray included).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run, one rank per GPU; the sun
+directions are independent, so each rank traces its own 4096 directions
+(sun_base = rank * 4096; weak scaling, no data-path collective).
+--impl reference times the FP64 CPU oracle (brute force, no BVH) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_SUN = 4096
+NX = 2048
+K_BOUNCE = 3
+WORKLOAD = "procedural satellite 49,776 tris, 64 groups, 4096 Fibonacci suns x 2048^2 rays, K<=3"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(ws, x):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU oracle leg (the reference arm and the cpu_baseline)
+# --------------------------------------------------------------------------
+def oracle_sample(m, rho, sun, com, n_sun, n_rays):
+    """Time the FP64 oracle on a bounded sample: n_sun directions x n_rays
+    rays of the full 2048^2 grid (evenly strided)."""
+    import oracle
+    stride = (NX * NX) // n_rays
+    t0 = time.perf_counter()
+    for s in range(n_sun):
+        oracle.force(m.verts, m.tris, m.group, rho, sun[s * (N_SUN // n_sun)], com, nx=NX, K=K_BOUNCE,
+                     ray_offset=0, ray_stride=stride, ray_count=n_rays, sun_base=s)
+    dt = time.perf_counter() - t0
+    return n_sun * n_rays / dt, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    m, rho, sun, com = W.config2(N_SUN)
+    cores = os.cpu_count() or 1
+    n_sun, n_rays = 1, 4096
+    for _ in range(args.warmup):
+        oracle_sample(m, rho, sun, com, n_sun, 1024)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample(m, rho, sun, com, n_sun, n_rays)
+        times.append(dt)
+    value = args.steps * n_sun * n_rays / sum(times)
+    sample = f"{n_sun} sun direction x {n_rays} rays (every {NX * NX // n_rays}th ray of the 2048^2 grid) per step"
+    line = {"impl": "reference", "metric": "rays/s", "value": value, "unit": "rays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "FP64 brute-force CPU oracle (no BVH), host cores"},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU leg
+# --------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_2602_10712_gb300 as srp
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = srp.Context(local, stream)
+    m, rho, _, com = W.config2(N_SUN)
+    sun = W.fibonacci_directions(N_SUN)
+    t0 = time.perf_counter()
+    bvh = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, args.width)
+    info = bvh.info()
+    build_ms = (time.perf_counter() - t0) * 1e3
+    r_t = torch.from_numpy(rho[None].copy()).to(dev)
+    s_t = torch.from_numpy(sun.copy()).to(dev)
+    c_t = torch.from_numpy(com[None].copy()).to(dev)
+    out = torch.empty((1, N_SUN, 6), dtype=torch.float64, device=dev)
+    sig = torch.empty((1, N_SUN, 6), dtype=torch.float64, device=dev)
+    sun_base = rank * N_SUN
+    kw = dict(rays_x=NX, max_bounces=K_BOUNCE, seed=0, sun_base=sun_base, block_threads=args.block)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def step():
+        srp.srp_force(ctx, [bvh], r_t, s_t, c_t, out_ft=out, out_sigma=sig, **kw)
+
+    # traversal counters on a strided sample of the same workload (outside timing)
+    srp.srp_collect_stats(ctx, True)
+    samp_rays = 65536
+    srp.srp_force(ctx, [bvh], r_t, s_t[::16].contiguous(), c_t, ray_offset=0, ray_stride=(NX * NX) // samp_rays,
+                  ray_count=samp_rays, **{k: v for k, v in kw.items() if k != "sun_base"})
+    vis, tests, segs = srp.srp_collect_stats(ctx, False)
+    n_samp = samp_rays * (N_SUN // 16)
+    node_bytes = 128 if args.width == 4 else 256
+    bytes_per_ray = (vis * node_bytes + tests * 48) / n_samp
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # timed: K steps, each bracketed by events on the launching stream; L2
+    # flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    t_max = allmax(ws, t_dev)
+    rays_step = N_SUN * NX * NX
+    value = ws * rays_step * args.steps / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+
+    # e2e: the public host-buffer call (copies in and out inside the call)
+    rho_h = rho[None].copy(); sun_h = sun.copy(); com_h = com[None].copy()
+    out_h = np.zeros((1, N_SUN, 6)); sig_h = np.zeros((1, N_SUN, 6))
+    srp.srp_force(ctx, [bvh], rho_h, sun_h, com_h, out_ft=out_h, out_sigma=sig_h, **kw)  # warm
+    barrier(ws)
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        srp.srp_force(ctx, [bvh], rho_h, sun_h, com_h, out_ft=out_h, out_sigma=sig_h, **kw)
+    te = time.perf_counter() - te
+    te = allmax(ws, te)
+    e2e = ws * rays_step * args.steps / te
+    h2d = rho_h.nbytes + sun_h.nbytes + com_h.nbytes
+    d2h = out_h.nbytes + sig_h.nbytes
+
+    # roofline: dominant kernel (trace_kernel) against the FP32 issue peak
+    peaks, src = _peaks()
+    sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    ops_node = 4 * 14 if args.width == 4 else 8 * 14
+    ops_tri = 44
+    ops_per_ray = (vis * ops_node + tests * ops_tri) / n_samp
+    achieved = ops_per_ray * rays_step / (t_dev / args.steps) / 1e12
+    peak_alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    line = {
+        "metric": "rays/s", "value": value, "unit": "rays/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays_per_step": rays_step * ws, "bvh_width": args.width,
+                   "block_threads": args.block, "l2": "flushed between timed steps (512 MB write)",
+                   "bvh_build_ms": build_ms, "bvh_nodes": info["n_nodes"], "parallelism": f"replicas x{ws}"},
+        "force_evals_per_s": ws * N_SUN * args.steps / t_max,
+        "e2e": {"value": e2e, "unit": "rays/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                     "frac": achieved / peak_alu, "traffic": None,
+                     "note": (f"trace_kernel FP32 lane-ops: {ops_per_ray:.0f}/ray = node visits x {ops_node} + "
+                              f"triangle tests x {ops_tri}; peak = {n_sm} SM x 128 FP32 lanes x {sm_mhz:.0f} MHz; "
+                              f"algorithmic bytes {bytes_per_ray:.0f} B/ray from L1/L2 (scene {info['device_bytes']} B)"),
+                     "peaks_source": src},
+        "traversal": {"node_visits_per_ray": vis / n_samp, "tri_tests_per_ray": tests / n_samp,
+                      "segments_per_ray": segs / n_samp, "bytes_per_ray": bytes_per_ray},
+        "clocks": ck,
+    }
+    if rank == 0 and not args.no_cpu:
+        m_, rho_, sun_, com_ = m, rho, sun, com
+        val, dt = oracle_sample(m_, rho_, sun_, com_, 2, 4096)
+        line["cpu_baseline"] = {"value": val, "unit": "rays/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                                "sample": "2 sun directions x 4096 rays (strided over the 2048^2 grid), K<=3",
+                                "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--width", type=int, default=4)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * srp.h -- C ABI of the GB300 (sm_103a) solar-radiation-pressure library.
+ *
+ * The library computes, for triangulated spacecraft designs lit by the sun
+ * from direction w (a unit vector TOWARD the sun), the net radiation force
+ *   F(w, theta)   = integral over the surface M(theta) of f(x, w, theta) dx
+ * and torque about the centre of mass
+ *   tau(w, theta) = integral over M of (x - x_COM(theta)) x f(x, w, theta) dx
+ * (paper, Sec. 3.2, the force-field integral Eq. "Force" and the two surface
+ * integrals after it), where the force field f converts the radiance arriving
+ * at x into force through the light-to-force map l2f (Sec. 3.2): photons
+ * transfer their momentum when they arrive and reflected photons carry
+ * momentum away.  Units: with pressure P in N/m^2 and lengths in metres,
+ * F is in N and tau in N m.  P = 1 gives "unit radiation" (Sec. 3.3).
+ *
+ * Estimator.  A grid of parallel rays covers the square of side 2R centred on
+ * the design's vertex-AABB centre c, R = max |vertex - c|, in the plane normal
+ * to the travel direction d = -w.  Ray i = py*rays_x + px starts at pixel
+ * (px, py) jittered by (xi1, xi2) from Philox4x32-10 with counter
+ * (i, sun index, design index, 0) and key (seed lo, seed hi), and carries
+ * momentum weight w0 = P dx dy.  Closest hits are found through a wide BVH.
+ * At hit k of at most K = max_bounces (normal n flipped to face the ray,
+ * cos = -n.d, reflectances (rho_s, rho_d) of the triangle's material group):
+ *   k == K : deposit w [(1 - rho_s) d - (2 rho_s cos + 2/3 rho_d) n]
+ *            (the expected reflection: the per-plate law of Sec. 2.1)
+ *   k <  K : with probability 1/2 reflect specularly (weight 2 w rho_s),
+ *            else diffusely with a cosine-weighted direction (weight
+ *            2 w rho_d), deposit w d - w' d', and trace on (Philox counter
+ *            (i, sun, design, k)).
+ * The torque deposit is (x - COM) x deposit.  The branch probability does
+ * not depend on rho, so results are polynomials in rho along fixed paths.
+ * Sums are FP64; sigma is the collapsed-strata standard error (neighbouring
+ * rays k = 2j, 2j+1 paired: var = sum (y_2j - y_2j+1)^2).
+ *
+ * Conventions.
+ *  - Every function returns an int status (SRP_OK on success).  The message
+ *    of the last failure on the calling thread is srp_last_error().
+ *  - All calls are asynchronous on the context's CUDA stream unless their
+ *    buffers are host memory (mem = SRP_MEM_HOST), in which case they copy
+ *    in, compute, copy out and synchronise before returning.
+ *  - The caller owns every array argument; the library owns the opaque
+ *    handles (srp_ctx, srp_bvh) and frees them in srp_*_destroy.
+ *  - Device-side failures (a traversal stack overflow or a visit cap hit on
+ *    a corrupted BVH) set a flag that the next srp_sync() (or any HOST-mem
+ *    call) reports as SRP_EDEVICE_LIMIT.  No kernel traps or spins forever.
+ */
+#ifndef SRP_H
+#define SRP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SRP_OK 0
+#define SRP_EINVAL 1          /* invalid argument (message says which)      */
+#define SRP_ENOMEM 2          /* host or device allocation failed           */
+#define SRP_ECUDA 3           /* a CUDA runtime call failed                 */
+#define SRP_EDEVICE_LIMIT 4   /* a bounded device loop hit its limit        */
+#define SRP_ETIMEOUT 5        /* a bounded device wait gave up              */
+#define SRP_EUNSUPPORTED 6    /* valid request this build does not support  */
+
+typedef enum { SRP_MEM_HOST = 0, SRP_MEM_DEVICE = 1 } srp_mem;
+
+typedef struct srp_ctx srp_ctx;
+typedef struct srp_bvh srp_bvh;
+
+/* Options of one force evaluation.  srp_trace_opts_default() fills the
+ * defaults shown in brackets. */
+typedef struct srp_trace_opts {
+    int32_t rays_x, rays_y;   /* ray grid resolution [1024 x 1024]          */
+    int32_t max_bounces;      /* K in 1..3 [1]                              */
+    int32_t jitter;           /* 1 stratified jitter, 0 pixel centres [1]  */
+    uint64_t seed;            /* Philox key [0]                             */
+    double pressure;          /* P in N/m^2 [1.0 = unit radiation]          */
+    int64_t ray_offset;       /* ray subset: trace i = off + k*stride for   */
+    int64_t ray_stride;       /*   k < ray_count; ray_count 0 = whole grid  */
+    int64_t ray_count;        /*   [0, 1, 0]                                */
+    int32_t sun_base;         /* added to the sun index in the RNG counter  */
+    int32_t design_base;      /* added to the design index in the counter   */
+    int32_t mem;              /* srp_mem of rho/sun_dir/com/outputs [DEVICE]*/
+    int32_t sun_per_design;   /* 1: sun_dir is [D][S][3], 0: [S][3] [0]     */
+    int32_t block_threads;    /* 0 = autotuned; else 128 or 256             */
+    int32_t chunks_per_item;  /* 0 = automatic; else ray chunks per item    */
+} srp_trace_opts;
+
+/* ---- context ----------------------------------------------------------- */
+const char* srp_last_error(void);
+void srp_trace_opts_default(srp_trace_opts* o);
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+int srp_ctx_create(srp_ctx** out, int device, void* cuda_stream);
+int srp_ctx_destroy(srp_ctx* ctx);
+/* Wait for the context's stream; report deferred device errors. */
+int srp_sync(srp_ctx* ctx);
+
+/* Traversal work counters of the tracer kernels on this context (for the
+ * roofline's algorithmic work): out[0] BVH node visits, out[1] ray/triangle
+ * tests, out[2] ray segments traced.  Synchronises the stream, copies the
+ * counters accumulated since the previous call into `out` (if not NULL),
+ * zeroes them, and turns collection on (enable != 0) or off for later
+ * launches.  The kernels count in registers either way; only the final
+ * per-warp atomic adds depend on `enable`. */
+int srp_collect_stats(srp_ctx* ctx, int enable, uint64_t out[3]);
+
+/* ---- design instantiation (Sec. 3.2: "a mapping from design parameters to
+ * triangle meshes") ------------------------------------------------------- */
+/* Rotate every vertex v with vhinge[v] = h >= 0 about hinge h's axis
+ * (hinges[h] = point p (3) then unit axis a (3), right-hand rule) by
+ * angles[h]:  v' = p + Rot(a, angle)(v - p).  Host arrays:
+ * verts_in/out [V][3] float32 (may alias), vhinge [V], hinges [H][6],
+ * angles [H].  Pure host code; no device work. */
+int srp_design_instantiate(const float* verts_in, int V, const int32_t* vhinge,
+                           const double* hinges, const double* angles, int H,
+                           float* verts_out);
+
+/* ---- acceleration structure ------------------------------------------- */
+/* Build a BVH of `width` (4 or 8) children per node over one design's
+ * triangles (binned SAH on the host, collapsed to a wide SoA layout) and
+ * upload triangles and nodes to the context's device.  Host arrays:
+ * verts [V][3] float32 (world frame), tris [T][3] int32 vertex indices,
+ * group [T] int32 material group (0 <= group < 64).  T may be 0.
+ * The handle keeps the grid centre c and radius R of the design. */
+int srp_build_bvh(srp_ctx* ctx, const float* verts, int V, const int32_t* tris,
+                  const int32_t* group, int T, int width, srp_bvh** out);
+int srp_bvh_destroy(srp_bvh* bvh);
+
+typedef struct srp_bvh_info {
+    int32_t width, n_nodes, n_leaves, depth, n_tris;
+    int64_t device_bytes;     /* nodes + triangles on the device            */
+    double build_ms;          /* host build time                             */
+    double center[3], radius; /* ray-grid centre c and radius R              */
+} srp_bvh_info;
+int srp_bvh_get_info(const srp_bvh* bvh, srp_bvh_info* info);
+
+/* Host-only build of the same wide BVH, for inspection and serialisation
+ * (no device, no context).  Two-call pattern: with node_data == NULL it
+ * stores the sizes in *n_node_floats and *n_nodes and returns.  Otherwise
+ * node_data [*n_node_floats] receives the node array (layout: per node,
+ * 6*W floats of child bounds lo_x[W] hi_x[W] lo_y[W] hi_y[W] lo_z[W] hi_z[W],
+ * then W int32 child codes: >= 0 inner node index, < 0 leaf with
+ * ~code = first << 3 | (count-1) into the leaf-order triangle list, then
+ * padding to 128 B (W=4) or 256 B (W=8)), and tri_order [T] the original
+ * triangle index of each leaf-order slot. */
+int srp_build_bvh_host(const float* verts, int V, const int32_t* tris, int T, int width,
+                       float* node_data, int64_t* n_node_floats, int32_t* tri_order, int32_t* n_nodes);
+
+/* ---- force and torque (Sec. 3.2) ---------------------------------------- */
+/* For D designs (bvhs[d], built on this context) and S sun directions:
+ *   rho      [D][G][2] float32  (rho_s, rho_d) per material group, each in
+ *                               [0,1] with rho_s + rho_d <= 1; G <= 64
+ *   sun_dir  [S][3] (or [D][S][3] with opts->sun_per_design) float64 unit
+ *                               vectors toward the sun
+ *   com      [D][3] float64     torque reference point (centre of mass)
+ *   out_ft   [D][S][6] float64  (F, tau)
+ *   out_sigma[D][S][6] float64  standard errors, or NULL
+ * Array memory is opts->mem (all host or all device).  Device-mem calls are
+ * asynchronous; the scratch they use belongs to the context, so calls on
+ * one context must not overlap on different streams.  Validation of rho
+ * and sun_dir values happens only for host-mem calls. */
+int srp_force(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+              const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
+              double* out_ft, double* out_sigma);
+
+/* Per-ray inspection (the estimator's individual samples): trace the n
+ * grid rays ray_idx[n] (int64, each < rays_x*rays_y) of ONE design and ONE
+ * sun direction with the same arithmetic as srp_force.
+ *   rho [G][2] float32, sun_dir [3] float64, com [3] float64
+ *   sun_index, design_index: the indices used in the Philox counter
+ *   out_y    [n][6] float64: the ray's force and torque deposits
+ *   out_hits [n][K] int32: original index of the triangle hit at each
+ *            bounce (-1 when the path has ended), K = opts->max_bounces
+ * Memory per opts->mem.  ray_offset/stride/count and sun_per_design in
+ * opts are ignored. */
+int srp_trace_rays(srp_ctx* ctx, const srp_bvh* bvh, const float* rho, int G, const double* sun_dir,
+                   const double* com, const int64_t* ray_idx, int64_t n, int sun_index, int design_index,
+                   const srp_trace_opts* opts, double* out_y, int32_t* out_hits);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SRP_H */

@@ -71,6 +71,9 @@ def _load():
                                                P, P, P, i32, f64, P]
         lib.or_primary_hit.argtypes = [P, i32, P, i32, P, i32, i32, i32, u64, u32, u32, i64, P]
         lib.or_primary_hit.restype = i32
+        lib.or_trace_rays.argtypes = [P, i32, P, P, i32, P, P, P, i32, i32, i32, i32, u64, f64,
+                                      u32, u32, P, i64, P, P, i32]
+        lib.or_trace_rays.restype = i32
         _lib = lib
     return _lib
 
@@ -166,6 +169,24 @@ def hinge_fd_fixed_hits(verts, tris, group, rho, sun, com, upstream, tri_hinge, 
                                _p(s), s.shape[0], _p(cm), nx, ny, jitter, seed, P,
                                _p(up), _p(th), _p(ha), ha.shape[0], h, _p(out))
     return out
+
+
+def trace_rays(verts, tris, group, rho, sun, com, ray_idx, *, nx, ny=None, K=1, jitter=1, seed=0,
+               P=1.0, sun_index=0, design_index=0, threads=None):
+    """Per-ray samples: (y [n,6] force/torque deposits, hits [n,K] original
+    triangle index per bounce, -1 after the path ends)."""
+    lib = _load()
+    ny = nx if ny is None else ny
+    v = _c(verts, np.float32); t = _c(tris, np.int32); g = _c(group, np.int32)
+    r = _c(rho, np.float64); s = _c(sun, np.float64).reshape(3); cm = _c(com, np.float64)
+    idx = _c(ray_idx, np.int64)
+    y = np.zeros((idx.shape[0], 6)); h = np.zeros((idx.shape[0], K), np.int32)
+    rc = lib.or_trace_rays(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(s), _p(cm),
+                           nx, ny, K, jitter, seed, P, sun_index, design_index, _p(idx), idx.shape[0],
+                           _p(y), _p(h), threads or os.cpu_count() or 1)
+    if rc != 0:
+        raise ValueError("oracle trace_rays: bad arguments")
+    return y, h
 
 
 def primary_hit(verts, tris, sun, i, *, nx, ny=None, jitter=1, seed=0, sun_index=0, design_index=0):

@@ -605,3 +605,61 @@ int or_primary_hit(const float* verts, int V, const int32_t* tris, int T, const 
     free(tv); free(tn);
     return f;
 }
+
+/* Per-ray samples: for each listed grid ray index, the ray's force and
+ * torque deposits out_y [n][6] and the original index of the triangle hit
+ * at each bounce out_hits [n][K] (-1 after the path ends). */
+typedef struct {
+    const scene_t* sc;
+    const double* sun;
+    uint32_t sun_idx;
+    const int64_t* idx;
+    int64_t q0, q1;
+    double* out_y;
+    int32_t* out_hits;
+} rays_job;
+
+static void* rays_worker(void* arg)
+{
+    rays_job* j = (rays_job*)arg;
+    path_t p;
+    const int K = j->sc->K;
+    for (int64_t q = j->q0; q < j->q1; ++q) {
+        double y[6] = {0, 0, 0, 0, 0, 0};
+        trace_path(j->sc, j->sun, (uint64_t)j->idx[q], j->sun_idx, y, &p);
+        for (int c = 0; c < 6; ++c) j->out_y[6 * q + c] = y[c];
+        for (int k = 0; k < K; ++k) j->out_hits[q * K + k] = k < p.m ? p.f[k] : -1;
+    }
+    return NULL;
+}
+
+int or_trace_rays(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
+                  const double* rho, const double* sun, const double* com,
+                  int nx, int ny, int K, int jitter, uint64_t seed, double P,
+                  uint32_t sun_idx, uint32_t dsg, const int64_t* idx, int64_t n,
+                  double* out_y, int32_t* out_hits, int threads)
+{
+    if (K < 1 || K > 8) return 1;
+    double* tv = (double*)malloc(sizeof(double) * 9 * (size_t)(T > 0 ? T : 1));
+    double* tn = (double*)malloc(sizeof(double) * 3 * (size_t)(T > 0 ? T : 1));
+    scene_t sc;
+    memset(&sc, 0, sizeof sc);
+    build_scene(&sc, tv, tn, verts, V, tris, T);
+    sc.group = group; sc.rho = rho;
+    for (int j = 0; j < 3; ++j) sc.com[j] = com[j];
+    sc.P = P; sc.nx = nx; sc.ny = ny; sc.K = K; sc.jitter = jitter; sc.seed = seed; sc.dsg = dsg;
+    if (threads < 1) threads = 1;
+    if (threads > n) threads = n > 0 ? (int)n : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * threads);
+    rays_job* jb = (rays_job*)calloc(threads, sizeof(rays_job));
+    for (int t = 0; t < threads; ++t) {
+        jb[t].sc = &sc; jb[t].sun = sun; jb[t].sun_idx = sun_idx; jb[t].idx = idx;
+        jb[t].q0 = n * t / threads; jb[t].q1 = n * (t + 1) / threads;
+        jb[t].out_y = out_y; jb[t].out_hits = out_hits;
+    }
+    for (int t = 1; t < threads; ++t) pthread_create(&th[t], NULL, rays_worker, &jb[t]);
+    rays_worker(&jb[0]);
+    for (int t = 1; t < threads; ++t) pthread_join(th[t], NULL);
+    free(jb); free(th); free(tv); free(tn);
+    return 0;
+}

@@ -1,0 +1,298 @@
+"""Python binding of libsrp (include/srp.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module
+converts numpy arrays / torch tensors to pointers, checks shapes and dtypes,
+and raises on a non-zero status.  If the library cannot be loaded it raises:
+there is no CPU fallback.
+
+Names follow the C ABI: srp_ctx_create, srp_build_bvh, srp_force, ...
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
+           "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
+           "srp_build_bvh_host", "srp_trace_rays",
+           "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
+
+SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_EDEVICE_LIMIT, SRP_ETIMEOUT, SRP_EUNSUPPORTED = range(7)
+SRP_MEM_HOST, SRP_MEM_DEVICE = 0, 1
+_STATUS = {1: "SRP_EINVAL", 2: "SRP_ENOMEM", 3: "SRP_ECUDA", 4: "SRP_EDEVICE_LIMIT",
+           5: "SRP_ETIMEOUT", 6: "SRP_EUNSUPPORTED"}
+
+
+class SRPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class TraceOpts(C.Structure):
+    _fields_ = [("rays_x", C.c_int32), ("rays_y", C.c_int32), ("max_bounces", C.c_int32),
+                ("jitter", C.c_int32), ("seed", C.c_uint64), ("pressure", C.c_double),
+                ("ray_offset", C.c_int64), ("ray_stride", C.c_int64), ("ray_count", C.c_int64),
+                ("sun_base", C.c_int32), ("design_base", C.c_int32), ("mem", C.c_int32),
+                ("sun_per_design", C.c_int32), ("block_threads", C.c_int32),
+                ("chunks_per_item", C.c_int32)]
+
+
+class BVHInfo(C.Structure):
+    _fields_ = [("width", C.c_int32), ("n_nodes", C.c_int32), ("n_leaves", C.c_int32),
+                ("depth", C.c_int32), ("n_tris", C.c_int32), ("device_bytes", C.c_int64),
+                ("build_ms", C.c_double), ("center", C.c_double * 3), ("radius", C.c_double)]
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def load(build_if_needed: bool = True):
+    """Load libsrp.so (building it with nvcc first if it is missing/stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_needed else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libsrp.so not found at {path}: run __graft_entry__.build()")
+    lib = C.CDLL(path, mode=C.RTLD_GLOBAL)
+    i32, i64 = C.c_int, C.c_int64
+    lib.srp_last_error.restype = C.c_char_p
+    lib.srp_trace_opts_default.argtypes = [C.POINTER(TraceOpts)]
+    lib.srp_ctx_create.argtypes = [C.POINTER(_P), i32, _P]
+    lib.srp_ctx_destroy.argtypes = [_P]
+    lib.srp_sync.argtypes = [_P]
+    lib.srp_design_instantiate.argtypes = [_P, i32, _P, _P, _P, i32, _P]
+    lib.srp_build_bvh.argtypes = [_P, _P, i32, _P, _P, i32, i32, C.POINTER(_P)]
+    lib.srp_bvh_destroy.argtypes = [_P]
+    lib.srp_bvh_get_info.argtypes = [_P, C.POINTER(BVHInfo)]
+    lib.srp_force.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P]
+    lib.srp_collect_stats.argtypes = [_P, i32, _P]
+    lib.srp_build_bvh_host.argtypes = [_P, i32, _P, i32, i32, _P, C.POINTER(C.c_int64), _P, C.POINTER(C.c_int32)]
+    lib.srp_trace_rays.argtypes = [_P, _P, _P, i32, _P, _P, _P, i64, i32, i32, C.POINTER(TraceOpts), _P, _P]
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != SRP_OK:
+        raise SRPError(rc, _lib.srp_last_error().decode(errors="replace"))
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _ptr(a):
+    """Pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(_P)
+    return _P(a.data_ptr())
+
+
+# ----------------------------------------------------------------- context
+class Context:
+    """An srp_ctx bound to one device and one CUDA stream (a torch stream or
+    a raw cudaStream_t integer; default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.device = device
+        self.stream = int(stream)
+        h = _P()
+        _check(lib.srp_ctx_create(C.byref(h), device, _P(self.stream)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.srp_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def srp_ctx_create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def srp_ctx_destroy(ctx: Context):
+    ctx.close()
+
+
+def srp_sync(ctx: Context):
+    _check(load().srp_sync(ctx.handle))
+
+
+class BVH:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.srp_bvh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return srp_bvh_get_info(self)
+
+
+def srp_collect_stats(ctx: Context, enable: bool = True):
+    """Counters since the last call: (node visits, triangle tests, segments)."""
+    out = np.zeros(3, np.uint64)
+    _check(load().srp_collect_stats(ctx.handle, 1 if enable else 0, _ptr(out)))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def srp_design_instantiate(verts, vhinge, hinges, angles):
+    lib = load()
+    v = _np(verts, np.float32)
+    out = np.empty_like(v)
+    vh = _np(vhinge, np.int32)
+    hg = _np(hinges, np.float64).reshape(-1, 6)
+    an = _np(angles, np.float64).reshape(-1)
+    _check(lib.srp_design_instantiate(_ptr(v), v.shape[0], _ptr(vh), _ptr(hg), _ptr(an), hg.shape[0], _ptr(out)))
+    return out
+
+
+def srp_build_bvh(ctx: Context, verts, tris, group, width: int = 4) -> BVH:
+    lib = load()
+    v = _np(verts, np.float32).reshape(-1, 3)
+    t = _np(tris, np.int32).reshape(-1, 3)
+    g = _np(group, np.int32).reshape(-1)
+    if g.shape[0] != t.shape[0]:
+        raise ValueError("group must have one entry per triangle")
+    h = _P()
+    _check(lib.srp_build_bvh(ctx.handle, _ptr(v), v.shape[0], _ptr(t), _ptr(g), t.shape[0], width, C.byref(h)))
+    return BVH(h)
+
+
+def srp_bvh_destroy(b: BVH):
+    b.close()
+
+
+def srp_bvh_get_info(b: BVH) -> dict:
+    info = BVHInfo()
+    _check(load().srp_bvh_get_info(b.handle, C.byref(info)))
+    return {"width": info.width, "n_nodes": info.n_nodes, "n_leaves": info.n_leaves, "depth": info.depth,
+            "n_tris": info.n_tris, "device_bytes": info.device_bytes, "build_ms": info.build_ms,
+            "center": tuple(info.center), "radius": info.radius}
+
+
+def srp_build_bvh_host(verts, tris, width: int = 4):
+    """Host-only wide BVH: (node_data float32 [n_node_floats], tri_order int32 [T], n_nodes)."""
+    lib = load()
+    v = _np(verts, np.float32).reshape(-1, 3)
+    t = _np(tris, np.int32).reshape(-1, 3)
+    nf = C.c_int64(0); nn = C.c_int32(0)
+    _check(lib.srp_build_bvh_host(_ptr(v), v.shape[0], _ptr(t), t.shape[0], width, None, C.byref(nf), None,
+                                  C.byref(nn)))
+    nodes = np.zeros(nf.value, np.float32)
+    order = np.zeros(t.shape[0], np.int32)
+    _check(lib.srp_build_bvh_host(_ptr(v), v.shape[0], _ptr(t), t.shape[0], width, _ptr(nodes), C.byref(nf),
+                                  _ptr(order), C.byref(nn)))
+    return nodes, order, nn.value
+
+
+def make_opts(*, rays_x=1024, rays_y=None, max_bounces=1, jitter=1, seed=0, pressure=1.0,
+              ray_offset=0, ray_stride=1, ray_count=0, sun_base=0, design_base=0, mem=SRP_MEM_DEVICE,
+              sun_per_design=0, block_threads=0, chunks_per_item=0) -> TraceOpts:
+    o = TraceOpts()
+    load().srp_trace_opts_default(C.byref(o))
+    o.rays_x = rays_x
+    o.rays_y = rays_x if rays_y is None else rays_y
+    o.max_bounces = max_bounces; o.jitter = jitter; o.seed = seed; o.pressure = pressure
+    o.ray_offset = ray_offset; o.ray_stride = ray_stride; o.ray_count = ray_count
+    o.sun_base = sun_base; o.design_base = design_base; o.mem = mem
+    o.sun_per_design = sun_per_design; o.block_threads = block_threads; o.chunks_per_item = chunks_per_item
+    return o
+
+
+def srp_force(ctx: Context, bvhs, rho, sun_dir, com, out_ft=None, out_sigma=None, **opts):
+    """Force and torque [D,S,6] (plus sigma) of D designs x S sun directions.
+
+    Device mode: rho (float32 [D,G,2]), sun_dir (float64 [S,3] or [D,S,3]),
+    com (float64 [D,3]) and the outputs are torch CUDA tensors; the call is
+    asynchronous on the context's stream.  Host mode: numpy arrays; the call
+    returns when the results are in the output arrays."""
+    lib = load()
+    bvhs = list(bvhs)
+    D = len(bvhs)
+    arr = (_P * max(D, 1))(*[b.handle for b in bvhs])
+    device = not isinstance(rho, np.ndarray)
+    if device:
+        import torch
+        for name, x, dt in (("rho", rho, torch.float32), ("sun_dir", sun_dir, torch.float64),
+                            ("com", com, torch.float64)):
+            if not (x.is_cuda and x.dtype == dt and x.is_contiguous()):
+                raise TypeError(f"{name} must be a contiguous CUDA {dt} tensor")
+        S = sun_dir.shape[-2]
+        G = rho.shape[-2]
+        if out_ft is None:
+            out_ft = torch.empty((D, S, 6), dtype=torch.float64, device=rho.device)
+        opts.setdefault("mem", SRP_MEM_DEVICE)
+    else:
+        rho = _np(rho, np.float32)
+        sun_dir = _np(sun_dir, np.float64)
+        com = _np(com, np.float64)
+        S = sun_dir.shape[-2]
+        G = rho.shape[-2]
+        if out_ft is None:
+            out_ft = np.zeros((D, S, 6))
+        if out_sigma is True:
+            out_sigma = np.zeros((D, S, 6))
+        opts["mem"] = SRP_MEM_HOST
+    if out_sigma is True:
+        import torch
+        out_sigma = torch.empty((D, S, 6), dtype=torch.float64, device=rho.device)
+    if opts.get("sun_per_design"):
+        if tuple(sun_dir.shape[:2]) != (D, S):
+            raise ValueError("sun_dir must be [D,S,3] with sun_per_design")
+    o = make_opts(**opts)
+    _check(lib.srp_force(ctx.handle, arr, D, _ptr(rho), G, _ptr(sun_dir), S, _ptr(com), C.byref(o),
+                         _ptr(out_ft), _ptr(out_sigma) if out_sigma is not None else None))
+    return (out_ft, out_sigma) if out_sigma is not None else out_ft
+
+
+def srp_trace_rays(ctx: Context, bvh: BVH, rho, sun_dir, com, ray_idx, sun_index=0, design_index=0, **opts):
+    """Per-ray samples of one (design, sun): (y [n,6] float64, hits [n,K] int32).
+    numpy inputs -> host mode (synchronous); torch CUDA tensors -> device mode."""
+    lib = load()
+    K = opts.get("max_bounces", 1)
+    if isinstance(rho, np.ndarray) or isinstance(ray_idx, np.ndarray):
+        rho = _np(rho, np.float32).reshape(-1, 2)
+        sun_dir = _np(sun_dir, np.float64).reshape(3)
+        com = _np(com, np.float64).reshape(3)
+        ray_idx = _np(ray_idx, np.int64).reshape(-1)
+        y = np.zeros((ray_idx.shape[0], 6)); h = np.zeros((ray_idx.shape[0], K), np.int32)
+        opts["mem"] = SRP_MEM_HOST
+    else:
+        import torch
+        y = torch.empty((ray_idx.shape[0], 6), dtype=torch.float64, device=rho.device)
+        h = torch.empty((ray_idx.shape[0], K), dtype=torch.int32, device=rho.device)
+        opts["mem"] = SRP_MEM_DEVICE
+    o = make_opts(**opts)
+    _check(lib.srp_trace_rays(ctx.handle, bvh.handle, _ptr(rho), rho.shape[0], _ptr(sun_dir), _ptr(com),
+                              _ptr(ray_idx), ray_idx.shape[0], sun_index, design_index, C.byref(o), _ptr(y), _ptr(h)))
+    return y, h

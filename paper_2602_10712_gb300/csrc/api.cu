@@ -1,0 +1,490 @@
+// api.cu -- C ABI of the SRP library: contexts, validation, BVH upload and
+// the host side of srp_force (see include/srp.h for the contract).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "srp_internal.h"
+
+namespace srp {
+int trace_resident_blocks(int width, int block);
+cudaError_t launch_trace(const std::vector<DesignDev>& designs, const TraceParams& p, int width, int grid_cap,
+                         int block, cudaStream_t st);
+cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* out_ft, double* out_sigma,
+                          cudaStream_t st);
+cudaError_t launch_trace_rays(const DesignDev& dz, const TraceParams& p, const int64_t* ray_idx, int64_t nr,
+                              int sidx, int didx, double* out_y, int32_t* out_hits, cudaStream_t st);
+}  // namespace srp
+
+using namespace srp;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(SRP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CU(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+// A device buffer that only grows.
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr; n = 0;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    void release() { if (p) cudaFree(p); p = nullptr; n = 0; }
+};
+}  // namespace
+
+struct srp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n_sm = 0;
+    int* d_err = nullptr;
+    unsigned long long* d_stats = nullptr;     // traversal counters
+    bool stats_on = false;
+    DevBuf part;                               // trace partials
+    DevBuf stage_in, stage_out;                // host-mem staging
+};
+
+extern "C" {
+
+const char* srp_last_error(void) { return g_err.c_str(); }
+
+void srp_trace_opts_default(srp_trace_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->rays_x = 1024; o->rays_y = 1024;
+    o->max_bounces = 1;
+    o->jitter = 1;
+    o->seed = 0;
+    o->pressure = 1.0;
+    o->ray_offset = 0; o->ray_stride = 1; o->ray_count = 0;
+    o->mem = SRP_MEM_DEVICE;
+    o->sun_per_design = 0;
+    o->block_threads = 0;
+    o->chunks_per_item = 0;
+}
+
+int srp_ctx_create(srp_ctx** out, int device, void* cuda_stream) {
+    if (!out) return fail(SRP_EINVAL, "srp_ctx_create: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    CU(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(SRP_EINVAL, "srp_ctx_create: no such device");
+    CU(cudaSetDevice(device), "cudaSetDevice");
+    srp_ctx* c = new (std::nothrow) srp_ctx();
+    if (!c) return fail(SRP_ENOMEM, "srp_ctx_create: out of host memory");
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDeviceProperties"); }
+    c->n_sm = prop.multiProcessorCount;
+    e = cudaMalloc((void**)&c->d_err, sizeof(int));
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(err)"); }
+    e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_stats, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) { cudaFree(c->d_err); delete c; return cuda_fail(e, "ctx set-up"); }
+    *out = c;
+    return SRP_OK;
+}
+
+int srp_ctx_destroy(srp_ctx* c) {
+    if (!c) return SRP_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    c->part.release(); c->stage_in.release(); c->stage_out.release();
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->d_stats) cudaFree(c->d_stats);
+    delete c;
+    return SRP_OK;
+}
+
+int srp_sync(srp_ctx* c) {
+    if (!c) return fail(SRP_EINVAL, "srp_sync: ctx is NULL");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    CU(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    int flag = 0;
+    CU(cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy(err)");
+    if (flag) {
+        CU(cudaMemset(c->d_err, 0, sizeof(int)), "cudaMemset(err)");
+        std::string what;
+        if (flag & kErrStackOverflow) what += " traversal stack overflow;";
+        if (flag & kErrVisitCap) what += " node-visit cap reached (corrupt BVH?);";
+        return fail(SRP_EDEVICE_LIMIT, "device limit:" + what);
+    }
+    return SRP_OK;
+}
+
+int srp_collect_stats(srp_ctx* c, int enable, uint64_t out[3]) {
+    if (!c) return fail(SRP_EINVAL, "srp_collect_stats: ctx is NULL");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    if (out) {
+        CU(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        unsigned long long h[3];
+        CU(cudaMemcpy(h, c->d_stats, sizeof h, cudaMemcpyDeviceToHost), "cudaMemcpy(stats)");
+        for (int j = 0; j < 3; ++j) out[j] = (uint64_t)h[j];
+    }
+    CU(cudaMemset(c->d_stats, 0, 3 * sizeof(unsigned long long)), "cudaMemset(stats)");
+    c->stats_on = enable != 0;
+    return SRP_OK;
+}
+
+int srp_design_instantiate(const float* vin, int V, const int32_t* vhinge, const double* hinges,
+                           const double* angles, int H, float* vout) {
+    if (V < 0 || H < 0) return fail(SRP_EINVAL, "srp_design_instantiate: negative size");
+    if (V > 0 && (!vin || !vout)) return fail(SRP_EINVAL, "srp_design_instantiate: NULL vertices");
+    if (H > 0 && (!vhinge || !hinges || !angles)) return fail(SRP_EINVAL, "srp_design_instantiate: NULL hinge data");
+    std::vector<double> Rm(9 * (size_t)H);
+    for (int h = 0; h < H; ++h) {
+        const double* a = hinges + 6 * h + 3;
+        const double nrm = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        if (!(std::fabs(nrm - 1.0) < 1e-6)) return fail(SRP_EINVAL, "srp_design_instantiate: hinge axis not unit");
+        const double c = std::cos(angles[h]), s = std::sin(angles[h]), t = 1.0 - c;
+        const double x = a[0] / nrm, y = a[1] / nrm, z = a[2] / nrm;
+        double* R = &Rm[9 * h];
+        R[0] = c + x * x * t;     R[1] = x * y * t - z * s; R[2] = x * z * t + y * s;
+        R[3] = y * x * t + z * s; R[4] = c + y * y * t;     R[5] = y * z * t - x * s;
+        R[6] = z * x * t - y * s; R[7] = z * y * t + x * s; R[8] = c + z * z * t;
+    }
+    for (int v = 0; v < V; ++v) {
+        const int h = H > 0 ? vhinge[v] : -1;
+        if (h >= H) return fail(SRP_EINVAL, "srp_design_instantiate: hinge id out of range");
+        if (h < 0) {
+            if (vout != vin) for (int j = 0; j < 3; ++j) vout[3 * v + j] = vin[3 * v + j];
+            continue;
+        }
+        const double* p = hinges + 6 * h;
+        const double* R = &Rm[9 * h];
+        const double q[3] = {vin[3 * v] - p[0], vin[3 * v + 1] - p[1], vin[3 * v + 2] - p[2]};
+        for (int j = 0; j < 3; ++j)
+            vout[3 * v + j] = (float)(p[j] + R[3 * j] * q[0] + R[3 * j + 1] * q[1] + R[3 * j + 2] * q[2]);
+    }
+    return SRP_OK;
+}
+
+int srp_build_bvh(srp_ctx* c, const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
+                  int width, srp_bvh** out) {
+    if (!c || !out) return fail(SRP_EINVAL, "srp_build_bvh: NULL ctx/out");
+    *out = nullptr;
+    if (V < 0 || T < 0) return fail(SRP_EINVAL, "srp_build_bvh: negative size");
+    if (T > 0 && (!verts || !tris || !group)) return fail(SRP_EINVAL, "srp_build_bvh: NULL arrays");
+    if (T >= (1 << 28)) return fail(SRP_EINVAL, "srp_build_bvh: too many triangles (>= 2^28)");
+    for (int t = 0; t < T; ++t)
+        if (group[t] < 0 || group[t] >= kMaxGroups) return fail(SRP_EINVAL, "srp_build_bvh: group out of [0,64)");
+    auto t0 = std::chrono::steady_clock::now();
+    BuiltBVH b;
+    std::string err;
+    int rc = build_wide_bvh(verts, V, tris, T, width, &b, &err);
+    if (rc != SRP_OK) return fail(rc, "srp_build_bvh: " + err);
+    // grid: centre = vertex AABB centre, radius = max distance (FP64)
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < V; ++v)
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = std::min(lo[j], (double)verts[3 * v + j]);
+            hi[j] = std::max(hi[j], (double)verts[3 * v + j]);
+        }
+    double cen[3] = {0, 0, 0}, R2 = 0.0;
+    if (V > 0) {
+        for (int j = 0; j < 3; ++j) cen[j] = 0.5 * (lo[j] + hi[j]);
+        for (int v = 0; v < V; ++v) {
+            double r2 = 0;
+            for (int j = 0; j < 3; ++j) { double q = verts[3 * v + j] - cen[j]; r2 += q * q; }
+            R2 = std::max(R2, r2);
+        }
+    }
+    std::vector<float> tri(12 * (size_t)std::max(T, 1), 0.0f);
+    for (int k = 0; k < T; ++k) {
+        const int t = b.tri_order[k];
+        for (int cidx = 0; cidx < 3; ++cidx)
+            for (int j = 0; j < 3; ++j) tri[12 * k + 4 * cidx + j] = verts[3 * (size_t)tris[3 * t + cidx] + j];
+        uint32_t id = (uint32_t)t, g = (uint32_t)group[t];
+        std::memcpy(&tri[12 * k + 3], &id, 4);
+        std::memcpy(&tri[12 * k + 7], &g, 4);
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    srp_bvh* h = new (std::nothrow) srp_bvh();
+    if (!h) return fail(SRP_ENOMEM, "srp_build_bvh: out of host memory");
+    h->device = c->device; h->width = width; h->T = T;
+    h->n_nodes = b.n_nodes; h->n_leaves = b.n_leaves; h->depth = b.depth;
+    h->build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    for (int j = 0; j < 3; ++j) h->c[j] = cen[j];
+    h->R = std::sqrt(R2);
+    const size_t tb = tri.size() * sizeof(float), nb = b.node_data.size() * sizeof(float);
+    h->bytes = (int64_t)(tb + nb);
+    cudaError_t e = cudaMalloc(&h->d_tri, tb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_nodes, nb);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_tri, tri.data(), tb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_nodes, b.node_data.data(), nb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (h->d_tri) cudaFree(h->d_tri);
+        if (h->d_nodes) cudaFree(h->d_nodes);
+        delete h;
+        return e == cudaErrorMemoryAllocation ? fail(SRP_ENOMEM, "srp_build_bvh: device out of memory")
+                                              : cuda_fail(e, "srp_build_bvh upload");
+    }
+    *out = h;
+    return SRP_OK;
+}
+
+int srp_build_bvh_host(const float* verts, int V, const int32_t* tris, int T, int width, float* node_data,
+                       int64_t* n_node_floats, int32_t* tri_order, int32_t* n_nodes) {
+    if (V < 0 || T < 0 || !n_node_floats || !n_nodes) return fail(SRP_EINVAL, "srp_build_bvh_host: bad arguments");
+    if (T > 0 && (!verts || !tris)) return fail(SRP_EINVAL, "srp_build_bvh_host: NULL arrays");
+    if (T >= (1 << 28)) return fail(SRP_EINVAL, "srp_build_bvh_host: too many triangles");
+    BuiltBVH b;
+    std::string err;
+    int rc = build_wide_bvh(verts, V, tris, T, width, &b, &err);
+    if (rc != SRP_OK) return fail(rc, "srp_build_bvh_host: " + err);
+    if (!node_data) {
+        *n_node_floats = (int64_t)b.node_data.size();
+        *n_nodes = b.n_nodes;
+        return SRP_OK;
+    }
+    if (*n_node_floats < (int64_t)b.node_data.size()) return fail(SRP_EINVAL, "srp_build_bvh_host: node buffer too small");
+    std::memcpy(node_data, b.node_data.data(), sizeof(float) * b.node_data.size());
+    if (tri_order && T > 0) std::memcpy(tri_order, b.tri_order.data(), sizeof(int32_t) * T);
+    *n_node_floats = (int64_t)b.node_data.size();
+    *n_nodes = b.n_nodes;
+    return SRP_OK;
+}
+
+int srp_bvh_destroy(srp_bvh* h) {
+    if (!h) return SRP_OK;
+    cudaSetDevice(h->device);
+    if (h->d_tri) cudaFree(h->d_tri);
+    if (h->d_nodes) cudaFree(h->d_nodes);
+    delete h;
+    return SRP_OK;
+}
+
+int srp_bvh_get_info(const srp_bvh* h, srp_bvh_info* info) {
+    if (!h || !info) return fail(SRP_EINVAL, "srp_bvh_get_info: NULL argument");
+    info->width = h->width; info->n_nodes = h->n_nodes; info->n_leaves = h->n_leaves;
+    info->depth = h->depth; info->n_tris = h->T;
+    info->device_bytes = h->bytes; info->build_ms = h->build_ms;
+    for (int j = 0; j < 3; ++j) info->center[j] = h->c[j];
+    info->radius = h->R;
+    return SRP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// srp_force
+// ---------------------------------------------------------------------------
+namespace {
+
+int validate_values(const float* rho, int D, int G, const double* sun, int64_t nsun) {
+    for (int64_t q = 0; q < (int64_t)D * G; ++q) {
+        const float rs = rho[2 * q], rd = rho[2 * q + 1];
+        if (!(rs >= 0.0f && rs <= 1.0f && rd >= 0.0f && rd <= 1.0f && rs + rd <= 1.0f + 1e-6f))
+            return fail(SRP_EINVAL, "srp_force: reflectances must satisfy 0 <= rho_s, rho_d and rho_s + rho_d <= 1");
+    }
+    for (int64_t s = 0; s < nsun; ++s) {
+        const double* e = sun + 3 * s;
+        const double nn = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        if (!(std::fabs(nn - 1.0) < 1e-6)) return fail(SRP_EINVAL, "srp_force: sun_dir must be unit vectors");
+    }
+    return SRP_OK;
+}
+
+}  // namespace
+
+// Shared by srp_force and its variants: everything but memory placement.
+namespace srp {
+int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, const srp_trace_opts* o,
+               std::vector<DesignDev>* designs, TraceParams* p, int* width, int* block, int* grid_cap) {
+    if (!c || !o) return fail(SRP_EINVAL, "srp_force: NULL ctx/opts");
+    if (D < 0 || S < 0) return fail(SRP_EINVAL, "srp_force: negative D or S");
+    if (G < 1 || G > kMaxGroups) return fail(SRP_EINVAL, "srp_force: G must be in 1..64");
+    if (o->rays_x < 1 || o->rays_y < 1) return fail(SRP_EINVAL, "srp_force: rays_x/rays_y must be >= 1");
+    const int64_t grid_n = (int64_t)o->rays_x * o->rays_y;
+    if (grid_n > 0xffffffffLL) return fail(SRP_EINVAL, "srp_force: rays_x*rays_y must be < 2^32");
+    if (o->max_bounces < 1 || o->max_bounces > kMaxBounces) return fail(SRP_EINVAL, "srp_force: max_bounces must be 1..3");
+    if (!(o->pressure >= 0.0) || !std::isfinite(o->pressure)) return fail(SRP_EINVAL, "srp_force: bad pressure");
+    int64_t n = o->ray_count, off = o->ray_offset, stride = o->ray_stride;
+    if (n == 0) { n = grid_n; off = 0; stride = 1; }
+    if (n < 0 || off < 0 || stride < 1 || off + (n - 1) * stride >= grid_n)
+        return fail(SRP_EINVAL, "srp_force: ray subset outside the grid");
+    int w = 0;
+    designs->resize(D);
+    for (int d = 0; d < D; ++d) {
+        const srp_bvh* h = bvhs ? bvhs[d] : nullptr;
+        if (!h) return fail(SRP_EINVAL, "srp_force: NULL bvh");
+        if (h->device != c->device) return fail(SRP_EINVAL, "srp_force: bvh built on another device");
+        if (w == 0) w = h->width;
+        if (h->width != w) return fail(SRP_EUNSUPPORTED, "srp_force: all designs of one call need the same BVH width");
+        DesignDev& dz = (*designs)[d];
+        dz.tri = (const float4*)h->d_tri; dz.nodes = (const float4*)h->d_nodes;
+        dz.cx = h->c[0]; dz.cy = h->c[1]; dz.cz = h->c[2]; dz.R = h->R;
+        dz.T = h->T; dz.width = h->width;
+    }
+    *width = w ? w : 4;
+    int bt = o->block_threads ? o->block_threads : 256;
+    if (bt != 128 && bt != 256) return fail(SRP_EINVAL, "srp_force: block_threads must be 0, 128 or 256");
+    *block = bt;
+    const int64_t items = (int64_t)D * S;
+    int64_t cpb = o->chunks_per_item;
+    if (cpb < 0) return fail(SRP_EINVAL, "srp_force: negative chunks_per_item");
+    if (cpb == 0) {
+        const int64_t target = 16384;
+        cpb = items > 0 ? (target + items - 1) / items : 1;
+        cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
+    }
+    int64_t chunk = (n + cpb - 1) / cpb;
+    chunk = std::max<int64_t>(64, (chunk + 63) / 64 * 64);
+    cpb = std::max<int64_t>(1, (n + chunk - 1) / chunk);
+    p->D = D; p->S = S; p->G = G;
+    p->nx = o->rays_x; p->ny = o->rays_y; p->K = o->max_bounces; p->jitter = o->jitter ? 1 : 0;
+    p->sun_per_design = o->sun_per_design ? 1 : 0;
+    p->seed = o->seed; p->P = o->pressure;
+    p->off = off; p->stride = stride; p->n = n;
+    p->sun_base = o->sun_base; p->design_base = o->design_base;
+    p->chunk = chunk; p->cpb = (int32_t)cpb;
+    p->err = c->d_err;
+    p->stats = c->stats_on ? c->d_stats : nullptr;
+    *grid_cap = c->n_sm * trace_resident_blocks(*width, bt);
+    return SRP_OK;
+}
+
+int force_launch(srp_ctx* c, const std::vector<DesignDev>& designs, TraceParams& p, int width, int block,
+                 int grid_cap, double* d_part, double* d_ft, double* d_sigma) {
+    p.part = d_part;
+    const int64_t items = (int64_t)p.D * p.S;
+    if (items == 0 || p.n == 0) {
+        if (items > 0) {
+            CU(cudaMemsetAsync(d_ft, 0, sizeof(double) * 6 * items, c->stream), "cudaMemsetAsync");
+            if (d_sigma) CU(cudaMemsetAsync(d_sigma, 0, sizeof(double) * 6 * items, c->stream), "cudaMemsetAsync");
+        }
+        return SRP_OK;
+    }
+    CU(launch_trace(designs, p, width, grid_cap, block, c->stream), "trace_kernel launch");
+    CU(launch_reduce(d_part, items, p.cpb, d_ft, d_sigma, c->stream), "reduce kernel launch");
+    return SRP_OK;
+}
+}  // namespace srp
+
+extern "C" int srp_force(srp_ctx* c, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                         const double* sun_dir, int S, const double* com, const srp_trace_opts* o,
+                         double* out_ft, double* out_sigma) {
+    std::vector<DesignDev> designs;
+    TraceParams p;
+    std::memset(&p, 0, sizeof p);
+    int width, block, grid_cap;
+    int rc = force_plan(c, bvhs, D, G, S, o, &designs, &p, &width, &block, &grid_cap);
+    if (rc != SRP_OK) return rc;
+    const int64_t items = (int64_t)D * S;
+    if (items > 0 && (!rho || !sun_dir || !com || !out_ft))
+        return fail(SRP_EINVAL, "srp_force: NULL array argument");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    const size_t part_bytes = sizeof(double) * 12 * (size_t)std::max<int64_t>(items * p.cpb, 1);
+    cudaError_t e = c->part.ensure(part_bytes);
+    if (e != cudaSuccess) return fail(SRP_ENOMEM, "srp_force: cannot allocate partials");
+    const int64_t nsun = o->sun_per_design ? (int64_t)D * S : S;
+    if (o->mem == SRP_MEM_DEVICE) {
+        p.rho = rho; p.sun = sun_dir; p.com = com;
+        return force_launch(c, designs, p, width, block, grid_cap, (double*)c->part.p, out_ft, out_sigma);
+    }
+    if (o->mem != SRP_MEM_HOST) return fail(SRP_EINVAL, "srp_force: mem must be SRP_MEM_HOST or SRP_MEM_DEVICE");
+    if (items > 0) {
+        rc = validate_values(rho, D, G, sun_dir, nsun);
+        if (rc != SRP_OK) return rc;
+    }
+    // stage: rho | sun | com  and  ft | sigma
+    const size_t rb = sizeof(float) * 2 * (size_t)D * G, sb = sizeof(double) * 3 * (size_t)nsun,
+                 cb = sizeof(double) * 3 * (size_t)D;
+    const size_t rb_al = (rb + 255) / 256 * 256, sb_al = (sb + 255) / 256 * 256;
+    if (c->stage_in.ensure(rb_al + sb_al + cb + 256) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force: staging");
+    const size_t ob = sizeof(double) * 6 * (size_t)items;
+    const size_t ob_al = (ob + 255) / 256 * 256;
+    if (c->stage_out.ensure(2 * ob_al + 256) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force: staging");
+    char* in = (char*)c->stage_in.p;
+    char* outb = (char*)c->stage_out.p;
+    if (items > 0) {
+        CU(cudaMemcpyAsync(in, rho, rb, cudaMemcpyHostToDevice, c->stream), "H2D rho");
+        CU(cudaMemcpyAsync(in + rb_al, sun_dir, sb, cudaMemcpyHostToDevice, c->stream), "H2D sun");
+        CU(cudaMemcpyAsync(in + rb_al + sb_al, com, cb, cudaMemcpyHostToDevice, c->stream), "H2D com");
+    }
+    p.rho = (const float*)in; p.sun = (const double*)(in + rb_al); p.com = (const double*)(in + rb_al + sb_al);
+    double* d_ft = (double*)outb;
+    double* d_sg = out_sigma ? (double*)(outb + ob_al) : nullptr;
+    rc = force_launch(c, designs, p, width, block, grid_cap, (double*)c->part.p, d_ft, d_sg);
+    if (rc != SRP_OK) return rc;
+    if (items > 0) {
+        CU(cudaMemcpyAsync(out_ft, d_ft, ob, cudaMemcpyDeviceToHost, c->stream), "D2H ft");
+        if (out_sigma) CU(cudaMemcpyAsync(out_sigma, d_sg, ob, cudaMemcpyDeviceToHost, c->stream), "D2H sigma");
+    }
+    return srp_sync(c);
+}
+
+extern "C" int srp_trace_rays(srp_ctx* c, const srp_bvh* bvh, const float* rho, int G, const double* sun_dir,
+                              const double* com, const int64_t* ray_idx, int64_t n, int sun_index,
+                              int design_index, const srp_trace_opts* o, double* out_y, int32_t* out_hits) {
+    if (!o) return fail(SRP_EINVAL, "srp_trace_rays: NULL opts");
+    srp_trace_opts oo = *o;
+    oo.ray_offset = 0; oo.ray_stride = 1; oo.ray_count = 0; oo.sun_per_design = 0;
+    std::vector<DesignDev> designs;
+    TraceParams p;
+    std::memset(&p, 0, sizeof p);
+    int width, block, grid_cap;
+    const srp_bvh* one[1] = {bvh};
+    int rc = force_plan(c, one, 1, G, 1, &oo, &designs, &p, &width, &block, &grid_cap);
+    if (rc != SRP_OK) return rc;
+    if (n < 0) return fail(SRP_EINVAL, "srp_trace_rays: negative n");
+    if (n == 0) return SRP_OK;
+    if (!rho || !sun_dir || !com || !ray_idx || !out_y || !out_hits) return fail(SRP_EINVAL, "srp_trace_rays: NULL array");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    const int64_t grid_n = (int64_t)o->rays_x * o->rays_y;
+    const int K = o->max_bounces;
+    if (o->mem == SRP_MEM_DEVICE) {
+        p.rho = rho; p.sun = sun_dir; p.com = com;
+        CU(launch_trace_rays(designs[0], p, ray_idx, n, sun_index, design_index, out_y, out_hits, c->stream),
+           "trace_rays launch");
+        return SRP_OK;
+    }
+    for (int64_t q = 0; q < n; ++q)
+        if (ray_idx[q] < 0 || ray_idx[q] >= grid_n) return fail(SRP_EINVAL, "srp_trace_rays: ray index outside the grid");
+    rc = validate_values(rho, 1, G, sun_dir, 1);
+    if (rc != SRP_OK) return rc;
+    const size_t rb = 256 * ((sizeof(float) * 2 * G + 255) / 256), sb = 256, cb = 256;
+    const size_t ib = 256 * ((sizeof(int64_t) * n + 255) / 256);
+    const size_t yb = 256 * ((sizeof(double) * 6 * n + 255) / 256), hb = sizeof(int32_t) * K * n;
+    if (c->stage_in.ensure(rb + sb + cb + ib) != cudaSuccess) return fail(SRP_ENOMEM, "srp_trace_rays: staging");
+    if (c->stage_out.ensure(yb + hb + 256) != cudaSuccess) return fail(SRP_ENOMEM, "srp_trace_rays: staging");
+    char* in = (char*)c->stage_in.p;
+    char* ob = (char*)c->stage_out.p;
+    CU(cudaMemcpyAsync(in, rho, sizeof(float) * 2 * G, cudaMemcpyHostToDevice, c->stream), "H2D");
+    CU(cudaMemcpyAsync(in + rb, sun_dir, 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D");
+    CU(cudaMemcpyAsync(in + rb + sb, com, 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D");
+    CU(cudaMemcpyAsync(in + rb + sb + cb, ray_idx, sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream), "H2D");
+    p.rho = (const float*)in; p.sun = (const double*)(in + rb); p.com = (const double*)(in + rb + sb);
+    CU(launch_trace_rays(designs[0], p, (const int64_t*)(in + rb + sb + cb), n, sun_index, design_index,
+                         (double*)ob, (int32_t*)(ob + yb), c->stream), "trace_rays launch");
+    CU(cudaMemcpyAsync(out_y, ob, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream), "D2H");
+    CU(cudaMemcpyAsync(out_hits, ob + yb, hb, cudaMemcpyDeviceToHost, c->stream), "D2H");
+    return srp_sync(c);
+}

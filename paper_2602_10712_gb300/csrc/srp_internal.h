@@ -1,0 +1,84 @@
+// srp_internal.h -- internal layouts of the SRP library (host + device).
+//
+// Device memory layout of one design (an srp_bvh):
+//   tri   float4 [T][3]   triangles in BVH leaf order:
+//                         [0] = (v0.xyz, bits(original index))
+//                         [1] = (v1.xyz, bits(material group))
+//                         [2] = (v2.xyz, 0)
+//   nodes W-wide nodes, structure-of-arrays inside each node:
+//     W = 4: 128 B  = lo_x, hi_x, lo_y, hi_y, lo_z, hi_z (float4 each,
+//                     lane c = child c), child (int4), pad (int4)
+//     W = 8: 256 B  = the same six bounds as 2 float4 each (12 float4),
+//                     child as 2 int4, 2 int4 pad
+//   child >= 0: inner node index; child < 0: leaf, ~child = first << 3 |
+//   (count - 1), count in 1..8 triangles starting at tri[first].  Empty
+//   slots have lo = +inf, hi = -inf and never hit.
+#pragma once
+#include <stdint.h>
+#include <vector_types.h>
+#include <string>
+#include <vector>
+
+#include "../../include/srp.h"
+
+namespace srp {
+
+constexpr int kMaxGroups = 64;
+constexpr int kMaxBounces = 3;
+constexpr int kStackSize = 64;          // traversal stack entries per ray
+constexpr int kMaxDesignsPerLaunch = 128;
+constexpr int kVisitCap = 1 << 20;      // node visits per ray segment (corruption guard)
+
+// Error flags written by kernels (bitwise OR into one device word).
+constexpr int kErrStackOverflow = 1;
+constexpr int kErrVisitCap = 2;
+
+struct BuiltBVH {                  // host result of the builder
+    int width = 4;
+    std::vector<float> node_data;  // W-wide nodes, packed as described above
+    std::vector<int32_t> tri_order;  // leaf order -> original triangle index
+    int n_nodes = 0, n_leaves = 0, depth = 0;
+};
+
+// Binned-SAH binary build, collapsed to `width` (4 or 8) children.
+// Bounds are padded outward so the FP32 slab test is conservative.
+int build_wide_bvh(const float* verts, int V, const int32_t* tris, int T, int width,
+                   BuiltBVH* out, std::string* err);
+
+// Per-design parameters passed to the trace kernel by value.
+struct DesignDev {
+    const float4* tri;
+    const float4* nodes;
+    double cx, cy, cz, R;      // ray-grid centre and radius
+    int32_t T, width;
+};
+
+struct TraceParams {
+    int32_t D, S, G;
+    int32_t nx, ny, K, jitter, sun_per_design;
+    uint64_t seed;
+    double P;
+    int64_t off, stride, n;    // ray subset (n rays per item)
+    int32_t sun_base, design_base;
+    int64_t chunk;             // rays per unit (multiple of 64)
+    int32_t cpb;               // chunks (units) per item
+    const float* rho;          // [D][G][2]
+    const double* sun;         // [S][3] or [D][S][3]
+    const double* com;         // [D][3]
+    double* part;              // [D*S*cpb][12]
+    int* err;                  // device error word
+    unsigned long long* stats; // [3] node visits, triangle tests, segments (or NULL)
+};
+
+}  // namespace srp
+
+struct srp_bvh {
+    int device;
+    int width;
+    int T, n_nodes, n_leaves, depth;
+    double build_ms;
+    double c[3], R;
+    void* d_tri;    // float4[T][3]
+    void* d_nodes;  // node data
+    int64_t bytes;
+};

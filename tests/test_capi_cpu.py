@@ -1,0 +1,130 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, and
+exports every function include/srp.h declares; host-only entry points
+(design instantiation, BVH construction) are checked against the oracle's
+definitions and the BVH's structural invariants.  No GPU needed."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2602_10712_gb300 as srp
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(srp_\w+)\s*\(", txt, flags=re.M))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = srp.load()
+    names = declared_functions()
+    assert "srp_force" in names and "srp_build_bvh" in names and len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), f"libsrp.so does not export {n}"
+
+
+def test_design_instantiate_matches_oracle():
+    m = W.box_wing()
+    ang = np.array([0.7, -1.2])
+    a = srp.srp_design_instantiate(m.verts, m.vhinge, m.hinges, ang)
+    b = oracle.instantiate(m.verts, m.vhinge, m.hinges, ang)
+    assert np.allclose(a, b, atol=2e-6)
+    assert np.array_equal(a[:8], m.verts[:8])
+
+
+def test_design_instantiate_rejects_bad_axis():
+    m = W.box_wing()
+    h = m.hinges.copy(); h[0, 3:] = [0, 2, 0]
+    with pytest.raises(srp.SRPError) as ei:
+        srp.srp_design_instantiate(m.verts, m.vhinge, h, [0.1, 0.2])
+    assert ei.value.code == srp.SRP_EINVAL
+
+
+def _walk(nodes, W_, T, verts, tris, order):
+    nf = 32 if W_ == 4 else 64
+    nodes = nodes.reshape(-1, nf)
+    seen = np.zeros(T, int)
+
+    def box(n, c):
+        lo = np.array([nodes[n, 0 * W_ + c], nodes[n, 2 * W_ + c], nodes[n, 4 * W_ + c]])
+        hi = np.array([nodes[n, 1 * W_ + c], nodes[n, 3 * W_ + c], nodes[n, 5 * W_ + c]])
+        return lo, hi
+
+    stack = [(0, None)]
+    visited = 0
+    while stack:
+        n, parent_box = stack.pop()
+        visited += 1
+        ch = nodes[n, 6 * W_:7 * W_].view(np.int32)
+        for c in range(W_):
+            lo, hi = box(n, c)
+            if lo[0] > hi[0]:
+                continue  # empty slot
+            if parent_box is not None:
+                assert np.all(lo >= parent_box[0] - 1e-6) and np.all(hi <= parent_box[1] + 1e-6)
+            if ch[c] >= 0:
+                assert ch[c] > n
+                stack.append((int(ch[c]), (lo, hi)))
+            else:
+                code = ~int(ch[c])
+                first, cnt = code >> 3, (code & 7) + 1
+                for k in range(first, first + cnt):
+                    t = order[k]
+                    seen[t] += 1
+                    p = verts[tris[t]]
+                    assert np.all(p >= lo) and np.all(p <= hi), "triangle outside its leaf box"
+    return seen, visited
+
+
+@pytest.mark.parametrize("width", [4, 8])
+def test_bvh_host_invariants(width):
+    """Every triangle in exactly one leaf; triangles inside their leaf box;
+    child boxes inside parent boxes; every node reachable from the root."""
+    m = W.procedural_satellite(dish_segments=32, dish_rings=12, n_boxes=20)
+    nodes, order, nn = srp.srp_build_bvh_host(m.verts, m.tris, width)
+    assert sorted(order.tolist()) == list(range(m.T))
+    seen, visited = _walk(nodes, width, m.T, m.verts.astype(np.float64), m.tris, order)
+    assert np.all(seen == 1)
+    assert visited == nn
+
+
+@pytest.mark.parametrize("T", [0, 1, 3, 5])
+def test_bvh_host_tiny(T):
+    m = W.icosphere(1)
+    tris = m.tris[:T]
+    nodes, order, nn = srp.srp_build_bvh_host(m.verts, tris, 4)
+    assert nn >= 1
+    if T:
+        seen, _ = _walk(nodes, 4, T, m.verts.astype(np.float64), tris, order)
+        assert np.all(seen == 1)
+
+
+def test_bvh_host_rejects_bad_input():
+    m = W.box_wing()
+    with pytest.raises(srp.SRPError) as e:
+        srp.srp_build_bvh_host(m.verts, m.tris, 6)
+    assert e.value.code == srp.SRP_EINVAL
+    bad = m.tris.copy(); bad[0, 0] = 999
+    with pytest.raises(srp.SRPError):
+        srp.srp_build_bvh_host(m.verts, bad, 4)
+    v = m.verts.copy(); v[0, 0] = np.nan
+    with pytest.raises(srp.SRPError):
+        srp.srp_build_bvh_host(v, m.tris, 4)
+
+
+def test_opts_struct_matches_header():
+    """ctypes mirror of srp_trace_opts has the C layout (defaults round-trip)."""
+    o = srp.make_opts()
+    assert o.rays_x == 1024 and o.max_bounces == 1 and o.pressure == 1.0 and o.mem == srp.SRP_MEM_DEVICE
+    assert C.sizeof(srp.TraceOpts) == 80 and srp.TraceOpts.pressure.offset == 24
