@@ -37,6 +37,8 @@
  *       k <  K:  branch with fixed probability 1/2 (xi_b = u(x0)):
  *                specular r = d - 2(d.n)n,        w' = 2 w rs
  *                diffuse  cosine-weighted about n, w' = 2 w rd
+ *                         (direction of n + s, s uniform on the unit
+ *                         sphere from (u(x1), u(x2)))
  *                deposit w d - w' d'; continue with (x, d', w')
  *     torque deposit (x - COM) x deposit.  Rays that miss deposit nothing.
  *  6. Sums in FP64 in ray order k.  Uncertainty: each pixel is one
@@ -260,11 +262,13 @@ static void trace_path(const scene_t* sc, const double e[3], uint64_t i, uint32_
             wout = 2.0 * w * rs;
             pth->br[h] = 0;
         } else {
-            double b1[3], b2[3];
-            or_onb(n, b1, b2);
-            double rr = sqrt(u[1]), phi = 2.0 * M_PI * u[2];
-            double lx = rr * cos(phi), ly = rr * sin(phi), lz = sqrt(fmax(0.0, 1.0 - u[1]));
-            for (int j = 0; j < 3; ++j) dout[j] = lx * b1[j] + ly * b2[j] + lz * n[j];
+            /* Lambertian reflection: the direction from x to a uniform point
+             * on the unit sphere centred at x + n is cosine-distributed about
+             * n (pdf cos/pi); no tangent frame is needed. */
+            double z = 1.0 - 2.0 * u[1], rr = sqrt(fmax(0.0, 1.0 - z * z)), phi = 2.0 * M_PI * u[2];
+            double v[3] = {n[0] + rr * cos(phi), n[1] + rr * sin(phi), n[2] + z};
+            double L = sqrt(dot3(v, v));
+            for (int j = 0; j < 3; ++j) dout[j] = L > 0.0 ? v[j] / L : n[j];
             wout = 2.0 * w * rd;
             pth->br[h] = 1;
         }
