@@ -82,7 +82,7 @@ typedef struct srp_trace_opts {
     int32_t design_base;      /* added to the design index in the counter   */
     int32_t mem;              /* srp_mem of rho/sun_dir/com/outputs [DEVICE]*/
     int32_t sun_per_design;   /* 1: sun_dir is [D][S][3], 0: [S][3] [0]     */
-    int32_t block_threads;    /* 0 = autotuned; else 128 or 256             */
+    int32_t block_threads;    /* 0 or 128 (threads per block)               */
     int32_t chunks_per_item;  /* 0 = automatic; else ray chunks per item    */
 } srp_trace_opts;
 

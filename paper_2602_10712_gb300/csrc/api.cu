@@ -344,14 +344,15 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
         dz.T = h->T; dz.width = h->width;
     }
     *width = w ? w : 4;
-    int bt = o->block_threads ? o->block_threads : 256;
-    if (bt != 128 && bt != 256) return fail(SRP_EINVAL, "srp_force: block_threads must be 0, 128 or 256");
+    int bt = o->block_threads ? o->block_threads : 128;
+    if (bt != 128) return fail(SRP_EINVAL, "srp_force: block_threads must be 0 or 128");
     *block = bt;
     const int64_t items = (int64_t)D * S;
     int64_t cpb = o->chunks_per_item;
     if (cpb < 0) return fail(SRP_EINVAL, "srp_force: negative chunks_per_item");
     if (cpb == 0) {
-        const int64_t target = 16384;
+        const int64_t target = 40960;   // ~16 units per resident warp
+
         cpb = items > 0 ? (target + items - 1) / items : 1;
         cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
     }

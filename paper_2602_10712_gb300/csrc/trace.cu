@@ -61,15 +61,6 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 }
 __device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
 
-// Branchless orthonormal basis around unit n (Duff et al. 2017), FP32.
-__device__ __forceinline__ void onb_f(float3 n, float3& b1, float3& b2) {
-    const float sign = n.z >= 0.0f ? 1.0f : -1.0f;
-    const float a = -1.0f / (sign + n.z);
-    const float b = n.x * n.y * a;
-    b1 = f3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
-    b2 = f3(b, sign + n.y * n.y * a, -n.y);
-}
-
 // ---------------------------------------------------------------------------
 // Ray state for traversal: slab-test constants and watertight shear.
 // ---------------------------------------------------------------------------
@@ -228,65 +219,130 @@ __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& 
 }
 
 // ---------------------------------------------------------------------------
-// One primary ray with its bounces: force (y[0..2]) and torque (y[3..5]).
+// A ray segment and the shading of its hit.
 // ---------------------------------------------------------------------------
-template <int W>
-__device__ __forceinline__ void trace_ray(const DesignDev& dz, const TraceParams& p, int dglob, int sglob,
-                                          uint32_t i, float3 o, float3 d, float w, float3 com,
-                                          const float* __restrict__ rho, float tmin_b, float y[6],
-                                          uint32_t& nvis, uint32_t& ntest, uint32_t& nseg,
-                                          int32_t* hits = nullptr) {
-    int src = -1;
-    float tmin = 0.0f;
-    for (int k = 1; k <= p.K; ++k) {
-        RaySetup r;
-        setup_ray(r, o, d);
-        float t;
-        ++nseg;
-        const int f = closest_hit<W>(dz, r, tmin, src, t, p.err, nvis, ntest);
-        if (f < 0) break;
-        const float4 a = __ldg(dz.tri + 3 * (size_t)f);
-        if (hits) hits[k - 1] = (int32_t)__float_as_uint(a.w);
-        const float4 b = __ldg(dz.tri + 3 * (size_t)f + 1);
-        const float4 c = __ldg(dz.tri + 3 * (size_t)f + 2);
-        float3 n = cross(xyz(b) - xyz(a), xyz(c) - xyz(a));
-        n = rsqrtf(dot(n, n)) * n;
-        if (dot(n, d) > 0.0f) n = -1.0f * n;
-        const float cs = -dot(n, d);
-        const int g = (int)__float_as_uint(b.w);
-        const float rs = __ldg(rho + 2 * g), rd = __ldg(rho + 2 * g + 1);
-        const float3 x = o + t * d;
-        const float3 arm = x - com;
-        float3 dp;
-        if (k == p.K) {
-            const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
-            dp = w * ((1.0f - rs) * d - cn * n);
-            const float3 tq = cross(arm, dp);
-            y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
-            break;
-        }
-        const uint4 rnd = philox4x32_10(make_uint4(i, (uint32_t)sglob, (uint32_t)dglob, (uint32_t)k),
+struct Seg {
+    float3 o, d;
+    float w;
+    int src;  // leaf-order index of the triangle the segment leaves (-1: primary)
+};
+
+// Per-item constants shared by every ray of one (design, sun).
+struct ItemConst {
+    float3 ob, bu, bv, dd, com;
+    float fdx, fdy, w0, tmin_b;
+    const float* rho;
+    int dglob, sglob;
+};
+
+__device__ __forceinline__ void item_setup(ItemConst& ic, const DesignDev& dz, const TraceParams& p,
+                                           const double* sp, const double* cp, const float* rho,
+                                           int dglob, int sglob) {
+    // branchless ONB of d = -e (Duff et al. 2017) in FP64, rounded once
+    const double dx_ = -sp[0], dy_ = -sp[1], dz_ = -sp[2];
+    const double sgn = dz_ >= 0.0 ? 1.0 : -1.0;
+    const double aa = -1.0 / (sgn + dz_);
+    const double bb = dx_ * dy_ * aa;
+    const double u0 = 1.0 + sgn * dx_ * dx_ * aa, u1 = sgn * bb, u2 = -sgn * dx_;
+    const double v0 = bb, v1 = sgn + dy_ * dy_ * aa, v2 = -dy_;
+    const double R = dz.R;
+    const double pdx = 2.0 * R / p.nx, pdy = 2.0 * R / p.ny;
+    ic.ob = f3((float)(dz.cx - R * u0 - R * v0 - 2.0 * R * dx_), (float)(dz.cy - R * u1 - R * v1 - 2.0 * R * dy_),
+               (float)(dz.cz - R * u2 - R * v2 - 2.0 * R * dz_));
+    ic.bu = f3((float)u0, (float)u1, (float)u2);
+    ic.bv = f3((float)v0, (float)v1, (float)v2);
+    ic.dd = f3((float)dx_, (float)dy_, (float)dz_);
+    ic.fdx = (float)pdx; ic.fdy = (float)pdy;
+    ic.w0 = (float)(p.P * pdx * pdy);
+    ic.com = f3((float)cp[0], (float)cp[1], (float)cp[2]);
+    ic.tmin_b = (float)(1e-6 * R);
+    ic.rho = rho;
+    ic.dglob = dglob; ic.sglob = sglob;
+}
+
+// Primary segment of grid ray i (jittered pixel origin, travel direction d).
+__device__ __forceinline__ Seg primary_seg(const ItemConst& ic, const TraceParams& p, uint64_t i) {
+    const uint32_t px = (uint32_t)(i % (uint64_t)p.nx), py = (uint32_t)(i / (uint64_t)p.nx);
+    float xi1 = 0.5f, xi2 = 0.5f;
+    if (p.jitter) {
+        const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)ic.sglob, (uint32_t)ic.dglob, 0u),
                                         (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-        float3 dout;
-        float wout;
-        if (unit24(rnd.x) < 0.5f) {
-            dout = d + (2.0f * cs) * n;
-            wout = 2.0f * w * rs;
-        } else {
-            float3 b1, b2;
-            onb_f(n, b1, b2);
-            const float u1 = unit24(rnd.y), u2 = unit24(rnd.z);
-            const float rr = sqrtf(u1);
-            float sp, cp;
-            sincospif(2.0f * u2, &sp, &cp);
-            const float lz = sqrtf(fmaxf(0.0f, 1.0f - u1));
-            dout = (rr * cp) * b1 + (rr * sp) * b2 + lz * n;
-            wout = 2.0f * w * rd;
-        }
-        dp = w * d - wout * dout;
+        xi1 = unit24(rnd.x); xi2 = unit24(rnd.y);
+    }
+    const float a = ((float)px + xi1) * ic.fdx, b = ((float)py + xi2) * ic.fdy;
+    Seg s;
+    s.o = f3(fmaf(a, ic.bu.x, fmaf(b, ic.bv.x, ic.ob.x)), fmaf(a, ic.bu.y, fmaf(b, ic.bv.y, ic.ob.y)),
+             fmaf(a, ic.bu.z, fmaf(b, ic.bv.z, ic.ob.z)));
+    s.d = ic.dd;
+    s.w = ic.w0;
+    s.src = -1;
+    return s;
+}
+
+// Momentum deposit of hit k (1-based) on leaf-order triangle f at ray
+// parameter t; returns true (and the outgoing segment) if the path goes on.
+__device__ __forceinline__ bool shade_hit(const DesignDev& dz, const ItemConst& ic, const TraceParams& p,
+                                          uint32_t i, int k, int f, float t, const Seg& s, float y[6],
+                                          Seg& out) {
+    const float4 a = __ldg(dz.tri + 3 * (size_t)f);
+    const float4 b = __ldg(dz.tri + 3 * (size_t)f + 1);
+    const float4 c = __ldg(dz.tri + 3 * (size_t)f + 2);
+    float3 n = cross(xyz(b) - xyz(a), xyz(c) - xyz(a));
+    n = rsqrtf(dot(n, n)) * n;
+    if (dot(n, s.d) > 0.0f) n = -1.0f * n;
+    const float cs = -dot(n, s.d);
+    const int g = (int)__float_as_uint(b.w);
+    const float rs = __ldg(ic.rho + 2 * g), rd = __ldg(ic.rho + 2 * g + 1);
+    const float3 x = s.o + t * s.d;
+    const float3 arm = x - ic.com;
+    if (k == p.K) {
+        const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
+        const float3 dp = s.w * ((1.0f - rs) * s.d - cn * n);
         const float3 tq = cross(arm, dp);
         y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
-        o = x; d = dout; w = wout; src = f; tmin = tmin_b;
+        return false;
+    }
+    const uint4 rnd = philox4x32_10(make_uint4(i, (uint32_t)ic.sglob, (uint32_t)ic.dglob, (uint32_t)k),
+                                    (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+    float3 dout;
+    float wout;
+    if (unit24(rnd.x) < 0.5f) {
+        dout = s.d + (2.0f * cs) * n;
+        wout = 2.0f * s.w * rs;
+    } else {
+        // Lambertian: direction of n + (uniform unit vector), pdf cos/pi
+        const float z = 1.0f - 2.0f * unit24(rnd.y);
+        const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+        float sp, cp;
+        sincospif(2.0f * unit24(rnd.z), &sp, &cp);
+        const float3 v = f3(n.x + rr * cp, n.y + rr * sp, n.z + z);
+        const float l2 = dot(v, v);
+        dout = l2 > 0.0f ? rsqrtf(l2) * v : n;
+        wout = 2.0f * s.w * rd;
+    }
+    const float3 dp = s.w * s.d - wout * dout;
+    const float3 tq = cross(arm, dp);
+    y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
+    out.o = x; out.d = dout; out.w = wout; out.src = f;
+    return true;
+}
+
+// Whole path of one ray in one thread (used by the per-ray inspection).
+template <int W>
+__device__ __forceinline__ void trace_path(const DesignDev& dz, const ItemConst& ic, const TraceParams& p,
+                                           uint32_t i, Seg s, float y[6], uint32_t& nvis, uint32_t& ntest,
+                                           uint32_t& nseg, int32_t* hits) {
+    for (int k = 1; k <= p.K; ++k) {
+        RaySetup r;
+        setup_ray(r, s.o, s.d);
+        float t;
+        ++nseg;
+        const int f = closest_hit<W>(dz, r, k == 1 ? 0.0f : ic.tmin_b, s.src, t, p.err, nvis, ntest);
+        if (f < 0) break;
+        if (hits) hits[k - 1] = (int32_t)__float_as_uint(__ldg(dz.tri + 3 * (size_t)f).w);
+        Seg nx;
+        if (!shade_hit(dz, ic, p, i, k, f, t, s, y, nx)) break;
+        s = nx;
     }
 }
 
@@ -297,110 +353,183 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// Trace kernel: blocks loop over units (item, chunk) of this launch.
+// Trace kernel: a warp-level wavefront.  Every warp is an independent worker
+// looping over units (item, chunk) with a static stride; a unit's rays are
+// processed in tiles of 32*kBatches rays:
+//   primary batches  the warp traces 32 neighbouring pixels at a time
+//                    (coherent parallel rays share node fetches); each
+//                    ray's deposit goes to its slot in shared memory and
+//                    paths that continue are pushed on the warp's queue;
+//   bounce batches   whenever 32 segments are queued, all 32 lanes trace
+//                    them together; the tile's last segments are drained
+//                    at its end;
+//   tile reduce      per-ray sums -> per-lane FP32 partials (lane pairs
+//                    give the collapsed-strata variance) -> FP64.
+// Only __syncwarp is needed inside a unit.  Each ray's arithmetic and
+// deposit order (bounce 1, 2, 3) are those of trace_path.
 // ---------------------------------------------------------------------------
+constexpr int kBatches = 8;               // primary batches of 32 rays per tile
+constexpr int kTile = 32 * kBatches;      // rays per warp tile
+constexpr int kQueue = 64;                // bounce segments per warp (<= 31 + 32 live)
+constexpr int kWarpsPerBlock = 4;
+
+struct WarpSmem {
+    float ys[6][kTile];        // per-ray force/torque sums of the tile
+    float4 qa[kQueue];         // (o.xyz, w)
+    float4 qb[kQueue];         // (d.xyz, src)
+    int qs[kQueue];            // slot | (bounce << 16)
+    double dacc[12][32];       // per-lane FP64 sums (force, torque, squared pair differences)
+};
+
+__host__ __device__ constexpr size_t trace_smem_bytes(int block) {
+    return (size_t)(block / 32) * sizeof(WarpSmem);
+}
+
+// Append the segments of lanes with `want` to the warp queue.
+__device__ __forceinline__ void q_push(WarpSmem& ws, int& qcount, bool want, const Seg& s, int slot, int kb,
+                                       int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (want) {
+        const int pos = qcount + __popc(m & ((1u << lane) - 1u));
+        ws.qa[pos] = make_float4(s.o.x, s.o.y, s.o.z, s.w);
+        ws.qb[pos] = make_float4(s.d.x, s.d.y, s.d.z, __int_as_float(s.src));
+        ws.qs[pos] = slot | (kb << 16);
+    }
+    qcount += __popc(m);
+    __syncwarp();
+}
+
 template <int W>
-__global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ DesignTable tab, const TraceParams p,
-                                                    int d0, int Dl) {
-    __shared__ double red[8][12];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+__global__ void __launch_bounds__(128, 4) trace_kernel(const __grid_constant__ DesignTable tab, const TraceParams p,
+                                                       int d0, int Dl) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem& ws = reinterpret_cast<WarpSmem*>(smem)[warp];
     const int64_t units = (int64_t)Dl * p.S * p.cpb;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    uint32_t nvis = 0, ntest = 0, nseg = 0;
+    for (int64_t u = gw; u < units; u += nw) {
         const int64_t item_l = u / p.cpb;
         const int64_t cidx = u % p.cpb;
         const int dl = (int)(item_l / p.S), s = (int)(item_l % p.S);
         const int dg = d0 + dl;
         const DesignDev& dz = tab.d[dl];
-        // per-item constants (FP64 set-up, rounded once)
-        const double* sp = p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dg * p.S + s : s));
-        const double dx_ = -sp[0], dy_ = -sp[1], dz_ = -sp[2];
-        const double sgn = dz_ >= 0.0 ? 1.0 : -1.0;
-        const double aa = -1.0 / (sgn + dz_);
-        const double bb = dx_ * dy_ * aa;
-        const double u0 = 1.0 + sgn * dx_ * dx_ * aa, u1 = sgn * bb, u2 = -sgn * dx_;
-        const double v0 = bb, v1 = sgn + dy_ * dy_ * aa, v2 = -dy_;
-        const double R = dz.R;
-        const double pdx = 2.0 * R / p.nx, pdy = 2.0 * R / p.ny;
-        const float3 ob = f3((float)(dz.cx - R * u0 - R * v0 - 2.0 * R * dx_),
-                             (float)(dz.cy - R * u1 - R * v1 - 2.0 * R * dy_),
-                             (float)(dz.cz - R * u2 - R * v2 - 2.0 * R * dz_));
-        const float3 bu = f3((float)u0, (float)u1, (float)u2), bv = f3((float)v0, (float)v1, (float)v2);
-        const float3 dd = f3((float)dx_, (float)dy_, (float)dz_);
-        const float fdx = (float)pdx, fdy = (float)pdy;
-        const float w0 = (float)(p.P * pdx * pdy);
-        const float3 com = f3((float)p.com[3 * dg], (float)p.com[3 * dg + 1], (float)p.com[3 * dg + 2]);
-        const float* rho = p.rho + (size_t)dg * p.G * 2;
-        const float tmin_b = (float)(1e-6 * R);
-        const int dglob = p.design_base + dg, sglob = p.sun_base + s;
-
-        // per-thread sums: FP32 over up to 32 rays, then flushed into FP64
-        double acc[6] = {0, 0, 0, 0, 0, 0}, sq[6] = {0, 0, 0, 0, 0, 0};
-        float accf[6] = {0, 0, 0, 0, 0, 0}, sqf[6] = {0, 0, 0, 0, 0, 0};
-        uint32_t nvis = 0, ntest = 0, nseg = 0;
+        ItemConst ic;
+        item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dg * p.S + s : s)), p.com + 3 * dg,
+                   p.rho + (size_t)dg * p.G * 2, p.design_base + dg, p.sun_base + s);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) ws.dacc[q][lane] = 0.0;
         const int64_t k0 = cidx * p.chunk;
         const int64_t k1 = min(k0 + p.chunk, p.n);
-        const int64_t span = k1 - k0;
-        const int nj = (int)((span + blockDim.x - 1) / blockDim.x);
-        for (int j = 0; j < nj; ++j) {
-            const int64_t k = k0 + threadIdx.x + (int64_t)j * blockDim.x;
-            float y[6] = {0, 0, 0, 0, 0, 0};
-            const bool valid = k < k1;
-            if (valid) {
-                const uint64_t i = (uint64_t)(p.off + k * p.stride);
-                const uint32_t px = (uint32_t)(i % (uint64_t)p.nx), py = (uint32_t)(i / (uint64_t)p.nx);
-                float xi1 = 0.5f, xi2 = 0.5f;
-                if (p.jitter) {
-                    const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)sglob, (uint32_t)dglob, 0u),
-                                                    (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-                    xi1 = unit24(rnd.x); xi2 = unit24(rnd.y);
-                }
-                const float a = ((float)px + xi1) * fdx, b = ((float)py + xi2) * fdy;
-                const float3 o = f3(fmaf(a, bu.x, fmaf(b, bv.x, ob.x)), fmaf(a, bu.y, fmaf(b, bv.y, ob.y)),
-                                    fmaf(a, bu.z, fmaf(b, bv.z, ob.z)));
-                trace_ray<W>(dz, p, dglob, sglob, (uint32_t)i, o, dd, w0, com, rho, tmin_b, y, nvis, ntest, nseg);
-            }
-            // collapsed strata: pair rays k (even) and k+1 held by lanes 2m, 2m+1
-            const bool pvalid = __shfl_xor_sync(0xffffffffu, (int)valid, 1);
+        int qcount = 0;
+        for (int64_t ts = k0; ts < k1; ts += kTile) {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                const float yo = __shfl_xor_sync(0xffffffffu, y[q], 1);
-                accf[q] += y[q];
-                if ((lane & 1) == 0 && valid) {
-                    const float df = pvalid ? y[q] - yo : y[q];
-                    sqf[q] = fmaf(df, df, sqf[q]);
+            for (int j = 0; j < kBatches; ++j)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) ws.ys[q][j * 32 + lane] = 0.0f;
+            __syncwarp();
+            // ---- one work loop, one trace site: each iteration the warp takes
+            // 32 queued bounce segments if there are that many, else the next
+            // batch of 32 primary rays, else the remaining queued segments.
+            int next_batch = 0;
+#pragma unroll 1
+            while (true) {
+                int nb;
+                const bool primary = qcount < 32 && next_batch < kBatches;
+                if (primary) nb = 32;
+                else if (qcount > 0) nb = min(qcount, 32);
+                else break;
+                bool has;
+                Seg sg;
+                int slot, kb;
+                uint64_t i = 0;
+                if (primary) {
+                    slot = next_batch * 32 + lane;
+                    const int64_t k = ts + slot;
+                    has = k < k1;
+                    kb = 1;
+                    if (has) {
+                        i = (uint64_t)(p.off + k * p.stride);
+                        sg = primary_seg(ic, p, i);
+                    }
+                    ++next_batch;
+                } else {
+                    has = lane < nb;
+                    slot = 0; kb = 0;
+                    if (has) {
+                        const int e = qcount - 1 - lane;
+                        const float4 A = ws.qa[e], Bv = ws.qb[e];
+                        const int q = ws.qs[e];
+                        sg.o = f3(A.x, A.y, A.z); sg.w = A.w;
+                        sg.d = f3(Bv.x, Bv.y, Bv.z); sg.src = __float_as_int(Bv.w);
+                        slot = q & 0xffff; kb = q >> 16;
+                        i = (uint64_t)(p.off + (ts + slot) * p.stride);
+                    }
+                    __syncwarp();
+                    qcount -= nb;
                 }
+                bool cont = false;
+                Seg nx;
+                if (has) {
+                    RaySetup rs;
+                    setup_ray(rs, sg.o, sg.d);
+                    float t;
+                    ++nseg;
+                    const int f = closest_hit<W>(dz, rs, kb == 1 ? 0.0f : ic.tmin_b, sg.src, t, p.err, nvis, ntest);
+                    if (f >= 0) {
+                        float y[6];
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) y[q] = ws.ys[q][slot];
+                        cont = shade_hit(dz, ic, p, (uint32_t)i, kb, f, t, sg, y, nx);
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) ws.ys[q][slot] = y[q];
+                    }
+                }
+                q_push(ws, qcount, cont, nx, slot, kb + 1, lane);
             }
-            if ((j & 31) == 31 || j == nj - 1) {
+            // ---- per-ray sums -> per-lane partials (slot parity = ray parity)
+            float accf[6] = {0, 0, 0, 0, 0, 0}, sqf[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < kBatches; ++j) {
+                const int slot = j * 32 + lane;
+                const bool valid = ts + slot < k1;
+                const bool pvalid = __shfl_xor_sync(0xffffffffu, (int)valid, 1);
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
-                    acc[q] += (double)accf[q]; sq[q] += (double)sqf[q];
-                    accf[q] = 0.0f; sqf[q] = 0.0f;
+                    const float y = ws.ys[q][slot];
+                    const float yo = __shfl_xor_sync(0xffffffffu, y, 1);
+                    accf[q] += y;
+                    if ((lane & 1) == 0 && valid) {
+                        const float df = pvalid ? y - yo : y;
+                        sqf[q] = fmaf(df, df, sqf[q]);
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int q = 0; q < 6; ++q) { acc[q] = warp_sum_d(acc[q]); sq[q] = warp_sum_d(sq[q]); }
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) { red[warp][q] = acc[q]; red[warp][6 + q] = sq[q]; }
-        }
-        __syncthreads();
-        if (threadIdx.x < 12) {
-            double t = 0.0;
-            for (int wi = 0; wi < nwarp; ++wi) t += red[wi][threadIdx.x];
-            p.part[((size_t)(d0 * (int64_t)p.S * p.cpb) + u) * 12 + threadIdx.x] = t;
-        }
-        if (p.stats) {  // traversal work counters (node visits, triangle tests, segments)
-            unsigned long long a = nvis, b = ntest, c = nseg;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, off);
-                b += __shfl_xor_sync(0xffffffffu, b, off);
-                c += __shfl_xor_sync(0xffffffffu, c, off);
+            for (int q = 0; q < 6; ++q) {
+                ws.dacc[q][lane] += (double)accf[q];
+                ws.dacc[6 + q][lane] += (double)sqf[q];
             }
-            if (lane == 0) { atomicAdd(p.stats, a); atomicAdd(p.stats + 1, b); atomicAdd(p.stats + 2, c); }
+            __syncwarp();
         }
-        __syncthreads();
+        // warp reduction in a fixed order -> the unit's partial
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const double v = warp_sum_d(ws.dacc[q][lane]);
+            if (lane == q) p.part[((size_t)(d0 * (int64_t)p.S * p.cpb) + u) * 12 + q] = v;
+        }
+        __syncwarp();
+    }
+    if (p.stats) {  // traversal work counters (node visits, triangle tests, segments)
+        unsigned long long a = nvis, b = ntest, c = nseg;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, off);
+            b += __shfl_xor_sync(0xffffffffu, b, off);
+            c += __shfl_xor_sync(0xffffffffu, c, off);
+        }
+        if (lane == 0) { atomicAdd(p.stats, a); atomicAdd(p.stats + 1, b); atomicAdd(p.stats + 2, c); }
     }
 }
 
@@ -412,38 +541,13 @@ __global__ void __launch_bounds__(128) trace_rays_kernel(const DesignDev dz, con
                                                          int32_t* __restrict__ out_hits) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nr) return;
-    const double dx_ = -p.sun[0], dy_ = -p.sun[1], dz_ = -p.sun[2];
-    const double sgn = dz_ >= 0.0 ? 1.0 : -1.0;
-    const double aa = -1.0 / (sgn + dz_);
-    const double bb = dx_ * dy_ * aa;
-    const double u0 = 1.0 + sgn * dx_ * dx_ * aa, u1 = sgn * bb, u2 = -sgn * dx_;
-    const double v0 = bb, v1 = sgn + dy_ * dy_ * aa, v2 = -dy_;
-    const double R = dz.R;
-    const double pdx = 2.0 * R / p.nx, pdy = 2.0 * R / p.ny;
-    const float3 ob = f3((float)(dz.cx - R * u0 - R * v0 - 2.0 * R * dx_),
-                         (float)(dz.cy - R * u1 - R * v1 - 2.0 * R * dy_),
-                         (float)(dz.cz - R * u2 - R * v2 - 2.0 * R * dz_));
-    const float3 bu = f3((float)u0, (float)u1, (float)u2), bv = f3((float)v0, (float)v1, (float)v2);
-    const float3 dd = f3((float)dx_, (float)dy_, (float)dz_);
-    const float w0 = (float)(p.P * pdx * pdy);
-    const float3 com = f3((float)p.com[0], (float)p.com[1], (float)p.com[2]);
-    const int dglob = p.design_base + didx, sglob = p.sun_base + sidx;
+    ItemConst ic;
+    item_setup(ic, dz, p, p.sun, p.com, p.rho, p.design_base + didx, p.sun_base + sidx);
     const uint64_t i = (uint64_t)ray_idx[q];
-    const uint32_t px = (uint32_t)(i % (uint64_t)p.nx), py = (uint32_t)(i / (uint64_t)p.nx);
-    float xi1 = 0.5f, xi2 = 0.5f;
-    if (p.jitter) {
-        const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)sglob, (uint32_t)dglob, 0u),
-                                        (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-        xi1 = unit24(rnd.x); xi2 = unit24(rnd.y);
-    }
-    const float a = ((float)px + xi1) * (float)pdx, b = ((float)py + xi2) * (float)pdy;
-    const float3 o = f3(fmaf(a, bu.x, fmaf(b, bv.x, ob.x)), fmaf(a, bu.y, fmaf(b, bv.y, ob.y)),
-                        fmaf(a, bu.z, fmaf(b, bv.z, ob.z)));
     float y[6] = {0, 0, 0, 0, 0, 0};
     int32_t hits[kMaxBounces] = {-1, -1, -1};
     uint32_t nvis = 0, ntest = 0, nseg = 0;
-    trace_ray<W>(dz, p, dglob, sglob, (uint32_t)i, o, dd, w0, com, p.rho, (float)(1e-6 * R), y, nvis, ntest, nseg,
-                 hits);
+    trace_path<W>(dz, ic, p, (uint32_t)i, primary_seg(ic, p, i), y, nvis, ntest, nseg, hits);
     for (int j = 0; j < 6; ++j) out_y[6 * q + j] = (double)y[j];
     for (int k = 0; k < p.K; ++k) out_hits[q * p.K + k] = hits[k];
 }
@@ -467,16 +571,23 @@ __global__ void reduce_items_kernel(const double* __restrict__ part, int64_t ite
 template <int W>
 static cudaError_t launch_w(const DesignTable& tab, const TraceParams& p, int d0, int Dl, int grid, int block,
                             cudaStream_t st) {
-    trace_kernel<W><<<grid, block, 0, st>>>(tab, p, d0, Dl);
+    const size_t sm = trace_smem_bytes(block);
+    cudaError_t e = cudaFuncSetAttribute(trace_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    trace_kernel<W><<<grid, block, sm, st>>>(tab, p, d0, Dl);
     return cudaGetLastError();
 }
 
 int trace_resident_blocks(int width, int block) {
     int nb = 0;
-    if (width == 8)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<8>, block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<4>, block, 0);
+    const size_t sm = trace_smem_bytes(block);
+    if (width == 8) {
+        cudaFuncSetAttribute(trace_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<8>, block, sm);
+    } else {
+        cudaFuncSetAttribute(trace_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<4>, block, sm);
+    }
     return nb > 0 ? nb : 1;
 }
 
@@ -488,7 +599,8 @@ cudaError_t launch_trace(const std::vector<DesignDev>& designs, const TraceParam
         DesignTable tab;
         for (int k = 0; k < Dl; ++k) tab.d[k] = designs[d0 + k];
         const int64_t units = (int64_t)Dl * p.S * p.cpb;
-        const int grid = (int)std::min<int64_t>(units, grid_cap);
+        const int64_t wpb = block / 32;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + wpb - 1) / wpb, grid_cap));
         cudaError_t e = width == 8 ? launch_w<8>(tab, p, d0, Dl, grid, block, st)
                                    : launch_w<4>(tab, p, d0, Dl, grid, block, st);
         if (e != cudaSuccess) return e;

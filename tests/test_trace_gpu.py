@@ -78,7 +78,7 @@ def test_boxwing_per_ray_paths(srp, ctx):
     w = (2 * b.info()["radius"] / 512) ** 2
     assert np.max(np.abs(yg[same] - yo[same])) <= 1e-5 * w * 10  # per-ray, in units of the ray weight
     ft = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=512, max_bounces=3)
-    assert np.allclose(ft[0, 0], yg.sum(0), rtol=1e-9, atol=1e-12 * w)
+    assert np.allclose(ft[0, 0], yg.sum(0), rtol=1e-6, atol=1e-9 * w)  # FP32 per-lane partials
 
 
 def test_boxwing_direction_sweep(srp, ctx):
@@ -171,13 +171,14 @@ def test_deterministic_and_host_equals_device(srp, ctx):
     assert np.array_equal(f1, f3.cpu().numpy())
 
 
-def test_block_size_and_chunking_only_change_rounding(srp, ctx):
+def test_chunking_only_changes_rounding(srp, ctx):
     m, rho, sun, com = W.config1()
     b = _bvh(srp, ctx, m)
-    a = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=512, max_bounces=2, block_threads=256)
+    a = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=512, max_bounces=2)
     c = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=512, max_bounces=2, block_threads=128,
                       chunks_per_item=3)
-    assert np.allclose(a, c, rtol=1e-12, atol=1e-15)
+    # per-thread FP32 partials (<= 32 rays) group rays differently: FP32-level rounding
+    assert np.allclose(a, c, rtol=2e-7, atol=1e-12)
 
 
 def test_sun_sharding_bitwise(srp, ctx):
