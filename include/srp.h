@@ -165,6 +165,29 @@ int srp_force(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho,
               const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
               double* out_ft, double* out_sigma);
 
+/* ---- gradient (Sec. 4.1: the simulation is differentiable by construction
+ * in continuous parameters such as reflectance; Sec. 3.4 design parameters)
+ * For ONE design (bvh) and S sun directions, with upstream weights
+ * upstream [S][6] = dL/d(F_s, tau_s), returns the gradient of
+ * L = sum_s upstream_s . (F_s, tau_s) of the same estimate srp_force
+ * computes (same rays, same options):
+ *   d_rho   [G][2] float64   dL/d(rho_s, rho_d) per material group (exact
+ *                            along the fixed paths: the bounce branch
+ *                            probability does not depend on rho)
+ *   d_hinge [H]    float64   dL/d(hinge angle) (K = 1 only; H = 0 skips it):
+ *                            each ray's hit point is carried rigidly by its
+ *                            facet as the hinge turns, visibility fixed
+ * tri_hinge [T] int32 (by original triangle index; -1 = not on a hinge) and
+ * hinge_axes [H][6] (point, unit axis; the axes the design was instantiated
+ * with, srp_design_instantiate) describe the hinges; H <= 8.  The COM is
+ * held fixed.  Memory per opts->mem; SRP_EUNSUPPORTED for H > 0 with K > 1.
+ * Results are reproducible to FP32 rounding (per-warp FP32 atomics). */
+int srp_force_grad(srp_ctx* ctx, const srp_bvh* bvh, const float* rho, int G,
+                   const double* sun_dir, int S, const double* com,
+                   const int32_t* tri_hinge, const double* hinge_axes, int H,
+                   const srp_trace_opts* opts, const double* upstream,
+                   double* d_rho, double* d_hinge);
+
 /* Per-ray inspection (the estimator's individual samples): trace the n
  * grid rays ray_idx[n] (int64, each < rays_x*rays_y) of ONE design and ONE
  * sun direction with the same arithmetic as srp_force.

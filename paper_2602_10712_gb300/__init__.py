@@ -18,7 +18,8 @@ from . import _build
 
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
-           "srp_build_bvh_host", "srp_trace_rays",
+           "srp_build_bvh_host", "srp_trace_rays", "srp_force_grad", "SRPForce", "MLP",
+           "mlp_param_count",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
 SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_EDEVICE_LIMIT, SRP_ETIMEOUT, SRP_EUNSUPPORTED = range(7)
@@ -60,7 +61,7 @@ def load(build_if_needed: bool = True):
     path = _build.build() if build_if_needed else _build.LIB
     if not os.path.exists(path):
         raise ImportError(f"libsrp.so not found at {path}: run __graft_entry__.build()")
-    lib = C.CDLL(path, mode=C.RTLD_GLOBAL)
+    lib = C.CDLL(path)
     i32, i64 = C.c_int, C.c_int64
     lib.srp_last_error.restype = C.c_char_p
     lib.srp_trace_opts_default.argtypes = [C.POINTER(TraceOpts)]
@@ -73,6 +74,13 @@ def load(build_if_needed: bool = True):
     lib.srp_bvh_get_info.argtypes = [_P, C.POINTER(BVHInfo)]
     lib.srp_force.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P]
     lib.srp_collect_stats.argtypes = [_P, i32, _P]
+    lib.srp_force_grad.argtypes = [_P, _P, _P, i32, _P, i32, _P, _P, _P, i32, C.POINTER(TraceOpts), _P, _P, _P]
+    lib.srp_mlp_param_count.argtypes = [C.POINTER(C.c_int64)]
+    lib.srp_mlp_create.argtypes = [_P, _P, C.c_uint64, C.POINTER(_P)]
+    lib.srp_mlp_destroy.argtypes = [_P]
+    lib.srp_mlp_set_params.argtypes = [_P, _P, _P]
+    lib.srp_mlp_get_params.argtypes = [_P, _P, _P]
+    lib.srp_mlp_infer.argtypes = [_P, _P, _P, i64, _P, i32]
     lib.srp_build_bvh_host.argtypes = [_P, i32, _P, i32, i32, _P, C.POINTER(C.c_int64), _P, C.POINTER(C.c_int32)]
     lib.srp_trace_rays.argtypes = [_P, _P, _P, i32, _P, _P, _P, i64, i32, i32, C.POINTER(TraceOpts), _P, _P]
     _lib = lib
@@ -296,3 +304,135 @@ def srp_trace_rays(ctx: Context, bvh: BVH, rho, sun_dir, com, ray_idx, sun_index
     _check(lib.srp_trace_rays(ctx.handle, bvh.handle, _ptr(rho), rho.shape[0], _ptr(sun_dir), _ptr(com),
                               _ptr(ray_idx), ray_idx.shape[0], sun_index, design_index, C.byref(o), _ptr(y), _ptr(h)))
     return y, h
+
+
+def srp_force_grad(ctx: Context, bvh: BVH, rho, sun_dir, com, upstream, tri_hinge=None, hinge_axes=None, **opts):
+    """Gradient of L = sum_s upstream[s].(F_s, tau_s): (d_rho [G,2], d_hinge [H]).
+    numpy inputs -> host mode (synchronous); torch CUDA tensors -> device
+    mode (asynchronous; d_rho/d_hinge are new CUDA tensors)."""
+    lib = load()
+    H = 0 if hinge_axes is None else int(np.asarray(hinge_axes.shape[0] if hasattr(hinge_axes, "shape") else len(hinge_axes)))
+    if isinstance(rho, np.ndarray):
+        rho = _np(rho, np.float32).reshape(-1, 2)
+        sun_dir = _np(sun_dir, np.float64).reshape(-1, 3)
+        com = _np(com, np.float64).reshape(3)
+        up = _np(upstream, np.float64).reshape(-1, 6)
+        th = None if tri_hinge is None else _np(tri_hinge, np.int32)
+        ha = None if hinge_axes is None else _np(hinge_axes, np.float64).reshape(-1, 6)
+        d_rho = np.zeros((rho.shape[0], 2)); d_h = np.zeros(max(H, 1))
+        opts["mem"] = SRP_MEM_HOST
+    else:
+        import torch
+        up, th, ha = upstream, tri_hinge, hinge_axes
+        d_rho = torch.empty((rho.shape[-2], 2), dtype=torch.float64, device=rho.device)
+        d_h = torch.empty((max(H, 1),), dtype=torch.float64, device=rho.device)
+        opts["mem"] = SRP_MEM_DEVICE
+    o = make_opts(**opts)
+    _check(lib.srp_force_grad(ctx.handle, bvh.handle, _ptr(rho), rho.shape[-2], _ptr(sun_dir), sun_dir.shape[-2],
+                              _ptr(com), _ptr(th), _ptr(ha), H, C.byref(o), _ptr(up), _ptr(d_rho),
+                              _ptr(d_h) if H > 0 else None))
+    return d_rho, d_h[:H]
+
+
+class SRPForce:
+    """torch.autograd.Function over the tracer: (rho [G,2] float32, hinge
+    angles [H] float64) -> (F, tau) [S,6] float64 for one hinged design.
+    forward: srp_design_instantiate + srp_build_bvh + srp_force;
+    backward: srp_force_grad with the incoming gradient as upstream weights.
+    Use SRPForce.apply(ctx, design, rho, angles, sun_dir, com, opts_dict);
+    `design` = dict(verts, tris, group, vhinge, hinges)."""
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, ctx, design, rho, angles, sun_dir, com, opts):
+                v = srp_design_instantiate(design["verts"], design["vhinge"], design["hinges"],
+                                           angles.detach().cpu().numpy())
+                bvh = srp_build_bvh(ctx, v, design["tris"], design["group"], opts.get("width", 4))
+                o = {k: x for k, x in opts.items() if k != "width"}
+                r = rho.detach().reshape(1, -1, 2).contiguous().to(torch.float32)
+                sd = sun_dir.detach().contiguous().to(torch.float64)
+                cm = com.detach().reshape(1, 3).contiguous().to(torch.float64)
+                out = srp_force(ctx, [bvh], r, sd, cm, **o)[0]
+                fctx.save_for_backward(rho, angles, sun_dir, com)
+                fctx.bvh, fctx.srp_ctx, fctx.design, fctx.opts = bvh, ctx, design, o
+                return out
+
+            @staticmethod
+            def backward(fctx, g):
+                rho, angles, sun_dir, com = fctx.saved_tensors
+                d = fctx.design
+                H = len(d["hinges"])
+                th = torch.from_numpy(np.asarray(d["vhinge"])[np.asarray(d["tris"])[:, 0]].astype(np.int32)).to(rho.device)
+                ha = torch.from_numpy(np.asarray(d["hinges"], np.float64)).to(rho.device)
+                o = dict(fctx.opts)
+                use_h = H > 0 and o.get("max_bounces", 1) == 1
+                dr, dh = srp_force_grad(fctx.srp_ctx, fctx.bvh, rho.detach().reshape(-1, 2).contiguous().float(),
+                                        sun_dir.detach().contiguous().double(), com.detach().reshape(3).contiguous().double(),
+                                        g.contiguous().double(), th if use_h else None, ha if use_h else None, **o)
+                da = dh.to(angles.dtype) if use_h else None
+                return None, None, dr.to(rho.dtype).reshape(rho.shape), da, None, None, None
+
+        return _F
+
+    @classmethod
+    def apply(cls, *args):
+        return cls._fn().apply(*args)
+
+
+# ----------------------------------------------------------------- proxy MLP
+def mlp_param_count() -> int:
+    n = C.c_int64(0)
+    _check(load().srp_mlp_param_count(C.byref(n)))
+    return n.value
+
+
+class MLP:
+    """The neural proxy (srp_mlp): 19 -> 4x256 SiLU -> 6 on the tensor cores.
+    Parameters are the flat FP32 vector (W_l row-major [out][in], then b_l,
+    for l = 0..4)."""
+
+    def __init__(self, ctx: Context, params=None, seed: int = 0):
+        lib = load()
+        self.ctx = ctx
+        h = _P()
+        p = None if params is None else _np(params, np.float32)
+        _check(lib.srp_mlp_create(ctx.handle, _ptr(p), seed, C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.srp_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(mlp_param_count(), np.float32)
+        _check(load().srp_mlp_get_params(self.ctx.handle, self.handle, _ptr(out)))
+        return out
+
+    def set_params(self, p):
+        p = _np(p, np.float32)
+        _check(load().srp_mlp_set_params(self.ctx.handle, self.handle, _ptr(p)))
+
+    def infer(self, x, y=None):
+        """y [B,6] = P(x [B,19]); numpy -> synchronous host call, torch CUDA
+        float32 tensors -> asynchronous device call."""
+        if isinstance(x, np.ndarray):
+            x = _np(x, np.float32).reshape(-1, 19)
+            y = np.zeros((x.shape[0], 6), np.float32) if y is None else y
+            mem = SRP_MEM_HOST
+        else:
+            import torch
+            y = torch.empty((x.shape[0], 6), dtype=torch.float32, device=x.device) if y is None else y
+            mem = SRP_MEM_DEVICE
+        _check(load().srp_mlp_infer(self.ctx.handle, self.handle, _ptr(x), x.shape[0], _ptr(y), mem))
+        return y

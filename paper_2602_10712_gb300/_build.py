@@ -30,19 +30,19 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
-def _digest():
+def _digest(extra=()):
     h = hashlib.sha256()
     for f in sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))):
         h.update(open(f, "rb").read())
     h.update(open(os.path.join(os.path.dirname(HERE), "include", "srp.h"), "rb").read())
-    h.update(" ".join(ARCH + COMMON).encode())
+    h.update(" ".join(ARCH + COMMON + list(extra)).encode())
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     stamp = os.path.join(LIBDIR, "libsrp.stamp")
-    dg = _digest()
+    dg = _digest(extra_flags)
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dg:
         return LIB
     nvcc = _nvcc()
@@ -50,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(LIBDIR, os.path.basename(src) + ".o")
-        cmd = [nvcc] + ARCH + COMMON + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + COMMON + list(extra_flags) + ["-c", src, "-o", obj]
         if src.endswith(".cu"):
             cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and log:
                 print(log)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "-Bsymbolic", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -20,12 +20,23 @@ cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* ou
                           cudaStream_t st);
 cudaError_t launch_trace_rays(const DesignDev& dz, const TraceParams& p, const int64_t* ray_idx, int64_t nr,
                               int sidx, int didx, double* out_y, int32_t* out_hits, cudaStream_t st);
+void set_last_error(const std::string& msg);
+cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double* up, const int32_t* thinge,
+                        const double* hax, int H, double* gpart, double* d_rho, double* d_hinge, int n_sm,
+                        cudaStream_t st);
 }  // namespace srp
 
 using namespace srp;
 
 namespace {
 thread_local std::string g_err;
+}  // namespace
+
+// Message for srp_last_error() from other translation units of the library.
+void srp::set_last_error(const std::string& msg) { g_err = msg; }
+
+
+namespace {
 
 int fail(int code, const std::string& msg) {
     g_err = msg;
@@ -64,6 +75,7 @@ struct srp_ctx {
     unsigned long long* d_stats = nullptr;     // traversal counters
     bool stats_on = false;
     DevBuf part;                               // trace partials
+    DevBuf gpart;                              // gradient partials
     DevBuf stage_in, stage_out;                // host-mem staging
 };
 
@@ -115,7 +127,7 @@ int srp_ctx_destroy(srp_ctx* c) {
     if (!c) return SRP_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    c->part.release(); c->stage_in.release(); c->stage_out.release();
+    c->part.release(); c->gpart.release(); c->stage_in.release(); c->stage_out.release();
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_stats) cudaFree(c->d_stats);
     delete c;
@@ -489,3 +501,91 @@ extern "C" int srp_trace_rays(srp_ctx* c, const srp_bvh* bvh, const float* rho, 
     CU(cudaMemcpyAsync(out_hits, ob + yb, hb, cudaMemcpyDeviceToHost, c->stream), "D2H");
     return srp_sync(c);
 }
+
+extern "C" int srp_force_grad(srp_ctx* c, const srp_bvh* bvh, const float* rho, int G, const double* sun_dir, int S,
+                              const double* com, const int32_t* tri_hinge, const double* hinge_axes, int H,
+                              const srp_trace_opts* o, const double* upstream, double* d_rho, double* d_hinge) {
+    if (!o) return fail(SRP_EINVAL, "srp_force_grad: NULL opts");
+    if (H < 0 || H > 8) return fail(SRP_EINVAL, "srp_force_grad: H must be in 0..8");
+    if (H > 0 && o->max_bounces != 1)
+        return fail(SRP_EUNSUPPORTED, "srp_force_grad: hinge gradients are defined for max_bounces == 1");
+    if (H > 0 && (!tri_hinge || !hinge_axes || !d_hinge)) return fail(SRP_EINVAL, "srp_force_grad: NULL hinge arrays");
+    srp_trace_opts oo = *o;
+    oo.sun_per_design = 0;
+    std::vector<DesignDev> designs;
+    TraceParams p;
+    std::memset(&p, 0, sizeof p);
+    int width, block, grid_cap;
+    const srp_bvh* one[1] = {bvh};
+    if (oo.chunks_per_item == 0) {
+        const int64_t grid_n = (int64_t)o->rays_x * o->rays_y;
+        const int64_t n = o->ray_count > 0 ? o->ray_count : grid_n;
+        int64_t cpb = S > 0 ? (8192 + S - 1) / S : 1;
+        cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
+        oo.chunks_per_item = (int32_t)cpb;
+    }
+    int rc = force_plan(c, one, 1, G, S, &oo, &designs, &p, &width, &block, &grid_cap);
+    if (rc != SRP_OK) return rc;
+    if (S > 0 && (!rho || !sun_dir || !com || !upstream || !d_rho))
+        return fail(SRP_EINVAL, "srp_force_grad: NULL array argument");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    const int ng = 2 * G + H;
+    const int64_t units = (int64_t)S * p.cpb;
+    if (c->gpart.ensure(sizeof(double) * ng * (size_t)std::max<int64_t>(units, 1)) != cudaSuccess)
+        return fail(SRP_ENOMEM, "srp_force_grad: cannot allocate gradient partials");
+    if (o->mem == SRP_MEM_DEVICE) {
+        p.rho = rho; p.sun = sun_dir; p.com = com;
+        CU(launch_grad(designs[0], p, upstream, tri_hinge, hinge_axes, H, (double*)c->gpart.p, d_rho, d_hinge,
+                       c->n_sm, c->stream), "grad kernel launch");
+        return SRP_OK;
+    }
+    if (o->mem != SRP_MEM_HOST) return fail(SRP_EINVAL, "srp_force_grad: mem must be SRP_MEM_HOST or SRP_MEM_DEVICE");
+    if (S > 0) {
+        rc = validate_values(rho, 1, G, sun_dir, S);
+        if (rc != SRP_OK) return rc;
+    }
+    for (int h = 0; h < H; ++h) {
+        const double* a = hinge_axes + 6 * h + 3;
+        if (!(std::fabs(std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) - 1.0) < 1e-6))
+            return fail(SRP_EINVAL, "srp_force_grad: hinge axes must be unit vectors");
+    }
+    const int T = bvh->T;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t rb = al(sizeof(float) * 2 * G), sb = al(sizeof(double) * 3 * S), cb = al(sizeof(double) * 3),
+                 ub = al(sizeof(double) * 6 * S), tb = al(sizeof(int32_t) * std::max(T, 1)),
+                 hb = al(sizeof(double) * 6 * std::max(H, 1));
+    if (c->stage_in.ensure(rb + sb + cb + ub + tb + hb) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_grad: staging");
+    if (c->stage_out.ensure(al(sizeof(double) * ng) + 256) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_grad: staging");
+    char* in = (char*)c->stage_in.p;
+    char* ob = (char*)c->stage_out.p;
+    size_t off = 0;
+    auto put = [&](const void* src, size_t bytes, size_t slot) -> char* {
+        char* dst = in + off;
+        if (bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+        off += slot;
+        return dst;
+    };
+    p.rho = (const float*)put(rho, sizeof(float) * 2 * G, rb);
+    p.sun = (const double*)put(sun_dir, sizeof(double) * 3 * S, sb);
+    p.com = (const double*)put(com, sizeof(double) * 3, cb);
+    const double* d_up = (const double*)put(upstream, sizeof(double) * 6 * S, ub);
+    const int32_t* d_th = H > 0 ? (const int32_t*)put(tri_hinge, sizeof(int32_t) * T, tb) : nullptr;
+    if (H == 0) off += tb;
+    const double* d_hx = H > 0 ? (const double*)put(hinge_axes, sizeof(double) * 6 * H, hb) : nullptr;
+    CU(cudaGetLastError(), "H2D staging");
+    double* dr = (double*)ob;
+    double* dh = H > 0 ? dr + 2 * G : nullptr;
+    CU(launch_grad(designs[0], p, d_up, d_th, d_hx, H, (double*)c->gpart.p, dr, dh, c->n_sm, c->stream),
+       "grad kernel launch");
+    CU(cudaMemcpyAsync(d_rho, dr, sizeof(double) * 2 * G, cudaMemcpyDeviceToHost, c->stream), "D2H d_rho");
+    if (H > 0) CU(cudaMemcpyAsync(d_hinge, dh, sizeof(double) * H, cudaMemcpyDeviceToHost, c->stream), "D2H d_hinge");
+    return srp_sync(c);
+}
+
+// Context internals for other translation units of the library.
+namespace srp {
+cudaStream_t ctx_stream(srp_ctx* c) { return c->stream; }
+int ctx_device(srp_ctx* c) { return c->device; }
+int* ctx_err(srp_ctx* c) { return c->d_err; }
+int ctx_n_sm(srp_ctx* c) { return c->n_sm; }
+}  // namespace srp

@@ -1,0 +1,190 @@
+// grad.cu -- reverse-mode gradient of the SRP ray-grid estimate.
+//
+// For upstream weights g_s = dL/d(F_s, tau_s) (6 per sun direction) the
+// kernel returns dL/d(rho_s, rho_d) per material group and, for K = 1,
+// dL/d(hinge angle) per hinge.  It replays exactly the forward's rays (same
+// Philox counters, same traversal and shading helpers), so the gradient is
+// that of the very estimate srp_force returns:
+//  * reflectances: the branch choice has a fixed probability, so every path
+//    is fixed and its deposits are polynomials in rho (exact derivative);
+//    reverse sweep over the recorded hits, last hit first;
+//  * hinges (K = 1): each ray's surface element is carried rigidly by its
+//    facet, so its contribution (w / cos0) cos(a) q.G(n(a)) is differentiated
+//    in the rotation angle a (d n = axis x n, d x = axis x (x - p)); the
+//    visibility of each ray is held fixed (the estimate's boundary terms,
+//    where a shadow edge or silhouette moves, are not included).
+// Accumulation: per-warp FP32 shared-memory sums over <= 128 rays, flushed
+// into per-warp FP64, written as per-unit FP64 partials, summed in unit
+// order by grad_reduce_kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "trace_common.cuh"
+
+namespace srp {
+
+struct GradParams {
+    const double* up;       // [S][6] upstream weights
+    const int32_t* thinge;  // [T] hinge id by ORIGINAL triangle index (-1: fixed), or NULL
+    const double* hax;      // [H][6] hinge point (3), unit axis (3)
+    int H;
+    int ng;                 // 2G + H accumulated entries
+    double* gpart;          // [units][ng]
+};
+
+constexpr int kMaxGradEntries = 2 * kMaxGroups + 8;
+
+struct GradWarpSmem {
+    float f[kMaxGradEntries];
+    double d[kMaxGradEntries];
+};
+
+template <int W>
+__global__ void __launch_bounds__(128) grad_kernel(const DesignDev dz, const TraceParams p, const GradParams g) {
+    __shared__ GradWarpSmem sm[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    GradWarpSmem& ws = sm[warp];
+    const int64_t units = (int64_t)p.S * p.cpb;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    uint32_t nvis = 0, ntest = 0;
+    for (int e = lane; e < kMaxGradEntries; e += 32) { ws.f[e] = 0.0f; ws.d[e] = 0.0; }
+    __syncwarp();
+    for (int64_t u = gw; u < units; u += nw) {
+        const int s = (int)(u / p.cpb);
+        const int64_t cidx = u % p.cpb;
+        ItemConst ic;
+        item_setup(ic, dz, p, p.sun + 3 * (size_t)s, p.com, p.rho, p.design_base, p.sun_base + s);
+        const double* up = g.up + 6 * (size_t)s;
+        const float3 gF = f3((float)up[0], (float)up[1], (float)up[2]);
+        const float3 gT = f3((float)up[3], (float)up[4], (float)up[5]);
+        const int64_t k0 = cidx * p.chunk;
+        const int64_t k1 = min(k0 + p.chunk, p.n);
+        int batch = 0;
+        for (int64_t kb = k0; kb < k1; kb += 32, ++batch) {
+            const int64_t k = kb + lane;
+            if (k < k1) {
+                const uint64_t i = (uint64_t)(p.off + k * p.stride);
+                Seg s0 = primary_seg(ic, p, i);
+                // ---- forward replay with the path recorded
+                int m = 0;
+                int fr[kMaxBounces], br[kMaxBounces];
+                float3 xr[kMaxBounces], nr[kMaxBounces], dr[kMaxBounces], dout_r[kMaxBounces];
+                float csr[kMaxBounces], wr[kMaxBounces], rsr[kMaxBounces], rdr[kMaxBounces];
+                int gr[kMaxBounces];
+                Seg sg = s0;
+#pragma unroll 1
+                for (int kk = 1; kk <= p.K; ++kk) {
+                    RaySetup rs;
+                    setup_ray(rs, sg.o, sg.d);
+                    float t;
+                    const int f = closest_hit<W>(dz, rs, kk == 1 ? 0.0f : ic.tmin_b, sg.src, t, p.err, nvis, ntest);
+                    if (f < 0) break;
+                    const HitGeom h = hit_geom(dz, ic, f, t, sg);
+                    const int q = kk - 1;
+                    fr[q] = f; xr[q] = h.x; nr[q] = h.n; dr[q] = sg.d; csr[q] = h.cs; wr[q] = sg.w;
+                    rsr[q] = h.rs; rdr[q] = h.rd; gr[q] = h.g;
+                    m = kk;
+                    if (kk == p.K) break;
+                    float3 dout;
+                    float wout;
+                    br[q] = bounce_dir(ic, p, (uint32_t)i, kk, h, sg, dout, wout);
+                    dout_r[q] = dout;
+                    sg.o = h.x; sg.d = dout; sg.w = wout; sg.src = f;
+                }
+                // ---- reverse sweep: L = sum_k q_k . dp_k, q_k = gF + gT x (x_k - com)
+                float wbar_next = 0.0f;
+#pragma unroll 1
+                for (int q = m - 1; q >= 0; --q) {
+                    const float3 qv = gF + cross(gT, xr[q] - ic.com);
+                    const float w = wr[q];
+                    float wbar;
+                    if (q + 1 == p.K) {
+                        const float qd = dot(qv, dr[q]), qn = dot(qv, nr[q]);
+                        atomicAdd(&ws.f[2 * gr[q]], w * (-qd - 2.0f * csr[q] * qn));
+                        atomicAdd(&ws.f[2 * gr[q] + 1], w * (-(2.0f / 3.0f) * qn));
+                        wbar = (1.0f - rsr[q]) * qd - (2.0f * rsr[q] * csr[q] + (2.0f / 3.0f) * rdr[q]) * qn;
+                    } else {
+                        const float wbar_out = wbar_next - dot(qv, dout_r[q]);
+                        wbar = dot(qv, dr[q]);
+                        const float rb = br[q] == 0 ? rsr[q] : rdr[q];
+                        atomicAdd(&ws.f[2 * gr[q] + br[q]], wbar_out * 2.0f * w);
+                        wbar += wbar_out * 2.0f * rb;
+                    }
+                    wbar_next = wbar;
+                }
+                // ---- hinge angle (K = 1): surface element carried by its facet
+                if (g.H > 0 && p.K == 1 && m == 1) {
+                    const uint32_t orig = __float_as_uint(__ldg(dz.tri + 3 * (size_t)fr[0]).w);
+                    const int hh = g.thinge ? __ldg(g.thinge + orig) : -1;
+                    if (hh >= 0 && hh < g.H) {
+                        const double* hp = g.hax + 6 * hh;
+                        const float3 ap = f3((float)hp[0], (float)hp[1], (float)hp[2]);
+                        const float3 aa = f3((float)hp[3], (float)hp[4], (float)hp[5]);
+                        const float3 x = xr[0], n = nr[0], d = dr[0];
+                        const float c = csr[0], rs = rsr[0], rd = rdr[0];
+                        const float3 qv = gF + cross(gT, x - ic.com);
+                        const float cn = 2.0f * rs * c + (2.0f / 3.0f) * rd;
+                        const float3 Gv = (1.0f - rs) * d - cn * n;
+                        const float3 dn = cross(aa, n);
+                        const float3 dx = cross(aa, x - ap);
+                        const float dc = -dot(dn, d);
+                        const float3 dq = cross(gT, dx);
+                        const float3 dG = (-2.0f * rs * dc) * n - cn * dn;
+                        const float dphi = dc * dot(qv, Gv) + c * (dot(dq, Gv) + dot(qv, dG));
+                        atomicAdd(&ws.f[2 * p.G + hh], (wr[0] / c) * dphi);
+                    }
+                }
+            }
+            __syncwarp();
+            if ((batch & 3) == 3 || kb + 32 >= k1) {   // flush FP32 sums (<= 128 rays) to FP64
+                for (int e = lane; e < g.ng; e += 32) { ws.d[e] += (double)ws.f[e]; ws.f[e] = 0.0f; }
+                __syncwarp();
+            }
+        }
+        for (int e = lane; e < g.ng; e += 32) {
+            g.gpart[(size_t)u * g.ng + e] = ws.d[e];
+            ws.d[e] = 0.0;
+        }
+        __syncwarp();
+    }
+    if (p.stats) {
+        unsigned long long a = nvis, b = ntest;
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, off);
+            b += __shfl_xor_sync(0xffffffffu, b, off);
+        }
+        if (lane == 0) { atomicAdd(p.stats, a); atomicAdd(p.stats + 1, b); }
+    }
+}
+
+__global__ void grad_reduce_kernel(const double* __restrict__ gpart, int64_t units, int ng, int G, double* d_rho,
+                                   double* d_hinge) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ng) return;
+    double t = 0.0;
+    for (int64_t u = 0; u < units; ++u) t += gpart[(size_t)u * ng + e];
+    if (e < 2 * G) d_rho[e] = t;
+    else if (d_hinge) d_hinge[e - 2 * G] = t;
+}
+
+cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double* up, const int32_t* thinge,
+                        const double* hax, int H, double* gpart, double* d_rho, double* d_hinge, int n_sm,
+                        cudaStream_t st) {
+    GradParams g;
+    g.up = up; g.thinge = thinge; g.hax = hax; g.H = H; g.ng = 2 * p.G + H; g.gpart = gpart;
+    const int64_t units = (int64_t)p.S * p.cpb;
+    if (units > 0 && p.n > 0) {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + 3) / 4, (int64_t)n_sm * 8));
+        if (dz.width == 8) grad_kernel<8><<<grid, 128, 0, st>>>(dz, p, g);
+        else grad_kernel<4><<<grid, 128, 0, st>>>(dz, p, g);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    grad_reduce_kernel<<<(g.ng + 127) / 128, 128, 0, st>>>(gpart, units, g.ng, p.G, d_rho, d_hinge);
+    return cudaGetLastError();
+}
+
+}  // namespace srp

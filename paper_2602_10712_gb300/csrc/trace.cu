@@ -24,308 +24,9 @@
 #include <algorithm>
 #include <vector>
 
-#include "srp_internal.h"
+#include "trace_common.cuh"
 
 namespace srp {
-
-struct DesignTable {
-    DesignDev d[kMaxDesignsPerLaunch];
-};
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), 10 rounds.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    }
-    return c;
-}
-// uniform in [0,1) from the top 24 bits (exact in FP32)
-__device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
-
-// ---------------------------------------------------------------------------
-// small vector helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
-__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 cross(float3 a, float3 b) {
-    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
-
-// ---------------------------------------------------------------------------
-// Ray state for traversal: slab-test constants and watertight shear.
-// ---------------------------------------------------------------------------
-struct RaySetup {
-    float3 o, d;
-    float3 inv;      // 1/d (zeros replaced by +-1e-30)
-    float3 oinv;     // o * inv
-    float3 mx, my, mz;  // shear rows: A_x = mx.A, A_y = my.A, A_z = mz.A
-};
-
-__device__ __forceinline__ float safe_inv(float x) {
-    return 1.0f / (fabsf(x) > 1e-30f ? x : copysignf(1e-30f, x));
-}
-
-__device__ __forceinline__ void setup_ray(RaySetup& r, float3 o, float3 d) {
-    r.o = o; r.d = d;
-    r.inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
-    r.oinv = f3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
-    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-    int kz = 0;
-    if (ay > ax && ay >= az) kz = 1;
-    else if (az > ax && az > ay) kz = 2;
-    int kx = kz == 2 ? 0 : kz + 1;
-    int ky = kx == 2 ? 0 : kx + 1;
-    const float dk[3] = {d.x, d.y, d.z};
-    if (dk[kz] < 0.0f) { int t = kx; kx = ky; ky = t; }
-    const float Sx = dk[kx] / dk[kz], Sy = dk[ky] / dk[kz], Sz = 1.0f / dk[kz];
-    float m[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    m[0][kx] = 1.0f; m[0][kz] = -Sx;
-    m[1][ky] = 1.0f; m[1][kz] = -Sy;
-    m[2][kz] = Sz;
-    r.mx = f3(m[0][0], m[0][1], m[0][2]);
-    r.my = f3(m[1][0], m[1][1], m[1][2]);
-    r.mz = f3(m[2][0], m[2][1], m[2][2]);
-}
-
-// Watertight test; returns t, or -1 when missed (callers need t > tmin >= 0).  Edge functions use
-// products without FMA contraction so shared edges are exactly antisymmetric.
-__device__ __forceinline__ float hit_triangle(const RaySetup& r, float3 p0, float3 p1, float3 p2) {
-    const float3 A = p0 - r.o, B = p1 - r.o, C = p2 - r.o;
-    const float Ax = dot(r.mx, A), Ay = dot(r.my, A);
-    const float Bx = dot(r.mx, B), By = dot(r.my, B);
-    const float Cx = dot(r.mx, C), Cy = dot(r.my, C);
-    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-    if (U == 0.0f || V == 0.0f || W == 0.0f) {   // recompute exactly-zero edges in FP64
-        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
-        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
-        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
-    }
-    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
-    const float det = U + V + W;
-    if (det == 0.0f) return -1.0f;
-    const float T = U * dot(r.mz, A) + V * dot(r.mz, B) + W * dot(r.mz, C);
-    return T / det;
-}
-
-// ---------------------------------------------------------------------------
-// Closest hit through a W-wide BVH.  Returns the leaf-order triangle index
-// (or -1) and sets tb.  Ties on t go to the smaller original index.
-// ---------------------------------------------------------------------------
-template <int W>
-__device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& r, float tmin, int skip,
-                                           float& tb, int* err, uint32_t& nvis, uint32_t& ntest) {
-    constexpr int NF4 = W == 4 ? 8 : 16;  // float4 per node
-    const float4* __restrict__ nodes = dz.nodes;
-    const float4* __restrict__ tri = dz.tri;
-    int2 stack[kStackSize];
-    int sp = 0;
-    int best = -1;
-    uint32_t best_id = 0xffffffffu;
-    tb = INFINITY;
-    int ni = 0;
-    int visits = 0;
-    const bool nx_ = r.inv.x < 0.0f, ny_ = r.inv.y < 0.0f, nz_ = r.inv.z < 0.0f;
-    while (true) {
-        if (++visits > kVisitCap) { atomicOr(err, kErrVisitCap); return -1; }
-        ++nvis;
-        const float4* nd = nodes + (size_t)ni * NF4;
-        float tn[W];
-        bool hit[W];
-        int child[W];
-#pragma unroll
-        for (int h = 0; h < W / 4; ++h) {
-            const float4 lox = __ldg(nd + 0 * (W / 4) + h), hix = __ldg(nd + 1 * (W / 4) + h);
-            const float4 loy = __ldg(nd + 2 * (W / 4) + h), hiy = __ldg(nd + 3 * (W / 4) + h);
-            const float4 loz = __ldg(nd + 4 * (W / 4) + h), hiz = __ldg(nd + 5 * (W / 4) + h);
-            const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * (W / 4)) + h);
-            const float4 ax = nx_ ? hix : lox, bx = nx_ ? lox : hix;
-            const float4 ay = ny_ ? hiy : loy, by = ny_ ? loy : hiy;
-            const float4 az = nz_ ? hiz : loz, bz = nz_ ? loz : hiz;
-            const float ax_[4] = {ax.x, ax.y, ax.z, ax.w}, bx_[4] = {bx.x, bx.y, bx.z, bx.w};
-            const float ay_[4] = {ay.x, ay.y, ay.z, ay.w}, by_[4] = {by.x, by.y, by.z, by.w};
-            const float az_[4] = {az.x, az.y, az.z, az.w}, bz_[4] = {bz.x, bz.y, bz.z, bz.w};
-            const int ch_[4] = {ch.x, ch.y, ch.z, ch.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float n0 = fmaf(ax_[q], r.inv.x, -r.oinv.x), f0 = fmaf(bx_[q], r.inv.x, -r.oinv.x);
-                const float n1 = fmaf(ay_[q], r.inv.y, -r.oinv.y), f1 = fmaf(by_[q], r.inv.y, -r.oinv.y);
-                const float n2 = fmaf(az_[q], r.inv.z, -r.oinv.z), f2 = fmaf(bz_[q], r.inv.z, -r.oinv.z);
-                const float tnear = fmaxf(fmaxf(n0, n1), fmaxf(n2, tmin));
-                const float tfar = fminf(fminf(f0, f1), fminf(f2, tb));
-                tn[4 * h + q] = tnear;
-                hit[4 * h + q] = tnear <= tfar;
-                child[4 * h + q] = ch_[q];
-            }
-        }
-        // leaves first: they may shrink tb before inner children are queued
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-            if (hit[c] && child[c] < 0) {
-                const int code = ~child[c];
-                const int first = code >> 3, cnt = (code & 7) + 1;
-                ntest += cnt;
-                for (int q = 0; q < cnt; ++q) {
-                    const int f = first + q;
-                    if (f == skip) continue;
-                    const float4 a = __ldg(tri + 3 * (size_t)f);
-                    const float4 b = __ldg(tri + 3 * (size_t)f + 1);
-                    const float4 cc = __ldg(tri + 3 * (size_t)f + 2);
-                    const float t = hit_triangle(r, xyz(a), xyz(b), xyz(cc));
-                    if (t > tmin && t <= tb) {
-                        const uint32_t id = __float_as_uint(a.w);
-                        if (t < tb || id < best_id) { tb = t; best = f; best_id = id; }
-                    }
-                }
-            }
-        }
-        int next = -1;
-        float tnext = INFINITY;
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-            if (hit[c] && child[c] >= 0 && tn[c] <= tb) {
-                if (tn[c] < tnext) {
-                    if (next >= 0) {
-                        if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
-                        stack[sp++] = make_int2(next, __float_as_int(tnext));
-                    }
-                    next = child[c]; tnext = tn[c];
-                } else {
-                    if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
-                    stack[sp++] = make_int2(child[c], __float_as_int(tn[c]));
-                }
-            }
-        }
-        if (next >= 0) { ni = next; continue; }
-        bool found = false;
-        while (sp > 0) {
-            const int2 e = stack[--sp];
-            if (__int_as_float(e.y) <= tb) { ni = e.x; found = true; break; }
-        }
-        if (!found) break;
-    }
-    return best;
-}
-
-// ---------------------------------------------------------------------------
-// A ray segment and the shading of its hit.
-// ---------------------------------------------------------------------------
-struct Seg {
-    float3 o, d;
-    float w;
-    int src;  // leaf-order index of the triangle the segment leaves (-1: primary)
-};
-
-// Per-item constants shared by every ray of one (design, sun).
-struct ItemConst {
-    float3 ob, bu, bv, dd, com;
-    float fdx, fdy, w0, tmin_b;
-    const float* rho;
-    int dglob, sglob;
-};
-
-__device__ __forceinline__ void item_setup(ItemConst& ic, const DesignDev& dz, const TraceParams& p,
-                                           const double* sp, const double* cp, const float* rho,
-                                           int dglob, int sglob) {
-    // branchless ONB of d = -e (Duff et al. 2017) in FP64, rounded once
-    const double dx_ = -sp[0], dy_ = -sp[1], dz_ = -sp[2];
-    const double sgn = dz_ >= 0.0 ? 1.0 : -1.0;
-    const double aa = -1.0 / (sgn + dz_);
-    const double bb = dx_ * dy_ * aa;
-    const double u0 = 1.0 + sgn * dx_ * dx_ * aa, u1 = sgn * bb, u2 = -sgn * dx_;
-    const double v0 = bb, v1 = sgn + dy_ * dy_ * aa, v2 = -dy_;
-    const double R = dz.R;
-    const double pdx = 2.0 * R / p.nx, pdy = 2.0 * R / p.ny;
-    ic.ob = f3((float)(dz.cx - R * u0 - R * v0 - 2.0 * R * dx_), (float)(dz.cy - R * u1 - R * v1 - 2.0 * R * dy_),
-               (float)(dz.cz - R * u2 - R * v2 - 2.0 * R * dz_));
-    ic.bu = f3((float)u0, (float)u1, (float)u2);
-    ic.bv = f3((float)v0, (float)v1, (float)v2);
-    ic.dd = f3((float)dx_, (float)dy_, (float)dz_);
-    ic.fdx = (float)pdx; ic.fdy = (float)pdy;
-    ic.w0 = (float)(p.P * pdx * pdy);
-    ic.com = f3((float)cp[0], (float)cp[1], (float)cp[2]);
-    ic.tmin_b = (float)(1e-6 * R);
-    ic.rho = rho;
-    ic.dglob = dglob; ic.sglob = sglob;
-}
-
-// Primary segment of grid ray i (jittered pixel origin, travel direction d).
-__device__ __forceinline__ Seg primary_seg(const ItemConst& ic, const TraceParams& p, uint64_t i) {
-    const uint32_t px = (uint32_t)(i % (uint64_t)p.nx), py = (uint32_t)(i / (uint64_t)p.nx);
-    float xi1 = 0.5f, xi2 = 0.5f;
-    if (p.jitter) {
-        const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)ic.sglob, (uint32_t)ic.dglob, 0u),
-                                        (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-        xi1 = unit24(rnd.x); xi2 = unit24(rnd.y);
-    }
-    const float a = ((float)px + xi1) * ic.fdx, b = ((float)py + xi2) * ic.fdy;
-    Seg s;
-    s.o = f3(fmaf(a, ic.bu.x, fmaf(b, ic.bv.x, ic.ob.x)), fmaf(a, ic.bu.y, fmaf(b, ic.bv.y, ic.ob.y)),
-             fmaf(a, ic.bu.z, fmaf(b, ic.bv.z, ic.ob.z)));
-    s.d = ic.dd;
-    s.w = ic.w0;
-    s.src = -1;
-    return s;
-}
-
-// Momentum deposit of hit k (1-based) on leaf-order triangle f at ray
-// parameter t; returns true (and the outgoing segment) if the path goes on.
-__device__ __forceinline__ bool shade_hit(const DesignDev& dz, const ItemConst& ic, const TraceParams& p,
-                                          uint32_t i, int k, int f, float t, const Seg& s, float y[6],
-                                          Seg& out) {
-    const float4 a = __ldg(dz.tri + 3 * (size_t)f);
-    const float4 b = __ldg(dz.tri + 3 * (size_t)f + 1);
-    const float4 c = __ldg(dz.tri + 3 * (size_t)f + 2);
-    float3 n = cross(xyz(b) - xyz(a), xyz(c) - xyz(a));
-    n = rsqrtf(dot(n, n)) * n;
-    if (dot(n, s.d) > 0.0f) n = -1.0f * n;
-    const float cs = -dot(n, s.d);
-    const int g = (int)__float_as_uint(b.w);
-    const float rs = __ldg(ic.rho + 2 * g), rd = __ldg(ic.rho + 2 * g + 1);
-    const float3 x = s.o + t * s.d;
-    const float3 arm = x - ic.com;
-    if (k == p.K) {
-        const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
-        const float3 dp = s.w * ((1.0f - rs) * s.d - cn * n);
-        const float3 tq = cross(arm, dp);
-        y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
-        return false;
-    }
-    const uint4 rnd = philox4x32_10(make_uint4(i, (uint32_t)ic.sglob, (uint32_t)ic.dglob, (uint32_t)k),
-                                    (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-    float3 dout;
-    float wout;
-    if (unit24(rnd.x) < 0.5f) {
-        dout = s.d + (2.0f * cs) * n;
-        wout = 2.0f * s.w * rs;
-    } else {
-        // Lambertian: direction of n + (uniform unit vector), pdf cos/pi
-        const float z = 1.0f - 2.0f * unit24(rnd.y);
-        const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
-        float sp, cp;
-        sincospif(2.0f * unit24(rnd.z), &sp, &cp);
-        const float3 v = f3(n.x + rr * cp, n.y + rr * sp, n.z + z);
-        const float l2 = dot(v, v);
-        dout = l2 > 0.0f ? rsqrtf(l2) * v : n;
-        wout = 2.0f * s.w * rd;
-    }
-    const float3 dp = s.w * s.d - wout * dout;
-    const float3 tq = cross(arm, dp);
-    y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
-    out.o = x; out.d = dout; out.w = wout; out.src = f;
-    return true;
-}
 
 // Whole path of one ray in one thread (used by the per-ray inspection).
 template <int W>
@@ -344,6 +45,70 @@ __device__ __forceinline__ void trace_path(const DesignDev& dz, const ItemConst&
         if (!shade_hit(dz, ic, p, i, k, f, t, s, y, nx)) break;
         s = nx;
     }
+}
+
+// Out-of-line trace and shade, so the wavefront kernel holds one copy of
+// each however many places it traces from (keeps the code in the I-cache).
+struct HitOut {
+    int f;
+    float t;
+    uint32_t nvis, ntest;
+};
+
+template <int W>
+__device__ __noinline__ HitOut trace_segment(const float4* __restrict__ nodes, const float4* __restrict__ tri,
+                                             float ox, float oy, float oz, float dx, float dy, float dz,
+                                             float tmin, int skip, int* err) {
+    RaySetup r;
+    setup_ray(r, f3(ox, oy, oz), f3(dx, dy, dz));
+    DesignDev z;
+    z.nodes = nodes;
+    z.tri = tri;
+    HitOut h;
+    h.nvis = 0;
+    h.ntest = 0;
+    h.f = closest_hit<W>(z, r, tmin, skip, h.t, err, h.nvis, h.ntest);
+    return h;
+}
+
+struct ShadeOut {
+    float ox, oy, oz, dx, dy, dz, w;
+    int src;
+    int cont;
+};
+
+// Shade hit k of segment (o, d, w) on triangle f; y points at the ray's
+// six running sums (shared memory, stride ys) and is updated in place.
+__device__ __noinline__ ShadeOut shade_segment(const float4* __restrict__ tri, const float* __restrict__ rho,
+                                               float cx, float cy, float cz, int K, uint64_t seed, int sglob,
+                                               int dglob, uint32_t i, int k, int f, float t, float ox, float oy,
+                                               float oz, float dx, float dy, float dz, float w, float* y, int ys) {
+    DesignDev z;
+    z.tri = tri;
+    ItemConst ic;
+    ic.com = f3(cx, cy, cz);
+    ic.rho = rho;
+    ic.sglob = sglob;
+    ic.dglob = dglob;
+    TraceParams p;
+    p.K = K;
+    p.seed = seed;
+    Seg s;
+    s.o = f3(ox, oy, oz);
+    s.d = f3(dx, dy, dz);
+    s.w = w;
+    s.src = -1;
+    float yy[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) yy[q] = y[q * ys];
+    Seg nx;
+    const bool cont = shade_hit(z, ic, p, i, k, f, t, s, yy, nx);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) y[q * ys] = yy[q];
+    ShadeOut o;
+    o.ox = nx.o.x; o.oy = nx.o.y; o.oz = nx.o.z; o.dx = nx.d.x; o.dy = nx.d.y; o.dz = nx.d.z;
+    o.w = nx.w; o.src = nx.src; o.cont = cont ? 1 : 0;
+    return o;
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -368,7 +133,13 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // Only __syncwarp is needed inside a unit.  Each ray's arithmetic and
 // deposit order (bounce 1, 2, 3) are those of trace_path.
 // ---------------------------------------------------------------------------
-constexpr int kBatches = 8;               // primary batches of 32 rays per tile
+#ifndef SRP_BATCHES
+#define SRP_BATCHES 4
+#endif
+#ifndef SRP_MIN_BLOCKS
+#define SRP_MIN_BLOCKS 5
+#endif
+constexpr int kBatches = SRP_BATCHES;     // primary batches of 32 rays per tile
 constexpr int kTile = 32 * kBatches;      // rays per warp tile
 constexpr int kQueue = 64;                // bounce segments per warp (<= 31 + 32 live)
 constexpr int kWarpsPerBlock = 4;
@@ -399,8 +170,42 @@ __device__ __forceinline__ void q_push(WarpSmem& ws, int& qcount, bool want, con
     __syncwarp();
 }
 
+// Trace the top `nb` queued segments (one per lane) and shade their hits.
 template <int W>
-__global__ void __launch_bounds__(128, 4) trace_kernel(const __grid_constant__ DesignTable tab, const TraceParams p,
+__device__ __forceinline__ void q_batch(WarpSmem& ws, int& qcount, int nb, const DesignDev& dz, const ItemConst& ic,
+                                        const TraceParams& p, int64_t ts, int lane, uint32_t& nvis,
+                                        uint32_t& ntest, uint32_t& nseg) {
+    const bool has = lane < nb;
+    float4 A = make_float4(0, 0, 0, 0), Bv = make_float4(0, 0, 0, 0);
+    int q = 0;
+    if (has) {
+        const int e = qcount - 1 - lane;
+        A = ws.qa[e]; Bv = ws.qb[e]; q = ws.qs[e];
+    }
+    __syncwarp();
+    qcount -= nb;
+    const int slot = q & 0xffff, kb = q >> 16;
+    bool cont = false;
+    Seg nx;
+    if (has) {
+        ++nseg;
+        const HitOut h = trace_segment<W>(dz.nodes, dz.tri, A.x, A.y, A.z, Bv.x, Bv.y, Bv.z, ic.tmin_b,
+                                          __float_as_int(Bv.w), p.err);
+        nvis += h.nvis; ntest += h.ntest;
+        if (h.f >= 0) {
+            const uint64_t i = (uint64_t)(p.off + (ts + slot) * p.stride);
+            const ShadeOut so = shade_segment(dz.tri, ic.rho, ic.com.x, ic.com.y, ic.com.z, p.K, p.seed, ic.sglob,
+                                              ic.dglob, (uint32_t)i, kb, h.f, h.t, A.x, A.y, A.z, Bv.x, Bv.y, Bv.z,
+                                              A.w, &ws.ys[0][slot], kTile);
+            cont = so.cont != 0;
+            nx.o = f3(so.ox, so.oy, so.oz); nx.d = f3(so.dx, so.dy, so.dz); nx.w = so.w; nx.src = so.src;
+        }
+    }
+    q_push(ws, qcount, cont, nx, slot, kb + 1, lane);
+}
+
+template <int W>
+__global__ void __launch_bounds__(128, SRP_MIN_BLOCKS) trace_kernel(const __grid_constant__ DesignTable tab, const TraceParams p,
                                                        int d0, int Dl) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -429,65 +234,33 @@ __global__ void __launch_bounds__(128, 4) trace_kernel(const __grid_constant__ D
 #pragma unroll
                 for (int q = 0; q < 6; ++q) ws.ys[q][j * 32 + lane] = 0.0f;
             __syncwarp();
-            // ---- one work loop, one trace site: each iteration the warp takes
-            // 32 queued bounce segments if there are that many, else the next
-            // batch of 32 primary rays, else the remaining queued segments.
-            int next_batch = 0;
+            // ---- primary batches (coherent), bounce batches whenever 32 are queued
 #pragma unroll 1
-            while (true) {
-                int nb;
-                const bool primary = qcount < 32 && next_batch < kBatches;
-                if (primary) nb = 32;
-                else if (qcount > 0) nb = min(qcount, 32);
-                else break;
-                bool has;
-                Seg sg;
-                int slot, kb;
-                uint64_t i = 0;
-                if (primary) {
-                    slot = next_batch * 32 + lane;
-                    const int64_t k = ts + slot;
-                    has = k < k1;
-                    kb = 1;
-                    if (has) {
-                        i = (uint64_t)(p.off + k * p.stride);
-                        sg = primary_seg(ic, p, i);
-                    }
-                    ++next_batch;
-                } else {
-                    has = lane < nb;
-                    slot = 0; kb = 0;
-                    if (has) {
-                        const int e = qcount - 1 - lane;
-                        const float4 A = ws.qa[e], Bv = ws.qb[e];
-                        const int q = ws.qs[e];
-                        sg.o = f3(A.x, A.y, A.z); sg.w = A.w;
-                        sg.d = f3(Bv.x, Bv.y, Bv.z); sg.src = __float_as_int(Bv.w);
-                        slot = q & 0xffff; kb = q >> 16;
-                        i = (uint64_t)(p.off + (ts + slot) * p.stride);
-                    }
-                    __syncwarp();
-                    qcount -= nb;
-                }
-                bool cont = false;
+            for (int j = 0; j < kBatches; ++j) {
+                const int slot = j * 32 + lane;
+                const int64_t k = ts + slot;
                 Seg nx;
-                if (has) {
-                    RaySetup rs;
-                    setup_ray(rs, sg.o, sg.d);
-                    float t;
+                bool cont = false;
+                if (k < k1) {
+                    const uint64_t i = (uint64_t)(p.off + k * p.stride);
+                    const Seg sg = primary_seg(ic, p, i);
                     ++nseg;
-                    const int f = closest_hit<W>(dz, rs, kb == 1 ? 0.0f : ic.tmin_b, sg.src, t, p.err, nvis, ntest);
-                    if (f >= 0) {
-                        float y[6];
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) y[q] = ws.ys[q][slot];
-                        cont = shade_hit(dz, ic, p, (uint32_t)i, kb, f, t, sg, y, nx);
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) ws.ys[q][slot] = y[q];
+                    const HitOut h = trace_segment<W>(dz.nodes, dz.tri, sg.o.x, sg.o.y, sg.o.z, sg.d.x, sg.d.y,
+                                                      sg.d.z, 0.0f, -1, p.err);
+                    nvis += h.nvis; ntest += h.ntest;
+                    if (h.f >= 0) {
+                        const ShadeOut so = shade_segment(dz.tri, ic.rho, ic.com.x, ic.com.y, ic.com.z, p.K, p.seed,
+                                                          ic.sglob, ic.dglob, (uint32_t)i, 1, h.f, h.t, sg.o.x,
+                                                          sg.o.y, sg.o.z, sg.d.x, sg.d.y, sg.d.z, sg.w,
+                                                          &ws.ys[0][slot], kTile);
+                        cont = so.cont != 0;
+                        nx.o = f3(so.ox, so.oy, so.oz); nx.d = f3(so.dx, so.dy, so.dz); nx.w = so.w; nx.src = so.src;
                     }
                 }
-                q_push(ws, qcount, cont, nx, slot, kb + 1, lane);
+                q_push(ws, qcount, cont, nx, slot, 2, lane);
+                while (qcount >= 32) q_batch<W>(ws, qcount, 32, dz, ic, p, ts, lane, nvis, ntest, nseg);
             }
+            while (qcount > 0) q_batch<W>(ws, qcount, min(qcount, 32), dz, ic, p, ts, lane, nvis, ntest, nseg);
             // ---- per-ray sums -> per-lane partials (slot parity = ray parity)
             float accf[6] = {0, 0, 0, 0, 0, 0}, sqf[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll

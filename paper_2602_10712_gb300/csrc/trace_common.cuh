@@ -1,0 +1,338 @@
+// trace_common.cuh -- device-side pieces shared by the SRP tracer kernels
+// (trace.cu) and the gradient kernels (grad.cu): Philox4x32-10, ray set-up,
+// the watertight ray/triangle test, wide-BVH closest-hit traversal, ray
+// generation and the per-hit shading of the estimator.  Keeping them in one
+// place keeps the forward and the adjoint on identical arithmetic.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "srp_internal.h"
+
+namespace srp {
+
+struct DesignTable {
+    DesignDev d[kMaxDesignsPerLaunch];
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), 10 rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+// uniform in [0,1) from the top 24 bits (exact in FP32)
+__device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
+
+// ---------------------------------------------------------------------------
+// Ray state for traversal: slab-test constants and watertight shear.
+// ---------------------------------------------------------------------------
+struct RaySetup {
+    float3 o, d;
+    float3 inv;      // 1/d (zeros replaced by +-1e-30)
+    float3 oinv;     // o * inv
+    float3 mx, my, mz;  // shear rows: A_x = mx.A, A_y = my.A, A_z = mz.A
+};
+
+__device__ __forceinline__ float safe_inv(float x) {
+    return 1.0f / (fabsf(x) > 1e-30f ? x : copysignf(1e-30f, x));
+}
+
+__device__ __forceinline__ void setup_ray(RaySetup& r, float3 o, float3 d) {
+    r.o = o; r.d = d;
+    r.inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    r.oinv = f3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = 0;
+    if (ay > ax && ay >= az) kz = 1;
+    else if (az > ax && az > ay) kz = 2;
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const float dk[3] = {d.x, d.y, d.z};
+    if (dk[kz] < 0.0f) { int t = kx; kx = ky; ky = t; }
+    const float Sx = dk[kx] / dk[kz], Sy = dk[ky] / dk[kz], Sz = 1.0f / dk[kz];
+    float m[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    m[0][kx] = 1.0f; m[0][kz] = -Sx;
+    m[1][ky] = 1.0f; m[1][kz] = -Sy;
+    m[2][kz] = Sz;
+    r.mx = f3(m[0][0], m[0][1], m[0][2]);
+    r.my = f3(m[1][0], m[1][1], m[1][2]);
+    r.mz = f3(m[2][0], m[2][1], m[2][2]);
+}
+
+// Watertight test; returns t, or -1 when missed (callers need t > tmin >= 0).  Edge functions use
+// products without FMA contraction so shared edges are exactly antisymmetric.
+__device__ __forceinline__ float hit_triangle(const RaySetup& r, float3 p0, float3 p1, float3 p2) {
+    const float3 A = p0 - r.o, B = p1 - r.o, C = p2 - r.o;
+    const float Ax = dot(r.mx, A), Ay = dot(r.my, A);
+    const float Bx = dot(r.mx, B), By = dot(r.my, B);
+    const float Cx = dot(r.mx, C), Cy = dot(r.my, C);
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {   // recompute exactly-zero edges in FP64
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
+    const float det = U + V + W;
+    if (det == 0.0f) return -1.0f;
+    const float T = U * dot(r.mz, A) + V * dot(r.mz, B) + W * dot(r.mz, C);
+    return T / det;
+}
+
+// ---------------------------------------------------------------------------
+// Closest hit through a W-wide BVH.  Returns the leaf-order triangle index
+// (or -1) and sets tb.  Ties on t go to the smaller original index.
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& r, float tmin, int skip,
+                                           float& tb, int* err, uint32_t& nvis, uint32_t& ntest) {
+    constexpr int NF4 = W == 4 ? 8 : 16;  // float4 per node
+    const float4* __restrict__ nodes = dz.nodes;
+    const float4* __restrict__ tri = dz.tri;
+    int2 stack[kStackSize];
+    int sp = 0;
+    int best = -1;
+    uint32_t best_id = 0xffffffffu;
+    tb = INFINITY;
+    int ni = 0;
+    int visits = 0;
+    const bool nx_ = r.inv.x < 0.0f, ny_ = r.inv.y < 0.0f, nz_ = r.inv.z < 0.0f;
+    while (true) {
+        if (++visits > kVisitCap) { atomicOr(err, kErrVisitCap); return -1; }
+        ++nvis;
+        const float4* nd = nodes + (size_t)ni * NF4;
+        float tn[W];
+        bool hit[W];
+        int child[W];
+#pragma unroll
+        for (int h = 0; h < W / 4; ++h) {
+            const float4 lox = __ldg(nd + 0 * (W / 4) + h), hix = __ldg(nd + 1 * (W / 4) + h);
+            const float4 loy = __ldg(nd + 2 * (W / 4) + h), hiy = __ldg(nd + 3 * (W / 4) + h);
+            const float4 loz = __ldg(nd + 4 * (W / 4) + h), hiz = __ldg(nd + 5 * (W / 4) + h);
+            const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * (W / 4)) + h);
+            const float4 ax = nx_ ? hix : lox, bx = nx_ ? lox : hix;
+            const float4 ay = ny_ ? hiy : loy, by = ny_ ? loy : hiy;
+            const float4 az = nz_ ? hiz : loz, bz = nz_ ? loz : hiz;
+            const float ax_[4] = {ax.x, ax.y, ax.z, ax.w}, bx_[4] = {bx.x, bx.y, bx.z, bx.w};
+            const float ay_[4] = {ay.x, ay.y, ay.z, ay.w}, by_[4] = {by.x, by.y, by.z, by.w};
+            const float az_[4] = {az.x, az.y, az.z, az.w}, bz_[4] = {bz.x, bz.y, bz.z, bz.w};
+            const int ch_[4] = {ch.x, ch.y, ch.z, ch.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float n0 = fmaf(ax_[q], r.inv.x, -r.oinv.x), f0 = fmaf(bx_[q], r.inv.x, -r.oinv.x);
+                const float n1 = fmaf(ay_[q], r.inv.y, -r.oinv.y), f1 = fmaf(by_[q], r.inv.y, -r.oinv.y);
+                const float n2 = fmaf(az_[q], r.inv.z, -r.oinv.z), f2 = fmaf(bz_[q], r.inv.z, -r.oinv.z);
+                const float tnear = fmaxf(fmaxf(n0, n1), fmaxf(n2, tmin));
+                const float tfar = fminf(fminf(f0, f1), fminf(f2, tb));
+                tn[4 * h + q] = tnear;
+                hit[4 * h + q] = tnear <= tfar;
+                child[4 * h + q] = ch_[q];
+            }
+        }
+        // leaves first: they may shrink tb before inner children are queued
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            if (hit[c] && child[c] < 0) {
+                const int code = ~child[c];
+                const int first = code >> 3, cnt = (code & 7) + 1;
+                ntest += cnt;
+                for (int q = 0; q < cnt; ++q) {
+                    const int f = first + q;
+                    if (f == skip) continue;
+                    const float4 a = __ldg(tri + 3 * (size_t)f);
+                    const float4 b = __ldg(tri + 3 * (size_t)f + 1);
+                    const float4 cc = __ldg(tri + 3 * (size_t)f + 2);
+                    const float t = hit_triangle(r, xyz(a), xyz(b), xyz(cc));
+                    if (t > tmin && t <= tb) {
+                        const uint32_t id = __float_as_uint(a.w);
+                        if (t < tb || id < best_id) { tb = t; best = f; best_id = id; }
+                    }
+                }
+            }
+        }
+        int next = -1;
+        float tnext = INFINITY;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            if (hit[c] && child[c] >= 0 && tn[c] <= tb) {
+                if (tn[c] < tnext) {
+                    if (next >= 0) {
+                        if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
+                        stack[sp++] = make_int2(next, __float_as_int(tnext));
+                    }
+                    next = child[c]; tnext = tn[c];
+                } else {
+                    if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
+                    stack[sp++] = make_int2(child[c], __float_as_int(tn[c]));
+                }
+            }
+        }
+        if (next >= 0) { ni = next; continue; }
+        bool found = false;
+        while (sp > 0) {
+            const int2 e = stack[--sp];
+            if (__int_as_float(e.y) <= tb) { ni = e.x; found = true; break; }
+        }
+        if (!found) break;
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------------------
+// A ray segment and the shading of its hit.
+// ---------------------------------------------------------------------------
+struct Seg {
+    float3 o, d;
+    float w;
+    int src;  // leaf-order index of the triangle the segment leaves (-1: primary)
+};
+
+// Per-item constants shared by every ray of one (design, sun).
+struct ItemConst {
+    float3 ob, bu, bv, dd, com;
+    float fdx, fdy, w0, tmin_b;
+    const float* rho;
+    int dglob, sglob;
+};
+
+__device__ __forceinline__ void item_setup(ItemConst& ic, const DesignDev& dz, const TraceParams& p,
+                                           const double* sp, const double* cp, const float* rho,
+                                           int dglob, int sglob) {
+    // branchless ONB of d = -e (Duff et al. 2017) in FP64, rounded once
+    const double dx_ = -sp[0], dy_ = -sp[1], dz_ = -sp[2];
+    const double sgn = dz_ >= 0.0 ? 1.0 : -1.0;
+    const double aa = -1.0 / (sgn + dz_);
+    const double bb = dx_ * dy_ * aa;
+    const double u0 = 1.0 + sgn * dx_ * dx_ * aa, u1 = sgn * bb, u2 = -sgn * dx_;
+    const double v0 = bb, v1 = sgn + dy_ * dy_ * aa, v2 = -dy_;
+    const double R = dz.R;
+    const double pdx = 2.0 * R / p.nx, pdy = 2.0 * R / p.ny;
+    ic.ob = f3((float)(dz.cx - R * u0 - R * v0 - 2.0 * R * dx_), (float)(dz.cy - R * u1 - R * v1 - 2.0 * R * dy_),
+               (float)(dz.cz - R * u2 - R * v2 - 2.0 * R * dz_));
+    ic.bu = f3((float)u0, (float)u1, (float)u2);
+    ic.bv = f3((float)v0, (float)v1, (float)v2);
+    ic.dd = f3((float)dx_, (float)dy_, (float)dz_);
+    ic.fdx = (float)pdx; ic.fdy = (float)pdy;
+    ic.w0 = (float)(p.P * pdx * pdy);
+    ic.com = f3((float)cp[0], (float)cp[1], (float)cp[2]);
+    ic.tmin_b = (float)(1e-6 * R);
+    ic.rho = rho;
+    ic.dglob = dglob; ic.sglob = sglob;
+}
+
+// Primary segment of grid ray i (jittered pixel origin, travel direction d).
+__device__ __forceinline__ Seg primary_seg(const ItemConst& ic, const TraceParams& p, uint64_t i) {
+    const uint32_t px = (uint32_t)(i % (uint64_t)p.nx), py = (uint32_t)(i / (uint64_t)p.nx);
+    float xi1 = 0.5f, xi2 = 0.5f;
+    if (p.jitter) {
+        const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)ic.sglob, (uint32_t)ic.dglob, 0u),
+                                        (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+        xi1 = unit24(rnd.x); xi2 = unit24(rnd.y);
+    }
+    const float a = ((float)px + xi1) * ic.fdx, b = ((float)py + xi2) * ic.fdy;
+    Seg s;
+    s.o = f3(fmaf(a, ic.bu.x, fmaf(b, ic.bv.x, ic.ob.x)), fmaf(a, ic.bu.y, fmaf(b, ic.bv.y, ic.ob.y)),
+             fmaf(a, ic.bu.z, fmaf(b, ic.bv.z, ic.ob.z)));
+    s.d = ic.dd;
+    s.w = ic.w0;
+    s.src = -1;
+    return s;
+}
+
+// Geometry and material of hit on leaf-order triangle f at parameter t.
+struct HitGeom {
+    float3 x, n;   // hit point, unit normal facing the arriving ray
+    float cs;      // cos = -n.d > 0
+    float rs, rd;  // reflectances of the triangle's group
+    int g;         // material group
+};
+
+__device__ __forceinline__ HitGeom hit_geom(const DesignDev& dz, const ItemConst& ic, int f, float t, const Seg& s) {
+    const float4 a = __ldg(dz.tri + 3 * (size_t)f);
+    const float4 b = __ldg(dz.tri + 3 * (size_t)f + 1);
+    const float4 c = __ldg(dz.tri + 3 * (size_t)f + 2);
+    float3 n = cross(xyz(b) - xyz(a), xyz(c) - xyz(a));
+    n = rsqrtf(dot(n, n)) * n;
+    if (dot(n, s.d) > 0.0f) n = -1.0f * n;
+    HitGeom h;
+    h.n = n;
+    h.cs = -dot(n, s.d);
+    h.g = (int)__float_as_uint(b.w);
+    h.rs = __ldg(ic.rho + 2 * h.g);
+    h.rd = __ldg(ic.rho + 2 * h.g + 1);
+    h.x = s.o + t * s.d;
+    return h;
+}
+
+// Sampled reflection at hit k < K: branch 0 specular (weight 2 w rs),
+// 1 Lambertian (weight 2 w rd, direction of n + uniform unit vector).
+__device__ __forceinline__ int bounce_dir(const ItemConst& ic, const TraceParams& p, uint32_t i, int k,
+                                          const HitGeom& h, const Seg& s, float3& dout, float& wout) {
+    const uint4 rnd = philox4x32_10(make_uint4(i, (uint32_t)ic.sglob, (uint32_t)ic.dglob, (uint32_t)k),
+                                    (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+    if (unit24(rnd.x) < 0.5f) {
+        dout = s.d + (2.0f * h.cs) * h.n;
+        wout = 2.0f * s.w * h.rs;
+        return 0;
+    }
+    const float z = 1.0f - 2.0f * unit24(rnd.y);
+    const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    float sp, cp;
+    sincospif(2.0f * unit24(rnd.z), &sp, &cp);
+    const float3 v = f3(h.n.x + rr * cp, h.n.y + rr * sp, h.n.z + z);
+    const float l2 = dot(v, v);
+    dout = l2 > 0.0f ? rsqrtf(l2) * v : h.n;
+    wout = 2.0f * s.w * h.rd;
+    return 1;
+}
+
+// Momentum deposit of hit k (1-based) on leaf-order triangle f at ray
+// parameter t; returns true (and the outgoing segment) if the path goes on.
+__device__ __forceinline__ bool shade_hit(const DesignDev& dz, const ItemConst& ic, const TraceParams& p,
+                                          uint32_t i, int k, int f, float t, const Seg& s, float y[6],
+                                          Seg& out) {
+    const HitGeom h = hit_geom(dz, ic, f, t, s);
+    const float3 arm = h.x - ic.com;
+    if (k == p.K) {
+        const float cn = 2.0f * h.rs * h.cs + (2.0f / 3.0f) * h.rd;
+        const float3 dp = s.w * ((1.0f - h.rs) * s.d - cn * h.n);
+        const float3 tq = cross(arm, dp);
+        y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
+        return false;
+    }
+    float3 dout;
+    float wout;
+    bounce_dir(ic, p, i, k, h, s, dout, wout);
+    const float3 dp = s.w * s.d - wout * dout;
+    const float3 tq = cross(arm, dp);
+    y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
+    out.o = h.x; out.d = dout; out.w = wout; out.src = f;
+    return true;
+}
+
+
+}  // namespace srp

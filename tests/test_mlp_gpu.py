@@ -1,0 +1,81 @@
+"""GPU parity of the tensor-core proxy network (srp_mlp_*) against the FP64
+numpy oracle (oracle/mlp.py) fed the same BF16 operands: weights and inputs
+rounded to bfloat16, hidden activations rounded to bfloat16 at the same
+points as the kernel.  What remains is FP32 (kernel) vs FP64 (oracle)
+accumulation and rare one-ulp BF16 rounding flips of an activation; the bound
+1e-2 * rms(y) per output is an order of magnitude above their measured size
+and two orders below an operand-layout or descriptor error (wrong row/column
+pairing gives O(rms) differences)."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def flat(params):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params]).astype(np.float32)
+
+
+def unflat(v):
+    out, o = [], 0
+    for i in range(5):
+        a, b = omlp.SIZES[i], omlp.SIZES[i + 1]
+        W = v[o:o + a * b].reshape(b, a); o += a * b
+        bb = v[o:o + b]; o += b
+        out.append((W.astype(np.float64), bb.astype(np.float64)))
+    return out
+
+
+def inputs(B, seed):
+    rng = np.random.default_rng(seed)
+    e = rng.normal(size=(B, 3)); e /= np.linalg.norm(e, axis=1, keepdims=True)
+    rho = rng.uniform(0, 0.5, size=(B, 14))
+    hin = rng.uniform(-1.5, 1.5, size=(B, 2))
+    return np.concatenate([e, rho, hin], axis=1).astype(np.float32)
+
+
+def oracle_bf16(x, p):
+    pb = [(omlp.bf16_round(W), b) for W, b in p]
+    y, _, _ = omlp.forward(omlp.bf16_round(x), pb, round_act=True)
+    return y
+
+
+@pytest.fixture(scope="module")
+def srp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_10712_gb300 as srp
+    return srp
+
+
+@pytest.mark.parametrize("B", [1, 129, 1000])
+def test_forward_parity(srp, B):
+    ctx = srp.Context(0)
+    p = omlp.init_params(seed=7)
+    p = [(W, np.random.default_rng(l).normal(size=b.shape) * 0.1) for l, (W, b) in enumerate(p)]
+    net = srp.MLP(ctx, flat(p))
+    x = inputs(B, seed=B)
+    y = net.infer(x)
+    yo = oracle_bf16(x, unflat(flat(p)))
+    rms = np.sqrt(np.mean(yo ** 2))
+    err = np.abs(y - yo).max()
+    assert err <= 1e-2 * rms, (err, rms)
+
+
+def test_params_roundtrip_and_device_mode(srp):
+    ctx = srp.Context(0)
+    net = srp.MLP(ctx, seed=3)
+    p = net.params()
+    assert p.shape == (srp.mlp_param_count(),) and np.all(np.isfinite(p))
+    x = inputs(300, seed=1)
+    yh = net.infer(x)
+    dev = torch.device("cuda:0")
+    yd = net.infer(torch.from_numpy(x).to(dev))
+    torch.cuda.synchronize()
+    assert np.array_equal(yd.cpu().numpy(), yh)
+    net.set_params(p * 0.5)
+    assert np.array_equal(net.params(), (p * 0.5).astype(np.float32))

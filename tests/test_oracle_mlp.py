@@ -1,0 +1,77 @@
+"""Pins of the FP64 proxy-network oracle (oracle/mlp.py): reverse-mode
+gradients against central finite differences, Adam's first step against its
+closed form (the bias-corrected update is -lr*sign(g)), SiLU special values,
+and bfloat16 rounding (round to nearest even) on hand-worked ties."""
+import numpy as np
+
+from oracle import mlp
+
+
+def _small():
+    return mlp.init_params(seed=3, sizes=(19, 16, 16, 16, 16, 6))
+
+
+def test_silu_special_values():
+    assert mlp.silu(0.0) == 0.0 and mlp.dsilu(0.0) == 0.5
+    assert abs(mlp.silu(40.0) - 40.0) < 1e-12 and abs(mlp.silu(-40.0)) < 1e-15
+    z = np.linspace(-5, 5, 11)
+    fd = (mlp.silu(z + 1e-6) - mlp.silu(z - 1e-6)) / 2e-6
+    assert np.allclose(fd, mlp.dsilu(z), atol=1e-8)
+
+
+def test_bf16_round_ties_to_even():
+    one = 1.0
+    assert mlp.bf16_round(one) == 1.0
+    assert mlp.bf16_round(1.0 + 2 ** -8) == 1.0                  # tie -> even mantissa 0
+    assert mlp.bf16_round(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6     # tie -> even mantissa 2
+    assert mlp.bf16_round(1.0 + 2 ** -7) == 1.0 + 2 ** -7         # representable
+    assert mlp.bf16_round(-3.0) == -3.0
+
+
+def test_loss_gradient_matches_fd():
+    rng = np.random.default_rng(0)
+    p = _small()
+    x = rng.normal(size=(32, 19))
+    t = rng.normal(size=(32, 6)) * 10.0  # far from outputs: |y-t| has no kink nearby
+    loss, grads = mlp.l1_loss_and_grad(x, t, p)
+    h = 1e-6
+    for l, (i, j) in [(0, (3, 5)), (2, (7, 1)), (4, (2, 9))]:
+        W, b = p[l]
+        Wp = W.copy(); Wp[i, j] += h
+        Wm = W.copy(); Wm[i, j] -= h
+        pp = list(p); pp[l] = (Wp, b)
+        pm = list(p); pm[l] = (Wm, b)
+        fd = (mlp.l1_loss_and_grad(x, t, pp)[0] - mlp.l1_loss_and_grad(x, t, pm)[0]) / (2 * h)
+        assert abs(fd - grads[l][0][i, j]) <= 1e-6 * max(1.0, abs(fd)), (l, fd, grads[l][0][i, j])
+    for l in (1, 4):
+        W, b = p[l]
+        bp = b.copy(); bp[1] += h
+        bm = b.copy(); bm[1] -= h
+        pp = list(p); pp[l] = (W, bp)
+        pm = list(p); pm[l] = (W, bm)
+        fd = (mlp.l1_loss_and_grad(x, t, pp)[0] - mlp.l1_loss_and_grad(x, t, pm)[0]) / (2 * h)
+        assert abs(fd - grads[l][1][1]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_input_gradient_matches_fd():
+    rng = np.random.default_rng(1)
+    p = _small()
+    x = rng.normal(size=(4, 19))
+    wy = rng.normal(size=(4, 6))
+    g = mlp.input_grad(x, p, wy)
+    h = 1e-6
+    for j in (0, 7, 18):
+        xp = x.copy(); xp[:, j] += h
+        xm = x.copy(); xm[:, j] -= h
+        fd = ((mlp.forward(xp, p)[0] - mlp.forward(xm, p)[0]) * wy).sum(axis=1) / (2 * h)
+        assert np.allclose(fd, g[:, j], rtol=1e-6, atol=1e-9)
+
+
+def test_adam_first_step_closed_form():
+    p = [(np.array([[1.0, -2.0]]), np.array([0.5]))]
+    g = [(np.array([[3.0, -0.25]]), np.array([1e-3]))]
+    st = {}
+    q = mlp.adam_step(p, g, st, lr=0.01)
+    # m_hat = g, v_hat = g^2 after one step -> update = -lr * g / (|g| + eps)
+    assert np.allclose(q[0][0], [[1.0 - 0.01, -2.0 + 0.01]], atol=1e-9)
+    assert np.allclose(q[0][1], [0.5 - 0.01 * 1e-3 / (1e-3 + 1e-8)], atol=1e-12)
