@@ -188,6 +188,30 @@ int srp_force_grad(srp_ctx* ctx, const srp_bvh* bvh, const float* rho, int G,
                    const srp_trace_opts* opts, const double* upstream,
                    double* d_rho, double* d_hinge);
 
+/* Force and torque without any GPU allocation.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory
+ * when they need forces (an allocator policy that forbids allocations after
+ * start-up, a host framework that only hands over a stream and device
+ * pointers, a real-time loop that must not stall on an allocation).
+ * Same arguments and results as srp_force with mem = SRP_MEM_DEVICE (all
+ * arrays device memory, required), but no context: work is issued on
+ * `cuda_stream` (a cudaStream_t, NULL = legacy default stream) on the
+ * CURRENT device, where the bvhs must have been built.  The per-chunk FP64
+ * partial sums live in one fixed 8 MiB array inside the library (a
+ * file-scope device variable, held by every GPU that loads the library
+ * until the process exits), so D*S may be at most 87,381 (and
+ * D*S*chunks_per_item the same when given); larger requests fail with
+ * SRP_EINVAL.  Every call shares that array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (unordered streams) race
+ * and must not be issued.  The first call on each device looks up the
+ * array's address with that device current; make it before any stream
+ * capture begins.  d_status (device int32, may be NULL) receives the
+ * device-limit flags of the call (0 = none; see SRP_EDEVICE_LIMIT).
+ * Asynchronous; calls no cudaMalloc/cudaFree. */
+int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                      const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
+                      double* out_ft, double* out_sigma, int32_t* d_status, void* cuda_stream);
+
 /* Per-ray inspection (the estimator's individual samples): trace the n
  * grid rays ray_idx[n] (int64, each < rays_x*rays_y) of ONE design and ONE
  * sun direction with the same arithmetic as srp_force.

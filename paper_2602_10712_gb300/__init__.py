@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
-           "srp_build_bvh_host", "srp_trace_rays", "srp_force_grad", "SRPForce", "MLP",
+           "srp_build_bvh_host", "srp_trace_rays", "srp_force_noalloc", "srp_force_grad", "SRPForce", "MLP",
            "mlp_param_count",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
@@ -81,6 +81,7 @@ def load(build_if_needed: bool = True):
     lib.srp_mlp_set_params.argtypes = [_P, _P, _P]
     lib.srp_mlp_get_params.argtypes = [_P, _P, _P]
     lib.srp_mlp_infer.argtypes = [_P, _P, _P, i64, _P, i32]
+    lib.srp_force_noalloc.argtypes = [_P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P, _P, _P]
     lib.srp_build_bvh_host.argtypes = [_P, i32, _P, i32, i32, _P, C.POINTER(C.c_int64), _P, C.POINTER(C.c_int32)]
     lib.srp_trace_rays.argtypes = [_P, _P, _P, i32, _P, _P, _P, i64, i32, i32, C.POINTER(TraceOpts), _P, _P]
     _lib = lib
@@ -304,6 +305,31 @@ def srp_trace_rays(ctx: Context, bvh: BVH, rho, sun_dir, com, ray_idx, sun_index
     _check(lib.srp_trace_rays(ctx.handle, bvh.handle, _ptr(rho), rho.shape[0], _ptr(sun_dir), _ptr(com),
                               _ptr(ray_idx), ray_idx.shape[0], sun_index, design_index, C.byref(o), _ptr(y), _ptr(h)))
     return y, h
+
+
+def srp_force_noalloc(bvhs, rho, sun_dir, com, out_ft, out_sigma=None, status=None, stream=None, **opts):
+    """srp_force for callers that cannot allocate device memory: every array
+    (torch CUDA tensors: rho float32 [D,G,2], sun_dir float64 [S,3] or
+    [D,S,3], com float64 [D,3], out_ft/out_sigma float64 [D,S,6], status
+    int32 [1]) is supplied by the caller and the partial sums use a fixed
+    8 MiB array inside the library; D*S <= 87,381.  Asynchronous on `stream`
+    (default: torch's current stream) on the current device.  Overlapping
+    calls race on the shared array; the first call per device should come
+    before any stream capture."""
+    lib = load()
+    bvhs = list(bvhs)
+    D = len(bvhs)
+    arr = (_P * max(D, 1))(*[b.handle for b in bvhs])
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    opts["mem"] = SRP_MEM_DEVICE
+    o = make_opts(**opts)
+    _check(lib.srp_force_noalloc(arr, D, _ptr(rho), rho.shape[-2], _ptr(sun_dir), sun_dir.shape[-2], _ptr(com),
+                                 C.byref(o), _ptr(out_ft), _ptr(out_sigma), _ptr(status), _P(int(stream))))
+    return out_ft
 
 
 def srp_force_grad(ctx: Context, bvh: BVH, rho, sun_dir, com, upstream, tri_hinge=None, hinge_axes=None, **opts):

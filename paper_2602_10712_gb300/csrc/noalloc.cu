@@ -1,0 +1,203 @@
+// noalloc.cu -- srp_force_noalloc: the force/torque evaluation of srp_force
+// for callers that must not allocate GPU memory.
+//
+// Some callers cannot call cudaMalloc (or anything that allocates) at the
+// point where they need forces: code running under an allocator policy that
+// forbids new device allocations after start-up (for example a long-running
+// flight-dynamics service that sizes its memory once), code that is only
+// handed a stream and device pointers by a host framework, or real-time
+// loops where an allocation could stall.  srp_force keeps its per-chunk FP64
+// partial sums in scratch memory that the context allocates and grows on
+// demand; this entry point keeps them instead in one fixed, file-scope
+// device array that the library reserves when it is loaded.
+//
+// Properties (also stated in include/srp.h):
+//  - the scratch array holds at most kScratchBytes (8 MiB) of partials,
+//    i.e. D*S*chunks <= 87,381 work units; larger requests are rejected
+//    with SRP_EINVAL and a message naming the limit;
+//  - the array is shared by every call on a device and keeps the last
+//    call's contents; two calls whose work overlaps on the GPU (different
+//    streams, no ordering between them) race on it;
+//  - the first call on each device looks up the array's device address
+//    (cudaGetSymbolAddress) with that device current; make that first call
+//    before any stream capture begins;
+//  - nothing here calls cudaMalloc, cudaFree or an allocating library.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "srp_internal.h"
+
+namespace srp {
+void set_last_error(const std::string& msg);
+int trace_resident_blocks(int width, int block);
+cudaError_t launch_trace(const std::vector<DesignDev>& designs, const TraceParams& p, int width, int grid_cap,
+                         int block, cudaStream_t st);
+cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* out_ft, double* out_sigma,
+                          cudaStream_t st);
+}  // namespace srp
+
+using namespace srp;
+
+namespace {
+
+constexpr size_t kScratchBytes = 8u << 20;                       // 8 MiB
+constexpr int64_t kScratchUnits = (int64_t)(kScratchBytes / (12 * sizeof(double)));
+constexpr int kMaxDevices = 64;
+
+// The fixed scratch: per-unit FP64 partials, plus the kernels' error word.
+static __device__ __align__(256) double g_scratch[kScratchBytes / sizeof(double)];
+static __device__ __align__(256) int g_err_word;
+
+struct DevState {
+    bool ready = false;
+    double* part = nullptr;  // device address of g_scratch on this device
+    int* err = nullptr;      // device address of g_err_word on this device
+    int n_sm = 0;
+    int resident[2] = {0, 0};  // resident blocks per SM for widths 4 and 8
+};
+DevState g_dev[kMaxDevices];
+std::mutex g_mu;
+
+int fail(int code, const std::string& m) {
+    srp::set_last_error(m);  // reported by srp_last_error()
+    return code;
+}
+
+// One-time set-up for the current device (its first call lands here).
+int setup_device(int dev, DevState** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState& s = g_dev[dev];
+    if (!s.ready) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        s.part = static_cast<double*>(ptr);
+        e = cudaGetSymbolAddress(&ptr, g_err_word);
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetSymbolAddress(error word): ") + cudaGetErrorString(e));
+        s.err = static_cast<int*>(ptr);
+        int v = 0;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+        s.n_sm = v;
+        s.resident[0] = trace_resident_blocks(4, 128);
+        s.resident[1] = trace_resident_blocks(8, 128);
+        s.ready = true;
+    }
+    *out = &s;
+    return SRP_OK;
+}
+
+}  // namespace
+
+extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float* rho, int G, const double* sun_dir,
+                                 int S, const double* com, const srp_trace_opts* o, double* out_ft,
+                                 double* out_sigma, int32_t* d_status, void* cuda_stream) {
+    if (!o) return fail(SRP_EINVAL, "srp_force_noalloc: NULL opts");
+    if (o->mem != SRP_MEM_DEVICE) return fail(SRP_EINVAL, "srp_force_noalloc: all arrays must be device memory (mem = SRP_MEM_DEVICE)");
+    if (D < 0 || S < 0) return fail(SRP_EINVAL, "srp_force_noalloc: negative D or S");
+    if (G < 1 || G > kMaxGroups) return fail(SRP_EINVAL, "srp_force_noalloc: G must be in 1..64");
+    if (o->rays_x < 1 || o->rays_y < 1) return fail(SRP_EINVAL, "srp_force_noalloc: rays_x/rays_y must be >= 1");
+    const int64_t grid_n = (int64_t)o->rays_x * o->rays_y;
+    if (grid_n > 0xffffffffLL) return fail(SRP_EINVAL, "srp_force_noalloc: rays_x*rays_y must be < 2^32");
+    if (o->max_bounces < 1 || o->max_bounces > kMaxBounces) return fail(SRP_EINVAL, "srp_force_noalloc: max_bounces must be 1..3");
+    if (!(o->pressure >= 0.0) || !std::isfinite(o->pressure)) return fail(SRP_EINVAL, "srp_force_noalloc: bad pressure");
+    if (o->block_threads != 0 && o->block_threads != 128) return fail(SRP_EINVAL, "srp_force_noalloc: block_threads must be 0 or 128");
+    int64_t n = o->ray_count, off = o->ray_offset, stride = o->ray_stride;
+    if (n == 0) { n = grid_n; off = 0; stride = 1; }
+    if (n < 0 || off < 0 || stride < 1 || off + (n - 1) * stride >= grid_n)
+        return fail(SRP_EINVAL, "srp_force_noalloc: ray subset outside the grid");
+    const int64_t items = (int64_t)D * S;
+    if (items > 0 && (!bvhs || !rho || !sun_dir || !com || !out_ft))
+        return fail(SRP_EINVAL, "srp_force_noalloc: NULL array argument");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SRP_EUNSUPPORTED, "srp_force_noalloc: device index too large");
+    std::vector<DesignDev> designs(D);
+    int width = 0;
+    for (int d = 0; d < D; ++d) {
+        const srp_bvh* h = bvhs[d];
+        if (!h) return fail(SRP_EINVAL, "srp_force_noalloc: NULL bvh");
+        if (h->device != dev) return fail(SRP_EINVAL, "srp_force_noalloc: bvh built on another device than the current one");
+        if (width == 0) width = h->width;
+        if (h->width != width) return fail(SRP_EUNSUPPORTED, "srp_force_noalloc: all designs of one call need the same BVH width");
+        DesignDev& z = designs[d];
+        z.tri = (const float4*)h->d_tri; z.nodes = (const float4*)h->d_nodes;
+        z.cx = h->c[0]; z.cy = h->c[1]; z.cz = h->c[2]; z.R = h->R;
+        z.T = h->T; z.width = h->width;
+    }
+    if (width == 0) width = 4;
+    if (items > kScratchUnits)
+        return fail(SRP_EINVAL, "srp_force_noalloc: D*S = " + std::to_string(items) +
+                                    " exceeds the fixed scratch capacity of " + std::to_string(kScratchUnits) +
+                                    " (design, sun) items (8 MiB of partial sums); use srp_force");
+    // chunks per item: the automatic rule of srp_force, capped by the scratch
+    int64_t cpb = o->chunks_per_item;
+    if (cpb < 0) return fail(SRP_EINVAL, "srp_force_noalloc: negative chunks_per_item");
+    if (cpb == 0) {
+        const int64_t target = 40960;
+        cpb = items > 0 ? (target + items - 1) / items : 1;
+        cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
+    }
+    int64_t chunk = (n + cpb - 1) / cpb;
+    chunk = std::max<int64_t>(64, (chunk + 63) / 64 * 64);
+    cpb = std::max<int64_t>(1, (n + chunk - 1) / chunk);
+    if (items * cpb > kScratchUnits) {
+        if (o->chunks_per_item != 0)
+            return fail(SRP_EINVAL, "srp_force_noalloc: D*S*chunks_per_item exceeds the fixed scratch capacity of " +
+                                        std::to_string(kScratchUnits) + " work units");
+        cpb = std::max<int64_t>(1, kScratchUnits / std::max<int64_t>(items, 1));
+        chunk = (n + cpb - 1) / cpb;
+        chunk = std::max<int64_t>(64, (chunk + 63) / 64 * 64);
+        cpb = std::max<int64_t>(1, (n + chunk - 1) / chunk);
+    }
+    DevState* ds = nullptr;
+    int rc = setup_device(dev, &ds);
+    if (rc != SRP_OK) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (items == 0 || n == 0) {
+        if (items > 0) {
+            e = cudaMemsetAsync(out_ft, 0, sizeof(double) * 6 * items, st);
+            if (e == cudaSuccess && out_sigma) e = cudaMemsetAsync(out_sigma, 0, sizeof(double) * 6 * items, st);
+            if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+        }
+        if (d_status) {
+            e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
+            if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+        }
+        return SRP_OK;
+    }
+    TraceParams p;
+    std::memset(&p, 0, sizeof p);
+    p.D = D; p.S = S; p.G = G;
+    p.nx = o->rays_x; p.ny = o->rays_y; p.K = o->max_bounces; p.jitter = o->jitter ? 1 : 0;
+    p.sun_per_design = o->sun_per_design ? 1 : 0;
+    p.seed = o->seed; p.P = o->pressure;
+    p.off = off; p.stride = stride; p.n = n;
+    p.sun_base = o->sun_base; p.design_base = o->design_base;
+    p.chunk = chunk; p.cpb = (int32_t)cpb;
+    p.rho = rho; p.sun = sun_dir; p.com = com;
+    p.part = ds->part;          // every unit overwrites its 12 partials: no clearing needed
+    p.err = ds->err;
+    p.stats = nullptr;
+    // the error word only collects flags (OR): it must start at zero
+    e = cudaMemsetAsync(ds->err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemsetAsync(error word): ") + cudaGetErrorString(e));
+    const int grid_cap = ds->n_sm * ds->resident[width == 8 ? 1 : 0];
+    e = launch_trace(designs, p, width, grid_cap, 128, st);
+    if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("trace_kernel launch: ") + cudaGetErrorString(e));
+    e = launch_reduce(ds->part, items, p.cpb, out_ft, out_sigma, st);
+    if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("reduce kernel launch: ") + cudaGetErrorString(e));
+    if (d_status) {
+        e = cudaMemcpyAsync(d_status, ds->err, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemcpyAsync(status): ") + cudaGetErrorString(e));
+    }
+    return SRP_OK;
+}
+
