@@ -363,9 +363,14 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
     int64_t cpb = o->chunks_per_item;
     if (cpb < 0) return fail(SRP_EINVAL, "srp_force: negative chunks_per_item");
     if (cpb == 0) {
-        const int64_t target = 40960;   // ~16 units per resident warp
-
-        cpb = items > 0 ? (target + items - 1) / items : 1;
+        // Enough chunks per item that the resident warps (which take units in
+        // order) all work on the same (design, sun) item at a time: rays of one
+        // direction share BVH nodes in L1; a mix of directions per SM thrashed
+        // it (2x slower).  At least ~40k units for balance; at most 16M units
+        // of partials (1.5 GB); chunks of at least 256 rays.
+        const int64_t warps = (int64_t)c->n_sm * trace_resident_blocks(w ? w : 4, bt) * (bt / 32);
+        cpb = items > 0 ? std::max<int64_t>((40960 + items - 1) / items, warps) : 1;
+        if (items > 0) cpb = std::min<int64_t>(cpb, std::max<int64_t>(1, (int64_t)16777216 / items));
         cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
     }
     int64_t chunk = (n + cpb - 1) / cpb;
