@@ -77,9 +77,10 @@ def forward(x, params, round_act=False):
     return h, zs, hs
 
 
-def l1_loss_and_grad(x, t, params):
-    """L1 risk and its gradient w.r.t. every (W, b) by reverse mode."""
-    y, zs, hs = forward(x, params)
+def l1_loss_and_grad(x, t, params, round_act=False):
+    """L1 risk and its gradient w.r.t. every (W, b) by reverse mode
+    (round_act: hidden activations rounded to bfloat16 in the forward)."""
+    y, zs, hs = forward(x, params, round_act=round_act)
     B = y.shape[0]
     loss = np.abs(y - t).sum() / B
     dy = np.sign(y - t) / B

@@ -81,6 +81,7 @@ def load(build_if_needed: bool = True):
     lib.srp_mlp_set_params.argtypes = [_P, _P, _P]
     lib.srp_mlp_get_params.argtypes = [_P, _P, _P]
     lib.srp_mlp_infer.argtypes = [_P, _P, _P, i64, _P, i32]
+    lib.srp_mlp_train_step.argtypes = [_P, _P, _P, _P, i64, C.c_float, _P, _P, i32]
     lib.srp_force_noalloc.argtypes = [_P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P, _P, _P]
     lib.srp_build_bvh_host.argtypes = [_P, i32, _P, i32, i32, _P, C.POINTER(C.c_int64), _P, C.POINTER(C.c_int32)]
     lib.srp_trace_rays.argtypes = [_P, _P, _P, i32, _P, _P, _P, i64, i32, i32, C.POINTER(TraceOpts), _P, _P]
@@ -462,3 +463,16 @@ class MLP:
             mem = SRP_MEM_DEVICE
         _check(load().srp_mlp_infer(self.ctx.handle, self.handle, _ptr(x), x.shape[0], _ptr(y), mem))
         return y
+
+    def train_step(self, x, t, lr: float, want_loss: bool = True, want_grad: bool = False):
+        """One Adam step on the L1 loss (lr = 0: gradient only).  Returns
+        (loss or None, grad [P] or None); numpy -> host mode."""
+        host = isinstance(x, np.ndarray)
+        if host:
+            x = _np(x, np.float32).reshape(-1, 19)
+            t = _np(t, np.float32).reshape(-1, 6)
+        loss = np.zeros(1, np.float32) if want_loss else None
+        grad = np.zeros(mlp_param_count(), np.float32) if want_grad else None
+        _check(load().srp_mlp_train_step(self.ctx.handle, self.handle, _ptr(x), _ptr(t), x.shape[0], float(lr),
+                                         _ptr(loss), _ptr(grad), SRP_MEM_HOST if host else SRP_MEM_DEVICE))
+        return (float(loss[0]) if want_loss else None), grad

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -85,7 +86,6 @@ struct MlpFwdSmem {
     alignas(8) uint64_t bar_w;
     alignas(8) uint64_t bar_mma;
     uint32_t tmem_base;
-    int failed;
 };
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
@@ -102,7 +102,6 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
     if (tid == 0) {
         tc::mbar_init(&sm.bar_w, 1);
         tc::mbar_init(&sm.bar_mma, 1);
-        sm.failed = 0;
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -133,6 +132,7 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
     tc::tc_fence_after();
     const uint32_t tbase = sm.tmem_base;
     uint32_t ph_w = 0, ph_m = 0;
+    int failed = 0;  // block-uniform (decided with __syncthreads_or)
     for (int l = 0; l < kMlpLayers; ++l) {
         const int K = mlp_K(l), N = mlp_N(l);
         const uint32_t wbytes = (uint32_t)(N * K * 2);
@@ -144,10 +144,9 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
                 tc::bulk_g2s(sm.w + o, src + o, nb, &sm.bar_w);
             }
         }
-        if (!tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit)) sm.failed = 1;
+        const bool okw = tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
         ph_w ^= 1;
-        __syncthreads();
-        if (sm.failed) break;
+        if (__syncthreads_or(!okw)) { failed = 1; break; }
         if (tid == 0) {
             tc::tc_fence_after();
             const uint32_t a0 = tc::smem_u32(sm.act), b0 = tc::smem_u32(sm.w);
@@ -160,10 +159,9 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
             }
             tc::mma_commit(&sm.bar_mma);
         }
-        if (!tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit)) sm.failed = 1;
+        const bool okm = tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit);
         ph_m ^= 1;
-        __syncthreads();
-        if (sm.failed) break;
+        if (__syncthreads_or(!okm)) { failed = 1; break; }
         tc::tc_fence_after();
         // epilogue: warp w owns TMEM lanes (rows) 32w..32w+31
         const int r = 32 * warp + lane;
@@ -197,7 +195,7 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
         __syncthreads();
         tc::tc_fence_after();
     }
-    if (sm.failed) {
+    if (failed) {
         if (tid == 0) atomicOr(err, kErrMlpTimeout);
         // wait (bounded) for anything still in flight before freeing TMEM
         tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit);
@@ -221,6 +219,160 @@ cudaError_t mlp_forward(const float* x, int64_t B, const void* packed, const flo
     const unsigned grid = (unsigned)((B + 127) / 128);
     mlp_fwd_kernel<<<grid, 128, sm, st>>>(x, B, (const __nv_bfloat16*)packed, params, y, err);
     return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Training: forward with saved pre-activations, L1 loss, backward, Adam.
+// GEMMs run on gemm.cu's tensor-core kernel (BF16 operands, FP32 sums).
+// ---------------------------------------------------------------------------
+struct GemmOp {
+    const float* p;
+    int64_t ld;
+    int trans;
+};
+cudaError_t tc_gemm(GemmOp A, GemmOp B, int M, int N, int K, float alpha, float* C, int64_t ldc, int atomic,
+                    int k_split, int* err, cudaStream_t st);
+
+// Z += b (row-wise), H = silu(Z) (if H != null)
+__global__ void bias_silu_kernel(float* Z, const float* b, float* H, int64_t rows, int cols) {
+    const int64_t n = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float z = Z[e] + b[e % cols];
+        Z[e] = z;
+        if (H) H[e] = silu_f(z);
+    }
+}
+
+// dY = sign(Y - T) / B; loss += sum |Y - T| / B
+__global__ void l1_kernel(const float* Y, const float* T, float* dY, float* loss, int64_t n, float invB) {
+    float acc = 0.0f;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float d = Y[e] - T[e];
+        dY[e] = (d > 0.0f ? invB : (d < 0.0f ? -invB : 0.0f));
+        acc += fabsf(d);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * invB);
+}
+
+// dZ = dH * silu'(Z)
+__global__ void dsilu_kernel(const float* dH, const float* Z, float* dZ, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float z = Z[e];
+        const float sg = 1.0f / (1.0f + __expf(-z));
+        dZ[e] = dH[e] * sg * (1.0f + z * (1.0f - sg));
+    }
+}
+
+// db[c] = sum_r dZ[r][c]  (one block per column chunk)
+__global__ void colsum_kernel(const float* dZ, int64_t rows, int cols, float* db) {
+    const int c = blockIdx.x;
+    float acc = 0.0f;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) acc += dZ[r * cols + c];
+    __shared__ float red[32];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        db[c] = t;
+    }
+}
+
+// Adam (Kingma & Ba): bias-corrected moments, in place.
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float gg = g[e];
+        const float mm = b1 * m[e] + (1.0f - b1) * gg;
+        const float vv = b2 * v[e] + (1.0f - b2) * gg * gg;
+        m[e] = mm;
+        v[e] = vv;
+        p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    }
+}
+
+struct TrainBufs {
+    float* H[kMlpLayers];   // H[0] = x (caller), H[1..4] hidden [B][256]
+    float* Z[kMlpLayers];   // pre-activations; Z[4] = outputs [B][6]
+    float* dA;              // [B][256]
+    float* dB;              // [B][256]
+    float* loss;            // [1]
+};
+
+size_t train_bytes(int64_t B) {
+    return sizeof(float) * (size_t)(B * (4 * 256 + 4 * 256 + 6 + 2 * 256) + 64);
+}
+
+void train_carve(void* base, int64_t B, TrainBufs& t) {
+    float* q = (float*)base;
+    for (int l = 1; l < kMlpLayers; ++l) { t.H[l] = q; q += B * 256; }
+    for (int l = 0; l < kMlpLayers; ++l) { t.Z[l] = q; q += B * mlp_out(l); }
+    t.dA = q; q += B * 256;
+    t.dB = q; q += B * 256;
+    t.loss = q;
+}
+
+static unsigned ew_grid(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 4096); }
+
+// One optimisation step; grad receives dL/dparams; Adam applied when lr > 0.
+cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params, float* grad, float* adam_m,
+                      float* adam_v, int64_t step, float lr, void* work, void* packed, int* err, cudaStream_t st) {
+    const MlpLayout L = mlp_layout();
+    TrainBufs tb;
+    train_carve(work, B, tb);
+    tb.H[0] = const_cast<float*>(x);
+    cudaError_t e;
+    const int Bi = (int)B;
+    // forward
+    for (int l = 0; l < kMlpLayers; ++l) {
+        const int in = mlp_in(l), out = mlp_out(l);
+        e = tc_gemm(GemmOp{tb.H[l], in, 0}, GemmOp{params + L.w_off[l], in, 0}, Bi, out, in, 1.0f, tb.Z[l], out, 0, 0,
+                    err, st);
+        if (e != cudaSuccess) return e;
+        bias_silu_kernel<<<ew_grid(B * out), 256, 0, st>>>(tb.Z[l], params + L.b_off[l],
+                                                           l < kMlpLayers - 1 ? tb.H[l + 1] : nullptr, B, out);
+    }
+    // loss and dY
+    e = cudaMemsetAsync(tb.loss, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    l1_kernel<<<ew_grid(B * 6), 256, 0, st>>>(tb.Z[4], tgt, tb.dA, tb.loss, B * 6, 1.0f / (float)B);
+    e = cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, st);
+    if (e != cudaSuccess) return e;
+    float* dZ = tb.dA;
+    float* dH = tb.dB;
+    for (int l = kMlpLayers - 1; l >= 0; --l) {
+        const int in = mlp_in(l), out = mlp_out(l);
+        // dW_l = dZ_l^T H_l  (K = batch, split over 1024-row slices, atomic)
+        e = tc_gemm(GemmOp{dZ, out, 1}, GemmOp{tb.H[l], in, 1}, out, in, Bi, 1.0f, grad + L.w_off[l], in, 1, 1024,
+                    err, st);
+        if (e != cudaSuccess) return e;
+        colsum_kernel<<<out, 256, 0, st>>>(dZ, B, out, grad + L.b_off[l]);
+        if (l > 0) {
+            // dH = dZ_l W_l ; dZ_{l-1} = dH * silu'(Z_{l-1})
+            e = tc_gemm(GemmOp{dZ, out, 0}, GemmOp{params + L.w_off[l], in, 1}, Bi, in, out, 1.0f, dH, in, 0, 0, err,
+                        st);
+            if (e != cudaSuccess) return e;
+            dsilu_kernel<<<ew_grid(B * in), 256, 0, st>>>(dH, tb.Z[l - 1], dH, B * in);
+            float* t = dZ; dZ = dH; dH = t;
+        }
+    }
+    if (lr > 0.0f) {
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+        adam_kernel<<<ew_grid(kMlpParams), 256, 0, st>>>(params, grad, adam_m, adam_v, kMlpParams, lr, b1, b2, 1e-8f,
+                                                          c1, c2);
+        mlp_pack_kernel<<<256, 256, 0, st>>>(params, (__nv_bfloat16*)packed);
+    }
+    return cudaGetLastError();
+}
+
+float* train_loss_ptr(void* work, int64_t B) {
+    TrainBufs tb;
+    train_carve(work, B, tb);
+    return tb.loss;
 }
 
 int64_t mlp_param_count() { return kMlpParams; }
@@ -375,4 +527,40 @@ extern "C" int srp_mlp_infer(srp_ctx* c, const srp_mlp* m, const float* x, int64
     MCU(cudaFreeAsync(dx, st), "cudaFreeAsync");
     MCU(cudaFreeAsync(dy, st), "cudaFreeAsync");
     return srp_sync(c);
+}
+
+
+extern "C" int srp_mlp_train_step(srp_ctx* c, srp_mlp* m, const float* x, const float* t, int64_t B, float lr,
+                                  float* loss_out, float* grad_out, int mem) {
+    if (!c || !m) return mfail(SRP_EINVAL, "srp_mlp_train_step: NULL ctx/mlp");
+    if (B < 1 || B > (1 << 24)) return mfail(SRP_EINVAL, "srp_mlp_train_step: batch must be in 1..2^24");
+    if (!x || !t) return mfail(SRP_EINVAL, "srp_mlp_train_step: NULL x/t");
+    if (!(lr >= 0.0f) || !std::isfinite(lr)) return mfail(SRP_EINVAL, "srp_mlp_train_step: bad learning rate");
+    MCU(cudaSetDevice(m->device), "cudaSetDevice");
+    cudaStream_t st = ctx_stream(c);
+    const size_t need = train_bytes(B) + (mem == SRP_MEM_HOST ? sizeof(float) * 25 * (size_t)B + 512 : 0);
+    if (m->work_bytes < need) {
+        if (m->work) cudaFree(m->work);
+        m->work = nullptr; m->work_bytes = 0;
+        if (cudaMalloc(&m->work, need) != cudaSuccess) return mfail(SRP_ENOMEM, "srp_mlp_train_step: workspace");
+        m->work_bytes = need;
+    }
+    const float* dx = x;
+    const float* dt = t;
+    if (mem == SRP_MEM_HOST) {
+        float* sx = (float*)((char*)m->work + (train_bytes(B) + 255) / 256 * 256);
+        float* stg = sx + 19 * B;
+        MCU(cudaMemcpyAsync(sx, x, sizeof(float) * 19 * B, cudaMemcpyHostToDevice, st), "H2D x");
+        MCU(cudaMemcpyAsync(stg, t, sizeof(float) * 6 * B, cudaMemcpyHostToDevice, st), "H2D t");
+        dx = sx; dt = stg;
+    } else if (mem != SRP_MEM_DEVICE) {
+        return mfail(SRP_EINVAL, "srp_mlp_train_step: bad mem");
+    }
+    if (lr > 0.0f) m->step += 1;
+    MCU(mlp_train(dx, dt, B, m->params, m->grad, m->adam_m, m->adam_v, m->step, lr, m->work, m->packed, ctx_err(c), st),
+        "training launch");
+    if (grad_out) MCU(cudaMemcpyAsync(grad_out, m->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, st), "D2H grad");
+    if (loss_out) MCU(cudaMemcpyAsync(loss_out, train_loss_ptr(m->work, B), sizeof(float), cudaMemcpyDeviceToHost, st), "D2H loss");
+    if (grad_out || loss_out || mem == SRP_MEM_HOST) return srp_sync(c);
+    return SRP_OK;
 }
