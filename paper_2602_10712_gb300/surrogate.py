@@ -1,0 +1,136 @@
+"""The neural proxy of Sec. 3.3 trained on data the tracer generates.
+
+Design space (16 parameters, the box-wing with 7 material groups): rho_s and
+rho_d of the 6 bus faces and the panels (14 values in [0, 0.5]) and the two
+panel hinge angles (in [-pi/2, pi/2]); inputs are the body-frame sun
+direction (3) and the scaled design vector (16).  Outputs: force and torque
+for unit radiation pressure, standardised per component.
+
+Everything numeric runs in the library's kernels: design instantiation and
+BVH build (host C++), srp_force (tracer), srp_mlp_train_step / srp_mlp_infer
+(tensor-core MLP).  This module only orchestrates them.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import MLP, Context, srp_build_bvh, srp_design_instantiate, srp_force
+
+N_DESIGN = 16
+HINGE_MAX = math.pi / 2
+
+
+def sample_designs(n: int, seed: int) -> np.ndarray:
+    """theta [n,16]: rho_s[7], rho_d[7] ~ U[0,0.5], hinge[2] ~ U[-pi/2, pi/2]."""
+    rng = np.random.default_rng(seed)
+    th = np.empty((n, N_DESIGN))
+    th[:, :14] = rng.uniform(0.0, 0.5, size=(n, 14))
+    th[:, 14:] = rng.uniform(-HINGE_MAX, HINGE_MAX, size=(n, 2))
+    return th
+
+
+def sample_suns(n: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def encode(sun: np.ndarray, theta: np.ndarray) -> np.ndarray:
+    """Network input [.,19]: sun (3), 4*rho - 1 (14), hinge / (pi/2) (2)."""
+    x = np.empty(sun.shape[:-1] + (19,), np.float32)
+    x[..., :3] = sun
+    x[..., 3:17] = 4.0 * theta[..., :14] - 1.0
+    x[..., 17:] = theta[..., 14:] / HINGE_MAX
+    return x
+
+
+def trace_dataset(ctx: Context, mesh, theta: np.ndarray, suns_per_design: int, rays: int, bounces: int,
+                  seed: int, sun_seed: int):
+    """MC force/torque for every (design, sun): (sun [D,S,3], ft [D,S,6])."""
+    D = theta.shape[0]
+    sun = sample_suns(D * suns_per_design, sun_seed).reshape(D, suns_per_design, 3)
+    rho = np.zeros((D, mesh.n_groups, 2), np.float32)
+    rho[:, :, 0] = theta[:, :7]
+    rho[:, :, 1] = theta[:, 7:14]
+    com = np.zeros((D, 3))
+    ft = np.zeros((D, suns_per_design, 6))
+    chunk = 512
+    for d0 in range(0, D, chunk):
+        d1 = min(D, d0 + chunk)
+        bvhs = []
+        for d in range(d0, d1):
+            v = srp_design_instantiate(mesh.verts, mesh.vhinge, mesh.hinges, theta[d, 14:])
+            bvhs.append(srp_build_bvh(ctx, v, mesh.tris, mesh.group, 4))
+        ft[d0:d1] = srp_force(ctx, bvhs, rho[d0:d1], sun[d0:d1], com[d0:d1], rays_x=rays, max_bounces=bounces,
+                              seed=seed, sun_per_design=1, design_base=d0)
+        for b in bvhs:
+            b.close()
+    return sun, ft
+
+
+class Surrogate:
+    """A trained proxy: MLP + output standardisation."""
+
+    def __init__(self, ctx: Context, net: MLP, mean: np.ndarray, std: np.ndarray):
+        self.ctx, self.net, self.mean, self.std = ctx, net, mean, std
+
+    def predict(self, sun: np.ndarray, theta: np.ndarray) -> np.ndarray:
+        x = encode(sun, theta).reshape(-1, 19)
+        y = self.net.infer(x)
+        return y.astype(np.float64) * self.std + self.mean
+
+
+def fit(ctx: Context, mesh, n_designs=4096, suns_per_design=256, rays=256, bounces=3, epochs=20, batch=8192,
+        lr=2e-3, seed=0, log=None):
+    """Generate the data with the tracer and train the proxy; returns
+    (Surrogate, info dict with timings)."""
+    t0 = time.perf_counter()
+    theta = sample_designs(n_designs, seed)
+    sun, ft = trace_dataset(ctx, mesh, theta, suns_per_design, rays, bounces, seed=seed, sun_seed=seed + 1)
+    t_data = time.perf_counter() - t0
+    x = encode(sun, theta[:, None, :].repeat(suns_per_design, axis=1)).reshape(-1, 19)
+    y = ft.reshape(-1, 6)
+    mean = y.mean(axis=0)
+    std = y.std(axis=0) + 1e-12
+    yn = ((y - mean) / std).astype(np.float32)
+    net = MLP(ctx, seed=seed)
+    n = x.shape[0]
+    rng = np.random.default_rng(seed + 7)
+    steps = max(1, epochs * (n // batch))
+    t1 = time.perf_counter()
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    xt = torch.from_numpy(x).to(dev)
+    yt = torch.from_numpy(yn).to(dev)
+    step = 0
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(n)).to(dev)
+        for b0 in range(0, n - batch + 1, batch):
+            idx = perm[b0:b0 + batch]
+            xb = xt.index_select(0, idx).contiguous()
+            yb = yt.index_select(0, idx).contiguous()
+            lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * step / steps)) + 1e-5
+            net.train_step(xb, yb, lr_t, want_loss=False)
+            step += 1
+        if log is not None:
+            l, _ = net.train_step(xt[:batch].contiguous(), yt[:batch].contiguous(), 0.0)
+            log(f"epoch {ep} loss {l:.4f}")
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    return Surrogate(ctx, net, mean, std), {"data_s": t_data, "train_s": t_train, "samples": n, "steps": step}
+
+
+def force_rms_error(sur: Surrogate, ctx: Context, mesh, n_designs=256, suns_per_design=16, rays=1024, bounces=3,
+                    seed=99):
+    """sqrt(mean |F_nn - F_mc|^2) / sqrt(mean |F_mc|^2) on held-out designs
+    and directions, F_mc traced with `rays`^2 rays (16x the training rays
+    by default)."""
+    theta = sample_designs(n_designs, seed)
+    sun, ft = trace_dataset(ctx, mesh, theta, suns_per_design, rays, bounces, seed=seed, sun_seed=seed + 1)
+    pred = sur.predict(sun, theta[:, None, :].repeat(suns_per_design, axis=1)).reshape(ft.shape)
+    num = np.sqrt(np.mean(np.sum((pred[..., :3] - ft[..., :3]) ** 2, axis=-1)))
+    den = np.sqrt(np.mean(np.sum(ft[..., :3] ** 2, axis=-1)))
+    return num / den
