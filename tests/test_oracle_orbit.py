@@ -1,0 +1,73 @@
+"""Pins of the orbit oracle (oracle/orbit.py) against closed forms of
+Sec. 3.4's ODE: two-body energy and angular-momentum conservation, the
+circular-orbit period 2 pi sqrt(a^3/mu), torque-free spin of a symmetric
+body (q(t) = q0 (x) (cos(wt/2), sin(wt/2) axis)), the cannonball
+acceleration, and complex-step vs central-difference gradients."""
+import math
+
+import numpy as np
+
+from oracle import mlp as omlp
+from oracle import orbit as O
+
+
+def test_two_body_invariants_one_day():
+    m = O.Model("none", j2=0.0)
+    z0 = O.circular_state(26560e3, math.radians(55))
+    z0[3:6] *= 1.05  # eccentric
+    z, tr = O.rk4(m, z0, np.zeros(1), 60.0, 1440, keep=True)
+    E = 0.5 * np.sum(tr[:, 3:6] ** 2, axis=1) - O.MU / np.linalg.norm(tr[:, :3], axis=1)
+    Hm = np.linalg.norm(np.cross(tr[:, :3], tr[:, 3:6]), axis=1)
+    assert np.max(np.abs(E / E[0] - 1)) < 1e-9
+    assert np.max(np.abs(Hm / Hm[0] - 1)) < 1e-9
+
+
+def test_circular_period():
+    a = 26560e3
+    T = 2 * math.pi * math.sqrt(a ** 3 / O.MU)
+    m = O.Model("none", j2=0.0)
+    z0 = O.circular_state(a, math.radians(55), 0.3, 0.7)
+    z = O.rk4(m, z0, np.zeros(1), T / 720, 720)
+    assert np.linalg.norm(z[:3] - z0[:3]) / a < 1e-7
+
+
+def test_torque_free_symmetric_spin():
+    m = O.Model("none", inertia=(300.0, 300.0, 300.0), j2=0.0)
+    z0 = O.circular_state(7000e3, 0.1)
+    w = 0.01
+    z0[10:13] = [0.0, 0.0, w]
+    t = 600.0
+    z = O.rk4(m, z0, np.zeros(1), 1.0, 600)
+    q = z[6:10]
+    assert np.allclose(q, [math.cos(w * t / 2), 0, 0, math.sin(w * t / 2)], atol=1e-10)
+    assert np.allclose(z[10:13], [0, 0, w], atol=1e-15)
+
+
+def test_cannonball_acceleration():
+    m = O.Model("cannonball", P=4.56e-6, mass=800.0, sun=(0.0, 0.6, 0.8))
+    rng = np.random.default_rng(0)
+    q = rng.normal(size=4); q /= np.linalg.norm(q)
+    z = np.concatenate([[7e6, 1e5, -2e5], [0, 7.5e3, 0], q, [1e-3, -2e-3, 5e-4]])
+    k = m.f(z, np.array([12.0]))
+    a_srp = k[3:6] - O.gravity(z[:3])
+    # recovered by subtracting ~8 m/s^2 gravity from the total: round-off ~1e-15 m/s^2
+    assert np.allclose(a_srp, -4.56e-6 * 12.0 / 800.0 * np.array([0.0, 0.6, 0.8]), rtol=0, atol=1e-14)
+
+
+def test_complex_step_matches_central_difference():
+    p = omlp.init_params(seed=2, sizes=(19, 16, 16, 16, 16, 6))
+    scale = np.concatenate([np.ones(3), 4 * np.ones(14), np.ones(2) / (math.pi / 2)])
+    offset = np.concatenate([np.zeros(3), -np.ones(14), np.zeros(2)])
+    m = O.Model("proxy", P=4.56e-6 * 1e3, mass=100.0, sun=(0.3, 0.5, 0.81), params=p, scale=scale,
+                offset=offset, mean=np.zeros(6), std=np.full(6, 5.0))
+    z0 = O.circular_state(7000e3, 0.9)
+    z0[10:13] = [1e-3, 2e-3, -1e-3]
+    th = np.random.default_rng(1).uniform(0, 0.5, size=16)
+    wN = np.random.default_rng(2).normal(size=13)
+    gt, gz = O.cs_grad(m, z0, th, 10.0, 60, wN)
+    for j in (0, 7, 15):
+        # central differences are O(h^2): Richardson-combine steps 3e-3 and 1e-3 (O(h^4))
+        f3 = O.fd_grad(m, z0, th, 10.0, 60, wN, j, 3e-3)
+        f1 = O.fd_grad(m, z0, th, 10.0, 60, wN, j, 1e-3)
+        fd = (9.0 * f1 - f3) / 8.0
+        assert abs(fd - gt[j]) <= 1e-5 * abs(fd) + 1e-7, (j, fd, gt[j])
