@@ -188,6 +188,71 @@ int srp_force_grad(srp_ctx* ctx, const srp_bvh* bvh, const float* rho, int G,
                    const srp_trace_opts* opts, const double* upstream,
                    double* d_rho, double* d_hinge);
 
+/* ---- the neural proxy P(omega, theta | psi) (Sec. 3.3) --------------------
+ * 19 inputs (body-frame sun direction, 16 design parameters) -> 4 hidden
+ * layers of 256 with SiLU -> 6 outputs (force, torque); BF16 tensor-core
+ * GEMMs with FP32 accumulation, FP32 master weights, Adam (Sec. 3.3).
+ * Parameter vector (float32, srp_mlp_param_count() entries): for
+ * l = 0..4, W_l [out][in] row-major then b_l [out]; sizes 19-256-256-256-
+ * 256-6.  Training minimises the L1 risk mean_b sum_j |y_j - t_j| (Alg. 1,
+ * NNLoss).  Inputs/targets are whatever scaling the caller chose. */
+typedef struct srp_mlp srp_mlp;
+int srp_mlp_param_count(int64_t* out);
+/* params: host [P] initial weights, or NULL for He-uniform from `seed`. */
+int srp_mlp_create(srp_ctx* ctx, const float* params, uint64_t seed, srp_mlp** out);
+int srp_mlp_destroy(srp_mlp* mlp);
+int srp_mlp_set_params(srp_ctx* ctx, srp_mlp* mlp, const float* params /* host [P]; resets Adam */);
+int srp_mlp_get_params(srp_ctx* ctx, const srp_mlp* mlp, float* out /* host [P] */);
+/* y [B][6] = P(x [B][19]); mem = srp_mem of x and y. */
+int srp_mlp_infer(srp_ctx* ctx, const srp_mlp* mlp, const float* x, int64_t B, float* y, int mem);
+/* One step on (x [B][19], t [B][6]): gradient of the L1 risk, then Adam
+ * (beta 0.9 / 0.999, eps 1e-8) with learning rate lr when lr > 0.
+ * loss_out (host float, may be NULL) receives the risk before the step;
+ * grad_out (host [P], may be NULL) the gradient.  1 <= B <= 2^24. */
+int srp_mlp_train_step(srp_ctx* ctx, srp_mlp* mlp, const float* x, const float* t, int64_t B, float lr,
+                       float* loss_out, float* grad_out, int mem);
+
+/* ---- orbit integration and its adjoint (Sec. 3.4, Eq. "ODE", RK4 of
+ * Sec. 3.4.1, adjoint of Sec. 3.4.3) --------------------------------------
+ * State z (13) = (r [m], v [m/s] inertial; unit quaternion q = (q0..q3)
+ * taking body vectors to inertial; body rate w [rad/s]).
+ *   r' = v,  v' = R(q) F / m + gravity(r) (two-body + J2),
+ *   q' = q (x) (0, w) / 2,  w' = I^-1 (tau - w x I w)  (I diagonal),
+ * (F, tau) = pressure * (out_std * y + out_mean), y = force model at the
+ * body-frame sun direction wbar = R(q)^T sun and the design theta:
+ *   SRP_FM_NONE        y = 0
+ *   SRP_FM_CANNONBALL  y = (-theta[0] wbar, 0) (theta[0] = area x (1+4 rho_d/9))
+ *   SRP_FM_PROXY       y = MLP(in_scale * (wbar, theta) + in_offset), n_theta = 16
+ * RK4 in FP64 with step dt (the MLP runs in FP32).  With dL_dzN given, the
+ * discrete adjoint of the RK4 map (checkpoints every ckpt_every steps,
+ * 0 = ceil(sqrt(n_steps)), at most 64) returns dL/dtheta and dL/dz0. */
+#define SRP_FM_NONE 0
+#define SRP_FM_CANNONBALL 1
+#define SRP_FM_PROXY 2
+typedef struct srp_orbit_opts {
+    double mu, j2, re;        /* [3.986004418e14, 1.08263e-3, 6378137]       */
+    double mass;              /* kg [1000]                                    */
+    double inertia[3];        /* diagonal, kg m^2 [500, 400, 300]             */
+    double pressure;          /* N/m^2 [1361 / c]                             */
+    double sun[3];            /* inertial unit vector toward the sun [1,0,0] */
+    double dt;                /* s [60]                                       */
+    int32_t n_steps;          /* [1440]                                       */
+    int32_t ckpt_every;       /* [0]                                          */
+    int32_t model;            /* SRP_FM_* [NONE]                              */
+    int32_t n_theta;          /* 1..16 [1]                                    */
+    float in_scale[19], in_offset[19];   /* proxy input map [1, 0]            */
+    float out_mean[6], out_std[6];       /* model output map [0, 1]           */
+} srp_orbit_opts;
+void srp_orbit_opts_default(srp_orbit_opts* o);
+/* n_traj trajectories, one CTA each:  z0 [n][13], theta [n][n_theta] ->
+ * zN [n][13], traj [n][n_steps+1][13] (or NULL); adjoint when dL_dzN
+ * [n][13] is given: dL_dtheta [n][n_theta], dL_dz0 [n][13] (either may be
+ * NULL).  proxy may be NULL unless model = SRP_FM_PROXY.  mem = srp_mem of
+ * every array. */
+int srp_integrate(srp_ctx* ctx, const srp_orbit_opts* opts, const srp_mlp* proxy, int n_traj,
+                  const double* z0, const double* theta, double* zN, double* traj,
+                  const double* dL_dzN, double* dL_dtheta, double* dL_dz0, int mem);
+
 /* Force and torque without any GPU allocation.  The paper has no
  * counterpart; this exists for callers that cannot allocate device memory
  * when they need forces (an allocator policy that forbids allocations after

@@ -19,7 +19,7 @@ from . import _build
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
            "srp_build_bvh_host", "srp_trace_rays", "srp_force_noalloc", "srp_force_grad", "SRPForce", "MLP",
-           "mlp_param_count",
+           "mlp_param_count", "srp_integrate", "orbit_opts", "OrbitOpts",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
 SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_EDEVICE_LIMIT, SRP_ETIMEOUT, SRP_EUNSUPPORTED = range(7)
@@ -81,6 +81,8 @@ def load(build_if_needed: bool = True):
     lib.srp_mlp_set_params.argtypes = [_P, _P, _P]
     lib.srp_mlp_get_params.argtypes = [_P, _P, _P]
     lib.srp_mlp_infer.argtypes = [_P, _P, _P, i64, _P, i32]
+    lib.srp_orbit_opts_default.argtypes = [_P]
+    lib.srp_integrate.argtypes = [_P, _P, _P, i32, _P, _P, _P, _P, _P, _P, _P, i32]
     lib.srp_mlp_train_step.argtypes = [_P, _P, _P, _P, i64, C.c_float, _P, _P, i32]
     lib.srp_force_noalloc.argtypes = [_P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P, _P, _P]
     lib.srp_build_bvh_host.argtypes = [_P, i32, _P, i32, i32, _P, C.POINTER(C.c_int64), _P, C.POINTER(C.c_int32)]
@@ -476,3 +478,44 @@ class MLP:
         _check(load().srp_mlp_train_step(self.ctx.handle, self.handle, _ptr(x), _ptr(t), x.shape[0], float(lr),
                                          _ptr(loss), _ptr(grad), SRP_MEM_HOST if host else SRP_MEM_DEVICE))
         return (float(loss[0]) if want_loss else None), grad
+
+
+# ----------------------------------------------------------------- orbits
+SRP_FM_NONE, SRP_FM_CANNONBALL, SRP_FM_PROXY = 0, 1, 2
+
+
+class OrbitOpts(C.Structure):
+    _fields_ = [("mu", C.c_double), ("j2", C.c_double), ("re", C.c_double), ("mass", C.c_double),
+                ("inertia", C.c_double * 3), ("pressure", C.c_double), ("sun", C.c_double * 3), ("dt", C.c_double),
+                ("n_steps", C.c_int32), ("ckpt_every", C.c_int32), ("model", C.c_int32), ("n_theta", C.c_int32),
+                ("in_scale", C.c_float * 19), ("in_offset", C.c_float * 19), ("out_mean", C.c_float * 6),
+                ("out_std", C.c_float * 6)]
+
+
+def orbit_opts(**kw) -> OrbitOpts:
+    o = OrbitOpts()
+    load().srp_orbit_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if isinstance(v, (list, tuple, np.ndarray)):
+            arr = getattr(o, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def srp_integrate(ctx: Context, opts: OrbitOpts, z0, theta, proxy=None, want_traj=False, dL_dzN=None):
+    """Integrate n trajectories (host numpy): returns dict(zN, traj, dL_dtheta, dL_dz0)."""
+    lib = load()
+    z0 = _np(z0, np.float64).reshape(-1, 13)
+    n = z0.shape[0]
+    th = _np(theta, np.float64).reshape(n, -1)
+    zN = np.zeros((n, 13))
+    traj = np.zeros((n, opts.n_steps + 1, 13)) if want_traj else None
+    lam = None if dL_dzN is None else _np(dL_dzN, np.float64).reshape(n, 13)
+    dth = np.zeros((n, th.shape[1])) if lam is not None else None
+    dz0 = np.zeros((n, 13)) if lam is not None else None
+    _check(lib.srp_integrate(ctx.handle, C.byref(opts), proxy.handle if proxy is not None else None, n, _ptr(z0),
+                             _ptr(th), _ptr(zN), _ptr(traj), _ptr(lam), _ptr(dth), _ptr(dz0), SRP_MEM_HOST))
+    return {"zN": zN, "traj": traj, "dL_dtheta": dth, "dL_dz0": dz0}

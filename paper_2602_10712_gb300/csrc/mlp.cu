@@ -383,6 +383,7 @@ cudaStream_t ctx_stream(srp_ctx* c);
 int ctx_device(srp_ctx* c);
 int* ctx_err(srp_ctx* c);
 int ctx_n_sm(srp_ctx* c);
+const float* mlp_params_ptr(const srp_mlp* m);
 
 }  // namespace srp
 
@@ -433,6 +434,8 @@ void init_params_host(uint64_t seed, std::vector<float>& p) {
     }
 }
 }  // namespace
+
+const float* srp::mlp_params_ptr(const srp_mlp* m) { return m->params; }
 
 extern "C" int srp_mlp_param_count(int64_t* out) {
     if (!out) return mfail(SRP_EINVAL, "srp_mlp_param_count: NULL out");
