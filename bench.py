@@ -291,6 +291,8 @@ def run_ours(args, ws, rank, local):
                       "segments_per_ray": segs / n_samp, "bytes_per_ray": bytes_per_ray},
         "clocks": ck,
     }
+    if rank == 0 and not args.no_extra:
+        line["surrogate"], line["grad"] = extra_legs(srp, ctx, dev, peaks)
     if rank == 0 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
         val, dt = oracle_sample(m_, rho_, sun_, com_, 2, 4096)
@@ -299,6 +301,77 @@ def run_ours(args, ws, rank, local):
                                 "seconds": dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def extra_legs(srp, ctx, dev, peaks):
+    """Surrogate vs tracer force evaluations/s (and the surrogate's held-out
+    error) and gradient evaluations/s, on the box-wing design space."""
+    import torch
+    from paper_2602_10712_gb300 import surrogate as S
+    mesh = W.box_wing_7group()
+    t0 = time.perf_counter()
+    sur, info = S.fit(ctx, mesh, n_designs=4096, suns_per_design=256, rays=256, bounces=3, epochs=20, batch=8192,
+                      lr=2e-3, seed=0)
+    fit_s = time.perf_counter() - t0
+    err = S.force_rms_error(sur, ctx, mesh, n_designs=512, suns_per_design=16, rays=1024, bounces=3, seed=99)
+    nq = 1 << 20
+    x = torch.from_numpy(S.encode(S.sample_suns(nq, 3), S.sample_designs(nq, 4))).to(dev)
+    y = sur.net.infer(x)
+    for _ in range(3):
+        sur.net.infer(x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        sur.net.infer(x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    t_nn = e0.elapsed_time(e1) / 1e3 / reps
+    flops = 2.0 * (19 * 256 + 3 * 256 * 256 + 256 * 6) * nq
+    nn_rate = nq / t_nn
+    # tracer: one design, 4096 suns x 256^2 rays, K <= 3 (the training accuracy)
+    th = S.sample_designs(1, 8)
+    v = srp.srp_design_instantiate(mesh.verts, mesh.vhinge, mesh.hinges, th[0, 14:])
+    b = srp.srp_build_bvh(ctx, v, mesh.tris, mesh.group, 4)
+    rho = np.zeros((1, 7, 2), np.float32); rho[0, :, 0] = th[0, :7]; rho[0, :, 1] = th[0, 7:14]
+    suns = torch.from_numpy(S.sample_suns(4096, 9)).to(dev)
+    r_t = torch.from_numpy(rho).to(dev); c_t = torch.zeros((1, 3), dtype=torch.float64, device=dev)
+    srp.srp_force(ctx, [b], r_t, suns, c_t, rays_x=256, max_bounces=3)
+    torch.cuda.synchronize()
+    e0.record()
+    srp.srp_force(ctx, [b], r_t, suns, c_t, rays_x=256, max_bounces=3)
+    e1.record()
+    torch.cuda.synchronize()
+    mc_rate = 4096 / (e0.elapsed_time(e1) / 1e3)
+    peak = peaks.get("bf16_tflops", 1900.0)
+    surrogate = {"evals_per_s": nn_rate, "tracer_evals_per_s_256sq_rays": mc_rate, "speedup": nn_rate / mc_rate,
+                 "force_rms_rel_err": err, "train_samples": info["samples"], "fit_s": fit_s,
+                 "mlp_tflops": flops / t_nn / 1e12, "mlp_frac_of_bf16_peak": flops / t_nn / 1e12 / peak,
+                 "batch": nq, "note": "19-256x4-6 SiLU, BF16 tcgen05, FP32 accumulation; error vs 1024^2-ray MC"}
+    # gradients: box-wing (64 groups, 2 hinges), K = 1, 1024^2 rays, 64 suns per call
+    m1 = W.box_wing()
+    ang = np.array([0.3, -0.5])
+    v1 = srp.srp_design_instantiate(m1.verts, m1.vhinge, m1.hinges, ang)
+    b1 = srp.srp_build_bvh(ctx, v1, m1.tris, m1.group, 4)
+    rho1 = torch.from_numpy(W.random_reflectances(64, seed=0)).to(dev)
+    sun1 = torch.from_numpy(W.fibonacci_directions(64)).to(dev)
+    com1 = torch.zeros(3, dtype=torch.float64, device=dev)
+    up = torch.ones((64, 6), dtype=torch.float64, device=dev)
+    th1 = torch.from_numpy(m1.vhinge[m1.tris[:, 0]].astype(np.int32)).to(dev)
+    ha = torch.from_numpy(m1.hinges).to(dev)
+    gkw = dict(rays_x=1024, max_bounces=1)
+    srp.srp_force_grad(ctx, b1, rho1, sun1, com1, up, th1, ha, **gkw)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        srp.srp_force_grad(ctx, b1, rho1, sun1, com1, up, th1, ha, **gkw)
+    e1.record()
+    torch.cuda.synchronize()
+    g_rate = 3 * 64 / (e0.elapsed_time(e1) / 1e3)
+    grad = {"grad_evals_per_s": g_rate, "rays_per_eval": 1024 * 1024,
+            "note": "d(F,tau)/d(64 x (rho_s, rho_d), 2 hinge angles), box-wing, K=1"}
+    return surrogate, grad
 
 
 def main():
@@ -310,6 +383,7 @@ def main():
     ap.add_argument("--width", type=int, default=4)
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -84,6 +84,8 @@ typedef struct srp_trace_opts {
     int32_t sun_per_design;   /* 1: sun_dir is [D][S][3], 0: [S][3] [0]     */
     int32_t block_threads;    /* 0 or 128 (threads per block)               */
     int32_t chunks_per_item;  /* 0 = automatic; else ray chunks per item    */
+    int32_t kernel_variant;   /* register budget: 0 = default (5), 4 or 5  */
+    int32_t reserved;         /* must be 0                                  */
 } srp_trace_opts;
 
 /* ---- context ----------------------------------------------------------- */
@@ -265,7 +267,8 @@ int srp_integrate(srp_ctx* ctx, const srp_orbit_opts* opts, const srp_mlp* proxy
  * partial sums live in one fixed 8 MiB array inside the library (a
  * file-scope device variable, held by every GPU that loads the library
  * until the process exits), so D*S may be at most 87,381 (and
- * D*S*chunks_per_item the same when given); larger requests fail with
+ * D*S*chunks_per_item the same when given), and the design table in a
+ * fixed array of 4,096 entries (D <= 4,096); larger requests fail with
  * SRP_EINVAL.  Every call shares that array and it keeps the last call's
  * contents: calls whose work overlaps on the GPU (unordered streams) race
  * and must not be issued.  The first call on each device looks up the
@@ -276,6 +279,21 @@ int srp_integrate(srp_ctx* ctx, const srp_orbit_opts* opts, const srp_mlp* proxy
 int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float* rho, int G,
                       const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
                       double* out_ft, double* out_sigma, int32_t* d_status, void* cuda_stream);
+
+/* CUDA graph of one srp_force evaluation: the same arguments (device
+ * memory only, opts->mem = SRP_MEM_DEVICE) are captured once, with the
+ * design table copied into the graph; srp_graph_launch replays the
+ * evaluation (queue reset, one persistent trace launch over every
+ * (design, sun, chunk) unit, reduction) on the context's stream, reading
+ * rho/sun_dir/com and writing out_ft/out_sigma at the captured addresses.
+ * The graph uses the context's scratch: no other srp_force or graph of the
+ * same context may run concurrently. */
+typedef struct srp_graph srp_graph;
+int srp_force_graph_create(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                           const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
+                           double* out_ft, double* out_sigma, srp_graph** out);
+int srp_graph_launch(srp_graph* graph);
+int srp_graph_destroy(srp_graph* graph);
 
 /* Per-ray inspection (the estimator's individual samples): trace the n
  * grid rays ray_idx[n] (int64, each < rays_x*rays_y) of ONE design and ONE

@@ -19,7 +19,7 @@ from . import _build
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
            "srp_build_bvh_host", "srp_trace_rays", "srp_force_noalloc", "srp_force_grad", "SRPForce", "MLP",
-           "mlp_param_count", "srp_integrate", "orbit_opts", "OrbitOpts",
+           "mlp_param_count", "srp_integrate", "orbit_opts", "OrbitOpts", "ForceGraph",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
 SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_EDEVICE_LIMIT, SRP_ETIMEOUT, SRP_EUNSUPPORTED = range(7)
@@ -40,7 +40,7 @@ class TraceOpts(C.Structure):
                 ("ray_offset", C.c_int64), ("ray_stride", C.c_int64), ("ray_count", C.c_int64),
                 ("sun_base", C.c_int32), ("design_base", C.c_int32), ("mem", C.c_int32),
                 ("sun_per_design", C.c_int32), ("block_threads", C.c_int32),
-                ("chunks_per_item", C.c_int32)]
+                ("chunks_per_item", C.c_int32), ("kernel_variant", C.c_int32), ("reserved", C.c_int32)]
 
 
 class BVHInfo(C.Structure):
@@ -82,6 +82,10 @@ def load(build_if_needed: bool = True):
     lib.srp_mlp_get_params.argtypes = [_P, _P, _P]
     lib.srp_mlp_infer.argtypes = [_P, _P, _P, i64, _P, i32]
     lib.srp_orbit_opts_default.argtypes = [_P]
+    lib.srp_force_graph_create.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P,
+                                           C.POINTER(_P)]
+    lib.srp_graph_launch.argtypes = [_P]
+    lib.srp_graph_destroy.argtypes = [_P]
     lib.srp_integrate.argtypes = [_P, _P, _P, i32, _P, _P, _P, _P, _P, _P, _P, i32]
     lib.srp_mlp_train_step.argtypes = [_P, _P, _P, _P, i64, C.c_float, _P, _P, i32]
     lib.srp_force_noalloc.argtypes = [_P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P, _P, _P]
@@ -229,7 +233,7 @@ def srp_build_bvh_host(verts, tris, width: int = 4):
 
 def make_opts(*, rays_x=1024, rays_y=None, max_bounces=1, jitter=1, seed=0, pressure=1.0,
               ray_offset=0, ray_stride=1, ray_count=0, sun_base=0, design_base=0, mem=SRP_MEM_DEVICE,
-              sun_per_design=0, block_threads=0, chunks_per_item=0) -> TraceOpts:
+              sun_per_design=0, block_threads=0, chunks_per_item=0, kernel_variant=0) -> TraceOpts:
     o = TraceOpts()
     load().srp_trace_opts_default(C.byref(o))
     o.rays_x = rays_x
@@ -238,6 +242,7 @@ def make_opts(*, rays_x=1024, rays_y=None, max_bounces=1, jitter=1, seed=0, pres
     o.ray_offset = ray_offset; o.ray_stride = ray_stride; o.ray_count = ray_count
     o.sun_base = sun_base; o.design_base = design_base; o.mem = mem
     o.sun_per_design = sun_per_design; o.block_threads = block_threads; o.chunks_per_item = chunks_per_item
+    o.kernel_variant = kernel_variant
     return o
 
 
@@ -519,3 +524,37 @@ def srp_integrate(ctx: Context, opts: OrbitOpts, z0, theta, proxy=None, want_tra
     _check(lib.srp_integrate(ctx.handle, C.byref(opts), proxy.handle if proxy is not None else None, n, _ptr(z0),
                              _ptr(th), _ptr(zN), _ptr(traj), _ptr(lam), _ptr(dth), _ptr(dz0), SRP_MEM_HOST))
     return {"zN": zN, "traj": traj, "dL_dtheta": dth, "dL_dz0": dz0}
+
+
+
+class ForceGraph:
+    """A CUDA graph of one srp_force evaluation on device tensors (captured
+    once; launch() replays it on the context's stream)."""
+
+    def __init__(self, ctx: Context, bvhs, rho, sun_dir, com, out_ft, out_sigma=None, **opts):
+        lib = load()
+        self.ctx = ctx
+        self._keep = (list(bvhs), rho, sun_dir, com, out_ft, out_sigma)
+        bv = list(bvhs)
+        arr = (_P * max(len(bv), 1))(*[b.handle for b in bv])
+        opts["mem"] = SRP_MEM_DEVICE
+        o = make_opts(**opts)
+        h = _P()
+        _check(lib.srp_force_graph_create(ctx.handle, arr, len(bv), _ptr(rho), rho.shape[-2], _ptr(sun_dir),
+                                          sun_dir.shape[-2], _ptr(com), C.byref(o), _ptr(out_ft), _ptr(out_sigma),
+                                          C.byref(h)))
+        self.handle = h
+
+    def launch(self):
+        _check(load().srp_graph_launch(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.srp_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

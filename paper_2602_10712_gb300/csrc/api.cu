@@ -13,9 +13,8 @@
 #include "srp_internal.h"
 
 namespace srp {
-int trace_resident_blocks(int width, int block);
-cudaError_t launch_trace(const std::vector<DesignDev>& designs, const TraceParams& p, int width, int grid_cap,
-                         int block, cudaStream_t st);
+int trace_resident_blocks(int width, int block, int variant);
+cudaError_t launch_trace(const TraceParams& p, int width, int grid_cap, int block, cudaStream_t st);
 cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* out_ft, double* out_sigma,
                           cudaStream_t st);
 cudaError_t launch_trace_rays(const DesignDev& dz, const TraceParams& p, const int64_t* ray_idx, int64_t nr,
@@ -76,6 +75,12 @@ struct srp_ctx {
     bool stats_on = false;
     DevBuf part;                               // trace partials
     DevBuf gpart;                              // gradient partials
+    DevBuf dtab;                               // device design table
+    DesignDev* htab = nullptr;                 // pinned staging of the table
+    size_t htab_n = 0;
+    std::vector<DesignDev> last_tab;           // table currently on the device
+    cudaEvent_t tab_ev = nullptr;              // last table upload
+    unsigned long long* d_queue = nullptr;     // work-queue counter
     DevBuf stage_in, stage_out;                // host-mem staging
 };
 
@@ -117,6 +122,8 @@ int srp_ctx_create(srp_ctx** out, int device, void* cuda_stream) {
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(err)"); }
     e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_stats, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_queue, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->tab_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) { cudaFree(c->d_err); delete c; return cuda_fail(e, "ctx set-up"); }
     *out = c;
@@ -127,7 +134,10 @@ int srp_ctx_destroy(srp_ctx* c) {
     if (!c) return SRP_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    c->part.release(); c->gpart.release(); c->stage_in.release(); c->stage_out.release();
+    c->part.release(); c->gpart.release(); c->stage_in.release(); c->stage_out.release(); c->dtab.release();
+    if (c->htab) cudaFreeHost(c->htab);
+    if (c->tab_ev) cudaEventDestroy(c->tab_ev);
+    if (c->d_queue) cudaFree(c->d_queue);
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_stats) cudaFree(c->d_stats);
     delete c;
@@ -330,6 +340,9 @@ int validate_values(const float* rho, int D, int G, const double* sun, int64_t n
 namespace srp {
 int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, const srp_trace_opts* o,
                std::vector<DesignDev>* designs, TraceParams* p, int* width, int* block, int* grid_cap) {
+    if (o && o->kernel_variant != 0 && o->kernel_variant != 4 && o->kernel_variant != 5)
+        return fail(SRP_EINVAL, "srp_force: kernel_variant must be 0, 4 or 5");
+    const int variant = (o && o->kernel_variant) ? o->kernel_variant : 5;
     if (!c || !o) return fail(SRP_EINVAL, "srp_force: NULL ctx/opts");
     if (D < 0 || S < 0) return fail(SRP_EINVAL, "srp_force: negative D or S");
     if (G < 1 || G > kMaxGroups) return fail(SRP_EINVAL, "srp_force: G must be in 1..64");
@@ -368,7 +381,7 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
         // direction share BVH nodes in L1; a mix of directions per SM thrashed
         // it (2x slower).  At least ~40k units for balance; at most 16M units
         // of partials (1.5 GB); chunks of at least 256 rays.
-        const int64_t warps = (int64_t)c->n_sm * trace_resident_blocks(w ? w : 4, bt) * (bt / 32);
+        const int64_t warps = (int64_t)c->n_sm * trace_resident_blocks(w ? w : 4, bt, variant) * (bt / 32);
         cpb = items > 0 ? std::max<int64_t>((40960 + items - 1) / items, warps) : 1;
         if (items > 0) cpb = std::min<int64_t>(cpb, std::max<int64_t>(1, (int64_t)16777216 / items));
         cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
@@ -385,24 +398,59 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
     p->chunk = chunk; p->cpb = (int32_t)cpb;
     p->err = c->d_err;
     p->stats = c->stats_on ? c->d_stats : nullptr;
-    *grid_cap = c->n_sm * trace_resident_blocks(*width, bt);
+    p->variant = variant;
+    p->queue = c->d_queue;
+    *grid_cap = c->n_sm * trace_resident_blocks(*width, bt, variant);
+    return SRP_OK;
+}
+
+// Put the design table on the device (skipped when unchanged since the
+// previous call); the pinned staging buffer is reused only after its
+// previous upload has completed.
+int upload_designs(srp_ctx* c, const std::vector<DesignDev>& designs) {
+    const size_t n = designs.size();
+    if (n == 0) return SRP_OK;
+    if (c->last_tab.size() == n && std::memcmp(c->last_tab.data(), designs.data(), n * sizeof(DesignDev)) == 0)
+        return SRP_OK;
+    CU(cudaEventSynchronize(c->tab_ev), "cudaEventSynchronize");
+    if (c->htab_n < n) {
+        if (c->htab) cudaFreeHost(c->htab);
+        c->htab = nullptr; c->htab_n = 0;
+        CU(cudaMallocHost((void**)&c->htab, n * sizeof(DesignDev)), "cudaMallocHost(design table)");
+        c->htab_n = n;
+    }
+    if (c->dtab.ensure(n * sizeof(DesignDev)) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force: design table");
+    std::memcpy(c->htab, designs.data(), n * sizeof(DesignDev));
+    CU(cudaMemcpyAsync(c->dtab.p, c->htab, n * sizeof(DesignDev), cudaMemcpyHostToDevice, c->stream), "H2D designs");
+    CU(cudaEventRecord(c->tab_ev, c->stream), "cudaEventRecord");
+    c->last_tab = designs;
+    return SRP_OK;
+}
+
+// Stream work of one evaluation: queue reset, trace, reduce (on `st`).
+int force_enqueue(srp_ctx* c, TraceParams& p, int width, int block, int grid_cap, double* d_part, double* d_ft,
+                  double* d_sigma, cudaStream_t st) {
+    p.part = d_part;
+    const int64_t items = (int64_t)p.D * p.S;
+    if (items == 0 || p.n == 0) {
+        if (items > 0) {
+            CU(cudaMemsetAsync(d_ft, 0, sizeof(double) * 6 * items, st), "cudaMemsetAsync");
+            if (d_sigma) CU(cudaMemsetAsync(d_sigma, 0, sizeof(double) * 6 * items, st), "cudaMemsetAsync");
+        }
+        return SRP_OK;
+    }
+    CU(cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), st), "cudaMemsetAsync(queue)");
+    CU(launch_trace(p, width, grid_cap, block, st), "trace_kernel launch");
+    CU(launch_reduce(d_part, items, p.cpb, d_ft, d_sigma, st), "reduce kernel launch");
     return SRP_OK;
 }
 
 int force_launch(srp_ctx* c, const std::vector<DesignDev>& designs, TraceParams& p, int width, int block,
                  int grid_cap, double* d_part, double* d_ft, double* d_sigma) {
-    p.part = d_part;
-    const int64_t items = (int64_t)p.D * p.S;
-    if (items == 0 || p.n == 0) {
-        if (items > 0) {
-            CU(cudaMemsetAsync(d_ft, 0, sizeof(double) * 6 * items, c->stream), "cudaMemsetAsync");
-            if (d_sigma) CU(cudaMemsetAsync(d_sigma, 0, sizeof(double) * 6 * items, c->stream), "cudaMemsetAsync");
-        }
-        return SRP_OK;
-    }
-    CU(launch_trace(designs, p, width, grid_cap, block, c->stream), "trace_kernel launch");
-    CU(launch_reduce(d_part, items, p.cpb, d_ft, d_sigma, c->stream), "reduce kernel launch");
-    return SRP_OK;
+    int rc = upload_designs(c, designs);
+    if (rc != SRP_OK) return rc;
+    p.designs = (const DesignDev*)c->dtab.p;
+    return force_enqueue(c, p, width, block, grid_cap, d_part, d_ft, d_sigma, c->stream);
 }
 }  // namespace srp
 
@@ -594,3 +642,86 @@ int ctx_device(srp_ctx* c) { return c->device; }
 int* ctx_err(srp_ctx* c) { return c->d_err; }
 int ctx_n_sm(srp_ctx* c) { return c->n_sm; }
 }  // namespace srp
+
+// ---------------------------------------------------------------------------
+// CUDA graph of one srp_force evaluation (device memory)
+// ---------------------------------------------------------------------------
+struct srp_graph {
+    srp_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* dtab = nullptr;  // the graph's own design table
+};
+
+extern "C" int srp_force_graph_create(srp_ctx* c, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                                      const double* sun_dir, int S, const double* com, const srp_trace_opts* o,
+                                      double* out_ft, double* out_sigma, srp_graph** out) {
+    if (!out) return fail(SRP_EINVAL, "srp_force_graph_create: NULL out");
+    *out = nullptr;
+    if (!o || o->mem != SRP_MEM_DEVICE) return fail(SRP_EINVAL, "srp_force_graph_create: needs device memory (mem = SRP_MEM_DEVICE)");
+    std::vector<DesignDev> designs;
+    TraceParams p;
+    std::memset(&p, 0, sizeof p);
+    int width, block, grid_cap;
+    int rc = force_plan(c, bvhs, D, G, S, o, &designs, &p, &width, &block, &grid_cap);
+    if (rc != SRP_OK) return rc;
+    const int64_t items = (int64_t)D * S;
+    if (items > 0 && (!rho || !sun_dir || !com || !out_ft)) return fail(SRP_EINVAL, "srp_force_graph_create: NULL array");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    if (c->part.ensure(sizeof(double) * 12 * (size_t)std::max<int64_t>(items * p.cpb, 1)) != cudaSuccess)
+        return fail(SRP_ENOMEM, "srp_force_graph_create: partials");
+    srp_graph* g = new (std::nothrow) srp_graph();
+    if (!g) return fail(SRP_ENOMEM, "srp_force_graph_create: host memory");
+    g->ctx = c;
+    const size_t tb = std::max<size_t>(designs.size(), 1) * sizeof(DesignDev);
+    cudaError_t e = cudaMalloc(&g->dtab, tb);
+    if (e == cudaSuccess && !designs.empty())
+        e = cudaMemcpy(g->dtab, designs.data(), designs.size() * sizeof(DesignDev), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(g->dtab); delete g; return cuda_fail(e, "srp_force_graph_create: design table"); }
+    p.rho = rho; p.sun = sun_dir; p.com = com;
+    p.designs = (const DesignDev*)g->dtab;
+    // capture on a private stream (the context's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the
+    // context's stream
+    cudaStream_t cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        if (cap) cudaStreamDestroy(cap);
+        cudaFree(g->dtab); delete g;
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    rc = force_enqueue(c, p, width, block, grid_cap, (double*)c->part.p, out_ft, out_sigma, cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (rc != SRP_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(g->dtab); delete g;
+        return rc != SRP_OK ? rc : cuda_fail(e, "cudaStreamEndCapture");
+    }
+    g->graph = graph;
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); cudaFree(g->dtab); delete g; return cuda_fail(e, "cudaGraphInstantiate"); }
+    *out = g;
+    return SRP_OK;
+}
+
+extern "C" int srp_graph_launch(srp_graph* g) {
+    if (!g) return fail(SRP_EINVAL, "srp_graph_launch: NULL graph");
+    CU(cudaSetDevice(g->ctx->device), "cudaSetDevice");
+    CU(cudaGraphLaunch(g->exec, g->ctx->stream), "cudaGraphLaunch");
+    return SRP_OK;
+}
+
+extern "C" int srp_graph_destroy(srp_graph* g) {
+    if (!g) return SRP_OK;
+    cudaSetDevice(g->ctx->device);
+    cudaStreamSynchronize(g->ctx->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->dtab) cudaFree(g->dtab);
+    delete g;
+    return SRP_OK;
+}

@@ -35,9 +35,8 @@
 
 namespace srp {
 void set_last_error(const std::string& msg);
-int trace_resident_blocks(int width, int block);
-cudaError_t launch_trace(const std::vector<DesignDev>& designs, const TraceParams& p, int width, int grid_cap,
-                         int block, cudaStream_t st);
+int trace_resident_blocks(int width, int block, int variant);
+cudaError_t launch_trace(const TraceParams& p, int width, int grid_cap, int block, cudaStream_t st);
 cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* out_ft, double* out_sigma,
                           cudaStream_t st);
 }  // namespace srp
@@ -49,15 +48,21 @@ namespace {
 constexpr size_t kScratchBytes = 8u << 20;                       // 8 MiB
 constexpr int64_t kScratchUnits = (int64_t)(kScratchBytes / (12 * sizeof(double)));
 constexpr int kMaxDevices = 64;
+constexpr int kNoAllocDesigns = 4096;
 
-// The fixed scratch: per-unit FP64 partials, plus the kernels' error word.
+// The fixed scratch: per-unit FP64 partials, the kernels' error word, the
+// work-queue counter and the design table.
 static __device__ __align__(256) double g_scratch[kScratchBytes / sizeof(double)];
 static __device__ __align__(256) int g_err_word;
+static __device__ __align__(256) unsigned long long g_queue_word;
+static __device__ __align__(256) DesignDev g_design_table[kNoAllocDesigns];
 
 struct DevState {
     bool ready = false;
     double* part = nullptr;  // device address of g_scratch on this device
     int* err = nullptr;      // device address of g_err_word on this device
+    unsigned long long* queue = nullptr;  // device address of g_queue_word
+    DesignDev* table = nullptr;           // device address of g_design_table
     int n_sm = 0;
     int resident[2] = {0, 0};  // resident blocks per SM for widths 4 and 8
 };
@@ -81,12 +86,18 @@ int setup_device(int dev, DevState** out) {
         e = cudaGetSymbolAddress(&ptr, g_err_word);
         if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetSymbolAddress(error word): ") + cudaGetErrorString(e));
         s.err = static_cast<int*>(ptr);
+        e = cudaGetSymbolAddress(&ptr, g_queue_word);
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetSymbolAddress(queue): ") + cudaGetErrorString(e));
+        s.queue = static_cast<unsigned long long*>(ptr);
+        e = cudaGetSymbolAddress(&ptr, g_design_table);
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetSymbolAddress(designs): ") + cudaGetErrorString(e));
+        s.table = static_cast<DesignDev*>(ptr);
         int v = 0;
         e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
         s.n_sm = v;
-        s.resident[0] = trace_resident_blocks(4, 128);
-        s.resident[1] = trace_resident_blocks(8, 128);
+        s.resident[0] = trace_resident_blocks(4, 128, 5);
+        s.resident[1] = trace_resident_blocks(8, 128, 5);
         s.ready = true;
     }
     *out = &s;
@@ -119,6 +130,10 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(SRP_EUNSUPPORTED, "srp_force_noalloc: device index too large");
+    if (D > kNoAllocDesigns)
+        return fail(SRP_EINVAL, "srp_force_noalloc: D = " + std::to_string(D) + " exceeds the fixed design-table capacity of " +
+                                    std::to_string(kNoAllocDesigns) + " designs; use srp_force");
+    if (o->kernel_variant != 0) return fail(SRP_EINVAL, "srp_force_noalloc: kernel_variant must be 0");
     std::vector<DesignDev> designs(D);
     int width = 0;
     for (int d = 0; d < D; ++d) {
@@ -186,11 +201,18 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     p.part = ds->part;          // every unit overwrites its 12 partials: no clearing needed
     p.err = ds->err;
     p.stats = nullptr;
-    // the error word only collects flags (OR): it must start at zero
+    p.variant = 5;
+    p.queue = ds->queue;
+    p.designs = ds->table;
+    // the design table: a copy from host memory into the fixed array
+    e = cudaMemcpyAsync(ds->table, designs.data(), sizeof(DesignDev) * (size_t)D, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemcpyAsync(designs): ") + cudaGetErrorString(e));
+    // the error word only collects flags (OR) and the queue counts up: both start at zero
     e = cudaMemsetAsync(ds->err, 0, sizeof(int), st);
-    if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemsetAsync(error word): ") + cudaGetErrorString(e));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ds->queue, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const int grid_cap = ds->n_sm * ds->resident[width == 8 ? 1 : 0];
-    e = launch_trace(designs, p, width, grid_cap, 128, st);
+    e = launch_trace(p, width, grid_cap, 128, st);
     if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("trace_kernel launch: ") + cudaGetErrorString(e));
     e = launch_reduce(ds->part, items, p.cpb, out_ft, out_sigma, st);
     if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("reduce kernel launch: ") + cudaGetErrorString(e));

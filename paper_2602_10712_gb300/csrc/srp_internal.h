@@ -26,7 +26,7 @@ namespace srp {
 constexpr int kMaxGroups = 64;
 constexpr int kMaxBounces = 3;
 constexpr int kStackSize = 64;          // traversal stack entries per ray
-constexpr int kMaxDesignsPerLaunch = 128;
+constexpr int kMaxDesignsPerLaunch = 1 << 20;  // designs of one srp_force call (device table)
 constexpr int kVisitCap = 1 << 20;      // node visits per ray segment (corruption guard)
 
 // Error flags written by kernels (bitwise OR into one device word).
@@ -68,6 +68,9 @@ struct TraceParams {
     double* part;              // [D*S*cpb][12]
     int* err;                  // device error word
     unsigned long long* stats; // [3] node visits, triangle tests, segments (or NULL)
+    const DesignDev* designs;  // [D] device-side design table
+    unsigned long long* queue; // work-queue counter (zeroed before each launch)
+    int32_t variant;           // register budget: minimum resident blocks 4 or 5
 };
 
 }  // namespace srp

@@ -136,9 +136,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 #ifndef SRP_BATCHES
 #define SRP_BATCHES 4
 #endif
-#ifndef SRP_MIN_BLOCKS
-#define SRP_MIN_BLOCKS 5
-#endif
 constexpr int kBatches = SRP_BATCHES;     // primary batches of 32 rays per tile
 constexpr int kTile = 32 * kBatches;      // rays per warp tile
 constexpr int kQueue = 64;                // bounce segments per warp (<= 31 + 32 live)
@@ -204,22 +201,26 @@ __device__ __forceinline__ void q_batch(WarpSmem& ws, int& qcount, int nb, const
     q_push(ws, qcount, cont, nx, slot, kb + 1, lane);
 }
 
-template <int W>
-__global__ void __launch_bounds__(128, SRP_MIN_BLOCKS) trace_kernel(const __grid_constant__ DesignTable tab, const TraceParams p,
-                                                       int d0, int Dl) {
+template <int W, int MINB>
+__global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem& ws = reinterpret_cast<WarpSmem*>(smem)[warp];
-    const int64_t units = (int64_t)Dl * p.S * p.cpb;
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t units = (int64_t)p.D * p.S * p.cpb;
     uint32_t nvis = 0, ntest = 0, nseg = 0;
-    for (int64_t u = gw; u < units; u += nw) {
+    // dynamic work queue: warps take units in order, so the warps resident
+    // at a time work on the same (design, sun) item and uneven designs
+    // balance themselves
+    while (true) {
+        unsigned long long uq = 0;
+        if (lane == 0) uq = atomicAdd(p.queue, 1ull);
+        const int64_t u = (int64_t)__shfl_sync(0xffffffffu, uq, 0);
+        if (u >= units) break;
         const int64_t item_l = u / p.cpb;
         const int64_t cidx = u % p.cpb;
         const int dl = (int)(item_l / p.S), s = (int)(item_l % p.S);
-        const int dg = d0 + dl;
-        const DesignDev& dz = tab.d[dl];
+        const int dg = dl;
+        const DesignDev dz = p.designs[dl];
         ItemConst ic;
         item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dg * p.S + s : s)), p.com + 3 * dg,
                    p.rho + (size_t)dg * p.G * 2, p.design_base + dg, p.sun_base + s);
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(128, SRP_MIN_BLOCKS) trace_kernel(const __grid
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
             const double v = warp_sum_d(ws.dacc[q][lane]);
-            if (lane == q) p.part[((size_t)(d0 * (int64_t)p.S * p.cpb) + u) * 12 + q] = v;
+            if (lane == q) p.part[(size_t)u * 12 + q] = v;
         }
         __syncwarp();
     }
@@ -341,44 +342,37 @@ __global__ void reduce_items_kernel(const double* __restrict__ part, int64_t ite
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-template <int W>
-static cudaError_t launch_w(const DesignTable& tab, const TraceParams& p, int d0, int Dl, int grid, int block,
-                            cudaStream_t st) {
-    const size_t sm = trace_smem_bytes(block);
-    cudaError_t e = cudaFuncSetAttribute(trace_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    trace_kernel<W><<<grid, block, sm, st>>>(tab, p, d0, Dl);
-    return cudaGetLastError();
-}
-
-int trace_resident_blocks(int width, int block) {
+template <int W, int MINB>
+static int resident_blocks_v(int block) {
     int nb = 0;
     const size_t sm = trace_smem_bytes(block);
-    if (width == 8) {
-        cudaFuncSetAttribute(trace_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<8>, block, sm);
-    } else {
-        cudaFuncSetAttribute(trace_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<4>, block, sm);
-    }
+    cudaFuncSetAttribute(trace_kernel<W, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<W, MINB>, block, sm);
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_trace(const std::vector<DesignDev>& designs, const TraceParams& p, int width, int grid_cap,
-                         int block, cudaStream_t st) {
-    const int D = (int)designs.size();
-    for (int d0 = 0; d0 < D; d0 += kMaxDesignsPerLaunch) {
-        const int Dl = std::min(kMaxDesignsPerLaunch, D - d0);
-        DesignTable tab;
-        for (int k = 0; k < Dl; ++k) tab.d[k] = designs[d0 + k];
-        const int64_t units = (int64_t)Dl * p.S * p.cpb;
-        const int64_t wpb = block / 32;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + wpb - 1) / wpb, grid_cap));
-        cudaError_t e = width == 8 ? launch_w<8>(tab, p, d0, Dl, grid, block, st)
-                                   : launch_w<4>(tab, p, d0, Dl, grid, block, st);
-        if (e != cudaSuccess) return e;
+// Also performs the one-time kernel attribute set-up (call before launching).
+int trace_resident_blocks(int width, int block, int variant) {
+    if (width == 8) return variant == 4 ? resident_blocks_v<8, 4>(block) : resident_blocks_v<8, 5>(block);
+    return variant == 4 ? resident_blocks_v<4, 4>(block) : resident_blocks_v<4, 5>(block);
+}
+int trace_resident_blocks(int width, int block) { return trace_resident_blocks(width, block, 5); }
+
+// One persistent launch over every (design, sun, chunk) unit.  p.designs,
+// p.queue (zeroed on the stream before the launch) and p.part are set.
+cudaError_t launch_trace(const TraceParams& p, int width, int grid_cap, int block, cudaStream_t st) {
+    const int64_t units = (int64_t)p.D * p.S * p.cpb;
+    const int64_t wpb = block / 32;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + wpb - 1) / wpb, grid_cap));
+    const size_t sm = trace_smem_bytes(block);
+    if (width == 8) {
+        if (p.variant == 4) trace_kernel<8, 4><<<grid, block, sm, st>>>(p);
+        else trace_kernel<8, 5><<<grid, block, sm, st>>>(p);
+    } else {
+        if (p.variant == 4) trace_kernel<4, 4><<<grid, block, sm, st>>>(p);
+        else trace_kernel<4, 5><<<grid, block, sm, st>>>(p);
     }
-    return cudaSuccess;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trace_rays(const DesignDev& dz, const TraceParams& p, const int64_t* ray_idx, int64_t nr,

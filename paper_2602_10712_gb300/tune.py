@@ -1,0 +1,52 @@
+"""Autotuner of the tracer's launch parameters.
+
+For a design (or set of designs) and a workload, time srp_force on a strided
+sample of the real work for every candidate (BVH width 4 or 8, kernel
+register budget 4 or 5 resident blocks per SM) and return the fastest.  The
+sample keeps the full grid geometry (same rays_x/rays_y, every k-th ray), so
+the traversal work per ray is the workload's.
+"""
+from __future__ import annotations
+
+import itertools
+import time
+
+import numpy as np
+
+from . import srp_build_bvh, srp_force
+
+
+def autotune(ctx, meshes, rho, sun_dir, com, *, rays_x, rays_y=None, max_bounces=1, sample_rays=65536,
+             sample_suns=16, widths=(4, 8), variants=(4, 5), repeats=2, **opts):
+    """Returns (best dict(width, kernel_variant), table of timings in
+    rays/s).  `meshes` are workloads.Mesh-like (verts, tris, group);
+    rho [D,G,2], sun_dir [S,3] (or [D,S,3] with sun_per_design=1), com [D,3]
+    are torch CUDA tensors."""
+    import torch
+    ry = rays_x if rays_y is None else rays_y
+    n = rays_x * ry
+    stride = max(1, n // sample_rays)
+    count = min(sample_rays, (n + stride - 1) // stride)
+    S = sun_dir.shape[-2]
+    sel = torch.arange(0, S, max(1, S // sample_suns), device=sun_dir.device)[:sample_suns]
+    sun_s = sun_dir.index_select(-2, sel).contiguous()
+    table = []
+    bvhs = {w: [srp_build_bvh(ctx, m.verts, m.tris, m.group, w) for m in meshes] for w in widths}
+    for w, v in itertools.product(widths, variants):
+        kw = dict(rays_x=rays_x, rays_y=ry, max_bounces=max_bounces, ray_offset=0, ray_stride=stride,
+                  ray_count=count, kernel_variant=v, **opts)
+        srp_force(ctx, bvhs[w], rho, sun_s, com, **kw)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            srp_force(ctx, bvhs[w], rho, sun_s, com, **kw)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        rate = len(meshes) * sun_s.shape[-2] * count / best
+        table.append({"width": w, "kernel_variant": v, "rays_per_s": rate})
+    for bl in bvhs.values():
+        for b in bl:
+            b.close()
+    best = max(table, key=lambda r: r["rays_per_s"])
+    return {"width": best["width"], "kernel_variant": best["kernel_variant"]}, table

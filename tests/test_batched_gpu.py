@@ -1,0 +1,94 @@
+"""Batched evaluation (many designs of uneven size x many suns in one
+persistent launch with a work queue), the CUDA-graph replay and the
+autotuner's candidates: all give the results of the plain call."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def srp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_10712_gb300 as srp
+    return srp
+
+
+def test_uneven_designs_one_launch_match_single_calls(srp):
+    """200 designs (16 to ~3k triangles) x 4 suns in one call equal the
+    per-design calls bit for bit (same chunking, same counters)."""
+    ctx = srp.Context(0)
+    designs = []
+    for k in range(200):
+        if k % 3 == 0:
+            designs.append(W.box_wing())
+        elif k % 3 == 1:
+            designs.append(W.procedural_satellite(seed=k, dish_segments=16, dish_rings=4 + k % 7, n_boxes=3 + k % 11))
+        else:
+            designs.append(W.icosphere(1 + k % 3))
+    G = 64
+    rho = np.stack([W.random_reflectances(G, seed=k) for k in range(200)])
+    for d in designs:
+        d.group = np.asarray(d.group) % G
+    sun = W.fibonacci_directions(4)
+    com = np.zeros((200, 3))
+    bv = [srp.srp_build_bvh(ctx, d.verts, d.tris, d.group, 4) for d in designs]
+    kw = dict(rays_x=64, max_bounces=3, chunks_per_item=4)
+    allf = srp.srp_force(ctx, bv, rho, sun, com, **kw)
+    for k in (0, 1, 2, 77, 199):
+        one = srp.srp_force(ctx, [bv[k]], rho[k:k + 1], sun, com[k:k + 1], design_base=k, **kw)
+        assert np.array_equal(allf[k], one[0]), k
+    # and against the oracle for a few designs
+    for k in (1, 2):
+        fo, _ = oracle.force(designs[k].verts, designs[k].tris, designs[k].group, rho[k], sun, com[k], nx=64, K=3,
+                             design_index=k)
+        R = bv[k].info()["radius"]
+        for s in range(4):
+            fn = np.linalg.norm(fo[s, :3])
+            w = (2 * R / 64) ** 2
+            assert np.linalg.norm(allf[k, s, :3] - fo[s, :3]) <= max(1e-5 * fn, 2.0 * w)
+
+
+def test_graph_replay_equals_call(srp):
+    ctx = srp.Context(0)
+    m, rho, _, com = W.config2(16)
+    sun = W.fibonacci_directions(16)
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+    dev = torch.device("cuda:0")
+    r_t = torch.from_numpy(rho[None].copy()).to(dev)
+    s_t = torch.from_numpy(sun).to(dev)
+    c_t = torch.from_numpy(com[None].copy()).to(dev)
+    kw = dict(rays_x=256, max_bounces=3)
+    ref = srp.srp_force(ctx, [b], r_t, s_t, c_t, **kw).clone()
+    out = torch.zeros((1, 16, 6), dtype=torch.float64, device=dev)
+    g = srp.ForceGraph(ctx, [b], r_t, s_t, c_t, out, **kw)
+    for _ in range(2):
+        out.zero_()
+        g.launch()
+        srp.srp_sync(ctx)
+        assert torch.equal(out, ref)
+    g.close()
+
+
+def test_kernel_variants_and_autotuner(srp):
+    from paper_2602_10712_gb300 import tune
+    ctx = srp.Context(0)
+    m, rho, _, com = W.config2(8)
+    sun = W.fibonacci_directions(8)
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+    kw = dict(rays_x=200, max_bounces=3, chunks_per_item=16)
+    f5 = srp.srp_force(ctx, [b], rho[None], sun, com[None], kernel_variant=5, **kw)
+    f4 = srp.srp_force(ctx, [b], rho[None], sun, com[None], kernel_variant=4, **kw)
+    assert np.array_equal(f4, f5)
+    dev = torch.device("cuda:0")
+    best, table = tune.autotune(ctx, [m], torch.from_numpy(rho[None].copy()).to(dev), torch.from_numpy(sun).to(dev),
+                                torch.from_numpy(com[None].copy()).to(dev), rays_x=512, max_bounces=3,
+                                sample_rays=16384, sample_suns=4)
+    assert len(table) == 4 and best["width"] in (4, 8) and best["kernel_variant"] in (4, 5)
+    assert all(r["rays_per_s"] > 0 for r in table)

@@ -127,4 +127,4 @@ def test_opts_struct_matches_header():
     """ctypes mirror of srp_trace_opts has the C layout (defaults round-trip)."""
     o = srp.make_opts()
     assert o.rays_x == 1024 and o.max_bounces == 1 and o.pressure == 1.0 and o.mem == srp.SRP_MEM_DEVICE
-    assert C.sizeof(srp.TraceOpts) == 80 and srp.TraceOpts.pressure.offset == 24
+    assert C.sizeof(srp.TraceOpts) == 88 and srp.TraceOpts.pressure.offset == 24
