@@ -96,8 +96,8 @@ int setup_device(int dev, DevState** out) {
         e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
         s.n_sm = v;
-        s.resident[0] = trace_resident_blocks(4, 128, 5);
-        s.resident[1] = trace_resident_blocks(8, 128, 5);
+        s.resident[0] = trace_resident_blocks(4, 128, 6);
+        s.resident[1] = trace_resident_blocks(8, 128, 6);
         s.ready = true;
     }
     *out = &s;
@@ -201,7 +201,7 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     p.part = ds->part;          // every unit overwrites its 12 partials: no clearing needed
     p.err = ds->err;
     p.stats = nullptr;
-    p.variant = 5;
+    p.variant = 6;
     p.queue = ds->queue;
     p.designs = ds->table;
     // the design table: a copy from host memory into the fixed array

@@ -146,7 +146,7 @@ struct WarpSmem {
     float4 qa[kQueue];         // (o.xyz, w)
     float4 qb[kQueue];         // (d.xyz, src)
     int qs[kQueue];            // slot | (bounce << 16)
-    double dacc[12][32];       // per-lane FP64 sums (force, torque, squared pair differences)
+    double dacc[12];           // warp FP64 sums (force, torque, squared pair differences)
 };
 
 __host__ __device__ constexpr size_t trace_smem_bytes(int block) {
@@ -224,8 +224,7 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
         ItemConst ic;
         item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dg * p.S + s : s)), p.com + 3 * dg,
                    p.rho + (size_t)dg * p.G * 2, p.design_base + dg, p.sun_base + s);
-#pragma unroll
-        for (int q = 0; q < 12; ++q) ws.dacc[q][lane] = 0.0;
+        if (lane < 12) ws.dacc[lane] = 0.0;
         const int64_t k0 = cidx * p.chunk;
         const int64_t k1 = min(k0 + p.chunk, p.n);
         int qcount = 0;
@@ -280,19 +279,20 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
                     }
                 }
             }
+            // tile sums: fixed-order FP32 warp tree (<= 4 rays per lane), then FP64
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
-                ws.dacc[q][lane] += (double)accf[q];
-                ws.dacc[6 + q][lane] += (double)sqf[q];
+                float a = accf[q], b = sqf[q];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, off);
+                    b += __shfl_xor_sync(0xffffffffu, b, off);
+                }
+                if (lane == 0) { ws.dacc[q] += (double)a; ws.dacc[6 + q] += (double)b; }
             }
             __syncwarp();
         }
-        // warp reduction in a fixed order -> the unit's partial
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            const double v = warp_sum_d(ws.dacc[q][lane]);
-            if (lane == q) p.part[(size_t)u * 12 + q] = v;
-        }
+        if (lane < 12) p.part[(size_t)u * 12 + lane] = ws.dacc[lane];
         __syncwarp();
     }
     if (p.stats) {  // traversal work counters (node visits, triangle tests, segments)
@@ -353,8 +353,14 @@ static int resident_blocks_v(int block) {
 
 // Also performs the one-time kernel attribute set-up (call before launching).
 int trace_resident_blocks(int width, int block, int variant) {
-    if (width == 8) return variant == 4 ? resident_blocks_v<8, 4>(block) : resident_blocks_v<8, 5>(block);
-    return variant == 4 ? resident_blocks_v<4, 4>(block) : resident_blocks_v<4, 5>(block);
+    if (width == 8) {
+        if (variant == 4) return resident_blocks_v<8, 4>(block);
+        if (variant == 6) return resident_blocks_v<8, 6>(block);
+        return resident_blocks_v<8, 5>(block);
+    }
+    if (variant == 4) return resident_blocks_v<4, 4>(block);
+    if (variant == 6) return resident_blocks_v<4, 6>(block);
+    return resident_blocks_v<4, 5>(block);
 }
 int trace_resident_blocks(int width, int block) { return trace_resident_blocks(width, block, 5); }
 
@@ -367,9 +373,11 @@ cudaError_t launch_trace(const TraceParams& p, int width, int grid_cap, int bloc
     const size_t sm = trace_smem_bytes(block);
     if (width == 8) {
         if (p.variant == 4) trace_kernel<8, 4><<<grid, block, sm, st>>>(p);
+        else if (p.variant == 6) trace_kernel<8, 6><<<grid, block, sm, st>>>(p);
         else trace_kernel<8, 5><<<grid, block, sm, st>>>(p);
     } else {
         if (p.variant == 4) trace_kernel<4, 4><<<grid, block, sm, st>>>(p);
+        else if (p.variant == 6) trace_kernel<4, 6><<<grid, block, sm, st>>>(p);
         else trace_kernel<4, 5><<<grid, block, sm, st>>>(p);
     }
     return cudaGetLastError();

@@ -17,7 +17,7 @@ from . import srp_build_bvh, srp_force
 
 
 def autotune(ctx, meshes, rho, sun_dir, com, *, rays_x, rays_y=None, max_bounces=1, sample_rays=65536,
-             sample_suns=16, widths=(4, 8), variants=(4, 5), repeats=2, **opts):
+             sample_suns=16, widths=(4, 8), variants=(4, 5, 6), repeats=2, **opts):
     """Returns (best dict(width, kernel_variant), table of timings in
     rays/s).  `meshes` are workloads.Mesh-like (verts, tris, group);
     rho [D,G,2], sun_dir [S,3] (or [D,S,3] with sun_per_design=1), com [D,3]

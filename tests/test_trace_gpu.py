@@ -119,7 +119,8 @@ def test_procedural_satellite_sampled_full_grid(srp, ctx):
         # aggregate over the sample through srp_force (same rays, same counters)
         ft = srp.srp_force(ctx, [b], rho[None], sun_all[s:s + 1], com[None], rays_x=2048, max_bounces=3,
                            ray_offset=0, ray_stride=1021, ray_count=len(idx), sun_base=s)
-        assert np.allclose(ft[0, 0], yg.sum(0), rtol=1e-7, atol=1e-9 * w)
+        # FP32 tile partials (<= 128 rays) then FP64: rounding ~1e-7 of the sums' scale
+        assert np.linalg.norm(ft[0, 0] - yg.sum(0)) <= 1e-6 * np.linalg.norm(yg.sum(0)) + 1e-9 * w
         # oracle aggregate, with the differing rays' contributions swapped in
         fo_agree = yo[same].sum(0)
         fg_agree = yg[same].sum(0)
