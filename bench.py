@@ -38,6 +38,10 @@ N_SUN = 4096
 NX = 2048
 K_BOUNCE = 3
 WORKLOAD = "procedural satellite 49,776 tris, 64 groups, 4096 Fibonacci suns x 2048^2 rays, K<=3"
+# dram__bytes_read.sum + dram__bytes_write.sum of trace_kernel<4,6> from the ncu
+# capture of 16 of the 4096 suns (profiles/trace_kernel_config2_16suns_full.md),
+# scaled by the units processed (x256) to one benchmark launch
+TRACE_DRAM_BYTES_PER_LAUNCH = (12.849664e6 + 42.426368e6) * 256
 
 
 def _peaks():
@@ -282,7 +286,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": e2e, "unit": "rays/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                     "frac": achieved / peak_alu, "traffic": None,
+                     "frac": achieved / peak_alu, "traffic": TRACE_DRAM_BYTES_PER_LAUNCH,
                      "note": (f"trace_kernel FP32 lane-ops: {ops_per_ray:.0f}/ray = node visits x {ops_node} + "
                               f"triangle tests x {ops_tri}; peak = {n_sm} SM x 128 FP32 lanes x {sm_mhz:.0f} MHz; "
                               f"algorithmic bytes {bytes_per_ray:.0f} B/ray from L1/L2 (scene {info['device_bytes']} B)"),

@@ -11,7 +11,7 @@
 //   core-matrix layout (tc_common.cuh), so a layer is one contiguous block
 //   that a 1-D bulk copy moves into shared memory.
 //
-// Forward kernel (one CTA of 128 threads per 128 batch rows):
+// Forward kernel (one CTA of 256 threads per 128 batch rows):
 //   X (FP32) -> BF16 tile in smem; per layer: bulk-copy W_l into smem,
 //   one thread issues K_l/16 tcgen05.mma (M=128, N=N_l, K=16) into a
 //   256-column TMEM accumulator, commit -> mbarrier; the four warps read
@@ -88,15 +88,32 @@ struct MlpFwdSmem {
     uint32_t tmem_base;
 };
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
-__global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict__ x, int64_t B,
+// Issue the bulk copies of layer l's packed weights into smem (one thread).
+__device__ __forceinline__ void load_layer_weights(MlpFwdSmem& sm, const __nv_bfloat16* packed, const MlpLayout& L,
+                                                   int l) {
+    const uint32_t wbytes = (uint32_t)(mlp_N(l) * mlp_K(l) * 2);
+    tc::mbar_expect_tx(&sm.bar_w, wbytes);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(packed + L.p_off[l]);
+    for (uint32_t o = 0; o < wbytes; o += 32768u) {
+        const uint32_t nb = wbytes - o < 32768u ? wbytes - o : 32768u;
+        tc::bulk_g2s(sm.w + o, src + o, nb, &sm.bar_w);
+    }
+}
+
+// 256 threads: warps w and w+4 share TMEM lane quarter w%4 (rows) and
+// split each layer's output columns in halves for the epilogue.  The next
+// layer's weights are requested as soon as this layer's MMAs have released
+// the weight buffer, so the copy overlaps the epilogue.
+__global__ void __launch_bounds__(256, 1) mlp_fwd_kernel(const float* __restrict__ x, int64_t B,
                                                         const __nv_bfloat16* __restrict__ packed,
                                                         const float* __restrict__ params, float* __restrict__ y,
                                                         int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     MlpFwdSmem& sm = *reinterpret_cast<MlpFwdSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
     const MlpLayout L = mlp_layout();
     const int64_t row0 = (int64_t)blockIdx.x * 128;
     if (tid == 0) {
@@ -108,8 +125,10 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
         tc::tmem_alloc(&sm.tmem_base, 256);
         tc::tmem_relinquish();
     }
-    // input tile: row r = tid, K = 32 (19 used)
-    {
+    __syncthreads();
+    if (tid == 0) load_layer_weights(sm, packed, L, 0);
+    // input tile: row r = tid (threads < 128), K = 32 (19 used)
+    if (tid < 128) {
         const int64_t row = row0 + tid;
         float v[32];
 #pragma unroll
@@ -135,15 +154,6 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
     int failed = 0;  // block-uniform (decided with __syncthreads_or)
     for (int l = 0; l < kMlpLayers; ++l) {
         const int K = mlp_K(l), N = mlp_N(l);
-        const uint32_t wbytes = (uint32_t)(N * K * 2);
-        if (tid == 0) {
-            tc::mbar_expect_tx(&sm.bar_w, wbytes);
-            const unsigned char* src = reinterpret_cast<const unsigned char*>(packed + L.p_off[l]);
-            for (uint32_t o = 0; o < wbytes; o += 32768u) {
-                const uint32_t nb = wbytes - o < 32768u ? wbytes - o : 32768u;
-                tc::bulk_g2s(sm.w + o, src + o, nb, &sm.bar_w);
-            }
-        }
         const bool okw = tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
         ph_w ^= 1;
         if (__syncthreads_or(!okw)) { failed = 1; break; }
@@ -163,12 +173,16 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
         ph_m ^= 1;
         if (__syncthreads_or(!okm)) { failed = 1; break; }
         tc::tc_fence_after();
-        // epilogue: warp w owns TMEM lanes (rows) 32w..32w+31
-        const int r = 32 * warp + lane;
-        const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+        // the weight buffer is free: fetch the next layer's weights now
+        if (tid == 0 && l + 1 < kMlpLayers) load_layer_weights(sm, packed, L, l + 1);
+        // epilogue: rows 32*quarter + lane, column half `half`
+        const int r = 32 * quarter + lane;
+        const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
         if (l < kMlpLayers - 1) {
             const float* bias = params + L.b_off[l];
-            for (int c = 0; c < N / 32; ++c) {
+            const int nc = N / 64;  // 32-column chunks per half
+            for (int cc = 0; cc < nc; ++cc) {
+                const int c = half * nc + cc;
                 float v[32];
                 tc::tmem_ld32(taddr + 32u * c, v);
 #pragma unroll
@@ -180,7 +194,7 @@ __global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const float* __restrict
                         *reinterpret_cast<uint4*>(h);
                 }
             }
-        } else {
+        } else if (half == 0) {
             const float* bias = params + L.b_off[l];
             float v[32];
             tc::tmem_ld32(taddr, v);
@@ -217,7 +231,7 @@ cudaError_t mlp_forward(const float* x, int64_t B, const void* packed, const flo
     cudaError_t e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((B + 127) / 128);
-    mlp_fwd_kernel<<<grid, 128, sm, st>>>(x, B, (const __nv_bfloat16*)packed, params, y, err);
+    mlp_fwd_kernel<<<grid, 256, sm, st>>>(x, B, (const __nv_bfloat16*)packed, params, y, err);
     return cudaGetLastError();
 }
 
