@@ -314,7 +314,7 @@ def extra_legs(srp, ctx, dev, peaks):
     from paper_2602_10712_gb300 import surrogate as S
     mesh = W.box_wing_7group()
     t0 = time.perf_counter()
-    sur, info = S.fit(ctx, mesh, n_designs=4096, suns_per_design=256, rays=256, bounces=3, epochs=20, batch=8192,
+    sur, info = S.fit(ctx, mesh, n_designs=4096, suns_per_design=256, rays=256, bounces=3, epochs=100, batch=8192,
                       lr=2e-3, seed=0)
     fit_s = time.perf_counter() - t0
     err = S.force_rms_error(sur, ctx, mesh, n_designs=512, suns_per_design=16, rays=1024, bounces=3, seed=99)
@@ -350,7 +350,7 @@ def extra_legs(srp, ctx, dev, peaks):
     mc_rate = 4096 / (e0.elapsed_time(e1) / 1e3)
     peak = peaks.get("bf16_tflops", 1900.0)
     surrogate = {"evals_per_s": nn_rate, "tracer_evals_per_s_256sq_rays": mc_rate, "speedup": nn_rate / mc_rate,
-                 "force_rms_rel_err": err, "train_samples": info["samples"], "fit_s": fit_s,
+                 "force_rms_rel_err": err, "train_samples": info["samples"], "train_steps": info["steps"], "fit_s": fit_s,
                  "mlp_tflops": flops / t_nn / 1e12, "mlp_frac_of_bf16_peak": flops / t_nn / 1e12 / peak,
                  "batch": nq, "note": "19-256x4-6 SiLU, BF16 tcgen05, FP32 accumulation; error vs 1024^2-ray MC"}
     # gradients: box-wing (64 groups, 2 hinges), K = 1, 1024^2 rays, 64 suns per call
@@ -378,6 +378,33 @@ def extra_legs(srp, ctx, dev, peaks):
     return surrogate, grad
 
 
+def run_profile_case(case):
+    """Small cases for ncu captures (3 calls each; capture the third):
+    trace -- srp_force on 16 of the 4096 suns x 2048^2 rays, K <= 3;
+    mlp   -- proxy inference on 262,144 queries."""
+    import torch
+
+    import paper_2602_10712_gb300 as srp
+    ctx = srp.Context(0)
+    dev = torch.device("cuda:0")
+    if case == "trace":
+        m, rho, _, com = W.config2(16)
+        sun = W.fibonacci_directions(N_SUN)[::256].copy()
+        b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+        r_t = torch.from_numpy(rho[None].copy()).to(dev)
+        s_t = torch.from_numpy(sun).to(dev)
+        c_t = torch.from_numpy(com[None].copy()).to(dev)
+        for _ in range(3):
+            srp.srp_force(ctx, [b], r_t, s_t, c_t, rays_x=NX, max_bounces=K_BOUNCE)
+    elif case == "mlp":
+        net = srp.MLP(ctx, seed=1)
+        x = torch.randn((1 << 18, 19), device=dev)
+        for _ in range(3):
+            net.infer(x)
+    torch.cuda.synchronize()
+    print(f"profile case {case}: ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,7 +415,12 @@ def main():
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--profile", choices=["trace", "mlp"], default=None,
+                    help="run a small ncu capture case and exit")
     args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args.profile)
+        return
     ws, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -107,3 +107,18 @@ def test_batched_trajectories_independent(srp):
     r0 = srp.srp_integrate(ctx, o, z0[:1], th[:1])
     r1 = srp.srp_integrate(ctx, o, z0[1:], th[1:])
     assert np.array_equal(r2["zN"][0], r0["zN"][0]) and np.array_equal(r2["zN"][1], r1["zN"][0])
+
+
+def test_design_optimisation_loop(srp):
+    """Alg. 1's optimisation: recover the cannonball parameter that produced
+    a reference end position (2 h arc) from a start 40% off, with bounds."""
+    from paper_2602_10712_gb300.design import optimize_design
+    ctx = srp.Context(0)
+    o = srp.orbit_opts(model=srp.SRP_FM_CANNONBALL, pressure=4.56e-6 * 100, mass=100.0, sun=SUN, dt=60.0,
+                       n_steps=120, n_theta=1)
+    z0 = _z0()
+    ref = srp.srp_integrate(ctx, o, z0, np.array([30.0]))["zN"][0, :3]
+    th, losses = optimize_design(ctx, o, z0, np.array([18.0]), ref, steps=100, lr=1.0, lo=np.array([0.0]),
+                                 hi=np.array([100.0]))
+    assert losses[-1] < 1e-4 * losses[0], losses[[0, -1]]
+    assert abs(th[0] - 30.0) < 0.05

@@ -129,25 +129,21 @@ def random_reflectances(n_groups: int, seed: int = 0, hi: float = 0.5):
 def _paraboloid_dish(z0, focal, radius, segments, rings, v0):
     """Open paraboloid z = z0 + r^2/(4 f), r <= radius; a fan of `segments`
     triangles at the apex and (rings-1) rings of quads."""
-    verts = [(0.0, 0.0, z0)]
-    for j in range(1, rings + 1):
-        r = radius * j / rings
-        z = z0 + r * r / (4.0 * focal)
-        for s in range(segments):
-            a = 2.0 * math.pi * s / segments
-            verts.append((r * math.cos(a), r * math.sin(a), z))
-    verts = np.asarray(verts)
-    tris = []
-    ring = lambda j, s: 1 + (j - 1) * segments + (s % segments)
-    for s in range(segments):
-        tris.append((0, ring(1, s), ring(1, s + 1)))
-    for j in range(1, rings):
-        for s in range(segments):
-            a, b = ring(j, s), ring(j, s + 1)
-            c, d = ring(j + 1, s + 1), ring(j + 1, s)
-            tris.append((a, d, c))
-            tris.append((a, c, b))
-    return verts, np.asarray(tris, dtype=np.int64) + v0
+    j = np.arange(1, rings + 1, dtype=np.float64)
+    r = radius * j / rings
+    a = 2.0 * math.pi * np.arange(segments, dtype=np.float64) / segments
+    ring_v = np.stack([np.outer(r, np.cos(a)), np.outer(r, np.sin(a)),
+                       np.repeat((z0 + r * r / (4.0 * focal))[:, None], segments, axis=1)], axis=-1)
+    verts = np.concatenate([np.array([[0.0, 0.0, z0]]), ring_v.reshape(-1, 3)])
+    s_ = np.arange(segments)
+    ring = lambda jj, ss: 1 + (jj - 1) * segments + (ss % segments)
+    fan = np.stack([np.zeros(segments, np.int64), ring(1, s_), ring(1, s_ + 1)], axis=1)
+    jj = np.arange(1, rings)[:, None]
+    a_, b_ = ring(jj, s_), ring(jj, s_ + 1)
+    c_, d_ = ring(jj + 1, s_ + 1), ring(jj + 1, s_)
+    quads = np.stack([np.stack([a_, d_, c_], -1), np.stack([a_, c_, b_], -1)], axis=2).reshape(-1, 3)
+    tris = np.concatenate([fan, quads]).astype(np.int64)
+    return verts, tris + v0
 
 
 def procedural_satellite(seed: int = 1, dish_segments: int = 256, dish_rings: int = 93,
