@@ -138,6 +138,15 @@ typedef struct srp_bvh_info {
 } srp_bvh_info;
 int srp_bvh_get_info(const srp_bvh* bvh, srp_bvh_info* info);
 
+/* Replace the device node array of `bvh` with node_data [n_floats] (host,
+ * the layout srp_build_bvh_host produces; same node count and width), e.g.
+ * a structure built or stored elsewhere.  Every child index is checked
+ * against the node and triangle counts (SRP_EINVAL otherwise); a
+ * structurally wrong but in-range tree (a cycle) is caught on the device
+ * by the traversal's stack-depth and node-visit limits, reported as
+ * SRP_EDEVICE_LIMIT. */
+int srp_bvh_set_nodes(srp_ctx* ctx, srp_bvh* bvh, const float* node_data, int64_t n_floats);
+
 /* Host-only build of the same wide BVH, for inspection and serialisation
  * (no device, no context).  Two-call pattern: with node_data == NULL it
  * stores the sizes in *n_node_floats and *n_nodes and returns.  Otherwise

@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
-           "srp_build_bvh_host", "srp_trace_rays", "srp_force_noalloc", "srp_force_grad", "SRPForce", "MLP",
+           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_force_noalloc", "srp_force_grad", "SRPForce", "MLP",
            "mlp_param_count", "srp_integrate", "orbit_opts", "OrbitOpts", "ForceGraph",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
@@ -74,6 +74,7 @@ def load(build_if_needed: bool = True):
     lib.srp_bvh_get_info.argtypes = [_P, C.POINTER(BVHInfo)]
     lib.srp_force.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P]
     lib.srp_collect_stats.argtypes = [_P, i32, _P]
+    lib.srp_bvh_set_nodes.argtypes = [_P, _P, _P, i64]
     lib.srp_force_grad.argtypes = [_P, _P, _P, i32, _P, i32, _P, _P, _P, i32, C.POINTER(TraceOpts), _P, _P, _P]
     lib.srp_mlp_param_count.argtypes = [C.POINTER(C.c_int64)]
     lib.srp_mlp_create.argtypes = [_P, _P, C.c_uint64, C.POINTER(_P)]
@@ -214,6 +215,11 @@ def srp_bvh_get_info(b: BVH) -> dict:
     return {"width": info.width, "n_nodes": info.n_nodes, "n_leaves": info.n_leaves, "depth": info.depth,
             "n_tris": info.n_tris, "device_bytes": info.device_bytes, "build_ms": info.build_ms,
             "center": tuple(info.center), "radius": info.radius}
+
+
+def srp_bvh_set_nodes(ctx: Context, b: BVH, node_data):
+    nd = _np(node_data, np.float32).reshape(-1)
+    _check(load().srp_bvh_set_nodes(ctx.handle, b.handle, _ptr(nd), nd.shape[0]))
 
 
 def srp_build_bvh_host(verts, tris, width: int = 4):

@@ -294,6 +294,34 @@ int srp_build_bvh_host(const float* verts, int V, const int32_t* tris, int T, in
     return SRP_OK;
 }
 
+int srp_bvh_set_nodes(srp_ctx* c, srp_bvh* h, const float* node_data, int64_t n_floats) {
+    if (!c || !h || !node_data) return fail(SRP_EINVAL, "srp_bvh_set_nodes: NULL argument");
+    const int nf = h->width == 4 ? 32 : 64;
+    if (n_floats != (int64_t)h->n_nodes * nf) return fail(SRP_EINVAL, "srp_bvh_set_nodes: size differs from the BVH's");
+    const int W = h->width;
+    for (int64_t n = 0; n < h->n_nodes; ++n) {
+        const int32_t* ch = reinterpret_cast<const int32_t*>(node_data + n * nf + 6 * W);
+        for (int k = 0; k < W; ++k) {
+            const float lo = node_data[n * nf + k];  // lo_x of child k
+            const float hi = node_data[n * nf + W + k];
+            if (!(lo <= hi)) continue;  // empty slot (never traversed)
+            const int32_t code = ch[k];
+            if (code >= 0) {
+                if (code >= h->n_nodes) return fail(SRP_EINVAL, "srp_bvh_set_nodes: inner child index out of range");
+            } else {
+                const int32_t d = ~code;
+                const int64_t first = d >> 3, cnt = (d & 7) + 1;
+                if (first + cnt > h->T) return fail(SRP_EINVAL, "srp_bvh_set_nodes: leaf range out of range");
+            }
+        }
+    }
+    CU(cudaSetDevice(h->device), "cudaSetDevice");
+    CU(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    CU(cudaMemcpy(h->d_nodes, node_data, sizeof(float) * n_floats, cudaMemcpyHostToDevice), "H2D nodes");
+    c->last_tab.clear();  // force a fresh design-table upload
+    return SRP_OK;
+}
+
 int srp_bvh_destroy(srp_bvh* h) {
     if (!h) return SRP_OK;
     cudaSetDevice(h->device);

@@ -279,3 +279,33 @@ def test_bvh_info(srp, ctx):
     c, R = oracle.grid(m.verts)
     assert info["n_tris"] == m.T and info["width"] == 8 and info["n_leaves"] >= m.T / 4
     assert np.allclose(info["center"], c) and abs(info["radius"] - R) < 1e-12
+
+
+def test_corrupted_bvh_reports_device_limit(srp, ctx):
+    """Failure detection without a GPU fault: node data with out-of-range
+    indices is rejected on the host; an in-range cycle (a node that is its
+    own child) makes the traversal hit its stack-depth / visit bounds, which
+    end the ray and flag SRP_EDEVICE_LIMIT; the context stays usable."""
+    m, rho, sun, com = W.config1()
+    b = _bvh(srp, ctx, m)
+    nodes, order, nn = srp.srp_build_bvh_host(m.verts, m.tris, 4)
+    bad = nodes.copy().reshape(nn, 32)
+    ch = bad[:, 24:28].view(np.int32)
+    ch[0, 0] = nn + 5
+    with pytest.raises(srp.SRPError) as e:
+        srp.srp_bvh_set_nodes(ctx, b, bad)
+    assert e.value.code == srp.SRP_EINVAL
+    cyc = nodes.copy().reshape(nn, 32)
+    cyc[0, 0], cyc[0, 4 * 0 + 4] = -1e3, 1e3   # child 0 box: everything (lo_x, hi_x)
+    cyc[0, 8], cyc[0, 12] = -1e3, 1e3           # lo_y, hi_y
+    cyc[0, 16], cyc[0, 20] = -1e3, 1e3          # lo_z, hi_z
+    cyc[0, 24:28].view(np.int32)[0] = 0         # node 0 is its own child
+    srp.srp_bvh_set_nodes(ctx, b, cyc)
+    with pytest.raises(srp.SRPError) as e:
+        srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=32)
+    assert e.value.code == srp.SRP_EDEVICE_LIMIT
+    # restore and check the context still works
+    srp.srp_bvh_set_nodes(ctx, b, nodes)
+    ft = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=256, max_bounces=1)
+    fo, _ = oracle.force(m.verts, m.tris, m.group, rho, sun, com, nx=256, K=1)
+    _assert_parity(ft[0], fo, b.info()["radius"])
