@@ -120,7 +120,10 @@ __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& 
     tb = INFINITY;
     int ni = 0;
     int visits = 0;
-    const bool nx_ = r.inv.x < 0.0f, ny_ = r.inv.y < 0.0f, nz_ = r.inv.z < 0.0f;
+    // near/far slab planes chosen by load address (per-ray float4 offsets):
+    // lo_a at float4 (2a)*(W/4) + h, hi_a at (2a+1)*(W/4) + h
+    constexpr int Q = W / 4;
+    const int nxo = r.inv.x < 0.0f ? Q : 0, nyo = r.inv.y < 0.0f ? Q : 0, nzo = r.inv.z < 0.0f ? Q : 0;
     while (true) {
         if (++visits > kVisitCap) { atomicOr(err, kErrVisitCap); return -1; }
         ++nvis;
@@ -129,14 +132,11 @@ __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& 
         bool hit[W];
         int child[W];
 #pragma unroll
-        for (int h = 0; h < W / 4; ++h) {
-            const float4 lox = __ldg(nd + 0 * (W / 4) + h), hix = __ldg(nd + 1 * (W / 4) + h);
-            const float4 loy = __ldg(nd + 2 * (W / 4) + h), hiy = __ldg(nd + 3 * (W / 4) + h);
-            const float4 loz = __ldg(nd + 4 * (W / 4) + h), hiz = __ldg(nd + 5 * (W / 4) + h);
-            const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * (W / 4)) + h);
-            const float4 ax = nx_ ? hix : lox, bx = nx_ ? lox : hix;
-            const float4 ay = ny_ ? hiy : loy, by = ny_ ? loy : hiy;
-            const float4 az = nz_ ? hiz : loz, bz = nz_ ? loz : hiz;
+        for (int h = 0; h < Q; ++h) {
+            const float4 ax = __ldg(nd + nxo + h), bx = __ldg(nd + (Q - nxo) + h);
+            const float4 ay = __ldg(nd + 2 * Q + nyo + h), by = __ldg(nd + 2 * Q + (Q - nyo) + h);
+            const float4 az = __ldg(nd + 4 * Q + nzo + h), bz = __ldg(nd + 4 * Q + (Q - nzo) + h);
+            const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * Q) + h);
             const float ax_[4] = {ax.x, ax.y, ax.z, ax.w}, bx_[4] = {bx.x, bx.y, bx.z, bx.w};
             const float ay_[4] = {ay.x, ay.y, ay.z, ay.w}, by_[4] = {by.x, by.y, by.z, by.w};
             const float az_[4] = {az.x, az.y, az.z, az.w}, bz_[4] = {bz.x, bz.y, bz.z, bz.w};
