@@ -16,6 +16,12 @@ paper's definitions:
 * ``facet_law``        -- the per-plate closed form (box-wing model,
                           Sec. 2.1): sum over sunlit facets of
                           P A cos [(1-rs) d - (2 rs cos + 2/3 rd) n].
+* ``force_area``       -- the paper's own estimator without bounces
+                          (Sec. 3.2 "Estimation"): area-weighted surface
+                          samples, a shadow ray toward the sun per sample
+                          (next-event estimation), the per-plate expected
+                          reflection deposited where the sample is lit.
+* ``area_counts``      -- its sample allocation n_f = max(1, ceil(rho A_f)).
 * ``instantiate``      -- design instantiation: hinge rotations of the
                           panel vertices (Rodrigues' formula).
 * ``philox``           -- Philox4x32-10 (Salmon et al., SC'11).
@@ -74,6 +80,10 @@ def _load():
         lib.or_trace_rays.argtypes = [P, i32, P, P, i32, P, P, P, i32, i32, i32, i32, u64, f64,
                                       u32, u32, P, i64, P, P, i32]
         lib.or_trace_rays.restype = i32
+        lib.or_area_counts.argtypes = [P, i32, P, i32, C.c_float, P]
+        lib.or_area_counts.restype = i64
+        lib.or_force_area.argtypes = [P, i32, P, P, i32, P, P, i32, P, C.c_float, u64, f64, u32, u32, i32, P, P]
+        lib.or_force_area.restype = i32
         _lib = lib
     return _lib
 
@@ -187,6 +197,28 @@ def trace_rays(verts, tris, group, rho, sun, com, ray_idx, *, nx, ny=None, K=1, 
     if rc != 0:
         raise ValueError("oracle trace_rays: bad arguments")
     return y, h
+
+
+def area_counts(verts, tris, density):
+    """Samples per triangle of the area estimator: max(1, ceil(density*A)) in FP32."""
+    lib = _load()
+    v = _c(verts, np.float32); t = _c(tris, np.int32)
+    c = np.zeros(t.shape[0], np.int32)
+    lib.or_area_counts(_p(v), v.shape[0], _p(t), t.shape[0], float(density), _p(c))
+    return c
+
+
+def force_area(verts, tris, group, rho, sun, com, *, density, seed=0, P=1.0, sun_base=0, design_index=0,
+               threads=None):
+    """Area-sampling / next-event estimate of (F, tau) [S,6] and sigma [S,6]."""
+    lib = _load()
+    v = _c(verts, np.float32); t = _c(tris, np.int32); g = _c(group, np.int32)
+    r = _c(rho, np.float64); s = _c(np.atleast_2d(sun), np.float64); cm = _c(com, np.float64)
+    S = s.shape[0]
+    ft = np.zeros((S, 6)); sg = np.zeros((S, 6))
+    lib.or_force_area(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(s), S, _p(cm), float(density), seed,
+                      P, sun_base, design_index, threads or os.cpu_count() or 1, _p(ft), _p(sg))
+    return ft, sg
 
 
 def primary_hit(verts, tris, sun, i, *, nx, ny=None, jitter=1, seed=0, sun_index=0, design_index=0):

@@ -667,3 +667,161 @@ int or_trace_rays(const float* verts, int V, const int32_t* tris, const int32_t*
     free(jb); free(th); free(tv); free(tn);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Area-sampling estimator with next-event estimation (the paper's own  */
+/* estimator, Sec. 3.2 "Estimation", without bounces):                 */
+/*  - triangle f (original order) receives n_f = max(1, ceil(rho A_f))  */
+/*    samples, A_f and the product computed in FP32 with every         */
+/*    operation rounded (the integer count is a floating-point          */
+/*    decision: both sides take it in FP32);                           */
+/*  - sample j: Philox counter (j, f, sun, design | 2^31), uniform point */
+/*    on the triangle x = v0 + s(1-u2) e1 + s u2 e2, s = sqrt(u1)       */
+/*    (Osada, Funkhouser, Chazelle, Dobkin 2002);                       */
+/*  - facing normal n (n.e >= 0), cos = n.e; shadow ray from x toward   */
+/*    the sun (skip f, t > 1e-6 R): visible -> deposit                  */
+/*    (A_f / n_f) P cos [(1-rs) d - (2 rs cos + 2/3 rd) n], d = -e,      */
+/*    torque (x - COM) x deposit;                                       */
+/*  - sums in sample order k = prefix(f) + j; sigma: collapsed strata   */
+/*    over pairs (k = 2i, 2i+1).                                        */
+/* ------------------------------------------------------------------ */
+static float area32(const double* tv)
+{
+    float a0 = (float)tv[0], a1 = (float)tv[1], a2 = (float)tv[2];
+    float e1x = (float)tv[3] - a0, e1y = (float)tv[4] - a1, e1z = (float)tv[5] - a2;
+    float e2x = (float)tv[6] - a0, e2y = (float)tv[7] - a1, e2z = (float)tv[8] - a2;
+    float p, q;
+    p = e1y * e2z; q = e1z * e2y; float cx = p - q;
+    p = e1z * e2x; q = e1x * e2z; float cy = p - q;
+    p = e1x * e2y; q = e1y * e2x; float cz = p - q;
+    float s = cx * cx; s = s + cy * cy; s = s + cz * cz;
+    return 0.5f * sqrtf(s);
+}
+
+int64_t or_area_counts(const float* verts, int V, const int32_t* tris, int T, float density, int32_t* counts)
+{
+    double tv[9];
+    int64_t tot = 0;
+    for (int f = 0; f < T; ++f) {
+        for (int c = 0; c < 3; ++c)
+            for (int j = 0; j < 3; ++j) tv[3 * c + j] = verts[3 * tris[3 * f + c] + j];
+        float a = area32(tv);
+        float prod = density * a;
+        int32_t n = (int32_t)ceilf(prod);
+        if (n < 1) n = 1;
+        counts[f] = n;
+        tot += n;
+    }
+    (void)V;
+    return tot;
+}
+
+typedef struct {
+    const scene_t* sc;
+    const double* sun;
+    const int32_t* counts;
+    const int64_t* prefix;
+    int S;
+    uint32_t sun_base;
+    double* out;        /* [S][12] */
+    int s0, s1;
+} area_job;
+
+static void* area_worker(void* arg)
+{
+    area_job* jb = (area_job*)arg;
+    const scene_t* sc = jb->sc;
+    for (int s = jb->s0; s < jb->s1; ++s) {
+        const double* e = jb->sun + 3 * (size_t)s;
+        double d[3] = {-e[0], -e[1], -e[2]};
+        double acc[6] = {0}, sq[6] = {0}, pend[6] = {0};
+        int64_t k = 0;
+        for (int f = 0; f < sc->T; ++f) {
+            const double* v = sc->tv + 9 * (size_t)f;
+            double e1[3], e2[3];
+            for (int j = 0; j < 3; ++j) { e1[j] = v[3 + j] - v[j]; e2[j] = v[6 + j] - v[j]; }
+            double cr[3];
+            cross3(e1, e2, cr);
+            const double A = 0.5 * sqrt(dot3(cr, cr));
+            const double* ng = sc->tn + 3 * (size_t)f;
+            double n[3];
+            double sg = dot3(ng, e) < 0.0 ? -1.0 : 1.0;
+            for (int j = 0; j < 3; ++j) n[j] = sg * ng[j];
+            const double cs = dot3(n, e);
+            const double rs = sc->rho[2 * sc->group[f]], rd = sc->rho[2 * sc->group[f] + 1];
+            const int32_t nf = jb->counts[f];
+            const double wgt = sc->P * A / nf;
+            for (int32_t j = 0; j < nf; ++j, ++k) {
+                double u[4];
+                uint32_t ctr[4] = {(uint32_t)j, (uint32_t)f, jb->sun_base + (uint32_t)s, sc->dsg | 0x80000000u};
+                uint32_t key[2] = {(uint32_t)sc->seed, (uint32_t)(sc->seed >> 32)};
+                uint32_t o[4];
+                or_philox4x32_10(ctr, key, o);
+                for (int q = 0; q < 4; ++q) u[q] = u24(o[q]);
+                const double ss = sqrt(u[0]);
+                const double b1 = ss * (1.0 - u[1]), b2 = ss * u[1];
+                double x[3];
+                for (int q = 0; q < 3; ++q) x[q] = v[q] + b1 * e1[q] + b2 * e2[q];
+                double y[6] = {0, 0, 0, 0, 0, 0};
+                if (cs > 0.0) {
+                    wray r;
+                    wray_setup(&r, x, e);
+                    double t;
+                    const int hit = closest(sc, &r, 1e-6 * sc->R, f, &t);
+                    if (hit < 0) {
+                        const double cn = 2.0 * rs * cs + (2.0 / 3.0) * rd;
+                        double dp[3], arm[3], tq[3];
+                        for (int q = 0; q < 3; ++q) { dp[q] = wgt * cs * ((1.0 - rs) * d[q] - cn * n[q]); arm[q] = x[q] - sc->com[q]; }
+                        cross3(arm, dp, tq);
+                        for (int q = 0; q < 3; ++q) { y[q] = dp[q]; y[3 + q] = tq[q]; }
+                    }
+                }
+                for (int q = 0; q < 6; ++q) acc[q] += y[q];
+                if ((k & 1) == 0) {
+                    for (int q = 0; q < 6; ++q) pend[q] = y[q];
+                } else {
+                    for (int q = 0; q < 6; ++q) { double dd = y[q] - pend[q]; sq[q] += dd * dd; }
+                }
+            }
+        }
+        if (k & 1) for (int q = 0; q < 6; ++q) sq[q] += pend[q] * pend[q];
+        for (int q = 0; q < 6; ++q) { jb->out[12 * s + q] = acc[q]; jb->out[12 * s + 6 + q] = sq[q]; }
+    }
+    return NULL;
+}
+
+int or_force_area(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
+                  const double* rho, const double* sun, int S, const double* com, float density,
+                  uint64_t seed, double P, uint32_t sun_base, uint32_t dsg, int threads,
+                  double* out_ft, double* out_sigma)
+{
+    double* tv = (double*)malloc(sizeof(double) * 9 * (size_t)(T > 0 ? T : 1));
+    double* tn = (double*)malloc(sizeof(double) * 3 * (size_t)(T > 0 ? T : 1));
+    int32_t* counts = (int32_t*)malloc(sizeof(int32_t) * (size_t)(T > 0 ? T : 1));
+    scene_t sc;
+    memset(&sc, 0, sizeof sc);
+    build_scene(&sc, tv, tn, verts, V, tris, T);
+    sc.group = group; sc.rho = rho;
+    for (int j = 0; j < 3; ++j) sc.com[j] = com[j];
+    sc.P = P; sc.seed = seed; sc.dsg = dsg; sc.K = 1;
+    or_area_counts(verts, V, tris, T, density, counts);
+    double* out = (double*)calloc((size_t)S * 12 + 1, sizeof(double));
+    if (threads < 1) threads = 1;
+    if (threads > S) threads = S > 0 ? S : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * threads);
+    area_job* jb = (area_job*)calloc(threads, sizeof(area_job));
+    for (int t = 0; t < threads; ++t) {
+        jb[t].sc = &sc; jb[t].sun = sun; jb[t].counts = counts; jb[t].S = S; jb[t].sun_base = sun_base;
+        jb[t].out = out; jb[t].s0 = S * t / threads; jb[t].s1 = S * (t + 1) / threads;
+    }
+    for (int t = 1; t < threads; ++t) pthread_create(&th[t], NULL, area_worker, &jb[t]);
+    area_worker(&jb[0]);
+    for (int t = 1; t < threads; ++t) pthread_join(th[t], NULL);
+    for (int s = 0; s < S; ++s)
+        for (int q = 0; q < 6; ++q) {
+            out_ft[6 * s + q] = out[12 * s + q];
+            if (out_sigma) out_sigma[6 * s + q] = sqrt(out[12 * s + 6 + q]);
+        }
+    free(jb); free(th); free(out); free(counts); free(tv); free(tn);
+    return 0;
+}
