@@ -176,6 +176,33 @@ int srp_force(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho,
               const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
               double* out_ft, double* out_sigma);
 
+/* ---- the paper's own estimator without bounces (Sec. 3.2 "Estimation";
+ * the no-bounce variant "NB" of Table 3) ---------------------------------
+ * Same items, arrays, memory rules and outputs as srp_force, estimated by
+ * surface sampling with next-event estimation instead of a ray grid:
+ *   - triangle f (original order) receives n_f = max(1, ceil(density*A_f))
+ *     samples (A_f and the product in FP32, every operation rounded);
+ *   - sample j of triangle f is the uniform point of Philox4x32-10 counter
+ *     (j, f, sun_base + s, (design_base + d) | 2^31), key (seed lo, hi):
+ *     x = v0 + sqrt(u1)(1-u2) e1 + sqrt(u1) u2 e2 (u = top 24 bits / 2^24);
+ *   - with n the facet normal turned toward the sun and cos = n.e > 0, an
+ *     any-hit shadow ray from x along e (the source triangle skipped, hits
+ *     at t > 1e-6 R counted) decides whether x is lit; a lit sample adds
+ *     (A_f/n_f) P cos [(1-rs) d - (2 rs cos + 2/3 rd) n], d = -e, and its
+ *     torque (x - com) x F; every other sample adds zero;
+ *   - out_sigma: collapsed-strata standard errors over the sample pairs
+ *     (2i, 2i+1) of k = prefix(f) + j.
+ * opts: seed, pressure, mem, sun_per_design, sun_base, design_base and
+ * block_threads (0 or 128) are used; max_bounces must be 1
+ * (SRP_EUNSUPPORTED otherwise); the ray-grid fields are ignored.
+ * density: samples per unit area, finite and >= 0; a design's samples must
+ * stay below 2^31 (SRP_EINVAL when the planned bound exceeds it).
+ * out_samples [D] int64 (opts->mem, or NULL): samples per design.
+ * Uses the context's scratch like srp_force (no overlap across streams). */
+int srp_force_area(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                   const double* sun_dir, int S, const double* com, float density,
+                   const srp_trace_opts* opts, double* out_ft, double* out_sigma, int64_t* out_samples);
+
 /* ---- gradient (Sec. 4.1: the simulation is differentiable by construction
  * in continuous parameters such as reflectance; Sec. 3.4 design parameters)
  * For ONE design (bvh) and S sun directions, with upstream weights

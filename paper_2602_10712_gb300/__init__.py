@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
-           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_force_noalloc", "srp_force_grad", "SRPForce", "MLP",
+           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_force_noalloc", "srp_force_area", "srp_force_grad", "SRPForce", "MLP",
            "mlp_param_count", "srp_integrate", "orbit_opts", "OrbitOpts", "ForceGraph",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
@@ -73,6 +73,7 @@ def load(build_if_needed: bool = True):
     lib.srp_bvh_destroy.argtypes = [_P]
     lib.srp_bvh_get_info.argtypes = [_P, C.POINTER(BVHInfo)]
     lib.srp_force.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P]
+    lib.srp_force_area.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.c_float, C.POINTER(TraceOpts), _P, _P, _P]
     lib.srp_collect_stats.argtypes = [_P, i32, _P]
     lib.srp_bvh_set_nodes.argtypes = [_P, _P, _P, i64]
     lib.srp_force_grad.argtypes = [_P, _P, _P, i32, _P, i32, _P, _P, _P, i32, C.POINTER(TraceOpts), _P, _P, _P]
@@ -296,6 +297,60 @@ def srp_force(ctx: Context, bvhs, rho, sun_dir, com, out_ft=None, out_sigma=None
     _check(lib.srp_force(ctx.handle, arr, D, _ptr(rho), G, _ptr(sun_dir), S, _ptr(com), C.byref(o),
                          _ptr(out_ft), _ptr(out_sigma) if out_sigma is not None else None))
     return (out_ft, out_sigma) if out_sigma is not None else out_ft
+
+
+def srp_force_area(ctx: Context, bvhs, rho, sun_dir, com, density, out_ft=None, out_sigma=None, out_samples=None,
+                   **opts):
+    """The paper's no-bounce estimator (surface samples + next-event shadow
+    rays) of (F, tau) [D,S,6]; `density` is samples per unit area.  Same
+    array conventions as srp_force; out_samples=True also returns the
+    samples per design [D] (int64)."""
+    lib = load()
+    bvhs = list(bvhs)
+    D = len(bvhs)
+    arr = (_P * max(D, 1))(*[b.handle for b in bvhs])
+    device = not isinstance(rho, np.ndarray)
+    if device:
+        import torch
+        for name, x, dt in (("rho", rho, torch.float32), ("sun_dir", sun_dir, torch.float64),
+                            ("com", com, torch.float64)):
+            if not (x.is_cuda and x.dtype == dt and x.is_contiguous()):
+                raise TypeError(f"{name} must be a contiguous CUDA {dt} tensor")
+        S = sun_dir.shape[-2]
+        G = rho.shape[-2]
+        if out_ft is None:
+            out_ft = torch.empty((D, S, 6), dtype=torch.float64, device=rho.device)
+        if out_sigma is True:
+            out_sigma = torch.empty((D, S, 6), dtype=torch.float64, device=rho.device)
+        if out_samples is True:
+            out_samples = torch.empty((D,), dtype=torch.int64, device=rho.device)
+        opts.setdefault("mem", SRP_MEM_DEVICE)
+    else:
+        rho = _np(rho, np.float32)
+        sun_dir = _np(sun_dir, np.float64)
+        com = _np(com, np.float64)
+        S = sun_dir.shape[-2]
+        G = rho.shape[-2]
+        if out_ft is None:
+            out_ft = np.zeros((D, S, 6))
+        if out_sigma is True:
+            out_sigma = np.zeros((D, S, 6))
+        if out_samples is True:
+            out_samples = np.zeros(D, np.int64)
+        opts["mem"] = SRP_MEM_HOST
+    if opts.get("sun_per_design"):
+        if tuple(sun_dir.shape[:2]) != (D, S):
+            raise ValueError("sun_dir must be [D,S,3] with sun_per_design")
+    o = make_opts(**opts)
+    _check(lib.srp_force_area(ctx.handle, arr, D, _ptr(rho), G, _ptr(sun_dir), S, _ptr(com), float(density), C.byref(o),
+                              _ptr(out_ft), _ptr(out_sigma) if out_sigma is not None else None,
+                              _ptr(out_samples) if out_samples is not None else None))
+    res = [out_ft]
+    if out_sigma is not None:
+        res.append(out_sigma)
+    if out_samples is not None:
+        res.append(out_samples)
+    return res[0] if len(res) == 1 else tuple(res)
 
 
 def srp_trace_rays(ctx: Context, bvh: BVH, rho, sun_dir, com, ray_idx, sun_index=0, design_index=0, **opts):

@@ -20,6 +20,8 @@ cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* ou
 cudaError_t launch_trace_rays(const DesignDev& dz, const TraceParams& p, const int64_t* ray_idx, int64_t nr,
                               int sidx, int didx, double* out_y, int32_t* out_hits, cudaStream_t st);
 void set_last_error(const std::string& msg);
+int area_resident_blocks(int width);
+cudaError_t launch_area(const AreaParams& p, int width, int t_max, int grid_cap, cudaStream_t st);
 cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double* up, const int32_t* thinge,
                         const double* hax, int H, double* gpart, double* d_rho, double* d_hinge, int n_sm,
                         cudaStream_t st);
@@ -82,6 +84,8 @@ struct srp_ctx {
     cudaEvent_t tab_ev = nullptr;              // last table upload
     unsigned long long* d_queue = nullptr;     // work-queue counter
     DevBuf stage_in, stage_out;                // host-mem staging
+    DevBuf atab;                               // area estimator: cnt | map | ex (int32)
+    DevBuf axb;                                // area estimator: xbase | ntot (int64)
 };
 
 extern "C" {
@@ -135,6 +139,7 @@ int srp_ctx_destroy(srp_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     c->part.release(); c->gpart.release(); c->stage_in.release(); c->stage_out.release(); c->dtab.release();
+    c->atab.release(); c->axb.release();
     if (c->htab) cudaFreeHost(c->htab);
     if (c->tab_ev) cudaEventDestroy(c->tab_ev);
     if (c->d_queue) cudaFree(c->d_queue);
@@ -155,6 +160,8 @@ int srp_sync(srp_ctx* c) {
         std::string what;
         if (flag & kErrStackOverflow) what += " traversal stack overflow;";
         if (flag & kErrVisitCap) what += " node-visit cap reached (corrupt BVH?);";
+        if (flag & kErrAreaCount) what += " area-estimator sample count above its planned bound;";
+        if (flag & kErrTriIndex) what += " triangle index outside the mesh (corrupt triangle table?);";
         return fail(SRP_EDEVICE_LIMIT, "device limit:" + what);
     }
     return SRP_OK;
@@ -255,6 +262,17 @@ int srp_build_bvh(srp_ctx* c, const float* verts, int V, const int32_t* tris, co
     h->build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     for (int j = 0; j < 3; ++j) h->c[j] = cen[j];
     h->R = std::sqrt(R2);
+    h->area = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const float* a = verts + 3 * (size_t)tris[3 * t];
+        const float* b = verts + 3 * (size_t)tris[3 * t + 1];
+        const float* q = verts + 3 * (size_t)tris[3 * t + 2];
+        const double e1[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+        const double e2[3] = {(double)q[0] - a[0], (double)q[1] - a[1], (double)q[2] - a[2]};
+        const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                     cz = e1[0] * e2[1] - e1[1] * e2[0];
+        h->area += 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
     const size_t tb = tri.size() * sizeof(float), nb = b.node_data.size() * sizeof(float);
     h->bytes = (int64_t)(tb + nb);
     cudaError_t e = cudaMalloc(&h->d_tri, tb);
@@ -752,4 +770,129 @@ extern "C" int srp_graph_destroy(srp_graph* g) {
     if (g->dtab) cudaFree(g->dtab);
     delete g;
     return SRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// srp_force_area: surface sampling with next-event estimation (area.cu)
+// ---------------------------------------------------------------------------
+extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                              const double* sun_dir, int S, const double* com, float density,
+                              const srp_trace_opts* o, double* out_ft, double* out_sigma, int64_t* out_samples) {
+    if (!c || !o) return fail(SRP_EINVAL, "srp_force_area: NULL ctx/opts");
+    if (D < 0 || S < 0) return fail(SRP_EINVAL, "srp_force_area: negative D or S");
+    if (D > kMaxDesignsPerLaunch) return fail(SRP_EINVAL, "srp_force_area: too many designs in one call");
+    if (G < 1 || G > kMaxGroups) return fail(SRP_EINVAL, "srp_force_area: G must be in 1..64");
+    if (o->max_bounces != 1)
+        return fail(SRP_EUNSUPPORTED, "srp_force_area: only the no-bounce estimator (max_bounces = 1) is built");
+    if (!(density >= 0.0f) || !std::isfinite(density)) return fail(SRP_EINVAL, "srp_force_area: bad density");
+    if (!(o->pressure >= 0.0) || !std::isfinite(o->pressure)) return fail(SRP_EINVAL, "srp_force_area: bad pressure");
+    if (o->block_threads != 0 && o->block_threads != 128)
+        return fail(SRP_EINVAL, "srp_force_area: block_threads must be 0 or 128");
+    if (o->mem != SRP_MEM_HOST && o->mem != SRP_MEM_DEVICE)
+        return fail(SRP_EINVAL, "srp_force_area: mem must be SRP_MEM_HOST or SRP_MEM_DEVICE");
+    std::vector<DesignDev> designs(D);
+    std::vector<int64_t> xbase(D);
+    int w = 0, t_max = 0;
+    int64_t sum_x = 0, b_max = 0;
+    for (int d = 0; d < D; ++d) {
+        const srp_bvh* h = bvhs ? bvhs[d] : nullptr;
+        if (!h) return fail(SRP_EINVAL, "srp_force_area: NULL bvh");
+        if (h->device != c->device) return fail(SRP_EINVAL, "srp_force_area: bvh built on another device");
+        if (w == 0) w = h->width;
+        if (h->width != w) return fail(SRP_EUNSUPPORTED, "srp_force_area: all designs of one call need the same BVH width");
+        DesignDev& dz = designs[d];
+        dz.tri = (const float4*)h->d_tri; dz.nodes = (const float4*)h->d_nodes;
+        dz.cx = h->c[0]; dz.cy = h->c[1]; dz.cz = h->c[2]; dz.R = h->R;
+        dz.T = h->T; dz.width = h->width;
+        // bound on sum_f max(1, ceil(density * A_f)): FP32 areas and products
+        // differ from the FP64 total by a few ulps each
+        const double bnd = (double)h->T + std::ceil((double)density * h->area * (1.0 + 1e-5)) + 64.0;
+        if (!(bnd < 2147483647.0)) return fail(SRP_EINVAL, "srp_force_area: more than 2^31 samples for one design");
+        b_max = std::max<int64_t>(b_max, (int64_t)bnd);
+        xbase[d] = sum_x;
+        sum_x += (int64_t)h->T + 1;
+        t_max = std::max(t_max, h->T);
+    }
+    const int width = w ? w : 4;
+    const int64_t items = (int64_t)D * S;
+    if (items > 0 && (!rho || !sun_dir || !com || !out_ft))
+        return fail(SRP_EINVAL, "srp_force_area: NULL array argument");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    // units: chunks of a multiple of 1024 samples, at most 16M units of partials
+    const int64_t tile = 1024;
+    int64_t chunk = tile;
+    int64_t cpd = std::max<int64_t>(1, (b_max + chunk - 1) / chunk);
+    const int64_t max_units = 16777216;
+    if (items > 0 && items * cpd > max_units) {
+        const int64_t per_item = std::max<int64_t>(1, max_units / items);
+        chunk = (b_max + per_item - 1) / per_item;
+        chunk = std::max<int64_t>(tile, (chunk + tile - 1) / tile * tile);
+        cpd = std::max<int64_t>(1, (b_max + chunk - 1) / chunk);
+    }
+    const size_t tab_n = (size_t)std::max<int64_t>(sum_x, 1);
+    if (c->atab.ensure(3 * tab_n * sizeof(int32_t)) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_area: sample tables");
+    if (c->axb.ensure(2 * (size_t)std::max(D, 1) * sizeof(int64_t)) != cudaSuccess)
+        return fail(SRP_ENOMEM, "srp_force_area: sample tables");
+    const size_t part_bytes = sizeof(double) * 12 * (size_t)std::max<int64_t>(items * cpd, 1);
+    if (c->part.ensure(part_bytes) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_area: cannot allocate partials");
+    int rc = upload_designs(c, designs);
+    if (rc != SRP_OK) return rc;
+    int64_t* d_xb = (int64_t*)c->axb.p;
+    if (D > 0) CU(cudaMemcpyAsync(d_xb, xbase.data(), sizeof(int64_t) * D, cudaMemcpyHostToDevice, c->stream), "H2D xbase");
+    AreaParams p;
+    std::memset(&p, 0, sizeof p);
+    p.D = D; p.S = S; p.G = G; p.sun_per_design = o->sun_per_design ? 1 : 0;
+    p.seed = o->seed; p.P = (float)o->pressure; p.density = density;
+    p.sun_base = o->sun_base; p.design_base = o->design_base;
+    p.chunk = chunk; p.cpd = (int32_t)cpd; p.cap = cpd * chunk;
+    p.designs = (const DesignDev*)c->dtab.p;
+    p.xbase = d_xb; p.ntot = d_xb + std::max(D, 1);
+    p.cnt = (int32_t*)c->atab.p; p.map = p.cnt + tab_n; p.ex = p.map + tab_n;
+    p.part = (double*)c->part.p;
+    p.err = c->d_err;
+    p.stats = c->stats_on ? c->d_stats : nullptr;
+    p.queue = c->d_queue;
+    const int grid_cap = c->n_sm * area_resident_blocks(width);
+    const int64_t nsun = o->sun_per_design ? (int64_t)D * S : S;
+    double* d_ft = out_ft;
+    double* d_sg = out_sigma;
+    const size_t ob = sizeof(double) * 6 * (size_t)items;
+    if (o->mem == SRP_MEM_DEVICE) {
+        p.rho = rho; p.sun = sun_dir; p.com = com;
+    } else {
+        if (items > 0) {
+            rc = validate_values(rho, D, G, sun_dir, nsun);
+            if (rc != SRP_OK) return rc;
+        }
+        const size_t rb = sizeof(float) * 2 * (size_t)D * G, sb = sizeof(double) * 3 * (size_t)nsun,
+                     cb = sizeof(double) * 3 * (size_t)D;
+        const size_t rb_al = (rb + 255) / 256 * 256, sb_al = (sb + 255) / 256 * 256;
+        if (c->stage_in.ensure(rb_al + sb_al + cb + 256) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_area: staging");
+        const size_t ob_al = (ob + 255) / 256 * 256;
+        if (c->stage_out.ensure(2 * ob_al + 256) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_area: staging");
+        char* in = (char*)c->stage_in.p;
+        if (items > 0) {
+            CU(cudaMemcpyAsync(in, rho, rb, cudaMemcpyHostToDevice, c->stream), "H2D rho");
+            CU(cudaMemcpyAsync(in + rb_al, sun_dir, sb, cudaMemcpyHostToDevice, c->stream), "H2D sun");
+            CU(cudaMemcpyAsync(in + rb_al + sb_al, com, cb, cudaMemcpyHostToDevice, c->stream), "H2D com");
+        }
+        p.rho = (const float*)in; p.sun = (const double*)(in + rb_al); p.com = (const double*)(in + rb_al + sb_al);
+        d_ft = (double*)c->stage_out.p;
+        d_sg = out_sigma ? (double*)((char*)c->stage_out.p + ob_al) : nullptr;
+    }
+    CU(cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync(queue)");
+    CU(launch_area(p, width, t_max, grid_cap, c->stream), "area kernels launch");
+    if (items > 0) CU(launch_reduce(p.part, items, p.cpd, d_ft, d_sg, c->stream), "reduce kernel launch");
+    if (o->mem == SRP_MEM_DEVICE) {
+        if (out_samples && D > 0)
+            CU(cudaMemcpyAsync(out_samples, p.ntot, sizeof(int64_t) * D, cudaMemcpyDeviceToDevice, c->stream), "D2D samples");
+        return SRP_OK;
+    }
+    if (items > 0) {
+        CU(cudaMemcpyAsync(out_ft, d_ft, ob, cudaMemcpyDeviceToHost, c->stream), "D2H ft");
+        if (out_sigma) CU(cudaMemcpyAsync(out_sigma, d_sg, ob, cudaMemcpyDeviceToHost, c->stream), "D2H sigma");
+    }
+    if (out_samples && D > 0)
+        CU(cudaMemcpyAsync(out_samples, p.ntot, sizeof(int64_t) * D, cudaMemcpyDeviceToHost, c->stream), "D2H samples");
+    return srp_sync(c);
 }

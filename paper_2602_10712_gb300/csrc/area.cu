@@ -1,0 +1,262 @@
+// area.cu -- the paper's own estimator without bounces (Sec. 3.2
+// "Estimation", the "NB" variant of Table 3) for sm_103a.
+//
+// For every (design, sun) item: surface samples are spread over the
+// triangles by area (triangle f gets n_f = max(1, ceil(density * A_f))
+// samples, A_f and the product in FP32 with every operation rounded), a
+// sample is a uniform point on its triangle (Osada et al. 2002 square-root
+// mapping of two Philox4x32-10 uniforms), and next-event estimation toward
+// the sun decides whether it is lit: an any-hit shadow ray from the point
+// along e through the design's BVH.  A lit sample deposits the expected
+// momentum of the facet BRDF,
+//   (A_f / n_f) P cos [(1 - rs) d - (2 rs cos + 2/3 rd) n],   d = -e,
+// and its torque about the centre of mass.  Samples are numbered
+// k = prefix(f) + j in original triangle order; sigma is the collapsed-strata
+// estimate over the pairs (2i, 2i + 1).
+//
+// Kernels:
+//   area_prep_kernel   per (design, leaf slot): FP32 area, n_f, leaf map
+//   area_scan_kernel   per design: exclusive prefix of n_f (one block)
+//   area_kernel<W>     persistent warps over (item, chunk) units taken from
+//                      an atomic queue; a lane owns one sample at a time,
+//                      finds its triangle by binary search of the prefix,
+//                      draws the point and traces the shadow ray; per-lane
+//                      FP32 sums of 32 samples, FP32 warp tree, FP64 unit
+//                      sums -> partials
+// and the ray-grid tracer's reduce kernel sums the partials of each item.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "trace_common.cuh"
+
+namespace srp {
+
+
+constexpr int kAreaTile = 1024;   // samples per FP32 tile of a warp (32 per lane)
+
+// FP32 area of a triangle, every operation rounded (no contraction).
+__device__ __forceinline__ float tri_area_rn(float4 a, float4 b, float4 c) {
+    const float e1x = __fsub_rn(b.x, a.x), e1y = __fsub_rn(b.y, a.y), e1z = __fsub_rn(b.z, a.z);
+    const float e2x = __fsub_rn(c.x, a.x), e2y = __fsub_rn(c.y, a.y), e2z = __fsub_rn(c.z, a.z);
+    const float cx = __fsub_rn(__fmul_rn(e1y, e2z), __fmul_rn(e1z, e2y));
+    const float cy = __fsub_rn(__fmul_rn(e1z, e2x), __fmul_rn(e1x, e2z));
+    const float cz = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
+    float s = __fmul_rn(cx, cx);
+    s = __fadd_rn(s, __fmul_rn(cy, cy));
+    s = __fadd_rn(s, __fmul_rn(cz, cz));
+    return __fmul_rn(0.5f, __fsqrt_rn(s));
+}
+
+__global__ void __launch_bounds__(256) area_prep_kernel(const AreaParams p) {
+    const int d = blockIdx.y;
+    const DesignDev dz = p.designs[d];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= dz.T) return;
+    const float4 a = __ldg(dz.tri + 3 * (size_t)k), b = __ldg(dz.tri + 3 * (size_t)k + 1),
+                 c = __ldg(dz.tri + 3 * (size_t)k + 2);
+    const uint32_t f = __float_as_uint(a.w);
+    if (f >= (uint32_t)dz.T) { atomicOr(p.err, kErrTriIndex); return; }
+    const float prod = __fmul_rn(p.density, tri_area_rn(a, b, c));
+    int32_t n = 1;
+    if (prod > 1.0f) {
+        if (!(prod < 1.0e9f)) { atomicOr(p.err, kErrAreaCount); n = 1; }
+        else n = (int32_t)ceilf(prod);
+    }
+    const int64_t base = p.xbase[d];
+    p.cnt[base + f] = n;
+    p.map[base + f] = k;
+}
+
+// One block of 1024 threads per design: thread t scans a contiguous run of
+// triangles; a block-wide scan of the run totals gives each run's offset.
+__global__ void __launch_bounds__(1024) area_scan_kernel(const AreaParams p) {
+    __shared__ long long wsum[32];
+    const int d = blockIdx.x;
+    const int T = p.designs[d].T;
+    const int64_t base = p.xbase[d];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int run = (T + 1023) / 1024;
+    const int t0 = min(T, tid * run), t1 = min(T, t0 + run);
+    long long loc = 0;
+    for (int f = t0; f < t1; ++f) loc += p.cnt[base + f];
+    // inclusive warp scan, then scan of warp totals
+    long long v = loc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long o = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += o;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = wsum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long o = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += o;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    long long run_off = v - loc + (warp > 0 ? wsum[warp - 1] : 0);
+    const long long total = wsum[31];
+    const bool over = total > p.cap || total > 0x7fffffffLL;
+    for (int f = t0; f < t1; ++f) {
+        p.ex[base + f] = over ? 0 : (int32_t)run_off;
+        run_off += p.cnt[base + f];
+    }
+    if (tid == 0) {
+        p.ex[base + T] = over ? 0 : (int32_t)total;
+        p.ntot[d] = over ? 0 : total;
+        if (over) atomicOr(p.err, kErrAreaCount);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) area_kernel(const AreaParams p) {
+    __shared__ double dacc[4][12];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t units = (int64_t)p.D * p.S * p.cpd;
+    uint32_t nvis = 0, ntest = 0, nseg = 0;
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    while (true) {
+        unsigned long long uq = 0;
+        if (lane == 0) uq = atomicAdd(p.queue, 1ull);
+        const int64_t u = (int64_t)__shfl_sync(0xffffffffu, uq, 0);
+        if (u >= units) break;
+        const int64_t item = u / p.cpd;
+        const int64_t cidx = u % p.cpd;
+        const int dl = (int)(item / p.S), s = (int)(item % p.S);
+        const DesignDev dz = p.designs[dl];
+        const int64_t base = p.xbase[dl];
+        const int64_t N = p.ntot[dl];
+        const int64_t k0 = cidx * p.chunk;
+        const int64_t k1 = min(k0 + p.chunk, N);
+        if (lane < 12) dacc[warp][lane] = 0.0;
+        __syncwarp();
+        if (k0 < k1) {
+            const double* sp = p.sun + 3 * (size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s);
+            const float3 e = f3((float)sp[0], (float)sp[1], (float)sp[2]);
+            const double* cp = p.com + 3 * (size_t)dl;
+            const float3 com = f3((float)cp[0], (float)cp[1], (float)cp[2]);
+            const float* rho = p.rho + (size_t)dl * p.G * 2;
+            const float tmin = (float)(1e-6 * dz.R);
+            const uint32_t sg = (uint32_t)(p.sun_base + s), dg = (uint32_t)(p.design_base + dl) | 0x80000000u;
+            const int32_t* __restrict__ ex = p.ex + base;
+            const int T = dz.T;
+            for (int64_t ts = k0; ts < k1; ts += kAreaTile) {
+                float acc[6] = {0, 0, 0, 0, 0, 0}, sq[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 1
+                for (int j = 0; j < 32 && ts + 32 * j < k1; ++j) {
+                    const int64_t k = ts + 32 * j + lane;
+                    const bool valid = k < k1;
+                    float y[6] = {0, 0, 0, 0, 0, 0};
+                    if (valid) {
+                        // triangle of sample k: largest f with ex[f] <= k
+                        int lo = 0, hi = T;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if ((int64_t)__ldg(ex + mid) <= k) lo = mid; else hi = mid;
+                        }
+                        const int f = lo;
+                        const uint32_t jj = (uint32_t)(k - __ldg(ex + f));
+                        const int32_t nf = __ldg(p.cnt + base + f);
+                        const int L = __ldg(p.map + base + f);
+                        const float4 a = __ldg(dz.tri + 3 * (size_t)L), b = __ldg(dz.tri + 3 * (size_t)L + 1),
+                                     c = __ldg(dz.tri + 3 * (size_t)L + 2);
+                        const float3 e1 = xyz(b) - xyz(a), e2 = xyz(c) - xyz(a);
+                        float3 n = cross(e1, e2);
+                        const float len = sqrtf(dot(n, n));
+                        n = (1.0f / len) * n;
+                        float cs = dot(n, e);
+                        if (cs < 0.0f) { n = -1.0f * n; cs = -cs; }
+                        if (cs > 0.0f) {
+                            const uint4 rnd = philox4x32_10(make_uint4(jj, (uint32_t)f, sg, dg), key0, key1);
+                            const float u1 = unit24(rnd.x), u2 = unit24(rnd.y);
+                            const float sr = sqrtf(u1);
+                            const float b1 = sr * (1.0f - u2), b2 = sr * u2;
+                            const float3 x = f3(fmaf(b2, e2.x, fmaf(b1, e1.x, a.x)), fmaf(b2, e2.y, fmaf(b1, e1.y, a.y)),
+                                                fmaf(b2, e2.z, fmaf(b1, e1.z, a.z)));
+                            RaySetup r;
+                            setup_ray(r, x, e);
+                            ++nseg;
+                            if (!any_hit<W>(dz, r, tmin, L, p.err, nvis, ntest)) {
+                                const int g = (int)__float_as_uint(b.w);
+                                const float rs = __ldg(rho + 2 * g), rd = __ldg(rho + 2 * g + 1);
+                                const float wgt = p.P * (0.5f * len) / (float)nf;
+                                const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
+                                const float ws = wgt * cs, a1 = ws * (1.0f - rs), a2 = ws * cn;
+                                const float3 dp = f3(-a1 * e.x - a2 * n.x, -a1 * e.y - a2 * n.y, -a1 * e.z - a2 * n.z);
+                                const float3 tq = cross(x - com, dp);
+                                y[0] = dp.x; y[1] = dp.y; y[2] = dp.z; y[3] = tq.x; y[4] = tq.y; y[5] = tq.z;
+                            }
+                        }
+                    }
+                    const bool pvalid = __shfl_xor_sync(0xffffffffu, (int)valid, 1);
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const float yo = __shfl_xor_sync(0xffffffffu, y[q], 1);
+                        acc[q] += y[q];
+                        if ((lane & 1) == 0 && valid) {
+                            const float df = pvalid ? y[q] - yo : y[q];
+                            sq[q] = fmaf(df, df, sq[q]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    float a = acc[q], b = sq[q];
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        a += __shfl_xor_sync(0xffffffffu, a, off);
+                        b += __shfl_xor_sync(0xffffffffu, b, off);
+                    }
+                    if (lane == 0) { dacc[warp][q] += (double)a; dacc[warp][6 + q] += (double)b; }
+                }
+                __syncwarp();
+            }
+        }
+        if (lane < 12) p.part[(size_t)u * 12 + lane] = dacc[warp][lane];
+        __syncwarp();
+    }
+    if (p.stats) {
+        unsigned long long a = nvis, b = ntest, c = nseg;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, off);
+            b += __shfl_xor_sync(0xffffffffu, b, off);
+            c += __shfl_xor_sync(0xffffffffu, c, off);
+        }
+        if (lane == 0) { atomicAdd(p.stats, a); atomicAdd(p.stats + 1, b); atomicAdd(p.stats + 2, c); }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+int area_resident_blocks(int width) {
+    int nb = 0;
+    if (width == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, area_kernel<8>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, area_kernel<4>, 128, 0);
+    return nb > 0 ? nb : 1;
+}
+
+// Prep + scan (the sample tables), then the persistent sampling kernel.
+// p.queue must be zeroed on `st` before this call.
+cudaError_t launch_area(const AreaParams& p, int width, int t_max, int grid_cap, cudaStream_t st) {
+    if (p.D > 0 && t_max > 0) {
+        area_prep_kernel<<<dim3((unsigned)((t_max + 255) / 256), (unsigned)p.D), 256, 0, st>>>(p);
+        area_scan_kernel<<<(unsigned)p.D, 1024, 0, st>>>(p);
+    }
+    const int64_t units = (int64_t)p.D * p.S * p.cpd;
+    if (units == 0) return cudaGetLastError();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + 3) / 4, grid_cap));
+    if (width == 8) area_kernel<8><<<grid, 128, 0, st>>>(p);
+    else area_kernel<4><<<grid, 128, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace srp

@@ -32,6 +32,8 @@ constexpr int kVisitCap = 1 << 20;      // node visits per ray segment (corrupti
 // Error flags written by kernels (bitwise OR into one device word).
 constexpr int kErrStackOverflow = 1;
 constexpr int kErrVisitCap = 2;
+constexpr int kErrAreaCount = 8;        // area estimator: sample counts above the planned bound
+constexpr int kErrTriIndex = 16;        // triangle table holds an index outside 0..T-1
 
 struct BuiltBVH {                  // host result of the builder
     int width = 4;
@@ -73,6 +75,30 @@ struct TraceParams {
     int32_t variant;           // register budget: minimum resident blocks 4 or 5
 };
 
+// Parameters of the area-sampling estimator (area.cu).
+struct AreaParams {
+    int32_t D, S, G, sun_per_design;
+    uint64_t seed;
+    float P, density;
+    int32_t sun_base, design_base;
+    int64_t chunk;            // samples per unit (multiple of 1024)
+    int32_t cpd;              // units per item
+    int64_t cap;              // planned bound on the samples of one design (cpd * chunk)
+    const DesignDev* designs;
+    const int64_t* xbase;     // [D] first entry of design d in cnt/map/ex (T_d + 1 entries each)
+    int32_t* cnt;             // samples of original triangle f
+    int32_t* map;             // leaf slot of original triangle f
+    int32_t* ex;              // exclusive prefix of cnt (T_d + 1 entries)
+    int64_t* ntot;            // [D] samples of design d
+    const float* rho;
+    const double* sun;
+    const double* com;
+    double* part;             // [units][12]
+    int* err;
+    unsigned long long* stats;
+    unsigned long long* queue;
+};
+
 }  // namespace srp
 
 struct srp_bvh {
@@ -84,4 +110,5 @@ struct srp_bvh {
     void* d_tri;    // float4[T][3]
     void* d_nodes;  // node data
     int64_t bytes;
+    double area;    // total surface area (FP64, from the build's vertices)
 };

@@ -203,6 +203,93 @@ __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& 
 }
 
 // ---------------------------------------------------------------------------
+// Any hit through a W-wide BVH (shadow rays): true as soon as one triangle
+// other than `skip` is hit at t > tmin.  Same node layout and slab test as
+// closest_hit, no far-plane shrinking and no child ordering beyond taking
+// the nearest child next.
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ bool any_hit(const DesignDev& dz, const RaySetup& r, float tmin, int skip, int* err,
+                                        uint32_t& nvis, uint32_t& ntest) {
+    constexpr int NF4 = W == 4 ? 8 : 16;
+    constexpr int Q = W / 4;
+    const float4* __restrict__ nodes = dz.nodes;
+    const float4* __restrict__ tri = dz.tri;
+    int stack[kStackSize];
+    int sp = 0;
+    int ni = 0;
+    int visits = 0;
+    const int nxo = r.inv.x < 0.0f ? Q : 0, nyo = r.inv.y < 0.0f ? Q : 0, nzo = r.inv.z < 0.0f ? Q : 0;
+    while (true) {
+        if (++visits > kVisitCap) { atomicOr(err, kErrVisitCap); return false; }
+        ++nvis;
+        const float4* nd = nodes + (size_t)ni * NF4;
+        float tn[W];
+        bool hit[W];
+        int child[W];
+#pragma unroll
+        for (int h = 0; h < Q; ++h) {
+            const float4 ax = __ldg(nd + nxo + h), bx = __ldg(nd + (Q - nxo) + h);
+            const float4 ay = __ldg(nd + 2 * Q + nyo + h), by = __ldg(nd + 2 * Q + (Q - nyo) + h);
+            const float4 az = __ldg(nd + 4 * Q + nzo + h), bz = __ldg(nd + 4 * Q + (Q - nzo) + h);
+            const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * Q) + h);
+            const float ax_[4] = {ax.x, ax.y, ax.z, ax.w}, bx_[4] = {bx.x, bx.y, bx.z, bx.w};
+            const float ay_[4] = {ay.x, ay.y, ay.z, ay.w}, by_[4] = {by.x, by.y, by.z, by.w};
+            const float az_[4] = {az.x, az.y, az.z, az.w}, bz_[4] = {bz.x, bz.y, bz.z, bz.w};
+            const int ch_[4] = {ch.x, ch.y, ch.z, ch.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float n0 = fmaf(ax_[q], r.inv.x, -r.oinv.x), f0 = fmaf(bx_[q], r.inv.x, -r.oinv.x);
+                const float n1 = fmaf(ay_[q], r.inv.y, -r.oinv.y), f1 = fmaf(by_[q], r.inv.y, -r.oinv.y);
+                const float n2 = fmaf(az_[q], r.inv.z, -r.oinv.z), f2 = fmaf(bz_[q], r.inv.z, -r.oinv.z);
+                const float tnear = fmaxf(fmaxf(n0, n1), fmaxf(n2, tmin));
+                const float tfar = fminf(fminf(f0, f1), f2);
+                tn[4 * h + q] = tnear;
+                hit[4 * h + q] = tnear <= tfar;
+                child[4 * h + q] = ch_[q];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            if (hit[c] && child[c] < 0) {
+                const int code = ~child[c];
+                const int first = code >> 3, cnt = (code & 7) + 1;
+                ntest += cnt;
+                for (int q = 0; q < cnt; ++q) {
+                    const int f = first + q;
+                    if (f == skip) continue;
+                    const float4 a = __ldg(tri + 3 * (size_t)f);
+                    const float4 b = __ldg(tri + 3 * (size_t)f + 1);
+                    const float4 cc = __ldg(tri + 3 * (size_t)f + 2);
+                    if (hit_triangle(r, xyz(a), xyz(b), xyz(cc)) > tmin) return true;
+                }
+            }
+        }
+        int next = -1;
+        float tnext = INFINITY;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            if (hit[c] && child[c] >= 0) {
+                if (tn[c] < tnext) {
+                    if (next >= 0) {
+                        if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return false; }
+                        stack[sp++] = next;
+                    }
+                    next = child[c]; tnext = tn[c];
+                } else {
+                    if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return false; }
+                    stack[sp++] = child[c];
+                }
+            }
+        }
+        if (next >= 0) { ni = next; continue; }
+        if (sp == 0) break;
+        ni = stack[--sp];
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // A ray segment and the shading of its hit.
 // ---------------------------------------------------------------------------
 struct Seg {

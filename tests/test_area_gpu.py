@@ -1,0 +1,198 @@
+"""GPU parity of the area-sampling estimator (srp_force_area through the C
+ABI) against the FP64 oracle on the same Philox samples.
+
+Bar: sample counts are integers decided in FP32 on both sides and must match
+exactly; (F, tau) within 1e-5 relative (|F_gpu - F_or| <= 1e-5 |F_or|,
+|tau_gpu - tau_or| <= 1e-5 |F_or| R) -- a sample whose shadow ray grazes an
+occluder edge within FP32 rounding may be decided differently, which moves
+the sum by about 1/N; sigma within 1e-3 relative."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def srp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_10712_gb300 as srp
+    return srp
+
+
+@pytest.fixture(scope="module")
+def ctx(srp):
+    return srp.Context(0)
+
+
+def _parity(ft_gpu, ft_or, R, tol=1e-5, what=""):
+    ft_gpu = np.asarray(ft_gpu).reshape(-1, 6)
+    ft_or = np.asarray(ft_or).reshape(-1, 6)
+    for s in range(ft_or.shape[0]):
+        fn = np.linalg.norm(ft_or[s, :3])
+        if fn == 0.0:
+            assert np.all(np.abs(ft_gpu[s]) <= 1e-12), (what, s, ft_gpu[s])
+            continue
+        ef = np.linalg.norm(ft_gpu[s, :3] - ft_or[s, :3]) / fn
+        et = np.linalg.norm(ft_gpu[s, 3:] - ft_or[s, 3:]) / (fn * R)
+        assert ef <= tol and et <= tol, (what, s, ef, et, ft_gpu[s], ft_or[s])
+
+
+def _sigma_parity(sg_gpu, sg_or, tol=1e-3):
+    sg_gpu = np.asarray(sg_gpu).reshape(-1, 6)
+    sg_or = np.asarray(sg_or).reshape(-1, 6)
+    scale = np.maximum(sg_or.max(axis=1, keepdims=True), 1e-300)
+    assert np.all(np.abs(sg_gpu - sg_or) <= tol * scale), np.max(np.abs(sg_gpu - sg_or) / scale)
+
+
+def _small_satellite():
+    return W.procedural_satellite(dish_segments=64, dish_rings=20, n_boxes=60)
+
+
+@pytest.mark.parametrize("density", [0.0, 37.5, 2.0e4])
+def test_sample_counts_exact(srp, ctx, density):
+    """n_f = max(1, ceil(density A_f)) in FP32: totals equal the oracle's."""
+    for m in (W.box_wing(), _small_satellite()):
+        b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+        rho = W.random_reflectances(m.n_groups, seed=1)
+        _, n = srp.srp_force_area(ctx, [b], rho[None], W.SUN_C1[None], np.zeros((1, 3)), density, out_samples=True)
+        assert int(n[0]) == int(oracle.area_counts(m.verts, m.tris, density).astype(np.int64).sum())
+
+
+@pytest.mark.parametrize("width", [4, 8])
+def test_boxwing_parity(srp, ctx, width):
+    """Box-wing (16 triangles, self-shadowing panels), ~1M samples, 8 suns."""
+    m, rho, _, com = W.config1()
+    suns = W.fibonacci_directions(8)
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, width)
+    dens = 2.0e4
+    ft, sg = srp.srp_force_area(ctx, [b], rho[None], suns, com[None], dens, out_sigma=True, seed=11, pressure=4.56e-6)
+    fo, so = oracle.force_area(m.verts, m.tris, m.group, rho, suns, com, density=dens, seed=11, P=4.56e-6)
+    R = b.info()["radius"]
+    _parity(ft[0], fo, R, what=f"W{width}")
+    _sigma_parity(sg[0], so)
+
+
+def test_satellite_parity(srp, ctx):
+    """Procedural satellite (dish + boxes, ~5k triangles): many occluders."""
+    m = _small_satellite()
+    rho = W.random_reflectances(m.n_groups, seed=3)
+    suns = W.fibonacci_directions(6)
+    com = np.array([0.1, -0.2, 0.3])
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+    dens = 2000.0
+    ft, sg = srp.srp_force_area(ctx, [b], rho[None], suns, com[None], dens, out_sigma=True, seed=5)
+    fo, so = oracle.force_area(m.verts, m.tris, m.group, rho, suns, com, density=dens, seed=5)
+    _parity(ft[0], fo, b.info()["radius"], what="satellite")
+    _sigma_parity(sg[0], so)
+
+
+def test_full_satellite_one_sample_per_triangle(srp, ctx):
+    """The ~50k-triangle satellite at density 0 (one sample per triangle)."""
+    m, rho, _, com = W.config2(1)
+    suns = W.fibonacci_directions(3)
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+    ft = srp.srp_force_area(ctx, [b], rho[None], suns, com[None], 0.0, seed=2)
+    fo, _ = oracle.force_area(m.verts, m.tris, m.group, rho, suns, com, density=0.0, seed=2)
+    _parity(ft[0], fo, b.info()["radius"], tol=2e-5, what="config2 mesh")
+
+
+def test_multi_design_sun_per_design_parity(srp, ctx):
+    """Three hinge designs of the 7-group box-wing, own suns per design,
+    design_base and sun_base offsets in the counters; device-memory call."""
+    m = W.box_wing_7group()
+    angles = np.array([[0.0, 0.0], [0.4, -0.3], [-1.1, 0.9]])
+    D, S = 3, 4
+    rho = np.stack([W.random_reflectances(7, seed=20 + d) for d in range(D)])
+    suns = W.random_unit_vectors(D * S, seed=4).reshape(D, S, 3)
+    com = np.array([[0.0, 0.0, 0.0], [0.1, 0.0, -0.1], [0.0, 0.2, 0.0]])
+    verts = [srp.srp_design_instantiate(m.verts, m.vhinge, m.hinges, a) for a in angles]
+    bvhs = [srp.srp_build_bvh(ctx, v, m.tris, m.group, 4) for v in verts]
+    dev = torch.device("cuda", 0)
+    ft, sg, n = srp.srp_force_area(ctx, bvhs, torch.from_numpy(rho).to(dev), torch.from_numpy(suns).to(dev),
+                                   torch.from_numpy(com).to(dev), 5000.0, out_sigma=True, out_samples=True,
+                                   sun_per_design=1, design_base=7, sun_base=100, seed=9)
+    torch.cuda.synchronize()
+    ft = ft.cpu().numpy(); sg = sg.cpu().numpy(); n = n.cpu().numpy()
+    for d in range(D):
+        fo, so = oracle.force_area(verts[d], m.tris, m.group, rho[d], suns[d], com[d], density=5000.0, seed=9,
+                                   sun_base=100, design_index=7 + d)
+        _parity(ft[d], fo, bvhs[d].info()["radius"], what=f"design {d}")
+        _sigma_parity(sg[d], so)
+        assert n[d] == oracle.area_counts(verts[d], m.tris, 5000.0).sum()
+
+
+def test_agrees_with_ray_grid(srp, ctx):
+    """Both estimators target the same single-bounce integral: GPU area
+    estimate vs GPU ray grid (K = 1) on the satellite, 4 sigma."""
+    m = _small_satellite()
+    rho = W.random_reflectances(m.n_groups, seed=8)
+    suns = W.fibonacci_directions(5)
+    com = np.zeros(3)
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+    fa, sa = srp.srp_force_area(ctx, [b], rho[None], suns, com[None], 4.0e4, out_sigma=True, seed=1)
+    fg, sgg = srp.srp_force(ctx, [b], rho[None], suns, com[None], out_sigma=True, rays_x=2048, rays_y=2048,
+                            max_bounces=1, seed=1)
+    tol = 4.0 * np.sqrt(sa ** 2 + sgg ** 2) + 1e-12
+    assert np.all(np.abs(fa - fg) <= tol), np.max(np.abs(fa - fg) / tol)
+
+
+def test_convex_box_force_matches_facet_law(srp, ctx):
+    """Convex body: the force is point-independent, so the estimate equals the
+    per-facet closed form up to FP32 rounding of the deposits."""
+    bv, bt = W.axis_box((0.1, -0.2, 0.3), (0.5, 0.7, 1.1), 0)
+    verts = bv.astype(np.float32); tris = bt.astype(np.int32)
+    group = (np.arange(12) // 2).astype(np.int32)
+    rho = W.random_reflectances(6, seed=4)
+    suns = W.fibonacci_directions(16)
+    b = srp.srp_build_bvh(ctx, verts, tris, group, 4)
+    ft = srp.srp_force_area(ctx, [b], rho[None], suns, np.zeros((1, 3)), 3000.0, seed=3)
+    for s in range(16):
+        ref = oracle.facet_law(verts, tris, group, rho, suns[s], np.zeros(3))
+        assert np.linalg.norm(ft[0, s, :3] - ref[:3]) <= 1e-5 * np.linalg.norm(ref[:3])
+
+
+def test_edge_cases_and_errors(srp, ctx):
+    m, rho, sun, com = W.config1()
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+    # no suns: nothing to compute, counts still reported
+    ft, n = srp.srp_force_area(ctx, [b], rho[None], np.zeros((0, 3)), com[None], 10.0, out_samples=True)
+    assert ft.shape == (1, 0, 6) and n[0] == oracle.area_counts(m.verts, m.tris, 10.0).sum()
+    # no designs
+    ft = srp.srp_force_area(ctx, [], np.zeros((0, 64, 2), np.float32), sun, np.zeros((0, 3)), 10.0)
+    assert ft.shape == (0, 1, 6)
+    # zero pressure -> zero force
+    ft = srp.srp_force_area(ctx, [b], rho[None], sun, com[None], 100.0, pressure=0.0)
+    assert np.all(ft == 0.0)
+    with pytest.raises(srp.SRPError, match="SRP_EUNSUPPORTED"):
+        srp.srp_force_area(ctx, [b], rho[None], sun, com[None], 100.0, max_bounces=2)
+    with pytest.raises(srp.SRPError, match="SRP_EINVAL"):
+        srp.srp_force_area(ctx, [b], rho[None], sun, com[None], -1.0)
+    with pytest.raises(srp.SRPError, match="SRP_EINVAL"):
+        srp.srp_force_area(ctx, [b], rho[None], sun, com[None], float("nan"))
+    with pytest.raises(srp.SRPError, match="SRP_EINVAL"):
+        srp.srp_force_area(ctx, [b], rho[None], sun, com[None], 1.0e12)   # > 2^31 samples
+    # the context stays usable
+    ft = srp.srp_force_area(ctx, [b], rho[None], sun, com[None], 100.0)
+    assert np.all(np.isfinite(ft))
+
+
+def test_launch_configuration_independence(srp, ctx):
+    """A sun evaluated inside a 512-sun launch equals the same sun evaluated
+    alone (the sample set is the same; only the partial-sum grouping can
+    differ)."""
+    m = _small_satellite()
+    rho = W.random_reflectances(m.n_groups, seed=2)
+    suns = W.fibonacci_directions(512)
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+    dens = 1.0e4
+    ft = srp.srp_force_area(ctx, [b], rho[None], suns, np.zeros((1, 3)), dens, seed=4)
+    for s in (0, 77, 511):
+        one = srp.srp_force_area(ctx, [b], rho[None], suns[s:s + 1], np.zeros((1, 3)), dens, seed=4, sun_base=s)
+        scale = np.linalg.norm(one[0, 0, :3])
+        assert np.all(np.abs(ft[0, s] - one[0, 0]) <= 1e-9 * scale * np.array([1, 1, 1, 10, 10, 10]))
