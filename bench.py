@@ -296,6 +296,7 @@ def run_ours(args, ws, rank, local):
         "clocks": ck,
     }
     if rank == 0 and not args.no_extra:
+        line["area_estimator"] = area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, args.width)
         line["surrogate"], line["grad"] = extra_legs(srp, ctx, dev, peaks)
     if rank == 0 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
@@ -378,9 +379,100 @@ def extra_legs(srp, ctx, dev, peaks):
     return surrogate, grad
 
 
+def area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, width):
+    """The paper's own no-bounce estimator (srp_force_area) on the same
+    satellite and suns: density chosen so each sun gets about 2048^2 surface
+    samples (the ray grid's budget); samples/s, shadow-ray traversal work,
+    and the variance per unit time against the ray grid at K = 1."""
+    import torch
+    v = m.verts.astype(np.float64)
+    t = m.tris
+    area = 0.5 * np.linalg.norm(np.cross(v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 0]]), axis=1).sum()
+    dens = float(NX * NX) / area
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, width)
+    r_t = torch.from_numpy(rho[None].copy()).to(dev)
+    s_t = torch.from_numpy(sun.copy()).to(dev)
+    c_t = torch.from_numpy(com[None].copy()).to(dev)
+    S = s_t.shape[0]
+    ft = torch.empty((1, S, 6), dtype=torch.float64, device=dev)
+    sg = torch.empty((1, S, 6), dtype=torch.float64, device=dev)
+    ns = torch.empty((1,), dtype=torch.int64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        srp.srp_force_area(ctx, [b], r_t, s_t, c_t, dens, out_ft=ft, out_sigma=sg, out_samples=ns)
+    torch.cuda.synchronize()
+    n_per_sun = int(ns.cpu()[0])
+    reps = 3
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        srp.srp_force_area(ctx, [b], r_t, s_t, c_t, dens, out_ft=ft, out_sigma=sg, out_samples=ns)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = sum(ms) / reps / 1e3
+    # traversal counters on 64 of the suns (outside timing)
+    srp.srp_collect_stats(ctx, True)
+    sub = s_t[::S // 64].contiguous()
+    fa, sa = srp.srp_force_area(ctx, [b], r_t, sub, c_t, dens, out_sigma=True)
+    torch.cuda.synchronize()
+    vis, tests, segs = srp.srp_collect_stats(ctx, False)
+    # variance against the ray grid (K = 1) at the same budget: empirical
+    # variance over 8 seeds (the collapsed-strata sigma overstates the area
+    # estimator's, whose pairs straddle triangles), and time per call
+    seeds = 8
+    fa_s, fg_s = [], []
+    for sd in range(seeds):
+        fa_s.append(srp.srp_force_area(ctx, [b], r_t, sub, c_t, dens, seed=100 + sd).cpu().numpy()[0, :, :3])
+        fg_s.append(srp.srp_force(ctx, [b], r_t, sub, c_t, rays_x=NX, max_bounces=1, seed=100 + sd).cpu().numpy()[0, :, :3])
+    var_a = float(np.mean(np.sum(np.var(np.stack(fa_s), axis=0, ddof=1), axis=1)))
+    var_g = float(np.mean(np.sum(np.var(np.stack(fg_s), axis=0, ddof=1), axis=1)))
+    fg, sgg = srp.srp_force(ctx, [b], r_t, sub, c_t, out_sigma=True, rays_x=NX, max_bounces=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    srp.srp_force(ctx, [b], r_t, sub, c_t, out_sigma=True, rays_x=NX, max_bounces=1)
+    e1.record()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    srp.srp_force_area(ctx, [b], r_t, sub, c_t, dens, out_sigma=True)
+    e3.record()
+    torch.cuda.synchronize()
+    t_g, t_a = e0.elapsed_time(e1), e2.elapsed_time(e3)
+    sa_n = sa.cpu().numpy()[0, :, :3]; sg_n = sgg.cpu().numpy()[0, :, :3]
+    fa_n = fa.cpu().numpy()[0, :, :3]; fg_n = fg.cpu().numpy()[0, :, :3]
+    z = np.abs(fa_n - fg_n) / np.sqrt(sa_n ** 2 + sg_n ** 2 + 1e-300)
+    sig_over_emp_a = float(np.mean(np.sum(sa_n ** 2, axis=1))) / var_a
+    sig_over_emp_g = float(np.mean(np.sum(sg_n ** 2, axis=1))) / var_g
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    ops_node = 4 * 14 if width == 4 else 8 * 14
+    ops = (vis * ops_node + tests * 44) / max(segs, 1)
+    rate = n_per_sun * S / t
+    achieved = ops * rate / 1e12
+    peak_alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    b.close()
+    return {"samples_per_s": rate, "samples_per_sun": n_per_sun, "suns": S, "density_per_m2": dens,
+            "ms_per_call": t * 1e3, "shadow_rays_per_sample": segs / max(1, n_per_sun * sub.shape[0]),
+            "node_visits_per_shadow_ray": vis / max(segs, 1), "tri_tests_per_shadow_ray": tests / max(segs, 1),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                         "frac": achieved / peak_alu, "traffic": None,
+                         "note": f"area_kernel FP32 lane-ops {ops:.0f}/shadow ray (same per-visit/per-test counts as "
+                                 f"trace_kernel); peak = {n_sm} SM x 128 lanes x {sm_mhz:.0f} MHz"},
+            "vs_ray_grid_k1": {"var_ratio_grid_over_area": var_g / var_a, "time_ratio_grid_over_area": t_g / t_a,
+                               "efficiency_ratio": (var_g * t_g) / (var_a * t_a), "max_z": float(z.max()),
+                               "sigma2_over_empirical_var": {"area": sig_over_emp_a, "grid": sig_over_emp_g},
+                               "suns": int(sub.shape[0]), "seeds": seeds,
+                               "note": "same 2048^2 budget per sun; empirical variance of F over 8 seeds; "
+                                       "efficiency = (var x time)_grid / (var x time)_area, > 1 favours the area "
+                                       "estimator; max_z = largest |F_area - F_grid| / combined sigma"},
+            "gpu_launches_per_call": 4}
+
+
 def run_profile_case(case):
     """Small cases for ncu captures (3 calls each; capture the third):
     trace -- srp_force on 16 of the 4096 suns x 2048^2 rays, K <= 3;
+    area  -- srp_force_area on the same 16 suns, ~2048^2 samples each;
     mlp   -- proxy inference on 262,144 queries."""
     import torch
 
@@ -396,6 +488,18 @@ def run_profile_case(case):
         c_t = torch.from_numpy(com[None].copy()).to(dev)
         for _ in range(3):
             srp.srp_force(ctx, [b], r_t, s_t, c_t, rays_x=NX, max_bounces=K_BOUNCE)
+    elif case == "area":
+        m, rho, _, com = W.config2(16)
+        sun = W.fibonacci_directions(N_SUN)[::256].copy()
+        b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+        v = m.verts.astype(np.float64)
+        t = m.tris
+        area = 0.5 * np.linalg.norm(np.cross(v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 0]]), axis=1).sum()
+        r_t = torch.from_numpy(rho[None].copy()).to(dev)
+        s_t = torch.from_numpy(sun).to(dev)
+        c_t = torch.from_numpy(com[None].copy()).to(dev)
+        for _ in range(3):
+            srp.srp_force_area(ctx, [b], r_t, s_t, c_t, float(NX * NX) / area)
     elif case == "mlp":
         net = srp.MLP(ctx, seed=1)
         x = torch.randn((1 << 18, 19), device=dev)
@@ -415,7 +519,7 @@ def main():
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
-    ap.add_argument("--profile", choices=["trace", "mlp"], default=None,
+    ap.add_argument("--profile", choices=["trace", "area", "mlp"], default=None,
                     help="run a small ncu capture case and exit")
     args = ap.parse_args()
     if args.profile:

@@ -192,8 +192,10 @@ int srp_force(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho,
  *     torque (x - com) x F; every other sample adds zero;
  *   - out_sigma: collapsed-strata standard errors over the sample pairs
  *     (2i, 2i+1) of k = prefix(f) + j.
- * opts: seed, pressure, mem, sun_per_design, sun_base, design_base and
- * block_threads (0 or 128) are used; max_bounces must be 1
+ * opts: seed, pressure, mem, sun_per_design, sun_base, design_base,
+ * block_threads (0 or 128) and kernel_variant (0 = 8, or 4, 6, 8: the
+ * minimum resident 128-thread blocks per SM the sampling kernel is
+ * compiled for) are used; max_bounces must be 1
  * (SRP_EUNSUPPORTED otherwise); the ray-grid fields are ignored.
  * density: samples per unit area, finite and >= 0; a design's samples must
  * stay below 2^31 (SRP_EINVAL when the planned bound exceeds it).

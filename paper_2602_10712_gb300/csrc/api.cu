@@ -20,8 +20,8 @@ cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* ou
 cudaError_t launch_trace_rays(const DesignDev& dz, const TraceParams& p, const int64_t* ray_idx, int64_t nr,
                               int sidx, int didx, double* out_y, int32_t* out_hits, cudaStream_t st);
 void set_last_error(const std::string& msg);
-int area_resident_blocks(int width);
-cudaError_t launch_area(const AreaParams& p, int width, int t_max, int grid_cap, cudaStream_t st);
+int area_resident_blocks(int width, int variant);
+cudaError_t launch_area(const AreaParams& p, int width, int variant, int t_max, int grid_cap, cudaStream_t st);
 cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double* up, const int32_t* thinge,
                         const double* hax, int H, double* gpart, double* d_rho, double* d_hinge, int n_sm,
                         cudaStream_t st);
@@ -790,6 +790,9 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
         return fail(SRP_EINVAL, "srp_force_area: block_threads must be 0 or 128");
     if (o->mem != SRP_MEM_HOST && o->mem != SRP_MEM_DEVICE)
         return fail(SRP_EINVAL, "srp_force_area: mem must be SRP_MEM_HOST or SRP_MEM_DEVICE");
+    if (o->kernel_variant != 0 && o->kernel_variant != 4 && o->kernel_variant != 6 && o->kernel_variant != 8)
+        return fail(SRP_EINVAL, "srp_force_area: kernel_variant must be 0, 4, 6 or 8");
+    const int variant = o->kernel_variant ? o->kernel_variant : 8;
     std::vector<DesignDev> designs(D);
     std::vector<int64_t> xbase(D);
     int w = 0, t_max = 0;
@@ -852,7 +855,7 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
     p.err = c->d_err;
     p.stats = c->stats_on ? c->d_stats : nullptr;
     p.queue = c->d_queue;
-    const int grid_cap = c->n_sm * area_resident_blocks(width);
+    const int grid_cap = c->n_sm * area_resident_blocks(width, variant);
     const int64_t nsun = o->sun_per_design ? (int64_t)D * S : S;
     double* d_ft = out_ft;
     double* d_sg = out_sigma;
@@ -881,7 +884,7 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
         d_sg = out_sigma ? (double*)((char*)c->stage_out.p + ob_al) : nullptr;
     }
     CU(cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync(queue)");
-    CU(launch_area(p, width, t_max, grid_cap, c->stream), "area kernels launch");
+    CU(launch_area(p, width, variant, t_max, grid_cap, c->stream), "area kernels launch");
     if (items > 0) CU(launch_reduce(p.part, items, p.cpd, d_ft, d_sg, c->stream), "reduce kernel launch");
     if (o->mem == SRP_MEM_DEVICE) {
         if (out_samples && D > 0)

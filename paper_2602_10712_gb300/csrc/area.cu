@@ -115,9 +115,19 @@ __global__ void __launch_bounds__(1024) area_scan_kernel(const AreaParams p) {
     }
 }
 
-template <int W>
-__global__ void __launch_bounds__(128) area_kernel(const AreaParams p) {
+// Triangle of sample k: the largest f with ex[f] <= k (binary search).
+__device__ __forceinline__ int find_tri(const int32_t* __restrict__ ex, int lo, int hi, int32_t k) {
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(ex + mid) <= k) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int W, int MINB>
+__global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
     __shared__ double dacc[4][12];
+    __shared__ float lacc[4][12][32];   // per-lane FP32 sums of a tile (kept out of registers)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t units = (int64_t)p.D * p.S * p.cpd;
     uint32_t nvis = 0, ntest = 0, nseg = 0;
@@ -132,9 +142,9 @@ __global__ void __launch_bounds__(128) area_kernel(const AreaParams p) {
         const int dl = (int)(item / p.S), s = (int)(item % p.S);
         const DesignDev dz = p.designs[dl];
         const int64_t base = p.xbase[dl];
-        const int64_t N = p.ntot[dl];
-        const int64_t k0 = cidx * p.chunk;
-        const int64_t k1 = min(k0 + p.chunk, N);
+        const int32_t N = (int32_t)p.ntot[dl];
+        const int32_t k0 = (int32_t)min(cidx * p.chunk, (int64_t)N);
+        const int32_t k1 = (int32_t)min(cidx * p.chunk + p.chunk, (int64_t)N);
         if (lane < 12) dacc[warp][lane] = 0.0;
         __syncwarp();
         if (k0 < k1) {
@@ -146,25 +156,43 @@ __global__ void __launch_bounds__(128) area_kernel(const AreaParams p) {
             const float tmin = (float)(1e-6 * dz.R);
             const uint32_t sg = (uint32_t)(p.sun_base + s), dg = (uint32_t)(p.design_base + dl) | 0x80000000u;
             const int32_t* __restrict__ ex = p.ex + base;
+            const int32_t* __restrict__ map = p.map + base;
             const int T = dz.T;
-            for (int64_t ts = k0; ts < k1; ts += kAreaTile) {
-                float acc[6] = {0, 0, 0, 0, 0, 0}, sq[6] = {0, 0, 0, 0, 0, 0};
+            // triangle of the first sample of the current group of 32 (warp-uniform)
+            int f_base = find_tri(ex, 0, T, k0);
+            for (int32_t ts = k0; ts < k1; ts += kAreaTile) {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) lacc[warp][q][lane] = 0.0f;
 #pragma unroll 1
                 for (int j = 0; j < 32 && ts + 32 * j < k1; ++j) {
-                    const int64_t k = ts + 32 * j + lane;
+                    const int32_t k = ts + 32 * j + lane;
                     const bool valid = k < k1;
+                    // window of 33 prefix entries from f_base: lane i holds ex[f_base + i]
+                    const int fi = f_base + lane;
+                    const int32_t wl = fi <= T ? __ldg(ex + fi) : 0x7fffffff;
+                    const int32_t w32 = f_base + 32 <= T ? __ldg(ex + f_base + 32) : 0x7fffffff;
+                    const int32_t kk = valid ? k : k1 - 1;
+                    int lo = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int32_t wv = __shfl_sync(0xffffffffu, wl, lo + step);
+                        if (wv <= kk) lo += step;
+                    }
+                    const int32_t ex_f = __shfl_sync(0xffffffffu, wl, lo);
+                    const int32_t nxt = __shfl_sync(0xffffffffu, wl, min(lo + 1, 31));
+                    int f = f_base + lo;
+                    int32_t ex_lo = ex_f, ex_hi = lo == 31 ? w32 : nxt;
+                    if (kk >= ex_hi) {  // the group spans more than 32 triangles
+                        f = find_tri(ex, f_base + 32, T, kk);
+                        ex_lo = __ldg(ex + f);
+                        ex_hi = __ldg(ex + f + 1);
+                    }
+                    f_base = __shfl_sync(0xffffffffu, f, 31);
                     float y[6] = {0, 0, 0, 0, 0, 0};
                     if (valid) {
-                        // triangle of sample k: largest f with ex[f] <= k
-                        int lo = 0, hi = T;
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if ((int64_t)__ldg(ex + mid) <= k) lo = mid; else hi = mid;
-                        }
-                        const int f = lo;
-                        const uint32_t jj = (uint32_t)(k - __ldg(ex + f));
-                        const int32_t nf = __ldg(p.cnt + base + f);
-                        const int L = __ldg(p.map + base + f);
+                        const uint32_t jj = (uint32_t)(k - ex_lo);
+                        const int32_t nf = ex_hi - ex_lo;
+                        const int L = __ldg(map + f);
                         const float4 a = __ldg(dz.tri + 3 * (size_t)L), b = __ldg(dz.tri + 3 * (size_t)L + 1),
                                      c = __ldg(dz.tri + 3 * (size_t)L + 2);
                         const float3 e1 = xyz(b) - xyz(a), e2 = xyz(c) - xyz(a);
@@ -199,16 +227,16 @@ __global__ void __launch_bounds__(128) area_kernel(const AreaParams p) {
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
                         const float yo = __shfl_xor_sync(0xffffffffu, y[q], 1);
-                        acc[q] += y[q];
+                        lacc[warp][q][lane] += y[q];
                         if ((lane & 1) == 0 && valid) {
                             const float df = pvalid ? y[q] - yo : y[q];
-                            sq[q] = fmaf(df, df, sq[q]);
+                            lacc[warp][6 + q][lane] = fmaf(df, df, lacc[warp][6 + q][lane]);
                         }
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
-                    float a = acc[q], b = sq[q];
+                    float a = lacc[warp][q][lane], b = lacc[warp][6 + q][lane];
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) {
                         a += __shfl_xor_sync(0xffffffffu, a, off);
@@ -237,16 +265,30 @@ __global__ void __launch_bounds__(128) area_kernel(const AreaParams p) {
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-int area_resident_blocks(int width) {
+template <int W, int MINB>
+static int area_blocks_v() {
     int nb = 0;
-    if (width == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, area_kernel<8>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, area_kernel<4>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, area_kernel<W, MINB>, 128, 0);
     return nb > 0 ? nb : 1;
+}
+
+// Resident 128-thread blocks per SM of the variant (minimum blocks per SM
+// the kernel is compiled for: 4, 6 or 8).
+int area_resident_blocks(int width, int variant) {
+    if (width == 8) return variant == 4 ? area_blocks_v<8, 4>() : variant == 8 ? area_blocks_v<8, 8>() : area_blocks_v<8, 6>();
+    return variant == 4 ? area_blocks_v<4, 4>() : variant == 8 ? area_blocks_v<4, 8>() : area_blocks_v<4, 6>();
+}
+
+template <int W>
+static void area_launch_w(const AreaParams& p, int variant, int grid, cudaStream_t st) {
+    if (variant == 4) area_kernel<W, 4><<<grid, 128, 0, st>>>(p);
+    else if (variant == 8) area_kernel<W, 8><<<grid, 128, 0, st>>>(p);
+    else area_kernel<W, 6><<<grid, 128, 0, st>>>(p);
 }
 
 // Prep + scan (the sample tables), then the persistent sampling kernel.
 // p.queue must be zeroed on `st` before this call.
-cudaError_t launch_area(const AreaParams& p, int width, int t_max, int grid_cap, cudaStream_t st) {
+cudaError_t launch_area(const AreaParams& p, int width, int variant, int t_max, int grid_cap, cudaStream_t st) {
     if (p.D > 0 && t_max > 0) {
         area_prep_kernel<<<dim3((unsigned)((t_max + 255) / 256), (unsigned)p.D), 256, 0, st>>>(p);
         area_scan_kernel<<<(unsigned)p.D, 1024, 0, st>>>(p);
@@ -254,8 +296,8 @@ cudaError_t launch_area(const AreaParams& p, int width, int t_max, int grid_cap,
     const int64_t units = (int64_t)p.D * p.S * p.cpd;
     if (units == 0) return cudaGetLastError();
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + 3) / 4, grid_cap));
-    if (width == 8) area_kernel<8><<<grid, 128, 0, st>>>(p);
-    else area_kernel<4><<<grid, 128, 0, st>>>(p);
+    if (width == 8) area_launch_w<8>(p, variant, grid, st);
+    else area_launch_w<4>(p, variant, grid, st);
     return cudaGetLastError();
 }
 
