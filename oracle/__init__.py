@@ -22,6 +22,10 @@ paper's definitions:
                           (next-event estimation), the per-plate expected
                           reflection deposited where the sample is lit.
 * ``area_counts``      -- its sample allocation n_f = max(1, ceil(rho A_f)).
+* ``force_thermal``    -- local Lambertian thermal emitters (Sec. 5.9):
+                          expected 2/3 recoil at the emitting surface plus
+                          the closed-form deposit where emitted packets hit
+                          the spacecraft; ``thermal_counts`` its allocation.
 * ``instantiate``      -- design instantiation: hinge rotations of the
                           panel vertices (Rodrigues' formula).
 * ``philox``           -- Philox4x32-10 (Salmon et al., SC'11).
@@ -84,6 +88,10 @@ def _load():
         lib.or_area_counts.restype = i64
         lib.or_force_area.argtypes = [P, i32, P, P, i32, P, P, i32, P, C.c_float, u64, f64, u32, u32, i32, P, P]
         lib.or_force_area.restype = i32
+        lib.or_thermal_counts.argtypes = [P, i32, P, P, i32, P, C.c_float, P]
+        lib.or_thermal_counts.restype = i64
+        lib.or_force_thermal.argtypes = [P, i32, P, P, i32, P, P, P, C.c_float, u64, f64, u32, i32, P, P, P]
+        lib.or_force_thermal.restype = i32
         _lib = lib
     return _lib
 
@@ -219,6 +227,26 @@ def force_area(verts, tris, group, rho, sun, com, *, density, seed=0, P=1.0, sun
     lib.or_force_area(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(s), S, _p(cm), float(density), seed,
                       P, sun_base, design_index, threads or os.cpu_count() or 1, _p(ft), _p(sg))
     return ft, sg
+
+
+def thermal_counts(verts, tris, group, emit, density):
+    """Samples per triangle of the thermal estimator (0 where emit == 0)."""
+    lib = _load()
+    v = _c(verts, np.float32); t = _c(tris, np.int32); g = _c(group, np.int32); e = _c(emit, np.float32)
+    c = np.zeros(t.shape[0], np.int32)
+    lib.or_thermal_counts(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(e), float(density), _p(c))
+    return c
+
+
+def force_thermal(verts, tris, group, rho, emit, com, *, density, seed=0, P=1.0, design_index=0, threads=None):
+    """Thermal-emitter estimate of (F, tau) [6], sigma [6] and the sample count."""
+    lib = _load()
+    v = _c(verts, np.float32); t = _c(tris, np.int32); g = _c(group, np.int32)
+    r = _c(rho, np.float64); e = _c(emit, np.float32); cm = _c(com, np.float64)
+    ft = np.zeros(6); sg = np.zeros(6); n = np.zeros(1, np.int64)
+    lib.or_force_thermal(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(e), _p(cm), float(density), seed,
+                         P, design_index, threads or os.cpu_count() or 1, _p(ft), _p(sg), _p(n))
+    return ft, sg, int(n[0])
 
 
 def primary_hit(verts, tris, sun, i, *, nx, ny=None, jitter=1, seed=0, sun_index=0, design_index=0):

@@ -825,3 +825,156 @@ int or_force_area(const float* verts, int V, const int32_t* tris, const int32_t*
     free(jb); free(th); free(out); free(counts); free(tv); free(tn);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Local Lambertian thermal emitters (Sec. 5.9 "Design": heat from      */
+/* on-board compute radiated as a Lambertian source, recoil factor 2/3  */
+/* of a collimated beam):                                               */
+/*  - triangles of group g emit on the side of their winding normal     */
+/*    n_e = unit(e1 x e2) with momentum flux P * emit[g] per unit area  */
+/*    (emit in W/m^2 and P = 1/c gives newtons);                        */
+/*  - triangle f with emit > 0 receives n_f = max(1, ceil(rho A_f))     */
+/*    samples (FP32 as for the area estimator), others none;            */
+/*  - sample j: Philox counter (j, f, 0, design | 2^30); point from      */
+/*    (u0, u1) as in or_force_area; direction omega = unit(n_e + s),     */
+/*    s the uniform unit vector of (u2, u3) (cosine-distributed about    */
+/*    n_e); packet momentum w = P emit A_f / n_f;                       */
+/*  - recoil: the packet's expected recoil -(2/3) w n_e at x (the mean   */
+/*    of -w omega), torque (x - com) x recoil;                          */
+/*  - the packet's ray (skip f, t > 1e-6 R) deposits at its closest hit  */
+/*    y the closed form w[(1-rs) omega - (2 rs cos + 2/3 rd) n], n the   */
+/*    hit normal facing the ray, cos = -n.omega; torque (y - com) x it;  */
+/*  - sums in sample order k = prefix(f) + j; sigma: collapsed strata.   */
+/* ------------------------------------------------------------------ */
+int64_t or_thermal_counts(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
+                          const float* emit, float density, int32_t* counts)
+{
+    double tv[9];
+    int64_t tot = 0;
+    for (int f = 0; f < T; ++f) {
+        if (!(emit[group[f]] > 0.0f)) { counts[f] = 0; continue; }
+        for (int c = 0; c < 3; ++c)
+            for (int j = 0; j < 3; ++j) tv[3 * c + j] = verts[3 * tris[3 * f + c] + j];
+        float a = area32(tv);
+        float prod = density * a;
+        int32_t n = (int32_t)ceilf(prod);
+        if (n < 1) n = 1;
+        counts[f] = n;
+        tot += n;
+    }
+    (void)V;
+    return tot;
+}
+
+typedef struct {
+    const scene_t* sc;
+    const float* emit;
+    const int32_t* counts;
+    const int64_t* prefix;
+    double* y;          /* [N][6] */
+    int f0, f1;
+} thermal_job;
+
+static void* thermal_worker(void* arg)
+{
+    thermal_job* jb = (thermal_job*)arg;
+    const scene_t* sc = jb->sc;
+    for (int f = jb->f0; f < jb->f1; ++f) {
+        const int32_t nf = jb->counts[f];
+        if (nf == 0) continue;
+        const double* v = sc->tv + 9 * (size_t)f;
+        double e1[3], e2[3], cr[3];
+        for (int j = 0; j < 3; ++j) { e1[j] = v[3 + j] - v[j]; e2[j] = v[6 + j] - v[j]; }
+        cross3(e1, e2, cr);
+        const double A = 0.5 * sqrt(dot3(cr, cr));
+        const double* ne = sc->tn + 3 * (size_t)f;
+        const double w = sc->P * (double)jb->emit[sc->group[f]] * A / nf;
+        for (int32_t j = 0; j < nf; ++j) {
+            double* y = jb->y + 6 * (size_t)(jb->prefix[f] + j);
+            double u[4];
+            uint32_t ctr[4] = {(uint32_t)j, (uint32_t)f, 0u, sc->dsg | 0x40000000u};
+            uint32_t key[2] = {(uint32_t)sc->seed, (uint32_t)(sc->seed >> 32)};
+            uint32_t o[4];
+            or_philox4x32_10(ctr, key, o);
+            for (int q = 0; q < 4; ++q) u[q] = u24(o[q]);
+            const double ss = sqrt(u[0]);
+            const double b1 = ss * (1.0 - u[1]), b2 = ss * u[1];
+            double x[3], arm[3], rc[3], tq[3];
+            for (int q = 0; q < 3; ++q) x[q] = v[q] + b1 * e1[q] + b2 * e2[q];
+            for (int q = 0; q < 3; ++q) { rc[q] = -(2.0 / 3.0) * w * ne[q]; arm[q] = x[q] - sc->com[q]; }
+            cross3(arm, rc, tq);
+            for (int q = 0; q < 3; ++q) { y[q] = rc[q]; y[3 + q] = tq[q]; }
+            /* cosine-distributed direction: unit(n_e + uniform unit vector) */
+            double z = 1.0 - 2.0 * u[2], rr = sqrt(fmax(0.0, 1.0 - z * z)), phi = 2.0 * M_PI * u[3];
+            double om[3] = {ne[0] + rr * cos(phi), ne[1] + rr * sin(phi), ne[2] + z};
+            double L = sqrt(dot3(om, om));
+            if (!(L > 0.0)) continue;
+            for (int q = 0; q < 3; ++q) om[q] /= L;
+            wray r;
+            wray_setup(&r, x, om);
+            double t;
+            const int h = closest(sc, &r, 1e-6 * sc->R, f, &t);
+            if (h < 0) continue;
+            const double* nh = sc->tn + 3 * (size_t)h;
+            double n[3];
+            double sg = dot3(nh, om) > 0.0 ? -1.0 : 1.0;
+            for (int q = 0; q < 3; ++q) n[q] = sg * nh[q];
+            const double cs = -dot3(n, om);
+            const double rs = sc->rho[2 * sc->group[h]], rd = sc->rho[2 * sc->group[h] + 1];
+            const double cn = 2.0 * rs * cs + (2.0 / 3.0) * rd;
+            double yh[3], dp[3];
+            for (int q = 0; q < 3; ++q) {
+                yh[q] = x[q] + t * om[q];
+                dp[q] = w * ((1.0 - rs) * om[q] - cn * n[q]);
+                arm[q] = yh[q] - sc->com[q];
+            }
+            cross3(arm, dp, tq);
+            for (int q = 0; q < 3; ++q) { y[q] += dp[q]; y[3 + q] += tq[q]; }
+        }
+    }
+    return NULL;
+}
+
+int or_force_thermal(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
+                     const double* rho, const float* emit, const double* com, float density, uint64_t seed,
+                     double P, uint32_t dsg, int threads, double* out_ft, double* out_sigma, int64_t* out_n)
+{
+    double* tv = (double*)malloc(sizeof(double) * 9 * (size_t)(T > 0 ? T : 1));
+    double* tn = (double*)malloc(sizeof(double) * 3 * (size_t)(T > 0 ? T : 1));
+    int32_t* counts = (int32_t*)malloc(sizeof(int32_t) * (size_t)(T > 0 ? T : 1));
+    int64_t* prefix = (int64_t*)malloc(sizeof(int64_t) * (size_t)(T > 0 ? T : 1));
+    scene_t sc;
+    memset(&sc, 0, sizeof sc);
+    build_scene(&sc, tv, tn, verts, V, tris, T);
+    sc.group = group; sc.rho = rho;
+    for (int j = 0; j < 3; ++j) sc.com[j] = com[j];
+    sc.P = P; sc.seed = seed; sc.dsg = dsg; sc.K = 1;
+    const int64_t N = or_thermal_counts(verts, V, tris, group, T, emit, density, counts);
+    int64_t acc_n = 0;
+    for (int f = 0; f < T; ++f) { prefix[f] = acc_n; acc_n += counts[f]; }
+    double* y = (double*)calloc((size_t)(N > 0 ? N : 1) * 6, sizeof(double));
+    if (threads < 1) threads = 1;
+    if (threads > T) threads = T > 0 ? T : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * threads);
+    thermal_job* jb = (thermal_job*)calloc(threads, sizeof(thermal_job));
+    for (int t = 0; t < threads; ++t) {
+        jb[t].sc = &sc; jb[t].emit = emit; jb[t].counts = counts; jb[t].prefix = prefix; jb[t].y = y;
+        jb[t].f0 = (int)((int64_t)T * t / threads); jb[t].f1 = (int)((int64_t)T * (t + 1) / threads);
+    }
+    for (int t = 1; t < threads; ++t) pthread_create(&th[t], NULL, thermal_worker, &jb[t]);
+    thermal_worker(&jb[0]);
+    for (int t = 1; t < threads; ++t) pthread_join(th[t], NULL);
+    double acc[6] = {0}, sq[6] = {0};
+    for (int64_t k = 0; k < N; ++k) {
+        const double* yk = y + 6 * (size_t)k;
+        for (int q = 0; q < 6; ++q) acc[q] += yk[q];
+        if (k & 1) {
+            for (int q = 0; q < 6; ++q) { double dd = yk[q] - yk[q - 6]; sq[q] += dd * dd; }
+        }
+    }
+    if (N & 1) for (int q = 0; q < 6; ++q) sq[q] += y[6 * (size_t)(N - 1) + q] * y[6 * (size_t)(N - 1) + q];
+    for (int q = 0; q < 6; ++q) { out_ft[q] = acc[q]; if (out_sigma) out_sigma[q] = sqrt(sq[q]); }
+    if (out_n) *out_n = N;
+    free(jb); free(th); free(y); free(prefix); free(counts); free(tv); free(tn);
+    return 0;
+}

@@ -301,3 +301,88 @@ def test_area_estimator_matches_ray_grid():
     fg, sgg = oracle.force(m.verts, m.tris, m.group, rho, sun, com, nx=512, K=1, seed=2)
     ok, r = _stat_ok(fa[0], fg[0], sa[0], sgg[0])
     assert ok, r
+
+
+# ---------------------------------------------------------------- thermal emitters (Sec. 5.9)
+C_LIGHT = 299792458.0
+
+
+def _plate(size, z=0.0, flip=False):
+    m = W.flat_plate(size, 2)
+    v = m.verts.copy(); v[:, 2] += z
+    t = m.tris.copy()
+    if flip:
+        t = t[:, ::-1].copy()
+    return v.astype(np.float32), t.astype(np.int32)
+
+
+def test_thermal_worked_number():
+    """Sec. 5.9: 100 GPUs x 700 W = 70 kW from a Lambertian emitter recoil
+    with 2/3 of the collimated momentum flux: about 1.55e-4 N.  An isolated
+    plate (nothing to hit) emitting 70 kW from one side."""
+    v, t = _plate((2.0, 1.0))
+    emit = np.array([70e3 / 2.0], np.float32)            # W/m^2 over the 2 m^2 plate
+    ft, sg, n = oracle.force_thermal(v, t, np.zeros(2, np.int32), np.zeros((1, 2)), emit, np.zeros(3),
+                                     density=100.0, P=1.0 / C_LIGHT)
+    assert np.allclose(ft[:3], [0.0, 0.0, -(2.0 / 3.0) * 70e3 / C_LIGHT], rtol=1e-6, atol=1e-15)
+    assert abs(np.linalg.norm(ft[:3]) - 1.55e-4) < 0.01 * 1.55e-4    # the paper's rounded figure (c = 3e8 m/s)
+    assert n == 200
+
+
+def test_thermal_cube_cancels():
+    """All six faces of a closed cube emitting equally: the recoils cancel
+    and outward emission never hits the convex cube."""
+    bv, bt = W.axis_box((0.0, 0.0, 0.0), (0.5, 0.5, 0.5), 0)
+    ft, sg, n = oracle.force_thermal(bv.astype(np.float32), bt.astype(np.int32), np.zeros(12, np.int32),
+                                     np.array([[0.3, 0.2]]), np.array([1000.0], np.float32), np.zeros(3),
+                                     density=400.0, P=1.0 / C_LIGHT)
+    assert np.all(np.abs(ft[:3]) <= 1e-12 * 1000.0 / C_LIGHT * 6)
+    assert np.all(np.abs(ft[3:]) <= 4.0 * sg[3:] + 1e-18)
+    assert n == 12 * 200
+
+
+def test_thermal_enclosure_conserves_momentum():
+    """An emitter inside a closed absorbing box: every packet is absorbed
+    inside the body, so recoil and deposits cancel in expectation (4 sigma)
+    while each alone is large; an absorbing plate above an upward emitter is
+    pushed up and the net force stays between 0 and the free recoil."""
+    bv, bt = W.axis_box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 0)
+    box_t = bt[:, ::-1].astype(np.int32)                 # inward-facing walls (they do not emit)
+    pv, pt = _plate((0.5, 0.5), z=-0.5)
+    v = np.concatenate([bv, pv]).astype(np.float32)
+    t = np.concatenate([box_t, pt + 8]).astype(np.int32)
+    g = np.array([0] * 12 + [1] * 2, np.int32)
+    rho = np.zeros((2, 2))
+    emit = np.array([0.0, 500.0], np.float32)
+    ft, sg, n = oracle.force_thermal(v, t, g, rho, emit, np.zeros(3), density=40000.0, P=1.0 / C_LIGHT, seed=3)
+    free = (2.0 / 3.0) * 500.0 * 0.25 / C_LIGHT
+    assert n == 2 * 5000
+    assert np.all(np.abs(ft[:3]) <= 4.0 * sg[:3] + 1e-20)
+    assert np.linalg.norm(ft[:3]) < 0.02 * free
+    # plate over the emitter: partial absorption
+    tv, tt = _plate((2.0, 2.0), z=0.5)
+    v2 = np.concatenate([pv, tv]).astype(np.float32)
+    t2 = np.concatenate([pt, tt + 4]).astype(np.int32)
+    ft2, sg2, _ = oracle.force_thermal(v2, t2, np.array([1, 1, 0, 0], np.int32), rho, emit, np.zeros(3),
+                                       density=40000.0, P=1.0 / C_LIGHT, seed=4)
+    assert -free < ft2[2] < 0.0 and ft2[2] > -free + 10 * sg2[2]
+
+
+@pytest.mark.parametrize("rho_hit", [(1.0, 0.0), (0.0, 1.0), (0.0, 0.0)])
+def test_thermal_reflector_push(rho_hit):
+    """A large plate close above a small upward emitter catches almost every
+    packet.  A perfect mirror (rho_s = 1) takes 2 cos w along its normal,
+    a perfect Lambertian reflector (rho_d = 1) takes w omega + 2/3 w n; with
+    E[cos] = 2/3 and E[omega] = 2/3 n both give 4/3 w and the net is
+    -2/3 + 4/3 = +2/3 of the free recoil; an absorber takes 2/3 w: net 0."""
+    pv, pt = _plate((0.2, 0.2))
+    mv, mt = _plate((40.0, 40.0), z=0.05)
+    v = np.concatenate([pv, mv]).astype(np.float32)
+    t = np.concatenate([pt, mt + 4]).astype(np.int32)
+    g = np.array([0, 0, 1, 1], np.int32)
+    rho = np.array([[0.0, 0.0], list(rho_hit)])
+    ft, sg, _ = oracle.force_thermal(v, t, g, rho, np.array([1.0, 0.0], np.float32), np.zeros(3),
+                                     density=2.0e5, P=1.0, seed=5)
+    free = (2.0 / 3.0) * 0.04
+    want = 0.0 if rho_hit == (0.0, 0.0) else free
+    assert abs(ft[2] - want) < 0.01 * free + 4 * sg[2]
