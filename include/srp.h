@@ -205,6 +205,31 @@ int srp_force_area(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float*
                    const double* sun_dir, int S, const double* com, float density,
                    const srp_trace_opts* opts, double* out_ft, double* out_sigma, int64_t* out_samples);
 
+/* ---- local Lambertian thermal emitters (Sec. 5.9 "Design": heat of
+ * on-board compute radiated from the spacecraft's faces) ------------------
+ * For D designs (one item each, no sun):
+ *   emit [D][G] float32   emitted flux per unit area of the triangles of each
+ *                         group (>= 0; e.g. W/m^2 with opts->pressure = 1/c
+ *                         gives newtons); a triangle emits on the side of
+ *                         its winding normal n_e = unit((v1-v0) x (v2-v0))
+ *   rho, com, bvhs, opts->mem, out_sigma, out_samples as srp_force_area;
+ *   out_ft [D][6] float64 (F, tau) of the emission and of its absorption and
+ *                         reflection by the spacecraft itself.
+ * Emitting triangles (emit > 0) receive n_f = max(1, ceil(density*A_f))
+ * samples (FP32 as in srp_force_area), others none.  Sample j of triangle
+ * f: Philox4x32-10 counter (j, f, 0, (design_base + d) | 2^30); point x
+ * from (u0, u1) as in srp_force_area; packet w = pressure * emit * A_f / n_f;
+ * recoil -(2/3) w n_e at x (the expected recoil of a Lambertian emitter);
+ * direction omega = unit(n_e + s), s the uniform unit vector
+ * z = 1 - 2 u2, phi = 2 pi u3 (cosine-distributed about n_e); the closest
+ * hit of x + t omega (source triangle skipped, t > 1e-6 R) receives
+ * w [(1-rs) omega - (2 rs cos + 2/3 rd) n] (n the hit normal facing the
+ * ray, cos = -n.omega) and its torque.  Same validation and errors as
+ * srp_force_area; emit values are validated for host-mem calls. */
+int srp_force_thermal(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                      const float* emit, const double* com, float density, const srp_trace_opts* opts,
+                      double* out_ft, double* out_sigma, int64_t* out_samples);
+
 /* ---- gradient (Sec. 4.1: the simulation is differentiable by construction
  * in continuous parameters such as reflectance; Sec. 3.4 design parameters)
  * For ONE design (bvh) and S sun directions, with upstream weights

@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
-           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_force_noalloc", "srp_force_area", "srp_force_grad", "SRPForce", "MLP",
+           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_force_noalloc", "srp_force_area", "srp_force_thermal", "srp_force_grad", "SRPForce", "MLP",
            "mlp_param_count", "srp_integrate", "orbit_opts", "OrbitOpts", "ForceGraph",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
@@ -74,6 +74,7 @@ def load(build_if_needed: bool = True):
     lib.srp_bvh_get_info.argtypes = [_P, C.POINTER(BVHInfo)]
     lib.srp_force.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P]
     lib.srp_force_area.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.c_float, C.POINTER(TraceOpts), _P, _P, _P]
+    lib.srp_force_thermal.argtypes = [_P, _P, i32, _P, i32, _P, _P, C.c_float, C.POINTER(TraceOpts), _P, _P, _P]
     lib.srp_collect_stats.argtypes = [_P, i32, _P]
     lib.srp_bvh_set_nodes.argtypes = [_P, _P, _P, i64]
     lib.srp_force_grad.argtypes = [_P, _P, _P, i32, _P, i32, _P, _P, _P, i32, C.POINTER(TraceOpts), _P, _P, _P]
@@ -345,6 +346,55 @@ def srp_force_area(ctx: Context, bvhs, rho, sun_dir, com, density, out_ft=None, 
     _check(lib.srp_force_area(ctx.handle, arr, D, _ptr(rho), G, _ptr(sun_dir), S, _ptr(com), float(density), C.byref(o),
                               _ptr(out_ft), _ptr(out_sigma) if out_sigma is not None else None,
                               _ptr(out_samples) if out_samples is not None else None))
+    res = [out_ft]
+    if out_sigma is not None:
+        res.append(out_sigma)
+    if out_samples is not None:
+        res.append(out_samples)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def srp_force_thermal(ctx: Context, bvhs, rho, emit, com, density, out_ft=None, out_sigma=None, out_samples=None,
+                      **opts):
+    """Force and torque [D,6] of local Lambertian thermal emitters: emit
+    [D,G] flux per unit area per group (times opts pressure, e.g. 1/c for
+    W/m^2).  Array conventions as srp_force_area."""
+    lib = load()
+    bvhs = list(bvhs)
+    D = len(bvhs)
+    arr = (_P * max(D, 1))(*[b.handle for b in bvhs])
+    device = not isinstance(rho, np.ndarray)
+    if device:
+        import torch
+        for name, x, dt in (("rho", rho, torch.float32), ("emit", emit, torch.float32), ("com", com, torch.float64)):
+            if not (x.is_cuda and x.dtype == dt and x.is_contiguous()):
+                raise TypeError(f"{name} must be a contiguous CUDA {dt} tensor")
+        G = rho.shape[-2]
+        if out_ft is None:
+            out_ft = torch.empty((D, 6), dtype=torch.float64, device=rho.device)
+        if out_sigma is True:
+            out_sigma = torch.empty((D, 6), dtype=torch.float64, device=rho.device)
+        if out_samples is True:
+            out_samples = torch.empty((D,), dtype=torch.int64, device=rho.device)
+        opts.setdefault("mem", SRP_MEM_DEVICE)
+    else:
+        rho = _np(rho, np.float32)
+        emit = _np(emit, np.float32)
+        com = _np(com, np.float64)
+        G = rho.shape[-2]
+        if emit.shape[-1] != G:
+            raise ValueError("emit must be [D,G] with the G of rho")
+        if out_ft is None:
+            out_ft = np.zeros((D, 6))
+        if out_sigma is True:
+            out_sigma = np.zeros((D, 6))
+        if out_samples is True:
+            out_samples = np.zeros(D, np.int64)
+        opts["mem"] = SRP_MEM_HOST
+    o = make_opts(**opts)
+    _check(lib.srp_force_thermal(ctx.handle, arr, D, _ptr(rho), G, _ptr(emit), _ptr(com), float(density), C.byref(o),
+                                 _ptr(out_ft), _ptr(out_sigma) if out_sigma is not None else None,
+                                 _ptr(out_samples) if out_samples is not None else None))
     res = [out_ft]
     if out_sigma is not None:
         res.append(out_sigma)

@@ -775,23 +775,27 @@ extern "C" int srp_graph_destroy(srp_graph* g) {
 // ---------------------------------------------------------------------------
 // srp_force_area: surface sampling with next-event estimation (area.cu)
 // ---------------------------------------------------------------------------
-extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, const float* rho, int G,
-                              const double* sun_dir, int S, const double* com, float density,
-                              const srp_trace_opts* o, double* out_ft, double* out_sigma, int64_t* out_samples) {
-    if (!c || !o) return fail(SRP_EINVAL, "srp_force_area: NULL ctx/opts");
-    if (D < 0 || S < 0) return fail(SRP_EINVAL, "srp_force_area: negative D or S");
-    if (D > kMaxDesignsPerLaunch) return fail(SRP_EINVAL, "srp_force_area: too many designs in one call");
-    if (G < 1 || G > kMaxGroups) return fail(SRP_EINVAL, "srp_force_area: G must be in 1..64");
+namespace {
+// Shared host side of srp_force_area (mode 0) and srp_force_thermal (mode 1;
+// S = 1, no sun directions, emit [D][G]).
+int area_common(srp_ctx* c, int mode, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                const double* sun_dir, int S, const double* com, const float* emit, float density,
+                const srp_trace_opts* o, double* out_ft, double* out_sigma, int64_t* out_samples) {
+    const std::string fn = mode == 1 ? "srp_force_thermal" : "srp_force_area";
+    if (!c || !o) return fail(SRP_EINVAL, fn + ": NULL ctx/opts");
+    if (D < 0 || S < 0) return fail(SRP_EINVAL, fn + ": negative D or S");
+    if (D > kMaxDesignsPerLaunch) return fail(SRP_EINVAL, fn + ": too many designs in one call");
+    if (G < 1 || G > kMaxGroups) return fail(SRP_EINVAL, fn + ": G must be in 1..64");
     if (o->max_bounces != 1)
-        return fail(SRP_EUNSUPPORTED, "srp_force_area: only the no-bounce estimator (max_bounces = 1) is built");
-    if (!(density >= 0.0f) || !std::isfinite(density)) return fail(SRP_EINVAL, "srp_force_area: bad density");
-    if (!(o->pressure >= 0.0) || !std::isfinite(o->pressure)) return fail(SRP_EINVAL, "srp_force_area: bad pressure");
+        return fail(SRP_EUNSUPPORTED, fn + ": only the no-bounce estimator (max_bounces = 1) is built");
+    if (!(density >= 0.0f) || !std::isfinite(density)) return fail(SRP_EINVAL, fn + ": bad density");
+    if (!(o->pressure >= 0.0) || !std::isfinite(o->pressure)) return fail(SRP_EINVAL, fn + ": bad pressure");
     if (o->block_threads != 0 && o->block_threads != 128)
-        return fail(SRP_EINVAL, "srp_force_area: block_threads must be 0 or 128");
+        return fail(SRP_EINVAL, fn + ": block_threads must be 0 or 128");
     if (o->mem != SRP_MEM_HOST && o->mem != SRP_MEM_DEVICE)
-        return fail(SRP_EINVAL, "srp_force_area: mem must be SRP_MEM_HOST or SRP_MEM_DEVICE");
+        return fail(SRP_EINVAL, fn + ": mem must be SRP_MEM_HOST or SRP_MEM_DEVICE");
     if (o->kernel_variant != 0 && o->kernel_variant != 4 && o->kernel_variant != 6 && o->kernel_variant != 8)
-        return fail(SRP_EINVAL, "srp_force_area: kernel_variant must be 0, 4, 6 or 8");
+        return fail(SRP_EINVAL, fn + ": kernel_variant must be 0, 4, 6 or 8");
     const int variant = o->kernel_variant ? o->kernel_variant : 8;
     std::vector<DesignDev> designs(D);
     std::vector<int64_t> xbase(D);
@@ -799,10 +803,10 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
     int64_t sum_x = 0, b_max = 0;
     for (int d = 0; d < D; ++d) {
         const srp_bvh* h = bvhs ? bvhs[d] : nullptr;
-        if (!h) return fail(SRP_EINVAL, "srp_force_area: NULL bvh");
-        if (h->device != c->device) return fail(SRP_EINVAL, "srp_force_area: bvh built on another device");
+        if (!h) return fail(SRP_EINVAL, fn + ": NULL bvh");
+        if (h->device != c->device) return fail(SRP_EINVAL, fn + ": bvh built on another device");
         if (w == 0) w = h->width;
-        if (h->width != w) return fail(SRP_EUNSUPPORTED, "srp_force_area: all designs of one call need the same BVH width");
+        if (h->width != w) return fail(SRP_EUNSUPPORTED, fn + ": all designs of one call need the same BVH width");
         DesignDev& dz = designs[d];
         dz.tri = (const float4*)h->d_tri; dz.nodes = (const float4*)h->d_nodes;
         dz.cx = h->c[0]; dz.cy = h->c[1]; dz.cz = h->c[2]; dz.R = h->R;
@@ -810,7 +814,7 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
         // bound on sum_f max(1, ceil(density * A_f)): FP32 areas and products
         // differ from the FP64 total by a few ulps each
         const double bnd = (double)h->T + std::ceil((double)density * h->area * (1.0 + 1e-5)) + 64.0;
-        if (!(bnd < 2147483647.0)) return fail(SRP_EINVAL, "srp_force_area: more than 2^31 samples for one design");
+        if (!(bnd < 2147483647.0)) return fail(SRP_EINVAL, fn + ": more than 2^31 samples for one design");
         b_max = std::max<int64_t>(b_max, (int64_t)bnd);
         xbase[d] = sum_x;
         sum_x += (int64_t)h->T + 1;
@@ -818,8 +822,8 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
     }
     const int width = w ? w : 4;
     const int64_t items = (int64_t)D * S;
-    if (items > 0 && (!rho || !sun_dir || !com || !out_ft))
-        return fail(SRP_EINVAL, "srp_force_area: NULL array argument");
+    if (items > 0 && (!rho || (mode == 0 && !sun_dir) || (mode == 1 && !emit) || !com || !out_ft))
+        return fail(SRP_EINVAL, fn + ": NULL array argument");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     // units: chunks of a multiple of 1024 samples, at most 16M units of partials
     const int64_t tile = 1024;
@@ -833,18 +837,19 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
         cpd = std::max<int64_t>(1, (b_max + chunk - 1) / chunk);
     }
     const size_t tab_n = (size_t)std::max<int64_t>(sum_x, 1);
-    if (c->atab.ensure(3 * tab_n * sizeof(int32_t)) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_area: sample tables");
+    if (c->atab.ensure(3 * tab_n * sizeof(int32_t)) != cudaSuccess) return fail(SRP_ENOMEM, fn + ": sample tables");
     if (c->axb.ensure(2 * (size_t)std::max(D, 1) * sizeof(int64_t)) != cudaSuccess)
-        return fail(SRP_ENOMEM, "srp_force_area: sample tables");
+        return fail(SRP_ENOMEM, fn + ": sample tables");
     const size_t part_bytes = sizeof(double) * 12 * (size_t)std::max<int64_t>(items * cpd, 1);
-    if (c->part.ensure(part_bytes) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_area: cannot allocate partials");
+    if (c->part.ensure(part_bytes) != cudaSuccess) return fail(SRP_ENOMEM, fn + ": cannot allocate partials");
     int rc = upload_designs(c, designs);
     if (rc != SRP_OK) return rc;
     int64_t* d_xb = (int64_t*)c->axb.p;
     if (D > 0) CU(cudaMemcpyAsync(d_xb, xbase.data(), sizeof(int64_t) * D, cudaMemcpyHostToDevice, c->stream), "H2D xbase");
     AreaParams p;
     std::memset(&p, 0, sizeof p);
-    p.D = D; p.S = S; p.G = G; p.sun_per_design = o->sun_per_design ? 1 : 0;
+    p.mode = mode;
+    p.D = D; p.S = S; p.G = G; p.sun_per_design = (mode == 0 && o->sun_per_design) ? 1 : 0;
     p.seed = o->seed; p.P = (float)o->pressure; p.density = density;
     p.sun_base = o->sun_base; p.design_base = o->design_base;
     p.chunk = chunk; p.cpd = (int32_t)cpd; p.cap = cpd * chunk;
@@ -856,30 +861,36 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
     p.stats = c->stats_on ? c->d_stats : nullptr;
     p.queue = c->d_queue;
     const int grid_cap = c->n_sm * area_resident_blocks(width, variant);
-    const int64_t nsun = o->sun_per_design ? (int64_t)D * S : S;
+    const int64_t nsun = mode == 1 ? 0 : (p.sun_per_design ? (int64_t)D * S : S);
     double* d_ft = out_ft;
     double* d_sg = out_sigma;
     const size_t ob = sizeof(double) * 6 * (size_t)items;
     if (o->mem == SRP_MEM_DEVICE) {
-        p.rho = rho; p.sun = sun_dir; p.com = com;
+        p.rho = rho; p.sun = sun_dir; p.com = com; p.emit = emit;
     } else {
         if (items > 0) {
             rc = validate_values(rho, D, G, sun_dir, nsun);
             if (rc != SRP_OK) return rc;
+            if (mode == 1)
+                for (int64_t q = 0; q < (int64_t)D * G; ++q)
+                    if (!(emit[q] >= 0.0f) || !std::isfinite(emit[q]))
+                        return fail(SRP_EINVAL, fn + ": emit must be finite and >= 0");
         }
         const size_t rb = sizeof(float) * 2 * (size_t)D * G, sb = sizeof(double) * 3 * (size_t)nsun,
-                     cb = sizeof(double) * 3 * (size_t)D;
-        const size_t rb_al = (rb + 255) / 256 * 256, sb_al = (sb + 255) / 256 * 256;
-        if (c->stage_in.ensure(rb_al + sb_al + cb + 256) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_area: staging");
+                     cb = sizeof(double) * 3 * (size_t)D, eb = mode == 1 ? sizeof(float) * (size_t)D * G : 0;
+        const size_t rb_al = (rb + 255) / 256 * 256, sb_al = (sb + 255) / 256 * 256, cb_al = (cb + 255) / 256 * 256;
+        if (c->stage_in.ensure(rb_al + sb_al + cb_al + eb + 256) != cudaSuccess) return fail(SRP_ENOMEM, fn + ": staging");
         const size_t ob_al = (ob + 255) / 256 * 256;
-        if (c->stage_out.ensure(2 * ob_al + 256) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force_area: staging");
+        if (c->stage_out.ensure(2 * ob_al + 256) != cudaSuccess) return fail(SRP_ENOMEM, fn + ": staging");
         char* in = (char*)c->stage_in.p;
         if (items > 0) {
             CU(cudaMemcpyAsync(in, rho, rb, cudaMemcpyHostToDevice, c->stream), "H2D rho");
             CU(cudaMemcpyAsync(in + rb_al, sun_dir, sb, cudaMemcpyHostToDevice, c->stream), "H2D sun");
             CU(cudaMemcpyAsync(in + rb_al + sb_al, com, cb, cudaMemcpyHostToDevice, c->stream), "H2D com");
+            if (eb) CU(cudaMemcpyAsync(in + rb_al + sb_al + cb_al, emit, eb, cudaMemcpyHostToDevice, c->stream), "H2D emit");
         }
         p.rho = (const float*)in; p.sun = (const double*)(in + rb_al); p.com = (const double*)(in + rb_al + sb_al);
+        p.emit = (const float*)(in + rb_al + sb_al + cb_al);
         d_ft = (double*)c->stage_out.p;
         d_sg = out_sigma ? (double*)((char*)c->stage_out.p + ob_al) : nullptr;
     }
@@ -898,4 +909,17 @@ extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, con
     if (out_samples && D > 0)
         CU(cudaMemcpyAsync(out_samples, p.ntot, sizeof(int64_t) * D, cudaMemcpyDeviceToHost, c->stream), "D2H samples");
     return srp_sync(c);
+}
+}  // namespace
+
+extern "C" int srp_force_area(srp_ctx* c, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                              const double* sun_dir, int S, const double* com, float density,
+                              const srp_trace_opts* o, double* out_ft, double* out_sigma, int64_t* out_samples) {
+    return area_common(c, 0, bvhs, D, rho, G, sun_dir, S, com, nullptr, density, o, out_ft, out_sigma, out_samples);
+}
+
+extern "C" int srp_force_thermal(srp_ctx* c, const srp_bvh* const* bvhs, int D, const float* rho, int G,
+                                 const float* emit, const double* com, float density, const srp_trace_opts* o,
+                                 double* out_ft, double* out_sigma, int64_t* out_samples) {
+    return area_common(c, 1, bvhs, D, rho, G, nullptr, 1, com, emit, density, o, out_ft, out_sigma, out_samples);
 }

@@ -24,6 +24,13 @@
 //                      FP32 sums of 32 samples, FP32 warp tree, FP64 unit
 //                      sums -> partials
 // and the ray-grid tracer's reduce kernel sums the partials of each item.
+//
+// Thermal mode (Sec. 5.9, local Lambertian emitters): only triangles of
+// groups with emit > 0 get samples; a sample's packet carries
+// w = P emit A_f / n_f, recoils by its expectation -(2/3) w n_e at x (n_e the
+// winding normal, the emitting side), leaves along unit(n_e + uniform unit
+// vector) (cosine-distributed) and deposits the closed-form facet-BRDF
+// momentum w[(1-rs) omega - (2 rs cos + 2/3 rd) n] at its closest hit.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -59,13 +66,21 @@ __global__ void __launch_bounds__(256) area_prep_kernel(const AreaParams p) {
                  c = __ldg(dz.tri + 3 * (size_t)k + 2);
     const uint32_t f = __float_as_uint(a.w);
     if (f >= (uint32_t)dz.T) { atomicOr(p.err, kErrTriIndex); return; }
+    const int64_t base = p.xbase[d];
+    if (p.mode == 1) {
+        const uint32_t g = __float_as_uint(b.w);
+        if (!(g < (uint32_t)p.G && p.emit[(size_t)d * p.G + g] > 0.0f)) {
+            p.cnt[base + f] = 0;
+            p.map[base + f] = k;
+            return;
+        }
+    }
     const float prod = __fmul_rn(p.density, tri_area_rn(a, b, c));
     int32_t n = 1;
     if (prod > 1.0f) {
         if (!(prod < 1.0e9f)) { atomicOr(p.err, kErrAreaCount); n = 1; }
         else n = (int32_t)ceilf(prod);
     }
-    const int64_t base = p.xbase[d];
     p.cnt[base + f] = n;
     p.map[base + f] = k;
 }
@@ -124,7 +139,97 @@ __device__ __forceinline__ int find_tri(const int32_t* __restrict__ ex, int lo, 
     return lo;
 }
 
-template <int W, int MINB>
+// One sun-light sample: point on leaf triangle L (original index f, sample
+// jj of nf), shadow ray along e, expected BRDF momentum if lit.
+template <int W>
+__device__ __forceinline__ void sample_sun(const DesignDev& dz, int L, int f, uint32_t jj, int32_t nf, float3 e,
+                                           float3 com, const float* rho, float tmin, uint32_t sg, uint32_t dg,
+                                           uint32_t key0, uint32_t key1, float P, int* err, float y[6],
+                                           uint32_t& nvis, uint32_t& ntest, uint32_t& nseg) {
+    const float4 a = __ldg(dz.tri + 3 * (size_t)L), b = __ldg(dz.tri + 3 * (size_t)L + 1),
+                 c = __ldg(dz.tri + 3 * (size_t)L + 2);
+    const float3 e1 = xyz(b) - xyz(a), e2 = xyz(c) - xyz(a);
+    float3 n = cross(e1, e2);
+    const float len = sqrtf(dot(n, n));
+    n = (1.0f / len) * n;
+    float cs = dot(n, e);
+    if (cs < 0.0f) { n = -1.0f * n; cs = -cs; }
+    if (!(cs > 0.0f)) return;
+    const uint4 rnd = philox4x32_10(make_uint4(jj, (uint32_t)f, sg, dg), key0, key1);
+    const float u1 = unit24(rnd.x), u2 = unit24(rnd.y);
+    const float sr = sqrtf(u1);
+    const float b1 = sr * (1.0f - u2), b2 = sr * u2;
+    const float3 x = f3(fmaf(b2, e2.x, fmaf(b1, e1.x, a.x)), fmaf(b2, e2.y, fmaf(b1, e1.y, a.y)),
+                        fmaf(b2, e2.z, fmaf(b1, e1.z, a.z)));
+    RaySetup r;
+    setup_ray(r, x, e);
+    ++nseg;
+    if (any_hit<W>(dz, r, tmin, L, err, nvis, ntest)) return;
+    const int g = (int)__float_as_uint(b.w);
+    const float rs = __ldg(rho + 2 * g), rd = __ldg(rho + 2 * g + 1);
+    const float wgt = P * (0.5f * len) / (float)nf;
+    const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
+    const float ws = wgt * cs, a1 = ws * (1.0f - rs), a2 = ws * cn;
+    const float3 dp = f3(-a1 * e.x - a2 * n.x, -a1 * e.y - a2 * n.y, -a1 * e.z - a2 * n.z);
+    const float3 tq = cross(x - com, dp);
+    y[0] = dp.x; y[1] = dp.y; y[2] = dp.z; y[3] = tq.x; y[4] = tq.y; y[5] = tq.z;
+}
+
+// One thermal packet of leaf triangle L: expected recoil at the point, and
+// the closed-form deposit at the closest hit of its cosine-distributed ray.
+template <int W>
+__device__ __forceinline__ void sample_thermal(const DesignDev& dz, int L, int f, uint32_t jj, int32_t nf,
+                                               float3 com, const float* rho, const float* emit, float tmin,
+                                               uint32_t dg, uint32_t key0, uint32_t key1, float P, int* err,
+                                               float y[6], uint32_t& nvis, uint32_t& ntest, uint32_t& nseg) {
+    const float4 a = __ldg(dz.tri + 3 * (size_t)L), b = __ldg(dz.tri + 3 * (size_t)L + 1),
+                 c = __ldg(dz.tri + 3 * (size_t)L + 2);
+    const float3 e1 = xyz(b) - xyz(a), e2 = xyz(c) - xyz(a);
+    float3 ne = cross(e1, e2);
+    const float len = sqrtf(dot(ne, ne));
+    ne = (1.0f / len) * ne;
+    const int g = (int)__float_as_uint(b.w);
+    const float w = P * __ldg(emit + g) * (0.5f * len) / (float)nf;
+    const uint4 rnd = philox4x32_10(make_uint4(jj, (uint32_t)f, 0u, dg), key0, key1);
+    const float sr = sqrtf(unit24(rnd.x)), u2 = unit24(rnd.y);
+    const float b1 = sr * (1.0f - u2), b2 = sr * u2;
+    const float3 x = f3(fmaf(b2, e2.x, fmaf(b1, e1.x, a.x)), fmaf(b2, e2.y, fmaf(b1, e1.y, a.y)),
+                        fmaf(b2, e2.z, fmaf(b1, e1.z, a.z)));
+    const float wr = -(2.0f / 3.0f) * w;
+    const float3 rc = wr * ne;
+    const float3 tr = cross(x - com, rc);
+    y[0] = rc.x; y[1] = rc.y; y[2] = rc.z; y[3] = tr.x; y[4] = tr.y; y[5] = tr.z;
+    const float z = 1.0f - 2.0f * unit24(rnd.z);
+    const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    float sp, cp;
+    sincospif(2.0f * unit24(rnd.w), &sp, &cp);
+    const float3 v = f3(ne.x + rr * cp, ne.y + rr * sp, ne.z + z);
+    const float l2 = dot(v, v);
+    if (!(l2 > 0.0f)) return;
+    const float3 om = rsqrtf(l2) * v;
+    RaySetup r;
+    setup_ray(r, x, om);
+    ++nseg;
+    float t;
+    const int h = closest_hit<W>(dz, r, tmin, L, t, err, nvis, ntest);
+    if (h < 0) return;
+    const float4 ha = __ldg(dz.tri + 3 * (size_t)h), hb = __ldg(dz.tri + 3 * (size_t)h + 1),
+                 hc = __ldg(dz.tri + 3 * (size_t)h + 2);
+    float3 n = cross(xyz(hb) - xyz(ha), xyz(hc) - xyz(ha));
+    n = rsqrtf(dot(n, n)) * n;
+    if (dot(n, om) > 0.0f) n = -1.0f * n;
+    const float cs = -dot(n, om);
+    const int gh = (int)__float_as_uint(hb.w);
+    const float rs = __ldg(rho + 2 * gh), rd = __ldg(rho + 2 * gh + 1);
+    const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
+    const float a1 = w * (1.0f - rs), a2 = w * cn;
+    const float3 dp = f3(a1 * om.x - a2 * n.x, a1 * om.y - a2 * n.y, a1 * om.z - a2 * n.z);
+    const float3 yh = x + t * om;
+    const float3 tq = cross(yh - com, dp);
+    y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
+}
+
+template <int W, int MINB, int MODE>
 __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
     __shared__ double dacc[4][12];
     __shared__ float lacc[4][12][32];   // per-lane FP32 sums of a tile (kept out of registers)
@@ -148,13 +253,18 @@ __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
         if (lane < 12) dacc[warp][lane] = 0.0;
         __syncwarp();
         if (k0 < k1) {
-            const double* sp = p.sun + 3 * (size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s);
-            const float3 e = f3((float)sp[0], (float)sp[1], (float)sp[2]);
+            float3 e = f3(0.0f, 0.0f, 1.0f);
+            if (MODE == 0) {
+                const double* sp = p.sun + 3 * (size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s);
+                e = f3((float)sp[0], (float)sp[1], (float)sp[2]);
+            }
+            const float* emit = MODE == 1 ? p.emit + (size_t)dl * p.G : nullptr;
             const double* cp = p.com + 3 * (size_t)dl;
             const float3 com = f3((float)cp[0], (float)cp[1], (float)cp[2]);
             const float* rho = p.rho + (size_t)dl * p.G * 2;
             const float tmin = (float)(1e-6 * dz.R);
-            const uint32_t sg = (uint32_t)(p.sun_base + s), dg = (uint32_t)(p.design_base + dl) | 0x80000000u;
+            const uint32_t sg = (uint32_t)(p.sun_base + s);
+            const uint32_t dg = (uint32_t)(p.design_base + dl) | (MODE == 0 ? 0x80000000u : 0x40000000u);
             const int32_t* __restrict__ ex = p.ex + base;
             const int32_t* __restrict__ map = p.map + base;
             const int T = dz.T;
@@ -193,35 +303,12 @@ __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
                         const uint32_t jj = (uint32_t)(k - ex_lo);
                         const int32_t nf = ex_hi - ex_lo;
                         const int L = __ldg(map + f);
-                        const float4 a = __ldg(dz.tri + 3 * (size_t)L), b = __ldg(dz.tri + 3 * (size_t)L + 1),
-                                     c = __ldg(dz.tri + 3 * (size_t)L + 2);
-                        const float3 e1 = xyz(b) - xyz(a), e2 = xyz(c) - xyz(a);
-                        float3 n = cross(e1, e2);
-                        const float len = sqrtf(dot(n, n));
-                        n = (1.0f / len) * n;
-                        float cs = dot(n, e);
-                        if (cs < 0.0f) { n = -1.0f * n; cs = -cs; }
-                        if (cs > 0.0f) {
-                            const uint4 rnd = philox4x32_10(make_uint4(jj, (uint32_t)f, sg, dg), key0, key1);
-                            const float u1 = unit24(rnd.x), u2 = unit24(rnd.y);
-                            const float sr = sqrtf(u1);
-                            const float b1 = sr * (1.0f - u2), b2 = sr * u2;
-                            const float3 x = f3(fmaf(b2, e2.x, fmaf(b1, e1.x, a.x)), fmaf(b2, e2.y, fmaf(b1, e1.y, a.y)),
-                                                fmaf(b2, e2.z, fmaf(b1, e1.z, a.z)));
-                            RaySetup r;
-                            setup_ray(r, x, e);
-                            ++nseg;
-                            if (!any_hit<W>(dz, r, tmin, L, p.err, nvis, ntest)) {
-                                const int g = (int)__float_as_uint(b.w);
-                                const float rs = __ldg(rho + 2 * g), rd = __ldg(rho + 2 * g + 1);
-                                const float wgt = p.P * (0.5f * len) / (float)nf;
-                                const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
-                                const float ws = wgt * cs, a1 = ws * (1.0f - rs), a2 = ws * cn;
-                                const float3 dp = f3(-a1 * e.x - a2 * n.x, -a1 * e.y - a2 * n.y, -a1 * e.z - a2 * n.z);
-                                const float3 tq = cross(x - com, dp);
-                                y[0] = dp.x; y[1] = dp.y; y[2] = dp.z; y[3] = tq.x; y[4] = tq.y; y[5] = tq.z;
-                            }
-                        }
+                        if (MODE == 0)
+                            sample_sun<W>(dz, L, f, jj, nf, e, com, rho, tmin, sg, dg, key0, key1, p.P, p.err, y, nvis,
+                                          ntest, nseg);
+                        else
+                            sample_thermal<W>(dz, L, f, jj, nf, com, rho, emit, tmin, dg, key0, key1, p.P, p.err, y,
+                                              nvis, ntest, nseg);
                     }
                     const bool pvalid = __shfl_xor_sync(0xffffffffu, (int)valid, 1);
 #pragma unroll
@@ -268,7 +355,7 @@ __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
 template <int W, int MINB>
 static int area_blocks_v() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, area_kernel<W, MINB>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, area_kernel<W, MINB, 0>, 128, 0);
     return nb > 0 ? nb : 1;
 }
 
@@ -279,11 +366,17 @@ int area_resident_blocks(int width, int variant) {
     return variant == 4 ? area_blocks_v<4, 4>() : variant == 8 ? area_blocks_v<4, 8>() : area_blocks_v<4, 6>();
 }
 
+template <int W, int MODE>
+static void area_launch_m(const AreaParams& p, int variant, int grid, cudaStream_t st) {
+    if (variant == 4) area_kernel<W, 4, MODE><<<grid, 128, 0, st>>>(p);
+    else if (variant == 8) area_kernel<W, 8, MODE><<<grid, 128, 0, st>>>(p);
+    else area_kernel<W, 6, MODE><<<grid, 128, 0, st>>>(p);
+}
+
 template <int W>
 static void area_launch_w(const AreaParams& p, int variant, int grid, cudaStream_t st) {
-    if (variant == 4) area_kernel<W, 4><<<grid, 128, 0, st>>>(p);
-    else if (variant == 8) area_kernel<W, 8><<<grid, 128, 0, st>>>(p);
-    else area_kernel<W, 6><<<grid, 128, 0, st>>>(p);
+    if (p.mode == 1) area_launch_m<W, 1>(p, variant, grid, st);
+    else area_launch_m<W, 0>(p, variant, grid, st);
 }
 
 // Prep + scan (the sample tables), then the persistent sampling kernel.

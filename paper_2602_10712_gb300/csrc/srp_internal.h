@@ -77,6 +77,7 @@ struct TraceParams {
 
 // Parameters of the area-sampling estimator (area.cu).
 struct AreaParams {
+    int32_t mode;             // 0: sun light with next-event shadow rays; 1: thermal emitters
     int32_t D, S, G, sun_per_design;
     uint64_t seed;
     float P, density;
@@ -93,6 +94,7 @@ struct AreaParams {
     const float* rho;
     const double* sun;
     const double* com;
+    const float* emit;        // thermal: [D][G] emitted momentum flux per unit area (times P)
     double* part;             // [units][12]
     int* err;
     unsigned long long* stats;
