@@ -451,6 +451,44 @@ def area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, width):
     rate = n_per_sun * S / t
     achieved = ops * rate / 1e12
     peak_alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    # thermal emitters (Sec. 5.9) on the same satellite: every third material
+    # group emits 700 W/m^2 (pressure 1/c), ~16 M packets per call
+    emit = np.zeros((1, 64), np.float32)
+    emit[0, ::3] = 700.0
+    e_t = torch.from_numpy(emit).to(dev)
+    grp = m.group
+    tr = m.tris
+    a_t = 0.5 * np.linalg.norm(np.cross(v[tr[:, 1]] - v[tr[:, 0]], v[tr[:, 2]] - v[tr[:, 0]]), axis=1)
+    a_emit = float(a_t[emit[0, grp] > 0].sum())
+    dens_t = 16.0e6 / a_emit
+    tft = torch.empty((1, 6), dtype=torch.float64, device=dev)
+    tn = torch.empty((1,), dtype=torch.int64, device=dev)
+    for _ in range(3):
+        srp.srp_force_thermal(ctx, [b], r_t, e_t, c_t, dens_t, out_ft=tft, out_samples=tn, pressure=1.0 / 299792458.0)
+    torch.cuda.synchronize()
+    n_th = int(tn.cpu()[0])
+    srp.srp_collect_stats(ctx, True)
+    srp.srp_force_thermal(ctx, [b], r_t, e_t, c_t, dens_t, out_ft=tft, pressure=1.0 / 299792458.0)
+    torch.cuda.synchronize()
+    tvis, ttests, tsegs = srp.srp_collect_stats(ctx, False)
+    tms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        srp.srp_force_thermal(ctx, [b], r_t, e_t, c_t, dens_t, out_ft=tft, pressure=1.0 / 299792458.0)
+        e1.record()
+        torch.cuda.synchronize()
+        tms.append(e0.elapsed_time(e1))
+    t_th = sum(tms) / reps / 1e3
+    ops_t = (tvis * ops_node + ttests * 44) / max(tsegs, 1)
+    thermal = {"packets_per_s": n_th / t_th, "packets_per_call": n_th, "ms_per_call": t_th * 1e3,
+               "emitting_area_m2": a_emit, "force_N": tft.cpu().numpy()[0, :3].tolist(),
+               "free_recoil_N": (2.0 / 3.0) * 700.0 * a_emit / 299792458.0,
+               "node_visits_per_packet": tvis / max(tsegs, 1), "tri_tests_per_packet": ttests / max(tsegs, 1),
+               "roofline": {"bound": "alu", "achieved": ops_t * n_th / t_th / 1e12, "peak": peak_alu,
+                            "unit": "TFLOP/s", "frac": ops_t * n_th / t_th / 1e12 / peak_alu, "traffic": None},
+               "note": "srp_force_thermal, every third group emits 700 W/m^2, closest-hit packets"}
     b.close()
     return {"samples_per_s": rate, "samples_per_sun": n_per_sun, "suns": S, "density_per_m2": dens,
             "ms_per_call": t * 1e3, "shadow_rays_per_sample": segs / max(1, n_per_sun * sub.shape[0]),
@@ -466,7 +504,7 @@ def area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, width):
                                "note": "same 2048^2 budget per sun; empirical variance of F over 8 seeds; "
                                        "efficiency = (var x time)_grid / (var x time)_area, > 1 favours the area "
                                        "estimator; max_z = largest |F_area - F_grid| / combined sigma"},
-            "gpu_launches_per_call": 4}
+            "gpu_launches_per_call": 4, "thermal": thermal}
 
 
 def run_profile_case(case):
