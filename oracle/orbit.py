@@ -18,6 +18,13 @@ Force models:
   'cannonball' F = -P theta[0] wbar, tau = 0   (area x (1 + 4 rho_d/9))
   'proxy'      (F, tau) = P (std * y + mean), y = MLP(scale * (wbar, theta)
                + offset)  (the proxy of Sec. 3.3, FP32 weights held in FP64)
+Optional terms of the paper's orbit force model (Sec. 3.4, "additional
+accelerations"; Montenbruck & Gill's formulas):
+  eclipse     cylinder shadow: SRP force and torque are zero while
+              r.e_sun < 0 and |r - (r.e_sun) e_sun| < Re;
+  third body  point masses at fixed inertial positions s (the Sun at
+              sun_dist along e_sun, an optional Moon position):
+              a = GM [(s - r)/|s - r|^3 - s/|s|^3].
 RK4 (Sec. 3.4.1): z+ = z + h/6 (k1 + 2 k2 + 2 k3 + k4).
 Gradient of L(z_N) w.r.t. theta and z0: complex-step differentiation of the
 discrete map (d/dp f = Im f(p + i h)/h with h = 1e-30), exact to round-off
@@ -56,7 +63,8 @@ def gravity(r, mu=MU, j2=J2, re=RE):
 
 class Model:
     def __init__(self, kind="none", P=1361.0 / 299792458.0, mass=1000.0, inertia=(500.0, 400.0, 300.0),
-                 sun=(1.0, 0.0, 0.0), params=None, scale=None, offset=None, mean=None, std=None, j2=J2):
+                 sun=(1.0, 0.0, 0.0), params=None, scale=None, offset=None, mean=None, std=None, j2=J2,
+                 eclipse=False, gm_sun=0.0, sun_dist=0.0, gm_moon=0.0, moon=(0.0, 0.0, 0.0)):
         self.kind, self.P, self.mass = kind, P, mass
         self.I = np.asarray(inertia, np.float64)
         self.sun = np.asarray(sun, np.float64)
@@ -66,6 +74,26 @@ class Model:
         self.mean = None if mean is None else np.asarray(mean, np.float64)
         self.std = None if std is None else np.asarray(std, np.float64)
         self.j2 = j2
+        self.eclipse = eclipse
+        self.gm_sun, self.sun_dist = gm_sun, sun_dist
+        self.gm_moon, self.moon = gm_moon, np.asarray(moon, np.float64)
+
+    def in_shadow(self, r):
+        """Cylinder eclipse test on the real part of r."""
+        rr = np.real(np.asarray(r))
+        p = rr @ self.sun
+        return p < 0.0 and (rr @ rr - p * p) < RE * RE
+
+    def third_body(self, r):
+        a = np.zeros(3, dtype=np.result_type(r, np.float64))
+        for gm, s in ((self.gm_sun, self.sun_dist * self.sun), (self.gm_moon, self.moon)):
+            if gm == 0.0:
+                continue
+            d = s - r
+            dn = np.sqrt(d @ d)
+            sn = np.sqrt(s @ s)
+            a = a + gm * (d / (dn * dn * dn) - s / (sn * sn * sn))
+        return a
 
     def srp(self, wbar, theta):
         if self.kind == "none":
@@ -86,7 +114,9 @@ class Model:
         R = rot(q)
         wbar = R.T @ self.sun
         F, tau = self.srp(wbar, theta)
-        a = R @ F / self.mass + gravity(r, j2=self.j2)
+        if self.eclipse and self.in_shadow(r):
+            F, tau = 0.0 * F, 0.0 * tau
+        a = R @ F / self.mass + gravity(r, j2=self.j2) + self.third_body(r)
         q0, q1, q2, q3 = q
         wx, wy, wz = w
         qd = 0.5 * np.array([-q1 * wx - q2 * wy - q3 * wz,

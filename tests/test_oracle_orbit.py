@@ -71,3 +71,65 @@ def test_complex_step_matches_central_difference():
         f1 = O.fd_grad(m, z0, th, 10.0, 60, wN, j, 1e-3)
         fd = (9.0 * f1 - f3) / 8.0
         assert abs(fd - gt[j]) <= 1e-5 * abs(fd) + 1e-7, (j, fd, gt[j])
+
+
+# ---------------------------------------------------------------- eclipse and third bodies (Sec. 3.4)
+GM_SUN = 1.32712440018e20
+AU = 1.495978707e11
+
+
+def test_cylinder_eclipse_switches_srp():
+    """Cylinder shadow: behind the Earth (r.e < 0) and within Re of the
+    Earth-sun line the SRP acceleration is zero; in front, or outside the
+    cylinder, it is the cannonball value."""
+    m = O.Model("cannonball", P=1e-5, mass=10.0, sun=(1.0, 0.0, 0.0), eclipse=True)
+    th = np.array([2.0])
+    q = np.array([1.0, 0.0, 0.0, 0.0])
+    def srp_acc(r):
+        z = np.concatenate([r, [0, 0, 0], q, [0, 0, 0]])
+        g = O.gravity(np.asarray(r, float))
+        return m.f(z, th)[3:6] - g
+    full = -1e-5 * 2.0 / 10.0 * np.array([1.0, 0.0, 0.0])
+    assert np.allclose(srp_acc([7e6, 0.0, 0.0]), full, rtol=1e-12)                  # sunlit side
+    assert np.allclose(srp_acc([-7e6, 0.0, 0.0]), 0.0, atol=1e-20)                  # umbra (on the axis)
+    assert np.allclose(srp_acc([-7e6, O.RE * 0.999, 0.0]), 0.0, atol=1e-20)         # inside the cylinder
+    assert np.allclose(srp_acc([-7e6, O.RE * 1.001, 0.0]), full, rtol=1e-12)        # just outside
+    assert np.allclose(srp_acc([1.0, 7e6, 0.0]), full, rtol=1e-12)                  # terminator, r.e > 0
+
+
+def test_third_body_tidal_limit():
+    """For |r| << |s| the point-mass difference tends to the tidal
+    acceleration GM/|s|^3 (3 (e.r) e - r) (Montenbruck & Gill Eq. 3.37's
+    leading term); at r = 0 it vanishes exactly."""
+    e = np.array([0.6, 0.8, 0.0])
+    m = O.Model("none", sun=e, gm_sun=GM_SUN, sun_dist=AU)
+    assert np.allclose(m.third_body(np.zeros(3)), 0.0, atol=1e-25)
+    r = np.array([7.0e6, -2.0e6, 3.0e6])
+    tidal = GM_SUN / AU ** 3 * (3.0 * (e @ r) * e - r)
+    assert np.allclose(m.third_body(r), tidal, rtol=1e-4)
+    moon = np.array([3.844e8, 0.0, 0.0])
+    mm = O.Model("none", gm_moon=4.9028e12, moon=moon)
+    rm = np.array([0.0, 7e6, 0.0])
+    d = moon - rm
+    want = 4.9028e12 * (d / np.linalg.norm(d) ** 3 - moon / np.linalg.norm(moon) ** 3)
+    assert np.allclose(mm.third_body(rm), want, rtol=1e-14)
+
+
+def test_complex_step_with_eclipse_and_third_bodies():
+    """The discrete-map gradient stays exact (complex step vs central
+    difference) with the eclipse switch and both point masses on, on an
+    orbit that enters the shadow (the switch is constant between steps)."""
+    m = O.Model("cannonball", P=1e-3, mass=10.0, sun=(1.0, 0.0, 0.0), eclipse=True, gm_sun=GM_SUN, sun_dist=AU,
+                gm_moon=4.9028e12, moon=(0.0, 3.844e8, 0.0))
+    z0 = O.circular_state(7.0e6, 0.3, u=2.5)
+    th = np.array([3.0])
+    wN = np.zeros(13); wN[0] = 1.0; wN[4] = 100.0
+    g_th, g_z = O.cs_grad(m, z0, th, 30.0, 40, wN)
+    fd = O.fd_grad(m, z0, th, 30.0, 40, wN, 0, 1e-4)
+    assert abs(g_th[0] - fd) <= 1e-6 * abs(fd) + 1e-12
+    # it really crossed into the shadow: the final state differs from the no-eclipse run
+    m2 = O.Model("cannonball", P=1e-3, mass=10.0, sun=(1.0, 0.0, 0.0), gm_sun=GM_SUN, sun_dist=AU,
+                 gm_moon=4.9028e12, moon=(0.0, 3.844e8, 0.0))
+    zs = O.rk4(m, z0, th, 30.0, 40)
+    zn = O.rk4(m2, z0, th, 30.0, 40)
+    assert np.linalg.norm(zs[:3] - zn[:3]) > 1e-3
