@@ -276,6 +276,18 @@ int srp_mlp_infer(srp_ctx* ctx, const srp_mlp* mlp, const float* x, int64_t B, f
  * grad_out (host [P], may be NULL) the gradient.  1 <= B <= 2^24. */
 int srp_mlp_train_step(srp_ctx* ctx, srp_mlp* mlp, const float* x, const float* t, int64_t B, float lr,
                        float* loss_out, float* grad_out, int mem);
+/* Input gradient of the proxy (what Alg. 1 back-propagates from the orbit
+ * loss into the design): gx [B][19] = (dy/dx)^T wy for wy [B][6], per row;
+ * BF16 GEMMs with FP32 accumulation as in training.  mem = srp_mem of x, wy
+ * and gx; device-mem calls are asynchronous.  0 <= B <= 2^24.  Shares the
+ * network's training scratch (do not overlap with train_step on another
+ * stream). */
+int srp_mlp_grad_input(srp_ctx* ctx, srp_mlp* mlp, const float* x, const float* wy, int64_t B, float* gx, int mem);
+/* Parameter files: 8-byte tag "SRPMLP1\0", int64 count, FP32 parameters in
+ * the order above (host byte order).  Load resets Adam; a file of another
+ * size or tag is SRP_EINVAL. */
+int srp_mlp_save(srp_ctx* ctx, const srp_mlp* mlp, const char* path);
+int srp_mlp_load(srp_ctx* ctx, srp_mlp* mlp, const char* path);
 
 /* ---- orbit integration and its adjoint (Sec. 3.4, Eq. "ODE", RK4 of
  * Sec. 3.4.1, adjoint of Sec. 3.4.3) --------------------------------------
@@ -288,6 +300,12 @@ int srp_mlp_train_step(srp_ctx* ctx, srp_mlp* mlp, const float* x, const float* 
  *   SRP_FM_NONE        y = 0
  *   SRP_FM_CANNONBALL  y = (-theta[0] wbar, 0) (theta[0] = area x (1+4 rho_d/9))
  *   SRP_FM_PROXY       y = MLP(in_scale * (wbar, theta) + in_offset), n_theta = 16
+ * Optional terms (Sec. 3.4 "additional accelerations"): the cylinder
+ * eclipse (SRP off while r.sun < 0 and |r - (r.sun) sun| < re) and point
+ * masses at fixed inertial positions, GM [(s - r)/|s - r|^3 - s/|s|^3]
+ * (the paper's Sun/Moon from ephemerides; positions are inputs here).
+ * The eclipse switch is piecewise constant: its derivative is zero (the
+ * adjoint does not see the shadow boundary).
  * RK4 in FP64 with step dt (the MLP runs in FP32).  With dL_dzN given, the
  * discrete adjoint of the RK4 map (checkpoints every ckpt_every steps,
  * 0 = ceil(sqrt(n_steps)), at most 64) returns dL/dtheta and dL/dz0. */
@@ -307,6 +325,13 @@ typedef struct srp_orbit_opts {
     int32_t n_theta;          /* 1..16 [1]                                    */
     float in_scale[19], in_offset[19];   /* proxy input map [1, 0]            */
     float out_mean[6], out_std[6];       /* model output map [0, 1]           */
+    int32_t eclipse;          /* 1: cylinder shadow of radius re along -sun  */
+                              /*    switches F and tau off [0]               */
+    int32_t reserved0;
+    double gm_sun;            /* m^3/s^2 point mass at sun_dist * sun [0=off] */
+    double sun_dist;          /* m [1.495978707e11]                           */
+    double gm_moon;           /* m^3/s^2 point mass at moon [0 = off]         */
+    double moon[3];           /* inertial position, m [0]                     */
 } srp_orbit_opts;
 void srp_orbit_opts_default(srp_orbit_opts* o);
 /* n_traj trajectories, one CTA each:  z0 [n][13], theta [n][n_theta] ->

@@ -91,6 +91,9 @@ def load(build_if_needed: bool = True):
     lib.srp_graph_destroy.argtypes = [_P]
     lib.srp_integrate.argtypes = [_P, _P, _P, i32, _P, _P, _P, _P, _P, _P, _P, i32]
     lib.srp_mlp_train_step.argtypes = [_P, _P, _P, _P, i64, C.c_float, _P, _P, i32]
+    lib.srp_mlp_grad_input.argtypes = [_P, _P, _P, _P, i64, _P, i32]
+    lib.srp_mlp_save.argtypes = [_P, _P, C.c_char_p]
+    lib.srp_mlp_load.argtypes = [_P, _P, C.c_char_p]
     lib.srp_force_noalloc.argtypes = [_P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P, _P, _P]
     lib.srp_build_bvh_host.argtypes = [_P, i32, _P, i32, i32, _P, C.POINTER(C.c_int64), _P, C.POINTER(C.c_int32)]
     lib.srp_trace_rays.argtypes = [_P, _P, _P, i32, _P, _P, _P, i64, i32, i32, C.POINTER(TraceOpts), _P, _P]
@@ -595,6 +598,28 @@ class MLP:
                                          _ptr(loss), _ptr(grad), SRP_MEM_HOST if host else SRP_MEM_DEVICE))
         return (float(loss[0]) if want_loss else None), grad
 
+    def grad_input(self, x, wy, gx=None):
+        """gx [B,19] = (dy/dx)^T wy for wy [B,6]; numpy -> host mode."""
+        if isinstance(x, np.ndarray):
+            x = _np(x, np.float32).reshape(-1, 19)
+            wy = _np(wy, np.float32).reshape(-1, 6)
+            gx = np.zeros((x.shape[0], 19), np.float32) if gx is None else gx
+            mem = SRP_MEM_HOST
+        else:
+            import torch
+            gx = torch.empty((x.shape[0], 19), dtype=torch.float32, device=x.device) if gx is None else gx
+            mem = SRP_MEM_DEVICE
+        if wy.shape[0] != x.shape[0]:
+            raise ValueError("wy must have the batch of x")
+        _check(load().srp_mlp_grad_input(self.ctx.handle, self.handle, _ptr(x), _ptr(wy), x.shape[0], _ptr(gx), mem))
+        return gx
+
+    def save(self, path: str):
+        _check(load().srp_mlp_save(self.ctx.handle, self.handle, os.fsencode(path)))
+
+    def load_file(self, path: str):
+        _check(load().srp_mlp_load(self.ctx.handle, self.handle, os.fsencode(path)))
+
 
 # ----------------------------------------------------------------- orbits
 SRP_FM_NONE, SRP_FM_CANNONBALL, SRP_FM_PROXY = 0, 1, 2
@@ -605,7 +630,8 @@ class OrbitOpts(C.Structure):
                 ("inertia", C.c_double * 3), ("pressure", C.c_double), ("sun", C.c_double * 3), ("dt", C.c_double),
                 ("n_steps", C.c_int32), ("ckpt_every", C.c_int32), ("model", C.c_int32), ("n_theta", C.c_int32),
                 ("in_scale", C.c_float * 19), ("in_offset", C.c_float * 19), ("out_mean", C.c_float * 6),
-                ("out_std", C.c_float * 6)]
+                ("out_std", C.c_float * 6), ("eclipse", C.c_int32), ("reserved0", C.c_int32), ("gm_sun", C.c_double),
+                ("sun_dist", C.c_double), ("gm_moon", C.c_double), ("moon", C.c_double * 3)]
 
 
 def orbit_opts(**kw) -> OrbitOpts:

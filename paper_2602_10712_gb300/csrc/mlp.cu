@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -383,6 +384,42 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     return cudaGetLastError();
 }
 
+// Input gradient gx[B][19] = (d y / d x)^T wy  (wy [B][6]): forward with
+// saved pre-activations, then the backward pass of mlp_train with wy in
+// place of dL/dy, ending in gx = dZ_0 W_0.
+cudaError_t mlp_input_grad(const float* x, const float* wy, int64_t B, const float* params, float* gx, void* work,
+                           int* err, cudaStream_t st) {
+    const MlpLayout L = mlp_layout();
+    TrainBufs tb;
+    train_carve(work, B, tb);
+    tb.H[0] = const_cast<float*>(x);
+    cudaError_t e;
+    const int Bi = (int)B;
+    for (int l = 0; l < kMlpLayers; ++l) {
+        const int in = mlp_in(l), out = mlp_out(l);
+        e = tc_gemm(GemmOp{tb.H[l], in, 0}, GemmOp{params + L.w_off[l], in, 0}, Bi, out, in, 1.0f, tb.Z[l], out, 0, 0,
+                    err, st);
+        if (e != cudaSuccess) return e;
+        bias_silu_kernel<<<ew_grid(B * out), 256, 0, st>>>(tb.Z[l], params + L.b_off[l],
+                                                           l < kMlpLayers - 1 ? tb.H[l + 1] : nullptr, B, out);
+    }
+    const float* dZ = wy;
+    float* bufs[2] = {tb.dA, tb.dB};
+    int nb = 0;
+    for (int l = kMlpLayers - 1; l >= 0; --l) {
+        const int in = mlp_in(l), out = mlp_out(l);
+        float* dH = l > 0 ? bufs[nb] : gx;
+        e = tc_gemm(GemmOp{dZ, out, 0}, GemmOp{params + L.w_off[l], in, 1}, Bi, in, out, 1.0f, dH, in, 0, 0, err, st);
+        if (e != cudaSuccess) return e;
+        if (l > 0) {
+            dsilu_kernel<<<ew_grid(B * in), 256, 0, st>>>(dH, tb.Z[l - 1], dH, B * in);
+            dZ = dH;
+            nb ^= 1;
+        }
+    }
+    return cudaGetLastError();
+}
+
 float* train_loss_ptr(void* work, int64_t B) {
     TrainBufs tb;
     train_carve(work, B, tb);
@@ -581,3 +618,67 @@ extern "C" int srp_mlp_train_step(srp_ctx* c, srp_mlp* m, const float* x, const 
     if (grad_out || loss_out || mem == SRP_MEM_HOST) return srp_sync(c);
     return SRP_OK;
 }
+
+extern "C" int srp_mlp_grad_input(srp_ctx* c, srp_mlp* m, const float* x, const float* wy, int64_t B, float* gx,
+                                  int mem) {
+    if (!c || !m) return mfail(SRP_EINVAL, "srp_mlp_grad_input: NULL ctx/mlp");
+    if (B < 0 || B > (1 << 24)) return mfail(SRP_EINVAL, "srp_mlp_grad_input: batch must be in 0..2^24");
+    if (B == 0) return SRP_OK;
+    if (!x || !wy || !gx) return mfail(SRP_EINVAL, "srp_mlp_grad_input: NULL x/wy/gx");
+    if (mem != SRP_MEM_HOST && mem != SRP_MEM_DEVICE) return mfail(SRP_EINVAL, "srp_mlp_grad_input: bad mem");
+    MCU(cudaSetDevice(m->device), "cudaSetDevice");
+    cudaStream_t st = ctx_stream(c);
+    const size_t stage = mem == SRP_MEM_HOST ? sizeof(float) * 44 * (size_t)B + 1024 : 0;
+    const size_t need = train_bytes(B) + stage;
+    if (m->work_bytes < need) {
+        if (m->work) cudaFree(m->work);
+        m->work = nullptr; m->work_bytes = 0;
+        if (cudaMalloc(&m->work, need) != cudaSuccess) return mfail(SRP_ENOMEM, "srp_mlp_grad_input: workspace");
+        m->work_bytes = need;
+    }
+    if (mem == SRP_MEM_DEVICE) {
+        MCU(mlp_input_grad(x, wy, B, m->params, gx, m->work, ctx_err(c), st), "input-gradient launch");
+        return SRP_OK;
+    }
+    float* sx = (float*)((char*)m->work + (train_bytes(B) + 255) / 256 * 256);
+    float* sw = sx + 19 * B;
+    float* sg = sw + 6 * B;
+    MCU(cudaMemcpyAsync(sx, x, sizeof(float) * 19 * B, cudaMemcpyHostToDevice, st), "H2D x");
+    MCU(cudaMemcpyAsync(sw, wy, sizeof(float) * 6 * B, cudaMemcpyHostToDevice, st), "H2D wy");
+    MCU(mlp_input_grad(sx, sw, B, m->params, sg, m->work, ctx_err(c), st), "input-gradient launch");
+    MCU(cudaMemcpyAsync(gx, sg, sizeof(float) * 19 * B, cudaMemcpyDeviceToHost, st), "D2H gx");
+    return srp_sync(c);
+}
+
+// File format: 8-byte tag "SRPMLP1", int64 parameter count, then the FP32
+// parameters in the order of srp_mlp_param_count (host byte order).
+extern "C" int srp_mlp_save(srp_ctx* c, const srp_mlp* m, const char* path) {
+    if (!c || !m || !path) return mfail(SRP_EINVAL, "srp_mlp_save: NULL argument");
+    std::vector<float> p(kMlpParams);
+    int rc = srp_mlp_get_params(c, m, p.data());
+    if (rc != SRP_OK) return rc;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return mfail(SRP_EINVAL, std::string("srp_mlp_save: cannot open ") + path);
+    const char tag[8] = {'S', 'R', 'P', 'M', 'L', 'P', '1', 0};
+    const int64_t n = kMlpParams;
+    bool ok = std::fwrite(tag, 1, 8, f) == 8 && std::fwrite(&n, sizeof n, 1, f) == 1 &&
+              std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? SRP_OK : mfail(SRP_EINVAL, std::string("srp_mlp_save: write failed: ") + path);
+}
+
+extern "C" int srp_mlp_load(srp_ctx* c, srp_mlp* m, const char* path) {
+    if (!c || !m || !path) return mfail(SRP_EINVAL, "srp_mlp_load: NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return mfail(SRP_EINVAL, std::string("srp_mlp_load: cannot open ") + path);
+    char tag[8];
+    int64_t n = 0;
+    std::vector<float> p(kMlpParams);
+    bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, "SRPMLP1", 8) == 0 &&
+              std::fread(&n, sizeof n, 1, f) == 1 && n == kMlpParams &&
+              std::fread(p.data(), sizeof(float), p.size(), f) == p.size();
+    std::fclose(f);
+    if (!ok) return mfail(SRP_EINVAL, std::string("srp_mlp_load: not a parameter file of this network: ") + path);
+    return srp_mlp_set_params(c, m, p.data());
+}
+

@@ -36,6 +36,8 @@ namespace srp {
 struct OrbitDev {
     double mu, j2, re, mass, I[3], P, sun[3], dt;
     int n_steps, ckpt, model, n_theta;
+    int eclipse;                          // cylinder shadow switches SRP off
+    double gm3[2], pos3[2][3];            // point masses at fixed positions (GM 0 = off)
     float in_scale[19], in_offset[19], out_mean[6], out_std[6];
     // proxy weights (FP32): W_l [out][in], Wt_l [in][out], b_l
     const float* W[5];
@@ -88,6 +90,13 @@ __device__ void sun_body(const S* q, const double* e, S* wb) {
 template <class S>
 __device__ void dyn(const OrbitDev& o, const S* z, const S* y, S* k) {
     const S x = z[0], yy = z[1], zz = z[2];
+    // cylinder eclipse (decided on the values; piecewise constant in r)
+    double nu = 1.0;
+    if (o.eclipse) {
+        const double rx = val(x), ry = val(yy), rz = val(zz);
+        const double pr = rx * o.sun[0] + ry * o.sun[1] + rz * o.sun[2];
+        if (pr < 0.0 && (rx * rx + ry * ry + rz * rz - pr * pr) < o.re * o.re) nu = 0.0;
+    }
     const S q0 = z[6], q1 = z[7], q2 = z[8], q3 = z[9];
     const S w0 = z[10], w1 = z[11], w2 = z[12];
     const S two = cst<S>(2.0);
@@ -97,8 +106,8 @@ __device__ void dyn(const OrbitDev& o, const S* z, const S* y, S* k) {
     const S R20 = two * (q1 * q3 - q0 * q2), R21 = two * (q2 * q3 + q0 * q1), R22 = q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3;
     S F[3], T[3];
     for (int j = 0; j < 3; ++j) {
-        F[j] = o.P * (cst<S>((double)o.out_std[j]) * y[j] + cst<S>((double)o.out_mean[j]));
-        T[j] = o.P * (cst<S>((double)o.out_std[3 + j]) * y[3 + j] + cst<S>((double)o.out_mean[3 + j]));
+        F[j] = (nu * o.P) * (cst<S>((double)o.out_std[j]) * y[j] + cst<S>((double)o.out_mean[j]));
+        T[j] = (nu * o.P) * (cst<S>((double)o.out_std[3 + j]) * y[3 + j] + cst<S>((double)o.out_mean[3 + j]));
     }
     // gravity: two-body + J2
     const S r2 = x * x + yy * yy + zz * zz;
@@ -112,6 +121,19 @@ __device__ void dyn(const OrbitDev& o, const S* z, const S* y, S* k) {
     k[3] = im * (R00 * F[0] + R01 * F[1] + R02 * F[2]) + c1 * x + kj * x * (one - f5);
     k[4] = im * (R10 * F[0] + R11 * F[1] + R12 * F[2]) + c1 * yy + kj * yy * (one - f5);
     k[5] = im * (R20 * F[0] + R21 * F[1] + R22 * F[2]) + c1 * zz + kj * zz * (three - f5);
+    // point masses at fixed positions: GM [(s - r)/|s - r|^3 - s/|s|^3]
+    for (int b = 0; b < 2; ++b) {
+        if (o.gm3[b] == 0.0) continue;
+        const double* sp = o.pos3[b];
+        const S dx = cst<S>(sp[0]) - x, dy = cst<S>(sp[1]) - yy, dz = cst<S>(sp[2]) - zz;
+        const S d2 = dx * dx + dy * dy + dz * dz;
+        const S g = cst<S>(o.gm3[b]) / (d2 * dsqrt(d2));
+        const double s2 = sp[0] * sp[0] + sp[1] * sp[1] + sp[2] * sp[2];
+        const double gs = o.gm3[b] / (s2 * std::sqrt(s2));
+        k[3] = k[3] + g * dx - cst<S>(gs * sp[0]);
+        k[4] = k[4] + g * dy - cst<S>(gs * sp[1]);
+        k[5] = k[5] + g * dz - cst<S>(gs * sp[2]);
+    }
     const S half = cst<S>(0.5);
     k[6] = half * (-(q1 * w0) - q2 * w1 - q3 * w2);
     k[7] = half * (q0 * w0 + q2 * w2 - q3 * w1);
@@ -445,6 +467,9 @@ extern "C" void srp_orbit_opts_default(srp_orbit_opts* o) {
     o->dt = 60.0; o->n_steps = 1440; o->ckpt_every = 0; o->model = SRP_FM_NONE; o->n_theta = 1;
     for (int j = 0; j < 19; ++j) o->in_scale[j] = 1.0f;
     for (int j = 0; j < 6; ++j) o->out_std[j] = 1.0f;
+    o->eclipse = 0;
+    o->gm_sun = 0.0; o->sun_dist = 1.495978707e11;
+    o->gm_moon = 0.0;
 }
 
 extern "C" int srp_integrate(srp_ctx* c, const srp_orbit_opts* oo, const srp_mlp* proxy, int n_traj,
@@ -459,6 +484,12 @@ extern "C" int srp_integrate(srp_ctx* c, const srp_orbit_opts* oo, const srp_mlp
         return ofail(SRP_EINVAL, "srp_integrate: the proxy model needs an srp_mlp and n_theta = 16");
     if (!(oo->mass > 0) || !(oo->inertia[0] > 0) || !(oo->inertia[1] > 0) || !(oo->inertia[2] > 0))
         return ofail(SRP_EINVAL, "srp_integrate: mass and inertia must be positive");
+    if (oo->eclipse != 0 && oo->eclipse != 1) return ofail(SRP_EINVAL, "srp_integrate: eclipse must be 0 or 1");
+    if (!std::isfinite(oo->gm_sun) || !std::isfinite(oo->gm_moon) || oo->gm_sun < 0.0 || oo->gm_moon < 0.0)
+        return ofail(SRP_EINVAL, "srp_integrate: third-body GM must be finite and >= 0");
+    if (oo->gm_sun > 0.0 && !(oo->sun_dist > 0.0)) return ofail(SRP_EINVAL, "srp_integrate: sun_dist must be > 0");
+    if (oo->gm_moon > 0.0 && !(oo->moon[0] * oo->moon[0] + oo->moon[1] * oo->moon[1] + oo->moon[2] * oo->moon[2] > 0.0))
+        return ofail(SRP_EINVAL, "srp_integrate: the moon position must be non-zero");
     if (n_traj == 0) return SRP_OK;
     if (!z0 || !theta || !zN) return ofail(SRP_EINVAL, "srp_integrate: NULL z0/theta/zN");
     const bool adj = dL_dzN != nullptr;
@@ -470,6 +501,9 @@ extern "C" int srp_integrate(srp_ctx* c, const srp_orbit_opts* oo, const srp_mlp
     o.mu = oo->mu; o.j2 = oo->j2; o.re = oo->re; o.mass = oo->mass;
     for (int j = 0; j < 3; ++j) { o.I[j] = oo->inertia[j]; o.sun[j] = oo->sun[j]; }
     o.P = oo->pressure; o.dt = oo->dt; o.n_steps = oo->n_steps; o.model = oo->model; o.n_theta = oo->n_theta;
+    o.eclipse = oo->eclipse;
+    o.gm3[0] = oo->gm_sun; o.gm3[1] = oo->gm_moon;
+    for (int j = 0; j < 3; ++j) { o.pos3[0][j] = oo->sun_dist * oo->sun[j]; o.pos3[1][j] = oo->moon[j]; }
     int C = oo->ckpt_every > 0 ? oo->ckpt_every : (int)std::ceil(std::sqrt((double)std::max(1, oo->n_steps)));
     C = std::max(1, std::min(C, kMaxCkptSeg));
     o.ckpt = C;

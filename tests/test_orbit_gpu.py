@@ -123,3 +123,33 @@ def test_design_optimisation_loop(srp):
     assert losses[-1] < 1e-4 * losses[0], losses[[0, -1]]
     # the loss fell 1e4x: the error of theta fell ~100x from the 12-unit start
     assert abs(th[0] - 30.0) < 0.2
+
+
+def test_eclipse_and_third_bodies_parity(srp):
+    """Cannonball SRP with the cylinder eclipse and Sun/Moon point masses on
+    a LEO orbit that passes through the Earth's shadow: trajectory and
+    adjoint (dL/dtheta, dL/dz0) against the oracle's RK4 and complex-step
+    gradient; the eclipse must change the result."""
+    ctx = srp.Context(0)
+    P = 4.56e-6 * 50.0
+    sun = np.array([1.0, 0.0, 0.0])
+    moon = np.array([0.0, 3.844e8, 1.0e7])
+    kw = dict(model=srp.SRP_FM_CANNONBALL, pressure=P, mass=100.0, sun=sun, dt=30.0, n_steps=300, n_theta=1,
+              ckpt_every=20, gm_sun=1.32712440018e20, sun_dist=1.495978707e11, gm_moon=4.9028e12, moon=moon)
+    z0 = O.circular_state(7.0e6, 0.2, u=1.2)
+    th = np.array([4.0])
+    wN = np.random.default_rng(1).normal(size=13) * np.array([1e-3] * 3 + [1.0] * 3 + [1e3] * 4 + [1e4] * 3)
+    r = srp.srp_integrate(ctx, srp.orbit_opts(eclipse=1, **kw), z0, th, dL_dzN=wN)
+    m = O.Model("cannonball", P=P, mass=100.0, sun=sun, eclipse=True, gm_sun=1.32712440018e20,
+                sun_dist=1.495978707e11, gm_moon=4.9028e12, moon=moon)
+    zo, tr = O.rk4(m, z0, th, 30.0, 300, keep=True)
+    shadow = [m.in_shadow(z[:3]) for z in tr]
+    assert any(shadow) and not all(shadow)
+    assert np.allclose(r["zN"][0], zo, rtol=1e-12, atol=1e-6)
+    gt, gz = O.cs_grad(m, z0, th, 30.0, 300, wN)
+    assert abs(r["dL_dtheta"][0, 0] - gt[0]) <= 1e-7 * abs(gt[0]) + 1e-15, (r["dL_dtheta"], gt)
+    assert np.allclose(r["dL_dz0"][0], gz, rtol=1e-7, atol=1e-12 * np.abs(gz).max())
+    r0 = srp.srp_integrate(ctx, srp.orbit_opts(eclipse=0, **kw), z0, th)
+    assert np.linalg.norm(r0["zN"][0][:3] - r["zN"][0][:3]) > 1.0
+    with pytest.raises(srp.SRPError, match="SRP_EINVAL"):
+        srp.srp_integrate(ctx, srp.orbit_opts(eclipse=2, **kw), z0, th)
