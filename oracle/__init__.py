@@ -26,6 +26,10 @@ paper's definitions:
                           expected 2/3 recoil at the emitting surface plus
                           the closed-form deposit where emitted packets hit
                           the spacecraft; ``thermal_counts`` its allocation.
+* ``trace_samples``    -- per-sample designs (Sec. 3.2 "Estimation", Alg. 1
+                          NNLoss): each sample instantiates its own design
+                          and traces one jittered ray over a fixed square by
+                          brute force.
 * ``instantiate``      -- design instantiation: hinge rotations of the
                           panel vertices (Rodrigues' formula).
 * ``philox``           -- Philox4x32-10 (Salmon et al., SC'11).
@@ -92,6 +96,9 @@ def _load():
         lib.or_thermal_counts.restype = i64
         lib.or_force_thermal.argtypes = [P, i32, P, P, i32, P, P, P, C.c_float, u64, f64, u32, i32, P, P, P]
         lib.or_force_thermal.restype = i32
+        lib.or_trace_samples.argtypes = [P, i32, P, P, i32, P, P, i32, P, P, i32, P, P, i64, P, f64, i32, u64, f64,
+                                         u32, i32, P, P]
+        lib.or_trace_samples.restype = i32
         _lib = lib
     return _lib
 
@@ -247,6 +254,24 @@ def force_thermal(verts, tris, group, rho, emit, com, *, density, seed=0, P=1.0,
     lib.or_force_thermal(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(e), _p(cm), float(density), seed,
                          P, design_index, threads or os.cpu_count() or 1, _p(ft), _p(sg), _p(n))
     return ft, sg, int(n[0])
+
+
+def trace_samples(verts, vhinge, hinges, tris, group, angles, rho, sun, com, center, R, *, K=1, seed=0, P=1.0,
+                  sample_base=0, threads=None):
+    """Per-sample designs: (y [N,6], hits [N,K]) of one jittered ray per
+    sample over its own instantiated mesh (brute force)."""
+    lib = _load()
+    v = _c(verts, np.float32); vh = _c(vhinge, np.int32); hg = _c(np.reshape(hinges, (-1, 6)), np.float64)
+    t = _c(tris, np.int32); g = _c(group, np.int32)
+    an = _c(np.reshape(angles, (np.shape(angles)[0], -1)), np.float64)
+    r = _c(rho, np.float64); sn = _c(sun, np.float64); cm = _c(com, np.float64); ce = _c(center, np.float64)
+    N = sn.shape[0]
+    H = hg.shape[0]
+    y = np.zeros((N, 6)); hits = np.zeros((N, K), np.int32)
+    lib.or_trace_samples(_p(v), v.shape[0], _p(vh), _p(hg), H, _p(t), _p(g), t.shape[0], _p(an), _p(r), r.shape[-2],
+                         _p(sn), _p(cm), N, _p(ce), float(R), K, seed, P, sample_base, threads or os.cpu_count() or 1,
+                         _p(y), _p(hits))
+    return y, hits
 
 
 def primary_hit(verts, tris, sun, i, *, nx, ny=None, jitter=1, seed=0, sun_index=0, design_index=0):

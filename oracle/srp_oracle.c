@@ -978,3 +978,95 @@ int or_force_thermal(const float* verts, int V, const int32_t* tris, const int32
     free(jb); free(th); free(y); free(prefix); free(counts); free(tv); free(tn);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Per-sample designs (the paper's training-data sampler, Sec. 3.2      */
+/* "Estimation" and Alg. 1 NNLoss: every sample has its own design and  */
+/* sun direction; intersection by brute force over its triangles):       */
+/*  - sample s instantiates the base mesh with its hinge angles          */
+/*    angles[s][H] (Rodrigues in FP64, rounded to float32);              */
+/*  - its ray is the single jittered pixel of a 1 x 1 grid over the      */
+/*    square of side 2R about the given centre c (c, R must bound every  */
+/*    design): Philox counter (0, sample_base + s, 2^29, k), weight       */
+/*    P (2R)^2; then the grid estimator's path (K bounces) with the      */
+/*    sample's reflectances rho[s][G][2] and torque reference com[s];    */
+/*  - out_y[s][6] is the sample's (F, tau) estimate, out_hits[s][K] the   */
+/*    hit triangles (-1 after the path ends).                             */
+/* ------------------------------------------------------------------ */
+static void rot_hinge(const double* hinge, double angle, double R[9])
+{
+    const double* a = hinge + 3;
+    const double nrm = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double x = a[0] / nrm, y = a[1] / nrm, z = a[2] / nrm;
+    const double c = cos(angle), s = sin(angle), t = 1.0 - c;
+    R[0] = c + x * x * t;     R[1] = x * y * t - z * s; R[2] = x * z * t + y * s;
+    R[3] = y * x * t + z * s; R[4] = c + y * y * t;     R[5] = y * z * t - x * s;
+    R[6] = z * x * t - y * s; R[7] = z * y * t + x * s; R[8] = c + z * z * t;
+}
+
+typedef struct {
+    const float* verts; int V; const int32_t* vhinge; const double* hinges; int H;
+    const int32_t* tris; const int32_t* group; int T;
+    const double* angles; const double* rho; int G; const double* sun; const double* com;
+    const double* center; double R; int K; uint64_t seed; double P; uint32_t sample_base;
+    double* out_y; int32_t* out_hits;
+    int64_t s0, s1;
+} samp_job;
+
+static void* samp_worker(void* arg)
+{
+    samp_job* jb = (samp_job*)arg;
+    float* v = (float*)malloc(sizeof(float) * 3 * (size_t)(jb->V > 0 ? jb->V : 1));
+    double* tv = (double*)malloc(sizeof(double) * 9 * (size_t)(jb->T > 0 ? jb->T : 1));
+    double* tn = (double*)malloc(sizeof(double) * 3 * (size_t)(jb->T > 0 ? jb->T : 1));
+    double* Rm = (double*)malloc(sizeof(double) * 9 * (size_t)(jb->H > 0 ? jb->H : 1));
+    for (int64_t s = jb->s0; s < jb->s1; ++s) {
+        for (int h = 0; h < jb->H; ++h) rot_hinge(jb->hinges + 6 * h, jb->angles[(size_t)s * jb->H + h], Rm + 9 * h);
+        for (int q = 0; q < jb->V; ++q) {
+            const int h = jb->H > 0 ? jb->vhinge[q] : -1;
+            if (h < 0) { for (int j = 0; j < 3; ++j) v[3 * q + j] = jb->verts[3 * q + j]; continue; }
+            const double* p = jb->hinges + 6 * h;
+            const double* R = Rm + 9 * h;
+            const double w[3] = {jb->verts[3 * q] - p[0], jb->verts[3 * q + 1] - p[1], jb->verts[3 * q + 2] - p[2]};
+            for (int j = 0; j < 3; ++j) v[3 * q + j] = (float)(p[j] + R[3 * j] * w[0] + R[3 * j + 1] * w[1] + R[3 * j + 2] * w[2]);
+        }
+        scene_t sc;
+        memset(&sc, 0, sizeof sc);
+        build_scene(&sc, tv, tn, v, jb->V, jb->tris, jb->T);
+        for (int j = 0; j < 3; ++j) { sc.c[j] = jb->center[j]; sc.com[j] = jb->com[3 * (size_t)s + j]; }
+        sc.R = jb->R;
+        sc.group = jb->group;
+        sc.rho = jb->rho + (size_t)s * jb->G * 2;
+        sc.P = jb->P; sc.nx = 1; sc.ny = 1; sc.K = jb->K; sc.jitter = 1;
+        sc.seed = jb->seed; sc.dsg = 0x20000000u;
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        path_t pth;
+        trace_path(&sc, jb->sun + 3 * (size_t)s, 0u, jb->sample_base + (uint32_t)s, acc, &pth);
+        for (int q = 0; q < 6; ++q) jb->out_y[6 * (size_t)s + q] = acc[q];
+        if (jb->out_hits)
+            for (int k = 0; k < jb->K; ++k) jb->out_hits[(size_t)s * jb->K + k] = k < pth.m ? pth.f[k] : -1;
+    }
+    free(v); free(tv); free(tn); free(Rm);
+    return NULL;
+}
+
+int or_trace_samples(const float* verts, int V, const int32_t* vhinge, const double* hinges, int H,
+                     const int32_t* tris, const int32_t* group, int T, const double* angles, const double* rho, int G,
+                     const double* sun, const double* com, int64_t N, const double* center, double R, int K,
+                     uint64_t seed, double P, uint32_t sample_base, int threads, double* out_y, int32_t* out_hits)
+{
+    if (threads < 1) threads = 1;
+    if (threads > N) threads = N > 0 ? (int)N : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * threads);
+    samp_job* jb = (samp_job*)calloc(threads, sizeof(samp_job));
+    for (int t = 0; t < threads; ++t) {
+        samp_job j = {verts, V, vhinge, hinges, H, tris, group, T, angles, rho, G, sun, com, center, R, K, seed, P,
+                      sample_base, out_y, out_hits, N * t / threads, N * (t + 1) / threads};
+        jb[t] = j;
+    }
+    for (int t = 1; t < threads; ++t) pthread_create(&th[t], NULL, samp_worker, &jb[t]);
+    samp_worker(&jb[0]);
+    for (int t = 1; t < threads; ++t) pthread_join(th[t], NULL);
+    free(jb); free(th);
+    return 0;
+}

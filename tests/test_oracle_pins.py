@@ -386,3 +386,68 @@ def test_thermal_reflector_push(rho_hit):
     free = (2.0 / 3.0) * 0.04
     want = 0.0 if rho_hit == (0.0, 0.0) else free
     assert abs(ft[2] - want) < 0.01 * free + 4 * sg[2]
+
+
+# ---------------------------------------------------------------- per-sample designs (Sec. 3.2, Alg. 1 NNLoss)
+def _boxwing_absorber_samples(angles, N, seed):
+    m = W.box_wing()
+    e = np.array([0.0, 0.0, 1.0])
+    R = 6.0
+    y, hits = oracle.trace_samples(m.verts, m.vhinge, m.hinges, m.tris, m.group, angles,
+                                   np.zeros((N, 64, 2)), np.tile(e, (N, 1)), np.zeros((N, 3)), np.zeros(3), R,
+                                   K=1, seed=seed, P=1.0)
+    return y, hits, R
+
+
+def test_samples_absorbing_boxwing_projected_area():
+    """Absorbing box-wing lit along -z: the panels (5 x 2 m, hinged about y
+    beside the bus) project 10 cos(theta) each and the bus top 1 m^2, with no
+    mutual shadowing, so one ray over the 12 x 12 m square deposits
+    P (2R)^2 d with probability A_proj / (2R)^2: per design the mean is
+    -P (1 + 10 cos t1 + 10 cos t2) z, and over theta ~ U[-pi/2, pi/2]^2 it is
+    -P (1 + 40/pi) z.  4 sigma of the binomial spread."""
+    N = 1 << 17
+    rng = np.random.default_rng(1)
+    ang = rng.uniform(-np.pi / 2, np.pi / 2, size=(N, 2))
+    y, hits, R = _boxwing_absorber_samples(ang, N, seed=5)
+    A = 4 * R * R
+    p = (1.0 + 40.0 / np.pi) / A
+    mean = y[:, 2].mean()
+    sd = A * np.sqrt(p * (1 - p) / N) * 1.2          # (the per-design p varies; 20 % margin on the spread)
+    assert abs(mean + (1.0 + 40.0 / np.pi)) <= 4 * sd, (mean, sd)
+    assert np.all(np.abs(y[:, :2]) <= 1e-9 * A)
+    # conditional: fixed angles
+    fixed = np.tile([0.7, -0.2], (N, 1))
+    y2, _, _ = _boxwing_absorber_samples(fixed, N, seed=6)
+    want = 1.0 + 10 * np.cos(0.7) + 10 * np.cos(0.2)
+    p2 = want / A
+    assert abs(y2[:, 2].mean() + want) <= 4 * A * np.sqrt(p2 * (1 - p2) / N)
+
+
+def test_samples_design_changes_hits():
+    """A panel rotated by 90 degrees is edge-on to a sun along z: no sample
+    hits it; at 0 degrees it is hit."""
+    N = 4096
+    m = W.box_wing()
+    e = np.tile([0.0, 0.0, 1.0], (N, 1))
+    y, hits = oracle.trace_samples(m.verts, m.vhinge, m.hinges, m.tris, m.group, np.tile([np.pi / 2, 0.0], (N, 1)),
+                                   np.zeros((N, 64, 2)), e, np.zeros((N, 3)), np.zeros(3), 6.0, K=1, seed=2)
+    assert not np.any(np.isin(hits[:, 0], [12, 13]))          # panel 1 (triangles 12, 13) edge-on
+    assert np.any(np.isin(hits[:, 0], [14, 15]))
+
+
+def test_samples_mean_matches_grid_estimate():
+    """With one fixed design, the mean of the per-sample estimates (one ray
+    each, K = 3, reflective materials) converges to the ray-grid estimate of
+    the same design: 4 sigma of the sample mean."""
+    m, rho, _, com = W.config1()
+    N = 1 << 16
+    ang = np.tile([0.4, -0.6], (N, 1))
+    v = oracle.instantiate(m.verts, m.vhinge, m.hinges, ang[0])
+    e = np.array([0.3, -0.2, 0.9]); e /= np.linalg.norm(e)
+    c, R = oracle.grid(v)
+    y, _ = oracle.trace_samples(m.verts, m.vhinge, m.hinges, m.tris, m.group, ang, np.tile(rho, (N, 1, 1)),
+                                np.tile(e, (N, 1)), np.tile(com, (N, 1)), c, R, K=3, seed=4)
+    fg, sg = oracle.force(v, m.tris, m.group, rho, e[None], com, nx=512, K=3, seed=1)
+    se = y.std(axis=0) / np.sqrt(N)
+    assert np.all(np.abs(y.mean(axis=0) - fg[0]) <= 4 * np.sqrt(se ** 2 + sg[0] ** 2) + 1e-12)
