@@ -230,6 +230,30 @@ int srp_force_thermal(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const flo
                       const float* emit, const double* com, float density, const srp_trace_opts* opts,
                       double* out_ft, double* out_sigma, int64_t* out_samples);
 
+/* ---- a design per sample (Sec. 3.2 "Estimation": each sample meets its
+ * own design, so the intersection is brute force over that design's
+ * triangles; Alg. 1 NNLoss draws a random design per sample) -------------
+ * Base mesh (host memory always): verts [V][3] float32, vhinge [V] int32
+ * (-1 fixed, else the hinge that moves the vertex), hinges [H][6] float64
+ * (pivot, unit axis; H <= 32), tris [T][3], group [T] in [0, G).
+ * Per sample s (opts->mem): angles [N][H] float64 hinge angles, rho
+ * [N][G][2] float32, sun [N][3] float64 unit vectors toward the sun, com
+ * [N][3] float64; out_y [N][6] float64 the sample's (F, tau) estimate,
+ * out_hits [N][K] int32 hit triangles (-1 after the path ends) or NULL.
+ * Sample s instantiates the mesh (vertex rotated about its hinge pivot by
+ * its angle, Rodrigues) and traces the jittered single pixel of a 1 x 1 grid
+ * over the square of side 2*radius about center (which must bound every
+ * design): Philox4x32-10 counter (0, opts->sun_base + s, 2^29, k), key
+ * (seed lo, hi), weight pressure * (2 radius)^2, then srp_force's path
+ * (max_bounces K <= 3, same shading, ties and t_min = 1e-6 radius).  Each
+ * sample is one unbiased estimate of srp_force for its design and sun.
+ * Shared memory bounds the mesh: 48 (T + H) bytes per warp <= 227 KB
+ * (T <= ~4800), else SRP_EUNSUPPORTED.  N < 2^32. */
+int srp_trace_samples(srp_ctx* ctx, const float* verts, int V, const int32_t* vhinge, const double* hinges, int H,
+                      const int32_t* tris, const int32_t* group, int T, const double* angles, const float* rho,
+                      int G, const double* sun, const double* com, int64_t N, const double* center, double radius,
+                      const srp_trace_opts* opts, double* out_y, int32_t* out_hits);
+
 /* ---- gradient (Sec. 4.1: the simulation is differentiable by construction
  * in continuous parameters such as reflectance; Sec. 3.4 design parameters)
  * For ONE design (bvh) and S sun directions, with upstream weights

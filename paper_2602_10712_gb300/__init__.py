@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
-           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_force_noalloc", "srp_force_area", "srp_force_thermal", "srp_force_grad", "SRPForce", "MLP",
+           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_force_noalloc", "srp_force_area", "srp_force_thermal", "srp_trace_samples", "srp_force_grad", "SRPForce", "MLP",
            "mlp_param_count", "srp_integrate", "orbit_opts", "OrbitOpts", "ForceGraph",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
@@ -74,6 +74,8 @@ def load(build_if_needed: bool = True):
     lib.srp_bvh_get_info.argtypes = [_P, C.POINTER(BVHInfo)]
     lib.srp_force.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P]
     lib.srp_force_area.argtypes = [_P, _P, i32, _P, i32, _P, i32, _P, C.c_float, C.POINTER(TraceOpts), _P, _P, _P]
+    lib.srp_trace_samples.argtypes = [_P, _P, i32, _P, _P, i32, _P, _P, i32, _P, _P, i32, _P, _P, i64, _P, C.c_double,
+                                      C.POINTER(TraceOpts), _P, _P]
     lib.srp_force_thermal.argtypes = [_P, _P, i32, _P, i32, _P, _P, C.c_float, C.POINTER(TraceOpts), _P, _P, _P]
     lib.srp_collect_stats.argtypes = [_P, i32, _P]
     lib.srp_bvh_set_nodes.argtypes = [_P, _P, _P, i64]
@@ -404,6 +406,44 @@ def srp_force_thermal(ctx: Context, bvhs, rho, emit, com, density, out_ft=None, 
     if out_samples is not None:
         res.append(out_samples)
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def srp_trace_samples(ctx: Context, mesh_verts, vhinge, hinges, tris, group, angles, rho, sun, com, center, radius,
+                      out_y=None, want_hits=False, **opts):
+    """Per-sample designs: one jittered ray per sample over its own
+    instantiated mesh (brute force).  The mesh is numpy (host); angles,
+    rho [N,G,2], sun [N,3], com [N,3] numpy (host mode) or CUDA tensors
+    (device mode).  Returns y [N,6] (and hits [N,K])."""
+    lib = load()
+    v = _np(mesh_verts, np.float32).reshape(-1, 3)
+    vh = _np(vhinge, np.int32).reshape(-1)
+    hg = _np(hinges, np.float64).reshape(-1, 6)
+    t = _np(tris, np.int32).reshape(-1, 3)
+    g = _np(group, np.int32).reshape(-1)
+    H = hg.shape[0]
+    K = opts.get("max_bounces", 1)
+    ce = _np(center, np.float64).reshape(3)
+    if isinstance(sun, np.ndarray):
+        sun = _np(sun, np.float64).reshape(-1, 3)
+        N = sun.shape[0]
+        angles = _np(angles, np.float64).reshape(N, max(H, 1) if H else 0) if H else np.zeros((N, 0))
+        rho = _np(rho, np.float32)
+        com = _np(com, np.float64).reshape(N, 3)
+        y = np.zeros((N, 6)) if out_y is None else out_y
+        hits = np.zeros((N, K), np.int32) if want_hits else None
+        opts["mem"] = SRP_MEM_HOST
+    else:
+        import torch
+        N = sun.shape[0]
+        y = torch.empty((N, 6), dtype=torch.float64, device=sun.device) if out_y is None else out_y
+        hits = torch.empty((N, K), dtype=torch.int32, device=sun.device) if want_hits else None
+        opts.setdefault("mem", SRP_MEM_DEVICE)
+    G = rho.shape[-2]
+    o = make_opts(**opts)
+    _check(lib.srp_trace_samples(ctx.handle, _ptr(v), v.shape[0], _ptr(vh), _ptr(hg), H, _ptr(t), _ptr(g), t.shape[0],
+                                 _ptr(angles), _ptr(rho), G, _ptr(sun), _ptr(com), N, _ptr(ce), float(radius),
+                                 C.byref(o), _ptr(y), _ptr(hits) if hits is not None else None))
+    return (y, hits) if want_hits else y
 
 
 def srp_trace_rays(ctx: Context, bvh: BVH, rho, sun_dir, com, ray_idx, sun_index=0, design_index=0, **opts):

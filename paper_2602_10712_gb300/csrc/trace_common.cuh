@@ -358,10 +358,10 @@ struct HitGeom {
     int g;         // material group
 };
 
-__device__ __forceinline__ HitGeom hit_geom(const DesignDev& dz, const ItemConst& ic, int f, float t, const Seg& s) {
-    const float4 a = __ldg(dz.tri + 3 * (size_t)f);
-    const float4 b = __ldg(dz.tri + 3 * (size_t)f + 1);
-    const float4 c = __ldg(dz.tri + 3 * (size_t)f + 2);
+// Geometry and material of a hit at parameter t on the triangle with vertices
+// (a, b, c) (group id in b.w).
+__device__ __forceinline__ HitGeom hit_geom_v(float4 a, float4 b, float4 c, const ItemConst& ic, float t,
+                                              const Seg& s) {
     float3 n = cross(xyz(b) - xyz(a), xyz(c) - xyz(a));
     n = rsqrtf(dot(n, n)) * n;
     if (dot(n, s.d) > 0.0f) n = -1.0f * n;
@@ -373,6 +373,11 @@ __device__ __forceinline__ HitGeom hit_geom(const DesignDev& dz, const ItemConst
     h.rd = __ldg(ic.rho + 2 * h.g + 1);
     h.x = s.o + t * s.d;
     return h;
+}
+
+__device__ __forceinline__ HitGeom hit_geom(const DesignDev& dz, const ItemConst& ic, int f, float t, const Seg& s) {
+    return hit_geom_v(__ldg(dz.tri + 3 * (size_t)f), __ldg(dz.tri + 3 * (size_t)f + 1),
+                      __ldg(dz.tri + 3 * (size_t)f + 2), ic, t, s);
 }
 
 // Sampled reflection at hit k < K: branch 0 specular (weight 2 w rs),
@@ -399,10 +404,10 @@ __device__ __forceinline__ int bounce_dir(const ItemConst& ic, const TraceParams
 
 // Momentum deposit of hit k (1-based) on leaf-order triangle f at ray
 // parameter t; returns true (and the outgoing segment) if the path goes on.
-__device__ __forceinline__ bool shade_hit(const DesignDev& dz, const ItemConst& ic, const TraceParams& p,
-                                          uint32_t i, int k, int f, float t, const Seg& s, float y[6],
-                                          Seg& out) {
-    const HitGeom h = hit_geom(dz, ic, f, t, s);
+// Deposit of hit k of segment s with geometry h (triangle f); returns true
+// and the next segment when the path continues (k < K).
+__device__ __forceinline__ bool shade_core(const HitGeom& h, const ItemConst& ic, const TraceParams& p, uint32_t i,
+                                           int k, int f, const Seg& s, float y[6], Seg& out) {
     const float3 arm = h.x - ic.com;
     if (k == p.K) {
         const float cn = 2.0f * h.rs * h.cs + (2.0f / 3.0f) * h.rd;
@@ -419,6 +424,12 @@ __device__ __forceinline__ bool shade_hit(const DesignDev& dz, const ItemConst& 
     y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
     out.o = h.x; out.d = dout; out.w = wout; out.src = f;
     return true;
+}
+
+__device__ __forceinline__ bool shade_hit(const DesignDev& dz, const ItemConst& ic, const TraceParams& p,
+                                          uint32_t i, int k, int f, float t, const Seg& s, float y[6],
+                                          Seg& out) {
+    return shade_core(hit_geom(dz, ic, f, t, s), ic, p, i, k, f, s, y, out);
 }
 
 
