@@ -297,6 +297,7 @@ def run_ours(args, ws, rank, local):
     }
     if rank == 0 and not args.no_extra:
         line["area_estimator"] = area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, args.width)
+        line["per_sample_designs"] = samples_leg(srp, ctx, dev, sm_mhz)
         line["surrogate"], line["grad"] = extra_legs(srp, ctx, dev, peaks)
     if rank == 0 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
@@ -505,6 +506,59 @@ def area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, width):
                                        "efficiency = (var x time)_grid / (var x time)_area, > 1 favours the area "
                                        "estimator; max_z = largest |F_area - F_grid| / combined sigma"},
             "gpu_launches_per_call": 4, "thermal": thermal}
+
+
+def samples_leg(srp, ctx, dev, sm_mhz):
+    """Per-sample designs (srp_trace_samples): the paper's training-data
+    sampler, every sample with its own random hinge angles, reflectances
+    and sun, brute force over its triangles; against rebuilding a BVH per
+    sample (host build time of one design)."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    out = []
+    cases = [("box-wing", W.box_wing(), 6.0, 1 << 22),
+             ("satellite 3,232 tris", W.procedural_satellite(dish_segments=64, dish_rings=20, n_boxes=60), 7.0, 1 << 18),
+             ("satellite 49,776 tris", W.procedural_satellite(), 7.0, 1 << 14)]
+    for name, m, R, N in cases:
+        rng = np.random.default_rng(0)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        ang = t(rng.uniform(-np.pi / 2, np.pi / 2, size=(N, m.hinges.shape[0])))
+        rho = t(rng.uniform(0.0, 0.5, size=(N, 64, 2)).astype(np.float32))
+        sun = rng.normal(size=(N, 3))
+        sun = t(sun / np.linalg.norm(sun, axis=1, keepdims=True))
+        com = t(np.zeros((N, 3)))
+        T = int(m.tris.shape[0])
+        row = {"case": name, "T": T, "samples": N}
+        for K in (1, 3):
+            y = srp.srp_trace_samples(ctx, m.verts, m.vhinge, m.hinges, m.tris, m.group, ang, rho, sun, com,
+                                      np.zeros(3), R, max_bounces=K)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            srp.srp_trace_samples(ctx, m.verts, m.vhinge, m.hinges, m.tris, m.group, ang, rho, sun, com, np.zeros(3),
+                                  R, max_bounces=K, out_y=y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[f"samples_per_s_K{K}"] = N / ms * 1e3
+            if K == 1:   # exactly N x T triangle tests at K = 1
+                tests = N * T / (ms / 1e3)
+                row["tri_tests_per_s_K1"] = tests
+                row["roofline_K1"] = {"bound": "alu", "achieved": tests * 44 / 1e12, "peak": peak_alu,
+                                      "unit": "TFLOP/s", "frac": tests * 44 / 1e12 / peak_alu, "traffic": None}
+        v = srp.srp_design_instantiate(m.verts, m.vhinge, m.hinges, np.array([0.3, -0.2]))
+        t0 = time.perf_counter()
+        reps = 3 if T > 10000 else 20
+        for _ in range(reps):
+            srp.srp_build_bvh_host(v, m.tris, 4)
+        bms = (time.perf_counter() - t0) / reps * 1e3
+        row["bvh_build_ms_per_design"] = bms
+        row["bvh_rebuild_samples_per_s_bound"] = 1e3 / bms
+        out.append(row)
+    return {"cases": out, "note": "srp_trace_samples: warp per sample, brute force (the paper's per-sample design "
+                                  "workload); the BVH route must build one BVH per sample (host build time shown); "
+                                  "roofline counts 44 FP32 ops per triangle test at K = 1 (N x T tests)"}
 
 
 def run_profile_case(case):

@@ -247,8 +247,9 @@ int srp_force_thermal(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const flo
  * (seed lo, hi), weight pressure * (2 radius)^2, then srp_force's path
  * (max_bounces K <= 3, same shading, ties and t_min = 1e-6 radius).  Each
  * sample is one unbiased estimate of srp_force for its design and sun.
- * Shared memory bounds the mesh: 48 (T + H) bytes per warp <= 227 KB
- * (T <= ~4800), else SRP_EUNSUPPORTED.  N < 2^32. */
+ * Meshes of up to 256 triangles are instantiated once per sample into
+ * shared memory; larger ones are instantiated triangle by triangle as they
+ * are tested.  T < 2^24, N < 2^32. */
 int srp_trace_samples(srp_ctx* ctx, const float* verts, int V, const int32_t* vhinge, const double* hinges, int H,
                       const int32_t* tris, const int32_t* group, int T, const double* angles, const float* rho,
                       int G, const double* sun, const double* com, int64_t N, const double* center, double radius,

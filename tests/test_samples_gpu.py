@@ -59,7 +59,7 @@ def test_boxwing_per_sample_parity(srp, ctx, K):
     yo, ho = oracle.trace_samples(m.verts, m.vhinge, m.hinges, m.tris, m.group, ang, rho, sun, com, center, R, K=K,
                                   seed=7, P=2.0, sample_base=100)
     same = _compare(y, h, yo, ho, 2.0 * (2 * R) ** 2, R)
-    assert np.count_nonzero(h[:, 0] >= 0) > N // 10     # the rays do hit
+    assert np.count_nonzero(h[:, 0] >= 0) > N // 20     # the rays do hit (~8 % of the square)
 
 
 def test_satellite_per_sample_parity_and_device_mode(srp, ctx):
@@ -80,6 +80,20 @@ def test_satellite_per_sample_parity_and_device_mode(srp, ctx):
                                    center, R, want_hits=True, max_bounces=3, seed=3)
     torch.cuda.synchronize()
     assert np.array_equal(yd.cpu().numpy(), y) and np.array_equal(hd.cpu().numpy(), h)
+
+
+def test_full_satellite_streaming_parity(srp, ctx):
+    """The 49,776-triangle satellite (streaming instantiation: each test
+    rotates its triangle from the base mesh), K = 2."""
+    m = W.procedural_satellite()
+    N = 512
+    ang, rho, sun, com = _inputs(m, N, 64, seed=21)
+    center, R = np.zeros(3), 7.0
+    y, h = srp.srp_trace_samples(ctx, m.verts, m.vhinge, m.hinges, m.tris, m.group, ang, rho, sun, com, center, R,
+                                 want_hits=True, max_bounces=2, seed=5)
+    yo, ho = oracle.trace_samples(m.verts, m.vhinge, m.hinges, m.tris, m.group, ang, rho, sun, com, center, R, K=2,
+                                  seed=5)
+    _compare(y, h, yo, ho, (2 * R) ** 2, R, max_frac=1e-2)
 
 
 def test_projected_area_pin_on_gpu(srp, ctx):
@@ -105,11 +119,6 @@ def test_errors(srp, ctx):
                               np.zeros(3), 6.0)
     with pytest.raises(srp.SRPError, match="SRP_EINVAL"):
         srp.srp_trace_samples(ctx, m.verts, m.vhinge, m.hinges, m.tris, m.group, ang, rho, sun, com, np.zeros(3), 0.0)
-    big = W.procedural_satellite()
-    with pytest.raises(srp.SRPError, match="SRP_EUNSUPPORTED"):
-        srp.srp_trace_samples(ctx, big.verts, big.vhinge, big.hinges, big.tris, big.group, np.zeros((1, 2)),
-                              np.zeros((1, 64, 2), np.float32), np.array([[0.0, 0.0, 1.0]]), np.zeros((1, 3)),
-                              np.zeros(3), 7.0)
     y = srp.srp_trace_samples(ctx, m.verts, m.vhinge, m.hinges, m.tris, m.group, ang[:0], rho[:0], sun[:0], com[:0],
                               np.zeros(3), 6.0)
     assert y.shape == (0, 6)
