@@ -564,6 +564,7 @@ def samples_leg(srp, ctx, dev, sm_mhz):
 def run_profile_case(case):
     """Small cases for ncu captures (3 calls each; capture the third):
     trace -- srp_force on 16 of the 4096 suns x 2048^2 rays, K <= 3;
+    trace_k1 -- the same at K = 1 (primary rays only);
     area  -- srp_force_area on the same 16 suns, ~2048^2 samples each;
     mlp   -- proxy inference on 262,144 queries."""
     import torch
@@ -571,7 +572,7 @@ def run_profile_case(case):
     import paper_2602_10712_gb300 as srp
     ctx = srp.Context(0)
     dev = torch.device("cuda:0")
-    if case == "trace":
+    if case in ("trace", "trace_k1"):
         m, rho, _, com = W.config2(16)
         sun = W.fibonacci_directions(N_SUN)[::256].copy()
         b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
@@ -579,7 +580,7 @@ def run_profile_case(case):
         s_t = torch.from_numpy(sun).to(dev)
         c_t = torch.from_numpy(com[None].copy()).to(dev)
         for _ in range(3):
-            srp.srp_force(ctx, [b], r_t, s_t, c_t, rays_x=NX, max_bounces=K_BOUNCE)
+            srp.srp_force(ctx, [b], r_t, s_t, c_t, rays_x=NX, max_bounces=K_BOUNCE if case == "trace" else 1)
     elif case == "area":
         m, rho, _, com = W.config2(16)
         sun = W.fibonacci_directions(N_SUN)[::256].copy()
@@ -611,7 +612,7 @@ def main():
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
-    ap.add_argument("--profile", choices=["trace", "area", "mlp"], default=None,
+    ap.add_argument("--profile", choices=["trace", "trace_k1", "area", "mlp"], default=None,
                     help="run a small ncu capture case and exit")
     args = ap.parse_args()
     if args.profile:
