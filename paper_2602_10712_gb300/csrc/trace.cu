@@ -55,12 +55,26 @@ struct HitOut {
     uint32_t nvis, ntest;
 };
 
+// dirc (or null): the direction-only parts of RaySetup (1/d and the shear
+// rows), shared by every primary ray of an item and computed once per item
+// by setup_ray; bounce segments pass null and set up in full.  One copy of
+// the traversal serves both (two copies thrashed the instruction cache).
 template <int W>
 __device__ __noinline__ HitOut trace_segment(const float4* __restrict__ nodes, const float4* __restrict__ tri,
                                              float ox, float oy, float oz, float dx, float dy, float dz,
-                                             float tmin, int skip, int* err) {
+                                             float tmin, int skip, const float* dirc, int* err) {
     RaySetup r;
-    setup_ray(r, f3(ox, oy, oz), f3(dx, dy, dz));
+    if (dirc) {
+        r.o = f3(ox, oy, oz);
+        r.d = f3(dx, dy, dz);
+        r.inv = f3(dirc[0], dirc[1], dirc[2]);
+        r.oinv = f3(ox * r.inv.x, oy * r.inv.y, oz * r.inv.z);
+        r.mx = f3(dirc[3], dirc[4], dirc[5]);
+        r.my = f3(dirc[6], dirc[7], dirc[8]);
+        r.mz = f3(dirc[9], dirc[10], dirc[11]);
+    } else {
+        setup_ray(r, f3(ox, oy, oz), f3(dx, dy, dz));
+    }
     DesignDev z;
     z.nodes = nodes;
     z.tri = tri;
@@ -147,6 +161,7 @@ struct WarpSmem {
     float4 qb[kQueue];         // (d.xyz, src)
     int qs[kQueue];            // slot | (bounce << 16)
     double dacc[12];           // warp FP64 sums (force, torque, squared pair differences)
+    float dirc[12];            // the item's 1/d and shear rows (trace_primary)
 };
 
 __host__ __device__ constexpr size_t trace_smem_bytes(int block) {
@@ -187,7 +202,7 @@ __device__ __forceinline__ void q_batch(WarpSmem& ws, int& qcount, int nb, const
     if (has) {
         ++nseg;
         const HitOut h = trace_segment<W>(dz.nodes, dz.tri, A.x, A.y, A.z, Bv.x, Bv.y, Bv.z, ic.tmin_b,
-                                          __float_as_int(Bv.w), p.err);
+                                          __float_as_int(Bv.w), nullptr, p.err);
         nvis += h.nvis; ntest += h.ntest;
         if (h.f >= 0) {
             const uint64_t i = (uint64_t)(p.off + (ts + slot) * p.stride);
@@ -225,6 +240,15 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
         item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dg * p.S + s : s)), p.com + 3 * dg,
                    p.rho + (size_t)dg * p.G * 2, p.design_base + dg, p.sun_base + s);
         if (lane < 12) ws.dacc[lane] = 0.0;
+        if (lane == 0) {
+            RaySetup rd;
+            setup_ray(rd, f3(0.0f, 0.0f, 0.0f), ic.dd);
+            ws.dirc[0] = rd.inv.x; ws.dirc[1] = rd.inv.y; ws.dirc[2] = rd.inv.z;
+            ws.dirc[3] = rd.mx.x; ws.dirc[4] = rd.mx.y; ws.dirc[5] = rd.mx.z;
+            ws.dirc[6] = rd.my.x; ws.dirc[7] = rd.my.y; ws.dirc[8] = rd.my.z;
+            ws.dirc[9] = rd.mz.x; ws.dirc[10] = rd.mz.y; ws.dirc[11] = rd.mz.z;
+        }
+        __syncwarp();
         const int64_t k0 = cidx * p.chunk;
         const int64_t k1 = min(k0 + p.chunk, p.n);
         int qcount = 0;
@@ -246,7 +270,7 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
                     const Seg sg = primary_seg(ic, p, i);
                     ++nseg;
                     const HitOut h = trace_segment<W>(dz.nodes, dz.tri, sg.o.x, sg.o.y, sg.o.z, sg.d.x, sg.d.y,
-                                                      sg.d.z, 0.0f, -1, p.err);
+                                                      sg.d.z, 0.0f, -1, ws.dirc, p.err);
                     nvis += h.nvis; ntest += h.ntest;
                     if (h.f >= 0) {
                         const ShadeOut so = shade_segment(dz.tri, ic.rho, ic.com.x, ic.com.y, ic.com.z, p.K, p.seed,
