@@ -41,7 +41,7 @@ WORKLOAD = "procedural satellite 49,776 tris, 64 groups, 4096 Fibonacci suns x 2
 # dram__bytes_read.sum + dram__bytes_write.sum of trace_kernel<4,6> from the ncu
 # capture of 16 of the 4096 suns (profiles/trace_kernel_config2_16suns_full.md),
 # scaled by the units processed (x256) to one benchmark launch
-TRACE_DRAM_BYTES_PER_LAUNCH = (12.849664e6 + 42.426368e6) * 256
+TRACE_DRAM_BYTES_PER_LAUNCH = (15.559424e6 + 59.597568e6) * 256
 
 
 def _peaks():
@@ -51,6 +51,31 @@ def _peaks():
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
             "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _l2_probe(dev):
+    """L2 copy bandwidth measured here: copy an L2-resident buffer (4, 8, 16
+    or 32 MiB) into another, read + write bytes, best of 20 timed loops of
+    50 copies at each size; the largest rate over the sizes."""
+    import torch
+    rate = 0.0
+    for mib in (4, 8, 16, 32):
+        n = mib * 1024 * 1024 // 4
+        a = torch.ones(n, dtype=torch.float32, device=dev)
+        b = torch.empty_like(a)
+        for _ in range(10):
+            b.copy_(a)
+        best = float("inf")
+        for _ in range(20):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(50):
+                b.copy_(a)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 50)
+        rate = max(rate, 2 * n * 4 / (best / 1e3) / 1e9)
+    return rate
 
 
 class ClockSampler:
@@ -268,6 +293,7 @@ def run_ours(args, ws, rank, local):
 
     # roofline: dominant kernel (trace_kernel) against the FP32 issue peak
     peaks, src = _peaks()
+    l2_gbs = _l2_probe(dev)
     sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     ops_node = 4 * 14 if args.width == 4 else 8 * 14
@@ -291,6 +317,15 @@ def run_ours(args, ws, rank, local):
                               f"triangle tests x {ops_tri}; peak = {n_sm} SM x 128 FP32 lanes x {sm_mhz:.0f} MHz; "
                               f"algorithmic bytes {bytes_per_ray:.0f} B/ray from L1/L2 (scene {info['device_bytes']} B)"),
                      "peaks_source": src},
+        "memory_roofline": {"bound": "l2", "achieved": bytes_per_ray * rays_step / (t_dev / args.steps) / 1e9,
+                            "peak": l2_gbs, "unit": "GB/s",
+                            "frac": bytes_per_ray * rays_step / (t_dev / args.steps) / 1e9 / l2_gbs,
+                            "frac_of_hbm": bytes_per_ray * rays_step / (t_dev / args.steps) / 1e9 / peaks["hbm_gbs"],
+                            "hbm_peak": peaks["hbm_gbs"],
+                            "note": ("traversal's algorithmic bytes (node visits x node bytes + triangle tests x 48 B, "
+                                     "kernel counters) per second, against the L2 copy bandwidth measured in this run "
+                                     "(4-32 MiB copies, L2-resident, best rate) and the measured HBM copy peak; the bytes are "
+                                     "served from L1/L2 (DRAM traffic per launch: see roofline.traffic)")},
         "traversal": {"node_visits_per_ray": vis / n_samp, "tri_tests_per_ray": tests / n_samp,
                       "segments_per_ray": segs / n_samp, "bytes_per_ray": bytes_per_ray},
         "clocks": ck,
