@@ -333,6 +333,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_extra:
         line["area_estimator"] = area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, args.width)
         line["per_sample_designs"] = samples_leg(srp, ctx, dev, sm_mhz)
+        line["batched_designs"] = batched_leg(srp, ctx, dev, sm_mhz)
         line["surrogate"], line["grad"] = extra_legs(srp, ctx, dev, peaks)
     if rank == 0 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
@@ -594,6 +595,67 @@ def samples_leg(srp, ctx, dev, sm_mhz):
     return {"cases": out, "note": "srp_trace_samples: warp per sample, brute force (the paper's per-sample design "
                                   "workload); the BVH route must build one BVH per sample (host build time shown); "
                                   "roofline counts 44 FP32 ops per triangle test at K = 1 (N x T tests)"}
+
+
+def batched_leg(srp, ctx, dev, sm_mhz):
+    """Many uneven designs x many suns in one persistent launch: 256
+    procedural designs with log-uniform 5k-200k triangles (13.2 M in all),
+    64 Fibonacci suns each, 1024^2 rays, K <= 3 -- one srp_force evaluation
+    captured as a CUDA graph and replayed; launch parameters from the
+    autotuner on 16 of the designs."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_2602_10712_gb300 import tune
+    t0 = time.perf_counter()
+    designs = W.config5_designs(256)
+    gen_s = time.perf_counter() - t0
+    D, S, nx = len(designs), 64, 1024
+    rng = np.random.default_rng(5)
+    rho = torch.from_numpy(rng.uniform(0.0, 0.5, size=(D, 64, 2)).astype(np.float32)).to(dev)
+    sun = torch.from_numpy(W.fibonacci_directions(S)).to(dev)
+    com = torch.zeros((D, 3), dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    best, table = tune.autotune(ctx, designs[::16], rho[::16].contiguous(), sun, com[::16].contiguous(), rays_x=nx,
+                                max_bounces=3, sample_rays=16384, sample_suns=8)
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        bvhs = list(ex.map(lambda m: srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, best["width"]), designs))
+    build_s = time.perf_counter() - t0
+    bvh_bytes = sum(b.info()["device_bytes"] for b in bvhs)
+    out = torch.zeros((D, S, 6), dtype=torch.float64, device=dev)
+    kw = dict(rays_x=nx, max_bounces=3, kernel_variant=best["kernel_variant"])
+    g = srp.ForceGraph(ctx, bvhs, rho, sun, com, out, **kw)
+    g.launch()
+    srp.srp_sync(ctx)
+    ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    g.close()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out2 = srp.srp_force(ctx, bvhs, rho, sun, com, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    same = bool(torch.equal(out2, out))
+    rays = D * S * nx * nx
+    t = sum(ms) / len(ms) / 1e3
+    Ts = [int(m.tris.shape[0]) for m in designs]
+    for b in bvhs:
+        b.close()
+    return {"rays_per_s_graph": rays / t, "rays_per_launch": rays, "ms_per_launch": t * 1e3,
+            "rays_per_s_call": rays / (e0.elapsed_time(e1) / 1e3), "graph_equals_call": same,
+            "designs": D, "suns": S, "rays_per_item": nx * nx, "tris_min": min(Ts), "tris_max": max(Ts),
+            "tris_total": sum(Ts), "bvh_device_bytes": bvh_bytes, "autotuned": best,
+            "autotune_table": table, "host_s": {"generate": gen_s, "autotune": tune_s, "bvh_build_16_threads": build_s},
+            "note": "srp_force over 256 uneven designs x 64 suns x 1024^2 rays (K <= 3) in one persistent launch "
+                    "(atomic work queue over (design, sun, chunk) units), captured with srp_force_graph_create"}
 
 
 def run_profile_case(case):

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import threading
 
 import numpy as np
 
@@ -53,11 +54,23 @@ _lib = None
 _P = C.c_void_p
 
 
+_load_lock = threading.Lock()
+
+
 def load(build_if_needed: bool = True):
-    """Load libsrp.so (building it with nvcc first if it is missing/stale)."""
+    """Load libsrp.so (building it with nvcc first if it is missing/stale).
+    Thread-safe: concurrent first calls build and load once."""
     global _lib
     if _lib is not None:
         return _lib
+    with _load_lock:
+        if _lib is not None:
+            return _lib
+        return _load_locked(build_if_needed)
+
+
+def _load_locked(build_if_needed: bool):
+    global _lib
     path = _build.build() if build_if_needed else _build.LIB
     if not os.path.exists(path):
         raise ImportError(f"libsrp.so not found at {path}: run __graft_entry__.build()")
