@@ -11,7 +11,7 @@
 //   core-matrix layout (tc_common.cuh), so a layer is one contiguous block
 //   that a 1-D bulk copy moves into shared memory.
 //
-// Forward kernel (one CTA of 256 threads per 128 batch rows):
+// Forward kernel (one CTA of 512 threads per 128 batch rows):
 //   X (FP32) -> BF16 tile in smem; per layer: bulk-copy W_l into smem,
 //   one thread issues K_l/16 tcgen05.mma (M=128, N=N_l, K=16) into a
 //   256-column TMEM accumulator, commit -> mbarrier; the four warps read
@@ -81,15 +81,30 @@ __global__ void mlp_pack_kernel(const float* __restrict__ params, __nv_bfloat16*
     }
 }
 
+constexpr int kFwdThreads = 512;   // 16 warps: 4 per TMEM lane quarter
+
 struct MlpFwdSmem {
     alignas(1024) unsigned char act[128 * 256 * 2];   // A tile (64 KB)
     alignas(1024) unsigned char w[256 * 256 * 2];     // B tile (128 KB)
+    float bias[4 * 256 + 16];                         // all layers' biases
     alignas(8) uint64_t bar_w;
     alignas(8) uint64_t bar_mma;
     uint32_t tmem_base;
 };
 
-__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// silu(z) = z sigmoid(z) = h + h tanh(h), h = z/2: one hardware tanh
+// (tanh.approx.f32, ~2^-11 relative) per activation instead of an exp and a
+// reciprocal -- the activation epilogue is bound by the SFU rate, and the
+// result is rounded to BF16 (2^-9) right after.
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float silu_f(float z) {
+    const float h = 0.5f * z;
+    return fmaf(h, tanh_approx(h), h);
+}
 
 // Issue the bulk copies of layer l's packed weights into smem (one thread).
 __device__ __forceinline__ void load_layer_weights(MlpFwdSmem& sm, const __nv_bfloat16* packed, const MlpLayout& L,
@@ -103,20 +118,26 @@ __device__ __forceinline__ void load_layer_weights(MlpFwdSmem& sm, const __nv_bf
     }
 }
 
-// 256 threads: warps w and w+4 share TMEM lane quarter w%4 (rows) and
-// split each layer's output columns in halves for the epilogue.  The next
-// layer's weights are requested as soon as this layer's MMAs have released
-// the weight buffer, so the copy overlaps the epilogue.
-__global__ void __launch_bounds__(256, 1) mlp_fwd_kernel(const float* __restrict__ x, int64_t B,
+// 512 threads: warps w, w+4, w+8, w+12 share TMEM lane quarter w%4 (rows)
+// and split each layer's output columns in quarters for the epilogue (16
+// warps keep the TMEM-load / SFU / shared-store chain busy); the biases sit
+// in shared memory.  The next layer's weights are requested as soon as this
+// layer's MMAs have released the weight buffer, so the copy overlaps the
+// epilogue.
+__global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const float* __restrict__ x, int64_t B,
                                                         const __nv_bfloat16* __restrict__ packed,
                                                         const float* __restrict__ params, float* __restrict__ y,
                                                         int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     MlpFwdSmem& sm = *reinterpret_cast<MlpFwdSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, part = warp >> 2;
     const MlpLayout L = mlp_layout();
     const int64_t row0 = (int64_t)blockIdx.x * 128;
+    for (int i = tid; i < 4 * 256 + 16; i += kFwdThreads) {
+        const int l = i >> 8, n = i & 255;
+        sm.bias[i] = l < 4 ? params[L.b_off[l] + n] : (n < 6 ? params[L.b_off[4] + n] : 0.0f);
+    }
     if (tid == 0) {
         tc::mbar_init(&sm.bar_w, 1);
         tc::mbar_init(&sm.bar_mma, 1);
@@ -176,14 +197,14 @@ __global__ void __launch_bounds__(256, 1) mlp_fwd_kernel(const float* __restrict
         tc::tc_fence_after();
         // the weight buffer is free: fetch the next layer's weights now
         if (tid == 0 && l + 1 < kMlpLayers) load_layer_weights(sm, packed, L, l + 1);
-        // epilogue: rows 32*quarter + lane, column half `half`
+        // epilogue: rows 32*quarter + lane, column quarter `part`
         const int r = 32 * quarter + lane;
         const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
         if (l < kMlpLayers - 1) {
-            const float* bias = params + L.b_off[l];
-            const int nc = N / 64;  // 32-column chunks per half
+            const float* bias = sm.bias + 256 * l;
+            const int nc = N / 128;  // 32-column chunks per quarter of the columns
             for (int cc = 0; cc < nc; ++cc) {
-                const int c = half * nc + cc;
+                const int c = part * nc + cc;
                 float v[32];
                 tc::tmem_ld32(taddr + 32u * c, v);
 #pragma unroll
@@ -195,8 +216,8 @@ __global__ void __launch_bounds__(256, 1) mlp_fwd_kernel(const float* __restrict
                         *reinterpret_cast<uint4*>(h);
                 }
             }
-        } else if (half == 0) {
-            const float* bias = params + L.b_off[l];
+        } else if (part == 0) {
+            const float* bias = sm.bias + 4 * 256;
             float v[32];
             tc::tmem_ld32(taddr, v);
             const int64_t row = row0 + r;
@@ -232,7 +253,7 @@ cudaError_t mlp_forward(const float* x, int64_t B, const void* packed, const flo
     cudaError_t e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((B + 127) / 128);
-    mlp_fwd_kernel<<<grid, 256, sm, st>>>(x, B, (const __nv_bfloat16*)packed, params, y, err);
+    mlp_fwd_kernel<<<grid, kFwdThreads, sm, st>>>(x, B, (const __nv_bfloat16*)packed, params, y, err);
     return cudaGetLastError();
 }
 
