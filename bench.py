@@ -54,27 +54,28 @@ def _peaks():
 
 
 def _l2_probe(dev):
-    """L2 copy bandwidth measured here: copy an L2-resident buffer (4, 8, 16
-    or 32 MiB) into another, read + write bytes, best of 20 timed loops of
-    50 copies at each size; the largest rate over the sizes."""
+    """L2 bandwidth measured here with library kernels on L2-resident buffers
+    (4-32 MiB): a copy (read + write bytes) and a sum reduction (read bytes),
+    best of 20 timed loops of 50 calls at each size; the largest rate."""
     import torch
     rate = 0.0
     for mib in (4, 8, 16, 32):
         n = mib * 1024 * 1024 // 4
         a = torch.ones(n, dtype=torch.float32, device=dev)
         b = torch.empty_like(a)
-        for _ in range(10):
-            b.copy_(a)
-        best = float("inf")
-        for _ in range(20):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(50):
-                b.copy_(a)
-            e1.record()
-            torch.cuda.synchronize()
-            best = min(best, e0.elapsed_time(e1) / 50)
-        rate = max(rate, 2 * n * 4 / (best / 1e3) / 1e9)
+        for op, nbytes in ((lambda: b.copy_(a), 2 * n * 4), (lambda: a.sum(), n * 4)):
+            for _ in range(10):
+                op()
+            best = float("inf")
+            for _ in range(20):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(50):
+                    op()
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 50)
+            rate = max(rate, nbytes / (best / 1e3) / 1e9)
     return rate
 
 
@@ -324,7 +325,7 @@ def run_ours(args, ws, rank, local):
                             "hbm_peak": peaks["hbm_gbs"],
                             "note": ("traversal's algorithmic bytes (node visits x node bytes + triangle tests x 48 B, "
                                      "kernel counters) per second, against the L2 copy bandwidth measured in this run "
-                                     "(4-32 MiB copies, L2-resident, best rate) and the measured HBM copy peak; the bytes are "
+                                     "(4-32 MiB copies and sums, L2-resident, best rate) and the measured HBM copy peak; the bytes are "
                                      "served from L1/L2 (DRAM traffic per launch: see roofline.traffic)")},
         "traversal": {"node_visits_per_ray": vis / n_samp, "tri_tests_per_ray": tests / n_samp,
                       "segments_per_ray": segs / n_samp, "bytes_per_ray": bytes_per_ray},
