@@ -141,10 +141,12 @@ __device__ __forceinline__ int find_tri(const int32_t* __restrict__ ex, int lo, 
 
 // One sun-light sample: point on leaf triangle L (original index f, sample
 // jj of nf), shadow ray along e, expected BRDF momentum if lit.
+// rset: setup_ray of the item's shadow direction e (origin 0): its 1/e and
+// shear rows serve every sample of the item; only o/e is per sample.
 template <int W>
 __device__ __forceinline__ void sample_sun(const DesignDev& dz, int L, int f, uint32_t jj, int32_t nf, float3 e,
-                                           float3 com, const float* rho, float tmin, uint32_t sg, uint32_t dg,
-                                           uint32_t key0, uint32_t key1, float P, int* err, float y[6],
+                                           const RaySetup& rset, float3 com, const float* rho, float tmin, uint32_t sg,
+                                           uint32_t dg, uint32_t key0, uint32_t key1, float P, int* err, float y[6],
                                            uint32_t& nvis, uint32_t& ntest, uint32_t& nseg) {
     const float4 a = __ldg(dz.tri + 3 * (size_t)L), b = __ldg(dz.tri + 3 * (size_t)L + 1),
                  c = __ldg(dz.tri + 3 * (size_t)L + 2);
@@ -161,8 +163,9 @@ __device__ __forceinline__ void sample_sun(const DesignDev& dz, int L, int f, ui
     const float b1 = sr * (1.0f - u2), b2 = sr * u2;
     const float3 x = f3(fmaf(b2, e2.x, fmaf(b1, e1.x, a.x)), fmaf(b2, e2.y, fmaf(b1, e1.y, a.y)),
                         fmaf(b2, e2.z, fmaf(b1, e1.z, a.z)));
-    RaySetup r;
-    setup_ray(r, x, e);
+    RaySetup r = rset;
+    r.o = x;
+    r.oinv = f3(x.x * r.inv.x, x.y * r.inv.y, x.z * r.inv.z);
     ++nseg;
     if (any_hit<W>(dz, r, tmin, L, err, nvis, ntest)) return;
     const int g = (int)__float_as_uint(b.w);
@@ -259,6 +262,8 @@ __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
                 e = f3((float)sp[0], (float)sp[1], (float)sp[2]);
             }
             const float* emit = MODE == 1 ? p.emit + (size_t)dl * p.G : nullptr;
+            RaySetup rset;
+            setup_ray(rset, f3(0.0f, 0.0f, 0.0f), e);
             const double* cp = p.com + 3 * (size_t)dl;
             const float3 com = f3((float)cp[0], (float)cp[1], (float)cp[2]);
             const float* rho = p.rho + (size_t)dl * p.G * 2;
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
                         const int32_t nf = ex_hi - ex_lo;
                         const int L = __ldg(map + f);
                         if (MODE == 0)
-                            sample_sun<W>(dz, L, f, jj, nf, e, com, rho, tmin, sg, dg, key0, key1, p.P, p.err, y, nvis,
+                            sample_sun<W>(dz, L, f, jj, nf, e, rset, com, rho, tmin, sg, dg, key0, key1, p.P, p.err, y, nvis,
                                           ntest, nseg);
                         else
                             sample_thermal<W>(dz, L, f, jj, nf, com, rho, emit, tmin, dg, key0, key1, p.P, p.err, y,
