@@ -3,7 +3,7 @@
 The proxy P(omega, theta | psi) maps the sun direction and the design
 parameters to force and torque (Sec. 3.3); it is fitted by minimising the
 empirical L1 risk E |P - (F|tau)| (Sec. 3.3, Alg. 1 NNLoss) with Adam
-(Sec. 3.3).  Architecture (spec reading of the paper's inconsistent
+(Sec. 3.3).  Architecture (a reading of the paper's inconsistent
 sizes): 19 inputs -> 4 hidden layers of 256 with SiLU -> 6 linear outputs.
 
 Plain definitions, no fusion:

@@ -73,7 +73,7 @@ def test_plate_facing_sun_exact(rs, rd):
 
 
 def test_plate_absorber_forms():
-    """The benchmark spec's absorbed / specular / diffuse plate forms at cos = 1."""
+    """The flat-plate forms of an absorber, a mirror and a Lambertian plate at cos = 1."""
     p = W.flat_plate((2.0, 1.0), 2)
     A = 2.0
     e = np.array([0, 0, 1.0]); d = -e; n = e
