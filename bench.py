@@ -242,13 +242,11 @@ def run_ours(args, ws, rank, local):
     def step():
         srp.srp_force(ctx, [bvh], r_t, s_t, c_t, out_ft=out, out_sigma=sig, **kw)
 
-    # traversal counters on a strided sample of the same workload (outside timing)
+    # traversal counters on 16 of the suns, full grid, as timed (outside timing)
     srp.srp_collect_stats(ctx, True)
-    samp_rays = 65536
-    srp.srp_force(ctx, [bvh], r_t, s_t[::16].contiguous(), c_t, ray_offset=0, ray_stride=(NX * NX) // samp_rays,
-                  ray_count=samp_rays, **{k: v for k, v in kw.items() if k != "sun_base"})
+    srp.srp_force(ctx, [bvh], r_t, s_t[::N_SUN // 16].contiguous(), c_t, **{k: v for k, v in kw.items() if k != "sun_base"})
     vis, tests, segs = srp.srp_collect_stats(ctx, False)
-    n_samp = samp_rays * (N_SUN // 16)
+    n_samp = 16 * NX * NX
     node_bytes = 128 if args.width == 4 else 256
     bytes_per_ray = (vis * node_bytes + tests * 48) / n_samp
 

@@ -14,6 +14,7 @@
 
 namespace srp {
 int trace_resident_blocks(int width, int block, int variant);
+cudaError_t launch_span(const TraceParams& p, int width, cudaStream_t st);
 cudaError_t launch_trace(const TraceParams& p, int width, int grid_cap, int block, cudaStream_t st);
 cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* out_ft, double* out_sigma,
                           cudaStream_t st);
@@ -84,6 +85,7 @@ struct srp_ctx {
     cudaEvent_t tab_ev = nullptr;              // last table upload
     unsigned long long* d_queue = nullptr;     // work-queue counter
     DevBuf stage_in, stage_out;                // host-mem staging
+    DevBuf span;                               // full-grid launches: rowfirst | rowoff (int32)
     DevBuf atab;                               // area estimator: cnt | map | ex (int32)
     DevBuf axb;                                // area estimator: xbase | ntot (int64)
 };
@@ -139,7 +141,7 @@ int srp_ctx_destroy(srp_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     c->part.release(); c->gpart.release(); c->stage_in.release(); c->stage_out.release(); c->dtab.release();
-    c->atab.release(); c->axb.release();
+    c->atab.release(); c->axb.release(); c->span.release();
     if (c->htab) cudaFreeHost(c->htab);
     if (c->tab_ev) cudaEventDestroy(c->tab_ev);
     if (c->d_queue) cudaFree(c->d_queue);
@@ -447,6 +449,16 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
     p->variant = variant;
     p->queue = c->d_queue;
     *grid_cap = c->n_sm * trace_resident_blocks(*width, bt, variant);
+    // full grids of whole 32-pixel batches: trace only the batches that can
+    // meet the scene (span_kernel); the tables need items * (2 ny + 1) int32
+    p->rowfirst = nullptr;
+    p->rowoff = nullptr;
+    const size_t span_bytes = sizeof(int32_t) * (size_t)items * (2 * (size_t)o->rays_y + 1);
+    if (items > 0 && off == 0 && stride == 1 && n == grid_n && o->rays_x % 32 == 0 && span_bytes <= ((size_t)1 << 30)) {
+        if (c->span.ensure(span_bytes) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force: cannot allocate the span tables");
+        p->rowfirst = (int32_t*)c->span.p;
+        p->rowoff = p->rowfirst + (size_t)items * o->rays_y;
+    }
     return SRP_OK;
 }
 
@@ -486,6 +498,7 @@ int force_enqueue(srp_ctx* c, TraceParams& p, int width, int block, int grid_cap
         return SRP_OK;
     }
     CU(cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), st), "cudaMemsetAsync(queue)");
+    if (p.rowoff) CU(launch_span(p, width, st), "span_kernel launch");
     CU(launch_trace(p, width, grid_cap, block, st), "trace_kernel launch");
     CU(launch_reduce(d_part, items, p.cpb, d_ft, d_sigma, st), "reduce kernel launch");
     return SRP_OK;

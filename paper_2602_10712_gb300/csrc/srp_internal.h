@@ -73,6 +73,11 @@ struct TraceParams {
     const DesignDev* designs;  // [D] device-side design table
     unsigned long long* queue; // work-queue counter (zeroed before each launch)
     int32_t variant;           // register budget: minimum resident blocks 4 or 5
+    // full-grid launches: per item and grid row, the first batch of 32 pixels
+    // that can meet the scene and the prefix of such batches (span_kernel);
+    // null: every ray of the subset is traced
+    int32_t* rowfirst;         // [D*S][ny]
+    int32_t* rowoff;           // [D*S][ny + 1]
 };
 
 // Parameters of the area-sampling estimator (area.cu).

@@ -161,7 +161,8 @@ struct WarpSmem {
     float4 qb[kQueue];         // (d.xyz, src)
     int qs[kQueue];            // slot | (bounce << 16)
     double dacc[12];           // warp FP64 sums (force, torque, squared pair differences)
-    float dirc[12];            // the item's 1/d and shear rows (trace_primary)
+    float dirc[12];            // the item's 1/d and shear rows (primary segments)
+    int64_t bbase[kBatches];   // ray index of the first ray of each batch of the tile
 };
 
 __host__ __device__ constexpr size_t trace_smem_bytes(int block) {
@@ -185,7 +186,7 @@ __device__ __forceinline__ void q_push(WarpSmem& ws, int& qcount, bool want, con
 // Trace the top `nb` queued segments (one per lane) and shade their hits.
 template <int W>
 __device__ __forceinline__ void q_batch(WarpSmem& ws, int& qcount, int nb, const DesignDev& dz, const ItemConst& ic,
-                                        const TraceParams& p, int64_t ts, int lane, uint32_t& nvis,
+                                        const TraceParams& p, int64_t bstride, int lane, uint32_t& nvis,
                                         uint32_t& ntest, uint32_t& nseg) {
     const bool has = lane < nb;
     float4 A = make_float4(0, 0, 0, 0), Bv = make_float4(0, 0, 0, 0);
@@ -205,7 +206,7 @@ __device__ __forceinline__ void q_batch(WarpSmem& ws, int& qcount, int nb, const
                                           __float_as_int(Bv.w), nullptr, p.err);
         nvis += h.nvis; ntest += h.ntest;
         if (h.f >= 0) {
-            const uint64_t i = (uint64_t)(p.off + (ts + slot) * p.stride);
+            const uint64_t i = (uint64_t)(ws.bbase[slot >> 5] + (int64_t)(slot & 31) * bstride);
             const ShadeOut so = shade_segment(dz.tri, ic.rho, ic.com.x, ic.com.y, ic.com.z, p.K, p.seed, ic.sglob,
                                               ic.dglob, (uint32_t)i, kb, h.f, h.t, A.x, A.y, A.z, Bv.x, Bv.y, Bv.z,
                                               A.w, &ws.ys[0][slot], kTile);
@@ -249,10 +250,52 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
             ws.dirc[9] = rd.mz.x; ws.dirc[10] = rd.mz.y; ws.dirc[11] = rd.mz.z;
         }
         __syncwarp();
-        const int64_t k0 = cidx * p.chunk;
-        const int64_t k1 = min(k0 + p.chunk, p.n);
+        // The unit's rays come in batches of 32 (a tile holds kBatches of them):
+        // span mode -- the unit's share of the item's live batches (batches of
+        // 32 neighbouring pixels that can meet the scene, in grid order; the
+        // others cannot hit anything and deposit nothing); otherwise -- the
+        // contiguous slots [k0, k1) of the ray subset.
+        const bool span = p.rowoff != nullptr;
+        const int64_t bstride = span ? 1 : p.stride;
+        int64_t t0, t1;           // this unit's batches (span) or slots
+        int row = 0;
+        const int32_t* rowoff = nullptr;
+        const int32_t* rowfirst = nullptr;
+        if (span) {
+            rowoff = p.rowoff + (size_t)item_l * (p.ny + 1);
+            rowfirst = p.rowfirst + (size_t)item_l * p.ny;
+            const int64_t L = __ldg(rowoff + p.ny);
+            t0 = cidx * L / p.cpb;
+            t1 = (cidx + 1) * L / p.cpb;
+            // first row with batches at or after t0
+            int lo = 0, hi = p.ny;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if ((int64_t)__ldg(rowoff + mid) <= t0) lo = mid; else hi = mid;
+            }
+            row = lo;
+        } else {
+            t0 = cidx * p.chunk;
+            t1 = min(t0 + p.chunk, p.n);
+        }
         int qcount = 0;
-        for (int64_t ts = k0; ts < k1; ts += kTile) {
+        for (int64_t ts = t0; ts < t1; ts += span ? kBatches : kTile) {
+            const int nslots = span ? 32 * (int)min((int64_t)kBatches, t1 - ts) : (int)min((int64_t)kTile, t1 - ts);
+            if (lane == 0) {
+                for (int j = 0; j < kBatches; ++j) {
+                    int64_t b = 0;
+                    if (span) {
+                        if (32 * j < nslots) {
+                            const int64_t lb = ts + j;
+                            while ((int64_t)__ldg(rowoff + row + 1) <= lb) ++row;
+                            b = (int64_t)row * p.nx + 32 * ((int64_t)__ldg(rowfirst + row) + (lb - __ldg(rowoff + row)));
+                        }
+                    } else {
+                        b = p.off + (ts + 32 * j) * p.stride;
+                    }
+                    ws.bbase[j] = b;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < kBatches; ++j)
 #pragma unroll
@@ -262,11 +305,10 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
 #pragma unroll 1
             for (int j = 0; j < kBatches; ++j) {
                 const int slot = j * 32 + lane;
-                const int64_t k = ts + slot;
                 Seg nx;
                 bool cont = false;
-                if (k < k1) {
-                    const uint64_t i = (uint64_t)(p.off + k * p.stride);
+                if (slot < nslots) {
+                    const uint64_t i = (uint64_t)(ws.bbase[j] + (int64_t)lane * bstride);
                     const Seg sg = primary_seg(ic, p, i);
                     ++nseg;
                     const HitOut h = trace_segment<W>(dz.nodes, dz.tri, sg.o.x, sg.o.y, sg.o.z, sg.d.x, sg.d.y,
@@ -282,15 +324,15 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
                     }
                 }
                 q_push(ws, qcount, cont, nx, slot, 2, lane);
-                while (qcount >= 32) q_batch<W>(ws, qcount, 32, dz, ic, p, ts, lane, nvis, ntest, nseg);
+                while (qcount >= 32) q_batch<W>(ws, qcount, 32, dz, ic, p, bstride, lane, nvis, ntest, nseg);
             }
-            while (qcount > 0) q_batch<W>(ws, qcount, min(qcount, 32), dz, ic, p, ts, lane, nvis, ntest, nseg);
+            while (qcount > 0) q_batch<W>(ws, qcount, min(qcount, 32), dz, ic, p, bstride, lane, nvis, ntest, nseg);
             // ---- per-ray sums -> per-lane partials (slot parity = ray parity)
             float accf[6] = {0, 0, 0, 0, 0, 0}, sqf[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int j = 0; j < kBatches; ++j) {
                 const int slot = j * 32 + lane;
-                const bool valid = ts + slot < k1;
+                const bool valid = slot < nslots;
                 const bool pvalid = __shfl_xor_sync(0xffffffffu, (int)valid, 1);
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
@@ -329,6 +371,112 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
         }
         if (lane == 0) { atomicAdd(p.stats, a); atomicAdd(p.stats + 1, b); atomicAdd(p.stats + 2, c); }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Span pre-pass (full-grid launches): which batches of 32 neighbouring
+// pixels can meet the scene.  One warp per (design, sun) item projects the
+// boxes two levels below the BVH root (W = 4: up to 16; W = 8: the root's 8
+// children) onto the grid plane as pixel rectangles widened by 2 pixels
+// (FP32 rounding of the ray origins is ~1e-4 pixel); a ray outside every
+// rectangle misses every box, so it cannot hit a triangle and deposits
+// nothing.  Per row y: rowfirst[y] = first batch of the row that meets a
+// rectangle, count = batches up to the last one that does; rowoff = the
+// exclusive prefix of the counts (rowoff[ny] = the item's live batches).
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ float4 top_rect(const DesignDev& dz, const ItemConst& ic, int lane) {
+    const float* nd0 = reinterpret_cast<const float*>(dz.nodes);
+    constexpr int NFL = W == 4 ? 32 : 64;   // floats per node
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    bool ok = false;
+    if (W == 4) {
+        const int c = lane >> 2, k = lane & 3;
+        const float l0 = __ldg(nd0 + c), h0 = __ldg(nd0 + 4 + c);
+        const int code = __float_as_int(__ldg(nd0 + 24 + c));
+        if (l0 <= h0) {
+            if (code < 0) {
+                if (k == 0) {
+                    for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd0 + 8 * a + c); hi[a] = __ldg(nd0 + 8 * a + 4 + c); }
+                    ok = true;
+                }
+            } else {
+                const float* nd = nd0 + (size_t)code * NFL;
+                for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd + 8 * a + k); hi[a] = __ldg(nd + 8 * a + 4 + k); }
+                ok = lo[0] <= hi[0];
+            }
+        }
+    } else if (lane < 8) {
+        for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd0 + 16 * a + lane); hi[a] = __ldg(nd0 + 16 * a + 8 + lane); }
+        ok = lo[0] <= hi[0];
+    }
+    float4 rc = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+    if (ok) {
+        const float3 cb = f3(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]));
+        const float3 h = f3(0.5f * (hi[0] - lo[0]), 0.5f * (hi[1] - lo[1]), 0.5f * (hi[2] - lo[2]));
+        const float3 q = cb - ic.ob;
+        const float ac = dot(q, ic.bu), bc = dot(q, ic.bv);
+        const float ea = fabsf(ic.bu.x) * h.x + fabsf(ic.bu.y) * h.y + fabsf(ic.bu.z) * h.z;
+        const float eb = fabsf(ic.bv.x) * h.x + fabsf(ic.bv.y) * h.y + fabsf(ic.bv.z) * h.z;
+        rc = make_float4((ac - ea) / ic.fdx - 2.0f, (ac + ea) / ic.fdx + 2.0f, (bc - eb) / ic.fdy - 2.0f,
+                         (bc + eb) / ic.fdy + 2.0f);
+    }
+    return rc;
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
+    __shared__ float4 rect[4][16];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+    if (item >= (int64_t)p.D * p.S) return;
+    const int dl = (int)(item / p.S), s = (int)(item % p.S);
+    const DesignDev dz = p.designs[dl];
+    ItemConst ic;
+    item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s)), p.com + 3 * dl,
+               p.rho + (size_t)dl * p.G * 2, p.design_base + dl, p.sun_base + s);
+    if (lane < 16) rect[warp][lane] = top_rect<W>(dz, ic, lane);
+    __syncwarp();
+    const int nbx = p.nx / 32, ny = p.ny;
+    int32_t* ro = p.rowoff + (size_t)item * (ny + 1);
+    int32_t* rf = p.rowfirst + (size_t)item * ny;
+    int carry = 0;
+    for (int y0 = 0; y0 < ny; y0 += 32) {
+        const int y = y0 + lane;
+        int cnt = 0;
+        if (y < ny) {
+            float xmin = INFINITY, xmax = -INFINITY;
+            for (int j = 0; j < 16; ++j) {
+                const float4 r = rect[warp][j];
+                if (r.z < (float)(y + 1) && r.w > (float)y) { xmin = fminf(xmin, r.x); xmax = fmaxf(xmax, r.y); }
+            }
+            int bf = 0;
+            if (xmin < xmax) {
+                const int b0 = (int)floorf(fminf(fmaxf(xmin * (1.0f / 32.0f), 0.0f), (float)nbx));
+                const int b1 = (int)ceilf(fminf(fmaxf(xmax * (1.0f / 32.0f), 0.0f), (float)nbx));
+                if (b1 > b0) { bf = b0; cnt = b1 - b0; }
+            }
+            rf[y] = bf;
+        }
+        int inc = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += o;
+        }
+        if (y < ny) ro[y] = carry + inc - cnt;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) ro[ny] = carry;
+}
+
+cudaError_t launch_span(const TraceParams& p, int width, cudaStream_t st) {
+    const int64_t items = (int64_t)p.D * p.S;
+    if (items == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((items + 3) / 4);
+    if (width == 8) span_kernel<8><<<grid, 128, 0, st>>>(p);
+    else span_kernel<4><<<grid, 128, 0, st>>>(p);
+    return cudaGetLastError();
 }
 
 // Per-ray inspection: one thread per listed ray of one (design, sun).

@@ -333,7 +333,9 @@ __device__ __forceinline__ void item_setup(ItemConst& ic, const DesignDev& dz, c
 
 // Primary segment of grid ray i (jittered pixel origin, travel direction d).
 __device__ __forceinline__ Seg primary_seg(const ItemConst& ic, const TraceParams& p, uint64_t i) {
-    const uint32_t px = (uint32_t)(i % (uint64_t)p.nx), py = (uint32_t)(i / (uint64_t)p.nx);
+    // i < nx * ny < 2^32 (checked on the host): 32-bit division
+    const uint32_t i32 = (uint32_t)i, nx32 = (uint32_t)p.nx;
+    const uint32_t py = i32 / nx32, px = i32 - py * nx32;
     float xi1 = 0.5f, xi2 = 0.5f;
     if (p.jitter) {
         const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)ic.sglob, (uint32_t)ic.dglob, 0u),

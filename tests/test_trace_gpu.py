@@ -148,12 +148,23 @@ def test_procedural_satellite_small_grid_aggregate(srp, ctx):
 
 # ------------------------------------------------------------------ equivalences
 def test_width4_equals_width8_bitwise(srp, ctx):
+    """The BVH width changes the traversal, not the rays or their deposits:
+    bit-identical on a grid whose rays are all traced (200 columns); on a
+    full grid of whole 32-pixel batches the batches that cannot meet the
+    scene are found from each BVH's top boxes, so the batches grouped per
+    FP32 tile sum differ and only rounding may change."""
     m, rho, sun, com = W.config2(8)
     b4 = _bvh(srp, ctx, m, width=4)
     b8 = _bvh(srp, ctx, m, width=8)
-    f4 = srp.srp_force(ctx, [b4], rho[None], sun, com[None], rays_x=256, max_bounces=3, chunks_per_item=8)
-    f8 = srp.srp_force(ctx, [b8], rho[None], sun, com[None], rays_x=256, max_bounces=3, chunks_per_item=8)
+    kw = dict(rays_x=200, rays_y=256, max_bounces=3, chunks_per_item=8)
+    f4 = srp.srp_force(ctx, [b4], rho[None], sun, com[None], **kw)
+    f8 = srp.srp_force(ctx, [b8], rho[None], sun, com[None], **kw)
     assert np.array_equal(f4, f8)
+    kw = dict(rays_x=256, max_bounces=3, chunks_per_item=8)
+    f4 = srp.srp_force(ctx, [b4], rho[None], sun, com[None], **kw)
+    f8 = srp.srp_force(ctx, [b8], rho[None], sun, com[None], **kw)
+    scale = np.abs(f4[..., :3]).max()
+    assert np.all(np.abs(f4 - f8) <= 1e-6 * scale * np.array([1, 1, 1, 10, 10, 10]))
 
 
 def test_deterministic_and_host_equals_device(srp, ctx):
