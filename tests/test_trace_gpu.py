@@ -320,3 +320,23 @@ def test_corrupted_bvh_reports_device_limit(srp, ctx):
     ft = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=256, max_bounces=1)
     fo, _ = oracle.force(m.verts, m.tris, m.group, rho, sun, com, nx=256, K=1)
     _assert_parity(ft[0], fo, b.info()["radius"])
+
+
+@pytest.mark.parametrize("width", [4, 8])
+def test_skipped_batches_deposit_nothing(srp, ctx, width):
+    """On a full grid of whole 32-pixel batches only the batches that can
+    meet the scene are traced; the rest must deposit nothing.  The same grid
+    without its last ray is traced ray by ray (a ray subset): full =
+    subset + last ray, to rounding, on the satellite with K = 3."""
+    m, rho, sun, com = W.config2(8)
+    b = _bvh(srp, ctx, m, width=width)
+    nx = 256
+    full = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=nx, max_bounces=3, seed=3)
+    sub = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=nx, max_bounces=3, seed=3, ray_offset=0,
+                        ray_stride=1, ray_count=nx * nx - 1)
+    for s in range(sun.shape[0]):
+        y, _ = srp.srp_trace_rays(ctx, b, rho, sun[s], com, np.array([nx * nx - 1]), sun_index=s, rays_x=nx,
+                                  max_bounces=3, seed=3)
+        want = sub[0, s] + y[0]
+        scale = np.linalg.norm(full[0, s, :3])
+        assert np.all(np.abs(full[0, s] - want) <= 1e-6 * scale * np.array([1, 1, 1, 10, 10, 10])), (s, full[0, s], want)
