@@ -41,7 +41,7 @@ WORKLOAD = "procedural satellite 49,776 tris, 64 groups, 4096 Fibonacci suns x 2
 # dram__bytes_read.sum + dram__bytes_write.sum of trace_kernel<4,6> from the ncu
 # capture of 16 of the 4096 suns (profiles/trace_kernel_config2_16suns_full.md),
 # scaled by the units processed (x256) to one benchmark launch
-TRACE_DRAM_BYTES_PER_LAUNCH = (15.559424e6 + 59.597568e6) * 256
+TRACE_DRAM_BYTES_PER_LAUNCH = (16.618496e6 + 85.631232e6) * 256
 
 
 def _peaks():
@@ -309,7 +309,7 @@ def run_ours(args, ws, rank, local):
                    "bvh_build_ms": build_ms, "bvh_nodes": info["n_nodes"], "parallelism": f"replicas x{ws}"},
         "force_evals_per_s": ws * N_SUN * args.steps / t_max,
         "e2e": {"value": e2e, "unit": "rays/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (3 if NX % 32 == 0 else 2) * args.steps,   # span pre-pass (full grids), trace, reduce
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                      "frac": achieved / peak_alu, "traffic": TRACE_DRAM_BYTES_PER_LAUNCH,
                      "note": (f"trace_kernel FP32 lane-ops: {ops_per_ray:.0f}/ray = node visits x {ops_node} + "
