@@ -376,39 +376,43 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
 // ---------------------------------------------------------------------------
 // Span pre-pass (full-grid launches): which batches of 32 neighbouring
 // pixels can meet the scene.  One warp per (design, sun) item projects the
-// boxes two levels below the BVH root (W = 4: up to 16; W = 8: the root's 8
-// children) onto the grid plane as pixel rectangles widened by 2 pixels
+// BVH boxes three levels below the root (W = 4: up to 64; W = 8: two
+// levels, up to 64) onto the grid plane as pixel rectangles widened by 2 pixels
 // (FP32 rounding of the ray origins is ~1e-4 pixel); a ray outside every
 // rectangle misses every box, so it cannot hit a triangle and deposits
 // nothing.  Per row y: rowfirst[y] = first batch of the row that meets a
 // rectangle, count = batches up to the last one that does; rowoff = the
 // exclusive prefix of the counts (rowoff[ny] = the item's live batches).
 // ---------------------------------------------------------------------------
+constexpr int kTopBoxes = 64;   // box slots of the span pre-pass
+
+// Pixel rectangle of box slot bi (0..63): W = 4 -- the node three levels
+// below the root along child digits (bi>>4, (bi>>2)&3, bi&3); W = 8 -- two
+// levels (bi>>3, bi&7).  A leaf on the way stands for its whole subtree (the
+// slot whose remaining digits are 0 carries it, the others are empty).
 template <int W>
-__device__ __forceinline__ float4 top_rect(const DesignDev& dz, const ItemConst& ic, int lane) {
+__device__ __forceinline__ float4 top_rect(const DesignDev& dz, const ItemConst& ic, int bi) {
     const float* nd0 = reinterpret_cast<const float*>(dz.nodes);
     constexpr int NFL = W == 4 ? 32 : 64;   // floats per node
+    constexpr int levels = W == 4 ? 3 : 2;
+    int digit[3];
+    if (W == 4) { digit[0] = bi >> 4; digit[1] = (bi >> 2) & 3; digit[2] = bi & 3; }
+    else { digit[0] = bi >> 3; digit[1] = bi & 7; digit[2] = 0; }
+    const float* nd = nd0;
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     bool ok = false;
-    if (W == 4) {
-        const int c = lane >> 2, k = lane & 3;
-        const float l0 = __ldg(nd0 + c), h0 = __ldg(nd0 + 4 + c);
-        const int code = __float_as_int(__ldg(nd0 + 24 + c));
-        if (l0 <= h0) {
-            if (code < 0) {
-                if (k == 0) {
-                    for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd0 + 8 * a + c); hi[a] = __ldg(nd0 + 8 * a + 4 + c); }
-                    ok = true;
-                }
-            } else {
-                const float* nd = nd0 + (size_t)code * NFL;
-                for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd + 8 * a + k); hi[a] = __ldg(nd + 8 * a + 4 + k); }
-                ok = lo[0] <= hi[0];
-            }
+    for (int lv = 0; lv < levels; ++lv) {
+        const int c = digit[lv];
+        for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd + 2 * W * a + c); hi[a] = __ldg(nd + 2 * W * a + W + c); }
+        if (!(lo[0] <= hi[0])) { ok = false; break; }
+        ok = true;
+        const int code = __float_as_int(__ldg(nd + 6 * W + c));
+        if (lv == levels - 1) break;
+        if (code < 0) {   // a leaf: only the slot with the remaining digits 0 keeps it
+            for (int l2 = lv + 1; l2 < levels; ++l2) ok = ok && digit[l2] == 0;
+            break;
         }
-    } else if (lane < 8) {
-        for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd0 + 16 * a + lane); hi[a] = __ldg(nd0 + 16 * a + 8 + lane); }
-        ok = lo[0] <= hi[0];
+        nd = nd0 + (size_t)code * NFL;
     }
     float4 rc = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
     if (ok) {
@@ -426,7 +430,7 @@ __device__ __forceinline__ float4 top_rect(const DesignDev& dz, const ItemConst&
 
 template <int W>
 __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
-    __shared__ float4 rect[4][16];
+    __shared__ float4 rect[4][kTopBoxes];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * 4 + warp;
     if (item >= (int64_t)p.D * p.S) return;
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
     ItemConst ic;
     item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s)), p.com + 3 * dl,
                p.rho + (size_t)dl * p.G * 2, p.design_base + dl, p.sun_base + s);
-    if (lane < 16) rect[warp][lane] = top_rect<W>(dz, ic, lane);
+    for (int bi = lane; bi < kTopBoxes; bi += 32) rect[warp][bi] = top_rect<W>(dz, ic, bi);
     __syncwarp();
     const int nbx = p.nx / 32, ny = p.ny;
     int32_t* ro = p.rowoff + (size_t)item * (ny + 1);
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
         int cnt = 0;
         if (y < ny) {
             float xmin = INFINITY, xmax = -INFINITY;
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < kTopBoxes; ++j) {
                 const float4 r = rect[warp][j];
                 if (r.z < (float)(y + 1) && r.w > (float)y) { xmin = fminf(xmin, r.x); xmax = fmaxf(xmax, r.y); }
             }
