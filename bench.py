@@ -333,6 +333,7 @@ def run_ours(args, ws, rank, local):
         line["area_estimator"] = area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, args.width)
         line["per_sample_designs"] = samples_leg(srp, ctx, dev, sm_mhz)
         line["batched_designs"] = batched_leg(srp, ctx, dev, sm_mhz)
+        line["design_optimisation"] = design_leg(srp, ctx, dev)
         line["surrogate"], line["grad"] = extra_legs(srp, ctx, dev, peaks)
     if rank == 0 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
@@ -655,6 +656,35 @@ def batched_leg(srp, ctx, dev, sm_mhz):
             "autotune_table": table, "host_s": {"generate": gen_s, "autotune": tune_s, "bvh_build_16_threads": build_s},
             "note": "srp_force over 256 uneven designs x 64 suns x 1024^2 rays (K <= 3) in one persistent launch "
                     "(atomic work queue over (design, sun, chunk) units), captured with srp_force_graph_create"}
+
+
+def design_leg(srp, ctx, dev):
+    """Design optimisation through the tracer's gradient: 100 Adam steps on
+    the 14 reflectances of the 7-group box-wing against the forces of a
+    reference design at 64 suns (512^2 rays per sun, K = 1); each step
+    instantiates the design, builds its BVH, traces and back-propagates."""
+    from paper_2602_10712_gb300.design import optimize_tracer
+    m = W.box_wing_7group()
+    rng = np.random.default_rng(4)
+    rho_true = rng.uniform(0.1, 0.4, size=(7, 2))
+    sun = W.fibonacci_directions(64)
+    com = np.zeros(3)
+    ang = np.array([0.2, -0.3])
+    kw = dict(rays_x=512, max_bounces=1, seed=1)
+    v = srp.srp_design_instantiate(m.verts, m.vhinge, m.hinges, ang)
+    b = srp.srp_build_bvh(ctx, v, m.tris, m.group, 4)
+    target = srp.srp_force(ctx, [b], rho_true.astype(np.float32)[None], sun, com[None], **kw)[0]
+    b.close()
+    rho0 = np.clip(rho_true + rng.choice([-0.15, 0.15], size=rho_true.shape), 0.0, 0.5)
+    t0 = time.perf_counter()
+    rho, _, losses = optimize_tracer(ctx, m, rho0, ang, sun, com, target, steps=100, lr=0.01, hinge_lo=ang,
+                                     hinge_hi=ang, **kw)
+    dt = time.perf_counter() - t0
+    return {"steps": 100, "steps_per_s": 100 / dt, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+            "median_rho_err_start": float(np.median(np.abs(rho0 - rho_true))),
+            "median_rho_err_end": float(np.median(np.abs(rho - rho_true))),
+            "note": "optimize_tracer: srp_design_instantiate + srp_build_bvh + srp_force + srp_force_grad per step, "
+                    "64 suns x 512^2 rays, K = 1, host-mode calls (wall clock)"}
 
 
 def run_profile_case(case):

@@ -36,3 +36,54 @@ def optimize_design(ctx, opts, z0, theta0, r_ref, *, proxy=None, steps=100, lr=0
         vh = v / (1 - b2 ** (it + 1))
         th = np.clip(th - lr * mh / (np.sqrt(vh) + eps), lo, hi)
     return th[0], np.array(losses)
+
+
+def _project_rho(rho):
+    """Reflectances back into the admissible set: 0 <= rho_s, rho_d and
+    rho_s + rho_d <= 1 (an excess is removed equally from both)."""
+    r = np.clip(rho, 0.0, 1.0)
+    ex = np.maximum(r.sum(axis=-1) - 1.0, 0.0)
+    r = r - 0.5 * ex[..., None]
+    return np.clip(r, 0.0, 1.0)
+
+
+def optimize_tracer(ctx, mesh, rho0, angles0, sun_dir, com, target_ft, *, steps=100, lr=0.01, hinge_lo=-np.pi / 2,
+                    hinge_hi=np.pi / 2, b1=0.9, b2=0.999, eps=1e-12, **trace_opts):
+    """Design optimisation through the tracer itself: Adam on the group
+    reflectances (rho [G,2]) and the hinge angles of one design to bring its
+    force and torque at the given suns (target_ft [S,6]) to the target,
+    L = sum_s |(F,tau)_s - target_s|^2, with the reflectances projected into
+    their admissible set and the angles clipped after every step.  Each step
+    instantiates the design, builds its BVH and calls srp_force and
+    srp_force_grad (upstream 2 (ft - target)); the hinge gradient holds the
+    visibility fixed (it is exact while no shadow boundary moves).
+    Returns (rho, angles, losses [steps+1])."""
+    from . import srp_build_bvh, srp_design_instantiate, srp_force, srp_force_grad
+    rho = _project_rho(np.array(rho0, dtype=np.float64))
+    ang = np.array(angles0, dtype=np.float64)
+    tri_hinge = np.asarray(mesh.vhinge)[np.asarray(mesh.tris)[:, 0]].astype(np.int32)
+    p = np.concatenate([rho.ravel(), ang])
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    losses = []
+    tgt = np.asarray(target_ft, np.float64)
+    for it in range(steps + 1):
+        verts = srp_design_instantiate(mesh.verts, mesh.vhinge, mesh.hinges, ang)
+        b = srp_build_bvh(ctx, verts, mesh.tris, mesh.group, 4)
+        ft = srp_force(ctx, [b], rho.astype(np.float32)[None], sun_dir, com[None], **trace_opts)[0]
+        d = ft - tgt
+        losses.append(float(np.sum(d * d)))
+        if it == steps:
+            b.close()
+            break
+        d_rho, d_h = srp_force_grad(ctx, b, rho.astype(np.float32), sun_dir, com, 2.0 * d, tri_hinge=tri_hinge,
+                                    hinge_axes=mesh.hinges, **trace_opts)
+        b.close()
+        g = np.concatenate([np.asarray(d_rho).ravel(), np.asarray(d_h)])
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        p = p - lr * (m / (1 - b1 ** (it + 1))) / (np.sqrt(v / (1 - b2 ** (it + 1))) + eps)
+        rho = _project_rho(p[:rho.size].reshape(rho.shape))
+        ang = np.clip(p[rho.size:], hinge_lo, hinge_hi)
+        p = np.concatenate([rho.ravel(), ang])
+    return rho, ang, np.array(losses)

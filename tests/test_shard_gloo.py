@@ -58,3 +58,14 @@ def test_two_gloo_ranks_equal_unsharded(tmp_path):
     m, rho, _, com = W.config1()
     ref, _ = oracle.force(m.verts, m.tris, m.group, rho, W.fibonacci_directions(7), com, nx=48, K=3, threads=2)
     assert np.array_equal(full, ref)
+
+
+def test_reflectance_projection():
+    """The design loop's projection keeps rho_s, rho_d >= 0 and
+    rho_s + rho_d <= 1 and leaves admissible values unchanged."""
+    import numpy as np
+    from paper_2602_10712_gb300.design import _project_rho
+    r = np.array([[0.2, 0.3], [0.9, 0.4], [-0.1, 0.5], [1.2, -0.3], [0.6, 0.6]])
+    p = _project_rho(r)
+    assert np.all(p >= 0.0) and np.all(p.sum(axis=1) <= 1.0 + 1e-12)
+    assert np.allclose(p[0], r[0])
