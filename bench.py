@@ -41,7 +41,7 @@ WORKLOAD = "procedural satellite 49,776 tris, 64 groups, 4096 Fibonacci suns x 2
 # dram__bytes_read.sum + dram__bytes_write.sum of trace_kernel<4,6> from the ncu
 # capture of 16 of the 4096 suns (profiles/trace_kernel_config2_16suns_full.md),
 # scaled by the units processed (x256) to one benchmark launch
-TRACE_DRAM_BYTES_PER_LAUNCH = (16.618496e6 + 85.631232e6) * 256
+TRACE_DRAM_BYTES_PER_LAUNCH = (16.359168e6 + 90.898944e6) * 256
 
 
 def _peaks():
@@ -330,6 +330,19 @@ def run_ours(args, ws, rank, local):
         "clocks": ck,
     }
     if rank == 0 and not args.no_extra:
+        # the same workload at K = 1 (primary hits only), device time, L2 flushed
+        kw1 = dict(kw, max_bounces=1)
+        srp.srp_force(ctx, [bvh], r_t, s_t, c_t, out_ft=out, **kw1)
+        ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        for a, b in ev1:
+            flush.zero_()
+            a.record(stream)
+            srp.srp_force(ctx, [bvh], r_t, s_t, c_t, out_ft=out, **kw1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms1 = sum(a.elapsed_time(b) for a, b in ev1) / len(ev1)
+        line["single_bounce"] = {"rays_per_s": rays_step / (ms1 / 1e3), "ms_per_step": ms1, "max_bounces": 1,
+                                 "note": "the timed workload with max_bounces = 1"}
         line["area_estimator"] = area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, args.width)
         line["per_sample_designs"] = samples_leg(srp, ctx, dev, sm_mhz)
         line["batched_designs"] = batched_leg(srp, ctx, dev, sm_mhz)
@@ -602,7 +615,7 @@ def batched_leg(srp, ctx, dev, sm_mhz):
     procedural designs with log-uniform 5k-200k triangles (13.2 M in all),
     64 Fibonacci suns each, 1024^2 rays, K <= 3 -- one srp_force evaluation
     captured as a CUDA graph and replayed; launch parameters from the
-    autotuner on 16 of the designs."""
+    autotuner on 16 of the designs x 8 of the suns (whole grids)."""
     import torch
     from concurrent.futures import ThreadPoolExecutor
 
@@ -617,7 +630,7 @@ def batched_leg(srp, ctx, dev, sm_mhz):
     com = torch.zeros((D, 3), dtype=torch.float64, device=dev)
     t0 = time.perf_counter()
     best, table = tune.autotune(ctx, designs[::16], rho[::16].contiguous(), sun, com[::16].contiguous(), rays_x=nx,
-                                max_bounces=3, sample_rays=16384, sample_suns=8)
+                                max_bounces=3, sample_suns=8)
     tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:

@@ -1,10 +1,14 @@
 """Autotuner of the tracer's launch parameters.
 
-For a design (or set of designs) and a workload, time srp_force on a strided
-sample of the real work for every candidate (BVH width 4 or 8, kernel
-register budget 4 or 5 resident blocks per SM) and return the fastest.  The
-sample keeps the full grid geometry (same rays_x/rays_y, every k-th ray), so
-the traversal work per ray is the workload's.
+For a design (or set of designs) and a workload, time srp_force on a sample
+of the real work for every candidate (BVH width 4 or 8, kernel register
+budget 4, 5 or 6 resident blocks per SM) and return the fastest.  By default
+the sample is whole grids for a subset of the sun directions, so each
+candidate runs the launch path of the workload itself (full grids take the
+pre-pass that skips the 32-pixel batches missing the scene, which changes
+how the candidates rank); `sample_rays` instead takes every k-th ray of each
+grid (same rays_x/rays_y, so the traversal work per ray is the workload's),
+for grids too large to time whole.
 """
 from __future__ import annotations
 
@@ -16,7 +20,7 @@ import numpy as np
 from . import srp_build_bvh, srp_force
 
 
-def autotune(ctx, meshes, rho, sun_dir, com, *, rays_x, rays_y=None, max_bounces=1, sample_rays=65536,
+def autotune(ctx, meshes, rho, sun_dir, com, *, rays_x, rays_y=None, max_bounces=1, sample_rays=None,
              sample_suns=16, widths=(4, 8), variants=(4, 5, 6), repeats=2, **opts):
     """Returns (best dict(width, kernel_variant), table of timings in
     rays/s).  `meshes` are workloads.Mesh-like (verts, tris, group);
@@ -25,16 +29,19 @@ def autotune(ctx, meshes, rho, sun_dir, com, *, rays_x, rays_y=None, max_bounces
     import torch
     ry = rays_x if rays_y is None else rays_y
     n = rays_x * ry
-    stride = max(1, n // sample_rays)
-    count = min(sample_rays, (n + stride - 1) // stride)
+    if sample_rays is None or sample_rays >= n:
+        count, sub = n, {}
+    else:
+        stride = max(1, n // sample_rays)
+        count = min(sample_rays, (n + stride - 1) // stride)
+        sub = dict(ray_offset=0, ray_stride=stride, ray_count=count)
     S = sun_dir.shape[-2]
     sel = torch.arange(0, S, max(1, S // sample_suns), device=sun_dir.device)[:sample_suns]
     sun_s = sun_dir.index_select(-2, sel).contiguous()
     table = []
     bvhs = {w: [srp_build_bvh(ctx, m.verts, m.tris, m.group, w) for m in meshes] for w in widths}
     for w, v in itertools.product(widths, variants):
-        kw = dict(rays_x=rays_x, rays_y=ry, max_bounces=max_bounces, ray_offset=0, ray_stride=stride,
-                  ray_count=count, kernel_variant=v, **opts)
+        kw = dict(rays_x=rays_x, rays_y=ry, max_bounces=max_bounces, kernel_variant=v, **sub, **opts)
         srp_force(ctx, bvhs[w], rho, sun_s, com, **kw)
         torch.cuda.synchronize()
         best = float("inf")
