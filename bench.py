@@ -20,11 +20,9 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np

@@ -34,8 +34,6 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import mlp as omlp
-
 MU = 3.986004418e14
 J2 = 1.08263e-3
 RE = 6378137.0

@@ -486,7 +486,7 @@ int upload_designs(srp_ctx* c, const std::vector<DesignDev>& designs) {
 }
 
 // Stream work of one evaluation: queue reset, trace, reduce (on `st`).
-int force_enqueue(srp_ctx* c, TraceParams& p, int width, int block, int grid_cap, double* d_part, double* d_ft,
+int force_enqueue(TraceParams& p, int width, int block, int grid_cap, double* d_part, double* d_ft,
                   double* d_sigma, cudaStream_t st) {
     p.part = d_part;
     const int64_t items = (int64_t)p.D * p.S;
@@ -509,7 +509,7 @@ int force_launch(srp_ctx* c, const std::vector<DesignDev>& designs, TraceParams&
     int rc = upload_designs(c, designs);
     if (rc != SRP_OK) return rc;
     p.designs = (const DesignDev*)c->dtab.p;
-    return force_enqueue(c, p, width, block, grid_cap, d_part, d_ft, d_sigma, c->stream);
+    return force_enqueue(p, width, block, grid_cap, d_part, d_ft, d_sigma, c->stream);
 }
 }  // namespace srp
 
@@ -751,7 +751,7 @@ extern "C" int srp_force_graph_create(srp_ctx* c, const srp_bvh* const* bvhs, in
         cudaFree(g->dtab); delete g;
         return cuda_fail(e, "cudaStreamBeginCapture");
     }
-    rc = force_enqueue(c, p, width, block, grid_cap, (double*)c->part.p, out_ft, out_sigma, cap);
+    rc = force_enqueue(p, width, block, grid_cap, (double*)c->part.p, out_ft, out_sigma, cap);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(cap, &graph);
     cudaStreamDestroy(cap);

@@ -153,7 +153,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 constexpr int kBatches = SRP_BATCHES;     // primary batches of 32 rays per tile
 constexpr int kTile = 32 * kBatches;      // rays per warp tile
 constexpr int kQueue = 64;                // bounce segments per warp (<= 31 + 32 live)
-constexpr int kWarpsPerBlock = 4;
 
 struct WarpSmem {
     float ys[6][kTile];        // per-ray force/torque sums of the tile

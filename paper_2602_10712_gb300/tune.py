@@ -15,7 +15,6 @@ from __future__ import annotations
 import itertools
 import time
 
-import numpy as np
 
 from . import srp_build_bvh, srp_force
 

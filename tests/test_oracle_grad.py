@@ -2,7 +2,6 @@
 hinge)) against finite differences of the oracle's forward estimate on the
 same random numbers, against finite differences of the per-plate closed form
 (box-wing model, Sec. 2.1) on an unoccluded panel, and sparsity."""
-import math
 
 import numpy as np
 import pytest

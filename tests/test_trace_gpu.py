@@ -9,7 +9,6 @@ the neighbouring triangle.  Where that can happen (fine meshes) the tests
 compare per-ray paths: rays whose hit sequences agree must agree to 1e-5, the
 count of rays whose paths differ is bounded and reported, and the aggregate
 is checked with those rays' differences accounted for exactly."""
-import math
 
 import numpy as np
 import pytest
