@@ -65,6 +65,16 @@ __host__ __device__ inline MlpLayout mlp_layout() {
     return L;
 }
 
+// Packed BF16 weights: per layer, K cut into chunks of KC = min(64, K)
+// columns; each chunk is a contiguous K-major no-swizzle N x KC tile, so
+// one bulk copy brings one chunk and the MMAs of that K range can start as
+// soon as it lands.
+__host__ __device__ constexpr int mlp_KC(int l) { return mlp_K(l) < 64 ? mlp_K(l) : 64; }
+__host__ __device__ inline uint32_t mlp_packed_off(int l, int n, int k) {   // bytes within layer l
+    const int KC = mlp_KC(l), c = k / KC;
+    return (uint32_t)c * (uint32_t)(mlp_N(l) * KC * 2) + tc::kmajor_off((uint32_t)n, (uint32_t)(k - c * KC), (uint32_t)KC);
+}
+
 // FP32 master weights -> BF16 packed per layer (zero padding).
 __global__ void mlp_pack_kernel(const float* __restrict__ params, __nv_bfloat16* __restrict__ packed) {
     const MlpLayout L = mlp_layout();
@@ -73,29 +83,49 @@ __global__ void mlp_pack_kernel(const float* __restrict__ params, __nv_bfloat16*
         int l = 0;
         while (l + 1 < kMlpLayers && e >= L.p_off[l + 1]) ++l;
         const int64_t loc = e - L.p_off[l];
-        const int K = mlp_K(l), N = mlp_N(l);
+        const int K = mlp_K(l);
         const int n = (int)(loc / K), k = (int)(loc % K);
-        (void)N;
         const float w = (n < mlp_out(l) && k < mlp_in(l)) ? params[L.w_off[l] + (int64_t)n * mlp_in(l) + k] : 0.0f;
-        packed[L.p_off[l] + tc::kmajor_off(n, k, K) / 2] = __float2bfloat16_rn(w);
+        packed[L.p_off[l] + mlp_packed_off(l, n, k) / 2] = __float2bfloat16_rn(w);
     }
 }
 
-constexpr int kFwdThreads = 512;   // 16 warps: 4 per TMEM lane quarter
+// Forward kernel: persistent, one CTA per SM, 128-row tiles.
+//   warps 0-15  epilogue: warp w reads TMEM lane quarter w % 4 (rows) and,
+//               in each 64-feature chunk c, the 16 features
+//               64 c + 16 (w / 4) ...; all 16 warps finish chunk 0, then 1,
+//               2, 3; warps 0-3 also load each tile's inputs and write its
+//               outputs;
+//   warp 16     producer: bulk copies of the weights and tcgen05.mma issue.
+// Layer l + 1's MMAs over K chunk c need only chunk c of layer l's
+// activations, so each chunk is signalled on its own mbarrier as soon as it
+// is written and the tensor core runs layer l + 1 while the later chunks of
+// layer l's epilogue are still in flight; consecutive layers alternate
+// between two 256-column TMEM accumulators.  Layers 0 and 4 (24 KB) stay
+// resident; the 128 KB hidden layers 1-3 stream through one buffer in four
+// 32 KB chunks, each copy issued as soon as the previous layer's MMAs have
+// released it.
+constexpr int kEpiWarps = 16;
+constexpr int kFwdThreads = 32 * (kEpiWarps + 1);
 
 struct MlpFwdSmem {
-    alignas(1024) unsigned char act[128 * 256 * 2];   // A tile (64 KB)
-    alignas(1024) unsigned char w[256 * 256 * 2];     // B tile (128 KB)
+    alignas(1024) unsigned char act[128 * 256 * 2];   // A: the layer's input activations (64 KB)
+    alignas(1024) unsigned char w[256 * 256 * 2];     // B: streamed hidden layer, 4 chunks of 32 KB
+    alignas(1024) unsigned char w0[256 * 32 * 2];     // B: layer 0 (resident)
+    alignas(1024) unsigned char w4[16 * 256 * 2];     // B: layer 4 (resident)
     float bias[4 * 256 + 16];                         // all layers' biases
-    alignas(8) uint64_t bar_w;
-    alignas(8) uint64_t bar_mma;
+    alignas(8) uint64_t bar_w[4];     // streamed weight chunk c landed
+    alignas(8) uint64_t bar_res;      // resident weights landed
+    alignas(8) uint64_t bar_mma;      // a layer's MMAs completed
+    alignas(8) uint64_t bar_act[4];   // activation chunk c written (16 warps arrive)
+    alignas(8) uint64_t bar_in;       // a tile's inputs written and every epilogue warp past the
+                                      // previous tile's last layer (16 warps arrive)
     uint32_t tmem_base;
 };
 
 // silu(z) = z sigmoid(z) = h + h tanh(h), h = z/2: one hardware tanh
 // (tanh.approx.f32, ~2^-11 relative) per activation instead of an exp and a
-// reciprocal -- the activation epilogue is bound by the SFU rate, and the
-// result is rounded to BF16 (2^-9) right after.
+// reciprocal; the result is rounded to BF16 (2^-9) right after.
 __device__ __forceinline__ float tanh_approx(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -106,24 +136,66 @@ __device__ __forceinline__ float silu_f(float z) {
     return fmaf(h, tanh_approx(h), h);
 }
 
-// Issue the bulk copies of layer l's packed weights into smem (one thread).
-__device__ __forceinline__ void load_layer_weights(MlpFwdSmem& sm, const __nv_bfloat16* packed, const MlpLayout& L,
-                                                   int l) {
-    const uint32_t wbytes = (uint32_t)(mlp_N(l) * mlp_K(l) * 2);
-    tc::mbar_expect_tx(&sm.bar_w, wbytes);
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(packed + L.p_off[l]);
-    for (uint32_t o = 0; o < wbytes; o += 32768u) {
-        const uint32_t nb = wbytes - o < 32768u ? wbytes - o : 32768u;
-        tc::bulk_g2s(sm.w + o, src + o, nb, &sm.bar_w);
+// Two floats -> BF16 (round to nearest even), a in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat162_raw h = __floats2bfloat162_rn(a, b);
+    return (uint32_t)h.x | ((uint32_t)h.y << 16);
+}
+
+// Producer: request the four chunks of streamed layer l (1..3).
+__device__ __forceinline__ void load_stream(MlpFwdSmem& sm, const unsigned char* packed_b, const MlpLayout& L, int l) {
+    const unsigned char* src = packed_b + 2 * L.p_off[l];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        tc::mbar_expect_tx(&sm.bar_w[c], 32768u);
+        tc::bulk_g2s(sm.w + 32768u * c, src + 32768u * c, 32768u, &sm.bar_w[c]);
     }
 }
 
-// 512 threads: warps w, w+4, w+8, w+12 share TMEM lane quarter w%4 (rows)
-// and split each layer's output columns in quarters for the epilogue (16
-// warps keep the TMEM-load / SFU / shared-store chain busy); the biases sit
-// in shared memory.  The next layer's weights are requested as soon as this
-// layer's MMAs have released the weight buffer, so the copy overlaps the
-// epilogue.
+// Warps 0-3: row tid of a tile's inputs (19 features; zeros past B) ...
+__device__ __forceinline__ void load_inputs(const float* __restrict__ x, int64_t B, int64_t row0, int tid,
+                                            float (&v)[19]) {
+    const int64_t row = row0 + tid;
+#pragma unroll
+    for (int j = 0; j < 19; ++j) v[j] = row < B ? __ldg(x + row * 19 + j) : 0.0f;
+}
+// ... into the A buffer in layer 0's layout (K = 32, zero padded), then
+// arrive on bar_in.
+__device__ __forceinline__ void store_inputs(MlpFwdSmem& sm, const float (&v)[19], int tid, int lane) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = 8 * q + 2 * j;
+            u[j] = pack_bf16x2(k < 19 ? v[k] : 0.0f, k + 1 < 19 ? v[k + 1] : 0.0f);
+        }
+        *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 8 * q, 32)) = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+    tc::fence_async_smem();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(&sm.bar_in);
+}
+
+// Epilogue of one 16-feature piece of chunk c (accumulator values v) for
+// row r: bias, SiLU, BF16 into the A buffer; then signal chunk c.
+__device__ __forceinline__ void epi_chunk(MlpFwdSmem& sm, const float (&v)[16], const float* bias, int c, int part,
+                                          int r, int lane) {
+    const int c0 = 64 * c + 16 * part;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            h[j] = __float2bfloat16_rn(silu_f(v[8 * q + j] + bias[c0 + 8 * q + j]));
+        *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, c0 + 8 * q, 256)) = *reinterpret_cast<uint4*>(h);
+    }
+    tc::tc_fence_before();
+    tc::fence_async_smem();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(&sm.bar_act[c]);
+}
+
 __global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const float* __restrict__ x, int64_t B,
                                                         const __nv_bfloat16* __restrict__ packed,
                                                         const float* __restrict__ params, float* __restrict__ y,
@@ -131,114 +203,148 @@ __global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const float* __
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     MlpFwdSmem& sm = *reinterpret_cast<MlpFwdSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, part = warp >> 2;
     const MlpLayout L = mlp_layout();
-    const int64_t row0 = (int64_t)blockIdx.x * 128;
+    const int64_t tiles = (B + 127) / 128;
     for (int i = tid; i < 4 * 256 + 16; i += kFwdThreads) {
         const int l = i >> 8, n = i & 255;
         sm.bias[i] = l < 4 ? params[L.b_off[l] + n] : (n < 6 ? params[L.b_off[4] + n] : 0.0f);
     }
     if (tid == 0) {
-        tc::mbar_init(&sm.bar_w, 1);
+        for (int c = 0; c < 4; ++c) { tc::mbar_init(&sm.bar_w[c], 1); tc::mbar_init(&sm.bar_act[c], kEpiWarps); }
+        tc::mbar_init(&sm.bar_res, 1);
         tc::mbar_init(&sm.bar_mma, 1);
+        tc::mbar_init(&sm.bar_in, kEpiWarps);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(&sm.tmem_base, 256);
+        tc::tmem_alloc(&sm.tmem_base, 512);
         tc::tmem_relinquish();
     }
-    __syncthreads();
-    if (tid == 0) load_layer_weights(sm, packed, L, 0);
-    // input tile: row r = tid (threads < 128), K = 32 (19 used)
-    if (tid < 128) {
-        const int64_t row = row0 + tid;
-        float v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = 0.0f;
-        if (row < B) {
-#pragma unroll
-            for (int j = 0; j < 19; ++j) v[j] = x[row * 19 + j];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(v[8 * q + j]);
-            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 8 * q, 32)) = *reinterpret_cast<uint4*>(h);
-        }
-    }
-    tc::fence_async_smem();
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = sm.tmem_base;
-    uint32_t ph_w = 0, ph_m = 0;
-    int failed = 0;  // block-uniform (decided with __syncthreads_or)
-    for (int l = 0; l < kMlpLayers; ++l) {
-        const int K = mlp_K(l), N = mlp_N(l);
-        const bool okw = tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
-        ph_w ^= 1;
-        if (__syncthreads_or(!okw)) { failed = 1; break; }
-        if (tid == 0) {
-            tc::tc_fence_after();
-            const uint32_t a0 = tc::smem_u32(sm.act), b0 = tc::smem_u32(sm.w);
-            const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-            const uint32_t idesc = tc::idesc_bf16(128, N);
-            for (int kk = 0; kk < K / 16; ++kk) {
-                const uint64_t ad = tc::sdesc(a0 + kk * 256u, 128u, sbo);
-                const uint64_t bd = tc::sdesc(b0 + kk * 256u, 128u, sbo);
-                tc::mma_bf16(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
-            }
-            tc::mma_commit(&sm.bar_mma);
-        }
-        const bool okm = tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit);
-        ph_m ^= 1;
-        if (__syncthreads_or(!okm)) { failed = 1; break; }
-        tc::tc_fence_after();
-        // the weight buffer is free: fetch the next layer's weights now
-        if (tid == 0 && l + 1 < kMlpLayers) load_layer_weights(sm, packed, L, l + 1);
-        // epilogue: rows 32*quarter + lane, column quarter `part`
-        const int r = 32 * quarter + lane;
-        const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
-        if (l < kMlpLayers - 1) {
-            const float* bias = sm.bias + 256 * l;
-            const int nc = N / 128;  // 32-column chunks per quarter of the columns
-            for (int cc = 0; cc < nc; ++cc) {
-                const int c = part * nc + cc;
-                float v[32];
-                tc::tmem_ld32(taddr + 32u * c, v);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(silu_f(v[8 * q + j] + bias[32 * c + 8 * q + j]));
-                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 32 * c + 8 * q, 256)) =
-                        *reinterpret_cast<uint4*>(h);
+    int failed = 0;
+    if (warp == kEpiWarps) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
+            tc::mbar_expect_tx(&sm.bar_res, 16384u + 8192u);
+            tc::bulk_g2s(sm.w0, pb + 2 * L.p_off[0], 16384u, &sm.bar_res);
+            tc::bulk_g2s(sm.w4, pb + 2 * L.p_off[4], 8192u, &sm.bar_res);
+            bool pending_w = blockIdx.x < tiles;   // a streamed layer requested and not yet waited
+            if (pending_w) load_stream(sm, pb, L, 1);
+            bool pending_mma = false;   // committed, completion not yet waited
+            bool issued = false;        // MMAs issued since the last commit
+            uint32_t ph_w = 0, ph_m = 0, ph_in = 0, ph_a[4] = {0, 0, 0, 0}, g = 0;
+            if (!tc::mbar_wait_bounded(&sm.bar_res, 0, kWaitLimit)) failed = 1;
+            for (int64_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+                for (int l = 0; l < kMlpLayers && !failed; ++l) {
+                    const uint32_t acc = tbase + ((g & 1u) ? 256u : 0u);
+                    const int N = mlp_N(l);
+                    const uint32_t idesc = tc::idesc_bf16(128, N);
+                    const bool streamed = l >= 1 && l <= 3;
+                    const int nch = l == 0 ? 1 : 4;
+                    for (int c = 0; c < nch && !failed; ++c) {
+                        if (l == 0) {
+                            if (!tc::mbar_wait_bounded(&sm.bar_in, ph_in, kWaitLimit)) { failed = 1; break; }
+                            ph_in ^= 1u;
+                        } else {
+                            if (!tc::mbar_wait_bounded(&sm.bar_act[c], ph_a[c], kWaitLimit)) { failed = 1; break; }
+                            ph_a[c] ^= 1u;
+                        }
+                        if (streamed && !tc::mbar_wait_bounded(&sm.bar_w[c], ph_w, kWaitLimit)) { failed = 1; break; }
+                        tc::tc_fence_after();
+                        const int KC = mlp_KC(l);
+                        const uint32_t sboA = l == 0 ? 512u : 4096u, sboB = (uint32_t)(KC / 8) * 128u;
+                        const uint32_t bch = tc::smem_u32(l == 0 ? sm.w0 : (streamed ? sm.w : sm.w4)) +
+                                             (uint32_t)c * (uint32_t)(N * KC * 2);
+                        for (int j = 0; j < KC / 16; ++j) {
+                            const int kk = c * (KC / 16) + j;
+                            const uint64_t ad = tc::sdesc(tc::smem_u32(sm.act) + 256u * kk, 128u, sboA);
+                            const uint64_t bd = tc::sdesc(bch + 256u * j, 128u, sboB);
+                            tc::mma_bf16(acc, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        }
+                        issued = true;
+                    }
+                    if (failed) break;
+                    if (streamed) { ph_w ^= 1u; pending_w = false; }
+                    tc::mma_commit(&sm.bar_mma);
+                    pending_mma = true;
+                    issued = false;
+                    ++g;
+                    // the layer's accumulator is done once the epilogue sees
+                    // it; the streamed buffer is free for the next layer
+                    if (!tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit)) { failed = 1; break; }
+                    ph_m ^= 1u;
+                    pending_mma = false;
+                    if (l == 1 || l == 2) { load_stream(sm, pb, L, l + 1); pending_w = true; }
+                    if (l == 3 && t + gridDim.x < tiles) { load_stream(sm, pb, L, 1); pending_w = true; }
                 }
             }
-        } else if (part == 0) {
-            const float* bias = sm.bias + 4 * 256;
-            float v[32];
-            tc::tmem_ld32(taddr, v);
-            const int64_t row = row0 + r;
-            if (row < B) {
-#pragma unroll
-                for (int j = 0; j < 6; ++j) y[row * 6 + j] = v[j] + bias[j];
+            if (failed) {
+                atomicOr(err, kErrMlpTimeout);
+                // let copies and MMAs in flight land before the CTA leaves
+                if (pending_w)
+                    for (int c = 0; c < 4; ++c) tc::mbar_wait_bounded(&sm.bar_w[c], ph_w, kWaitLimit);
+                if (issued && !pending_mma) { tc::mma_commit(&sm.bar_mma); pending_mma = true; }
+                if (pending_mma) tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit);
             }
         }
-        tc::fence_async_smem();
-        tc::tc_fence_before();
-        __syncthreads();
-        tc::tc_fence_after();
+    } else {
+        // ---------------- epilogue warps ----------------
+        const int quarter = warp & 3, part = warp >> 2;
+        const int r = 32 * quarter + lane;
+        uint32_t ph_m = 0, g = 0;
+        float xin[19];   // warps 0-3: the next tile's inputs, loaded a tile ahead
+        if (part == 0) {
+            load_inputs(x, B, (int64_t)blockIdx.x * 128, tid, xin);
+            store_inputs(sm, xin, tid, lane);
+            load_inputs(x, B, ((int64_t)blockIdx.x + gridDim.x) * 128, tid, xin);
+        } else if (lane == 0) {
+            tc::mbar_arrive(&sm.bar_in);
+        }
+        for (int64_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+            const int64_t row0 = t * 128;
+            for (int l = 0; l < kMlpLayers; ++l) {
+                if (!tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit)) { failed = 1; break; }
+                ph_m ^= 1u;
+                tc::tc_fence_after();
+                const uint32_t taddr = tbase + ((g & 1u) ? 256u : 0u) + ((uint32_t)(32 * quarter) << 16);
+                ++g;
+                if (l < kMlpLayers - 1) {
+                    const float* bias = sm.bias + 256 * l;
+#pragma unroll 1
+                    for (int c = 0; c < 4; ++c) {
+                        float v[16];
+                        tc::tmem_ld16(taddr + (uint32_t)(64 * c + 16 * part), v);
+                        epi_chunk(sm, v, bias, c, part, r, lane);
+                    }
+                } else if (part == 0) {
+                    const float* bias = sm.bias + 4 * 256;
+                    float v[16];
+                    tc::tmem_ld16(taddr, v);
+                    const int64_t row = row0 + r;
+                    if (row < B) {
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) y[row * 6 + j] = v[j] + bias[j];
+                    }
+                    tc::tc_fence_before();
+                    if (t + gridDim.x < tiles) {
+                        store_inputs(sm, xin, tid, lane);
+                        load_inputs(x, B, (t + 2 * (int64_t)gridDim.x) * 128, tid, xin);
+                    }
+                } else if (lane == 0 && t + gridDim.x < tiles) {
+                    tc::mbar_arrive(&sm.bar_in);
+                }
+            }
+        }
+        if (failed && lane == 0) atomicOr(err, kErrMlpTimeout);
     }
-    if (failed) {
-        if (tid == 0) atomicOr(err, kErrMlpTimeout);
-        // wait (bounded) for anything still in flight before freeing TMEM
-        tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit);
-        tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
-        __syncthreads();
-    }
-    if (warp == 0) tc::tmem_dealloc(tbase, 256);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
 cudaError_t mlp_pack(const float* params, void* packed, cudaStream_t st) {
@@ -252,7 +358,11 @@ cudaError_t mlp_forward(const float* x, int64_t B, const void* packed, const flo
     const size_t sm = sizeof(MlpFwdSmem);
     cudaError_t e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((B + 127) / 128);
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t tiles = (B + 127) / 128;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)nsm);
     mlp_fwd_kernel<<<grid, kFwdThreads, sm, st>>>(x, B, (const __nv_bfloat16*)packed, params, y, err);
     return cudaGetLastError();
 }
