@@ -113,7 +113,7 @@ struct MlpFwdSmem {
     alignas(1024) unsigned char w[256 * 256 * 2];     // B: streamed hidden layer, 4 chunks of 32 KB
     alignas(1024) unsigned char w0[256 * 32 * 2];     // B: layer 0 (resident)
     alignas(1024) unsigned char w4[16 * 256 * 2];     // B: layer 4 (resident)
-    float bias[4 * 256 + 16];                         // all layers' biases
+    float bias[4 * 256 + 16];                         // biases: halved for layers 0-3, as is for 4
     alignas(8) uint64_t bar_w[4];     // streamed weight chunk c landed
     alignas(8) uint64_t bar_res;      // resident weights landed
     alignas(8) uint64_t bar_mma;      // a layer's MMAs completed
@@ -177,20 +177,30 @@ __device__ __forceinline__ void store_inputs(MlpFwdSmem& sm, const float (&v)[19
     if (lane == 0) tc::mbar_arrive(&sm.bar_in);
 }
 
-// Epilogue of one 16-feature piece of chunk c (accumulator values v) for
-// row r: bias, SiLU, BF16 into the A buffer; then signal chunk c.
-__device__ __forceinline__ void epi_chunk(MlpFwdSmem& sm, const float (&v)[16], const float* bias, int c, int part,
+// Epilogue of one 16-feature piece of chunk c for row r: accumulator words
+// u (TMEM), hb = half the bias (smem).  h = z/2 = fma(0.5, acc, b/2) equals
+// 0.5 (acc + b) exactly (scaling by 2 commutes with rounding); silu =
+// h + h tanh(h); BF16 pairs by one cvt each; into the A buffer; then signal
+// chunk c.  Only the last chunk's signal carries the tcgen05 fence: the
+// next layer writes the other accumulator, and this one is rewritten only
+// after chunk 3 has been signalled.
+__device__ __forceinline__ void epi_chunk(MlpFwdSmem& sm, const uint32_t (&u)[16], const float* hb, int c, int part,
                                           int r, int lane) {
     const int c0 = 64 * c + 16 * part;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        __align__(16) __nv_bfloat16 h[8];
+        uint32_t p[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            h[j] = __float2bfloat16_rn(silu_f(v[8 * q + j] + bias[c0 + 8 * q + j]));
-        *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, c0 + 8 * q, 256)) = *reinterpret_cast<uint4*>(h);
+        for (int j = 0; j < 4; ++j) {
+            const int k = 8 * q + 2 * j;
+            const float h0 = fmaf(0.5f, __uint_as_float(u[k]), hb[c0 + k]);
+            const float h1 = fmaf(0.5f, __uint_as_float(u[k + 1]), hb[c0 + k + 1]);
+            const float s0 = fmaf(h0, tanh_approx(h0), h0), s1 = fmaf(h1, tanh_approx(h1), h1);
+            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p[j]) : "f"(s1), "f"(s0));   // s0 in the low half
+        }
+        *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, c0 + 8 * q, 256)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
-    tc::tc_fence_before();
+    if (c == 3) tc::tc_fence_before();
     tc::fence_async_smem();
     __syncwarp();
     if (lane == 0) tc::mbar_arrive(&sm.bar_act[c]);
@@ -207,7 +217,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const float* __
     const int64_t tiles = (B + 127) / 128;
     for (int i = tid; i < 4 * 256 + 16; i += kFwdThreads) {
         const int l = i >> 8, n = i & 255;
-        sm.bias[i] = l < 4 ? params[L.b_off[l] + n] : (n < 6 ? params[L.b_off[4] + n] : 0.0f);
+        sm.bias[i] = l < 4 ? 0.5f * params[L.b_off[l] + n] : (n < 6 ? params[L.b_off[4] + n] : 0.0f);
     }
     if (tid == 0) {
         for (int c = 0; c < 4; ++c) { tc::mbar_init(&sm.bar_w[c], 1); tc::mbar_init(&sm.bar_act[c], kEpiWarps); }
@@ -313,13 +323,21 @@ __global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const float* __
                 const uint32_t taddr = tbase + ((g & 1u) ? 256u : 0u) + ((uint32_t)(32 * quarter) << 16);
                 ++g;
                 if (l < kMlpLayers - 1) {
-                    const float* bias = sm.bias + 256 * l;
-#pragma unroll 1
-                    for (int c = 0; c < 4; ++c) {
-                        float v[16];
-                        tc::tmem_ld16(taddr + (uint32_t)(64 * c + 16 * part), v);
-                        epi_chunk(sm, v, bias, c, part, r, lane);
-                    }
+                    const float* hb = sm.bias + 256 * l;
+                    // chunk c + 1's TMEM load is in flight while chunk c is computed
+                    uint32_t ra[16], rb[16];
+                    tc::tmem_ld16_nowait(taddr + (uint32_t)(16 * part), ra);
+                    tc::tmem_wait_ld16(ra);
+                    tc::tmem_ld16_nowait(taddr + (uint32_t)(64 + 16 * part), rb);
+                    epi_chunk(sm, ra, hb, 0, part, r, lane);
+                    tc::tmem_wait_ld16(rb);
+                    tc::tmem_ld16_nowait(taddr + (uint32_t)(128 + 16 * part), ra);
+                    epi_chunk(sm, rb, hb, 1, part, r, lane);
+                    tc::tmem_wait_ld16(ra);
+                    tc::tmem_ld16_nowait(taddr + (uint32_t)(192 + 16 * part), rb);
+                    epi_chunk(sm, ra, hb, 2, part, r, lane);
+                    tc::tmem_wait_ld16(rb);
+                    epi_chunk(sm, rb, hb, 3, part, r, lane);
                 } else if (part == 0) {
                     const float* bias = sm.bias + 4 * 256;
                     float v[16];
