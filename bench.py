@@ -328,6 +328,26 @@ def run_ours(args, ws, rank, local):
         "clocks": ck,
     }
     if rank == 0 and not args.no_extra:
+        # box-wing, 1 sun direction, 1024^2 rays, K = 1 (one small call: launch-bound)
+        m1, rho1, sun1, com1 = W.config1()
+        b1 = srp.srp_build_bvh(ctx, m1.verts, m1.tris, m1.group, args.width)
+        r1 = torch.from_numpy(rho1[None].copy()).to(dev)
+        s1 = torch.from_numpy(sun1.copy()).to(dev)
+        c1 = torch.from_numpy(com1[None].copy()).to(dev)
+        o1 = torch.empty((1, 1, 6), dtype=torch.float64, device=dev)
+        for _ in range(3):
+            srp.srp_force(ctx, [b1], r1, s1, c1, out_ft=o1, rays_x=1024, max_bounces=1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            srp.srp_force(ctx, [b1], r1, s1, c1, out_ft=o1, rays_x=1024, max_bounces=1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_c1 = e0.elapsed_time(e1) / 20
+        line["box_wing"] = {"rays_per_s": 1024 * 1024 / (ms_c1 / 1e3), "ms_per_call": ms_c1,
+                            "note": "box-wing (16 triangles), 1 sun direction, 1024^2 rays, K=1, one srp_force "
+                                    "call per evaluation (three launches), device time"}
+        b1.close()
         # the same workload at K = 1 (primary hits only), device time, L2 flushed
         kw1 = dict(kw, max_bounces=1)
         srp.srp_force(ctx, [bvh], r_t, s_t, c_t, out_ft=out, **kw1)
@@ -352,6 +372,15 @@ def run_ours(args, ws, rank, local):
         line["cpu_baseline"] = {"value": val, "unit": "rays/s", "cores": os.cpu_count() or 1, "kind": "oracle",
                                 "sample": "2 sun directions x 4096 rays (strided over the 2048^2 grid), K<=3",
                                 "seconds": dt}
+        # the box-wing case in full: 1 sun direction, the whole 1024^2 grid, K = 1
+        import oracle
+        m1, rho1, sun1, com1 = W.config1()
+        t1 = time.perf_counter()
+        oracle.force(m1.verts, m1.tris, m1.group, rho1, sun1[0], com1, nx=1024, K=1)
+        t1 = time.perf_counter() - t1
+        line["cpu_baseline"]["box_wing_full"] = {
+            "value": 1024 * 1024 / t1, "unit": "rays/s", "seconds": t1,
+            "sample": "box-wing (16 triangles), 1 sun direction, the full 1024^2 grid, K=1"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -671,8 +700,9 @@ def batched_leg(srp, ctx, dev, sm_mhz):
 
 def design_leg(srp, ctx, dev):
     """Design optimisation through the tracer's gradient: 100 Adam steps on
-    the 14 reflectances of the 7-group box-wing against the forces of a
-    reference design at 64 suns (512^2 rays per sun, K = 1); each step
+    the 14 reflectances of the 7-group box-wing, and on the 128 reflectances
+    and 2 hinge angles of the first config-5 design, against the forces of
+    a reference design at 64 suns (512^2 rays per sun, K = 1); each step
     instantiates the design, builds its BVH, traces and back-propagates."""
     from paper_2602_10712_gb300.design import optimize_tracer
     m = W.box_wing_7group()
@@ -691,11 +721,33 @@ def design_leg(srp, ctx, dev):
     rho, _, losses = optimize_tracer(ctx, m, rho0, ang, sun, com, target, steps=100, lr=0.01, hinge_lo=ang,
                                      hinge_hi=ang, **kw)
     dt = time.perf_counter() - t0
-    return {"steps": 100, "steps_per_s": 100 / dt, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
-            "median_rho_err_start": float(np.median(np.abs(rho0 - rho_true))),
-            "median_rho_err_end": float(np.median(np.abs(rho - rho_true))),
-            "note": "optimize_tracer: srp_design_instantiate + srp_build_bvh + srp_force + srp_force_grad per step, "
-                    "64 suns x 512^2 rays, K = 1, host-mode calls (wall clock)"}
+    out = {"steps": 100, "steps_per_s": 100 / dt, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+           "median_rho_err_start": float(np.median(np.abs(rho0 - rho_true))),
+           "median_rho_err_end": float(np.median(np.abs(rho - rho_true))),
+           "note": "optimize_tracer: srp_design_instantiate + srp_build_bvh + srp_force + srp_force_grad per step, "
+                   "64 suns x 512^2 rays, K = 1, host-mode calls (wall clock)"}
+    # the first config-5 design (procedural satellite, hinged panels): 64
+    # groups' reflectances and both hinge angles free
+    d5 = W.config5_designs(1)[0]
+    rng = np.random.default_rng(6)
+    rho5 = rng.uniform(0.05, 0.45, size=(64, 2))
+    ang5 = np.array([0.25, -0.35])
+    v = srp.srp_design_instantiate(d5.verts, d5.vhinge, d5.hinges, ang5)
+    b = srp.srp_build_bvh(ctx, v, d5.tris, d5.group, 4)
+    target5 = srp.srp_force(ctx, [b], rho5.astype(np.float32)[None], sun, com[None], **kw)[0]
+    b.close()
+    rho50 = np.clip(rho5 + rng.choice([-0.1, 0.1], size=rho5.shape), 0.0, 0.5)
+    ang50 = ang5 + np.array([0.1, -0.1])
+    t0 = time.perf_counter()
+    r5, a5, l5 = optimize_tracer(ctx, d5, rho50, ang50, sun, com, target5, steps=100, lr=0.01, **kw)
+    dt5 = time.perf_counter() - t0
+    out["config5_design"] = {
+        "triangles": d5.T, "steps": 100, "steps_per_s": 100 / dt5, "loss_first": float(l5[0]),
+        "loss_last": float(l5[-1]), "median_rho_err_start": float(np.median(np.abs(rho50 - rho5))),
+        "median_rho_err_end": float(np.median(np.abs(r5 - rho5))),
+        "hinge_err_start": np.abs(ang50 - ang5).tolist(), "hinge_err_end": np.abs(a5 - ang5).tolist(),
+        "note": "first config-5 design; 64 groups x (rho_s, rho_d) and 2 hinge angles free; same per-step calls"}
+    return out
 
 
 def run_profile_case(case):

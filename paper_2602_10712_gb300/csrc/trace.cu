@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
 
 // ---------------------------------------------------------------------------
 // Span pre-pass (full-grid launches): which batches of 32 neighbouring
-// pixels can meet the scene.  One warp per (design, sun) item projects the
+// pixels can meet the scene.  One block per (design, sun) item projects the
 // BVH boxes three levels below the root (W = 4: up to 64; W = 8: two
 // levels, up to 64) onto the grid plane as pixel rectangles widened by 2 pixels
 // (FP32 rounding of the ray origins is ~1e-4 pixel); a ray outside every
@@ -429,54 +429,63 @@ __device__ __forceinline__ float4 top_rect(const DesignDev& dz, const ItemConst&
 
 template <int W>
 __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
-    __shared__ float4 rect[4][kTopBoxes];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
-    if (item >= (int64_t)p.D * p.S) return;
-    const int dl = (int)(item / p.S), s = (int)(item % p.S);
-    const DesignDev dz = p.designs[dl];
-    ItemConst ic;
-    item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s)), p.com + 3 * dl,
-               p.rho + (size_t)dl * p.G * 2, p.design_base + dl, p.sun_base + s);
-    for (int bi = lane; bi < kTopBoxes; bi += 32) rect[warp][bi] = top_rect<W>(dz, ic, bi);
-    __syncwarp();
-    const int nbx = p.nx / 32, ny = p.ny;
-    int32_t* ro = p.rowoff + (size_t)item * (ny + 1);
-    int32_t* rf = p.rowfirst + (size_t)item * ny;
-    int carry = 0;
-    for (int y0 = 0; y0 < ny; y0 += 32) {
-        const int y = y0 + lane;
-        int cnt = 0;
-        if (y < ny) {
-            float xmin = INFINITY, xmax = -INFINITY;
-            for (int j = 0; j < kTopBoxes; ++j) {
-                const float4 r = rect[warp][j];
-                if (r.z < (float)(y + 1) && r.w > (float)y) { xmin = fminf(xmin, r.x); xmax = fmaxf(xmax, r.y); }
+    __shared__ float4 rect[kTopBoxes];
+    __shared__ int wtot[4];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int64_t items = (int64_t)p.D * p.S;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int dl = (int)(item / p.S), s = (int)(item % p.S);
+        const DesignDev dz = p.designs[dl];
+        ItemConst ic;
+        item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s)),
+                   p.com + 3 * dl, p.rho + (size_t)dl * p.G * 2, p.design_base + dl, p.sun_base + s);
+        if (t < kTopBoxes) rect[t] = top_rect<W>(dz, ic, t);
+        __syncthreads();
+        const int nbx = p.nx / 32, ny = p.ny;
+        int32_t* ro = p.rowoff + (size_t)item * (ny + 1);
+        int32_t* rf = p.rowfirst + (size_t)item * ny;
+        int carry = 0;
+        for (int y0 = 0; y0 < ny; y0 += 128) {
+            const int y = y0 + t;
+            int cnt = 0;
+            if (y < ny) {
+                float xmin = INFINITY, xmax = -INFINITY;
+                for (int j = 0; j < kTopBoxes; ++j) {
+                    const float4 r = rect[j];
+                    if (r.z < (float)(y + 1) && r.w > (float)y) { xmin = fminf(xmin, r.x); xmax = fmaxf(xmax, r.y); }
+                }
+                int bf = 0;
+                if (xmin < xmax) {
+                    const int b0 = (int)floorf(fminf(fmaxf(xmin * (1.0f / 32.0f), 0.0f), (float)nbx));
+                    const int b1 = (int)ceilf(fminf(fmaxf(xmax * (1.0f / 32.0f), 0.0f), (float)nbx));
+                    if (b1 > b0) { bf = b0; cnt = b1 - b0; }
+                }
+                rf[y] = bf;
             }
-            int bf = 0;
-            if (xmin < xmax) {
-                const int b0 = (int)floorf(fminf(fmaxf(xmin * (1.0f / 32.0f), 0.0f), (float)nbx));
-                const int b1 = (int)ceilf(fminf(fmaxf(xmax * (1.0f / 32.0f), 0.0f), (float)nbx));
-                if (b1 > b0) { bf = b0; cnt = b1 - b0; }
-            }
-            rf[y] = bf;
-        }
-        int inc = cnt;
+            // exclusive prefix of the counts over rows: warp scans, then the
+            // warp totals in warp order
+            int inc = cnt;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int o = __shfl_up_sync(0xffffffffu, inc, off);
-            if (lane >= off) inc += o;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int o = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += o;
+            }
+            if (lane == 31) wtot[w] = inc;
+            __syncthreads();
+            int woff = 0;
+            for (int k = 0; k < w; ++k) woff += wtot[k];
+            if (y < ny) ro[y] = carry + woff + inc - cnt;
+            carry += wtot[0] + wtot[1] + wtot[2] + wtot[3];
+            __syncthreads();
         }
-        if (y < ny) ro[y] = carry + inc - cnt;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
+        if (t == 0) ro[ny] = carry;
     }
-    if (lane == 0) ro[ny] = carry;
 }
 
 cudaError_t launch_span(const TraceParams& p, int width, cudaStream_t st) {
     const int64_t items = (int64_t)p.D * p.S;
     if (items == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((items + 3) / 4);
+    const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)1 << 20);   // one block per item
     if (width == 8) span_kernel<8><<<grid, 128, 0, st>>>(p);
     else span_kernel<4><<<grid, 128, 0, st>>>(p);
     return cudaGetLastError();
@@ -501,17 +510,48 @@ __global__ void __launch_bounds__(128) trace_rays_kernel(const DesignDev dz, con
     for (int k = 0; k < p.K; ++k) out_hits[q * p.K + k] = hits[k];
 }
 
-// Sum each item's chunk partials in chunk order -> (F, tau), sigma.
-__global__ void reduce_items_kernel(const double* __restrict__ part, int64_t items, int cpb,
-                                    double* __restrict__ out_ft, double* __restrict__ out_sigma) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= items * 12) return;
-    const int64_t item = gid / 12;
-    const int q = (int)(gid % 12);
-    double t = 0.0;
-    for (int c = 0; c < cpb; ++c) t += part[((size_t)item * cpb + c) * 12 + q];
-    if (q < 6) out_ft[item * 6 + q] = t;
-    else if (out_sigma) out_sigma[item * 6 + (q - 6)] = sqrt(t);
+// Sum each item's chunk partials -> (F, tau), sigma.  One block per item
+// (grid-stride over items): thread t adds chunks t, t + 128, ... in chunk
+// order (a chunk's 12 sums are 96 contiguous bytes, so a warp's loads are
+// coalesced), then a fixed shuffle tree per warp and the four warp totals in
+// warp order -- the same summation order on every call.
+constexpr int kReduceThreads = 128;
+
+__global__ void __launch_bounds__(kReduceThreads) reduce_items_kernel(const double* __restrict__ part, int64_t items,
+                                                                     int cpb, double* __restrict__ out_ft,
+                                                                     double* __restrict__ out_sigma) {
+    __shared__ double wsum[12][kReduceThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        double acc[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+        const double2* base = reinterpret_cast<const double2*>(part + (size_t)item * cpb * 12);
+        for (int c = t; c < cpb; c += kReduceThreads) {
+#pragma unroll
+            for (int h = 0; h < 6; ++h) {
+                const double2 v = __ldg(base + (size_t)c * 6 + h);
+                acc[2 * h] += v.x;
+                acc[2 * h + 1] += v.y;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 12; ++q) wsum[q][w] = acc[q];
+        __syncthreads();
+        if (t < 12) {
+            double s = wsum[t][0];
+#pragma unroll
+            for (int k = 1; k < kReduceThreads / 32; ++k) s += wsum[t][k];
+            if (t < 6) out_ft[item * 6 + t] = s;
+            else if (out_sigma) out_sigma[item * 6 + (t - 6)] = sqrt(s);
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -576,10 +616,10 @@ cudaError_t launch_trace_rays(const DesignDev& dz, const TraceParams& p, const i
 
 cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* out_ft, double* out_sigma,
                           cudaStream_t st) {
-    const int64_t n = items * 12;
-    const int bs = 256;
-    const int64_t grid = (n + bs - 1) / bs;
-    reduce_items_kernel<<<(unsigned)grid, bs, 0, st>>>(part, items, cpb, out_ft, out_sigma);
+    if (items <= 0) return cudaSuccess;
+    if (reinterpret_cast<uintptr_t>(part) % 16 != 0) return cudaErrorMisalignedAddress;   // double2 loads
+    const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)1 << 20);
+    reduce_items_kernel<<<grid, kReduceThreads, 0, st>>>(part, items, cpb, out_ft, out_sigma);
     return cudaGetLastError();
 }
 
