@@ -429,8 +429,13 @@ def extra_legs(srp, ctx, dev, peaks):
     peak = peaks.get("bf16_tflops", 1900.0)
     surrogate = {"evals_per_s": nn_rate, "tracer_evals_per_s_256sq_rays": mc_rate, "speedup": nn_rate / mc_rate,
                  "force_rms_rel_err": err, "train_samples": info["samples"], "train_steps": info["steps"], "fit_s": fit_s,
+                 "data_s": info["data_s"], "train_s": info["train_s"],
+                 "train_samples_per_s": info["steps"] * 8192 / info["train_s"],
+                 "train_tflops": 3 * 2.0 * 203264 * 8192 * info["steps"] / info["train_s"] / 1e12,
                  "mlp_tflops": flops / t_nn / 1e12, "mlp_frac_of_bf16_peak": flops / t_nn / 1e12 / peak,
-                 "batch": nq, "note": "19-256x4-6 SiLU, BF16 tcgen05, FP32 accumulation; error vs 1024^2-ray MC"}
+                 "batch": nq, "note": "19-256x4-6 SiLU, BF16 tcgen05, FP32 accumulation; error vs 1024^2-ray MC; "
+                                      "training: batches of 8192 (fwd + bwd = 3 x 406 kFLOP per sample), wall clock "
+                                      "of the Python step loop"}
     # gradients: box-wing (64 groups, 2 hinges), K = 1, 1024^2 rays, 64 suns per call
     m1 = W.box_wing()
     ang = np.array([0.3, -0.5])

@@ -5,7 +5,7 @@
 // (element (r,k) at p[r*ld + k]) or transposed (p[k*ld + r]), so the same
 // kernel computes Z = H W^T (forward), dH = dZ W (backward, W read
 // transposed) and dW = dZ^T H (backward, both read transposed, K = batch).
-// CTA tile 128 x BN (BN <= 256, multiple of 32) x 64 in K: 128 threads
+// CTA tile 128 x BN (BN <= 128, multiple of 32) x 64 in K: 128 threads
 // convert a K chunk of A and B to BF16 into shared memory (K-major
 // no-swizzle core-matrix layout) while the tensor core works on the previous
 // chunk (double buffer, one mbarrier per buffer signalled by tcgen05.commit);
@@ -163,7 +163,7 @@ cudaError_t tc_gemm(GemmOp A, GemmOp B, int M, int N, int K, float alpha, float*
     if (M <= 0 || N <= 0) return cudaSuccess;
     GemmArgs g;
     g.A = A; g.B = B; g.M = M; g.N = N; g.K = K;
-    g.BN = std::min(256, (N + 31) / 32 * 32);
+    g.BN = std::min(128, (N + 31) / 32 * 32);   // N tiles of 128: twice the CTAs of 256 at N = 256
     g.k_split = k_split > 0 ? (k_split + kGemmBK - 1) / kGemmBK * kGemmBK : std::max(K, 1);
     g.alpha = alpha; g.C = C; g.ldc = ldc; g.atomic = atomic; g.err = err;
     const size_t sm = sizeof(GemmSmem);

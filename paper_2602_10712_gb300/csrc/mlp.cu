@@ -509,8 +509,10 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     float* dH = tb.dB;
     for (int l = kMlpLayers - 1; l >= 0; --l) {
         const int in = mlp_in(l), out = mlp_out(l);
-        // dW_l = dZ_l^T H_l  (K = batch, split over 1024-row slices, atomic)
-        e = tc_gemm(GemmOp{dZ, out, 1}, GemmOp{tb.H[l], in, 1}, out, in, Bi, 1.0f, grad + L.w_off[l], in, 1, 1024,
+        // dW_l = dZ_l^T H_l  (K = batch, split over 128-row slices and added
+        // atomically: the output is only out x in, so the batch is what
+        // spreads the work over the SMs -- 1024-row slices left 8-16 CTAs)
+        e = tc_gemm(GemmOp{dZ, out, 1}, GemmOp{tb.H[l], in, 1}, out, in, Bi, 1.0f, grad + L.w_off[l], in, 1, 128,
                     err, st);
         if (e != cudaSuccess) return e;
         colsum_kernel<<<out, 256, 0, st>>>(dZ, B, out, grad + L.b_off[l]);
