@@ -60,7 +60,7 @@ extern "C" {
 #define SRP_ECUDA 3           /* a CUDA runtime call failed                 */
 #define SRP_EDEVICE_LIMIT 4   /* a bounded device loop hit its limit        */
 #define SRP_ETIMEOUT 5        /* a bounded device wait gave up              */
-#define SRP_EUNSUPPORTED 6    /* valid request this build does not support  */
+#define SRP_EUNSUPPORTED 6    /* valid request the library does not support */
 
 typedef enum { SRP_MEM_HOST = 0, SRP_MEM_DEVICE = 1 } srp_mem;
 
