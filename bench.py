@@ -676,7 +676,8 @@ def batched_leg(srp, ctx, dev, sm_mhz):
     build_s = time.perf_counter() - t0
     bvh_bytes = sum(b.info()["device_bytes"] for b in bvhs)
     out = torch.zeros((D, S, 6), dtype=torch.float64, device=dev)
-    kw = dict(rays_x=nx, max_bounces=3, kernel_variant=best["kernel_variant"])
+    kw = dict(rays_x=nx, max_bounces=3, kernel_variant=best["kernel_variant"],
+              chunks_per_item=best["chunks_per_item"])
     g = srp.ForceGraph(ctx, bvhs, rho, sun, com, out, **kw)
     g.launch()
     srp.srp_sync(ctx)
