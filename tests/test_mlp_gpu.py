@@ -2,10 +2,13 @@
 numpy oracle (oracle/mlp.py) fed the same BF16 operands: weights and inputs
 rounded to bfloat16, hidden activations rounded to bfloat16 at the same
 points as the kernel.  What remains is FP32 (kernel) vs FP64 (oracle)
-accumulation and rare one-ulp BF16 rounding flips of an activation; the bound
-1e-2 * rms(y) per output is an order of magnitude above their measured size
-and two orders below an operand-layout or descriptor error (wrong row/column
-pairing gives O(rms) differences)."""
+accumulation and rare one-ulp BF16 rounding flips of an activation.  Their
+RMS effect does not depend on the batch (measured 4.3e-4 rms(y) at 1,000 rows,
+4.9e-4 at 58,445) but the largest one grows with the number of rows (6.1e-3
+and 1.3e-2 rms(y)).  The forward test therefore bounds the RMS deviation
+(3e-3 rms(y)) and the largest one (5e-2 rms(y)); an operand-layout or
+descriptor error (wrong row/column pairing) gives O(rms) differences, at
+least 20x above either bound."""
 import numpy as np
 import pytest
 
@@ -52,7 +55,10 @@ def srp():
     return srp
 
 
-@pytest.mark.parametrize("B", [1, 129, 1000])
+# 58,445 rows: three 128-row tiles per CTA of the persistent forward kernel
+# on 152 SMs (weights streamed across tiles, next inputs prefetched) and a
+# ragged last tile
+@pytest.mark.parametrize("B", [1, 129, 1000, 3 * 128 * 152 + 77])
 def test_forward_parity(srp, B):
     ctx = srp.Context(0)
     p = omlp.init_params(seed=7)
@@ -62,8 +68,9 @@ def test_forward_parity(srp, B):
     y = net.infer(x)
     yo = oracle_bf16(x, unflat(flat(p)))
     rms = np.sqrt(np.mean(yo ** 2))
-    err = np.abs(y - yo).max()
-    assert err <= 1e-2 * rms, (err, rms)
+    err = np.abs(y - yo)
+    assert np.sqrt(np.mean(err ** 2)) <= 3e-3 * rms, (np.sqrt(np.mean(err ** 2)), rms)
+    assert err.max() <= 5e-2 * rms, (err.max(), rms)
 
 
 def test_params_roundtrip_and_device_mode(srp):
