@@ -205,6 +205,34 @@ def test_sun_sharding_bitwise(srp, ctx):
     assert np.array_equal(full[0], np.concatenate([p1[0], p2[0]]))
 
 
+def test_more_items_than_one_grid(srp, ctx):
+    """2^20 + 4096 (design, sun) items -- more than the per-item kernels'
+    grids (2^20 blocks), so the span pre-pass and the reduction loop over
+    items: one call equals two half calls bit for bit (one chunk per item in
+    both), and sampled items match the oracle."""
+    import torch
+    m, rho, _, com = W.config1()
+    S = (1 << 20) + 4096
+    sun = W.fibonacci_directions(S)
+    b = _bvh(srp, ctx, m)
+    dev = torch.device("cuda:0")
+    r_t = torch.from_numpy(rho[None].copy()).to(dev)
+    c_t = torch.from_numpy(com[None].copy()).to(dev)
+    s_t = torch.from_numpy(sun).to(dev)
+    kw = dict(rays_x=32, rays_y=1, max_bounces=1)
+    full = srp.srp_force(ctx, [b], r_t, s_t, c_t, **kw)
+    h = S // 2
+    p1 = srp.srp_force(ctx, [b], r_t, s_t[:h].contiguous(), c_t, **kw)
+    p2 = srp.srp_force(ctx, [b], r_t, s_t[h:].contiguous(), c_t, sun_base=h, **kw)
+    srp.srp_sync(ctx)
+    assert torch.equal(full[0, :h], p1[0]) and torch.equal(full[0, h:], p2[0])
+    got = full[0].cpu().numpy()
+    R = b.info()["radius"]
+    for s in (0, 1, h, (1 << 20) - 1, 1 << 20, S - 1):
+        fo, _ = oracle.force(m.verts, m.tris, m.group, rho, sun[s], com, nx=32, ny=1, K=1, sun_base=s)
+        _assert_parity(got[s:s + 1], fo, R, what=f"sun {s}")
+
+
 # ------------------------------------------------------------------ edge cases
 def test_multi_design_uneven_and_sun_per_design(srp, ctx):
     """Three designs of 2, 16 and 320 triangles in one call, each with its own
