@@ -53,23 +53,35 @@ struct GemmSmem {
 };
 
 // Stage rows [r0, r0+R) x k [k0, k0+64) of an operand into smem (BF16).
-__device__ __forceinline__ void gemm_stage(unsigned char* dst, const GemmOp& op, int r0, int R, int rows_valid,
-                                           int k0, int k_end, int tid) {
-    for (int r = tid; r < R; r += 128) {
-        const int gr = r0 + r;
-        const bool rv = r < rows_valid;
-#pragma unroll 1
-        for (int k8 = 0; k8 < kGemmBK / 8; ++k8) {
-            __align__(16) __nv_bfloat16 h[8];
+// Items are (row r, 8-wide K chunk k8); a warp's 32 items are 8 rows x 4
+// chunks of one 8-row group, whose 16-byte slots in the core-matrix layout
+// are 512 contiguous bytes (no bank conflicts; one thread per row put a
+// warp's stores 1 KB apart).  An operand stored row-major in K is read with
+// two 16-byte loads per item when its base and leading dimension allow it.
+__device__ __forceinline__ void gemm_stage(unsigned char* dst, const GemmOp& op, bool vec, int r0, int R,
+                                           int rows_valid, int k0, int k_end, int tid) {
+    for (int it = tid; it < R * (kGemmBK / 8); it += 128) {
+        const int r = (it & 7) + 8 * (it >> 6), k8 = (it >> 3) & 7;
+        const int gr = r0 + r, kb = k0 + 8 * k8;
+        float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (r < rows_valid) {
+            if (!op.trans && vec && kb + 7 < k_end) {
+                const float4* q = reinterpret_cast<const float4*>(op.p + (int64_t)gr * op.ld + kb);
+                const float4 q0 = __ldg(q), q1 = __ldg(q + 1);
+                v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w;
+                v[4] = q1.x; v[5] = q1.y; v[6] = q1.z; v[7] = q1.w;
+            } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int k = k0 + 8 * k8 + j;
-                float v = 0.0f;
-                if (rv && k < k_end) v = op.trans ? op.p[(int64_t)k * op.ld + gr] : op.p[(int64_t)gr * op.ld + k];
-                h[j] = __float2bfloat16_rn(v);
+                for (int j = 0; j < 8; ++j) {
+                    const int k = kb + j;
+                    if (k < k_end) v[j] = op.trans ? op.p[(int64_t)k * op.ld + gr] : op.p[(int64_t)gr * op.ld + k];
+                }
             }
-            *reinterpret_cast<uint4*>(dst + tc::kmajor_off(r, 8 * k8, kGemmBK)) = *reinterpret_cast<uint4*>(h);
         }
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(v[j]);
+        *reinterpret_cast<uint4*>(dst + tc::kmajor_off(r, 8 * k8, kGemmBK)) = *reinterpret_cast<uint4*>(h);
     }
 }
 
@@ -96,6 +108,8 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmArgs g) {
     const uint32_t tbase = sm.tmem_base;
     const uint32_t idesc = tc::idesc_bf16(128, g.BN);
     const int mv = min(128, g.M - m0), nv = min(g.BN, g.N - n0);
+    const bool vec_a = (reinterpret_cast<uintptr_t>(g.A.p) & 15) == 0 && (g.A.ld & 3) == 0;
+    const bool vec_b = (reinterpret_cast<uintptr_t>(g.B.p) & 15) == 0 && (g.B.ld & 3) == 0;
     int failed = 0;  // block-uniform (decided with __syncthreads_or)
     for (int i = 0; i < nk; ++i) {
         const int buf = i & 1;
@@ -103,8 +117,8 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmArgs g) {
         if (i >= 2) ok = tc::mbar_wait_bounded(&sm.bar[buf], ((i >> 1) - 1) & 1, kGemmWait);
         if (__syncthreads_or(!ok)) { failed = 1; break; }
         const int k0 = kz0 + i * kGemmBK;
-        gemm_stage(sm.a[buf], g.A, m0, 128, mv, k0, kz1, tid);
-        gemm_stage(sm.b[buf], g.B, n0, g.BN, nv, k0, kz1, tid);
+        gemm_stage(sm.a[buf], g.A, vec_a, m0, 128, mv, k0, kz1, tid);
+        gemm_stage(sm.b[buf], g.B, vec_b, n0, g.BN, nv, k0, kz1, tid);
         tc::fence_async_smem();
         __syncthreads();
         if (tid == 0) {
