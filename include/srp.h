@@ -171,7 +171,12 @@ int srp_build_bvh_host(const float* verts, int V, const int32_t* tris, int T, in
  * Array memory is opts->mem (all host or all device).  Device-mem calls are
  * asynchronous; the scratch they use belongs to the context, so calls on
  * one context must not overlap on different streams.  Validation of rho
- * and sun_dir values happens only for host-mem calls. */
+ * and sun_dir values happens only for host-mem calls.  Whole grids
+ * (ray_count 0) with rays_x a multiple of 32 first find, per grid row, the
+ * batches of 32 pixels whose rays can meet the design (the BVH's top boxes
+ * projected onto the grid) and trace only those: the others deposit
+ * exactly nothing, so the estimate is the whole grid's, its sums grouped
+ * over the traced batches. */
 int srp_force(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho, int G,
               const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
               double* out_ft, double* out_sigma);
@@ -396,8 +401,9 @@ int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float* rho, int G
 /* CUDA graph of one srp_force evaluation: the same arguments (device
  * memory only, opts->mem = SRP_MEM_DEVICE) are captured once, with the
  * design table copied into the graph; srp_graph_launch replays the
- * evaluation (queue reset, one persistent trace launch over every
- * (design, sun, chunk) unit, reduction) on the context's stream, reading
+ * evaluation (queue reset, the batch pre-pass of whole grids, one
+ * persistent trace launch over every (design, sun, chunk) unit, reduction)
+ * on the context's stream, reading
  * rho/sun_dir/com and writing out_ft/out_sigma at the captured addresses.
  * The graph uses the context's scratch: no other srp_force or graph of the
  * same context may run concurrently. */
