@@ -19,3 +19,16 @@ def gpu_available():
         return torch.cuda.is_available()
     except Exception:
         return False
+
+
+def golden(name):
+    """key -> float of a `key value` fixture under tests/golden/ ('#' lines
+    are comments: each fixture states where its numbers come from)."""
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split()
+                out[k] = float(v)
+    return out

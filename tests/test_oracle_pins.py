@@ -317,15 +317,21 @@ def _plate(size, z=0.0, flip=False):
 
 
 def test_thermal_worked_number():
-    """Sec. 5.9: 100 GPUs x 700 W = 70 kW from a Lambertian emitter recoil
-    with 2/3 of the collimated momentum flux: about 1.55e-4 N.  An isolated
+    """Sec. 5.9 worked example (tests/golden/paper_worked_examples.txt):
+    70 kW from a Lambertian emitter recoil with 2/3 of the collimated
+    momentum flux, about 1.55e-4 N, 1.55e-7 m/s^2 on 1000 kg.  An isolated
     plate (nothing to hit) emitting 70 kW from one side."""
+    from conftest import golden
+    g = golden("paper_worked_examples.txt")
     v, t = _plate((2.0, 1.0))
-    emit = np.array([70e3 / 2.0], np.float32)            # W/m^2 over the 2 m^2 plate
+    emit = np.array([g["thermal_power_w"] / 2.0], np.float32)    # W/m^2 over the 2 m^2 plate
     ft, sg, n = oracle.force_thermal(v, t, np.zeros(2, np.int32), np.zeros((1, 2)), emit, np.zeros(3),
                                      density=100.0, P=1.0 / C_LIGHT)
-    assert np.allclose(ft[:3], [0.0, 0.0, -(2.0 / 3.0) * 70e3 / C_LIGHT], rtol=1e-6, atol=1e-15)
-    assert abs(np.linalg.norm(ft[:3]) - 1.55e-4) < 0.01 * 1.55e-4    # the paper's rounded figure (c = 3e8 m/s)
+    f = g["thermal_recoil_fraction"] * g["thermal_power_w"] / C_LIGHT
+    assert np.allclose(ft[:3], [0.0, 0.0, -f], rtol=1e-6, atol=1e-15)
+    tol = g["printed_rel_tol"]
+    assert abs(np.linalg.norm(ft[:3]) - g["thermal_recoil_n"]) < tol * g["thermal_recoil_n"]
+    assert abs(np.linalg.norm(ft[:3]) / 1000.0 - g["thermal_accel_m_s2"]) < tol * g["thermal_accel_m_s2"]
     assert n == 200
 
 

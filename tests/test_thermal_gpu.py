@@ -45,13 +45,19 @@ def _parity(ft, fo, Fs, R, tol=1e-5, what=""):
 
 
 def test_worked_number_on_gpu(srp, ctx):
-    """Sec. 5.9: 70 kW from a Lambertian emitter -> 70e3 * 2/3 / c N."""
+    """Sec. 5.9 worked example (tests/golden/paper_worked_examples.txt):
+    70 kW from a Lambertian emitter -> 70e3 * 2/3 / c N, ~1.55e-4 N."""
+    from conftest import golden
+    g = golden("paper_worked_examples.txt")
     m = W.flat_plate((2.0, 1.0), 2)
     b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
-    ft, n = srp.srp_force_thermal(ctx, [b], np.zeros((1, 1, 2), np.float32), np.array([[35e3]], np.float32),
+    ft, n = srp.srp_force_thermal(ctx, [b], np.zeros((1, 1, 2), np.float32),
+                                  np.array([[g["thermal_power_w"] / 2.0]], np.float32),
                                   np.zeros((1, 3)), 100.0, pressure=1.0 / C_LIGHT, out_samples=True)
     assert n[0] == 200
-    assert np.allclose(ft[0, :3], [0.0, 0.0, -(2.0 / 3.0) * 70e3 / C_LIGHT], rtol=1e-6, atol=1e-16)
+    f = g["thermal_recoil_fraction"] * g["thermal_power_w"] / C_LIGHT
+    assert np.allclose(ft[0, :3], [0.0, 0.0, -f], rtol=1e-6, atol=1e-16)
+    assert abs(np.linalg.norm(ft[0, :3]) - g["thermal_recoil_n"]) < g["printed_rel_tol"] * g["thermal_recoil_n"]
 
 
 @pytest.mark.parametrize("width", [4, 8])
