@@ -330,7 +330,10 @@ def run_ours(args, ws, rank, local):
                                   "(the kernel is bound by dependent-load latency and divergence, not by either "
                                   "roof)")},
         "traversal": {"node_visits_per_ray": vis / n_samp, "tri_tests_per_ray": tests / n_samp,
-                      "segments_per_ray": segs / n_samp, "bytes_per_ray": bytes_per_ray},
+                      "segments_per_ray": segs / n_samp, "bytes_per_ray": bytes_per_ray,
+                      "segments_per_s": segs / n_samp * value,
+                      "note": "per grid ray of the 2048^2 grid (batches that cannot meet the scene are counted "
+                              "and not traced); a segment is one closest-hit trace (primary or bounce)"},
         "clocks": ck,
     }
     if rank == 0 and not args.no_extra:
