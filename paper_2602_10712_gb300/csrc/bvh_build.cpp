@@ -7,9 +7,10 @@
 // amortised over all rays and directions of a design.
 //
 // Build: binary BVH by binned surface-area heuristic (16 bins per axis over
-// centroid bounds, leaf <= 4 triangles), then collapsed top-down into
-// 4- or 8-wide nodes by repeatedly opening the child of largest surface
-// area.  Node bounds are padded outward by a small relative epsilon so the
+// centroid bounds, split down to one triangle per leaf), then collapsed
+// top-down into 4- or 8-wide nodes by repeatedly opening the child of
+// largest surface area.  Node bounds are padded outward by a small relative
+// epsilon so the
 // FP32 slab test in the kernel never rejects a box whose triangle the
 // watertight triangle test would hit.
 #include <vector_types.h>
@@ -50,7 +51,12 @@ struct BNode {       // binary node
 };
 
 constexpr int kBins = 16;
-constexpr int kMaxLeaf = 4;
+// One triangle per leaf: a lane's leaf work is then one triangle test, and
+// the wide node tests (four boxes at once) do the sorting.  Measured on the
+// 49,776-triangle satellite, 512 suns x 2048^2 rays: leaves of <= 4, 2 and 1
+// triangles give 7.40, 8.70 and 8.77 G rays/s at K <= 3 (22.4, 23.9, 24.1 at
+// K = 1); the closest hit does not depend on the tree.
+constexpr int kMaxLeaf = 1;
 
 struct Builder {
     const std::vector<AABB>& pb;
