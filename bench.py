@@ -336,7 +336,9 @@ def run_ours(args, ws, rank, local):
                               "and not traced); a segment is one closest-hit trace (primary or bounce)"},
         "clocks": ck,
     }
-    if rank == 0 and not args.no_extra:
+    # the single-GPU legs and the CPU baseline run on one GPU only (N = 1):
+    # under N > 1 the other GPUs would sit idle while rank 0 measures them
+    if rank == 0 and ws == 1 and not args.no_extra:
         # box-wing, 1 sun direction, 1024^2 rays, K = 1 (one small call: launch-bound)
         m1, rho1, sun1, com1 = W.config1()
         b1 = srp.srp_build_bvh(ctx, m1.verts, m1.tris, m1.group, args.width)
@@ -375,7 +377,7 @@ def run_ours(args, ws, rank, local):
         line["batched_designs"] = batched_leg(srp, ctx, dev, sm_mhz)
         line["design_optimisation"] = design_leg(srp, ctx, dev)
         line["surrogate"], line["grad"] = extra_legs(srp, ctx, dev, peaks)
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
         val, dt = oracle_sample(m_, rho_, sun_, com_, 2, 4096)
         line["cpu_baseline"] = {"value": val, "unit": "rays/s", "cores": os.cpu_count() or 1, "kind": "oracle",
