@@ -131,7 +131,14 @@ int srp_ctx_create(srp_ctx** out, int device, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_queue, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->tab_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 4 * sizeof(unsigned long long));
-    if (e != cudaSuccess) { cudaFree(c->d_err); delete c; return cuda_fail(e, "ctx set-up"); }
+    if (e != cudaSuccess) {
+        if (c->tab_ev) cudaEventDestroy(c->tab_ev);
+        if (c->d_queue) cudaFree(c->d_queue);
+        if (c->d_stats) cudaFree(c->d_stats);
+        cudaFree(c->d_err);
+        delete c;
+        return cuda_fail(e, "ctx set-up");
+    }
     *out = c;
     return SRP_OK;
 }

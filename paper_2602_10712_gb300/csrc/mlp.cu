@@ -723,14 +723,26 @@ extern "C" int srp_mlp_infer(srp_ctx* c, const srp_mlp* m, const float* x, int64
         return SRP_OK;
     }
     if (mem != SRP_MEM_HOST) return mfail(SRP_EINVAL, "srp_mlp_infer: bad mem");
+    // host memory: stream-ordered staging, freed on every path out
     float *dx = nullptr, *dy = nullptr;
-    MCU(cudaMallocAsync((void**)&dx, sizeof(float) * 19 * B, st), "cudaMallocAsync");
-    MCU(cudaMallocAsync((void**)&dy, sizeof(float) * 6 * B, st), "cudaMallocAsync");
-    MCU(cudaMemcpyAsync(dx, x, sizeof(float) * 19 * B, cudaMemcpyHostToDevice, st), "H2D x");
-    MCU(mlp_forward(dx, B, m->packed, m->params, dy, ctx_err(c), st), "mlp forward launch");
-    MCU(cudaMemcpyAsync(y, dy, sizeof(float) * 6 * B, cudaMemcpyDeviceToHost, st), "D2H y");
-    MCU(cudaFreeAsync(dx, st), "cudaFreeAsync");
-    MCU(cudaFreeAsync(dy, st), "cudaFreeAsync");
+    cudaError_t e = cudaMallocAsync((void**)&dx, sizeof(float) * 19 * B, st);
+    const char* where = "cudaMallocAsync";
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&dy, sizeof(float) * 6 * B, st);
+    if (e == cudaSuccess) {
+        where = "H2D x";
+        e = cudaMemcpyAsync(dx, x, sizeof(float) * 19 * B, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) {
+        where = "mlp forward launch";
+        e = mlp_forward(dx, B, m->packed, m->params, dy, ctx_err(c), st);
+    }
+    if (e == cudaSuccess) {
+        where = "D2H y";
+        e = cudaMemcpyAsync(y, dy, sizeof(float) * 6 * B, cudaMemcpyDeviceToHost, st);
+    }
+    if (dx) cudaFreeAsync(dx, st);
+    if (dy) cudaFreeAsync(dy, st);
+    if (e != cudaSuccess) return mfail(SRP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
     return srp_sync(c);
 }
 

@@ -536,6 +536,14 @@ extern "C" int srp_integrate(srp_ctx* c, const srp_orbit_opts* oo, const srp_mlp
             off += outs[l];
         }
     }
+#define OCU_FREE(call, where)                                                                          \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            cleanup();                                                                                 \
+            return ofail(SRP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e_));              \
+        }                                                                                              \
+    } while (0)
     const double *d_z0 = z0, *d_th = theta, *d_lam = dL_dzN;
     double *d_zN = zN, *d_traj = traj, *d_dth = dL_dtheta, *d_dz0 = dL_dz0;
     const size_t zb = sizeof(double) * 13 * n_traj, tb = sizeof(double) * oo->n_theta * n_traj;
@@ -543,13 +551,14 @@ extern "C" int srp_integrate(srp_ctx* c, const srp_orbit_opts* oo, const srp_mlp
     if (mem == SRP_MEM_HOST) {
         double* a = (double*)dalloc(zb); double* b = (double*)dalloc(tb); double* cz = (double*)dalloc(zb);
         if (!a || !b || !cz) { cleanup(); return ofail(SRP_ENOMEM, "srp_integrate: staging"); }
-        OCU(cudaMemcpyAsync(a, z0, zb, cudaMemcpyHostToDevice, st), "H2D z0");
-        OCU(cudaMemcpyAsync(b, theta, tb, cudaMemcpyHostToDevice, st), "H2D theta");
+        OCU_FREE(cudaMemcpyAsync(a, z0, zb, cudaMemcpyHostToDevice, st), "H2D z0");
+        OCU_FREE(cudaMemcpyAsync(b, theta, tb, cudaMemcpyHostToDevice, st), "H2D theta");
         d_z0 = a; d_th = b; d_zN = cz;
         d_traj = traj ? (double*)dalloc(trb) : nullptr;
         if (adj) {
             double* l = (double*)dalloc(zb);
-            OCU(cudaMemcpyAsync(l, dL_dzN, zb, cudaMemcpyHostToDevice, st), "H2D lam");
+            if (!l) { cleanup(); return ofail(SRP_ENOMEM, "srp_integrate: staging"); }
+            OCU_FREE(cudaMemcpyAsync(l, dL_dzN, zb, cudaMemcpyHostToDevice, st), "H2D lam");
             d_lam = l;
             d_dth = dL_dtheta ? (double*)dalloc(tb) : nullptr;
             d_dz0 = dL_dz0 ? (double*)dalloc(zb) : nullptr;
@@ -559,23 +568,30 @@ extern "C" int srp_integrate(srp_ctx* c, const srp_orbit_opts* oo, const srp_mlp
         return ofail(SRP_EINVAL, "srp_integrate: bad mem");
     }
     double* ck = adj && n_ck > 0 ? (double*)dalloc(sizeof(double) * 13 * (size_t)n_ck * n_traj) : nullptr;
+    // a failed allocation must not reach a kernel as a NULL output
+    if ((traj && !d_traj) || (adj && n_ck > 0 && !ck) || (adj && dL_dtheta && !d_dth) ||
+        (adj && dL_dz0 && !d_dz0)) {
+        cleanup();
+        return ofail(SRP_ENOMEM, "srp_integrate: device scratch");
+    }
     rk4_forward_kernel<<<n_traj, 256, 0, st>>>(o, d_z0, d_th, d_zN, d_traj, ck, n_ck);
-    OCU(cudaGetLastError(), "rk4 forward launch");
+    OCU_FREE(cudaGetLastError(), "rk4 forward launch");
     if (adj) {
         if (n_ck > 0) {
             rk4_adjoint_kernel<<<n_traj, 256, 0, st>>>(o, d_th, ck, n_ck, d_lam, d_dth, d_dz0);
-            OCU(cudaGetLastError(), "rk4 adjoint launch");
+            OCU_FREE(cudaGetLastError(), "rk4 adjoint launch");
         } else {
-            if (d_dz0) OCU(cudaMemcpyAsync(d_dz0, d_lam, zb, cudaMemcpyDeviceToDevice, st), "copy");
-            if (d_dth) OCU(cudaMemsetAsync(d_dth, 0, tb, st), "memset");
+            if (d_dz0) OCU_FREE(cudaMemcpyAsync(d_dz0, d_lam, zb, cudaMemcpyDeviceToDevice, st), "copy");
+            if (d_dth) OCU_FREE(cudaMemsetAsync(d_dth, 0, tb, st), "memset");
         }
     }
     if (mem == SRP_MEM_HOST) {
-        OCU(cudaMemcpyAsync(zN, d_zN, zb, cudaMemcpyDeviceToHost, st), "D2H zN");
-        if (traj) OCU(cudaMemcpyAsync(traj, d_traj, trb, cudaMemcpyDeviceToHost, st), "D2H traj");
-        if (adj && dL_dtheta) OCU(cudaMemcpyAsync(dL_dtheta, d_dth, tb, cudaMemcpyDeviceToHost, st), "D2H dth");
-        if (adj && dL_dz0) OCU(cudaMemcpyAsync(dL_dz0, d_dz0, zb, cudaMemcpyDeviceToHost, st), "D2H dz0");
+        OCU_FREE(cudaMemcpyAsync(zN, d_zN, zb, cudaMemcpyDeviceToHost, st), "D2H zN");
+        if (traj) OCU_FREE(cudaMemcpyAsync(traj, d_traj, trb, cudaMemcpyDeviceToHost, st), "D2H traj");
+        if (adj && dL_dtheta) OCU_FREE(cudaMemcpyAsync(dL_dtheta, d_dth, tb, cudaMemcpyDeviceToHost, st), "D2H dth");
+        if (adj && dL_dz0) OCU_FREE(cudaMemcpyAsync(dL_dz0, d_dz0, zb, cudaMemcpyDeviceToHost, st), "D2H dz0");
     }
+#undef OCU_FREE
     cleanup();
     if (mem == SRP_MEM_HOST) return srp_sync(c);
     return SRP_OK;
