@@ -338,6 +338,7 @@ def run_ours(args, ws, rank, local):
     }
     # the single-GPU legs and the CPU baseline run on one GPU only (N = 1):
     # under N > 1 the other GPUs would sit idle while rank 0 measures them
+    orbit_check = None
     if rank == 0 and ws == 1 and not args.no_extra:
         # box-wing, 1 sun direction, 1024^2 rays, K = 1 (one small call: launch-bound)
         m1, rho1, sun1, com1 = W.config1()
@@ -377,6 +378,12 @@ def run_ours(args, ws, rank, local):
         line["batched_designs"] = batched_leg(srp, ctx, dev, sm_mhz)
         line["design_optimisation"] = design_leg(srp, ctx, dev)
         line["surrogate"], line["grad"] = extra_legs(srp, ctx, dev, peaks)
+        # the orbit integrator runs last: a failure there is recorded in the
+        # line and leaves the measurements above intact
+        try:
+            line["orbit"], orbit_check = orbit_leg(srp, ctx)
+        except Exception as exc:  # noqa: BLE001
+            line["orbit"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0 and ws == 1 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
         val, dt = oracle_sample(m_, rho_, sun_, com_, 2, 4096)
@@ -392,6 +399,11 @@ def run_ours(args, ws, rank, local):
         line["cpu_baseline"]["box_wing_full"] = {
             "value": 1024 * 1024 / t1, "unit": "rays/s", "seconds": t1,
             "sample": "box-wing (16 triangles), 1 sun direction, the full 1024^2 grid, K=1"}
+        if orbit_check:
+            try:
+                line["cpu_baseline"]["orbit"] = orbit_oracle(orbit_check)
+            except Exception as exc:  # noqa: BLE001
+                line["cpu_baseline"]["orbit"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -470,6 +482,81 @@ def extra_legs(srp, ctx, dev, peaks):
     grad = {"grad_evals_per_s": g_rate, "rays_per_eval": 1024 * 1024,
             "note": "d(F,tau)/d(64 x (rho_s, rho_d), 2 hinge angles), box-wing, K=1"}
     return surrogate, grad
+
+
+ORBIT_SUN = np.array([0.3, 0.5, 0.81]) / np.linalg.norm([0.3, 0.5, 0.81])
+ORBIT_STEPS = 1440      # one day of 60 s steps
+ORBIT_CKPT = 38         # checkpoint interval of the adjoint sweep
+
+
+def _orbit_cases(srp, ctx):
+    """(name, trajectories, orbit opts, theta [n][n_theta], proxy) of the
+    orbit leg: the cannonball model (theta = area x (1 + 4 rho_d / 9), m^2)
+    and the neural proxy (a seeded 19-256x4-6 network, theta = 14
+    reflectances and 2 hinge angles), on GPS-like circular orbits."""
+    net = srp.MLP(ctx, seed=3)
+    rng = np.random.default_rng(11)
+    th_p = np.concatenate([rng.uniform(0.0, 0.5, (256, 14)), rng.uniform(-0.5, 0.5, (256, 2))], axis=1)
+    common = dict(pressure=4.56e-6, mass=1000.0, sun=ORBIT_SUN, dt=60.0, n_steps=ORBIT_STEPS, ckpt_every=ORBIT_CKPT)
+    return [("cannonball", 1024, srp.orbit_opts(model=srp.SRP_FM_CANNONBALL, n_theta=1, **common),
+             rng.uniform(10.0, 30.0, (1024, 1)), None),
+            ("proxy", 256, srp.orbit_opts(model=srp.SRP_FM_PROXY, n_theta=16, **common), th_p, net)]
+
+
+def orbit_leg(srp, ctx):
+    """RK4 orbit + attitude (FP64) over one day, 1440 steps of 60 s, without
+    and with the discrete adjoint (checkpoints every 38 steps), through the
+    host-memory srp_integrate call (wall clock, copies included): 1024
+    trajectories under the cannonball model and 256 under the neural proxy
+    per call.  Returns the summary and, for the CPU leg's comparison, the
+    first trajectory's inputs and end state."""
+    out, check = {}, []
+    for name, n, o, th, net in _orbit_cases(srp, ctx):
+        z0 = W.orbit_states(n, seed=7)
+        wN = np.random.default_rng(1).normal(size=(n, 13)) * np.array([1e-3] * 3 + [1.0] * 3 + [1e3] * 4 + [1e4] * 3)
+        srp.srp_integrate(ctx, o, z0, th, proxy=net, dL_dzN=wN)  # warm-up
+        t0 = time.perf_counter()
+        r = srp.srp_integrate(ctx, o, z0, th, proxy=net)
+        t_f = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        srp.srp_integrate(ctx, o, z0, th, proxy=net, dL_dzN=wN)
+        t_a = time.perf_counter() - t0
+        out[name] = {"trajectories": n, "steps": ORBIT_STEPS, "forward_s": t_f, "forward_adjoint_s": t_a,
+                     "rk4_steps_per_s": n * ORBIT_STEPS / t_f,
+                     "rk4_steps_per_s_with_adjoint": n * ORBIT_STEPS / t_a}
+        check.append({"name": name, "z0": z0[0].copy(), "theta": th[0].copy(), "zN": r["zN"][0].copy(),
+                      "params": net.params() if net is not None else None})
+    out["note"] = ("srp_integrate (one CTA per trajectory), one day at dt = 60 s, two-body + J2 + SRP with attitude "
+                   "dynamics; wall clock of one host-memory call; FP64 and latency-bound (no roofline claim)")
+    return out, check
+
+
+def orbit_oracle(check):
+    """The FP64 oracle's RK4 on the first trajectory of each orbit case,
+    timed on the host, and its end position against the GPU's."""
+    from oracle import orbit as O
+    res = {}
+    for c in check:
+        if c["name"] == "cannonball":
+            m = O.Model("cannonball", P=4.56e-6, mass=1000.0, sun=ORBIT_SUN)
+        else:
+            flat, off, layers = c["params"], 0, []
+            sizes = (19, 256, 256, 256, 256, 6)
+            for i in range(5):
+                a, b = sizes[i], sizes[i + 1]
+                layers.append((flat[off:off + a * b].reshape(b, a).astype(np.float64),
+                               flat[off + a * b:off + a * b + b].astype(np.float64)))
+                off += a * b + b
+            m = O.Model("proxy", P=4.56e-6, mass=1000.0, sun=ORBIT_SUN, params=layers, scale=np.ones(19),
+                        offset=np.zeros(19), mean=np.zeros(6), std=np.ones(6))
+        t0 = time.perf_counter()
+        zN = O.rk4(m, c["z0"], c["theta"], 60.0, ORBIT_STEPS)
+        dt = time.perf_counter() - t0
+        res[c["name"]] = {"rk4_steps_per_s": ORBIT_STEPS / dt, "seconds": dt, "cores": 1,
+                          "sample": f"one trajectory, {ORBIT_STEPS} steps of 60 s, forward only",
+                          "end_position_rel_dev_vs_gpu": float(np.linalg.norm(zN[:3] - c["zN"][:3]) /
+                                                               np.linalg.norm(zN[:3]))}
+    return res
 
 
 def area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, width):

@@ -20,3 +20,58 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in line["config"]
+
+
+def test_orbit_leg_bookkeeping_with_an_oracle_binding(monkeypatch):
+    """The orbit leg's host logic (cases, shapes, rates, the hand-over of
+    the first trajectory to the CPU comparison) on a stand-in binding whose
+    srp_integrate runs the oracle's RK4 on trajectory 0: the comparison
+    then reports a zero deviation for both force models."""
+    import types
+
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import orbit as O
+    monkeypatch.setattr(bench, "ORBIT_STEPS", 6)
+    sizes = (19, 256, 256, 256, 256, 6)
+
+    class MLP:
+        def __init__(self, ctx, params=None, seed=0):
+            n = sum(a * b + b for a, b in zip(sizes[:-1], sizes[1:]))
+            self.p = (np.random.default_rng(seed).normal(size=n) * 0.05).astype(np.float32)
+
+        def params(self):
+            return self.p.copy()
+
+    def orbit_opts(**kw):
+        o = types.SimpleNamespace(in_scale=np.ones(19), in_offset=np.zeros(19), out_mean=np.zeros(6),
+                                  out_std=np.ones(6))
+        o.__dict__.update(kw)
+        return o
+
+    def srp_integrate(ctx, o, z0, th, proxy=None, want_traj=False, dL_dzN=None):
+        assert z0.shape[1] == 13 and th.shape == (z0.shape[0], o.n_theta)
+        if o.model == 1:
+            m = O.Model("cannonball", P=o.pressure, mass=o.mass, sun=o.sun)
+        else:
+            flat, off, layers = proxy.params(), 0, []
+            for a, b in zip(sizes[:-1], sizes[1:]):
+                layers.append((flat[off:off + a * b].reshape(b, a).astype(np.float64),
+                               flat[off + a * b:off + a * b + b].astype(np.float64)))
+                off += a * b + b
+            m = O.Model("proxy", P=o.pressure, mass=o.mass, sun=o.sun, params=layers, scale=o.in_scale,
+                        offset=o.in_offset, mean=o.out_mean, std=o.out_std)
+        zN = np.zeros((z0.shape[0], 13))
+        zN[0] = O.rk4(m, z0[0], th[0], o.dt, o.n_steps)
+        return {"zN": zN}
+
+    fake = types.SimpleNamespace(SRP_FM_CANNONBALL=1, SRP_FM_PROXY=2, MLP=MLP, orbit_opts=orbit_opts,
+                                 srp_integrate=srp_integrate)
+    summary, check = bench.orbit_leg(fake, None)
+    assert summary["cannonball"]["trajectories"] == 1024 and summary["proxy"]["trajectories"] == 256
+    assert all(summary[k]["rk4_steps_per_s"] > 0 for k in ("cannonball", "proxy"))
+    res = bench.orbit_oracle(check)
+    for k in ("cannonball", "proxy"):
+        assert res[k]["end_position_rel_dev_vs_gpu"] == 0.0 and res[k]["rk4_steps_per_s"] > 0

@@ -36,7 +36,7 @@ __all__ = [
     "Mesh", "box_wing", "box_wing_7group", "procedural_satellite",
     "random_reflectances", "fibonacci_directions", "random_unit_vectors",
     "config1", "config2", "config5_designs", "flat_plate", "icosphere",
-    "axis_box", "SUN_C1",
+    "axis_box", "SUN_C1", "orbit_states",
 ]
 
 #: Sun direction of the single-direction box-wing workload, e = (1,2,3)/|.|.
@@ -264,3 +264,26 @@ def config5_designs(n_designs: int = 256, t_lo: int = 5000, t_hi: int = 200000, 
         out.append(procedural_satellite(seed=1000 + k, dish_segments=seg, dish_rings=rings,
                                         n_boxes=nb, group_seed=2000 + k))
     return out
+
+
+def orbit_states(n: int, seed: int, radius: float = 26560e3, inc_deg: float = 55.0,
+                 gm: float = 3.986004418e14) -> np.ndarray:
+    """Initial states of the orbit workload, float64 [n, 13] = (r, v, q, w):
+    circular orbits of the given radius and inclination (a GPS-like orbit by
+    default) with the node and the argument of latitude uniform in
+    [0, 2 pi), a uniformly random unit attitude quaternion (scalar first)
+    and a body rate with components N(0, 1e-4) rad/s."""
+    rng = np.random.default_rng(seed)
+    raan = rng.uniform(0.0, 2.0 * math.pi, n)
+    u = rng.uniform(0.0, 2.0 * math.pi, n)
+    inc = math.radians(inc_deg)
+    speed = math.sqrt(gm / radius)
+    cO, sO, cu, su = np.cos(raan), np.sin(raan), np.cos(u), np.sin(u)
+    ci, si = math.cos(inc), math.sin(inc)
+    # in-plane unit vectors: radial p and along-track t
+    p = np.stack([cO * cu - sO * su * ci, sO * cu + cO * su * ci, su * si], axis=1)
+    t = np.stack([-cO * su - sO * cu * ci, -sO * su + cO * cu * ci, cu * si], axis=1)
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w = rng.normal(scale=1e-4, size=(n, 3))
+    return np.concatenate([radius * p, speed * t, q, w], axis=1)
