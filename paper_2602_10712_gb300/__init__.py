@@ -134,6 +134,47 @@ def _ptr(a):
     return _P(a.data_ptr())
 
 
+def _need(name, a, n, dtype, device, dev_index=None):
+    """Check that `a` can back the n elements of `dtype` the library reads
+    or writes through its pointer: a C-contiguous numpy array in host mode,
+    a contiguous CUDA tensor (on device `dev_index` when given) in device
+    mode, with at least n elements.  A smaller or mistyped buffer would be
+    an out-of-bounds access inside the library, so it is rejected here with
+    SRP_EINVAL."""
+    if a is None:
+        if n > 0:
+            raise SRPError(SRP_EINVAL, f"{name} is missing ({n} elements needed)")
+        return
+    dt = np.dtype(dtype)
+    if device:
+        import torch
+        tdt = getattr(torch, dt.name)
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == tdt and a.is_contiguous()):
+            raise SRPError(SRP_EINVAL, f"{name} must be a contiguous CUDA {tdt} tensor")
+        if dev_index is not None and a.device.index != dev_index:
+            raise SRPError(SRP_EINVAL, f"{name} is on cuda:{a.device.index}, the context on cuda:{dev_index}")
+        size = a.numel()
+    else:
+        if not (isinstance(a, np.ndarray) and a.dtype == dt and a.flags.c_contiguous):
+            raise SRPError(SRP_EINVAL, f"{name} must be a C-contiguous numpy {dt.name} array")
+        size = a.size
+    if size < n:
+        raise SRPError(SRP_EINVAL, f"{name} holds {size} elements; the call needs {n}")
+
+
+def _need_items(ctx, device, D, S, G, rho, sun_dir, com, per_design_sun, outs):
+    """Sizes of the (design, sun) calls: rho [D][G][2] float32, sun_dir
+    [S][3] (or [D][S][3]) float64, com [D][3] float64, and each output
+    (name, array, elements per item, dtype)."""
+    di = ctx.device if ctx is not None else None
+    _need("rho", rho, D * G * 2, np.float32, device, di)
+    _need("sun_dir", sun_dir, (D if per_design_sun else 1) * S * 3, np.float64, device, di)
+    _need("com", com, D * 3, np.float64, device, di)
+    for name, a, per, dt in outs:
+        if a is not None:
+            _need(name, a, per, dt, device, di)
+
+
 # ----------------------------------------------------------------- context
 class Context:
     """An srp_ctx bound to one device and one CUDA stream (a torch stream or
@@ -209,6 +250,8 @@ def srp_design_instantiate(verts, vhinge, hinges, angles):
     vh = _np(vhinge, np.int32)
     hg = _np(hinges, np.float64).reshape(-1, 6)
     an = _np(angles, np.float64).reshape(-1)
+    if hg.shape[0] > 0 and (vh.size < v.shape[0] or an.size < hg.shape[0]):
+        raise SRPError(SRP_EINVAL, "vhinge needs one entry per vertex and angles one per hinge")
     _check(lib.srp_design_instantiate(_ptr(v), v.shape[0], _ptr(vh), _ptr(hg), _ptr(an), hg.shape[0], _ptr(out)))
     return out
 
@@ -312,6 +355,8 @@ def srp_force(ctx: Context, bvhs, rho, sun_dir, com, out_ft=None, out_sigma=None
     if opts.get("sun_per_design"):
         if tuple(sun_dir.shape[:2]) != (D, S):
             raise ValueError("sun_dir must be [D,S,3] with sun_per_design")
+    _need_items(ctx, device, D, S, G, rho, sun_dir, com, opts.get("sun_per_design"),
+                [("out_ft", out_ft, D * S * 6, np.float64), ("out_sigma", out_sigma, D * S * 6, np.float64)])
     o = make_opts(**opts)
     _check(lib.srp_force(ctx.handle, arr, D, _ptr(rho), G, _ptr(sun_dir), S, _ptr(com), C.byref(o),
                          _ptr(out_ft), _ptr(out_sigma) if out_sigma is not None else None))
@@ -360,6 +405,9 @@ def srp_force_area(ctx: Context, bvhs, rho, sun_dir, com, density, out_ft=None, 
     if opts.get("sun_per_design"):
         if tuple(sun_dir.shape[:2]) != (D, S):
             raise ValueError("sun_dir must be [D,S,3] with sun_per_design")
+    _need_items(ctx, device, D, S, G, rho, sun_dir, com, opts.get("sun_per_design"),
+                [("out_ft", out_ft, D * S * 6, np.float64), ("out_sigma", out_sigma, D * S * 6, np.float64),
+                 ("out_samples", out_samples, D, np.int64)])
     o = make_opts(**opts)
     _check(lib.srp_force_area(ctx.handle, arr, D, _ptr(rho), G, _ptr(sun_dir), S, _ptr(com), float(density), C.byref(o),
                               _ptr(out_ft), _ptr(out_sigma) if out_sigma is not None else None,
@@ -409,6 +457,14 @@ def srp_force_thermal(ctx: Context, bvhs, rho, emit, com, density, out_ft=None, 
         if out_samples is True:
             out_samples = np.zeros(D, np.int64)
         opts["mem"] = SRP_MEM_HOST
+    di = ctx.device
+    _need("rho", rho, D * G * 2, np.float32, device, di)
+    _need("emit", emit, D * G, np.float32, device, di)
+    _need("com", com, D * 3, np.float64, device, di)
+    for name, a, n, dt in (("out_ft", out_ft, D * 6, np.float64), ("out_sigma", out_sigma, D * 6, np.float64),
+                           ("out_samples", out_samples, D, np.int64)):
+        if a is not None:
+            _need(name, a, n, dt, device, di)
     o = make_opts(**opts)
     _check(lib.srp_force_thermal(ctx.handle, arr, D, _ptr(rho), G, _ptr(emit), _ptr(com), float(density), C.byref(o),
                                  _ptr(out_ft), _ptr(out_sigma) if out_sigma is not None else None,
@@ -452,6 +508,20 @@ def srp_trace_samples(ctx: Context, mesh_verts, vhinge, hinges, tris, group, ang
         hits = torch.empty((N, K), dtype=torch.int32, device=sun.device) if want_hits else None
         opts.setdefault("mem", SRP_MEM_DEVICE)
     G = rho.shape[-2]
+    dm = opts["mem"] == SRP_MEM_DEVICE
+    di = ctx.device
+    if H:
+        _need("angles", angles, N * H, np.float64, dm, di)
+    _need("rho", rho, N * G * 2, np.float32, dm, di)
+    _need("sun", sun, N * 3, np.float64, dm, di)
+    _need("com", com, N * 3, np.float64, dm, di)
+    _need("out_y", y, N * 6, np.float64, dm, di)
+    if hits is not None:
+        _need("hits", hits, N * K, np.int32, dm, di)
+    if H and vh.shape[0] < v.shape[0]:
+        raise SRPError(SRP_EINVAL, "vhinge needs one entry per vertex")
+    if g.shape[0] < t.shape[0]:
+        raise SRPError(SRP_EINVAL, "group needs one entry per triangle")
     o = make_opts(**opts)
     _check(lib.srp_trace_samples(ctx.handle, _ptr(v), v.shape[0], _ptr(vh), _ptr(hg), H, _ptr(t), _ptr(g), t.shape[0],
                                  _ptr(angles), _ptr(rho), G, _ptr(sun), _ptr(com), N, _ptr(ce), float(radius),
@@ -476,6 +546,11 @@ def srp_trace_rays(ctx: Context, bvh: BVH, rho, sun_dir, com, ray_idx, sun_index
         y = torch.empty((ray_idx.shape[0], 6), dtype=torch.float64, device=rho.device)
         h = torch.empty((ray_idx.shape[0], K), dtype=torch.int32, device=rho.device)
         opts["mem"] = SRP_MEM_DEVICE
+    dm = opts["mem"] == SRP_MEM_DEVICE
+    _need("rho", rho, rho.shape[0] * 2, np.float32, dm, ctx.device)
+    _need("sun_dir", sun_dir, 3, np.float64, dm, ctx.device)
+    _need("com", com, 3, np.float64, dm, ctx.device)
+    _need("ray_idx", ray_idx, ray_idx.shape[0], np.int64, dm, ctx.device)
     o = make_opts(**opts)
     _check(lib.srp_trace_rays(ctx.handle, bvh.handle, _ptr(rho), rho.shape[0], _ptr(sun_dir), _ptr(com),
                               _ptr(ray_idx), ray_idx.shape[0], sun_index, design_index, C.byref(o), _ptr(y), _ptr(h)))
@@ -501,6 +576,10 @@ def srp_force_noalloc(bvhs, rho, sun_dir, com, out_ft, out_sigma=None, status=No
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     opts["mem"] = SRP_MEM_DEVICE
+    S = sun_dir.shape[-2]
+    _need_items(None, True, D, S, rho.shape[-2], rho, sun_dir, com, opts.get("sun_per_design"),
+                [("out_ft", out_ft, D * S * 6, np.float64), ("out_sigma", out_sigma, D * S * 6, np.float64),
+                 ("status", status, 1, np.int32)])
     o = make_opts(**opts)
     _check(lib.srp_force_noalloc(arr, D, _ptr(rho), rho.shape[-2], _ptr(sun_dir), sun_dir.shape[-2], _ptr(com),
                                  C.byref(o), _ptr(out_ft), _ptr(out_sigma), _ptr(status), _P(int(stream))))
@@ -528,6 +607,15 @@ def srp_force_grad(ctx: Context, bvh: BVH, rho, sun_dir, com, upstream, tri_hing
         d_rho = torch.empty((rho.shape[-2], 2), dtype=torch.float64, device=rho.device)
         d_h = torch.empty((max(H, 1),), dtype=torch.float64, device=rho.device)
         opts["mem"] = SRP_MEM_DEVICE
+    dm = opts["mem"] == SRP_MEM_DEVICE
+    G, S = rho.shape[-2], sun_dir.shape[-2]
+    _need("rho", rho, G * 2, np.float32, dm, ctx.device)
+    _need("sun_dir", sun_dir, S * 3, np.float64, dm, ctx.device)
+    _need("com", com, 3, np.float64, dm, ctx.device)
+    _need("upstream", up, S * 6, np.float64, dm, ctx.device)
+    if H > 0:
+        _need("tri_hinge", th, bvh.info()["n_tris"], np.int32, dm, ctx.device)
+        _need("hinge_axes", ha, H * 6, np.float64, dm, ctx.device)
     o = make_opts(**opts)
     _check(lib.srp_force_grad(ctx.handle, bvh.handle, _ptr(rho), rho.shape[-2], _ptr(sun_dir), sun_dir.shape[-2],
                               _ptr(com), _ptr(th), _ptr(ha), H, C.byref(o), _ptr(up), _ptr(d_rho),
@@ -601,6 +689,8 @@ class MLP:
         self.ctx = ctx
         h = _P()
         p = None if params is None else _np(params, np.float32)
+        if p is not None:
+            _need("params", p, mlp_param_count(), np.float32, False)
         _check(lib.srp_mlp_create(ctx.handle, _ptr(p), seed, C.byref(h)))
         self.handle = h
 
@@ -622,6 +712,7 @@ class MLP:
 
     def set_params(self, p):
         p = _np(p, np.float32)
+        _need("params", p, mlp_param_count(), np.float32, False)
         _check(load().srp_mlp_set_params(self.ctx.handle, self.handle, _ptr(p)))
 
     def infer(self, x, y=None):
@@ -635,6 +726,9 @@ class MLP:
             import torch
             y = torch.empty((x.shape[0], 6), dtype=torch.float32, device=x.device) if y is None else y
             mem = SRP_MEM_DEVICE
+        dm, B = mem == SRP_MEM_DEVICE, x.shape[0]
+        _need("x", x, B * 19, np.float32, dm, self.ctx.device)
+        _need("y", y, B * 6, np.float32, dm, self.ctx.device)
         _check(load().srp_mlp_infer(self.ctx.handle, self.handle, _ptr(x), x.shape[0], _ptr(y), mem))
         return y
 
@@ -645,6 +739,9 @@ class MLP:
         if host:
             x = _np(x, np.float32).reshape(-1, 19)
             t = _np(t, np.float32).reshape(-1, 6)
+        B = x.shape[0]
+        _need("x", x, B * 19, np.float32, not host, self.ctx.device)
+        _need("t", t, B * 6, np.float32, not host, self.ctx.device)
         loss = np.zeros(1, np.float32) if want_loss else None
         grad = np.zeros(mlp_param_count(), np.float32) if want_grad else None
         _check(load().srp_mlp_train_step(self.ctx.handle, self.handle, _ptr(x), _ptr(t), x.shape[0], float(lr),
@@ -664,6 +761,10 @@ class MLP:
             mem = SRP_MEM_DEVICE
         if wy.shape[0] != x.shape[0]:
             raise ValueError("wy must have the batch of x")
+        dm, B = mem == SRP_MEM_DEVICE, x.shape[0]
+        _need("x", x, B * 19, np.float32, dm, self.ctx.device)
+        _need("wy", wy, B * 6, np.float32, dm, self.ctx.device)
+        _need("gx", gx, B * 19, np.float32, dm, self.ctx.device)
         _check(load().srp_mlp_grad_input(self.ctx.handle, self.handle, _ptr(x), _ptr(wy), x.shape[0], _ptr(gx), mem))
         return gx
 
@@ -706,6 +807,8 @@ def srp_integrate(ctx: Context, opts: OrbitOpts, z0, theta, proxy=None, want_tra
     z0 = _np(z0, np.float64).reshape(-1, 13)
     n = z0.shape[0]
     th = _np(theta, np.float64).reshape(n, -1)
+    if th.shape[1] != opts.n_theta:
+        raise SRPError(SRP_EINVAL, f"theta has {th.shape[1]} values per trajectory, opts.n_theta = {opts.n_theta}")
     zN = np.zeros((n, 13))
     traj = np.zeros((n, opts.n_steps + 1, 13)) if want_traj else None
     lam = None if dL_dzN is None else _np(dL_dzN, np.float64).reshape(n, 13)
@@ -728,6 +831,9 @@ class ForceGraph:
         bv = list(bvhs)
         arr = (_P * max(len(bv), 1))(*[b.handle for b in bv])
         opts["mem"] = SRP_MEM_DEVICE
+        D, S = len(bv), sun_dir.shape[-2]
+        _need_items(ctx, True, D, S, rho.shape[-2], rho, sun_dir, com, opts.get("sun_per_design"),
+                    [("out_ft", out_ft, D * S * 6, np.float64), ("out_sigma", out_sigma, D * S * 6, np.float64)])
         o = make_opts(**opts)
         h = _P()
         _check(lib.srp_force_graph_create(ctx.handle, arr, len(bv), _ptr(rho), rho.shape[-2], _ptr(sun_dir),

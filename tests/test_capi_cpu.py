@@ -128,3 +128,42 @@ def test_opts_struct_matches_header():
     o = srp.make_opts()
     assert o.rays_x == 1024 and o.max_bounces == 1 and o.pressure == 1.0 and o.mem == srp.SRP_MEM_DEVICE
     assert C.sizeof(srp.TraceOpts) == 88 and srp.TraceOpts.pressure.offset == 24
+
+
+def test_binding_rejects_undersized_or_mistyped_buffers():
+    """Host-memory calls whose arrays are smaller than the sizes the call
+    implies, or of the wrong element type, are rejected by the binding with
+    SRP_EINVAL before the library is entered (the library would read or
+    write past their ends).  The stand-in context and BVH are never used."""
+    import types
+    ctx = types.SimpleNamespace(device=0, handle=None)
+    bvh = types.SimpleNamespace(handle=None, info=lambda: {"n_tris": 16})
+    m, rho, sun, com = W.config1()
+
+    def rejected(fn, *a, **kw):
+        with pytest.raises(srp.SRPError) as e:
+            fn(*a, **kw)
+        assert e.value.code == srp.SRP_EINVAL, str(e.value)
+        return str(e.value)
+
+    # two designs, one design's reflectances and COM
+    assert "rho" in rejected(srp.srp_force, ctx, [bvh, bvh], rho[None], sun, np.zeros((2, 3)))
+    assert "com" in rejected(srp.srp_force, ctx, [bvh, bvh], np.stack([rho, rho]), sun, com[None])
+    # outputs too small, of the wrong type or not contiguous
+    assert "out_ft" in rejected(srp.srp_force, ctx, [bvh], rho[None], sun, com[None], out_ft=np.zeros((1, 0, 6)))
+    assert "out_ft" in rejected(srp.srp_force, ctx, [bvh], rho[None], sun, com[None],
+                                out_ft=np.zeros((1, 1, 6), np.float32))
+    assert "out_sigma" in rejected(srp.srp_force, ctx, [bvh], rho[None], sun, com[None],
+                                   out_sigma=np.zeros((1, 1, 6))[:, :, ::2])
+    assert "out_samples" in rejected(srp.srp_force_area, ctx, [bvh], rho[None], sun, com[None], 10.0,
+                                     out_samples=np.zeros(1, np.int32))
+    assert "emit" in rejected(srp.srp_force_thermal, ctx, [bvh], rho[None], np.ones((0, 64), np.float32),
+                              com[None], 10.0)
+    assert "upstream" in rejected(srp.srp_force_grad, ctx, bvh, rho, W.fibonacci_directions(3), com,
+                                  np.ones((2, 6)))
+    assert "tri_hinge" in rejected(srp.srp_force_grad, ctx, bvh, rho, sun, com, np.ones((1, 6)),
+                                   tri_hinge=np.zeros(4, np.int32), hinge_axes=m.hinges)
+    assert "vhinge" in rejected(srp.srp_design_instantiate, m.verts, m.vhinge[:3], m.hinges, [0.1, 0.2])
+    assert "angles" in rejected(srp.srp_design_instantiate, m.verts, m.vhinge, m.hinges, [0.1])
+    o = srp.orbit_opts(n_theta=2)
+    assert "n_theta" in rejected(srp.srp_integrate, ctx, o, np.zeros(13), np.zeros(3))
