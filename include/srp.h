@@ -162,7 +162,10 @@ int srp_build_bvh_host(const float* verts, int V, const int32_t* tris, int T, in
 /* ---- force and torque (Sec. 3.2) ---------------------------------------- */
 /* For D designs (bvhs[d], built on this context) and S sun directions:
  *   rho      [D][G][2] float32  (rho_s, rho_d) per material group, each in
- *                               [0,1] with rho_s + rho_d <= 1; G <= 64
+ *                               [0,1] with rho_s + rho_d <= 1; G <= 64 and
+ *                               G above every group id of every design's
+ *                               mesh (else SRP_EINVAL; the same holds for
+ *                               every call below that takes rho and bvhs)
  *   sun_dir  [S][3] (or [D][S][3] with opts->sun_per_design) float64 unit
  *                               vectors toward the sun
  *   com      [D][3] float64     torque reference point (centre of mass)

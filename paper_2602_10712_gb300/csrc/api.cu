@@ -267,6 +267,8 @@ int srp_build_bvh(srp_ctx* c, const float* verts, int V, const int32_t* tris, co
     srp_bvh* h = new (std::nothrow) srp_bvh();
     if (!h) return fail(SRP_ENOMEM, "srp_build_bvh: out of host memory");
     h->device = c->device; h->width = width; h->T = T;
+    h->max_group = -1;
+    for (int t = 0; t < T; ++t) h->max_group = std::max(h->max_group, (int)group[t]);
     h->n_nodes = b.n_nodes; h->n_leaves = b.n_leaves; h->depth = b.depth;
     h->build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     for (int j = 0; j < 3; ++j) h->c[j] = cen[j];
@@ -418,6 +420,9 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
         if (h->device != c->device) return fail(SRP_EINVAL, "srp_force: bvh built on another device");
         if (w == 0) w = h->width;
         if (h->width != w) return fail(SRP_EUNSUPPORTED, "srp_force: all designs of one call need the same BVH width");
+        if (h->max_group >= G)
+            return fail(SRP_EINVAL, "srp_force: design " + std::to_string(d) + " uses material group " +
+                                        std::to_string(h->max_group) + " but rho has G = " + std::to_string(G) + " groups");
         DesignDev& dz = (*designs)[d];
         dz.tri = (const float4*)h->d_tri; dz.nodes = (const float4*)h->d_nodes;
         dz.cx = h->c[0]; dz.cy = h->c[1]; dz.cz = h->c[2]; dz.R = h->R;
@@ -827,6 +832,9 @@ int area_common(srp_ctx* c, int mode, const srp_bvh* const* bvhs, int D, const f
         if (h->device != c->device) return fail(SRP_EINVAL, fn + ": bvh built on another device");
         if (w == 0) w = h->width;
         if (h->width != w) return fail(SRP_EUNSUPPORTED, fn + ": all designs of one call need the same BVH width");
+        if (h->max_group >= G)
+            return fail(SRP_EINVAL, fn + ": design " + std::to_string(d) + " uses material group " +
+                                        std::to_string(h->max_group) + " but rho has G = " + std::to_string(G) + " groups");
         DesignDev& dz = designs[d];
         dz.tri = (const float4*)h->d_tri; dz.nodes = (const float4*)h->d_nodes;
         dz.cx = h->c[0]; dz.cy = h->c[1]; dz.cz = h->c[2]; dz.R = h->R;

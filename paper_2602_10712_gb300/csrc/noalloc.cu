@@ -142,6 +142,9 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
         if (h->device != dev) return fail(SRP_EINVAL, "srp_force_noalloc: bvh built on another device than the current one");
         if (width == 0) width = h->width;
         if (h->width != width) return fail(SRP_EUNSUPPORTED, "srp_force_noalloc: all designs of one call need the same BVH width");
+        if (h->max_group >= G)
+            return fail(SRP_EINVAL, "srp_force_noalloc: design " + std::to_string(d) + " uses material group " +
+                                        std::to_string(h->max_group) + " but rho has G = " + std::to_string(G) + " groups");
         DesignDev& z = designs[d];
         z.tri = (const float4*)h->d_tri; z.nodes = (const float4*)h->d_nodes;
         z.cx = h->c[0]; z.cy = h->c[1]; z.cz = h->c[2]; z.R = h->R;

@@ -118,4 +118,5 @@ struct srp_bvh {
     void* d_nodes;  // node data
     int64_t bytes;
     double area;    // total surface area (FP64, from the build's vertices)
+    int max_group;  // largest material group id of the mesh (-1 when empty)
 };

@@ -308,6 +308,10 @@ def test_invalid_arguments_rejected(srp, ctx):
         assert e.value.code == srp.SRP_EINVAL, kw
     with pytest.raises(srp.SRPError):
         srp.srp_build_bvh(ctx, m.verts, m.tris, np.full(16, 64, np.int32))
+    # the box-wing uses groups 0..15: reflectances for 8 groups are too few
+    with pytest.raises(srp.SRPError) as e:
+        srp.srp_force(ctx, [b], rho[None, :8], sun, com[None], rays_x=64)
+    assert e.value.code == srp.SRP_EINVAL and "group 15" in str(e.value)
 
 
 def test_bvh_info(srp, ctx):
