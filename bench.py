@@ -172,6 +172,11 @@ def allsum(ws, x):
 # --------------------------------------------------------------------------
 # CPU oracle leg (the reference arm and the cpu_baseline)
 # --------------------------------------------------------------------------
+def _oracle_threads():
+    import oracle
+    return oracle.host_threads()
+
+
 def oracle_sample(m, rho, sun, com, n_sun, n_rays):
     """Time the FP64 oracle on a bounded sample: n_sun directions x n_rays
     rays of the full 2048^2 grid (evenly strided)."""
@@ -191,7 +196,7 @@ def run_reference(args, ws, rank):
     import oracle
     oracle.build()
     m, rho, sun, com = W.config2(N_SUN)
-    cores = os.cpu_count() or 1
+    cores = oracle.host_threads()
     n_sun, n_rays = 1, 4096
     for _ in range(args.warmup):
         oracle_sample(m, rho, sun, com, n_sun, 1024)
@@ -387,7 +392,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
         val, dt = oracle_sample(m_, rho_, sun_, com_, 2, 4096)
-        line["cpu_baseline"] = {"value": val, "unit": "rays/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": val, "unit": "rays/s", "cores": _oracle_threads(), "kind": "oracle",
                                 "sample": "2 sun directions x 4096 rays (strided over the 2048^2 grid), K<=3",
                                 "seconds": dt}
         # the box-wing case in full: 1 sun direction, the whole 1024^2 grid, K = 1

@@ -46,6 +46,15 @@ import subprocess
 
 import numpy as np
 
+
+def host_threads() -> int:
+    """Worker threads of the multi-threaded oracle calls: the CPUs this
+    process may run on (its affinity mask), else the machine's count."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
 _SO = os.path.join(_LIBDIR, "libsrp_oracle.so")
@@ -144,7 +153,7 @@ def force(verts, tris, group, rho, sun, com, *, nx, ny=None, K=1, jitter=1, seed
     r = _c(rho, np.float64); s = _c(np.atleast_2d(sun), np.float64); cm = _c(com, np.float64)
     S = s.shape[0]
     ft = np.zeros((S, 6)); sg = np.zeros((S, 6))
-    threads = threads or os.cpu_count() or 1
+    threads = threads or host_threads()
     rc = lib.or_force(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), r.shape[0], _p(s), S, _p(cm),
                       nx, ny, K, jitter, seed, P, ray_offset, ray_stride, ray_count,
                       sun_base, design_index, threads, _p(ft), _p(sg),
@@ -169,7 +178,7 @@ def force_grad(verts, tris, group, rho, sun, com, upstream, *, nx, ny=None, K=1,
     else:
         th = _c(tri_hinge, np.int32); ha = _c(hinge_axes, np.float64).reshape(-1, 6); H = ha.shape[0]
     ft = np.zeros((S, 6)); drho = np.zeros((G, 2)); dh = np.zeros(max(H, 1))
-    threads = threads or os.cpu_count() or 1
+    threads = threads or host_threads()
     rc = lib.or_force(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), G, _p(s), S, _p(cm),
                       nx, ny, K, jitter, seed, P, ray_offset, ray_stride, ray_count,
                       sun_base, design_index, threads, _p(ft), None,
@@ -208,7 +217,7 @@ def trace_rays(verts, tris, group, rho, sun, com, ray_idx, *, nx, ny=None, K=1, 
     y = np.zeros((idx.shape[0], 6)); h = np.zeros((idx.shape[0], K), np.int32)
     rc = lib.or_trace_rays(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(s), _p(cm),
                            nx, ny, K, jitter, seed, P, sun_index, design_index, _p(idx), idx.shape[0],
-                           _p(y), _p(h), threads or os.cpu_count() or 1)
+                           _p(y), _p(h), threads or host_threads())
     if rc != 0:
         raise ValueError("oracle trace_rays: bad arguments")
     return y, h
@@ -232,7 +241,7 @@ def force_area(verts, tris, group, rho, sun, com, *, density, seed=0, P=1.0, sun
     S = s.shape[0]
     ft = np.zeros((S, 6)); sg = np.zeros((S, 6))
     lib.or_force_area(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(s), S, _p(cm), float(density), seed,
-                      P, sun_base, design_index, threads or os.cpu_count() or 1, _p(ft), _p(sg))
+                      P, sun_base, design_index, threads or host_threads(), _p(ft), _p(sg))
     return ft, sg
 
 
@@ -252,7 +261,7 @@ def force_thermal(verts, tris, group, rho, emit, com, *, density, seed=0, P=1.0,
     r = _c(rho, np.float64); e = _c(emit, np.float32); cm = _c(com, np.float64)
     ft = np.zeros(6); sg = np.zeros(6); n = np.zeros(1, np.int64)
     lib.or_force_thermal(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(e), _p(cm), float(density), seed,
-                         P, design_index, threads or os.cpu_count() or 1, _p(ft), _p(sg), _p(n))
+                         P, design_index, threads or host_threads(), _p(ft), _p(sg), _p(n))
     return ft, sg, int(n[0])
 
 
@@ -269,7 +278,7 @@ def trace_samples(verts, vhinge, hinges, tris, group, angles, rho, sun, com, cen
     H = hg.shape[0]
     y = np.zeros((N, 6)); hits = np.zeros((N, K), np.int32)
     lib.or_trace_samples(_p(v), v.shape[0], _p(vh), _p(hg), H, _p(t), _p(g), t.shape[0], _p(an), _p(r), r.shape[-2],
-                         _p(sn), _p(cm), N, _p(ce), float(R), K, seed, P, sample_base, threads or os.cpu_count() or 1,
+                         _p(sn), _p(cm), N, _p(ce), float(R), K, seed, P, sample_base, threads or host_threads(),
                          _p(y), _p(hits))
     return y, hits
 

@@ -22,6 +22,25 @@ def test_reference_arm_json_line():
     assert "workload" in line["config"]
 
 
+def test_reference_arm_under_torchrun_two_ranks():
+    """Launched as the multi-GPU benchmark is (torchrun, two ranks; gloo on
+    a machine without GPUs): rank 0 alone runs the oracle and prints one
+    line with n_gpus = 2; the other rank exits 0 without work."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "0"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
 def test_orbit_leg_bookkeeping_with_an_oracle_binding(monkeypatch):
     """The orbit leg's host logic (cases, shapes, rates, the hand-over of
     the first trajectory to the CPU comparison) on a stand-in binding whose
