@@ -107,7 +107,7 @@ def test_projected_area_pin_on_gpu(srp, ctx):
                               np.tile([0.0, 0.0, 1.0], (N, 1)), np.zeros((N, 3)), np.zeros(3), 6.0, seed=9)
     A = 144.0
     p = (1.0 + 40.0 / np.pi) / A
-    assert abs(y[:, 2].mean() + (1.0 + 40.0 / np.pi)) <= 4 * 1.2 * A * np.sqrt(p * (1 - p) / N)
+    assert abs(y[:, 2].mean() + (1.0 + 40.0 / np.pi)) <= 3 * 1.2 * A * np.sqrt(p * (1 - p) / N)
 
 
 def test_errors(srp, ctx):

@@ -287,12 +287,14 @@ def test_zero_items(srp, ctx):
 
 
 def test_statistical_agreement_other_seed(srp, ctx):
-    """GPU and oracle with different seeds agree within 4 sigma."""
+    """GPU and oracle with different seeds agree within 3 sigma per
+    component (the criterion for two independent estimates of the same
+    integral)."""
     m, rho, sun, com = W.config1()
     b = _bvh(srp, ctx, m)
     ft, sg = srp.srp_force(ctx, [b], rho[None], sun, com[None], out_sigma=True, rays_x=512, max_bounces=3, seed=77)
     fo, so = oracle.force(m.verts, m.tris, m.group, rho, sun, com, nx=512, K=3, seed=78)
-    tol = 4 * np.sqrt(sg[0, 0] ** 2 + so[0] ** 2) + 1e-12
+    tol = 3 * np.sqrt(sg[0, 0] ** 2 + so[0] ** 2) + 1e-12
     assert np.all(np.abs(ft[0, 0] - fo[0]) <= tol)
 
 
