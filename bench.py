@@ -409,6 +409,11 @@ def run_ours(args, ws, rank, local):
                 line["cpu_baseline"]["orbit"] = orbit_oracle(orbit_check)
             except Exception as exc:  # noqa: BLE001
                 line["cpu_baseline"]["orbit"] = {"error": f"{type(exc).__name__}: {exc}"}
+        if not args.no_extra:
+            try:
+                line["cpu_baseline"].update(oracle_extra_legs())
+            except Exception as exc:  # noqa: BLE001
+                line["cpu_baseline"]["extra_error"] = f"{type(exc).__name__}: {exc}"
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -562,6 +567,44 @@ def orbit_oracle(check):
                           "end_position_rel_dev_vs_gpu": float(np.linalg.norm(zN[:3] - c["zN"][:3]) /
                                                                np.linalg.norm(zN[:3]))}
     return res
+
+
+def oracle_extra_legs():
+    """The oracle beside the gradient and proxy legs, on the host cores and
+    the same workloads: gradient evaluations (box-wing, 64 groups x
+    (rho_s, rho_d) and 2 hinge angles, K = 1, the whole 1024^2 grid, 64
+    suns), the FP64 proxy forward (16,384 queries) and tracer evaluations at
+    the proxy's training accuracy (7-group box-wing, 256^2 rays, K <= 3, 64
+    suns)."""
+    import oracle
+    from oracle import mlp as omlp
+    out = {}
+    m1 = W.box_wing()
+    ang = np.array([0.3, -0.5])
+    v1 = oracle.instantiate(m1.verts, m1.vhinge, m1.hinges, ang)
+    sun = W.fibonacci_directions(64)
+    t0 = time.perf_counter()
+    oracle.force_grad(v1, m1.tris, m1.group, W.random_reflectances(64, seed=0), sun, np.zeros(3), np.ones((64, 6)),
+                      nx=1024, K=1, tri_hinge=oracle.tri_hinge(m1.tris, m1.vhinge), hinge_axes=m1.hinges)
+    dt = time.perf_counter() - t0
+    out["grad"] = {"grad_evals_per_s": 64 / dt, "seconds": dt, "cores": oracle.host_threads(),
+                   "sample": "box-wing, 64 suns x the whole 1024^2 grid, K=1, 64 groups and 2 hinges"}
+    params = omlp.init_params(seed=1)
+    x = np.random.default_rng(3).uniform(-1.0, 1.0, size=(1 << 14, 19))
+    t0 = time.perf_counter()
+    omlp.forward(x, params)
+    dt = time.perf_counter() - t0
+    out["surrogate"] = {"evals_per_s": x.shape[0] / dt, "seconds": dt,
+                        "sample": "FP64 forward of the 19-256x4-6 proxy on 16,384 queries (numpy, host BLAS threads)"}
+    m7 = W.box_wing_7group()
+    v7 = oracle.instantiate(m7.verts, m7.vhinge, m7.hinges, np.array([0.2, -0.4]))
+    rho7 = W.random_reflectances(7, seed=2)
+    t0 = time.perf_counter()
+    oracle.force(v7, m7.tris, m7.group, rho7, sun, np.zeros(3), nx=256, K=3)
+    dt = time.perf_counter() - t0
+    out["tracer_evals_per_s_256sq_rays"] = {"value": 64 / dt, "seconds": dt, "cores": oracle.host_threads(),
+                                            "sample": "7-group box-wing, 64 suns x 256^2 rays, K<=3"}
+    return out
 
 
 def area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, width):

@@ -94,3 +94,14 @@ def test_orbit_leg_bookkeeping_with_an_oracle_binding(monkeypatch):
     res = bench.orbit_oracle(check)
     for k in ("cannonball", "proxy"):
         assert res[k]["end_position_rel_dev_vs_gpu"] == 0.0 and res[k]["rk4_steps_per_s"] > 0
+
+
+def test_oracle_legs_beside_gradient_and_proxy():
+    """The CPU legs that time the oracle beside the GPU gradient, proxy and
+    256^2-ray tracer legs run on the host and report positive rates."""
+    sys.path.insert(0, ROOT)
+    import bench
+    out = bench.oracle_extra_legs()
+    assert out["grad"]["grad_evals_per_s"] > 0 and out["grad"]["cores"] >= 1
+    assert out["surrogate"]["evals_per_s"] > 0
+    assert out["tracer_evals_per_s_256sq_rays"]["value"] > 0
