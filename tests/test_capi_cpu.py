@@ -167,3 +167,22 @@ def test_binding_rejects_undersized_or_mistyped_buffers():
     assert "angles" in rejected(srp.srp_design_instantiate, m.verts, m.vhinge, m.hinges, [0.1])
     o = srp.orbit_opts(n_theta=2)
     assert "n_theta" in rejected(srp.srp_integrate, ctx, o, np.zeros(13), np.zeros(3))
+
+
+def test_plain_c_caller(tmp_path):
+    """The ABI as a C program sees it: tests/c_abi_host.c includes
+    include/srp.h, links libsrp.so and calls the host-only entry points."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib = srp._build.build()
+    libdir = os.path.dirname(lib)
+    exe = str(tmp_path / "c_abi_host")
+    r = subprocess.run([gcc, "-std=c11", "-O1", "-Wall", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c_abi_host.c"), "-L", libdir, "-lsrp", f"-Wl,-rpath,{libdir}",
+                        "-lm", "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and "c-abi ok" in r.stdout, r.stdout + r.stderr
