@@ -321,6 +321,18 @@ int srp_mlp_grad_input(srp_ctx* ctx, srp_mlp* mlp, const float* x, const float* 
  * size or tag is SRP_EINVAL. */
 int srp_mlp_save(srp_ctx* ctx, const srp_mlp* mlp, const char* path);
 int srp_mlp_load(srp_ctx* ctx, srp_mlp* mlp, const char* path);
+/* Trainer state for checkpoint and resume of training (Sec. 3.3 trains the
+ * proxy by Adam): parameters, both Adam moment vectors and the step count.
+ * File: 8-byte tag "SRPMLS1\0", int64 P, int64 step, then parameters, first
+ * moments and second moments as float32 [P] each (host byte order).  Save
+ * waits for the context's stream; load replaces all of it, so the next
+ * srp_mlp_train_step continues the interrupted run (the weight-gradient
+ * reduction sums in a run-dependent FP32 order, so a resumed run matches an
+ * uninterrupted one to that rounding, not bit for bit).  A file of another
+ * tag or size, or with non-finite or negative second moments, is SRP_EINVAL
+ * and leaves the network unchanged. */
+int srp_mlp_save_state(srp_ctx* ctx, const srp_mlp* mlp, const char* path);
+int srp_mlp_load_state(srp_ctx* ctx, srp_mlp* mlp, const char* path);
 
 /* ---- orbit integration and its adjoint (Sec. 3.4, Eq. "ODE", RK4 of
  * Sec. 3.4.1, adjoint of Sec. 3.4.3) --------------------------------------

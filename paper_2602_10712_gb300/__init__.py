@@ -109,6 +109,8 @@ def _load_locked(build_if_needed: bool):
     lib.srp_mlp_grad_input.argtypes = [_P, _P, _P, _P, i64, _P, i32]
     lib.srp_mlp_save.argtypes = [_P, _P, C.c_char_p]
     lib.srp_mlp_load.argtypes = [_P, _P, C.c_char_p]
+    lib.srp_mlp_save_state.argtypes = [_P, _P, C.c_char_p]
+    lib.srp_mlp_load_state.argtypes = [_P, _P, C.c_char_p]
     lib.srp_force_noalloc.argtypes = [_P, i32, _P, i32, _P, i32, _P, C.POINTER(TraceOpts), _P, _P, _P, _P]
     lib.srp_build_bvh_host.argtypes = [_P, i32, _P, i32, i32, _P, C.POINTER(C.c_int64), _P, C.POINTER(C.c_int32)]
     lib.srp_trace_rays.argtypes = [_P, _P, _P, i32, _P, _P, _P, i64, i32, i32, C.POINTER(TraceOpts), _P, _P]
@@ -773,6 +775,14 @@ class MLP:
 
     def load_file(self, path: str):
         _check(load().srp_mlp_load(self.ctx.handle, self.handle, os.fsencode(path)))
+
+    def save_state(self, path: str):
+        """Checkpoint of training: parameters, Adam moments and step."""
+        _check(load().srp_mlp_save_state(self.ctx.handle, self.handle, os.fsencode(path)))
+
+    def load_state(self, path: str):
+        """Resume training from a save_state file."""
+        _check(load().srp_mlp_load_state(self.ctx.handle, self.handle, os.fsencode(path)))
 
 
 # ----------------------------------------------------------------- orbits

@@ -845,3 +845,48 @@ extern "C" int srp_mlp_load(srp_ctx* c, srp_mlp* m, const char* path) {
     return srp_mlp_set_params(c, m, p.data());
 }
 
+
+// Trainer state: tag "SRPMLS1\0", int64 P, int64 Adam step, then params, the
+// first and the second moments as float32 [P] each (host byte order).
+extern "C" int srp_mlp_save_state(srp_ctx* c, const srp_mlp* m, const char* path) {
+    if (!c || !m || !path) return mfail(SRP_EINVAL, "srp_mlp_save_state: NULL argument");
+    MCU(cudaSetDevice(m->device), "cudaSetDevice");
+    MCU(cudaStreamSynchronize(ctx_stream(c)), "sync");   // training steps in flight finish first
+    std::vector<float> buf(3 * (size_t)kMlpParams);
+    const float* src[3] = {m->params, m->adam_m, m->adam_v};
+    for (int a = 0; a < 3; ++a)
+        MCU(cudaMemcpy(buf.data() + (size_t)a * kMlpParams, src[a], sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost),
+            "D2H state");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return mfail(SRP_EINVAL, std::string("srp_mlp_save_state: cannot open ") + path);
+    const char tag[8] = {'S', 'R', 'P', 'M', 'L', 'S', '1', 0};
+    const int64_t head[2] = {kMlpParams, m->step};
+    bool ok = std::fwrite(tag, 1, 8, f) == 8 && std::fwrite(head, sizeof(int64_t), 2, f) == 2 &&
+              std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? SRP_OK : mfail(SRP_EINVAL, std::string("srp_mlp_save_state: write failed: ") + path);
+}
+
+extern "C" int srp_mlp_load_state(srp_ctx* c, srp_mlp* m, const char* path) {
+    if (!c || !m || !path) return mfail(SRP_EINVAL, "srp_mlp_load_state: NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return mfail(SRP_EINVAL, std::string("srp_mlp_load_state: cannot open ") + path);
+    char tag[8];
+    int64_t head[2] = {0, 0};
+    std::vector<float> buf(3 * (size_t)kMlpParams);
+    bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, "SRPMLS1", 8) == 0 &&
+              std::fread(head, sizeof(int64_t), 2, f) == 2 && head[0] == kMlpParams && head[1] >= 0 &&
+              std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return mfail(SRP_EINVAL, std::string("srp_mlp_load_state: not a trainer-state file of this network: ") + path);
+    const float* mv = buf.data() + kMlpParams;
+    for (int64_t q = 0; q < 2 * kMlpParams; ++q)
+        if (!std::isfinite(mv[q]) || (q >= kMlpParams && mv[q] < 0.0f))
+            return mfail(SRP_EINVAL, "srp_mlp_load_state: invalid Adam moments");
+    int rc = srp_mlp_set_params(c, m, buf.data());   // parameters and their BF16 copies; resets Adam
+    if (rc != SRP_OK) return rc;
+    MCU(cudaMemcpy(m->adam_m, mv, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice), "H2D moments");
+    MCU(cudaMemcpy(m->adam_v, mv + kMlpParams, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice), "H2D moments");
+    m->step = head[1];
+    return SRP_OK;
+}
