@@ -84,9 +84,22 @@ class Surrogate:
 
 
 def fit(ctx: Context, mesh, n_designs=4096, suns_per_design=256, rays=256, bounces=3, epochs=20, batch=8192,
-        lr=2e-3, seed=0, log=None):
+        lr=2e-3, seed=0, log=None, checkpoint=None, resume=False, device=None):
     """Generate the data with the tracer and train the proxy; returns
-    (Surrogate, info dict with timings)."""
+    (Surrogate, info dict with timings).
+
+    checkpoint: a path prefix; after every epoch the network's trainer state
+    (parameters, Adam moments, step: <prefix>.state, srp_mlp_save_state) and
+    the loop's own state (epochs done, step, the batch-permutation RNG and
+    the output standardisation: <prefix>.npz) are written, each through a
+    temporary file and a rename.  resume=True continues from them when they
+    exist: the data set is traced again from the same seeds (the tracer is
+    deterministic), the finished epochs are skipped and the learning-rate
+    schedule and batch order continue where they stopped.  device: where
+    the training batches live (default: the context's GPU)."""
+    import json
+    import os
+
     t0 = time.perf_counter()
     theta = sample_designs(n_designs, seed)
     sun, ft = trace_dataset(ctx, mesh, theta, suns_per_design, rays, bounces, seed=seed, sun_seed=seed + 1)
@@ -100,13 +113,20 @@ def fit(ctx: Context, mesh, n_designs=4096, suns_per_design=256, rays=256, bounc
     n = x.shape[0]
     rng = np.random.default_rng(seed + 7)
     steps = max(1, epochs * (n // batch))
+    step, ep0 = 0, 0
+    if resume and checkpoint is not None and os.path.exists(checkpoint + ".npz"):
+        meta = np.load(checkpoint + ".npz", allow_pickle=False)
+        if not (np.array_equal(meta["mean"], mean) and np.array_equal(meta["std"], std)):
+            raise ValueError("checkpoint was written for another data set")
+        ep0, step = int(meta["epoch"]), int(meta["step"])
+        rng.bit_generator.state = json.loads(str(meta["rng"]))
+        net.load_state(checkpoint + ".state")
     t1 = time.perf_counter()
     import torch
-    dev = torch.device("cuda", ctx.device)
+    dev = torch.device(device) if device is not None else torch.device("cuda", ctx.device)
     xt = torch.from_numpy(x).to(dev)
     yt = torch.from_numpy(yn).to(dev)
-    step = 0
-    for ep in range(epochs):
+    for ep in range(ep0, epochs):
         perm = torch.from_numpy(rng.permutation(n)).to(dev)
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
@@ -118,7 +138,14 @@ def fit(ctx: Context, mesh, n_designs=4096, suns_per_design=256, rays=256, bounc
         if log is not None:
             l, _ = net.train_step(xt[:batch].contiguous(), yt[:batch].contiguous(), 0.0)
             log(f"epoch {ep} loss {l:.4f}")
-    torch.cuda.synchronize()
+        if checkpoint is not None:
+            net.save_state(checkpoint + ".state.tmp")
+            os.replace(checkpoint + ".state.tmp", checkpoint + ".state")
+            with open(checkpoint + ".tmp.npz", "wb") as f:
+                np.savez(f, epoch=ep + 1, step=step, rng=json.dumps(rng.bit_generator.state), mean=mean, std=std)
+            os.replace(checkpoint + ".tmp.npz", checkpoint + ".npz")
+    if dev.type == "cuda":
+        torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t1
     return Surrogate(ctx, net, mean, std), {"data_s": t_data, "train_s": t_train, "samples": n, "steps": step}
 

@@ -63,3 +63,61 @@ def test_trace_dataset_chunks_and_layout(monkeypatch):
     assert np.allclose(ft[:, 0, 1], theta[:, 7:14].sum(axis=1), rtol=1e-6)
     assert np.array_equal(ft[:, 0, 2], theta[:, 14])
     assert np.array_equal(ft[:, :, 3:], sun)
+
+
+def test_fit_resumes_after_a_crash(monkeypatch, tmp_path):
+    """Training checkpoints: a run that crashes after two of four epochs and
+    is resumed from its checkpoint ends with exactly the state of an
+    uninterrupted run (same batches in the same order, same learning
+    rates).  The network is a stand-in whose update depends on the batch
+    order and the learning rate; the real trainer state (srp_mlp_save_state)
+    is checked on the GPU."""
+    from paper_2602_10712_gb300 import surrogate as S
+    crash = {"at": None}
+
+    class Net:
+        def __init__(self, ctx, params=None, seed=0):
+            self.w, self.t = 0.0, 0
+
+        def train_step(self, xb, yb, lr, want_loss=True, want_grad=False):
+            if crash["at"] is not None and self.t == crash["at"]:
+                raise RuntimeError("simulated crash")
+            self.w = 0.999 * self.w + lr * float(xb[:, 0].sum() + 2.0 * yb[:, 1].sum() + xb[0, 5])
+            if lr > 0:
+                self.t += 1
+            return (self.w if want_loss else None), None
+
+        def save_state(self, path):
+            with open(path, "wb") as f:
+                np.save(f, np.array([self.w, self.t]))
+
+        def load_state(self, path):
+            with open(path, "rb") as f:
+                a = np.load(f)
+            self.w, self.t = float(a[0]), int(a[1])
+
+    def data(ctx, mesh, theta, spd, rays, bounces, seed, sun_seed):
+        r = np.random.default_rng(seed)
+        return S.sample_suns(theta.shape[0] * spd, sun_seed).reshape(-1, spd, 3), r.normal(size=(theta.shape[0], spd, 6))
+
+    monkeypatch.setattr(S, "MLP", Net)
+    monkeypatch.setattr(S, "trace_dataset", data)
+    kw = dict(n_designs=64, suns_per_design=16, epochs=4, batch=128, lr=1e-2, seed=3, device="cpu")
+    ref, info = S.fit(None, None, **kw)
+    assert info["steps"] == 32
+    prefix = str(tmp_path / "ckpt")
+    crash["at"] = 16                       # the first step of the third epoch
+    try:
+        S.fit(None, None, checkpoint=prefix, **kw)
+        raise AssertionError("the stand-in should have crashed")
+    except RuntimeError as e:
+        assert "simulated crash" in str(e)
+    meta = np.load(prefix + ".npz")
+    assert int(meta["epoch"]) == 2 and int(meta["step"]) == 16
+    crash["at"] = None
+    res, info2 = S.fit(None, None, checkpoint=prefix, resume=True, **kw)
+    assert info2["steps"] == 32 and res.net.t == 32
+    assert res.net.w == ref.net.w
+    # without resume the same call starts over (and gives the same result)
+    again, _ = S.fit(None, None, checkpoint=prefix, **kw)
+    assert again.net.w == ref.net.w
