@@ -457,3 +457,73 @@ def test_samples_mean_matches_grid_estimate():
     fg, sg = oracle.force(v, m.tris, m.group, rho, e[None], com, nx=512, K=3, seed=1)
     se = y.std(axis=0) / np.sqrt(N)
     assert np.all(np.abs(y.mean(axis=0) - fg[0]) <= 3 * np.sqrt(se ** 2 + sg[0] ** 2) + 1e-12)
+
+
+# ---------------------------------------------------------------- watertight intersection
+def _tiled_square():
+    """[-1,1]^2 at z = 0 in 8 x 8 cells of 0.25 m, each split along a
+    diagonal (alternating direction), plus two unreferenced vertices at
+    z = +-2 so that the grid radius is R = 2 about the origin: pixel centres
+    then fall exactly on lattice vertices, edges and diagonals."""
+    k = np.arange(9) * 0.25 - 1.0
+    X, Y = np.meshgrid(k, k, indexing="ij")
+    v = np.stack([X.ravel(), Y.ravel(), np.zeros(81)], axis=1)
+    v = np.concatenate([v, [[0.0, 0.0, 2.0], [0.0, 0.0, -2.0]]])
+    tris = []
+    for i in range(8):
+        for j in range(8):
+            a, b, c, d = 9 * i + j, 9 * (i + 1) + j, 9 * (i + 1) + j + 1, 9 * i + j + 1
+            tris += [[a, b, c], [a, c, d]] if (i + j) % 2 == 0 else [[a, b, d], [b, c, d]]
+    return v.astype(np.float32), np.array(tris, np.int32)
+
+
+def _contains(v, t, p):
+    """Closed point-in-triangle test in the z = 0 plane (exact for these
+    dyadic coordinates)."""
+    a, b, c = v[t[0], :2].astype(np.float64), v[t[1], :2].astype(np.float64), v[t[2], :2].astype(np.float64)
+    cr = lambda o, q, r: (q[0] - o[0]) * (r[1] - o[1]) - (q[1] - o[1]) * (r[0] - o[0])
+    s = [cr(a, b, p), cr(b, c, p), cr(c, a, p)]
+    return all(x >= 0 for x in s) or all(x <= 0 for x in s)
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 8), (16, 16), (8, 16), (16, 8), (32, 32)])
+def test_watertight_edges_vertices_and_ties(nx, ny):
+    """Woop-Benthin-Wald watertight intersection in the oracle: rays through
+    shared vertices (8 x 8), cell diagonals (16 x 16), vertical and
+    horizontal shared edges (8 x 16, 16 x 8) of the tiled square all hit it,
+    once each: the all-absorber force is exactly -P a z times the number of
+    pixel centres inside; each ray's triangle is the smallest index among
+    the triangles that contain its point (the tie rule on equal t)."""
+    v, t = _tiled_square()
+    g = np.zeros(len(t), np.int32)
+    e = np.array([0.0, 0.0, 1.0])
+    c, R = oracle.grid(v)
+    assert np.array_equal(c, np.zeros(3)) and R == 2.0
+    ft, _ = oracle.force(v, t, g, np.zeros((1, 2)), e, np.zeros(3), nx=nx, ny=ny, K=1, jitter=0)
+    dx, dy = 4.0 / nx, 4.0 / ny
+    xs = -2.0 + (np.arange(nx) + 0.5) * dx
+    ys = -2.0 + (np.arange(ny) + 0.5) * dy
+    inside = int(np.sum(np.abs(xs) < 1.0)) * int(np.sum(np.abs(ys) < 1.0))
+    assert ft[0, 2] == -inside * dx * dy and ft[0, 0] == 0.0 and ft[0, 1] == 0.0
+    # the grid's u axis is +x and its v axis -y for a sun along +z (the ONB of
+    # the travel direction -z)
+    for i in range(nx * ny):
+        p = np.array([xs[i % nx], -ys[i // nx]])
+        f, _ = oracle.primary_hit(v, t, e, i, nx=nx, ny=ny, jitter=0)
+        owners = [k for k in range(len(t)) if _contains(v, t[k], p)]
+        assert f == (min(owners) if owners else -1), (i, p, f, owners)
+
+
+def test_parallel_triangle_is_never_hit():
+    """A triangle whose plane contains the travel direction is never hit,
+    including by rays that lie in its plane."""
+    v = np.array([[-1.0, 0.25, -1.0], [1.0, 0.25, -1.0], [0.0, 0.25, 1.0], [0.0, 0.0, 2.0], [0.0, 0.0, -2.0],
+                  [0.0, -0.25, 0.0]], np.float32)
+    t = np.array([[0, 1, 2]], np.int32)
+    assert oracle.grid(v)[1] == 2.0
+    for nx in (8, 16):      # with 8 x 8 a row of pixel centres lies in the plane y = 0.25
+        ft, _ = oracle.force(v, t, np.zeros(1, np.int32), np.zeros((1, 2)), np.array([0.0, 0.0, 1.0]),
+                             np.zeros(3), nx=nx, K=1, jitter=0)
+        assert np.all(ft == 0.0)
+        assert all(oracle.primary_hit(v, t, np.array([0.0, 0.0, 1.0]), i, nx=nx, jitter=0)[0] == -1
+                   for i in range(nx * nx))
