@@ -57,8 +57,8 @@ __device__ __forceinline__ float tri_area_rn(float4 a, float4 b, float4 c) {
     return __fmul_rn(0.5f, __fsqrt_rn(s));
 }
 
-__global__ void __launch_bounds__(256) area_prep_kernel(const AreaParams p) {
-    const int d = blockIdx.y;
+__global__ void __launch_bounds__(256) area_prep_kernel(const AreaParams p, int d0) {
+    const int d = d0 + (int)blockIdx.y;
     const DesignDev dz = p.designs[d];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= dz.T) return;
@@ -388,7 +388,11 @@ static void area_launch_w(const AreaParams& p, int variant, int grid, cudaStream
 // p.queue must be zeroed on `st` before this call.
 cudaError_t launch_area(const AreaParams& p, int width, int variant, int t_max, int grid_cap, cudaStream_t st) {
     if (p.D > 0 && t_max > 0) {
-        area_prep_kernel<<<dim3((unsigned)((t_max + 255) / 256), (unsigned)p.D), 256, 0, st>>>(p);
+        // designs along grid y, at most 65,535 per launch (the y-dimension limit)
+        for (int d0 = 0; d0 < p.D; d0 += 65535) {
+            const unsigned nd = (unsigned)std::min(65535, p.D - d0);
+            area_prep_kernel<<<dim3((unsigned)((t_max + 255) / 256), nd), 256, 0, st>>>(p, d0);
+        }
         area_scan_kernel<<<(unsigned)p.D, 1024, 0, st>>>(p);
     }
     const int64_t units = (int64_t)p.D * p.S * p.cpd;
