@@ -408,7 +408,9 @@ int srp_integrate(srp_ctx* ctx, const srp_orbit_opts* opts, const srp_mlp* proxy
  * array's address with that device current; make it before any stream
  * capture begins.  d_status (device int32, may be NULL) receives the
  * device-limit flags of the call (0 = none; see SRP_EDEVICE_LIMIT).
- * Asynchronous; calls no cudaMalloc/cudaFree. */
+ * Asynchronous; calls no cudaMalloc/cudaFree or other allocating routine,
+ * and takes no host heap memory either when it succeeds (the design table is
+ * staged through a small stack buffer). */
 int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float* rho, int G,
                       const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
                       double* out_ft, double* out_sigma, int32_t* d_status, void* cuda_stream);

@@ -21,7 +21,8 @@
 //  - the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
 //    before any stream capture begins;
-//  - nothing here calls cudaMalloc, cudaFree or an allocating library.
+//  - nothing here calls cudaMalloc, cudaFree or an allocating library, and
+//    a successful call takes no host heap memory (only error messages do).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +30,6 @@
 #include <cstring>
 #include <mutex>
 #include <string>
-#include <vector>
 
 #include "srp_internal.h"
 
@@ -134,7 +134,8 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
         return fail(SRP_EINVAL, "srp_force_noalloc: D = " + std::to_string(D) + " exceeds the fixed design-table capacity of " +
                                     std::to_string(kNoAllocDesigns) + " designs; use srp_force");
     if (o->kernel_variant != 0) return fail(SRP_EINVAL, "srp_force_noalloc: kernel_variant must be 0");
-    std::vector<DesignDev> designs(D);
+    // every design is checked before anything is enqueued; the table itself is
+    // written further down, through a small stack buffer (no heap allocation)
     int width = 0;
     for (int d = 0; d < D; ++d) {
         const srp_bvh* h = bvhs[d];
@@ -145,10 +146,6 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
         if (h->max_group >= G)
             return fail(SRP_EINVAL, "srp_force_noalloc: design " + std::to_string(d) + " uses material group " +
                                         std::to_string(h->max_group) + " but rho has G = " + std::to_string(G) + " groups");
-        DesignDev& z = designs[d];
-        z.tri = (const float4*)h->d_tri; z.nodes = (const float4*)h->d_nodes;
-        z.cx = h->c[0]; z.cy = h->c[1]; z.cz = h->c[2]; z.R = h->R;
-        z.T = h->T; z.width = h->width;
     }
     if (width == 0) width = 4;
     if (items > kScratchUnits)
@@ -207,9 +204,26 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     p.variant = 6;
     p.queue = ds->queue;
     p.designs = ds->table;
-    // the design table: a copy from host memory into the fixed array
-    e = cudaMemcpyAsync(ds->table, designs.data(), sizeof(DesignDev) * (size_t)D, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemcpyAsync(designs): ") + cudaGetErrorString(e));
+    // the design table: copied into the fixed array in chunks of 64 entries
+    // staged on the stack (a copy from pageable memory returns once the
+    // driver has taken the bytes, so the buffer can be refilled at once)
+    {
+        constexpr int kStage = 64;
+        DesignDev stage[kStage];
+        for (int d0 = 0; d0 < D; d0 += kStage) {
+            const int nd = std::min(kStage, D - d0);
+            for (int k = 0; k < nd; ++k) {
+                const srp_bvh* h = bvhs[d0 + k];
+                DesignDev z{};
+                z.tri = (const float4*)h->d_tri; z.nodes = (const float4*)h->d_nodes;
+                z.cx = h->c[0]; z.cy = h->c[1]; z.cz = h->c[2]; z.R = h->R;
+                z.T = h->T; z.width = h->width;
+                stage[k] = z;
+            }
+            e = cudaMemcpyAsync(ds->table + d0, stage, sizeof(DesignDev) * (size_t)nd, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemcpyAsync(designs): ") + cudaGetErrorString(e));
+        }
+    }
     // the error word only collects flags (OR) and the queue counts up: both start at zero
     e = cudaMemsetAsync(ds->err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ds->queue, 0, sizeof(unsigned long long), st);
