@@ -169,6 +169,14 @@ def allsum(ws, x):
     return float(t.item())
 
 
+def _guarded(fn, *args):
+    """fn(*args), or {"error": ...} when it raises (a leg of the line)."""
+    try:
+        return fn(*args)
+    except Exception as exc:  # noqa: BLE001
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
 # --------------------------------------------------------------------------
 # CPU oracle leg (the reference arm and the cpu_baseline)
 # --------------------------------------------------------------------------
@@ -345,50 +353,58 @@ def run_ours(args, ws, rank, local):
     # under N > 1 the other GPUs would sit idle while rank 0 measures them
     orbit_check = None
     if rank == 0 and ws == 1 and not args.no_extra:
-        # box-wing, 1 sun direction, 1024^2 rays, K = 1 (one small call: launch-bound)
-        m1, rho1, sun1, com1 = W.config1()
-        b1 = srp.srp_build_bvh(ctx, m1.verts, m1.tris, m1.group, args.width)
-        r1 = torch.from_numpy(rho1[None].copy()).to(dev)
-        s1 = torch.from_numpy(sun1.copy()).to(dev)
-        c1 = torch.from_numpy(com1[None].copy()).to(dev)
-        o1 = torch.empty((1, 1, 6), dtype=torch.float64, device=dev)
-        for _ in range(3):
-            srp.srp_force(ctx, [b1], r1, s1, c1, out_ft=o1, rays_x=1024, max_bounces=1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(20):
-            srp.srp_force(ctx, [b1], r1, s1, c1, out_ft=o1, rays_x=1024, max_bounces=1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_c1 = e0.elapsed_time(e1) / 20
-        line["box_wing"] = {"rays_per_s": 1024 * 1024 / (ms_c1 / 1e3), "ms_per_call": ms_c1,
-                            "note": "box-wing (16 triangles), 1 sun direction, 1024^2 rays, K=1, one srp_force "
-                                    "call per evaluation (three launches), device time"}
-        b1.close()
-        # the same workload at K = 1 (primary hits only), device time, L2 flushed
-        kw1 = dict(kw, max_bounces=1)
-        srp.srp_force(ctx, [bvh], r_t, s_t, c_t, out_ft=out, **kw1)
-        ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
-        for a, b in ev1:
-            flush.zero_()
-            a.record(stream)
+        def box_wing_leg():
+            # box-wing, 1 sun direction, 1024^2 rays, K = 1 (one small call: launch-bound)
+            m1, rho1, sun1, com1 = W.config1()
+            b1 = srp.srp_build_bvh(ctx, m1.verts, m1.tris, m1.group, args.width)
+            r1 = torch.from_numpy(rho1[None].copy()).to(dev)
+            s1 = torch.from_numpy(sun1.copy()).to(dev)
+            c1 = torch.from_numpy(com1[None].copy()).to(dev)
+            o1 = torch.empty((1, 1, 6), dtype=torch.float64, device=dev)
+            for _ in range(3):
+                srp.srp_force(ctx, [b1], r1, s1, c1, out_ft=o1, rays_x=1024, max_bounces=1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(20):
+                srp.srp_force(ctx, [b1], r1, s1, c1, out_ft=o1, rays_x=1024, max_bounces=1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_c1 = e0.elapsed_time(e1) / 20
+            b1.close()
+            return {"rays_per_s": 1024 * 1024 / (ms_c1 / 1e3), "ms_per_call": ms_c1,
+                    "note": "box-wing (16 triangles), 1 sun direction, 1024^2 rays, K=1, one srp_force "
+                            "call per evaluation (three launches), device time"}
+
+        def single_bounce_leg():
+            # the same workload at K = 1 (primary hits only), device time, L2 flushed
+            kw1 = dict(kw, max_bounces=1)
             srp.srp_force(ctx, [bvh], r_t, s_t, c_t, out_ft=out, **kw1)
-            b.record(stream)
-        torch.cuda.synchronize()
-        ms1 = sum(a.elapsed_time(b) for a, b in ev1) / len(ev1)
-        line["single_bounce"] = {"rays_per_s": rays_step / (ms1 / 1e3), "ms_per_step": ms1, "max_bounces": 1,
-                                 "note": "the timed workload with max_bounces = 1"}
-        line["area_estimator"] = area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, args.width)
-        line["per_sample_designs"] = samples_leg(srp, ctx, dev, sm_mhz)
-        line["batched_designs"] = batched_leg(srp, ctx, dev, sm_mhz)
-        line["design_optimisation"] = design_leg(srp, ctx, dev)
-        line["surrogate"], line["grad"] = extra_legs(srp, ctx, dev, peaks)
-        # the orbit integrator runs last: a failure there is recorded in the
-        # line and leaves the measurements above intact
-        try:
-            line["orbit"], orbit_check = orbit_leg(srp, ctx)
-        except Exception as exc:  # noqa: BLE001
-            line["orbit"] = {"error": f"{type(exc).__name__}: {exc}"}
+            ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+            for a, b in ev1:
+                flush.zero_()
+                a.record(stream)
+                srp.srp_force(ctx, [bvh], r_t, s_t, c_t, out_ft=out, **kw1)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms1 = sum(a.elapsed_time(b) for a, b in ev1) / len(ev1)
+            return {"rays_per_s": rays_step / (ms1 / 1e3), "ms_per_step": ms1, "max_bounces": 1,
+                    "note": "the timed workload with max_bounces = 1"}
+
+        # each leg is recorded on its own: a failure in one is written into
+        # the line and leaves the headline measurement and the others intact
+        line["box_wing"] = _guarded(box_wing_leg)
+        line["single_bounce"] = _guarded(single_bounce_leg)
+        line["area_estimator"] = _guarded(area_leg, srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, args.width)
+        line["per_sample_designs"] = _guarded(samples_leg, srp, ctx, dev, sm_mhz)
+        line["batched_designs"] = _guarded(batched_leg, srp, ctx, dev, sm_mhz)
+        line["design_optimisation"] = _guarded(design_leg, srp, ctx, dev)
+        sg = _guarded(extra_legs, srp, ctx, dev, peaks)
+        line["surrogate"], line["grad"] = (sg, sg) if isinstance(sg, dict) else sg
+        orb = _guarded(orbit_leg, srp, ctx)
+        if isinstance(orb, dict):
+            line["orbit"] = orb
+        else:
+            line["orbit"], orbit_check = orb
     if rank == 0 and ws == 1 and not args.no_cpu:
         m_, rho_, sun_, com_ = m, rho, sun, com
         val, dt = oracle_sample(m_, rho_, sun_, com_, 2, 4096)
