@@ -206,7 +206,7 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     p.designs = ds->table;
     // the design table: copied into the fixed array in chunks of 64 entries
     // staged on the stack (a copy from pageable memory returns once the
-    // driver has taken the bytes, so the buffer can be refilled at once)
+    // CUDA runtime has staged the bytes, so the buffer can be refilled at once)
     {
         constexpr int kStage = 64;
         DesignDev stage[kStage];
