@@ -42,7 +42,9 @@
  *    handles (srp_ctx, srp_bvh) and frees them in srp_*_destroy.
  *  - Device-side failures (a traversal stack overflow or a visit cap hit on
  *    a corrupted BVH) set a flag that the next srp_sync() (or any HOST-mem
- *    call) reports as SRP_EDEVICE_LIMIT.  No kernel traps or spins forever.
+ *    call) reports as SRP_EDEVICE_LIMIT; a bounded wait of a tensor-core
+ *    kernel that gave up, alone, is reported as SRP_ETIMEOUT.  No kernel
+ *    traps or spins forever.
  */
 #ifndef SRP_H
 #define SRP_H

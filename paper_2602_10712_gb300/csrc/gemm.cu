@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmArgs g) {
         failed = __syncthreads_or(!ok);
     }
     if (failed) {
-        if (tid == 0) atomicOr(g.err, 4);
+        if (tid == 0) atomicOr(g.err, kErrWaitTimeout);
         // bounded wait for MMAs possibly still running, then free TMEM
         const int last = nk - 1;
         tc::mbar_wait_bounded(&sm.bar[last & 1], (last >> 1) & 1, kGemmWait);

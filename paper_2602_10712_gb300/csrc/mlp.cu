@@ -41,7 +41,6 @@ __host__ __device__ constexpr int mlp_K(int l) { return l == 0 ? 32 : 256; }    
 __host__ __device__ constexpr int mlp_N(int l) { return l == kMlpLayers - 1 ? 16 : 256; }    // padded N
 constexpr int kMlpParams = 19 * 256 + 256 + 3 * (256 * 256 + 256) + 256 * 6 + 6;
 constexpr uint32_t kWaitLimit = 1u << 24;
-constexpr int kErrMlpTimeout = 4;
 
 struct MlpLayout {
     int64_t w_off[kMlpLayers];   // FP32 weight offset in the flat vector
@@ -293,7 +292,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const float* __
                 }
             }
             if (failed) {
-                atomicOr(err, kErrMlpTimeout);
+                atomicOr(err, kErrWaitTimeout);
                 // let copies and MMAs in flight land before the CTA leaves
                 if (pending_w)
                     for (int c = 0; c < 4; ++c) tc::mbar_wait_bounded(&sm.bar_w[c], ph_w, kWaitLimit);
@@ -357,7 +356,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const float* __
                 }
             }
         }
-        if (failed && lane == 0) atomicOr(err, kErrMlpTimeout);
+        if (failed && lane == 0) atomicOr(err, kErrWaitTimeout);
     }
     tc::tc_fence_before();
     __syncthreads();

@@ -32,6 +32,7 @@ constexpr int kVisitCap = 1 << 20;      // node visits per ray segment (corrupti
 // Error flags written by kernels (bitwise OR into one device word).
 constexpr int kErrStackOverflow = 1;
 constexpr int kErrVisitCap = 2;
+constexpr int kErrWaitTimeout = 4;      // a bounded mbarrier wait of a tensor-core kernel gave up
 constexpr int kErrAreaCount = 8;        // area estimator: sample counts above the planned bound
 constexpr int kErrTriIndex = 16;        // triangle table holds an index outside 0..T-1
 
