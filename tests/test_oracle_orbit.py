@@ -164,3 +164,27 @@ def test_j2_nodal_regression():
     z2 = O.rk4(O.Model("none", j2=0.0), z0, np.zeros(1), T / steps_per_rev, 15 * steps_per_rev)
     h2 = np.cross(z2[:3], z2[3:6])
     assert abs(math.atan2(h2[0], -h2[1]) - 0.4) < 1e-9
+
+
+def test_torque_free_tumbling_conserves_inertial_angular_momentum():
+    """Torque-free asymmetric body (I = 500, 400, 300 kg m^2) tumbling about
+    all three axes: the inertial angular momentum R(q) I w and the kinetic
+    energy 1/2 w.I w are conserved (Euler's equations with the quaternion
+    kinematics q' = 1/2 q (x) (0, w)).  Only the consistent conventions
+    conserve the vector: a flipped gyroscopic term or a transposed R(q)
+    conserves the energy and |I w| but not R(q) I w."""
+    m = O.Model("none", j2=0.0)
+    z0 = O.circular_state(7000e3, 0.3)
+    q = np.array([0.8, -0.2, 0.5, 0.26]); q /= np.linalg.norm(q)
+    z0[6:10] = q
+    z0[10:13] = [0.01, 0.02, -0.015]
+    _, tr = O.rk4(m, z0, np.zeros(1), 0.5, 4000, keep=True)
+    I = np.array([500.0, 400.0, 300.0])
+    L = np.array([O.rot(s[6:10]) @ (I * s[10:13]) for s in tr])
+    E = 0.5 * np.sum(I * tr[:, 10:13] ** 2, axis=1)
+    assert np.max(np.linalg.norm(L - L[0], axis=1)) < 1e-9 * np.linalg.norm(L[0])
+    assert np.max(np.abs(E / E[0] - 1.0)) < 1e-9
+    assert np.max(np.abs(np.linalg.norm(tr[:, 6:10], axis=1) - 1.0)) < 1e-9
+    # the body rate really tumbles (w changes direction by a large angle)
+    w = tr[:, 10:13]
+    assert np.min(w @ w[0] / (np.linalg.norm(w, axis=1) * np.linalg.norm(w[0]))) < 0.5
