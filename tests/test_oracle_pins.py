@@ -70,6 +70,12 @@ def test_plate_facing_sun_exact(rs, rd):
     assert np.allclose(ft[0, :3], F, rtol=1e-12, atol=1e-15)
     # centred plate, symmetric pixel centres: torque zero to round-off
     assert np.all(np.abs(ft[0, 3:]) < 1e-12)
+    # COM 0.5 m below the plate's centre along -y: every hit point sits at
+    # r = x - com, whose mean is (0, 0.5, 0), so tau = r x F = (0.5 F_z, 0, 0)
+    # (the right-hand cross product, torque about the COM)
+    ft2, _ = oracle.force(p.verts, p.tris, p.group, rho, e, np.array([0.0, -0.5, 0.0]), nx=nx, jitter=0, K=1)
+    assert np.allclose(ft2[0, :3], F, rtol=1e-12, atol=1e-15)
+    assert np.allclose(ft2[0, 3:], [0.5 * F[2], 0.0, 0.0], rtol=1e-12, atol=1e-13)
 
 
 def test_plate_absorber_forms():
