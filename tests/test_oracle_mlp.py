@@ -75,3 +75,31 @@ def test_adam_first_step_closed_form():
     # m_hat = g, v_hat = g^2 after one step -> update = -lr * g / (|g| + eps)
     assert np.allclose(q[0][0], [[1.0 - 0.01, -2.0 + 0.01]], atol=1e-9)
     assert np.allclose(q[0][1], [0.5 - 0.01 * 1e-3 / (1e-3 + 1e-8)], atol=1e-12)
+
+
+def test_forward_against_a_hand_built_network():
+    """The forward pass y = W4 s(W3 s(W2 s(W1 s(W0 x + b0) + b1) + b2) + b3) + b4
+    (s = SiLU on the hidden layers only, linear output) on a network wired
+    by hand: unit 0 of each hidden layer carries x[2] forward through a
+    chain of scalars (weights 2, 0.5, -1, 3 and biases 0.1, -0.2, 0.3, 0.4),
+    output 5 reads unit 0 with weight -2 plus bias 0.7, outputs 0..4 read
+    nothing and keep their biases; the expected values are the same scalar
+    chain written out."""
+    import math
+    sizes = (19, 256, 256, 256, 256, 6)
+    p = [(np.zeros((sizes[i + 1], sizes[i])), np.zeros(sizes[i + 1])) for i in range(5)]
+    p[0][0][0, 2], p[0][1][0] = 2.0, 0.1
+    p[1][0][0, 0], p[1][1][0] = 0.5, -0.2
+    p[2][0][0, 0], p[2][1][0] = -1.0, 0.3
+    p[3][0][0, 0], p[3][1][0] = 3.0, 0.4
+    p[4][0][5, 0], p[4][1][:] = -2.0, [0.1, 0.2, 0.3, 0.4, 0.5, 0.7]
+    s = lambda z: z / (1.0 + math.exp(-z))
+    for x2 in (-1.5, 0.0, 0.8):
+        x = np.zeros((1, 19)); x[0, 2] = x2; x[0, 7] = 9.0      # input 7 is wired to nothing
+        h = s(2.0 * x2 + 0.1)
+        h = s(0.5 * h - 0.2)
+        h = s(-1.0 * h + 0.3)
+        h = s(3.0 * h + 0.4)
+        want = [0.1, 0.2, 0.3, 0.4, 0.5, -2.0 * h + 0.7]
+        y = mlp.forward(x, p)[0][0]
+        assert np.allclose(y, want, rtol=1e-14, atol=1e-15), (x2, y, want)
