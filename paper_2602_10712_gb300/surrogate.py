@@ -21,13 +21,14 @@ from . import MLP, Context, srp_build_bvh, srp_design_instantiate, srp_force
 
 N_DESIGN = 16
 HINGE_MAX = math.pi / 2
+RHO_MAX = 0.5   # the training range of every reflectance: [0, RHO_MAX]
 
 
 def sample_designs(n: int, seed: int) -> np.ndarray:
     """theta [n,16]: rho_s[7], rho_d[7] ~ U[0,0.5], hinge[2] ~ U[-pi/2, pi/2]."""
     rng = np.random.default_rng(seed)
     th = np.empty((n, N_DESIGN))
-    th[:, :14] = rng.uniform(0.0, 0.5, size=(n, 14))
+    th[:, :14] = rng.uniform(0.0, RHO_MAX, size=(n, 14))
     th[:, 14:] = rng.uniform(-HINGE_MAX, HINGE_MAX, size=(n, 2))
     return th
 
@@ -81,6 +82,36 @@ class Surrogate:
         x = encode(sun, theta).reshape(-1, 19)
         y = self.net.infer(x)
         return y.astype(np.float64) * self.std + self.mean
+
+    @staticmethod
+    def in_domain(theta: np.ndarray) -> np.ndarray:
+        """Rows of theta [N,16] inside the training domain (reflectances in
+        [0, 0.5], hinge angles in [-pi/2, pi/2])."""
+        th = np.asarray(theta, np.float64).reshape(-1, N_DESIGN)
+        return (np.all((th[:, :14] >= 0.0) & (th[:, :14] <= RHO_MAX), axis=1) &
+                np.all(np.abs(th[:, 14:]) <= HINGE_MAX, axis=1))
+
+    def evaluate(self, sun: np.ndarray, theta: np.ndarray, mesh, rays: int = 256, bounces: int = 3, seed: int = 0):
+        """Force and torque [N,6] for unit radiation at each row (sun [N,3],
+        theta [N,16]): the proxy where the design lies in its training
+        domain, the ray tracer (design instantiated, BVH built, srp_force
+        with rays^2 rays and up to `bounces` bounces) where it does not --
+        the tracer is the proxy's fallback outside the data it was fitted
+        to.  Returns (ft [N,6], traced [N] bool)."""
+        sun = np.asarray(sun, np.float64).reshape(-1, 3)
+        theta = np.asarray(theta, np.float64).reshape(-1, N_DESIGN)
+        ok = self.in_domain(theta)
+        ft = np.zeros((sun.shape[0], 6))
+        if ok.any():
+            ft[ok] = self.predict(sun[ok], theta[ok])
+        for i in np.flatnonzero(~ok):
+            v = srp_design_instantiate(mesh.verts, mesh.vhinge, mesh.hinges, theta[i, 14:])
+            b = srp_build_bvh(self.ctx, v, mesh.tris, mesh.group, 4)
+            rho = np.stack([theta[i, :7], theta[i, 7:14]], axis=1).astype(np.float32)[None]
+            ft[i] = srp_force(self.ctx, [b], rho, sun[i:i + 1], np.zeros((1, 3)), rays_x=rays, max_bounces=bounces,
+                              seed=seed, sun_base=int(i))[0, 0]
+            b.close()
+        return ft, ~ok
 
 
 def fit(ctx: Context, mesh, n_designs=4096, suns_per_design=256, rays=256, bounces=3, epochs=20, batch=8192,

@@ -121,3 +121,38 @@ def test_fit_resumes_after_a_crash(monkeypatch, tmp_path):
     # without resume the same call starts over (and gives the same result)
     again, _ = S.fit(None, None, checkpoint=prefix, **kw)
     assert again.net.w == ref.net.w
+
+
+def test_evaluate_falls_back_to_the_tracer_outside_the_domain(monkeypatch):
+    """Surrogate.evaluate answers with the proxy inside its training domain
+    and with the tracer (instantiate, BVH, srp_force) outside it; the
+    tracer receives the row's reflectance layout, hinge angles and sun."""
+    from paper_2602_10712_gb300 import surrogate as S
+    import workloads as W
+    traced = []
+
+    class Net:
+        def infer(self, x):
+            return np.tile(np.arange(6, dtype=np.float32), (x.shape[0], 1))
+
+    def fake_force(ctx, bvhs, rho, sun, com, **kw):
+        traced.append((rho.copy(), sun.copy(), bvhs[0].angles.copy(), kw))
+        return np.full((1, 1, 6), -7.0)
+
+    monkeypatch.setattr(S, "srp_design_instantiate", lambda v, vh, hg, ang: np.asarray(ang))
+    monkeypatch.setattr(S, "srp_build_bvh", lambda ctx, v, t, g, w: type("B", (), {"angles": v, "close": lambda self: None})())
+    monkeypatch.setattr(S, "srp_force", fake_force)
+    sur = S.Surrogate(None, Net(), np.zeros(6), np.ones(6))
+    theta = S.sample_designs(5, seed=2)
+    theta[1, 3] = 0.6                      # a reflectance above the training range
+    theta[3, 15] = 2.0                     # a hinge beyond pi/2
+    sun = S.sample_suns(5, seed=3)
+    assert list(sur.in_domain(theta)) == [True, False, True, False, True]
+    ft, tr = sur.evaluate(sun, theta, W.box_wing_7group(), rays=128, bounces=2, seed=4)
+    assert list(tr) == [False, True, False, True, False]
+    assert np.array_equal(ft[~tr], np.tile(np.arange(6.0), (3, 1)))
+    assert np.all(ft[tr] == -7.0) and len(traced) == 2
+    for (rho, s, ang, kw), i in zip(traced, (1, 3)):
+        assert rho.shape == (1, 7, 2) and np.allclose(rho[0, :, 0], theta[i, :7]) and np.allclose(rho[0, :, 1], theta[i, 7:14])
+        assert np.array_equal(s, sun[i:i + 1]) and np.array_equal(ang, theta[i, 14:])
+        assert kw["rays_x"] == 128 and kw["max_bounces"] == 2 and kw["seed"] == 4
