@@ -105,3 +105,22 @@ def test_oracle_legs_beside_gradient_and_proxy():
     assert out["grad"]["grad_evals_per_s"] > 0 and out["grad"]["cores"] >= 1
     assert out["surrogate"]["evals_per_s"] > 0
     assert out["tracer_evals_per_s_256sq_rays"]["value"] > 0
+
+
+def test_gpu_arm_line_has_the_contract_keys():
+    """The GPU arm's JSON line (built in run_ours, which needs a GPU to run)
+    carries every key of the benchmark contract, checked on its source."""
+    import ast
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    fn = next(n for n in tree.body if isinstance(n, ast.FunctionDef) and n.name == "run_ours")
+    keys = set()
+    for node in ast.walk(fn):
+        if isinstance(node, ast.Assign) and any(isinstance(t, ast.Name) and t.id == "line" for t in node.targets) \
+                and isinstance(node.value, ast.Dict):
+            keys |= {k.value for k in node.value.keys if isinstance(k, ast.Constant)}
+        if isinstance(node, ast.Subscript) and isinstance(node.value, ast.Name) and node.value.id == "line" \
+                and isinstance(node.slice, ast.Constant):
+            keys.add(node.slice.value)
+    need = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "roofline", "clocks", "cpu_baseline"}
+    assert need <= keys, need - keys
