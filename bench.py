@@ -37,8 +37,8 @@ NX = 2048
 K_BOUNCE = 3
 WORKLOAD = "procedural satellite 49,776 tris, 64 groups, 4096 Fibonacci suns x 2048^2 rays, K<=3"
 # dram__bytes_read.sum + dram__bytes_write.sum of trace_kernel<4,6> from the ncu
-# capture of 16 of the 4096 suns (profiles/trace_kernel_config2_16suns_full.md),
-# scaled by the units processed (x256) to one benchmark launch
+# capture of 16 of the 4096 suns (the ncu summary of the 16-sun case under
+# profiles/), scaled by the units processed (x256) to one benchmark launch
 TRACE_DRAM_BYTES_PER_LAUNCH = (19.011584e6 + 104.137216e6) * 256
 
 
@@ -51,30 +51,16 @@ def _peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _l2_probe(dev):
-    """L2 bandwidth measured here with library kernels on L2-resident buffers
-    (4-32 MiB): a copy (read + write bytes) and a sum reduction (read bytes),
-    best of 20 timed loops of 50 calls at each size; the largest rate."""
-    import torch
-    rate = 0.0
-    for mib in (4, 8, 16, 32):
-        n = mib * 1024 * 1024 // 4
-        a = torch.ones(n, dtype=torch.float32, device=dev)
-        b = torch.empty_like(a)
-        for op, nbytes in ((lambda: b.copy_(a), 2 * n * 4), (lambda: a.sum(), n * 4)):
-            for _ in range(10):
-                op()
-            best = float("inf")
-            for _ in range(20):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(50):
-                    op()
-                e1.record()
-                torch.cuda.synchronize()
-                best = min(best, e0.elapsed_time(e1) / 50)
-            rate = max(rate, nbytes / (best / 1e3) / 1e9)
-    return rate
+def _l2_probe(srp, ctx):
+    """L2 read ceiling measured here by the library's own probe kernel
+    (srp_probe_read_bandwidth: 16-byte ld.global.cg loads, which bypass L1,
+    from every SM at full occupancy) over L2-resident buffers of 8-64 MiB;
+    the best rate.  Also the HBM read rate over a 4 GiB buffer."""
+    rates = {}
+    for mib in (8, 16, 32, 64):
+        rates[mib] = srp.srp_probe_read_bandwidth(ctx, mib << 20, passes=64, reps=10)
+    hbm = srp.srp_probe_read_bandwidth(ctx, 4 << 30, passes=2, reps=5)
+    return max(rates.values()), {"l2_read_gbs_by_mib": rates, "hbm_read_gbs_4gib": hbm}
 
 
 class ClockSampler:
@@ -303,7 +289,7 @@ def run_ours(args, ws, rank, local):
 
     # roofline: dominant kernel (trace_kernel) against the FP32 issue peak
     peaks, src = _peaks()
-    l2_gbs = _l2_probe(dev)
+    l2_gbs, l2_detail = _l2_probe(srp, ctx)
     sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     ops_node = 4 * 14 if args.width == 4 else 8 * 14
@@ -324,18 +310,19 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": (3 if NX % 32 == 0 else 2) * args.steps,   # span pre-pass (full grids), trace, reduce
         # the traversal's memory roofline: algorithmic bytes per second (node
         # visits x node bytes + triangle tests x 48 B, kernel counters) against
-        # the L2 rate measured in this run (an L2-resident scene), with the
-        # measured HBM copy peak beside it
+        # the L2 read ceiling measured in this run by the library's probe
+        # kernel (the scene is L2-resident), with the measured HBM copy peak
+        # beside it
         "roofline": {"bound": "l2", "achieved": mem_gbs, "peak": l2_gbs, "unit": "GB/s", "frac": mem_gbs / l2_gbs,
                      "traffic": TRACE_DRAM_BYTES_PER_LAUNCH,
                      "frac_of_hbm": mem_gbs / peaks["hbm_gbs"], "hbm_peak": peaks["hbm_gbs"],
-                     "peaks_source": f"L2: copy/sum probe in this run (the measured peaks carry no L2 figure); "
-                                     f"HBM: {src}",
+                     "probe": l2_detail,
+                     "peaks_source": f"L2: srp_probe_read_bandwidth in this run (ld.global.cg over 8-64 MiB, "
+                                     f"best); HBM: {src}",
                      "note": (f"trace_kernel, algorithmic {bytes_per_ray:.0f} B per grid ray (node visits x "
                               f"{node_bytes} B + triangle tests x 48 B, kernel counters; scene "
-                              f"{info['device_bytes']} B, L2-resident, two thirds served by L1); traffic = DRAM "
-                              "bytes per launch (ncu); the probe is what a copy kernel reaches in L2, below the "
-                              "L2's own ceiling (~30 TB/s by ncu's lts__throughput)")},
+                              f"{info['device_bytes']} B, L2-resident, part of it served by L1); traffic = DRAM "
+                              "bytes per launch (ncu)")},
         "alu_roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                          "frac": achieved / peak_alu,
                          "note": (f"trace_kernel FP32 lane-ops: {ops_per_ray:.0f}/ray = node visits x {ops_node} + "
@@ -396,7 +383,7 @@ def run_ours(args, ws, rank, local):
         line["single_bounce"] = _guarded(single_bounce_leg)
         line["area_estimator"] = _guarded(area_leg, srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, args.width)
         line["per_sample_designs"] = _guarded(samples_leg, srp, ctx, dev, sm_mhz)
-        line["batched_designs"] = _guarded(batched_leg, srp, ctx, dev, sm_mhz)
+        line["batched_designs"] = _guarded(batched_leg, srp, ctx, dev, sm_mhz, peaks, l2_gbs)
         line["design_optimisation"] = _guarded(design_leg, srp, ctx, dev)
         sg = _guarded(extra_legs, srp, ctx, dev, peaks)
         line["surrogate"], line["grad"] = (sg, sg) if isinstance(sg, dict) else sg
@@ -804,12 +791,16 @@ def samples_leg(srp, ctx, dev, sm_mhz):
                                   "roofline counts 44 FP32 ops per triangle test at K = 1 (N x T tests)"}
 
 
-def batched_leg(srp, ctx, dev, sm_mhz):
-    """Many uneven designs x many suns in one persistent launch: 256
-    procedural designs with log-uniform 5k-200k triangles (13.2 M in all),
-    64 Fibonacci suns each, 1024^2 rays, K <= 3 -- one srp_force evaluation
-    captured as a CUDA graph and replayed; launch parameters from the
-    autotuner on 16 of the designs x 8 of the suns (whole grids)."""
+def batched_leg(srp, ctx, dev, sm_mhz, peaks, l2_gbs):
+    """Many uneven designs x many suns in one persistent launch, at the
+    configuration's full size: 256 procedural designs with log-uniform
+    5k-200k triangles (13.2 M in all) x 1024 Fibonacci suns each x 1024^2
+    rays, K <= 3 (275 G rays) -- one srp_force evaluation captured as a CUDA
+    graph and replayed once, timed; launch parameters from the autotuner on
+    16 of the designs x 8 of the suns (whole grids).  The traversal counters
+    of the timed launch give its algorithmic bytes, held against the
+    measured HBM peak (the designs' BVHs stream from HBM, 1.5 GB) and the
+    L2 read ceiling."""
     import torch
     from concurrent.futures import ThreadPoolExecutor
 
@@ -817,7 +808,7 @@ def batched_leg(srp, ctx, dev, sm_mhz):
     t0 = time.perf_counter()
     designs = W.config5_designs(256)
     gen_s = time.perf_counter() - t0
-    D, S, nx = len(designs), 64, 1024
+    D, S, nx = len(designs), 1024, 1024
     rng = np.random.default_rng(5)
     rho = torch.from_numpy(rng.uniform(0.0, 0.5, size=(D, 64, 2)).astype(np.float32)).to(dev)
     sun = torch.from_numpy(W.fibonacci_directions(S)).to(dev)
@@ -831,39 +822,56 @@ def batched_leg(srp, ctx, dev, sm_mhz):
         bvhs = list(ex.map(lambda m: srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, best["width"]), designs))
     build_s = time.perf_counter() - t0
     bvh_bytes = sum(b.info()["device_bytes"] for b in bvhs)
-    out = torch.zeros((D, S, 6), dtype=torch.float64, device=dev)
     kw = dict(rays_x=nx, max_bounces=3, kernel_variant=best["kernel_variant"],
               chunks_per_item=best["chunks_per_item"])
-    g = srp.ForceGraph(ctx, bvhs, rho, sun, com, out, **kw)
-    g.launch()
+    # warm-up: the same call on the first 64 suns (also the bitwise check
+    # below: with chunks per item fixed, each item's sum is independent of
+    # the other items in the launch)
+    S0 = 64
+    sun0 = sun[:S0].contiguous()
+    out0 = srp.srp_force(ctx, bvhs, rho, sun0, com, **kw)
     srp.srp_sync(ctx)
-    ms = []
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        g.launch()
-        e1.record()
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    g.close()
+    out = torch.zeros((D, S, 6), dtype=torch.float64, device=dev)
+    srp.srp_collect_stats(ctx, True)
+    g = srp.ForceGraph(ctx, bvhs, rho, sun, com, out, **kw)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
     e0.record()
-    out2 = srp.srp_force(ctx, bvhs, rho, sun, com, **kw)
+    g.launch()
     e1.record()
     torch.cuda.synchronize()
-    same = bool(torch.equal(out2, out))
+    ms = e0.elapsed_time(e1)
+    vis, tests, segs = srp.srp_collect_stats(ctx, False)
+    srp.srp_sync(ctx)
+    g.close()
+    same = bool(torch.equal(out[:, :S0], out0))
     rays = D * S * nx * nx
-    t = sum(ms) / len(ms) / 1e3
+    t = ms / 1e3
+    node_bytes = 128 if best["width"] == 4 else 256
+    alg_bytes = vis * node_bytes + tests * 48
+    achieved = alg_bytes / t / 1e9
     Ts = [int(m.tris.shape[0]) for m in designs]
     for b in bvhs:
         b.close()
-    return {"rays_per_s_graph": rays / t, "rays_per_launch": rays, "ms_per_launch": t * 1e3,
-            "rays_per_s_call": rays / (e0.elapsed_time(e1) / 1e3), "graph_equals_call": same,
+    return {"rays_per_s_graph": rays / t, "rays_per_launch": rays, "ms_per_launch": ms,
+            "graph_equals_call_first_64_suns": same,
             "designs": D, "suns": S, "rays_per_item": nx * nx, "tris_min": min(Ts), "tris_max": max(Ts),
             "tris_total": sum(Ts), "bvh_device_bytes": bvh_bytes, "autotuned": best,
             "autotune_table": table, "host_s": {"generate": gen_s, "autotune": tune_s, "bvh_build_16_threads": build_s},
-            "note": "srp_force over 256 uneven designs x 64 suns x 1024^2 rays (K <= 3) in one persistent launch "
-                    "(atomic work queue over (design, sun, chunk) units), captured with srp_force_graph_create"}
+            "traversal": {"node_visits_per_ray": vis / rays, "tri_tests_per_ray": tests / rays,
+                          "segments_per_ray": segs / rays, "bytes_per_ray": alg_bytes / rays},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "frac_of_l2": achieved / l2_gbs if l2_gbs else None, "l2_peak": l2_gbs,
+                         "note": f"algorithmic bytes of the timed launch (node visits x {node_bytes} B + triangle "
+                                 "tests x 48 B, kernel counters) / its duration, against the measured HBM copy "
+                                 "peak; work units go in (design, sun, chunk) order, so each design's BVH is read "
+                                 "from HBM about once and its 1024 suns are traced from L2/L1"},
+            "workload": "config 5 as stated: 256 designs (5k-200k triangles, log-uniform) x 1024 Fibonacci suns x "
+                        "1024^2 rays, K <= 3, one persistent launch in a CUDA graph",
+            "note": "srp_force over 256 uneven designs x 1024 suns x 1024^2 rays (K <= 3) in one persistent launch "
+                    "(atomic work queue over (design, sun, chunk) units), captured with srp_force_graph_create "
+                    "and launched once (timed, CUDA events)"}
 
 
 def design_leg(srp, ctx, dev):

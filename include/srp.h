@@ -110,6 +110,18 @@ int srp_sync(srp_ctx* ctx);
  * per-warp atomic adds depend on `enable`. */
 int srp_collect_stats(srp_ctx* ctx, int enable, uint64_t out[3]);
 
+/* Read-bandwidth probe (for the roofline of the traversal; the paper has no
+ * counterpart).  Allocates a device buffer of `bytes` (rounded down to a
+ * multiple of 16, >= 16) on the context's device, and reads all of it
+ * `passes` times per launch from every SM with 16-byte loads cached in L2
+ * only (ld.global.cg), at full occupancy; after one warm-up launch it times
+ * `reps` launches with CUDA events on the context's stream and writes the
+ * best rate in GB/s (1e9 bytes read per second) to *out_gbs.  A buffer that
+ * fits in L2 measures the L2 read rate, one of several GB the HBM read rate.
+ * Synchronous; frees the buffer before it returns.  SRP_EINVAL for bad
+ * arguments, SRP_ENOMEM if the buffer cannot be allocated. */
+int srp_probe_read_bandwidth(srp_ctx* ctx, int64_t bytes, int passes, int reps, double* out_gbs);
+
 /* ---- design instantiation (Sec. 3.2: "a mapping from design parameters to
  * triangle meshes") ------------------------------------------------------- */
 /* Rotate every vertex v with vhinge[v] = h >= 0 about hinge h's axis
@@ -404,15 +416,25 @@ int srp_integrate(srp_ctx* ctx, const srp_orbit_opts* opts, const srp_mlp* proxy
  * until the process exits), so D*S may be at most 87,381 (and
  * D*S*chunks_per_item the same when given), and the design table in a
  * fixed array of 4,096 entries (D <= 4,096); larger requests fail with
- * SRP_EINVAL.  Every call shares that array and it keeps the last call's
- * contents: calls whose work overlaps on the GPU (unordered streams) race
- * and must not be issued.  The first call on each device looks up the
- * array's address with that device current; make it before any stream
- * capture begins.  d_status (device int32, may be NULL) receives the
- * device-limit flags of the call (0 = none; see SRP_EDEVICE_LIMIT).
- * Asynchronous; calls no cudaMalloc/cudaFree or other allocating routine,
- * and takes no host heap memory either when it succeeds (the design table is
- * staged through a small stack buffer). */
+ * SRP_EINVAL.  Every fixed array (the partials, the design table, the
+ * error word and the work-queue counter) is shared by every call on a
+ * device and keeps the last call's contents: calls whose work overlaps on
+ * the GPU (unordered streams) race on all of them and must not be issued --
+ * besides corrupting the sums, one call can rewrite the design table while
+ * the other's kernel reads it and then read out of bounds.  The first call
+ * on each device looks up the arrays' addresses with that device current;
+ * make it before any stream capture begins.  Unlike srp_force it traces
+ * every ray of the grid: the batch pre-pass that lets srp_force skip the
+ * 32-pixel batches that cannot meet the scene (full grids whose rays_x is a
+ * multiple of 32) needs per-row tables this variant does not keep, so on
+ * such grids it is slower and groups its sums differently (results equal up
+ * to the rounding of that grouping).  With chunks_per_item = 0 it picks
+ * chunks as srp_force does, capped so that D*S*chunks fits the array.
+ * d_status (device int32, may be NULL) receives the device-limit flags of
+ * the call (0 = none; see SRP_EDEVICE_LIMIT).  Asynchronous; calls no
+ * cudaMalloc/cudaFree or other allocating routine, and takes no host heap
+ * memory either when it succeeds (the design table travels to the device in
+ * the parameters of small kernel launches, 64 entries each). */
 int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float* rho, int G,
                       const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
                       double* out_ft, double* out_sigma, int32_t* d_status, void* cuda_stream);

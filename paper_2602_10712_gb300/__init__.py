@@ -91,6 +91,7 @@ def _load_locked(build_if_needed: bool):
                                       C.POINTER(TraceOpts), _P, _P]
     lib.srp_force_thermal.argtypes = [_P, _P, i32, _P, i32, _P, _P, C.c_float, C.POINTER(TraceOpts), _P, _P, _P]
     lib.srp_collect_stats.argtypes = [_P, i32, _P]
+    lib.srp_probe_read_bandwidth.argtypes = [_P, i64, i32, i32, C.POINTER(C.c_double)]
     lib.srp_bvh_set_nodes.argtypes = [_P, _P, _P, i64]
     lib.srp_force_grad.argtypes = [_P, _P, _P, i32, _P, i32, _P, _P, _P, i32, C.POINTER(TraceOpts), _P, _P, _P]
     lib.srp_mlp_param_count.argtypes = [C.POINTER(C.c_int64)]
@@ -243,6 +244,14 @@ def srp_collect_stats(ctx: Context, enable: bool = True):
     out = np.zeros(3, np.uint64)
     _check(load().srp_collect_stats(ctx.handle, 1 if enable else 0, _ptr(out)))
     return int(out[0]), int(out[1]), int(out[2])
+
+
+def srp_probe_read_bandwidth(ctx: Context, nbytes: int, passes: int = 64, reps: int = 10) -> float:
+    """Best read rate (GB/s) over a device buffer of nbytes, 16-byte loads
+    cached in L2 only, from every SM (the roofline's L2 or HBM ceiling)."""
+    out = C.c_double(0.0)
+    _check(load().srp_probe_read_bandwidth(ctx.handle, int(nbytes), int(passes), int(reps), C.byref(out)))
+    return out.value
 
 
 def srp_design_instantiate(verts, vhinge, hinges, angles):

@@ -21,6 +21,7 @@ cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* ou
 cudaError_t launch_trace_rays(const DesignDev& dz, const TraceParams& p, const int64_t* ray_idx, int64_t nr,
                               int sidx, int didx, double* out_y, int32_t* out_hits, cudaStream_t st);
 void set_last_error(const std::string& msg);
+cudaError_t run_read_probe(int64_t bytes, int passes, int reps, cudaStream_t st, double* out_gbs);
 int area_resident_blocks(int width, int variant);
 cudaError_t launch_area(const AreaParams& p, int width, int variant, int t_max, int grid_cap, cudaStream_t st);
 cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double* up, const int32_t* thinge,
@@ -190,6 +191,18 @@ int srp_collect_stats(srp_ctx* c, int enable, uint64_t out[3]) {
     }
     CU(cudaMemset(c->d_stats, 0, 3 * sizeof(unsigned long long)), "cudaMemset(stats)");
     c->stats_on = enable != 0;
+    return SRP_OK;
+}
+
+int srp_probe_read_bandwidth(srp_ctx* c, int64_t bytes, int passes, int reps, double* out_gbs) {
+    if (!c || !out_gbs) return fail(SRP_EINVAL, "srp_probe_read_bandwidth: NULL ctx/out");
+    *out_gbs = 0.0;
+    if (bytes < 16 || passes < 1 || reps < 1)
+        return fail(SRP_EINVAL, "srp_probe_read_bandwidth: bytes >= 16, passes >= 1 and reps >= 1 required");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaError_t e = run_read_probe(bytes, passes, reps, c->stream, out_gbs);
+    if (e == cudaErrorMemoryAllocation) return fail(SRP_ENOMEM, "srp_probe_read_bandwidth: device out of memory");
+    if (e != cudaSuccess) return cuda_fail(e, "srp_probe_read_bandwidth");
     return SRP_OK;
 }
 
@@ -466,10 +479,11 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
     *grid_cap = c->n_sm * trace_resident_blocks(*width, bt, variant);
     // full grids of whole 32-pixel batches: trace only the batches that can
     // meet the scene (span_kernel); the tables need items * (2 ny + 1) int32
+    // (up to 4 GiB: 256 designs x 1024 suns x 1024 rows take 2.1 GB)
     p->rowfirst = nullptr;
     p->rowoff = nullptr;
     const size_t span_bytes = sizeof(int32_t) * (size_t)items * (2 * (size_t)o->rays_y + 1);
-    if (items > 0 && off == 0 && stride == 1 && n == grid_n && o->rays_x % 32 == 0 && span_bytes <= ((size_t)1 << 30)) {
+    if (items > 0 && off == 0 && stride == 1 && n == grid_n && o->rays_x % 32 == 0 && span_bytes <= ((size_t)4 << 30)) {
         if (c->span.ensure(span_bytes) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force: cannot allocate the span tables");
         p->rowfirst = (int32_t*)c->span.p;
         p->rowoff = p->rowfirst + (size_t)items * o->rays_y;

@@ -15,9 +15,18 @@
 //  - the scratch array holds at most kScratchBytes (8 MiB) of partials,
 //    i.e. D*S*chunks <= 87,381 work units; larger requests are rejected
 //    with SRP_EINVAL and a message naming the limit;
-//  - the array is shared by every call on a device and keeps the last
-//    call's contents; two calls whose work overlaps on the GPU (different
-//    streams, no ordering between them) race on it;
+//  - every fixed array here (the partials, the design table, the error
+//    word and the work-queue counter) is shared by every call on a device
+//    and keeps the last call's contents; two calls whose work overlaps on
+//    the GPU (different streams, no ordering between them) race on all of
+//    them: besides wrong sums, one call may rewrite the design table while
+//    the other's kernel reads it, pairing one design's triangles with
+//    another's nodes, which can read out of bounds;
+//  - it traces every ray of the grid: the batch pre-pass of srp_force,
+//    which skips 32-pixel batches that cannot meet the scene on full grids
+//    whose width is a multiple of 32, needs per-row tables this variant does
+//    not hold, so on such grids it is slower than srp_force and its sums are
+//    grouped differently (equal up to FP64 rounding of the grouping);
 //  - the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
 //    before any stream capture begins;
@@ -72,6 +81,18 @@ std::mutex g_mu;
 int fail(int code, const std::string& m) {
     srp::set_last_error(m);  // reported by srp_last_error()
     return code;
+}
+
+// Writes designs [d0, d0 + n) of the fixed table from a chunk passed by value
+// as the kernel parameter (3.5 KB, within the 4 KB parameter space): the
+// bytes travel with the launch, so no host buffer has to outlive the call.
+constexpr int kStage = 64;
+struct DesignChunk {
+    DesignDev d[kStage];
+};
+__global__ void store_designs_kernel(const DesignChunk c, int d0, int n) {
+    const int k = threadIdx.x;
+    if (k < n) g_design_table[d0 + k] = c.d[k];
 }
 
 // One-time set-up for the current device (its first call lands here).
@@ -152,12 +173,18 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
         return fail(SRP_EINVAL, "srp_force_noalloc: D*S = " + std::to_string(items) +
                                     " exceeds the fixed scratch capacity of " + std::to_string(kScratchUnits) +
                                     " (design, sun) items (8 MiB of partial sums); use srp_force");
-    // chunks per item: the automatic rule of srp_force, capped by the scratch
+    DevState* ds = nullptr;
+    int rc = setup_device(dev, &ds);
+    if (rc != SRP_OK) return rc;
+    // chunks per item: the automatic rule of srp_force (at least ~40k units
+    // in all, and at least one unit per resident warp per item so that the
+    // warps resident at a time share one (design, sun) item's BVH nodes in
+    // L1; chunks of at least 256 rays), then capped by the fixed scratch
     int64_t cpb = o->chunks_per_item;
     if (cpb < 0) return fail(SRP_EINVAL, "srp_force_noalloc: negative chunks_per_item");
     if (cpb == 0) {
-        const int64_t target = 40960;
-        cpb = items > 0 ? (target + items - 1) / items : 1;
+        const int64_t warps = (int64_t)ds->n_sm * ds->resident[width == 8 ? 1 : 0] * 4;
+        cpb = items > 0 ? std::max<int64_t>((40960 + items - 1) / items, warps) : 1;
         cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
     }
     int64_t chunk = (n + cpb - 1) / cpb;
@@ -172,9 +199,6 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
         chunk = std::max<int64_t>(64, (chunk + 63) / 64 * 64);
         cpb = std::max<int64_t>(1, (n + chunk - 1) / chunk);
     }
-    DevState* ds = nullptr;
-    int rc = setup_device(dev, &ds);
-    if (rc != SRP_OK) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (items == 0 || n == 0) {
         if (items > 0) {
@@ -204,25 +228,23 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     p.variant = 6;
     p.queue = ds->queue;
     p.designs = ds->table;
-    // the design table: copied into the fixed array in chunks of 64 entries
-    // staged on the stack (a copy from pageable memory returns once the
-    // CUDA runtime has staged the bytes, so the buffer can be refilled at once)
-    {
-        constexpr int kStage = 64;
-        DesignDev stage[kStage];
-        for (int d0 = 0; d0 < D; d0 += kStage) {
-            const int nd = std::min(kStage, D - d0);
-            for (int k = 0; k < nd; ++k) {
-                const srp_bvh* h = bvhs[d0 + k];
-                DesignDev z{};
-                z.tri = (const float4*)h->d_tri; z.nodes = (const float4*)h->d_nodes;
-                z.cx = h->c[0]; z.cy = h->c[1]; z.cz = h->c[2]; z.R = h->R;
-                z.T = h->T; z.width = h->width;
-                stage[k] = z;
-            }
-            e = cudaMemcpyAsync(ds->table + d0, stage, sizeof(DesignDev) * (size_t)nd, cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemcpyAsync(designs): ") + cudaGetErrorString(e));
+    // the design table: written into the fixed array by small kernels that
+    // carry 64 entries each in their parameters (stream-ordered, no host
+    // buffer outlives the call)
+    for (int d0 = 0; d0 < D; d0 += kStage) {
+        const int nd = std::min(kStage, D - d0);
+        DesignChunk chunk_tab;
+        std::memset(&chunk_tab, 0, sizeof chunk_tab);
+        for (int k = 0; k < nd; ++k) {
+            const srp_bvh* h = bvhs[d0 + k];
+            DesignDev& z = chunk_tab.d[k];
+            z.tri = (const float4*)h->d_tri; z.nodes = (const float4*)h->d_nodes;
+            z.cx = h->c[0]; z.cy = h->c[1]; z.cz = h->c[2]; z.R = h->R;
+            z.T = h->T; z.width = h->width;
         }
+        store_designs_kernel<<<1, kStage, 0, st>>>(chunk_tab, d0, nd);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("design table kernel launch: ") + cudaGetErrorString(e));
     }
     // the error word only collects flags (OR) and the queue counts up: both start at zero
     e = cudaMemsetAsync(ds->err, 0, sizeof(int), st);
