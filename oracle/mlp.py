@@ -77,9 +77,14 @@ def forward(x, params, round_act=False):
     return h, zs, hs
 
 
-def l1_loss_and_grad(x, t, params, round_act=False):
-    """L1 risk and its gradient w.r.t. every (W, b) by reverse mode
-    (round_act: hidden activations rounded to bfloat16 in the forward)."""
+def l1_loss_and_grad(x, t, params, round_act=False, round_grad=False):
+    """L1 risk and its gradient w.r.t. every (W, b) by reverse mode.
+
+    round_act: hidden activations rounded to bfloat16 in the forward.
+    round_grad: the back-propagated dL/dz of each layer is rounded to
+    bfloat16 where it enters a matrix product (the weight gradient
+    dz^T h and the next layer's dz W), as a BF16 tensor-core step consumes
+    it; the bias gradient sums the unrounded dL/dz."""
     y, zs, hs = forward(x, params, round_act=round_act)
     B = y.shape[0]
     loss = np.abs(y - t).sum() / B
@@ -88,21 +93,26 @@ def l1_loss_and_grad(x, t, params, round_act=False):
     g = dy
     for l in range(len(params) - 1, -1, -1):
         W, b = params[l]
-        gW = g.T @ hs[l]
+        gq = bf16_round(g) if round_grad else g
+        gW = gq.T @ hs[l]
         gb = g.sum(axis=0)
         grads[l] = (gW, gb)
         if l > 0:
-            g = (g @ W) * dsilu(zs[l - 1])
+            g = (gq @ W) * dsilu(zs[l - 1])
     return loss, grads
 
 
-def input_grad(x, params, wy):
-    """d(sum wy . y)/dx for weights wy [B,6] (the proxy's input gradient)."""
-    y, zs, hs = forward(x, params)
+def input_grad(x, params, wy, round_act=False, round_grad=False):
+    """d(sum wy . y)/dx for weights wy [B,6] (the proxy's input gradient).
+    round_act / round_grad as in l1_loss_and_grad: the forward's hidden
+    activations, and each layer's back-propagated vector where it enters
+    the product with W, rounded to bfloat16."""
+    y, zs, hs = forward(x, params, round_act=round_act)
     g = np.asarray(wy, np.float64)
     for l in range(len(params) - 1, -1, -1):
         W, _ = params[l]
-        g = g @ W
+        gq = bf16_round(g) if round_grad else g
+        g = gq @ W
         if l > 0:
             g = g * dsilu(zs[l - 1])
     return g

@@ -44,15 +44,29 @@ def test_uneven_designs_one_launch_match_single_calls(srp):
     for k in (0, 1, 2, 77, 199):
         one = srp.srp_force(ctx, [bv[k]], rho[k:k + 1], sun, com[k:k + 1], design_base=k, **kw)
         assert np.array_equal(allf[k], one[0]), k
-    # and against the oracle for a few designs
+    # and against the oracle for a few designs: rays whose hit lists differ
+    # (an FP32 argmin next to a shared edge) carry the oracle's deposits,
+    # then the aggregate is held to relative 1e-5 and every other ray to
+    # 1e-5 of its weight
+    idx = np.arange(64 * 64, dtype=np.int64)
     for k in (1, 2):
-        fo, _ = oracle.force(designs[k].verts, designs[k].tris, designs[k].group, rho[k], sun, com[k], nx=64, K=3,
-                             design_index=k)
+        d = designs[k]
+        fo, _ = oracle.force(d.verts, d.tris, d.group, rho[k], sun, com[k], nx=64, K=3, design_index=k)
         R = bv[k].info()["radius"]
+        w = (2 * R / 64) ** 2
         for s in range(4):
+            yg, hg = srp.srp_trace_rays(ctx, bv[k], rho[k], sun[s], com[k], idx, sun_index=s, design_index=k,
+                                        rays_x=64, max_bounces=3)
+            yo, ho = oracle.trace_rays(d.verts, d.tris, d.group, rho[k], sun[s], com[k], idx, nx=64, K=3,
+                                       sun_index=s, design_index=k)
+            diff = ~np.all(hg == ho, axis=1)
+            assert diff.sum() <= 4, (k, s, int(diff.sum()))
+            dev = np.abs(yg[~diff] - yo[~diff])
+            assert dev[:, :3].max(initial=0.0) <= 1e-5 * w and dev[:, 3:].max(initial=0.0) <= 1e-5 * w * R, (k, s)
+            corr = allf[k, s] - yg[diff].sum(0) + yo[diff].sum(0)
             fn = np.linalg.norm(fo[s, :3])
-            w = (2 * R / 64) ** 2
-            assert np.linalg.norm(allf[k, s, :3] - fo[s, :3]) <= max(1e-5 * fn, 2.0 * w)
+            assert np.linalg.norm(corr[:3] - fo[s, :3]) <= 1e-5 * fn, (k, s)
+            assert np.linalg.norm(corr[3:] - fo[s, 3:]) <= 1e-5 * fn * R, (k, s)
 
 
 def test_graph_replay_equals_call(srp):

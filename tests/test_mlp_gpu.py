@@ -71,6 +71,11 @@ def test_forward_parity(srp, B):
     err = np.abs(y - yo)
     assert np.sqrt(np.mean(err ** 2)) <= 3e-3 * rms, (np.sqrt(np.mean(err ** 2)), rms)
     assert err.max() <= 5e-2 * rms, (err.max(), rms)
+    # element by element within each output's own scale (force and torque
+    # components differ in magnitude): a wrong row or column pairing in one
+    # tile moves its elements by O(rms) of that output
+    col = np.sqrt(np.mean(yo ** 2, axis=0)) + 1e-30
+    assert np.all(err <= 5e-2 * col), ("per output", (err / col).max())
 
 
 def test_params_roundtrip_and_device_mode(srp):
@@ -92,27 +97,48 @@ def _grad_flat(grads):
     return np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
 
 
+def _elementwise(g, go, what, el=1e-2, rm=1e-3):
+    """Every element within el * rms(go) and the RMS deviation within
+    rm * rms(go): a layout or descriptor error confined to one row block or
+    one K chunk moves its elements by O(rms) and fails the first bound."""
+    scale = np.sqrt(np.mean(go ** 2)) + 1e-30
+    dev = np.abs(g - go)
+    assert dev.max() <= el * scale, (what, "max", dev.max() / scale)
+    assert np.sqrt(np.mean(dev ** 2)) <= rm * scale, (what, "rms", np.sqrt(np.mean(dev ** 2)) / scale)
+
+
 def test_training_gradient_parity(srp):
-    """One L1 gradient on 1024 samples vs the FP64 oracle with the same BF16
-    weights/inputs/activations; per-layer relative error <= 3e-2 (the kernel
-    also rounds the back-propagated dZ to BF16 at each GEMM)."""
+    """One L1 gradient on 1,000 samples (eight 128-row tiles, the last one
+    ragged) vs the FP64 oracle fed the same BF16 weights and inputs, with
+    the hidden activations and every back-propagated dL/dz rounded to BF16
+    where the kernel's GEMMs consume them (oracle round_act, round_grad).
+    Targets sit 0.2-1.0 away from the oracle's outputs on either side, so
+    the sign of y - t (an integer decided by floating point) is the same on
+    both sides.  Element by element, per parameter block: |g - g_or| <=
+    1e-2 rms(g_or) for every element and 1e-3 rms(g_or) in RMS.  What
+    remains is FP32 vs FP64 accumulation and one-ulp BF16 flips where the
+    two sides' values straddle a rounding boundary (the kernel's SiLU uses
+    the hardware tanh)."""
     ctx = srp.Context(0)
     p = omlp.init_params(seed=11)
+    p = [(W, np.random.default_rng(40 + l).normal(size=b.shape) * 0.1) for l, (W, b) in enumerate(p)]
     net = srp.MLP(ctx, flat(p))
-    x = inputs(1024, seed=5)
-    rng = np.random.default_rng(9)
-    t = rng.normal(size=(1024, 6)).astype(np.float32) * 3.0
-    loss, g = net.train_step(x, t, lr=0.0, want_grad=True)
+    B = 1000
+    x = inputs(B, seed=5)
     pb = [(omlp.bf16_round(W), b) for W, b in unflat(flat(p))]
-    lo, go = omlp.l1_loss_and_grad(omlp.bf16_round(x), t.astype(np.float64), pb, round_act=True)
-    assert abs(loss - lo) <= 1e-2 * lo, (loss, lo)
+    xb = omlp.bf16_round(x)
+    yo = omlp.forward(xb, pb, round_act=True)[0]
+    rng = np.random.default_rng(9)
+    t = (yo + rng.choice([-1.0, 1.0], size=yo.shape) * rng.uniform(0.2, 1.0, size=yo.shape)).astype(np.float32)
+    loss, g = net.train_step(x, t, lr=0.0, want_grad=True)
+    lo, go = omlp.l1_loss_and_grad(xb, t.astype(np.float64), pb, round_act=True, round_grad=True)
+    assert abs(loss - lo) <= 1e-4 * lo, (loss, lo)
     go = _grad_flat(go)
     o = 0
     for l in range(5):
         a, b = omlp.SIZES[l], omlp.SIZES[l + 1]
-        for n in (a * b, b):
-            gg, oo = g[o:o + n], go[o:o + n]
-            assert np.linalg.norm(gg - oo) <= 3e-2 * np.linalg.norm(oo) + 1e-7, (l, n, np.linalg.norm(gg - oo) / np.linalg.norm(oo))
+        for n, name in ((a * b, "W"), (b, "b")):
+            _elementwise(g[o:o + n], go[o:o + n], (l, name))
             o += n
 
 
@@ -148,8 +174,11 @@ def test_training_reduces_loss(srp):
 
 def test_input_gradient_parity(srp):
     """srp_mlp_grad_input vs the FP64 oracle's input gradient with the same
-    BF16 weights and inputs (the kernel's GEMMs round operands to BF16):
-    relative 3e-2 in norm, per row block; host and device modes agree."""
+    BF16 weights and inputs, the hidden activations and each back-propagated
+    vector (wy included) rounded to BF16 where the kernel's GEMMs consume
+    them (round_act, round_grad); row by row, every element within 1e-2 of
+    its row's RMS and the RMS deviation within 1e-3; host and device modes
+    agree bit for bit."""
     ctx = srp.Context(0)
     p = omlp.init_params(seed=21)
     net = srp.MLP(ctx, flat(p))
@@ -157,10 +186,13 @@ def test_input_gradient_parity(srp):
     wy = np.random.default_rng(3).normal(size=(777, 6)).astype(np.float32)
     gx = net.grad_input(x, wy)
     pb = [(omlp.bf16_round(W), b) for W, b in unflat(flat(p))]
-    go = omlp.input_grad(omlp.bf16_round(x), pb, wy.astype(np.float64))
-    assert np.linalg.norm(gx - go) <= 3e-2 * np.linalg.norm(go), np.linalg.norm(gx - go) / np.linalg.norm(go)
-    dev = torch.device("cuda", 0)
-    gd = net.grad_input(torch.from_numpy(x).to(dev), torch.from_numpy(wy).to(dev))
+    go = omlp.input_grad(omlp.bf16_round(x), pb, wy.astype(np.float64), round_act=True, round_grad=True)
+    row = np.sqrt(np.mean(go ** 2, axis=1, keepdims=True)) + 1e-30
+    dev = np.abs(gx - go)
+    assert np.all(dev <= 1e-2 * row), ("max per row", (dev / row).max())
+    assert np.sqrt(np.mean(dev ** 2)) <= 1e-3 * np.sqrt(np.mean(go ** 2)), np.sqrt(np.mean(dev ** 2))
+    dev_ = torch.device("cuda", 0)
+    gd = net.grad_input(torch.from_numpy(x).to(dev_), torch.from_numpy(wy).to(dev_))
     torch.cuda.synchronize()
     assert np.array_equal(gd.cpu().numpy(), gx)
 

@@ -103,3 +103,75 @@ def test_forward_against_a_hand_built_network():
         want = [0.1, 0.2, 0.3, 0.4, 0.5, -2.0 * h + 0.7]
         y = mlp.forward(x, p)[0][0]
         assert np.allclose(y, want, rtol=1e-14, atol=1e-15), (x2, y, want)
+
+
+def test_round_grad_single_layer_closed_form():
+    """round_grad on a network with no hidden layer (19 -> 6, linear): the
+    only back-propagated vector is dL/dy = sign(y - t)/B.  For B = 3 its
+    bfloat16 rounding is bf16(1/3) = 0.333984375 = (1/3)(1 + 2^-9), so the
+    weight gradient is the exact one times 3 * 0.333984375 = 1.001953125
+    (a rounding applied after the product, or to the inputs, gives another
+    factor), and the bias gradient, which sums the unrounded vector, is
+    exact.  For B = 4, 1/4 is a bfloat16 and nothing changes."""
+    rng = np.random.default_rng(5)
+    p = [(rng.normal(size=(6, 19)), rng.normal(size=6))]
+    for B, factor in ((3, 1.001953125), (4, 1.0)):
+        x = rng.normal(size=(B, 19))
+        t = rng.normal(size=(B, 6)) * 10.0
+        _, g0 = mlp.l1_loss_and_grad(x, t, p)
+        _, g1 = mlp.l1_loss_and_grad(x, t, p, round_grad=True)
+        assert np.array_equal(g1[0][1], g0[0][1])
+        mag = (np.ones((B, 6)) / B).T @ np.abs(x)      # |dL/dy|^T |x|
+        assert np.all(np.abs(g1[0][0] - factor * g0[0][0]) <= 1e-14 * mag), B
+
+
+def test_round_grad_deviation_is_bounded_by_bf16():
+    """round_grad on the full network: every back-propagated vector is
+    rounded to bfloat16 (relative error <= 2^-9 per element) where it
+    enters a product, so the weight gradients differ from the exact ones by
+    at most a few times 2^-9 relative to the products of magnitudes
+    |g| |h| summed over the batch, and the bias gradient of the last layer
+    (which sums the unrounded dL/dy) is exact.  The deviation is also not
+    zero: the rounding is applied."""
+    rng = np.random.default_rng(6)
+    p = mlp.init_params(seed=4)
+    x = rng.normal(size=(48, 19))
+    t = rng.normal(size=(48, 6)) * 10.0
+    _, g0 = mlp.l1_loss_and_grad(x, t, p)
+    _, g1 = mlp.l1_loss_and_grad(x, t, p, round_grad=True)
+    assert np.array_equal(g1[4][1], g0[4][1])
+    # magnitudes: |dL/dz_l|^T |h_l| along the exact backward
+    y, zs, hs = mlp.forward(x, p)
+    g = np.sign(y - t) / 48
+    for l in range(4, -1, -1):
+        mag = np.abs(g).T @ np.abs(hs[l])
+        dev = np.abs(g1[l][0] - g0[l][0])
+        assert np.all(dev <= (5 - l) * 2.0 ** -8 * mag + 1e-18), l
+        assert dev.max() > 0.0, l
+        if l > 0:
+            g = (g @ p[l][0]) * mlp.dsilu(zs[l - 1])
+
+
+def test_round_grad_input_gradient():
+    """input_grad with round_grad: with wy of bfloat16 values and a network
+    whose only layer is linear the rounding changes nothing; on the full
+    network the deviation from the exact input gradient stays within the
+    BF16 bound and is not zero."""
+    rng = np.random.default_rng(8)
+    p1 = [(rng.normal(size=(6, 19)), rng.normal(size=6))]
+    x = rng.normal(size=(5, 19))
+    wy = mlp.bf16_round(rng.normal(size=(5, 6)))
+    assert np.array_equal(mlp.input_grad(x, p1, wy, round_grad=True), mlp.input_grad(x, p1, wy))
+    p = mlp.init_params(seed=9)
+    wy = rng.normal(size=(5, 6))
+    g0 = mlp.input_grad(x, p, wy)
+    g1 = mlp.input_grad(x, p, wy, round_grad=True)
+    # magnitude of the exact chain: |wy| |W4| |s'| |W3| ... |W0|
+    _, zs, _ = mlp.forward(x, p)
+    m = np.abs(wy)
+    for l in range(4, -1, -1):
+        m = m @ np.abs(p[l][0])
+        if l > 0:
+            m = m * np.abs(mlp.dsilu(zs[l - 1]))
+    dev = np.abs(g1 - g0)
+    assert np.all(dev <= 5 * 2.0 ** -8 * m) and dev.max() > 0.0

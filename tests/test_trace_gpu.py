@@ -52,6 +52,24 @@ def _assert_parity(ft_gpu, ft_or, R, tol=1e-5, what=""):
         assert ef <= tol and et <= tol, (what, s, ef, et, ft_gpu[s], ft_or[s])
 
 
+def _assert_per_ray(yg, yo, w, R, what=""):
+    """Per-ray deposits of rays whose hit lists agree: force components
+    within 1e-5 of the ray weight w, torque components within 1e-5 w R
+    (the lever arm is up to the grid radius R)."""
+    if yg.shape[0] == 0:
+        return
+    df = np.abs(yg[:, :3] - yo[:, :3]).max() / w
+    dt = np.abs(yg[:, 3:] - yo[:, 3:]).max() / (w * R)
+    assert df <= 1e-5 and dt <= 1e-5, (what, "per-ray force / torque deviation in ray weights", df, dt)
+
+
+def _corrected(ft, yg, hg, yo, ho):
+    """The GPU aggregate with the contributions of rays whose hit lists
+    differ (an FP32 argmin next to a shared edge) replaced by the oracle's."""
+    diff = ~np.all(hg == ho, axis=1)
+    return ft - yg[diff].sum(0) + yo[diff].sum(0), int(diff.sum())
+
+
 # ------------------------------------------------------------------ config 1
 @pytest.mark.parametrize("K", [1, 2, 3])
 def test_boxwing_full_grid_parity(srp, ctx, K):
@@ -74,14 +92,18 @@ def test_boxwing_per_ray_paths(srp, ctx):
     yo, ho = oracle.trace_rays(m.verts, m.tris, m.group, rho, sun[0], com, idx, nx=512, K=3)
     same = np.all(hg == ho, axis=1)
     assert same.mean() > 0.99999, same.mean()
-    w = (2 * b.info()["radius"] / 512) ** 2
-    assert np.max(np.abs(yg[same] - yo[same])) <= 1e-5 * w * 10  # per-ray, in units of the ray weight
+    R = b.info()["radius"]
+    w = (2 * R / 512) ** 2
+    _assert_per_ray(yg[same], yo[same], w, R, "box-wing 512^2")
     ft = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=512, max_bounces=3)
     assert np.allclose(ft[0, 0], yg.sum(0), rtol=1e-6, atol=1e-9 * w)  # FP32 per-lane partials
 
 
 def test_boxwing_direction_sweep(srp, ctx):
-    """64 Fibonacci sun directions in one launch, K = 3."""
+    """64 Fibonacci sun directions in one launch, K = 3: per direction the
+    aggregate within 1e-5 once the rays whose hit lists differ (edge-grazing
+    FP32 argmins) carry the oracle's deposits, and every other ray within
+    1e-5 of its weight."""
     m, rho, _, com = W.config1()
     sun = W.fibonacci_directions(64)
     b = _bvh(srp, ctx, m)
@@ -89,11 +111,18 @@ def test_boxwing_direction_sweep(srp, ctx):
     fo, _ = oracle.force(m.verts, m.tris, m.group, rho, sun, com, nx=128, K=3)
     R = b.info()["radius"]
     w = (2 * R / 128) ** 2
-    # an edge-grazing ray may differ per direction: allow 2 ray weights
+    idx = np.arange(128 * 128, dtype=np.int64)
+    mis = 0
     for s in range(64):
-        fn = max(np.linalg.norm(fo[s, :3]), 1e-30)
-        ef = np.linalg.norm(ft[0, s, :3] - fo[s, :3])
-        assert ef <= 1e-5 * fn or ef <= 2.0 * w, (s, ef / fn)
+        yg, hg = srp.srp_trace_rays(ctx, b, rho, sun[s], com, idx, sun_index=s, rays_x=128, max_bounces=3)
+        yo, ho = oracle.trace_rays(m.verts, m.tris, m.group, rho, sun[s], com, idx, nx=128, K=3, sun_index=s)
+        same = np.all(hg == ho, axis=1)
+        _assert_per_ray(yg[same], yo[same], w, R, f"sun {s}")
+        corr, nd = _corrected(ft[0, s], yg, hg, yo, ho)
+        mis += nd
+        if np.linalg.norm(fo[s, :3]) > 0.0:
+            _assert_parity(corr, fo[s], R, what=f"sun {s}")
+    assert mis <= 1e-3 * 64 * idx.shape[0], mis
 
 
 # ------------------------------------------------------------------ config 2
@@ -114,7 +143,7 @@ def test_procedural_satellite_sampled_full_grid(srp, ctx):
         same = np.all(hg == ho, axis=1)
         mis = int((~same).sum())
         tot_mis += mis
-        assert np.max(np.abs(yg[same] - yo[same]), initial=0.0) <= 1e-4 * w
+        _assert_per_ray(yg[same], yo[same], w, R, f"sun {s}")
         # aggregate over the sample through srp_force (same rays, same counters)
         ft = srp.srp_force(ctx, [b], rho[None], sun_all[s:s + 1], com[None], rays_x=2048, max_bounces=3,
                            ray_offset=0, ray_stride=1021, ray_count=len(idx), sun_base=s)
