@@ -198,8 +198,9 @@ int srp_force(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho,
               const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
               double* out_ft, double* out_sigma);
 
-/* ---- the paper's own estimator without bounces (Sec. 3.2 "Estimation";
- * the no-bounce variant "NB" of Table 3) ---------------------------------
+/* ---- the paper's own estimator (Sec. 3.2 "Estimation": surface samples,
+ * next-event estimation toward the sun, BRDF-sampled incoming light; the
+ * no-bounce variant "NB" of Table 3 with max_bounces = 1) ------------------
  * Same items, arrays, memory rules and outputs as srp_force, estimated by
  * surface sampling with next-event estimation instead of a ray grid:
  *   - triangle f (original order) receives n_f = max(1, ceil(density*A_f))
@@ -211,14 +212,25 @@ int srp_force(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho,
  *     any-hit shadow ray from x along e (the source triangle skipped, hits
  *     at t > 1e-6 R counted) decides whether x is lit; a lit sample adds
  *     (A_f/n_f) P cos [(1-rs) d - (2 rs cos + 2/3 rd) n], d = -e, and its
- *     torque (x - com) x F; every other sample adds zero;
+ *     torque (x - com) x F;
+ *   - max_bounces = 2 adds, on each side n_s = +-n_e of the facet (n_e the
+ *     winding normal), one gathered Lambertian interreflection: direction
+ *     omega = unit(n_s + s), s the uniform unit vector z = 1 - 2 ua,
+ *     phi = 2 pi ub ((ua, ub) = (u3, u4) of the sample's counter for +n_e,
+ *     (u1, u2) of the counter with design word | 2^28 for -n_e); its
+ *     closest hit y (source skipped, t > 1e-6 R) on the side m facing x is
+ *     lit when m.e > 0 and the shadow ray from y along e is free; then
+ *     E = rd_y P (m.e) and x adds (A_f/n_f) E [(1-rs)(-omega) -
+ *     (2 rs cos + 2/3 rd) n_s], cos = omega.n_s, and its torque.  Only the
+ *     diffuse part of y's reflection is gathered (its specular lobe is a
+ *     delta that a sampled direction does not reach);
  *   - out_sigma: collapsed-strata standard errors over the sample pairs
  *     (2i, 2i+1) of k = prefix(f) + j.
  * opts: seed, pressure, mem, sun_per_design, sun_base, design_base,
- * block_threads (0 or 128) and kernel_variant (0 = 8, or 4, 6, 8: the
+ * block_threads (0 or 128), kernel_variant (0 = 8, or 4, 6, 8: the
  * minimum resident 128-thread blocks per SM the sampling kernel is
- * compiled for) are used; max_bounces must be 1
- * (SRP_EUNSUPPORTED otherwise); the ray-grid fields are ignored.
+ * compiled for) and max_bounces (1 or 2; SRP_EUNSUPPORTED otherwise) are
+ * used; the ray-grid fields are ignored.
  * density: samples per unit area, finite and >= 0; a design's samples must
  * stay below 2^31 (SRP_EINVAL when the planned bound exceeds it).
  * out_samples [D] int64 (opts->mem, or NULL): samples per design.
@@ -247,7 +259,8 @@ int srp_force_area(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float*
  * hit of x + t omega (source triangle skipped, t > 1e-6 R) receives
  * w [(1-rs) omega - (2 rs cos + 2/3 rd) n] (n the hit normal facing the
  * ray, cos = -n.omega) and its torque.  Same validation and errors as
- * srp_force_area; emit values are validated for host-mem calls. */
+ * srp_force_area; max_bounces must be 1; emit values are validated for
+ * host-mem calls. */
 int srp_force_thermal(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho, int G,
                       const float* emit, const double* com, float density, const srp_trace_opts* opts,
                       double* out_ft, double* out_sigma, int64_t* out_samples);

@@ -99,7 +99,7 @@ def _load():
         lib.or_trace_rays.restype = i32
         lib.or_area_counts.argtypes = [P, i32, P, i32, C.c_float, P]
         lib.or_area_counts.restype = i64
-        lib.or_force_area.argtypes = [P, i32, P, P, i32, P, P, i32, P, C.c_float, u64, f64, u32, u32, i32, P, P]
+        lib.or_force_area.argtypes = [P, i32, P, P, i32, P, P, i32, P, C.c_float, u64, f64, u32, u32, i32, i32, P, P]
         lib.or_force_area.restype = i32
         lib.or_thermal_counts.argtypes = [P, i32, P, P, i32, P, C.c_float, P]
         lib.or_thermal_counts.restype = i64
@@ -233,15 +233,18 @@ def area_counts(verts, tris, density):
 
 
 def force_area(verts, tris, group, rho, sun, com, *, density, seed=0, P=1.0, sun_base=0, design_index=0,
-               threads=None):
-    """Area-sampling / next-event estimate of (F, tau) [S,6] and sigma [S,6]."""
+               K=1, threads=None):
+    """Area-sampling / next-event estimate of (F, tau) [S,6] and sigma [S,6];
+    K = 2 adds one gathered Lambertian interreflection per sample and side."""
+    if K not in (1, 2):
+        raise ValueError("force_area: K must be 1 or 2")
     lib = _load()
     v = _c(verts, np.float32); t = _c(tris, np.int32); g = _c(group, np.int32)
     r = _c(rho, np.float64); s = _c(np.atleast_2d(sun), np.float64); cm = _c(com, np.float64)
     S = s.shape[0]
     ft = np.zeros((S, 6)); sg = np.zeros((S, 6))
     lib.or_force_area(_p(v), v.shape[0], _p(t), _p(g), t.shape[0], _p(r), _p(s), S, _p(cm), float(density), seed,
-                      P, sun_base, design_index, threads or host_threads(), _p(ft), _p(sg))
+                      P, sun_base, design_index, K, threads or host_threads(), _p(ft), _p(sg))
     return ft, sg
 
 

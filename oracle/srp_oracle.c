@@ -684,6 +684,24 @@ int or_trace_rays(const float* verts, int V, const int32_t* tris, const int32_t*
 /*    torque (x - COM) x deposit;                                       */
 /*  - sums in sample order k = prefix(f) + j; sigma: collapsed strata   */
 /*    over pairs (k = 2i, 2i+1).                                        */
+/*  With K = 2 each sample also gathers one Lambertian interreflection  */
+/*  (the indirect term of the estimator: a BRDF-sampled incoming         */
+/*  direction, its closest hit y, next-event estimation at y):          */
+/*  - per side sigma = +1, -1 of the facet (n_s = sigma n_e, n_e the     */
+/*    winding normal): direction omega = unit(n_s + s), s uniform on the */
+/*    unit sphere (cosine-distributed about n_s, pdf cos/pi); side +1    */
+/*    takes (u2, u3) of the sample's counter, side -1 (u0, u1) of the    */
+/*    counter (j, f, sun, design | 2^31 | 2^28);                         */
+/*  - closest hit y of the ray (x, omega) (skip f, t > 1e-6 R); y's side */
+/*    that faces x, m, is lit when m.e > 0 and the shadow ray from y     */
+/*    along e (skip y's triangle, t > 1e-6 R) is free;                   */
+/*  - the radiance y reflects toward x is rd_y P (m.e) / pi, so the      */
+/*    irradiance estimate at x is E = pi L / pdf * cos = rd_y P (m.e);   */
+/*  - x receives that light arriving along -omega at cos = omega.n_s and */
+/*    deposits (A_f / n_f) E [(1-rs) (-omega) - (2 rs cos + 2/3 rd) n_s] */
+/*    (its own BRDF, the per-plate law), torque about COM.               */
+/*  Only y's diffuse reflection is gathered: its specular reflection is  */
+/*  a delta lobe that a sampled direction reaches with probability 0.    */
 /* ------------------------------------------------------------------ */
 static float area32(const double* tv)
 {
@@ -723,9 +741,47 @@ typedef struct {
     const int64_t* prefix;
     int S;
     uint32_t sun_base;
+    int K;              /* 1: direct light only; 2: plus one Lambertian interreflection */
     double* out;        /* [S][12] */
     int s0, s1;
 } area_job;
+
+/* One gathered Lambertian interreflection at x (side normal ns, winding
+ * facet f) along omega = unit(ns + uniform unit vector(ua, ub)); adds the
+ * deposit and torque to y6.  wA = A_f / n_f, (rs, rd) of the facet of x. */
+static void gather_diffuse(const scene_t* sc, const double e[3], int f, const double x[3], const double ns[3],
+                           double ua, double ub, double wA, double rs, double rd, double y6[6])
+{
+    double z = 1.0 - 2.0 * ua, rr = sqrt(fmax(0.0, 1.0 - z * z)), phi = 2.0 * M_PI * ub;
+    double om[3] = {ns[0] + rr * cos(phi), ns[1] + rr * sin(phi), ns[2] + z};
+    double L = sqrt(dot3(om, om));
+    if (!(L > 0.0)) return;
+    for (int q = 0; q < 3; ++q) om[q] /= L;
+    wray r;
+    wray_setup(&r, x, om);
+    double t;
+    const int h = closest(sc, &r, 1e-6 * sc->R, f, &t);
+    if (h < 0) return;
+    const double* nh = sc->tn + 3 * (size_t)h;
+    double m[3];
+    double sg = dot3(nh, om) > 0.0 ? -1.0 : 1.0;          /* the side of y facing x */
+    for (int q = 0; q < 3; ++q) m[q] = sg * nh[q];
+    const double ce = dot3(m, e);
+    if (!(ce > 0.0)) return;
+    double yp[3];
+    for (int q = 0; q < 3; ++q) yp[q] = x[q] + t * om[q];
+    wray rs_;
+    wray_setup(&rs_, yp, e);
+    double ts;
+    if (closest(sc, &rs_, 1e-6 * sc->R, h, &ts) >= 0) return;
+    const double E = sc->rho[2 * sc->group[h] + 1] * sc->P * ce;
+    const double cs = dot3(om, ns);
+    const double cn = 2.0 * rs * cs + (2.0 / 3.0) * rd;
+    double dp[3], arm[3], tq[3];
+    for (int q = 0; q < 3; ++q) { dp[q] = wA * E * (-(1.0 - rs) * om[q] - cn * ns[q]); arm[q] = x[q] - sc->com[q]; }
+    cross3(arm, dp, tq);
+    for (int q = 0; q < 3; ++q) { y6[q] += dp[q]; y6[3 + q] += tq[q]; }
+}
 
 static void* area_worker(void* arg)
 {
@@ -776,6 +832,20 @@ static void* area_worker(void* arg)
                         for (int q = 0; q < 3; ++q) { y[q] = dp[q]; y[3 + q] = tq[q]; }
                     }
                 }
+                if (jb->K >= 2) {
+                    /* both sides of the facet gather one interreflection */
+                    const double wA = A / nf;
+                    double ns[3];
+                    for (int q = 0; q < 3; ++q) ns[q] = ng[q];
+                    gather_diffuse(sc, e, f, x, ns, u[2], u[3], wA, rs, rd, y);
+                    uint32_t ctr2[4] = {(uint32_t)j, (uint32_t)f, jb->sun_base + (uint32_t)s,
+                                        sc->dsg | 0x80000000u | 0x10000000u};
+                    uint32_t key2[2] = {(uint32_t)sc->seed, (uint32_t)(sc->seed >> 32)};
+                    uint32_t o2[4];
+                    or_philox4x32_10(ctr2, key2, o2);
+                    for (int q = 0; q < 3; ++q) ns[q] = -ng[q];
+                    gather_diffuse(sc, e, f, x, ns, u24(o2[0]), u24(o2[1]), wA, rs, rd, y);
+                }
                 for (int q = 0; q < 6; ++q) acc[q] += y[q];
                 if ((k & 1) == 0) {
                     for (int q = 0; q < 6; ++q) pend[q] = y[q];
@@ -792,7 +862,7 @@ static void* area_worker(void* arg)
 
 int or_force_area(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
                   const double* rho, const double* sun, int S, const double* com, float density,
-                  uint64_t seed, double P, uint32_t sun_base, uint32_t dsg, int threads,
+                  uint64_t seed, double P, uint32_t sun_base, uint32_t dsg, int K, int threads,
                   double* out_ft, double* out_sigma)
 {
     double* tv = (double*)malloc(sizeof(double) * 9 * (size_t)(T > 0 ? T : 1));
@@ -811,7 +881,7 @@ int or_force_area(const float* verts, int V, const int32_t* tris, const int32_t*
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * threads);
     area_job* jb = (area_job*)calloc(threads, sizeof(area_job));
     for (int t = 0; t < threads; ++t) {
-        jb[t].sc = &sc; jb[t].sun = sun; jb[t].counts = counts; jb[t].S = S; jb[t].sun_base = sun_base;
+        jb[t].sc = &sc; jb[t].sun = sun; jb[t].counts = counts; jb[t].S = S; jb[t].sun_base = sun_base; jb[t].K = K;
         jb[t].out = out; jb[t].s0 = S * t / threads; jb[t].s1 = S * (t + 1) / threads;
     }
     for (int t = 1; t < threads; ++t) pthread_create(&th[t], NULL, area_worker, &jb[t]);

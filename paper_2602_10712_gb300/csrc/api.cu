@@ -832,8 +832,11 @@ int area_common(srp_ctx* c, int mode, const srp_bvh* const* bvhs, int D, const f
     if (D < 0 || S < 0) return fail(SRP_EINVAL, fn + ": negative D or S");
     if (D > kMaxDesignsPerLaunch) return fail(SRP_EINVAL, fn + ": too many designs in one call");
     if (G < 1 || G > kMaxGroups) return fail(SRP_EINVAL, fn + ": G must be in 1..64");
-    if (o->max_bounces != 1)
-        return fail(SRP_EUNSUPPORTED, fn + ": only the no-bounce estimator (max_bounces = 1) is built");
+    if (mode == 1 && o->max_bounces != 1)
+        return fail(SRP_EUNSUPPORTED, fn + ": thermal packets deposit at their first hit (max_bounces = 1)");
+    if (mode == 0 && o->max_bounces != 1 && o->max_bounces != 2)
+        return fail(SRP_EUNSUPPORTED, fn + ": max_bounces must be 1 (direct light) or 2 (plus one Lambertian "
+                                          "interreflection)");
     if (!(density >= 0.0f) || !std::isfinite(density)) return fail(SRP_EINVAL, fn + ": bad density");
     if (!(o->pressure >= 0.0) || !std::isfinite(o->pressure)) return fail(SRP_EINVAL, fn + ": bad pressure");
     if (o->block_threads != 0 && o->block_threads != 128)
@@ -897,7 +900,7 @@ int area_common(srp_ctx* c, int mode, const srp_bvh* const* bvhs, int D, const f
     if (D > 0) CU(cudaMemcpyAsync(d_xb, xbase.data(), sizeof(int64_t) * D, cudaMemcpyHostToDevice, c->stream), "H2D xbase");
     AreaParams p;
     std::memset(&p, 0, sizeof p);
-    p.mode = mode;
+    p.mode = mode == 0 && o->max_bounces == 2 ? 2 : mode;
     p.D = D; p.S = S; p.G = G; p.sun_per_design = (mode == 0 && o->sun_per_design) ? 1 : 0;
     p.seed = o->seed; p.P = (float)o->pressure; p.density = density;
     p.sun_base = o->sun_base; p.design_base = o->design_base;

@@ -25,6 +25,12 @@
 //                      sums -> partials
 // and the ray-grid tracer's reduce kernel sums the partials of each item.
 //
+// Interreflection mode (max_bounces = 2): each sample also gathers one
+// Lambertian interreflection per side of its facet -- a cosine-sampled
+// incoming direction, its closest hit y, next-event estimation at y -- and
+// deposits the light y reflects toward it by its own facet BRDF (the
+// indirect term of the paper's estimator, diffuse part).
+//
 // Thermal mode (Sec. 5.9, local Lambertian emitters): only triangles of
 // groups with emit > 0 get samples; a sample's packet carries
 // w = P emit A_f / n_f, recoils by its expectation -(2/3) w n_e at x (n_e the
@@ -139,11 +145,63 @@ __device__ __forceinline__ int find_tri(const int32_t* __restrict__ ex, int lo, 
     return lo;
 }
 
+// One gathered Lambertian interreflection at x (leaf triangle L, side
+// normal ns) along omega = unit(ns + uniform unit vector(ua, ub)): the
+// closest hit y, y's side m facing x lit when m.e > 0 and its shadow ray
+// along e is free; then irradiance E = rd_y P (m.e) arrives at x along
+// -omega (cosine sampling cancels the 1/pi of the Lambertian radiance) and
+// x deposits (A/n) E [(1 - rs)(-omega) - (2 rs cos + 2/3 rd) ns],
+// cos = omega.ns, by its own facet BRDF.
+template <int W>
+__device__ __forceinline__ void gather_diffuse(const DesignDev& dz, int L, float3 x, float3 ns, float ua, float ub,
+                                               float wA, float rs, float rd, float3 e, const RaySetup& rset,
+                                               float3 com, const float* rho, float tmin, float P, int* err,
+                                               float y[6], uint32_t& nvis, uint32_t& ntest, uint32_t& nseg) {
+    const float z = 1.0f - 2.0f * ua;
+    const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    float sp, cp;
+    sincospif(2.0f * ub, &sp, &cp);
+    const float3 v = f3(ns.x + rr * cp, ns.y + rr * sp, ns.z + z);
+    const float l2 = dot(v, v);
+    if (!(l2 > 0.0f)) return;
+    const float3 om = rsqrtf(l2) * v;
+    RaySetup r;
+    setup_ray(r, x, om);
+    ++nseg;
+    float t;
+    const int h = closest_hit<W>(dz, r, tmin, L, t, err, nvis, ntest);
+    if (h < 0) return;
+    const float4 ha = __ldg(dz.tri + 3 * (size_t)h), hb = __ldg(dz.tri + 3 * (size_t)h + 1),
+                 hc = __ldg(dz.tri + 3 * (size_t)h + 2);
+    float3 m = cross(xyz(hb) - xyz(ha), xyz(hc) - xyz(ha));
+    m = rsqrtf(dot(m, m)) * m;
+    if (dot(m, om) > 0.0f) m = -1.0f * m;
+    const float ce = dot(m, e);
+    if (!(ce > 0.0f)) return;
+    const float3 yp = x + t * om;
+    RaySetup rs2 = rset;
+    rs2.o = yp;
+    rs2.oinv = f3(yp.x * rs2.inv.x, yp.y * rs2.inv.y, yp.z * rs2.inv.z);
+    ++nseg;
+    if (any_hit<W>(dz, rs2, tmin, h, err, nvis, ntest)) return;
+    const int gh = (int)__float_as_uint(hb.w);
+    const float E = __ldg(rho + 2 * gh + 1) * P * ce;
+    const float cs = dot(om, ns);
+    const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
+    const float a1 = wA * E * (1.0f - rs), a2 = wA * E * cn;
+    const float3 dp = f3(-a1 * om.x - a2 * ns.x, -a1 * om.y - a2 * ns.y, -a1 * om.z - a2 * ns.z);
+    const float3 tq = cross(x - com, dp);
+    y[0] += dp.x; y[1] += dp.y; y[2] += dp.z; y[3] += tq.x; y[4] += tq.y; y[5] += tq.z;
+}
+
 // One sun-light sample: point on leaf triangle L (original index f, sample
-// jj of nf), shadow ray along e, expected BRDF momentum if lit.
+// jj of nf), shadow ray along e, expected BRDF momentum if lit; with IND,
+// one gathered Lambertian interreflection on each side of the facet (side
+// +n_e from (u3, u4) of the sample's counter, side -n_e from the counter
+// with bit 28 of the design word set).
 // rset: setup_ray of the item's shadow direction e (origin 0): its 1/e and
 // shear rows serve every sample of the item; only o/e is per sample.
-template <int W>
+template <int W, bool IND>
 __device__ __forceinline__ void sample_sun(const DesignDev& dz, int L, int f, uint32_t jj, int32_t nf, float3 e,
                                            const RaySetup& rset, float3 com, const float* rho, float tmin, uint32_t sg,
                                            uint32_t dg, uint32_t key0, uint32_t key1, float P, int* err, float y[6],
@@ -151,31 +209,43 @@ __device__ __forceinline__ void sample_sun(const DesignDev& dz, int L, int f, ui
     const float4 a = __ldg(dz.tri + 3 * (size_t)L), b = __ldg(dz.tri + 3 * (size_t)L + 1),
                  c = __ldg(dz.tri + 3 * (size_t)L + 2);
     const float3 e1 = xyz(b) - xyz(a), e2 = xyz(c) - xyz(a);
-    float3 n = cross(e1, e2);
-    const float len = sqrtf(dot(n, n));
-    n = (1.0f / len) * n;
+    float3 ne = cross(e1, e2);
+    const float len = sqrtf(dot(ne, ne));
+    ne = (1.0f / len) * ne;
+    float3 n = ne;
     float cs = dot(n, e);
     if (cs < 0.0f) { n = -1.0f * n; cs = -cs; }
-    if (!(cs > 0.0f)) return;
+    if (!IND && !(cs > 0.0f)) return;
     const uint4 rnd = philox4x32_10(make_uint4(jj, (uint32_t)f, sg, dg), key0, key1);
     const float u1 = unit24(rnd.x), u2 = unit24(rnd.y);
     const float sr = sqrtf(u1);
     const float b1 = sr * (1.0f - u2), b2 = sr * u2;
     const float3 x = f3(fmaf(b2, e2.x, fmaf(b1, e1.x, a.x)), fmaf(b2, e2.y, fmaf(b1, e1.y, a.y)),
                         fmaf(b2, e2.z, fmaf(b1, e1.z, a.z)));
-    RaySetup r = rset;
-    r.o = x;
-    r.oinv = f3(x.x * r.inv.x, x.y * r.inv.y, x.z * r.inv.z);
-    ++nseg;
-    if (any_hit<W>(dz, r, tmin, L, err, nvis, ntest)) return;
     const int g = (int)__float_as_uint(b.w);
     const float rs = __ldg(rho + 2 * g), rd = __ldg(rho + 2 * g + 1);
-    const float wgt = P * (0.5f * len) / (float)nf;
-    const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
-    const float ws = wgt * cs, a1 = ws * (1.0f - rs), a2 = ws * cn;
-    const float3 dp = f3(-a1 * e.x - a2 * n.x, -a1 * e.y - a2 * n.y, -a1 * e.z - a2 * n.z);
-    const float3 tq = cross(x - com, dp);
-    y[0] = dp.x; y[1] = dp.y; y[2] = dp.z; y[3] = tq.x; y[4] = tq.y; y[5] = tq.z;
+    if (cs > 0.0f) {
+        RaySetup r = rset;
+        r.o = x;
+        r.oinv = f3(x.x * r.inv.x, x.y * r.inv.y, x.z * r.inv.z);
+        ++nseg;
+        if (!any_hit<W>(dz, r, tmin, L, err, nvis, ntest)) {
+            const float wgt = P * (0.5f * len) / (float)nf;
+            const float cn = 2.0f * rs * cs + (2.0f / 3.0f) * rd;
+            const float ws = wgt * cs, a1 = ws * (1.0f - rs), a2 = ws * cn;
+            const float3 dp = f3(-a1 * e.x - a2 * n.x, -a1 * e.y - a2 * n.y, -a1 * e.z - a2 * n.z);
+            const float3 tq = cross(x - com, dp);
+            y[0] = dp.x; y[1] = dp.y; y[2] = dp.z; y[3] = tq.x; y[4] = tq.y; y[5] = tq.z;
+        }
+    }
+    if (IND) {
+        const float wA = (0.5f * len) / (float)nf;
+        gather_diffuse<W>(dz, L, x, ne, unit24(rnd.z), unit24(rnd.w), wA, rs, rd, e, rset, com, rho, tmin, P, err, y,
+                          nvis, ntest, nseg);
+        const uint4 rnd2 = philox4x32_10(make_uint4(jj, (uint32_t)f, sg, dg | 0x10000000u), key0, key1);
+        gather_diffuse<W>(dz, L, x, -1.0f * ne, unit24(rnd2.x), unit24(rnd2.y), wA, rs, rd, e, rset, com, rho, tmin,
+                          P, err, y, nvis, ntest, nseg);
+    }
 }
 
 // One thermal packet of leaf triangle L: expected recoil at the point, and
@@ -257,7 +327,7 @@ __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
         __syncwarp();
         if (k0 < k1) {
             float3 e = f3(0.0f, 0.0f, 1.0f);
-            if (MODE == 0) {
+            if (MODE != 1) {
                 const double* sp = p.sun + 3 * (size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s);
                 e = f3((float)sp[0], (float)sp[1], (float)sp[2]);
             }
@@ -269,7 +339,7 @@ __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
             const float* rho = p.rho + (size_t)dl * p.G * 2;
             const float tmin = (float)(1e-6 * dz.R);
             const uint32_t sg = (uint32_t)(p.sun_base + s);
-            const uint32_t dg = (uint32_t)(p.design_base + dl) | (MODE == 0 ? 0x80000000u : 0x40000000u);
+            const uint32_t dg = (uint32_t)(p.design_base + dl) | (MODE != 1 ? 0x80000000u : 0x40000000u);
             const int32_t* __restrict__ ex = p.ex + base;
             const int32_t* __restrict__ map = p.map + base;
             const int T = dz.T;
@@ -309,8 +379,11 @@ __global__ void __launch_bounds__(128, MINB) area_kernel(const AreaParams p) {
                         const int32_t nf = ex_hi - ex_lo;
                         const int L = __ldg(map + f);
                         if (MODE == 0)
-                            sample_sun<W>(dz, L, f, jj, nf, e, rset, com, rho, tmin, sg, dg, key0, key1, p.P, p.err, y, nvis,
-                                          ntest, nseg);
+                            sample_sun<W, false>(dz, L, f, jj, nf, e, rset, com, rho, tmin, sg, dg, key0, key1, p.P, p.err,
+                                                 y, nvis, ntest, nseg);
+                        else if (MODE == 2)
+                            sample_sun<W, true>(dz, L, f, jj, nf, e, rset, com, rho, tmin, sg, dg, key0, key1, p.P, p.err,
+                                                y, nvis, ntest, nseg);
                         else
                             sample_thermal<W>(dz, L, f, jj, nf, com, rho, emit, tmin, dg, key0, key1, p.P, p.err, y,
                                               nvis, ntest, nseg);
@@ -381,6 +454,7 @@ static void area_launch_m(const AreaParams& p, int variant, int grid, cudaStream
 template <int W>
 static void area_launch_w(const AreaParams& p, int variant, int grid, cudaStream_t st) {
     if (p.mode == 1) area_launch_m<W, 1>(p, variant, grid, st);
+    else if (p.mode == 2) area_launch_m<W, 2>(p, variant, grid, st);
     else area_launch_m<W, 0>(p, variant, grid, st);
 }
 

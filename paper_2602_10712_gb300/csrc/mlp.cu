@@ -124,7 +124,11 @@ struct MlpFwdSmem {
 
 // silu(z) = z sigmoid(z) = h + h tanh(h), h = z/2: one hardware tanh
 // (tanh.approx.f32, ~2^-11 relative) per activation instead of an exp and a
-// reciprocal; the result is rounded to BF16 (2^-9) right after.
+// reciprocal; the result is rounded to BF16 (2^-9) right after.  The error
+// is about 2^-11 |h| in absolute terms: below the BF16 rounding where
+// silu(z) is O(z), but for z below about -4 (silu(z) -> 0 while h tanh(h)
+// cancels h) it is large relative to the value itself.  The inference
+// kernel takes it for speed; the training passes use silu_precise.
 __device__ __forceinline__ float tanh_approx(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -134,6 +138,11 @@ __device__ __forceinline__ float silu_f(float z) {
     const float h = 0.5f * z;
     return fmaf(h, tanh_approx(h), h);
 }
+// z / (1 + exp(-z)) with CUDA's accurate expf and an IEEE division: a few
+// ulps relative for every z (no cancellation); the training forward and the
+// input gradient's forward use it, so the activations they round to BF16
+// and back-propagate through are those of the definition.
+__device__ __forceinline__ float silu_precise(float z) { return z / (1.0f + expf(-z)); }
 
 // Two floats -> BF16 (round to nearest even), a in the low half.
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -403,7 +412,7 @@ __global__ void bias_silu_kernel(float* Z, const float* b, float* H, int64_t row
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const float z = Z[e] + b[e % cols];
         Z[e] = z;
-        if (H) H[e] = silu_f(z);
+        if (H) H[e] = silu_precise(z);
     }
 }
 
@@ -423,7 +432,7 @@ __global__ void l1_kernel(const float* Y, const float* T, float* dY, float* loss
 __global__ void dsilu_kernel(const float* dH, const float* Z, float* dZ, int64_t n) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const float z = Z[e];
-        const float sg = 1.0f / (1.0f + __expf(-z));
+        const float sg = 1.0f / (1.0f + expf(-z));
         dZ[e] = dH[e] * sg * (1.0f + z * (1.0f - sg));
     }
 }

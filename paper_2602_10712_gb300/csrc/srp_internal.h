@@ -112,7 +112,8 @@ struct TraceParams {
 
 // Parameters of the area-sampling estimator (area.cu).
 struct AreaParams {
-    int32_t mode;             // 0: sun light with next-event shadow rays; 1: thermal emitters
+    int32_t mode;             // 0: sun light with next-event shadow rays; 1: thermal emitters;
+                              // 2: sun light plus one gathered Lambertian interreflection
     int32_t D, S, G, sun_per_design;
     uint64_t seed;
     float P, density;

@@ -117,8 +117,7 @@ def test_training_gradient_parity(srp):
     both sides.  Element by element, per parameter block: |g - g_or| <=
     1e-2 rms(g_or) for every element and 1e-3 rms(g_or) in RMS.  What
     remains is FP32 vs FP64 accumulation and one-ulp BF16 flips where the
-    two sides' values straddle a rounding boundary (the kernel's SiLU uses
-    the hardware tanh)."""
+    two sides' values straddle a rounding boundary."""
     ctx = srp.Context(0)
     p = omlp.init_params(seed=11)
     p = [(W, np.random.default_rng(40 + l).normal(size=b.shape) * 0.1) for l, (W, b) in enumerate(p)]

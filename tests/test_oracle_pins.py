@@ -309,6 +309,85 @@ def test_area_estimator_matches_ray_grid():
     assert ok, r
 
 
+def _gauss_square(half, n):
+    """Gauss-Legendre nodes and weights over [-half, half]^2."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    return np.meshgrid(half * x, half * x, indexing="ij"), np.outer(half * w, half * w)
+
+
+def test_area_interreflection_closed_form():
+    """One Lambertian interreflection (K = 2): a sunlit diffuse square A
+    (side 2, z = 0, rho_d = 0.5) and a square B (side 0.5, rho_s = 0.3,
+    rho_d = 0.4) one metre above its centre, sun 70 degrees off the normal
+    so that B's shadow falls beside A.  A reflects radiance
+    L = rho_d P cos(70)/pi toward B's underside (normal -z); a beam arriving
+    there along d at cos_B = d.z pushes it by the per-plate law
+    (1 - rs) d - (2 rs cos_B + 2/3 rd)(-z), whose z part is
+    (1 + rs) cos_B + 2/3 rd.  With cos_A = cos_B = h/r and
+    dOmega = cos_A dA_A / r^2 the force is L [(1 + rs) I3 + 2/3 rd I2] along
+    +z, I_k = int_B int_A h^k / r^(k+2) dA_A dA_B (Gauss-Legendre), and the
+    x, y parts cancel by symmetry.  B's underside is not sunlit and A's lit
+    side sees only B's dark underside, so nothing else is gathered:
+    F(K=2) - F(K=1) on the same samples (the direct part is identical) is
+    that term, within 3 sigma of the sampled directions."""
+    va, ta = _plate((2.0, 2.0))
+    vb, tb = _plate((0.5, 0.5), z=1.0)
+    v = np.concatenate([va, vb]).astype(np.float32)
+    t = np.concatenate([ta, tb + 4]).astype(np.int32)
+    g = np.array([0, 0, 1, 1], np.int32)
+    rho = np.array([[0.0, 0.5], [0.3, 0.4]])
+    th = np.deg2rad(70.0)
+    e = np.array([np.sin(th), 0.0, np.cos(th)])
+    f1, _ = oracle.force_area(v, t, g, rho, e, np.zeros(3), density=1.0e5, seed=4)
+    f2, s2 = oracle.force_area(v, t, g, rho, e, np.zeros(3), density=1.0e5, seed=4, K=2)
+    (ax, ay), wa = _gauss_square(1.0, 24)
+    (bx, by), wb = _gauss_square(0.25, 12)
+    r2 = (ax.ravel()[:, None] - bx.ravel()[None, :]) ** 2 + (ay.ravel()[:, None] - by.ravel()[None, :]) ** 2 + 1.0
+    I3 = float(wa.ravel() @ (r2 ** -2.5) @ wb.ravel())
+    I2 = float(wa.ravel() @ (r2 ** -2.0) @ wb.ravel())
+    L = 0.5 * np.cos(th) / np.pi
+    want = np.array([0.0, 0.0, L * ((1.0 + 0.3) * I3 + (2.0 / 3.0) * 0.4 * I2)])
+    got = f2[0, :3] - f1[0, :3]
+    assert np.all(np.abs(got - want) <= 3.0 * s2[0, :3] + 1e-12), (got, want, s2[0, :3])
+    assert s2[0, 2] < 0.02 * want[2]   # the pin resolves the term to about 2 %
+
+
+def test_area_interreflection_convex_body_adds_nothing():
+    """A closed convex box sees no other lit surface from outside, and from
+    inside every gathered point is shadowed by the box itself: K = 2 gives
+    the K = 1 estimate bit for bit."""
+    bv, bt = W.axis_box((0.1, -0.2, 0.3), (0.5, 0.7, 1.1), 0)
+    verts = bv.astype(np.float32); tris = bt.astype(np.int32)
+    group = np.arange(12, dtype=np.int32) // 2
+    rho = W.random_reflectances(6, seed=4)
+    e = np.array([0.3, -0.5, 0.8]); e /= np.linalg.norm(e)
+    f1, s1 = oracle.force_area(verts, tris, group, rho, e, np.zeros(3), density=800.0, seed=3)
+    f2, s2 = oracle.force_area(verts, tris, group, rho, e, np.zeros(3), density=800.0, seed=3, K=2)
+    assert np.array_equal(f1, f2) and np.array_equal(s1, s2)
+
+
+def test_area_interreflection_matches_two_bounce_grid():
+    """With no specular reflection (rho_s = 0) the grid estimator at K = 2
+    (primary hit, one sampled Lambertian bounce, closed form at the second
+    hit) and the area estimator with one gathered interreflection estimate
+    the same truncated integral (light reflected once, by reciprocity of the
+    transport between the two surfaces): box-wing with both panels hinged
+    toward the bus, 3 sigma.  Their difference from K = 1 is resolved."""
+    m = W.box_wing()
+    v = oracle.instantiate(m.verts, m.vhinge, m.hinges, np.array([0.9, -0.8]))
+    rho = W.random_reflectances(64, seed=6)
+    rho[:, 0] = 0.0
+    rho[:, 1] = 0.3 + rho[:, 1]
+    e = np.array([0.2, 0.4, 0.9]); e /= np.linalg.norm(e)
+    com = np.zeros(3)
+    fa, sa = oracle.force_area(v, m.tris, m.group, rho, e, com, density=6000.0, seed=5, K=2)
+    fg, sgg = oracle.force(v, m.tris, m.group, rho, e, com, nx=512, K=2, seed=5)
+    ok, r = _stat_ok(fa[0], fg[0], sa[0], sgg[0])
+    assert ok, r
+    f1, _ = oracle.force_area(v, m.tris, m.group, rho, e, com, density=6000.0, seed=5)
+    assert np.linalg.norm(fa[0, :3] - f1[0, :3]) > 6.0 * np.linalg.norm(sa[0, :3])
+
+
 # ---------------------------------------------------------------- thermal emitters (Sec. 5.9)
 C_LIGHT = 299792458.0
 
