@@ -931,7 +931,10 @@ def run_profile_case(case):
     trace -- srp_force on 16 of the 4096 suns x 2048^2 rays, K <= 3;
     trace_k1 -- the same at K = 1 (primary rays only);
     area  -- srp_force_area on the same 16 suns, ~2048^2 samples each;
-    mlp   -- proxy inference on 262,144 queries."""
+    mlp   -- proxy inference on 262,144 queries;
+    train -- three proxy training steps of 8,192 samples;
+    grad  -- srp_force_grad on the box-wing, 64 suns x 1024^2 rays, K = 1;
+    probe -- the L2 read probe over 64 MiB (3 launches of one pass)."""
     import torch
 
     import paper_2602_10712_gb300 as srp
@@ -963,6 +966,27 @@ def run_profile_case(case):
         x = torch.randn((1 << 18, 19), device=dev)
         for _ in range(3):
             net.infer(x)
+    elif case == "train":
+        net = srp.MLP(ctx, seed=1)
+        x = torch.randn((8192, 19), device=dev)
+        t = torch.randn((8192, 6), device=dev)
+        for _ in range(3):
+            net.train_step(x, t, 1e-3, want_loss=False)
+    elif case == "grad":
+        m1 = W.box_wing()
+        v1 = srp.srp_design_instantiate(m1.verts, m1.vhinge, m1.hinges, np.array([0.3, -0.5]))
+        b1 = srp.srp_build_bvh(ctx, v1, m1.tris, m1.group, 4)
+        rho1 = torch.from_numpy(W.random_reflectances(64, seed=0)).to(dev)
+        sun1 = torch.from_numpy(W.fibonacci_directions(64)).to(dev)
+        com1 = torch.zeros(3, dtype=torch.float64, device=dev)
+        up = torch.ones((64, 6), dtype=torch.float64, device=dev)
+        th1 = torch.from_numpy(m1.vhinge[m1.tris[:, 0]].astype(np.int32)).to(dev)
+        ha = torch.from_numpy(m1.hinges).to(dev)
+        for _ in range(3):
+            srp.srp_force_grad(ctx, b1, rho1, sun1, com1, up, th1, ha, rays_x=1024, max_bounces=1)
+    elif case == "probe":
+        # the L2 read probe over 64 MiB (one pass per launch, 3 launches)
+        srp.srp_probe_read_bandwidth(ctx, 64 << 20, passes=1, reps=2)
     torch.cuda.synchronize()
     print(f"profile case {case}: ok")
 
@@ -977,7 +1001,7 @@ def main():
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
-    ap.add_argument("--profile", choices=["trace", "trace_k1", "area", "mlp"], default=None,
+    ap.add_argument("--profile", choices=["trace", "trace_k1", "area", "mlp", "train", "grad", "probe"], default=None,
                     help="run a small ncu capture case and exit")
     args = ap.parse_args()
     if args.profile:

@@ -300,14 +300,12 @@ int srp_build_bvh(srp_ctx* c, const float* verts, int V, const int32_t* tris, co
                      cz = e1[0] * e2[1] - e1[1] * e2[0];
         h->area += 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
     }
-    std::vector<float> dnodes;
-    device_nodes(b.node_data.data(), b.n_nodes, width, &dnodes);
-    const size_t tb = tri.size() * sizeof(float), nb = dnodes.size() * sizeof(float);
+    const size_t tb = tri.size() * sizeof(float), nb = b.node_data.size() * sizeof(float);
     h->bytes = (int64_t)(tb + nb);
     cudaError_t e = cudaMalloc(&h->d_tri, tb);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_nodes, nb);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_tri, tri.data(), tb, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(h->d_nodes, dnodes.data(), nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_nodes, b.node_data.data(), nb, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (h->d_tri) cudaFree(h->d_tri);
         if (h->d_nodes) cudaFree(h->d_nodes);
@@ -364,9 +362,7 @@ int srp_bvh_set_nodes(srp_ctx* c, srp_bvh* h, const float* node_data, int64_t n_
     }
     CU(cudaSetDevice(h->device), "cudaSetDevice");
     CU(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    std::vector<float> dnodes;
-    device_nodes(node_data, h->n_nodes, W, &dnodes);
-    CU(cudaMemcpy(h->d_nodes, dnodes.data(), sizeof(float) * dnodes.size(), cudaMemcpyHostToDevice), "H2D nodes");
+    CU(cudaMemcpy(h->d_nodes, node_data, sizeof(float) * n_floats, cudaMemcpyHostToDevice), "H2D nodes");
     c->last_tab.clear();  // force a fresh design-table upload
     return SRP_OK;
 }

@@ -251,77 +251,4 @@ int build_wide_bvh(const float* verts, int V, const int32_t* tris, int T, int wi
     return SRP_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Quantised device nodes: per node and axis an origin p (the smallest padded
-// child lo, kept in FP32 so the child that defines it is tested exactly as
-// with float bounds) and the smallest power-of-two step 2^e that spans the
-// node's children in 254 steps; child bounds become floor / ceil multiples
-// of the step (outward).  Where the outward rounding left less slack than
-// the float padding (a bound on the grid), one more step is added, so the
-// extra rounding of p + q 2^e in the kernel stays covered.
-// ---------------------------------------------------------------------------
-void device_nodes(const float* nd, int n_nodes, int W, std::vector<float>* out) {
-    const int nf = 8 * W;                      // floats per float-layout node
-    const int nq = 4 * node_f4_rt(W);          // floats per device node
-    out->assign((size_t)n_nodes * nq, 0.0f);
-    if (!SRP_QNODES) {
-        std::memcpy(out->data(), nd, sizeof(float) * (size_t)n_nodes * nf);
-        return;
-    }
-    const int Q = W / 4;
-    for (int n = 0; n < n_nodes; ++n) {
-        const float* src = nd + (size_t)n * nf;
-        float* dst = out->data() + (size_t)n * nq;
-        uint32_t* words = reinterpret_cast<uint32_t*>(dst + 4);
-        int32_t* child = reinterpret_cast<int32_t*>(dst + 4 + 4 * ((6 * Q + 3) / 4));
-        bool valid[8];
-        bool any = false;
-        for (int c = 0; c < W; ++c) {
-            valid[c] = src[c] <= src[W + c];
-            any = any || valid[c];
-            child[c] = valid[c] ? reinterpret_cast<const int32_t*>(src + 6 * W)[c] : 0;
-        }
-        uint32_t ebits = 0;
-        for (int a = 0; a < 3; ++a) {
-            float p = 0.0f;
-            int e = 0;
-            if (any) {
-                float lo_min = INFINITY, hi_max = -INFINITY;
-                for (int c = 0; c < W; ++c)
-                    if (valid[c]) {
-                        lo_min = std::min(lo_min, src[(2 * a) * W + c]);
-                        hi_max = std::max(hi_max, src[(2 * a + 1) * W + c]);
-                    }
-                p = lo_min;
-                const double range = std::max((double)hi_max - (double)p, 1e-30);
-                e = (int)std::ceil(std::log2(range / 254.0));
-                while (std::ldexp(254.0, e) < range) ++e;
-                while (e > -126 && std::ldexp(254.0, e - 1) >= range) --e;
-                e = std::max(-126, std::min(127, e));
-            }
-            ebits |= (uint32_t)(e + 128) << (8 * a);
-            dst[a] = p;
-            const double step = std::ldexp(1.0, e);
-            for (int c = 0; c < W; ++c) {
-                uint32_t qlo = 255, qhi = 0;
-                if (valid[c]) {
-                    const double lo = src[(2 * a) * W + c], hi = src[(2 * a + 1) * W + c];
-                    const double slack = 1e-6 * (std::fabs((double)p) + std::fabs(lo) + std::fabs(hi) +
-                                                 254.0 * step);
-                    double xl = std::floor((lo - p) / step);
-                    if (xl > 0.0 && lo - ((double)p + xl * step) < slack) xl -= 1.0;
-                    double xh = std::ceil((hi - p) / step);
-                    if ((double)p + xh * step - hi < slack) xh += 1.0;
-                    qlo = (uint32_t)std::max(0.0, std::min(255.0, xl));
-                    qhi = (uint32_t)std::max(0.0, std::min(255.0, xh));
-                }
-                const int wlo = (2 * a) * Q + c / 4, whi = (2 * a + 1) * Q + c / 4, sh = 8 * (c % 4);
-                words[wlo] |= qlo << sh;
-                words[whi] |= qhi << sh;
-            }
-        }
-        std::memcpy(&dst[3], &ebits, 4);
-    }
-}
-
 }  // namespace srp

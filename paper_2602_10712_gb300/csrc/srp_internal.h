@@ -13,19 +13,6 @@
 //   child >= 0: inner node index; child < 0: leaf, ~child = first << 3 |
 //   (count - 1), count in 1..8 triangles starting at tri[first].  Empty
 //   slots have lo = +inf, hi = -inf and never hit.
-//   This float layout is what the builder produces and what
-//   srp_build_bvh_host / srp_bvh_set_nodes exchange.  On the device the
-//   nodes are stored quantised (SRP_QNODES = 1):
-//     W = 4: 64 B  = float4 (p.x, p.y, p.z, bits(e)) -- per-node origin p (the
-//                    smallest padded child lo per axis) and per-axis scale
-//                    2^e (e + 128 in bytes 0..2 of the 4th word);
-//                    6 words of 8-bit child bounds, byte c = child c:
-//                    qlo_x, qhi_x, qlo_y, qhi_y, qlo_z, qhi_z, 2 words pad;
-//                    child (int4)
-//     W = 8: 96 B  = the header, 12 words (each bound array takes 2 words,
-//                    children 0-3 then 4-7), child as 2 int4
-//   with p + qlo 2^e <= lo and p + qhi 2^e >= hi (rounded outward; the FP32
-//   padding of the float bounds is kept), empty slots qlo = 255, qhi = 0.
 #pragma once
 #include <stdint.h>
 #include <vector_types.h>
@@ -35,10 +22,6 @@
 #include "../../include/srp.h"
 
 namespace srp {
-
-#ifndef SRP_QNODES
-#define SRP_QNODES 1
-#endif
 
 constexpr int kMaxGroups = 64;
 constexpr int kMaxBounces = 3;
@@ -64,18 +47,6 @@ struct BuiltBVH {                  // host result of the builder
 // Bounds are padded outward so the FP32 slab test is conservative.
 int build_wide_bvh(const float* verts, int V, const int32_t* tris, int T, int width,
                    BuiltBVH* out, std::string* err);
-
-// float4 per device node (float or quantised layout)
-template <int W>
-__host__ __device__ constexpr int node_f4() {
-    return SRP_QNODES ? 1 + (6 * (W / 4) + 3) / 4 + W / 4 : 2 * W;
-}
-inline int node_f4_rt(int W) { return W == 8 ? node_f4<8>() : node_f4<4>(); }
-
-// Device layout of n_nodes float-layout nodes (width W): the quantised
-// layout when SRP_QNODES, else a copy.  out receives node_f4_rt(W) * 4
-// floats per node.
-void device_nodes(const float* node_data, int n_nodes, int W, std::vector<float>* out);
 
 // Per-design parameters passed to the trace kernel by value.
 struct DesignDev {

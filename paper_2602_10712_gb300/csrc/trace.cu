@@ -391,24 +391,27 @@ constexpr int kTopBoxes = 64;   // box slots of the span pre-pass
 // slot whose remaining digits are 0 carries it, the others are empty).
 template <int W>
 __device__ __forceinline__ float4 top_rect(const DesignDev& dz, const ItemConst& ic, int bi) {
+    const float* nd0 = reinterpret_cast<const float*>(dz.nodes);
+    constexpr int NFL = W == 4 ? 32 : 64;   // floats per node
     constexpr int levels = W == 4 ? 3 : 2;
     int digit[3];
     if (W == 4) { digit[0] = bi >> 4; digit[1] = (bi >> 2) & 3; digit[2] = bi & 3; }
     else { digit[0] = bi >> 3; digit[1] = bi & 7; digit[2] = 0; }
-    const float4* nd = dz.nodes;
+    const float* nd = nd0;
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     bool ok = false;
     for (int lv = 0; lv < levels; ++lv) {
         const int c = digit[lv];
-        int code = 0;
-        if (!child_box<W>(nd, c, lo, hi, code)) { ok = false; break; }
+        for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd + 2 * W * a + c); hi[a] = __ldg(nd + 2 * W * a + W + c); }
+        if (!(lo[0] <= hi[0])) { ok = false; break; }
         ok = true;
+        const int code = __float_as_int(__ldg(nd + 6 * W + c));
         if (lv == levels - 1) break;
         if (code < 0) {   // a leaf: only the slot with the remaining digits 0 keeps it
             for (int l2 = lv + 1; l2 < levels; ++l2) ok = ok && digit[l2] == 0;
             break;
         }
-        nd = dz.nodes + (size_t)code * node_f4<W>();
+        nd = nd0 + (size_t)code * NFL;
     }
     float4 rc = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
     if (ok) {

@@ -104,199 +104,55 @@ __device__ __forceinline__ float hit_triangle(const RaySetup& r, float3 p0, floa
 }
 
 // ---------------------------------------------------------------------------
-// Traversal stack: the top kStackRegs entries live in registers (a shift
-// register, top at reg[0]); older entries spill to a per-thread array in
-// local memory only when the register part is full.  Pops take the register
-// part first, so most pushes and pops of a traversal never touch memory
-// (a pop from local memory is an L1 round trip on the critical path of the
-// next node fetch).  LIFO order is exact: an entry only spills when it is
-// the oldest of the register part, i.e. newer than every spilled entry.
-// ---------------------------------------------------------------------------
-#ifndef SRP_STACK_REGS
-#define SRP_STACK_REGS 4
-#endif
-constexpr int kStackRegs = SRP_STACK_REGS;
-
-template <typename E>
-struct TravStack {
-    E reg[kStackRegs > 0 ? kStackRegs : 1];
-    E mem[kStackSize];
-    int nreg = 0;   // entries in reg
-    int sp = 0;     // entries in mem
-    __device__ __forceinline__ bool empty() const { return nreg == 0 && sp == 0; }
-    // false on overflow (nothing pushed)
-    __device__ __forceinline__ bool push(E e) {
-        if (kStackRegs == 0) {
-            if (sp >= kStackSize) return false;
-            mem[sp++] = e;
-            return true;
-        }
-        if (nreg == kStackRegs) {
-            if (sp >= kStackSize) return false;
-            mem[sp++] = reg[kStackRegs - 1];
-        } else {
-            ++nreg;
-        }
-#pragma unroll
-        for (int j = kStackRegs - 1; j > 0; --j) reg[j] = reg[j - 1];
-        reg[0] = e;
-        return true;
-    }
-    // requires !empty()
-    __device__ __forceinline__ E pop() {
-        if (kStackRegs > 0 && nreg > 0) {
-            const E e = reg[0];
-#pragma unroll
-            for (int j = 0; j + 1 < kStackRegs; ++j) reg[j] = reg[j + 1];
-            --nreg;
-            return e;
-        }
-        return mem[--sp];
-    }
-};
-
-// ---------------------------------------------------------------------------
-// Slab test of the W children of one node: tn[c] = entry parameter, hit[c]
-// = the ray's [tmin, tcap] interval meets child c's box, child[c] = its code
-// (>= 0 inner node, < 0 leaf).  Two node formats (see srp_internal.h):
-//   float nodes   the padded FP32 child bounds;
-//   quantised     a per-node FP32 origin p and power-of-two scale 2^e per
-//                 axis, child bounds as 8-bit multiples of the scale
-//                 (rounded outward), so a BVH4 node is 64 B instead of 128 B;
-//                 the entry/exit parameters are (p - o)/d + q 2^e / d, with
-//                 (p - o)/d computed once per node and 2^e/d exact.
-// Near and far planes are chosen by the sign of 1/d per axis.
-// ---------------------------------------------------------------------------
-template <int W>
-__device__ __forceinline__ void node_slab(const float4* nd, const RaySetup& r, float tmin, float tcap, float tn[W],
-                                          bool hit[W], int child[W]) {
-    constexpr int Q = W / 4;
-#if SRP_QNODES
-    const float4 hd = __ldg(nd);
-    const uint32_t eb = __float_as_uint(hd.w);
-    // 2^e as an FP32 from its stored byte e + 128 (biased exponent e + 127)
-    const float scx = __uint_as_float(((eb & 0xffu) - 1u) << 23) * r.inv.x;
-    const float scy = __uint_as_float((((eb >> 8) & 0xffu) - 1u) << 23) * r.inv.y;
-    const float scz = __uint_as_float((((eb >> 16) & 0xffu) - 1u) << 23) * r.inv.z;
-    const float bx = fmaf(hd.x, r.inv.x, -r.oinv.x);
-    const float by = fmaf(hd.y, r.inv.y, -r.oinv.y);
-    const float bz = fmaf(hd.z, r.inv.z, -r.oinv.z);
-    uint32_t wq[6 * Q];
-#pragma unroll
-    for (int h = 0; h < (6 * Q + 3) / 4; ++h) {
-        const uint4 u = __ldg(reinterpret_cast<const uint4*>(nd + 1) + h);
-        if (4 * h + 0 < 6 * Q) wq[4 * h + 0] = u.x;
-        if (4 * h + 1 < 6 * Q) wq[4 * h + 1] = u.y;
-        if (4 * h + 2 < 6 * Q) wq[4 * h + 2] = u.z;
-        if (4 * h + 3 < 6 * Q) wq[4 * h + 3] = u.w;
-    }
-    const bool sx = r.inv.x < 0.0f, sy = r.inv.y < 0.0f, sz = r.inv.z < 0.0f;
-#pragma unroll
-    for (int h = 0; h < Q; ++h) {
-        const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 1 + (6 * Q + 3) / 4) + h);
-        const int ch_[4] = {ch.x, ch.y, ch.z, ch.w};
-        const uint32_t nxw = sx ? wq[1 * Q + h] : wq[0 * Q + h], fxw = sx ? wq[0 * Q + h] : wq[1 * Q + h];
-        const uint32_t nyw = sy ? wq[3 * Q + h] : wq[2 * Q + h], fyw = sy ? wq[2 * Q + h] : wq[3 * Q + h];
-        const uint32_t nzw = sz ? wq[5 * Q + h] : wq[4 * Q + h], fzw = sz ? wq[4 * Q + h] : wq[5 * Q + h];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            // byte q of a word as an exact float: 2^23 + byte, minus 2^23
-            const uint32_t sel = 0x7540u + (uint32_t)q;
-            const float qnx = __uint_as_float(__byte_perm(nxw, 0x4B000000u, sel)) - 8388608.0f;
-            const float qfx = __uint_as_float(__byte_perm(fxw, 0x4B000000u, sel)) - 8388608.0f;
-            const float qny = __uint_as_float(__byte_perm(nyw, 0x4B000000u, sel)) - 8388608.0f;
-            const float qfy = __uint_as_float(__byte_perm(fyw, 0x4B000000u, sel)) - 8388608.0f;
-            const float qnz = __uint_as_float(__byte_perm(nzw, 0x4B000000u, sel)) - 8388608.0f;
-            const float qfz = __uint_as_float(__byte_perm(fzw, 0x4B000000u, sel)) - 8388608.0f;
-            const float n0 = fmaf(qnx, scx, bx), f0 = fmaf(qfx, scx, bx);
-            const float n1 = fmaf(qny, scy, by), f1 = fmaf(qfy, scy, by);
-            const float n2 = fmaf(qnz, scz, bz), f2 = fmaf(qfz, scz, bz);
-            const float tnear = fmaxf(fmaxf(n0, n1), fmaxf(n2, tmin));
-            const float tfar = fminf(fminf(f0, f1), fminf(f2, tcap));
-            tn[4 * h + q] = tnear;
-            hit[4 * h + q] = tnear <= tfar;
-            child[4 * h + q] = ch_[q];
-        }
-    }
-#else
-    // near/far slab planes chosen by load address (per-ray float4 offsets):
-    // lo_a at float4 (2a)*(W/4) + h, hi_a at (2a+1)*(W/4) + h
-    const int nxo = r.inv.x < 0.0f ? Q : 0, nyo = r.inv.y < 0.0f ? Q : 0, nzo = r.inv.z < 0.0f ? Q : 0;
-#pragma unroll
-    for (int h = 0; h < Q; ++h) {
-        const float4 ax = __ldg(nd + nxo + h), bx = __ldg(nd + (Q - nxo) + h);
-        const float4 ay = __ldg(nd + 2 * Q + nyo + h), by = __ldg(nd + 2 * Q + (Q - nyo) + h);
-        const float4 az = __ldg(nd + 4 * Q + nzo + h), bz = __ldg(nd + 4 * Q + (Q - nzo) + h);
-        const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * Q) + h);
-        const float ax_[4] = {ax.x, ax.y, ax.z, ax.w}, bx_[4] = {bx.x, bx.y, bx.z, bx.w};
-        const float ay_[4] = {ay.x, ay.y, ay.z, ay.w}, by_[4] = {by.x, by.y, by.z, by.w};
-        const float az_[4] = {az.x, az.y, az.z, az.w}, bz_[4] = {bz.x, bz.y, bz.z, bz.w};
-        const int ch_[4] = {ch.x, ch.y, ch.z, ch.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float n0 = fmaf(ax_[q], r.inv.x, -r.oinv.x), f0 = fmaf(bx_[q], r.inv.x, -r.oinv.x);
-            const float n1 = fmaf(ay_[q], r.inv.y, -r.oinv.y), f1 = fmaf(by_[q], r.inv.y, -r.oinv.y);
-            const float n2 = fmaf(az_[q], r.inv.z, -r.oinv.z), f2 = fmaf(bz_[q], r.inv.z, -r.oinv.z);
-            const float tnear = fmaxf(fmaxf(n0, n1), fmaxf(n2, tmin));
-            const float tfar = fminf(fminf(f0, f1), fminf(f2, tcap));
-            tn[4 * h + q] = tnear;
-            hit[4 * h + q] = tnear <= tfar;
-            child[4 * h + q] = ch_[q];
-        }
-    }
-#endif
-}
-
-// Box and code of child c of a node (either layout), for code that inspects
-// the tree rather than tracing a ray through it.
-template <int W>
-__device__ __forceinline__ bool child_box(const float4* nd4, int c, float lo[3], float hi[3], int& code) {
-    const float* nd = reinterpret_cast<const float*>(nd4);
-#if SRP_QNODES
-    constexpr int Q = W / 4;
-    const uint32_t eb = __float_as_uint(__ldg(nd + 3));
-    const uint32_t* words = reinterpret_cast<const uint32_t*>(nd + 4);
-    bool ok = true;
-    for (int a = 0; a < 3; ++a) {
-        const float step = __uint_as_float((((eb >> (8 * a)) & 0xffu) - 1u) << 23);
-        const uint32_t ql = (__ldg(words + (2 * a) * Q + c / 4) >> (8 * (c % 4))) & 0xffu;
-        const uint32_t qh = (__ldg(words + (2 * a + 1) * Q + c / 4) >> (8 * (c % 4))) & 0xffu;
-        const float p = __ldg(nd + a);
-        lo[a] = fmaf((float)ql, step, p);
-        hi[a] = fmaf((float)qh, step, p);
-        ok = ok && ql <= qh;
-    }
-    code = __float_as_int(__ldg(nd + 4 + 4 * ((6 * Q + 3) / 4) + c));
-    return ok;
-#else
-    for (int a = 0; a < 3; ++a) { lo[a] = __ldg(nd + 2 * W * a + c); hi[a] = __ldg(nd + 2 * W * a + W + c); }
-    code = __float_as_int(__ldg(nd + 6 * W + c));
-    return lo[0] <= hi[0];
-#endif
-}
-
-// ---------------------------------------------------------------------------
 // Closest hit through a W-wide BVH.  Returns the leaf-order triangle index
 // (or -1) and sets tb.  Ties on t go to the smaller original index.
 // ---------------------------------------------------------------------------
 template <int W>
 __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& r, float tmin, int skip,
                                            float& tb, int* err, uint32_t& nvis, uint32_t& ntest) {
+    constexpr int NF4 = W == 4 ? 8 : 16;  // float4 per node
     const float4* __restrict__ nodes = dz.nodes;
     const float4* __restrict__ tri = dz.tri;
-    TravStack<int2> st;
+    int2 stack[kStackSize];
+    int sp = 0;
     int best = -1;
     uint32_t best_id = 0xffffffffu;
     tb = INFINITY;
     int ni = 0;
     int visits = 0;
+    // near/far slab planes chosen by load address (per-ray float4 offsets):
+    // lo_a at float4 (2a)*(W/4) + h, hi_a at (2a+1)*(W/4) + h
+    constexpr int Q = W / 4;
+    const int nxo = r.inv.x < 0.0f ? Q : 0, nyo = r.inv.y < 0.0f ? Q : 0, nzo = r.inv.z < 0.0f ? Q : 0;
     while (true) {
         if (++visits > kVisitCap) { atomicOr(err, kErrVisitCap); return -1; }
         ++nvis;
+        const float4* nd = nodes + (size_t)ni * NF4;
         float tn[W];
         bool hit[W];
         int child[W];
-        node_slab<W>(nodes + (size_t)ni * node_f4<W>(), r, tmin, tb, tn, hit, child);
+#pragma unroll
+        for (int h = 0; h < Q; ++h) {
+            const float4 ax = __ldg(nd + nxo + h), bx = __ldg(nd + (Q - nxo) + h);
+            const float4 ay = __ldg(nd + 2 * Q + nyo + h), by = __ldg(nd + 2 * Q + (Q - nyo) + h);
+            const float4 az = __ldg(nd + 4 * Q + nzo + h), bz = __ldg(nd + 4 * Q + (Q - nzo) + h);
+            const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * Q) + h);
+            const float ax_[4] = {ax.x, ax.y, ax.z, ax.w}, bx_[4] = {bx.x, bx.y, bx.z, bx.w};
+            const float ay_[4] = {ay.x, ay.y, ay.z, ay.w}, by_[4] = {by.x, by.y, by.z, by.w};
+            const float az_[4] = {az.x, az.y, az.z, az.w}, bz_[4] = {bz.x, bz.y, bz.z, bz.w};
+            const int ch_[4] = {ch.x, ch.y, ch.z, ch.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float n0 = fmaf(ax_[q], r.inv.x, -r.oinv.x), f0 = fmaf(bx_[q], r.inv.x, -r.oinv.x);
+                const float n1 = fmaf(ay_[q], r.inv.y, -r.oinv.y), f1 = fmaf(by_[q], r.inv.y, -r.oinv.y);
+                const float n2 = fmaf(az_[q], r.inv.z, -r.oinv.z), f2 = fmaf(bz_[q], r.inv.z, -r.oinv.z);
+                const float tnear = fmaxf(fmaxf(n0, n1), fmaxf(n2, tmin));
+                const float tfar = fminf(fminf(f0, f1), fminf(f2, tb));
+                tn[4 * h + q] = tnear;
+                hit[4 * h + q] = tnear <= tfar;
+                child[4 * h + q] = ch_[q];
+            }
+        }
         // leaves first: they may shrink tb before inner children are queued
 #pragma unroll
         for (int c = 0; c < W; ++c) {
@@ -324,21 +180,21 @@ __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& 
         for (int c = 0; c < W; ++c) {
             if (hit[c] && child[c] >= 0 && tn[c] <= tb) {
                 if (tn[c] < tnext) {
-                    if (next >= 0 && !st.push(make_int2(next, __float_as_int(tnext)))) {
-                        atomicOr(err, kErrStackOverflow);
-                        return -1;
+                    if (next >= 0) {
+                        if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
+                        stack[sp++] = make_int2(next, __float_as_int(tnext));
                     }
                     next = child[c]; tnext = tn[c];
-                } else if (!st.push(make_int2(child[c], __float_as_int(tn[c])))) {
-                    atomicOr(err, kErrStackOverflow);
-                    return -1;
+                } else {
+                    if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
+                    stack[sp++] = make_int2(child[c], __float_as_int(tn[c]));
                 }
             }
         }
         if (next >= 0) { ni = next; continue; }
         bool found = false;
-        while (!st.empty()) {
-            const int2 e = st.pop();
+        while (sp > 0) {
+            const int2 e = stack[--sp];
             if (__int_as_float(e.y) <= tb) { ni = e.x; found = true; break; }
         }
         if (!found) break;
@@ -355,18 +211,44 @@ __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& 
 template <int W>
 __device__ __forceinline__ bool any_hit(const DesignDev& dz, const RaySetup& r, float tmin, int skip, int* err,
                                         uint32_t& nvis, uint32_t& ntest) {
+    constexpr int NF4 = W == 4 ? 8 : 16;
+    constexpr int Q = W / 4;
     const float4* __restrict__ nodes = dz.nodes;
     const float4* __restrict__ tri = dz.tri;
-    TravStack<int> st;
+    int stack[kStackSize];
+    int sp = 0;
     int ni = 0;
     int visits = 0;
+    const int nxo = r.inv.x < 0.0f ? Q : 0, nyo = r.inv.y < 0.0f ? Q : 0, nzo = r.inv.z < 0.0f ? Q : 0;
     while (true) {
         if (++visits > kVisitCap) { atomicOr(err, kErrVisitCap); return false; }
         ++nvis;
+        const float4* nd = nodes + (size_t)ni * NF4;
         float tn[W];
         bool hit[W];
         int child[W];
-        node_slab<W>(nodes + (size_t)ni * node_f4<W>(), r, tmin, INFINITY, tn, hit, child);
+#pragma unroll
+        for (int h = 0; h < Q; ++h) {
+            const float4 ax = __ldg(nd + nxo + h), bx = __ldg(nd + (Q - nxo) + h);
+            const float4 ay = __ldg(nd + 2 * Q + nyo + h), by = __ldg(nd + 2 * Q + (Q - nyo) + h);
+            const float4 az = __ldg(nd + 4 * Q + nzo + h), bz = __ldg(nd + 4 * Q + (Q - nzo) + h);
+            const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * Q) + h);
+            const float ax_[4] = {ax.x, ax.y, ax.z, ax.w}, bx_[4] = {bx.x, bx.y, bx.z, bx.w};
+            const float ay_[4] = {ay.x, ay.y, ay.z, ay.w}, by_[4] = {by.x, by.y, by.z, by.w};
+            const float az_[4] = {az.x, az.y, az.z, az.w}, bz_[4] = {bz.x, bz.y, bz.z, bz.w};
+            const int ch_[4] = {ch.x, ch.y, ch.z, ch.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float n0 = fmaf(ax_[q], r.inv.x, -r.oinv.x), f0 = fmaf(bx_[q], r.inv.x, -r.oinv.x);
+                const float n1 = fmaf(ay_[q], r.inv.y, -r.oinv.y), f1 = fmaf(by_[q], r.inv.y, -r.oinv.y);
+                const float n2 = fmaf(az_[q], r.inv.z, -r.oinv.z), f2 = fmaf(bz_[q], r.inv.z, -r.oinv.z);
+                const float tnear = fmaxf(fmaxf(n0, n1), fmaxf(n2, tmin));
+                const float tfar = fminf(fminf(f0, f1), f2);
+                tn[4 * h + q] = tnear;
+                hit[4 * h + q] = tnear <= tfar;
+                child[4 * h + q] = ch_[q];
+            }
+        }
 #pragma unroll
         for (int c = 0; c < W; ++c) {
             if (hit[c] && child[c] < 0) {
@@ -389,17 +271,20 @@ __device__ __forceinline__ bool any_hit(const DesignDev& dz, const RaySetup& r, 
         for (int c = 0; c < W; ++c) {
             if (hit[c] && child[c] >= 0) {
                 if (tn[c] < tnext) {
-                    if (next >= 0 && !st.push(next)) { atomicOr(err, kErrStackOverflow); return false; }
+                    if (next >= 0) {
+                        if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return false; }
+                        stack[sp++] = next;
+                    }
                     next = child[c]; tnext = tn[c];
-                } else if (!st.push(child[c])) {
-                    atomicOr(err, kErrStackOverflow);
-                    return false;
+                } else {
+                    if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return false; }
+                    stack[sp++] = child[c];
                 }
             }
         }
         if (next >= 0) { ni = next; continue; }
-        if (st.empty()) break;
-        ni = st.pop();
+        if (sp == 0) break;
+        ni = stack[--sp];
     }
     return false;
 }
