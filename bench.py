@@ -54,10 +54,11 @@ def _peaks():
 def _l2_probe(srp, ctx):
     """L2 read ceiling measured here by the library's own probe kernel
     (srp_probe_read_bandwidth: 16-byte ld.global.cg loads, which bypass L1,
-    from every SM at full occupancy) over L2-resident buffers of 8-64 MiB;
-    the best rate.  Also the HBM read rate over a 4 GiB buffer."""
+    from every SM at full occupancy, 16 loads in flight per thread) over
+    L2-resident buffers of 4-64 MiB (the traversal's scene is 5.6 MB, read
+    by every SM); the best rate.  Also the HBM read rate over 4 GiB."""
     rates = {}
-    for mib in (8, 16, 32, 64):
+    for mib in (4, 8, 16, 32, 64):
         rates[mib] = srp.srp_probe_read_bandwidth(ctx, mib << 20, passes=64, reps=10)
     hbm = srp.srp_probe_read_bandwidth(ctx, 4 << 30, passes=2, reps=5)
     return max(rates.values()), {"l2_read_gbs_by_mib": rates, "hbm_read_gbs_4gib": hbm}
@@ -317,7 +318,7 @@ def run_ours(args, ws, rank, local):
                      "traffic": TRACE_DRAM_BYTES_PER_LAUNCH,
                      "frac_of_hbm": mem_gbs / peaks["hbm_gbs"], "hbm_peak": peaks["hbm_gbs"],
                      "probe": l2_detail,
-                     "peaks_source": f"L2: srp_probe_read_bandwidth in this run (ld.global.cg over 8-64 MiB, "
+                     "peaks_source": f"L2: srp_probe_read_bandwidth in this run (ld.global.cg over 4-64 MiB, "
                                      f"best); HBM: {src}",
                      "note": (f"trace_kernel, algorithmic {bytes_per_ray:.0f} B per grid ray (node visits x "
                               f"{node_bytes} B + triangle tests x 48 B, kernel counters; scene "
@@ -385,7 +386,7 @@ def run_ours(args, ws, rank, local):
         line["per_sample_designs"] = _guarded(samples_leg, srp, ctx, dev, sm_mhz)
         line["batched_designs"] = _guarded(batched_leg, srp, ctx, dev, sm_mhz, peaks, l2_gbs)
         line["design_optimisation"] = _guarded(design_leg, srp, ctx, dev)
-        sg = _guarded(extra_legs, srp, ctx, dev, peaks)
+        sg = _guarded(extra_legs, srp, ctx, dev, peaks, l2_gbs, sm_mhz, n_sm)
         line["surrogate"], line["grad"] = (sg, sg) if isinstance(sg, dict) else sg
         orb = _guarded(orbit_leg, srp, ctx)
         if isinstance(orb, dict):
@@ -421,7 +422,7 @@ def run_ours(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def extra_legs(srp, ctx, dev, peaks):
+def extra_legs(srp, ctx, dev, peaks, l2_gbs, sm_mhz, n_sm):
     """Surrogate vs tracer force evaluations/s (and the surrogate's held-out
     error) and gradient evaluations/s, on the box-wing design space."""
     import torch
@@ -486,13 +487,34 @@ def extra_legs(srp, ctx, dev, peaks):
     gkw = dict(rays_x=1024, max_bounces=1)
     srp.srp_force_grad(ctx, b1, rho1, sun1, com1, up, th1, ha, **gkw)
     torch.cuda.synchronize()
+    # traversal counters of one call (the kernel counts in registers either way)
+    srp.srp_collect_stats(ctx, True)
+    srp.srp_force_grad(ctx, b1, rho1, sun1, com1, up, th1, ha, **gkw)
+    gvis, gtests, _ = srp.srp_collect_stats(ctx, False)
     e0.record()
     for _ in range(3):
         srp.srp_force_grad(ctx, b1, rho1, sun1, com1, up, th1, ha, **gkw)
     e1.record()
     torch.cuda.synchronize()
-    g_rate = 3 * 64 / (e0.elapsed_time(e1) / 1e3)
+    t_call = e0.elapsed_time(e1) / 1e3 / 3
+    g_rate = 64 / t_call
+    rays = 64 * 1024 * 1024
+    node_bytes = 128
+    g_bytes = gvis * node_bytes + gtests * 48
+    g_ops = gvis * 4 * 14 + gtests * 44
+    peak_alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
     grad = {"grad_evals_per_s": g_rate, "rays_per_eval": 1024 * 1024,
+            "traversal": {"node_visits_per_ray": gvis / rays, "tri_tests_per_ray": gtests / rays,
+                          "bytes_per_ray": g_bytes / rays},
+            "roofline": {"bound": "l2", "achieved": g_bytes / t_call / 1e9, "peak": l2_gbs, "unit": "GB/s",
+                         "frac": g_bytes / t_call / 1e9 / l2_gbs,
+                         "note": "grad_kernel + its reduction, one call (64 suns x 1024^2 rays): algorithmic "
+                                 "traversal bytes (node visits x 128 B + triangle tests x 48 B, kernel counters) "
+                                 "per second against the L2 read probe; the 16-triangle scene lives in L1"},
+            "alu_roofline": {"bound": "alu", "achieved": g_ops / t_call / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+                             "frac": g_ops / t_call / 1e12 / peak_alu,
+                             "note": "FP32 lane-ops of the slab and triangle tests only (the adjoint's per-hit "
+                                     "shading and the per-group shared-memory accumulation come on top)"},
             "note": "d(F,tau)/d(64 x (rho_s, rho_d), 2 hinge angles), box-wing, K=1"}
     return surrogate, grad
 
@@ -720,8 +742,34 @@ def area_leg(srp, ctx, dev, m, rho, com, sun, peaks, sm_mhz, width):
                "roofline": {"bound": "alu", "achieved": ops_t * n_th / t_th / 1e12, "peak": peak_alu,
                             "unit": "TFLOP/s", "frac": ops_t * n_th / t_th / 1e12 / peak_alu, "traffic": None},
                "note": "srp_force_thermal, every third group emits 700 W/m^2, closest-hit packets"}
+    # one gathered Lambertian interreflection per sample and side (max_bounces
+    # = 2) on 64 of the suns: samples/s, rays per sample, and what the
+    # interreflection adds to F against the grid's two-bounce estimate
+    for _ in range(2):
+        f2 = srp.srp_force_area(ctx, [b], r_t, sub, c_t, dens, max_bounces=2)
+    torch.cuda.synchronize()
+    srp.srp_collect_stats(ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    f2, s2 = srp.srp_force_area(ctx, [b], r_t, sub, c_t, dens, out_sigma=True, max_bounces=2)
+    e1.record()
+    torch.cuda.synchronize()
+    t2 = e0.elapsed_time(e1) / 1e3
+    v2, te2, sg2 = srp.srp_collect_stats(ctx, False)
+    f2n = f2.cpu().numpy()[0, :, :3]
+    fgk2 = srp.srp_force(ctx, [b], r_t, sub, c_t, rays_x=NX, max_bounces=2).cpu().numpy()[0, :, :3]
+    n2 = n_per_sun * sub.shape[0]
+    interreflection = {
+        "samples_per_s": n2 / t2, "ms_per_call": t2 * 1e3, "suns": int(sub.shape[0]),
+        "rays_per_sample": sg2 / n2, "node_visits_per_ray": v2 / max(sg2, 1), "tri_tests_per_ray": te2 / max(sg2, 1),
+        "rel_change_of_F_vs_direct": float(np.mean(np.linalg.norm(f2n - fa_n, axis=1) / np.linalg.norm(fa_n, axis=1))),
+        "rel_diff_vs_grid_k2": float(np.mean(np.linalg.norm(f2n - fgk2, axis=1) / np.linalg.norm(fgk2, axis=1))),
+        "note": "srp_force_area max_bounces = 2: direct light plus one gathered Lambertian interreflection per "
+                "sample and facet side (cosine-sampled direction, closest hit, shadow ray there); the grid's K = 2 "
+                "also carries specular interreflection, which the area estimator leaves out"}
     b.close()
     return {"samples_per_s": rate, "samples_per_sun": n_per_sun, "suns": S, "density_per_m2": dens,
+            "interreflection": interreflection,
             "ms_per_call": t * 1e3, "shadow_rays_per_sample": segs / max(1, n_per_sun * sub.shape[0]),
             "node_visits_per_shadow_ray": vis / max(segs, 1), "tri_tests_per_shadow_ray": tests / max(segs, 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",

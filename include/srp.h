@@ -112,12 +112,15 @@ int srp_collect_stats(srp_ctx* ctx, int enable, uint64_t out[3]);
 
 /* Read-bandwidth probe (for the roofline of the traversal; the paper has no
  * counterpart).  Allocates a device buffer of `bytes` (rounded down to a
- * multiple of 16, >= 16) on the context's device, and reads all of it
- * `passes` times per launch from every SM with 16-byte loads cached in L2
- * only (ld.global.cg), at full occupancy; after one warm-up launch it times
- * `reps` launches with CUDA events on the context's stream and writes the
- * best rate in GB/s (1e9 bytes read per second) to *out_gbs.  A buffer that
- * fits in L2 measures the L2 read rate, one of several GB the HBM read rate.
+ * multiple of 16, >= 16) on the context's device and reads it with 16-byte
+ * loads cached in L2 only (ld.global.cg) from every SM at full occupancy,
+ * 16 independent loads in flight per thread: one launch sweeps the buffer
+ * `passes` times (a buffer smaller than what the grid reads in one round,
+ * about 80 MB, is read several times per round, by different SMs, as every
+ * SM reads the same BVH).  After one warm-up launch it times `reps`
+ * launches with CUDA events on the context's stream and writes the best
+ * rate in GB/s (1e9 bytes read per second) to *out_gbs.  A buffer that fits
+ * in L2 measures the L2 read rate, one of several GB the HBM read rate.
  * Synchronous; frees the buffer before it returns.  SRP_EINVAL for bad
  * arguments, SRP_ENOMEM if the buffer cannot be allocated. */
 int srp_probe_read_bandwidth(srp_ctx* ctx, int64_t bytes, int passes, int reps, double* out_gbs);

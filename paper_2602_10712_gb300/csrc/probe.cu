@@ -5,7 +5,7 @@
 // a few hundred thousand triangles) stay resident in the 129 MB L2, so its
 // bandwidth roof is the L2's, not HBM's.  The probe reads a buffer of a given
 // size from every SM with 16-byte loads that bypass L1 (ld.global.cg: cached
-// in L2 only), 8 independent loads in flight per thread, a full-occupancy
+// in L2 only), 16 independent loads in flight per thread, a full-occupancy
 // grid (resident blocks x SMs), many passes per launch.  A buffer that fits
 // in L2 gives the L2 read rate; one of several GB gives the HBM read rate.
 #include <cuda_runtime.h>
@@ -16,7 +16,7 @@
 namespace srp {
 
 constexpr int kProbeThreads = 512;
-constexpr int kProbeUnroll = 8;
+constexpr int kProbeUnroll = 16;
 
 __device__ __forceinline__ uint4 ld_cg_v4(const uint4* p) {
     uint4 v;
@@ -26,24 +26,32 @@ __device__ __forceinline__ uint4 ld_cg_v4(const uint4* p) {
     return v;
 }
 
-// Every pass reads each 16-byte word of buf[0, n16) once; thread t of the
-// grid reads words t, t + nth, t + 2 nth, ... in groups of kProbeUnroll.
+// Every round, every thread issues kProbeUnroll independent 16-byte loads at
+// consecutive grid strides (mod the buffer): words tid + k nth, k counting
+// on across rounds.  `rounds` is chosen on the host so that one launch
+// sweeps the buffer `passes` times (at least one round per pass); a buffer
+// smaller than one round's reach (nth x kProbeUnroll words) is read by
+// several SMs per round, as every SM reads the same BVH.  Bytes counted:
+// rounds x nth x kProbeUnroll x 16.
 __global__ void __launch_bounds__(kProbeThreads) read_probe_kernel(const uint4* __restrict__ buf, int64_t n16,
-                                                                   int passes, uint32_t* __restrict__ sink) {
+                                                                   int64_t rounds, uint32_t* __restrict__ sink) {
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t acc = 0;
-    for (int p = 0; p < passes; ++p) {
-        for (int64_t i = tid; i < n16; i += nth * kProbeUnroll) {
-            uint4 v[kProbeUnroll];
+    int64_t base = tid % n16;
+    const int64_t step = nth % n16;
+    for (int64_t p = 0; p < rounds; ++p) {
+        uint4 v[kProbeUnroll];
+        int64_t j = base;
 #pragma unroll
-            for (int u = 0; u < kProbeUnroll; ++u) {
-                const int64_t j = i + (int64_t)u * nth;
-                v[u] = j < n16 ? ld_cg_v4(buf + j) : make_uint4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int u = 0; u < kProbeUnroll; ++u) acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+        for (int u = 0; u < kProbeUnroll; ++u) {
+            v[u] = ld_cg_v4(buf + j);
+            j += step;
+            if (j >= n16) j -= n16;
         }
+#pragma unroll
+        for (int u = 0; u < kProbeUnroll; ++u) acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+        base = j;
     }
     // the loads stay live: the result is stored unless it matches a value
     // the buffer's fill pattern cannot produce
@@ -64,6 +72,8 @@ cudaError_t run_read_probe(int64_t bytes, int passes, int reps, cudaStream_t st,
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, read_probe_kernel, kProbeThreads, 0);
     if (e != cudaSuccess) return e;
     const int grid = n_sm * std::max(nb, 1);
+    const int64_t reach = (int64_t)grid * kProbeThreads * kProbeUnroll;   // words per round
+    const int64_t rounds = (int64_t)passes * std::max<int64_t>(1, (n16 + reach - 1) / reach);
     uint4* buf = nullptr;
     uint32_t* sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -73,14 +83,14 @@ cudaError_t run_read_probe(int64_t bytes, int passes, int reps, cudaStream_t st,
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) {
-        read_probe_kernel<<<grid, kProbeThreads, 0, st>>>(buf, n16, passes, sink);
+        read_probe_kernel<<<grid, kProbeThreads, 0, st>>>(buf, n16, rounds, sink);
         e = cudaGetLastError();
     }
     float best = 0.0f;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
         e = cudaEventRecord(e0, st);
         if (e == cudaSuccess) {
-            read_probe_kernel<<<grid, kProbeThreads, 0, st>>>(buf, n16, passes, sink);
+            read_probe_kernel<<<grid, kProbeThreads, 0, st>>>(buf, n16, rounds, sink);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -89,7 +99,7 @@ cudaError_t run_read_probe(int64_t bytes, int passes, int reps, cudaStream_t st,
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e == cudaSuccess && ms > 0.0f && (best == 0.0f || ms < best)) best = ms;
     }
-    if (e == cudaSuccess && best > 0.0f) *out_gbs = (double)n16 * 16.0 * passes / (best * 1e-3) / 1e9;
+    if (e == cudaSuccess && best > 0.0f) *out_gbs = (double)reach * 16.0 * (double)rounds / (best * 1e-3) / 1e9;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (sink) cudaFree(sink);

@@ -85,159 +85,6 @@ __device__ __noinline__ HitOut trace_segment(const float4* __restrict__ nodes, c
     return h;
 }
 
-// ---------------------------------------------------------------------------
-// Primary rays as a warp packet.  The 32 primary rays of a batch are
-// parallel (one sun direction d) and start from 32 neighbouring pixels, so
-// their traversals overlap almost entirely.  The warp walks the BVH once for
-// all of them: one node at a time (every lane loads the same address: one
-// L1 transaction per load instead of up to 32), each lane slab-tests its own
-// ray, and a child is entered when any lane's ray meets it (a ballot); the
-// stack is the warp's, in shared memory (no per-lane local memory).  Each
-// stack entry carries the mask of lanes whose rays entered that box, so a
-// lane tests a node's children only when its own ray reached the node --
-// the nodes and triangles each lane tests are those of its own traversal,
-// and its closest hit (smallest t, ties to the smaller original index) is
-// the one trace_segment finds.  Children are ordered near-to-far by the
-// depth of their nearest corner along d (the same for every ray of the
-// packet), and a popped node is skipped when that depth lies beyond every
-// entered lane's current hit: for a ray o + t d with |d| = 1 any point p of
-// the box has t = p.d - o.d >= near.d - o.d.
-// ---------------------------------------------------------------------------
-#ifndef SRP_PACKET
-#define SRP_PACKET 1
-#endif
-
-struct PacketStack {
-    int2 e[kStackSize];        // (node, bits(depth of its nearest corner along d))
-    uint32_t m[kStackSize];    // lanes whose rays entered the node's box
-};
-
-template <int W>
-__device__ __noinline__ HitOut trace_packet(const float4* __restrict__ nodes, const float4* __restrict__ tri,
-                                            float ox, float oy, float oz, float dx, float dy, float dz,
-                                            const float* dirc, bool active, PacketStack* stk, int* err) {
-    constexpr int NF4 = W == 4 ? 8 : 16;
-    constexpr int Q = W / 4;
-    const int lane = threadIdx.x & 31;
-    RaySetup r;
-    r.o = f3(ox, oy, oz);
-    r.d = f3(dx, dy, dz);
-    r.inv = f3(dirc[0], dirc[1], dirc[2]);
-    r.oinv = f3(ox * r.inv.x, oy * r.inv.y, oz * r.inv.z);
-    r.mx = f3(dirc[3], dirc[4], dirc[5]);
-    r.my = f3(dirc[6], dirc[7], dirc[8]);
-    r.mz = f3(dirc[9], dirc[10], dirc[11]);
-    HitOut h;
-    h.f = -1;
-    h.t = INFINITY;
-    h.nvis = 0;
-    h.ntest = 0;
-    float tb = active ? INFINITY : -1.0f;   // an inactive lane meets nothing
-    uint32_t best_id = 0xffffffffu;
-    const float od = ox * dx + oy * dy + oz * dz;
-    uint32_t nmask = __ballot_sync(0xffffffffu, active);
-    if (nmask == 0u) return h;
-    int ni = 0, sp = 0, visits = 0;
-    const int nxo = r.inv.x < 0.0f ? Q : 0, nyo = r.inv.y < 0.0f ? Q : 0, nzo = r.inv.z < 0.0f ? Q : 0;
-    while (true) {
-        if (++visits > kVisitCap) { if (lane == 0) atomicOr(err, kErrVisitCap); h.f = -1; h.t = INFINITY; return h; }
-        const bool mine = (nmask >> lane) & 1u;
-        h.nvis += mine ? 1u : 0u;
-        const float4* nd = nodes + (size_t)ni * NF4;
-        float tn[W], key[W];
-        bool hit[W];
-        int child[W];
-#pragma unroll
-        for (int q4 = 0; q4 < Q; ++q4) {
-            const float4 ax = __ldg(nd + nxo + q4), bx = __ldg(nd + (Q - nxo) + q4);
-            const float4 ay = __ldg(nd + 2 * Q + nyo + q4), by = __ldg(nd + 2 * Q + (Q - nyo) + q4);
-            const float4 az = __ldg(nd + 4 * Q + nzo + q4), bz = __ldg(nd + 4 * Q + (Q - nzo) + q4);
-            const int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 6 * Q) + q4);
-            const float ax_[4] = {ax.x, ax.y, ax.z, ax.w}, bx_[4] = {bx.x, bx.y, bx.z, bx.w};
-            const float ay_[4] = {ay.x, ay.y, ay.z, ay.w}, by_[4] = {by.x, by.y, by.z, by.w};
-            const float az_[4] = {az.x, az.y, az.z, az.w}, bz_[4] = {bz.x, bz.y, bz.z, bz.w};
-            const int ch_[4] = {ch.x, ch.y, ch.z, ch.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float n0 = fmaf(ax_[q], r.inv.x, -r.oinv.x), f0 = fmaf(bx_[q], r.inv.x, -r.oinv.x);
-                const float n1 = fmaf(ay_[q], r.inv.y, -r.oinv.y), f1 = fmaf(by_[q], r.inv.y, -r.oinv.y);
-                const float n2 = fmaf(az_[q], r.inv.z, -r.oinv.z), f2 = fmaf(bz_[q], r.inv.z, -r.oinv.z);
-                const float tnear = fmaxf(fmaxf(n0, n1), fmaxf(n2, 0.0f));
-                const float tfar = fminf(fminf(f0, f1), fminf(f2, tb));
-                tn[4 * q4 + q] = tnear;
-                hit[4 * q4 + q] = mine && tnear <= tfar;
-                child[4 * q4 + q] = ch_[q];
-                // depth of the child's nearest corner along d (the near planes
-                // are the corner that minimises p.d): the same on every lane
-                key[4 * q4 + q] = fmaf(az_[q], dz, fmaf(ay_[q], dy, ax_[q] * dx));
-            }
-        }
-        // leaves first: they may shrink tb before inner children are taken
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-            if (child[c] < 0 && __any_sync(0xffffffffu, hit[c]) && hit[c]) {
-                const int code = ~child[c];
-                const int first = code >> 3, cnt = (code & 7) + 1;
-                h.ntest += cnt;
-                for (int q = 0; q < cnt; ++q) {
-                    const int f = first + q;
-                    const float4 a = __ldg(tri + 3 * (size_t)f);
-                    const float4 b = __ldg(tri + 3 * (size_t)f + 1);
-                    const float4 cc = __ldg(tri + 3 * (size_t)f + 2);
-                    const float t = hit_triangle(r, xyz(a), xyz(b), xyz(cc));
-                    if (t > 0.0f && t <= tb) {
-                        const uint32_t id = __float_as_uint(a.w);
-                        if (t < tb || id < best_id) { tb = t; h.f = f; best_id = id; }
-                    }
-                }
-            }
-        }
-        // inner children some lane still needs, nearest (smallest key) next,
-        // the others pushed farthest first
-        uint32_t mc[W];
-#pragma unroll
-        for (int c = 0; c < W; ++c) mc[c] = __ballot_sync(0xffffffffu, child[c] >= 0 && hit[c] && tn[c] <= tb);
-        int next = -1;
-        uint32_t next_m = 0u;
-#pragma unroll
-        for (int it = 0; it < W; ++it) {
-            int far = -1;
-            float kf = -INFINITY;
-#pragma unroll
-            for (int c = 0; c < W; ++c)
-                if (mc[c] && key[c] >= kf) { kf = key[c]; far = c; }
-            if (far < 0) break;
-            const uint32_t m = mc[far];
-            mc[far] = 0u;
-            bool last = true;
-#pragma unroll
-            for (int c = 0; c < W; ++c) last = last && mc[c] == 0u;
-            if (last) { next = child[far]; next_m = m; break; }
-            if (sp >= kStackSize) { if (lane == 0) atomicOr(err, kErrStackOverflow); h.f = -1; h.t = INFINITY; return h; }
-            stk->e[sp] = make_int2(child[far], __float_as_int(kf));
-            stk->m[sp] = m;
-            ++sp;
-        }
-        __syncwarp();   // the pushed entries are visible to every lane before any pops them
-        if (next >= 0) { ni = next; nmask = next_m; continue; }
-        // pop: the node is needed by the lanes that entered it whose hit, if
-        // any, lies beyond its nearest corner (margin for FP32 rounding)
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            const int2 e = stk->e[sp];
-            const uint32_t m = stk->m[sp];
-            const float k = __int_as_float(e.y);
-            const float kl = k - 1e-6f * (fabsf(k) + fabsf(od)) - 1e-30f;
-            const uint32_t need = __ballot_sync(0xffffffffu, ((m >> lane) & 1u) && kl - od <= tb);
-            if (need) { ni = e.x; nmask = need; found = true; break; }
-        }
-        if (!found) break;
-    }
-    h.t = tb;
-    return h;
-}
-
 struct ShadeOut {
     float ox, oy, oz, dx, dy, dz, w;
     int src;
@@ -315,9 +162,6 @@ struct WarpSmem {
     double dacc[12];           // warp FP64 sums (force, torque, squared pair differences)
     float dirc[12];            // the item's 1/d and shear rows (primary segments)
     int64_t bbase[kBatches];   // ray index of the first ray of each batch of the tile
-#if SRP_PACKET
-    PacketStack pstk;          // the warp's stack for primary packets
-#endif
 };
 
 __host__ __device__ constexpr size_t trace_smem_bytes(int block) {
@@ -462,34 +306,6 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
                 const int slot = j * 32 + lane;
                 Seg nx;
                 bool cont = false;
-#if SRP_PACKET
-                // contiguous pixels (bstride 1): one packet for the warp
-                const bool valid = slot < nslots;
-                const uint64_t i = valid ? (uint64_t)(ws.bbase[j] + (int64_t)lane * bstride) : 0;
-                const Seg sg = primary_seg(ic, p, i);
-                HitOut h;
-                if (bstride == 1) {
-                    h = trace_packet<W>(dz.nodes, dz.tri, sg.o.x, sg.o.y, sg.o.z, sg.d.x, sg.d.y, sg.d.z, ws.dirc,
-                                        valid, &ws.pstk, p.err);
-                } else {
-                    h.f = -1; h.nvis = 0; h.ntest = 0;
-                    if (valid)
-                        h = trace_segment<W>(dz.nodes, dz.tri, sg.o.x, sg.o.y, sg.o.z, sg.d.x, sg.d.y, sg.d.z, 0.0f, -1,
-                                             ws.dirc, p.err);
-                }
-                if (valid) {
-                    ++nseg;
-                    nvis += h.nvis; ntest += h.ntest;
-                    if (h.f >= 0) {
-                        const ShadeOut so = shade_segment(dz.tri, ic.rho, ic.com.x, ic.com.y, ic.com.z, p.K, p.seed,
-                                                          ic.sglob, ic.dglob, (uint32_t)i, 1, h.f, h.t, sg.o.x,
-                                                          sg.o.y, sg.o.z, sg.d.x, sg.d.y, sg.d.z, sg.w,
-                                                          &ws.ys[0][slot], kTile);
-                        cont = so.cont != 0;
-                        nx.o = f3(so.ox, so.oy, so.oz); nx.d = f3(so.dx, so.dy, so.dz); nx.w = so.w; nx.src = so.src;
-                    }
-                }
-#else
                 if (slot < nslots) {
                     const uint64_t i = (uint64_t)(ws.bbase[j] + (int64_t)lane * bstride);
                     const Seg sg = primary_seg(ic, p, i);
@@ -506,7 +322,6 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
                         nx.o = f3(so.ox, so.oy, so.oz); nx.d = f3(so.dx, so.dy, so.dz); nx.w = so.w; nx.src = so.src;
                     }
                 }
-#endif
                 q_push(ws, qcount, cont, nx, slot, 2, lane);
                 while (qcount >= 32) q_batch<W>(ws, qcount, 32, dz, ic, p, bstride, lane, nvis, ntest, nseg);
             }
