@@ -39,7 +39,7 @@ WORKLOAD = "procedural satellite 49,776 tris, 64 groups, 4096 Fibonacci suns x 2
 # dram__bytes_read.sum + dram__bytes_write.sum of trace_kernel<4,6> from the ncu
 # capture of 16 of the 4096 suns (the ncu summary of the 16-sun case under
 # profiles/), scaled by the units processed (x256) to one benchmark launch
-TRACE_DRAM_BYTES_PER_LAUNCH = (19.011584e6 + 104.137216e6) * 256
+TRACE_DRAM_BYTES_PER_LAUNCH = (19.178752e6 + 105.754624e6) * 256
 
 
 def _peaks():

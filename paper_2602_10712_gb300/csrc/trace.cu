@@ -571,11 +571,13 @@ int trace_resident_blocks(int width, int block, int variant) {
     if (width == 8) {
         if (variant == 4) return resident_blocks_v<8, 4>(block);
         if (variant == 6) return resident_blocks_v<8, 6>(block);
+        if (variant == 7) return resident_blocks_v<8, 7>(block);
         if (variant == 8) return resident_blocks_v<8, 8>(block);
         return resident_blocks_v<8, 5>(block);
     }
     if (variant == 4) return resident_blocks_v<4, 4>(block);
     if (variant == 6) return resident_blocks_v<4, 6>(block);
+    if (variant == 7) return resident_blocks_v<4, 7>(block);
     if (variant == 8) return resident_blocks_v<4, 8>(block);
     return resident_blocks_v<4, 5>(block);
 }
@@ -591,11 +593,13 @@ cudaError_t launch_trace(const TraceParams& p, int width, int grid_cap, int bloc
     if (width == 8) {
         if (p.variant == 4) trace_kernel<8, 4><<<grid, block, sm, st>>>(p);
         else if (p.variant == 6) trace_kernel<8, 6><<<grid, block, sm, st>>>(p);
+        else if (p.variant == 7) trace_kernel<8, 7><<<grid, block, sm, st>>>(p);
         else if (p.variant == 8) trace_kernel<8, 8><<<grid, block, sm, st>>>(p);
         else trace_kernel<8, 5><<<grid, block, sm, st>>>(p);
     } else {
         if (p.variant == 4) trace_kernel<4, 4><<<grid, block, sm, st>>>(p);
         else if (p.variant == 6) trace_kernel<4, 6><<<grid, block, sm, st>>>(p);
+        else if (p.variant == 7) trace_kernel<4, 7><<<grid, block, sm, st>>>(p);
         else if (p.variant == 8) trace_kernel<4, 8><<<grid, block, sm, st>>>(p);
         else trace_kernel<4, 5><<<grid, block, sm, st>>>(p);
     }
