@@ -29,52 +29,14 @@
 #include <string>
 #include <vector>
 
+#include "mlp_common.cuh"
 #include "srp_internal.h"
 #include "tc_common.cuh"
 
 namespace srp {
 
-constexpr int kMlpLayers = 5;
-__host__ __device__ constexpr int mlp_in(int l) { return l == 0 ? 19 : 256; }
-__host__ __device__ constexpr int mlp_out(int l) { return l == kMlpLayers - 1 ? 6 : 256; }
-__host__ __device__ constexpr int mlp_K(int l) { return l == 0 ? 32 : 256; }                 // padded K
-__host__ __device__ constexpr int mlp_N(int l) { return l == kMlpLayers - 1 ? 16 : 256; }    // padded N
-constexpr int kMlpParams = 19 * 256 + 256 + 3 * (256 * 256 + 256) + 256 * 6 + 6;
-constexpr uint32_t kWaitLimit = 1u << 24;
-
-struct MlpLayout {
-    int64_t w_off[kMlpLayers];   // FP32 weight offset in the flat vector
-    int64_t b_off[kMlpLayers];
-    int64_t p_off[kMlpLayers];   // BF16 packed offset (elements)
-    int64_t packed_elems;
-};
-
-__host__ __device__ inline MlpLayout mlp_layout() {
-    MlpLayout L;
-    int64_t o = 0, q = 0;
-    for (int l = 0; l < kMlpLayers; ++l) {
-        L.w_off[l] = o;
-        o += (int64_t)mlp_in(l) * mlp_out(l);
-        L.b_off[l] = o;
-        o += mlp_out(l);
-        L.p_off[l] = q;
-        q += (int64_t)mlp_N(l) * mlp_K(l);
-    }
-    L.packed_elems = q;
-    return L;
-}
-
-// Packed BF16 weights: per layer, K cut into chunks of KC = min(64, K)
-// columns; each chunk is a contiguous K-major no-swizzle N x KC tile, so
-// one bulk copy brings one chunk and the MMAs of that K range can start as
-// soon as it lands.
-__host__ __device__ constexpr int mlp_KC(int l) { return mlp_K(l) < 64 ? mlp_K(l) : 64; }
-__host__ __device__ inline uint32_t mlp_packed_off(int l, int n, int k) {   // bytes within layer l
-    const int KC = mlp_KC(l), c = k / KC;
-    return (uint32_t)c * (uint32_t)(mlp_N(l) * KC * 2) + tc::kmajor_off((uint32_t)n, (uint32_t)(k - c * KC), (uint32_t)KC);
-}
-
-// FP32 master weights -> BF16 packed per layer (zero padding).
+// FP32 master weights -> BF16 packed per layer (zero padding), forward and
+// transposed layouts.
 __global__ void mlp_pack_kernel(const float* __restrict__ params, __nv_bfloat16* __restrict__ packed) {
     const MlpLayout L = mlp_layout();
     const int64_t tot = L.packed_elems;
@@ -86,6 +48,16 @@ __global__ void mlp_pack_kernel(const float* __restrict__ params, __nv_bfloat16*
         const int n = (int)(loc / K), k = (int)(loc % K);
         const float w = (n < mlp_out(l) && k < mlp_in(l)) ? params[L.w_off[l] + (int64_t)n * mlp_in(l) + k] : 0.0f;
         packed[L.p_off[l] + mlp_packed_off(l, n, k) / 2] = __float2bfloat16_rn(w);
+    }
+    const int64_t totT = mlp_packed_all_elems() - tot;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < totT; e += (int64_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < kMlpLayers && tot + e >= mlp_pT_off(l + 1)) ++l;
+        const int64_t loc = tot + e - mlp_pT_off(l);
+        const int K = mlp_KT(l);
+        const int n = (int)(loc / K), k = (int)(loc % K);   // n: input feature, k: output feature
+        const float w = (k < mlp_out(l) && n < mlp_in(l)) ? params[L.w_off[l] + (int64_t)k * mlp_in(l) + n] : 0.0f;
+        packed[mlp_pT_off(l) + mlp_packedT_off(l, n, k) / 2] = __float2bfloat16_rn(w);
     }
 }
 
@@ -128,21 +100,13 @@ struct MlpFwdSmem {
 // is about 2^-11 |h| in absolute terms: below the BF16 rounding where
 // silu(z) is O(z), but for z below about -4 (silu(z) -> 0 while h tanh(h)
 // cancels h) it is large relative to the value itself.  The inference
-// kernel takes it for speed; the training passes use silu_precise.
+// kernel takes it for speed; the training kernels (train.cu) evaluate
+// z / (1 + exp(-z)) with the accurate expf.
 __device__ __forceinline__ float tanh_approx(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float silu_f(float z) {
-    const float h = 0.5f * z;
-    return fmaf(h, tanh_approx(h), h);
-}
-// z / (1 + exp(-z)) with CUDA's accurate expf and an IEEE division: a few
-// ulps relative for every z (no cancellation); the training forward and the
-// input gradient's forward use it, so the activations they round to BF16
-// and back-propagate through are those of the definition.
-__device__ __forceinline__ float silu_precise(float z) { return z / (1.0f + expf(-z)); }
 
 // Two floats -> BF16 (round to nearest even), a in the low half.
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -394,199 +358,16 @@ cudaError_t mlp_forward(const float* x, int64_t B, const void* packed, const flo
 }
 
 
-// ---------------------------------------------------------------------------
-// Training: forward with saved pre-activations, L1 loss, backward, Adam.
-// GEMMs run on gemm.cu's tensor-core kernel (BF16 operands, FP32 sums).
-// ---------------------------------------------------------------------------
-struct GemmOp {
-    const float* p;
-    int64_t ld;
-    int trans;
-};
-cudaError_t tc_gemm(GemmOp A, GemmOp B, int M, int N, int K, float alpha, float* C, int64_t ldc, int atomic,
-                    int k_split, int* err, cudaStream_t st);
-
-// Z += b (row-wise), H = silu(Z) (if H != null)
-__global__ void bias_silu_kernel(float* Z, const float* b, float* H, int64_t rows, int cols) {
-    const int64_t n = rows * cols;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const float z = Z[e] + b[e % cols];
-        Z[e] = z;
-        if (H) H[e] = silu_precise(z);
-    }
-}
-
-// dY = sign(Y - T) / B; loss += sum |Y - T| / B
-__global__ void l1_kernel(const float* Y, const float* T, float* dY, float* loss, int64_t n, float invB) {
-    float acc = 0.0f;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const float d = Y[e] - T[e];
-        dY[e] = (d > 0.0f ? invB : (d < 0.0f ? -invB : 0.0f));
-        acc += fabsf(d);
-    }
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * invB);
-}
-
-// dZ = dH * silu'(Z)
-__global__ void dsilu_kernel(const float* dH, const float* Z, float* dZ, int64_t n) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const float z = Z[e];
-        const float sg = 1.0f / (1.0f + expf(-z));
-        dZ[e] = dH[e] * sg * (1.0f + z * (1.0f - sg));
-    }
-}
-
-// db[c] = sum_r dZ[r][c]  (one block per column chunk)
-__global__ void colsum_kernel(const float* dZ, int64_t rows, int cols, float* db) {
-    const int c = blockIdx.x;
-    float acc = 0.0f;
-    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) acc += dZ[r * cols + c];
-    __shared__ float red[32];
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        db[c] = t;
-    }
-}
-
-// Adam (Kingma & Ba): bias-corrected moments, in place.
-__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const float gg = g[e];
-        const float mm = b1 * m[e] + (1.0f - b1) * gg;
-        const float vv = b2 * v[e] + (1.0f - b2) * gg * gg;
-        m[e] = mm;
-        v[e] = vv;
-        p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
-    }
-}
-
-struct TrainBufs {
-    float* H[kMlpLayers];   // H[0] = x (caller), H[1..4] hidden [B][256]
-    float* Z[kMlpLayers];   // pre-activations; Z[4] = outputs [B][6]
-    float* dA;              // [B][256]
-    float* dB;              // [B][256]
-    float* loss;            // [1]
-};
-
-size_t train_bytes(int64_t B) {
-    return sizeof(float) * (size_t)(B * (4 * 256 + 4 * 256 + 6 + 2 * 256) + 64);
-}
-
-void train_carve(void* base, int64_t B, TrainBufs& t) {
-    float* q = (float*)base;
-    for (int l = 1; l < kMlpLayers; ++l) { t.H[l] = q; q += B * 256; }
-    for (int l = 0; l < kMlpLayers; ++l) { t.Z[l] = q; q += B * mlp_out(l); }
-    t.dA = q; q += B * 256;
-    t.dB = q; q += B * 256;
-    t.loss = q;
-}
-
-static unsigned ew_grid(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 4096); }
-
-// One optimisation step; grad receives dL/dparams; Adam applied when lr > 0.
+// Training and the input gradient run on the fused kernels of train.cu.
+size_t train_bytes(int64_t B);
+float* train_loss_ptr(void* work, int64_t B);
 cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params, float* grad, float* adam_m,
-                      float* adam_v, int64_t step, float lr, void* work, void* packed, int* err, cudaStream_t st) {
-    const MlpLayout L = mlp_layout();
-    TrainBufs tb;
-    train_carve(work, B, tb);
-    tb.H[0] = const_cast<float*>(x);
-    cudaError_t e;
-    const int Bi = (int)B;
-    // forward
-    for (int l = 0; l < kMlpLayers; ++l) {
-        const int in = mlp_in(l), out = mlp_out(l);
-        e = tc_gemm(GemmOp{tb.H[l], in, 0}, GemmOp{params + L.w_off[l], in, 0}, Bi, out, in, 1.0f, tb.Z[l], out, 0, 0,
-                    err, st);
-        if (e != cudaSuccess) return e;
-        bias_silu_kernel<<<ew_grid(B * out), 256, 0, st>>>(tb.Z[l], params + L.b_off[l],
-                                                           l < kMlpLayers - 1 ? tb.H[l + 1] : nullptr, B, out);
-    }
-    // loss and dY
-    e = cudaMemsetAsync(tb.loss, 0, sizeof(float), st);
-    if (e != cudaSuccess) return e;
-    l1_kernel<<<ew_grid(B * 6), 256, 0, st>>>(tb.Z[4], tgt, tb.dA, tb.loss, B * 6, 1.0f / (float)B);
-    e = cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, st);
-    if (e != cudaSuccess) return e;
-    float* dZ = tb.dA;
-    float* dH = tb.dB;
-    for (int l = kMlpLayers - 1; l >= 0; --l) {
-        const int in = mlp_in(l), out = mlp_out(l);
-        // dW_l = dZ_l^T H_l  (K = batch, split over 128-row slices and added
-        // atomically: the output is only out x in, so the batch is what
-        // spreads the work over the SMs -- 1024-row slices left 8-16 CTAs)
-        e = tc_gemm(GemmOp{dZ, out, 1}, GemmOp{tb.H[l], in, 1}, out, in, Bi, 1.0f, grad + L.w_off[l], in, 1, 128,
-                    err, st);
-        if (e != cudaSuccess) return e;
-        colsum_kernel<<<out, 256, 0, st>>>(dZ, B, out, grad + L.b_off[l]);
-        if (l > 0) {
-            // dH = dZ_l W_l ; dZ_{l-1} = dH * silu'(Z_{l-1})
-            e = tc_gemm(GemmOp{dZ, out, 0}, GemmOp{params + L.w_off[l], in, 1}, Bi, in, out, 1.0f, dH, in, 0, 0, err,
-                        st);
-            if (e != cudaSuccess) return e;
-            dsilu_kernel<<<ew_grid(B * in), 256, 0, st>>>(dH, tb.Z[l - 1], dH, B * in);
-            float* t = dZ; dZ = dH; dH = t;
-        }
-    }
-    if (lr > 0.0f) {
-        const float b1 = 0.9f, b2 = 0.999f;
-        const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-        adam_kernel<<<ew_grid(kMlpParams), 256, 0, st>>>(params, grad, adam_m, adam_v, kMlpParams, lr, b1, b2, 1e-8f,
-                                                          c1, c2);
-        mlp_pack_kernel<<<256, 256, 0, st>>>(params, (__nv_bfloat16*)packed);
-    }
-    return cudaGetLastError();
-}
-
-// Input gradient gx[B][19] = (d y / d x)^T wy  (wy [B][6]): forward with
-// saved pre-activations, then the backward pass of mlp_train with wy in
-// place of dL/dy, ending in gx = dZ_0 W_0.
-cudaError_t mlp_input_grad(const float* x, const float* wy, int64_t B, const float* params, float* gx, void* work,
-                           int* err, cudaStream_t st) {
-    const MlpLayout L = mlp_layout();
-    TrainBufs tb;
-    train_carve(work, B, tb);
-    tb.H[0] = const_cast<float*>(x);
-    cudaError_t e;
-    const int Bi = (int)B;
-    for (int l = 0; l < kMlpLayers; ++l) {
-        const int in = mlp_in(l), out = mlp_out(l);
-        e = tc_gemm(GemmOp{tb.H[l], in, 0}, GemmOp{params + L.w_off[l], in, 0}, Bi, out, in, 1.0f, tb.Z[l], out, 0, 0,
-                    err, st);
-        if (e != cudaSuccess) return e;
-        bias_silu_kernel<<<ew_grid(B * out), 256, 0, st>>>(tb.Z[l], params + L.b_off[l],
-                                                           l < kMlpLayers - 1 ? tb.H[l + 1] : nullptr, B, out);
-    }
-    const float* dZ = wy;
-    float* bufs[2] = {tb.dA, tb.dB};
-    int nb = 0;
-    for (int l = kMlpLayers - 1; l >= 0; --l) {
-        const int in = mlp_in(l), out = mlp_out(l);
-        float* dH = l > 0 ? bufs[nb] : gx;
-        e = tc_gemm(GemmOp{dZ, out, 0}, GemmOp{params + L.w_off[l], in, 1}, Bi, in, out, 1.0f, dH, in, 0, 0, err, st);
-        if (e != cudaSuccess) return e;
-        if (l > 0) {
-            dsilu_kernel<<<ew_grid(B * in), 256, 0, st>>>(dH, tb.Z[l - 1], dH, B * in);
-            dZ = dH;
-            nb ^= 1;
-        }
-    }
-    return cudaGetLastError();
-}
-
-float* train_loss_ptr(void* work, int64_t B) {
-    TrainBufs tb;
-    train_carve(work, B, tb);
-    return tb.loss;
-}
+                      float* adam_v, int64_t step, float lr, void* work, void* packed, int* err, cudaStream_t st);
+cudaError_t mlp_input_grad(const float* x, const float* wy, int64_t B, const float* params, const void* packed,
+                           float* gx, void* work, int* err, cudaStream_t st);
 
 int64_t mlp_param_count() { return kMlpParams; }
-int64_t mlp_packed_bytes() { return mlp_layout().packed_elems * 2; }
+int64_t mlp_packed_bytes() { return mlp_packed_all_elems() * 2; }
 
 void set_last_error(const std::string& msg);
 cudaStream_t ctx_stream(srp_ctx* c);
@@ -808,7 +589,7 @@ extern "C" int srp_mlp_grad_input(srp_ctx* c, srp_mlp* m, const float* x, const 
         m->work_bytes = need;
     }
     if (mem == SRP_MEM_DEVICE) {
-        MCU(mlp_input_grad(x, wy, B, m->params, gx, m->work, ctx_err(c), st), "input-gradient launch");
+        MCU(mlp_input_grad(x, wy, B, m->params, m->packed, gx, m->work, ctx_err(c), st), "input-gradient launch");
         return SRP_OK;
     }
     float* sx = (float*)((char*)m->work + (train_bytes(B) + 255) / 256 * 256);
@@ -816,7 +597,7 @@ extern "C" int srp_mlp_grad_input(srp_ctx* c, srp_mlp* m, const float* x, const 
     float* sg = sw + 6 * B;
     MCU(cudaMemcpyAsync(sx, x, sizeof(float) * 19 * B, cudaMemcpyHostToDevice, st), "H2D x");
     MCU(cudaMemcpyAsync(sw, wy, sizeof(float) * 6 * B, cudaMemcpyHostToDevice, st), "H2D wy");
-    MCU(mlp_input_grad(sx, sw, B, m->params, sg, m->work, ctx_err(c), st), "input-gradient launch");
+    MCU(mlp_input_grad(sx, sw, B, m->params, m->packed, sg, m->work, ctx_err(c), st), "input-gradient launch");
     MCU(cudaMemcpyAsync(gx, sg, sizeof(float) * 19 * B, cudaMemcpyDeviceToHost, st), "D2H gx");
     return srp_sync(c);
 }

@@ -1,0 +1,636 @@
+// train.cu -- training step and input gradient of the neural proxy
+// (Sec. 3.3: the proxy is fitted to traced forces by minimising the L1 risk
+// with Adam; Sec. 3.4 differentiates it inside the design loop) on the
+// tcgen05 tensor cores, BF16 operands and FP32 accumulators in TMEM.
+//
+// One step is four kernels:
+//   train_fwd_kernel  one CTA per 128-row tile: the five layers in turn
+//                     (weights by bulk copy, one thread issues the MMAs, the
+//                     four warps' epilogue reads its TMEM lane quarter);
+//                     the epilogue adds the bias, applies SiLU, writes the
+//                     next layer's BF16 A operand into shared memory, and
+//                     keeps for the backward pass silu'(z) (FP32) and the
+//                     BF16 activations transposed (batch along K); the last
+//                     layer gives the L1 loss, dL/dy = sign(y - t)/B and the
+//                     output bias gradient;
+//   train_bwd_kernel  one CTA per tile: dL/dh = dL/dz W through the layers
+//                     from the top (transposed packed weights), the
+//                     epilogue multiplies by silu'(z), writes the BF16
+//                     operand of the next product, dL/dz transposed, and
+//                     sums the bias gradient over the tile's rows;
+//   train_dw_kernel   the weight gradients dW_l = (dL/dz_l)^T h_l, batch
+//                     along K split over CTAs, bulk-copied double-buffered
+//                     K tiles, FP32 vector atomics into the gradient;
+//   adam_kernel + the weight packing (mlp.cu) when lr > 0.
+// Rounding points (what the oracle's round_act / round_grad reproduce):
+// every product consumes BF16 operands -- weights, inputs, activations,
+// back-propagated dL/dz -- and accumulates in FP32; silu'(z), the bias
+// gradients and the loss are FP32 from unrounded values.
+// Every mbarrier wait is bounded; a CTA that gives up records
+// kErrWaitTimeout, waits (bounded) for its copies and MMAs in flight, frees
+// its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mlp_common.cuh"
+#include "srp_internal.h"
+
+namespace srp {
+
+// ---------------------------------------------------------------------------
+// Workspace.  Bp = B rounded up to 128.  Transposed matrices X^T [R][Bp]
+// (R features, the batch along K) are stored "tile-blocked": tiles of
+// RT = min(R, 128) rows x 64 batch columns, each a K-major no-swizzle
+// core-matrix tile of RT * 128 bytes, tile (rt, kt) at byte
+// (rt * Bp/64 + kt) * RT * 128 -- so one K tile of an operand of the weight
+// gradient is one contiguous bulk copy.
+// ---------------------------------------------------------------------------
+struct TrainWS {
+    float* S[4];                 // silu'(z_l) [Bp][256] FP32, l = 0..3
+    __nv_bfloat16* HT[5];        // HT[0] = x^T (R = 32), HT[l] = h_l^T (R = 256)
+    __nv_bfloat16* DZT[5];       // (dL/dz_l)^T: l = 0..3 R = 256, l = 4 R = 16 (dL/dy)
+    float* dY;                   // dL/dy [Bp][8] FP32 (columns 6, 7 zero)
+    float* loss;                 // [1]
+};
+
+__host__ __device__ inline int64_t train_bp(int64_t B) { return (B + 127) / 128 * 128; }
+
+static size_t al1k(size_t x) { return (x + 1023) / 1024 * 1024; }
+
+size_t train_bytes(int64_t B) {
+    const size_t Bp = (size_t)train_bp(B);
+    return 4 * al1k(Bp * 256 * 4) + al1k(32 * Bp * 2) + 4 * al1k(256 * Bp * 2) + 4 * al1k(256 * Bp * 2) +
+           al1k(16 * Bp * 2) + al1k(Bp * 8 * 4) + 1024;
+}
+
+static TrainWS train_carve(void* base, int64_t B) {
+    const size_t Bp = (size_t)train_bp(B);
+    unsigned char* q = (unsigned char*)base;
+    TrainWS w;
+    for (int l = 0; l < 4; ++l) { w.S[l] = (float*)q; q += al1k(Bp * 256 * 4); }
+    w.HT[0] = (__nv_bfloat16*)q; q += al1k(32 * Bp * 2);
+    for (int l = 1; l < 5; ++l) { w.HT[l] = (__nv_bfloat16*)q; q += al1k(256 * Bp * 2); }
+    for (int l = 0; l < 4; ++l) { w.DZT[l] = (__nv_bfloat16*)q; q += al1k(256 * Bp * 2); }
+    w.DZT[4] = (__nv_bfloat16*)q; q += al1k(16 * Bp * 2);
+    w.dY = (float*)q; q += al1k(Bp * 8 * 4);
+    w.loss = (float*)q;
+    return w;
+}
+
+float* train_loss_ptr(void* work, int64_t B) { return train_carve(work, B).loss; }
+
+// byte offset of element (row, col) of a tile-blocked X^T with RT-row tiles
+__device__ __forceinline__ size_t tb_off(int row, int64_t col, int RT, int64_t Bp) {
+    const int rt = row / RT, r = row - rt * RT;
+    const int64_t kt = col >> 6;
+    return ((size_t)rt * (size_t)(Bp >> 6) + (size_t)kt) * (size_t)(RT * 128) +
+           tc::kmajor_off((uint32_t)r, (uint32_t)(col & 63), 64u);
+}
+__device__ __forceinline__ void st_bf16(__nv_bfloat16* base, size_t byte_off, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(base) + byte_off) = __float2bfloat16_rn(v);
+}
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    uint32_t p;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(hi), "f"(lo));
+    return p;
+}
+
+// Warp transpose-reduction: lane c ends with the sum over the warp's 32
+// lanes of their t[c] (recursive halving: 31 shuffles for 32 columns).
+__device__ __forceinline__ float warp_colsum32(float (&t)[32], int lane) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const float send = up ? t[i] : t[i + off];
+            const float keep = up ? t[i + off] : t[i];
+            t[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return t[0];
+}
+
+constexpr int kTrThreads = 128;
+
+struct TrainSmem {
+    alignas(1024) unsigned char act[128 * 256 * 2];   // A operand: the tile's 128 rows (64 KB)
+    alignas(1024) unsigned char w[256 * 256 * 2];     // B operand: one layer's packed weights (128 KB)
+    float colsum[256];                                 // bias-gradient sums of the tile
+    alignas(8) uint64_t bar_w;
+    alignas(8) uint64_t bar_mma;
+    uint32_t tmem_base;
+    int fail;
+};
+
+// Thread 0: bring `bytes` of packed weights (multiple of 16) into sm.w.
+__device__ __forceinline__ void load_w(TrainSmem& sm, const unsigned char* src, uint32_t bytes) {
+    tc::mbar_expect_tx(&sm.bar_w, bytes);
+    for (uint32_t o = 0; o < bytes; o += 32768u)
+        tc::bulk_g2s(sm.w + o, src + o, min(32768u, bytes - o), &sm.bar_w);
+}
+
+// Thread 0: D = A (act, K columns) x B^T (sm.w: N rows, chunks of KC), commit.
+__device__ __forceinline__ void issue_layer(TrainSmem& sm, uint32_t tbase, int N, int K, int KC) {
+    const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)N);
+    const uint32_t a0 = tc::smem_u32(sm.act), b0 = tc::smem_u32(sm.w);
+    const uint32_t sboA = (uint32_t)(K / 8) * 128u, sboB = (uint32_t)(KC / 8) * 128u;
+    for (int kk = 0; kk < K / 16; ++kk) {
+        const int c = kk / (KC / 16), j = kk - c * (KC / 16);
+        const uint64_t ad = tc::sdesc(a0 + 256u * (uint32_t)kk, 128u, sboA);
+        const uint64_t bd = tc::sdesc(b0 + (uint32_t)c * (uint32_t)(N * KC * 2) + 256u * (uint32_t)j, 128u, sboB);
+        tc::mma_bf16(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&sm.bar_mma);
+}
+
+// The per-layer handshake: thread 0 waits for the weights and issues the
+// MMAs; everyone waits for them.  Returns 0, or 1 (weights never landed) /
+// 2 (MMAs never completed) when a bounded wait gave up (block-uniform).
+__device__ __forceinline__ int run_layer(TrainSmem& sm, uint32_t tbase, int N, int K, int KC, uint32_t& ph_w,
+                                         uint32_t& ph_m) {
+    if (threadIdx.x == 0) {
+        const bool ok = tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
+        sm.fail = ok ? 0 : 1;
+        if (ok) {
+            tc::tc_fence_after();
+            issue_layer(sm, tbase, N, K, KC);
+        }
+    }
+    __syncthreads();
+    if (sm.fail) return 1;
+    ph_w ^= 1u;
+    const bool ok = tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit);
+    ph_m ^= 1u;
+    if (__syncthreads_or(!ok)) return 2;
+    tc::tc_fence_after();
+    return 0;
+}
+
+__device__ __forceinline__ void train_setup(TrainSmem& sm) {
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&sm.bar_w, 1);
+        tc::mbar_init(&sm.bar_mma, 1);
+        tc::fence_mbar_init();
+    }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(&sm.tmem_base, 256);
+        tc::tmem_relinquish();
+    }
+    for (int i = threadIdx.x; i < 256; i += kTrThreads) sm.colsum[i] = 0.0f;
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+}
+
+// After a failed wait: record it, let the copy or the MMAs in flight land
+// (bounded), free TMEM.  ph_w / ph_m are the parities still awaited.
+__device__ __forceinline__ void train_teardown(TrainSmem& sm, uint32_t tbase, int failed, uint32_t ph_w,
+                                               uint32_t ph_m, int* err) {
+    if (failed && threadIdx.x == 0) {
+        atomicOr(err, kErrWaitTimeout);
+        if (failed == 1) tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
+        else tc::mbar_wait_bounded(&sm.bar_mma, ph_m ^ 1u, kWaitLimit);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 256);
+}
+
+// ---------------------------------------------------------------------------
+// Forward.  mode 0: training (targets t: loss, dL/dy, output bias gradient,
+// transposed inputs and activations for the weight gradients); mode 1: the
+// input gradient's forward (silu'(z) of the hidden layers only).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* __restrict__ x,
+                                                                 const float* __restrict__ tgt, int64_t B, int64_t Bp,
+                                                                 const __nv_bfloat16* __restrict__ packed,
+                                                                 const float* __restrict__ params, TrainWS ws,
+                                                                 float* __restrict__ grad, int mode, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const MlpLayout L = mlp_layout();
+    const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
+    train_setup(sm);
+    const uint32_t tbase = sm.tmem_base;
+    const int64_t row0 = (int64_t)blockIdx.x * 128, row = row0 + tid;
+    if (tid == 0) load_w(sm, pb + 2 * L.p_off[0], (uint32_t)(mlp_N(0) * mlp_K(0) * 2));
+    // the tile's inputs: BF16 A operand (K = 32, zero padded) and x^T
+    {
+        float v[19];
+#pragma unroll
+        for (int j = 0; j < 19; ++j) v[j] = row < B ? __ldg(x + row * 19 + j) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = 8 * q + 2 * j;
+                u[j] = bf16x2(k < 19 ? v[k] : 0.0f, k + 1 < 19 ? v[k + 1] : 0.0f);
+            }
+            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 8 * q, 32)) = make_uint4(u[0], u[1], u[2], u[3]);
+        }
+        if (mode == 0) {
+#pragma unroll
+            for (int f = 0; f < 32; ++f) st_bf16(ws.HT[0], tb_off(f, row, 32, Bp), f < 19 ? v[f] : 0.0f);
+        }
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    uint32_t ph_w = 0, ph_m = 0;
+    int failed = 0;
+    const int nl = mode == 0 ? kMlpLayers : kMlpLayers - 1;
+    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+    for (int l = 0; l < nl; ++l) {
+        failed = run_layer(sm, tbase, mlp_N(l), mlp_K(l), mlp_KC(l), ph_w, ph_m);
+        if (failed) break;
+        // the weights of layer l are consumed: bring the next layer's
+        if (tid == 0 && l + 1 < nl) load_w(sm, pb + 2 * L.p_off[l + 1], (uint32_t)(mlp_N(l + 1) * mlp_K(l + 1) * 2));
+        if (l < kMlpLayers - 1) {
+            const float* bias = params + L.b_off[l];
+            float* S = ws.S[l] + row * 256;
+#pragma unroll 1
+            for (int cc = 0; cc < 8; ++cc) {
+                float v[32];
+                tc::tmem_ld32(taddr + 32u * (uint32_t)cc, v);
+                uint32_t pk[16];
+#pragma unroll
+                for (int j = 0; j < 32; j += 2) {
+                    float h[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int col = 32 * cc + j + e;
+                        const float z = v[j + e] + __ldg(bias + col);
+                        const float ez = 1.0f + expf(-z);
+                        const float s = 1.0f / ez;
+                        h[e] = z / ez;
+                        v[j + e] = s * (1.0f + z * (1.0f - s));   // silu'(z)
+                    }
+                    pk[j / 2] = bf16x2(h[0], h[1]);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    reinterpret_cast<float4*>(S + 32 * cc)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 32 * cc + 8 * q, 256)) =
+                        make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                if (mode == 0) {
+                    unsigned char* ht = reinterpret_cast<unsigned char*>(ws.HT[l + 1]);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const uint16_t hb = (uint16_t)(pk[j / 2] >> (16 * (j & 1)));
+                        *reinterpret_cast<uint16_t*>(ht + tb_off(32 * cc + j, row, 128, Bp)) = hb;
+                    }
+                }
+            }
+        } else {
+            // output layer: loss, dL/dy, its transposed BF16 copy, output bias gradient
+            float v[16];
+            tc::tmem_ld16(taddr, v);
+            const float invB = 1.0f / (float)B;
+            float lsum = 0.0f;
+            float dy[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                dy[j] = 0.0f;
+                if (j < 6 && row < B) {
+                    const float d = v[j] + __ldg(params + L.b_off[4] + j) - __ldg(tgt + row * 6 + j);
+                    dy[j] = d > 0.0f ? invB : (d < 0.0f ? -invB : 0.0f);
+                    lsum += fabsf(d);
+                }
+            }
+            reinterpret_cast<float4*>(ws.dY + row * 8)[0] = make_float4(dy[0], dy[1], dy[2], dy[3]);
+            reinterpret_cast<float4*>(ws.dY + row * 8)[1] = make_float4(dy[4], dy[5], dy[6], dy[7]);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) st_bf16(ws.DZT[4], tb_off(j, row, 16, Bp), j < 6 ? dy[j] : 0.0f);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                float sdy = dy[j];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sdy += __shfl_xor_sync(0xffffffffu, sdy, off);
+                if (lane == 0 && sdy != 0.0f) atomicAdd(grad + L.b_off[4] + j, sdy);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+            if (lane == 0) atomicAdd(ws.loss, lsum * invB);
+        }
+        tc::tc_fence_before();
+        tc::fence_async_smem();
+        __syncthreads();
+    }
+    train_teardown(sm, tbase, failed, ph_w, ph_m, err);
+}
+
+// ---------------------------------------------------------------------------
+// Backward.  dy: dL/dy rows (ld floats per row; training: the forward's dY,
+// input gradient: the caller's weights wy).  mode 0: training (down to
+// dL/dz_0, transposed dL/dz and bias gradients); mode 1: the input gradient
+// gx = dL/dz_0 W_0 (FP32 [B][19]).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* __restrict__ dy, int ld, int64_t B,
+                                                                 int64_t Bp, const __nv_bfloat16* __restrict__ packed,
+                                                                 TrainWS ws, float* __restrict__ grad,
+                                                                 float* __restrict__ gx, int mode, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const MlpLayout L = mlp_layout();
+    const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
+    train_setup(sm);
+    const uint32_t tbase = sm.tmem_base;
+    const int64_t row0 = (int64_t)blockIdx.x * 128, row = row0 + tid;
+    const int top = kMlpLayers - 1, lmin = mode == 0 ? 1 : 0;
+    if (tid == 0) load_w(sm, pb + 2 * mlp_pT_off(top), (uint32_t)(mlp_NT(top) * mlp_KT(top) * 2));
+    {
+        float a[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) a[j] = (j < 6 && row < B) ? __ldg(dy + row * ld + j) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 8 * q, 16)) =
+                make_uint4(bf16x2(a[8 * q], a[8 * q + 1]), bf16x2(a[8 * q + 2], a[8 * q + 3]),
+                           bf16x2(a[8 * q + 4], a[8 * q + 5]), bf16x2(a[8 * q + 6], a[8 * q + 7]));
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    uint32_t ph_w = 0, ph_m = 0;
+    int failed = 0;
+    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+    for (int l = top; l >= lmin; --l) {
+        failed = run_layer(sm, tbase, mlp_NT(l), mlp_KT(l), mlp_KCT(l), ph_w, ph_m);
+        if (failed) break;
+        if (tid == 0 && l - 1 >= lmin) load_w(sm, pb + 2 * mlp_pT_off(l - 1), (uint32_t)(mlp_NT(l - 1) * mlp_KT(l - 1) * 2));
+        if (l >= 1) {
+            // dL/dz_{l-1} = (dL/dz_l W_l) * silu'(z_{l-1})
+            const float* S = ws.S[l - 1] + row * 256;
+#pragma unroll 1
+            for (int cc = 0; cc < 8; ++cc) {
+                float v[32];
+                tc::tmem_ld32(taddr + 32u * (uint32_t)cc, v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 s4 = __ldg(reinterpret_cast<const float4*>(S + 32 * cc) + q);
+                    v[4 * q] *= s4.x; v[4 * q + 1] *= s4.y; v[4 * q + 2] *= s4.z; v[4 * q + 3] *= s4.w;
+                }
+                uint32_t pk[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pk[j] = bf16x2(v[2 * j], v[2 * j + 1]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 32 * cc + 8 * q, 256)) =
+                        make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                if (mode == 0) {
+                    unsigned char* dz = reinterpret_cast<unsigned char*>(ws.DZT[l - 1]);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const uint16_t hb = (uint16_t)(pk[j / 2] >> (16 * (j & 1)));
+                        *reinterpret_cast<uint16_t*>(dz + tb_off(32 * cc + j, row, 128, Bp)) = hb;
+                    }
+                    // bias gradient of layer l-1: this warp's 32 rows, column 32 cc + lane
+                    const float cs = warp_colsum32(v, lane);
+                    atomicAdd(&sm.colsum[32 * cc + lane], cs);
+                }
+            }
+            if (mode == 0) {
+                __syncthreads();
+                for (int c = tid; c < 256; c += kTrThreads) {
+                    atomicAdd(grad + L.b_off[l - 1] + c, sm.colsum[c]);
+                    sm.colsum[c] = 0.0f;
+                }
+            }
+        } else {
+            // input gradient: gx = dL/dz_0 W_0 (19 of the 32 columns)
+            float v[32];
+            tc::tmem_ld32(taddr, v);
+            if (row < B) {
+#pragma unroll
+                for (int j = 0; j < 19; ++j) gx[row * 19 + j] = v[j];
+            }
+        }
+        tc::tc_fence_before();
+        tc::fence_async_smem();
+        __syncthreads();
+    }
+    train_teardown(sm, tbase, failed, ph_w, ph_m, err);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradients.  Work item (layer l, M tile mt, K slice ks):
+//   l = 0..3: dW_l[o][i] += sum_r dZT_l[o][r] HT_l[i][r]   (M = o, N = i)
+//   l = 4:    dW_4[o][i] += sum_r HT_4[i][r] DZT_4[o][r]    (M = i, N = o:
+//             the 6 outputs fit an N = 16 tile; stored transposed)
+// over the batch columns of K slice ks (kDwSlice tiles of 64).
+// ---------------------------------------------------------------------------
+constexpr int kDwSlice = 8;
+
+struct DwSmem {
+    alignas(1024) unsigned char a[2][128 * 64 * 2];
+    alignas(1024) unsigned char b[2][256 * 64 * 2];
+    alignas(8) uint64_t full[2];
+    alignas(8) uint64_t mma[2];
+    uint32_t tmem_base;
+    int fail;
+};
+
+struct DwItem {
+    const unsigned char* A;   // tile-blocked, RT = 128
+    const unsigned char* Bm;  // tile-blocked, RT = min(N, 128)
+    int N, RTb;
+};
+
+__device__ __forceinline__ DwItem dw_item(const TrainWS& ws, int l) {
+    DwItem it;
+    if (l < 4) {
+        it.A = reinterpret_cast<const unsigned char*>(ws.DZT[l]);
+        it.Bm = reinterpret_cast<const unsigned char*>(ws.HT[l]);
+        it.N = l == 0 ? 32 : 256;
+    } else {
+        it.A = reinterpret_cast<const unsigned char*>(ws.HT[4]);
+        it.Bm = reinterpret_cast<const unsigned char*>(ws.DZT[4]);
+        it.N = 16;
+    }
+    it.RTb = it.N < 128 ? it.N : 128;
+    return it;
+}
+
+__global__ void __launch_bounds__(kTrThreads, 1) train_dw_kernel(int64_t Bp, int nks, TrainWS ws,
+                                                                float* __restrict__ grad, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    DwSmem& sm = *reinterpret_cast<DwSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const MlpLayout L = mlp_layout();
+    const int ks = blockIdx.x % nks, mt = (blockIdx.x / nks) % 2, l = blockIdx.x / (2 * nks);
+    const DwItem it = dw_item(ws, l);
+    const int64_t nkt_all = Bp >> 6;
+    const int kt0 = ks * kDwSlice;
+    const int nk = (int)min((int64_t)kDwSlice, nkt_all - kt0);
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) { tc::mbar_init(&sm.full[s], 1); tc::mbar_init(&sm.mma[s], 1); }
+        tc::fence_mbar_init();
+        sm.fail = 0;
+    }
+    if (tid < 32) {
+        tc::tmem_alloc(&sm.tmem_base, 256);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tbase = sm.tmem_base;
+    const uint32_t abytes = 128u * 128u, bbytes = (uint32_t)it.RTb * 128u;
+    const int nbt = it.N / it.RTb;   // B row tiles (2 for N = 256)
+    auto issue = [&](int i) {
+        const int s = i & 1;
+        const int64_t kt = kt0 + i;
+        tc::mbar_expect_tx(&sm.full[s], abytes + bbytes * (uint32_t)nbt);
+        tc::bulk_g2s(sm.a[s], it.A + ((size_t)mt * nkt_all + kt) * abytes, abytes, &sm.full[s]);
+        for (int bt = 0; bt < nbt; ++bt)
+            tc::bulk_g2s(sm.b[s] + bt * bbytes, it.Bm + ((size_t)bt * nkt_all + kt) * bbytes, bbytes, &sm.full[s]);
+    };
+    int failed = 0;
+    if (tid == 0 && nk > 0) {
+        const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)it.N);
+        issue(0);
+        if (nk > 1) issue(1);
+        for (int i = 0; i < nk; ++i) {
+            const int s = i & 1;
+            const uint32_t par = (uint32_t)(i >> 1) & 1u;
+            if (!tc::mbar_wait_bounded(&sm.full[s], par, kWaitLimit)) { failed = 1; break; }
+            tc::tc_fence_after();
+            const uint32_t a0 = tc::smem_u32(sm.a[s]), b0 = tc::smem_u32(sm.b[s]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                tc::mma_bf16(tbase, tc::sdesc(a0 + 256u * j, 128u, 1024u), tc::sdesc(b0 + 256u * j, 128u, 1024u), idesc,
+                             (i > 0 || j > 0) ? 1u : 0u);
+            tc::mma_commit(&sm.mma[s]);
+            if (i + 2 < nk) {
+                // the buffer is refilled once its MMAs are done
+                if (!tc::mbar_wait_bounded(&sm.mma[s], par, kWaitLimit)) { failed = 2; break; }
+                issue(i + 2);
+            }
+        }
+        sm.fail = failed;
+    }
+    __syncthreads();
+    failed = sm.fail;
+    if (!failed && nk > 0) {
+        const int last = nk - 1;
+        const bool ok = tc::mbar_wait_bounded(&sm.mma[last & 1], (uint32_t)(last >> 1) & 1u, kWaitLimit);
+        if (__syncthreads_or(!ok)) failed = 2;
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(err, kErrWaitTimeout);
+            // copies and MMAs in flight land before the CTA leaves
+            for (int s = 0; s < 2; ++s) {
+                tc::mbar_wait_bounded(&sm.full[s], 0u, 1u << 16);
+                tc::mbar_wait_bounded(&sm.mma[s], 0u, 1u << 16);
+            }
+        }
+    } else if (nk > 0) {
+        tc::tc_fence_after();
+        const int r = 32 * warp + (tid & 31);   // M row of the tile
+        const int m = 128 * mt + r;
+        const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+        if (l == 4) {
+            float v[16];
+            tc::tmem_ld16(taddr, v);
+#pragma unroll
+            for (int o = 0; o < 6; ++o) atomicAdd(grad + L.w_off[4] + o * 256 + m, v[o]);
+        } else if (l == 0) {
+            float v[32];
+            tc::tmem_ld32(taddr, v);
+#pragma unroll
+            for (int i = 0; i < 19; ++i) atomicAdd(grad + L.w_off[0] + (int64_t)m * 19 + i, v[i]);
+        } else {
+            float4* dst = reinterpret_cast<float4*>(grad + L.w_off[l] + (int64_t)m * 256);
+#pragma unroll 1
+            for (int cc = 0; cc < 8; ++cc) {
+                float v[32];
+                tc::tmem_ld32(taddr + 32u * (uint32_t)cc, v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    atomicAdd(dst + 8 * cc + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (tid < 32) tc::tmem_dealloc(tbase, 256);
+}
+
+// Adam (Kingma & Ba): bias-corrected moments, in place.
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float gg = g[e];
+        const float mm = b1 * m[e] + (1.0f - b1) * gg;
+        const float vv = b2 * v[e] + (1.0f - b2) * gg * gg;
+        m[e] = mm;
+        v[e] = vv;
+        p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    }
+}
+
+cudaError_t mlp_pack(const float* params, void* packed, cudaStream_t st);
+
+static cudaError_t train_attrs() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(TrainSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(train_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DwSmem));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+// One optimisation step; grad receives dL/dparams; Adam applied when lr > 0.
+cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params, float* grad, float* adam_m,
+                      float* adam_v, int64_t step, float lr, void* work, void* packed, int* err, cudaStream_t st) {
+    cudaError_t e = train_attrs();
+    if (e != cudaSuccess) return e;
+    const int64_t Bp = train_bp(B);
+    const TrainWS ws = train_carve(work, B);
+    if ((e = cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws.loss, 0, sizeof(float), st)) != cudaSuccess) return e;
+    const unsigned tiles = (unsigned)(Bp / 128);
+    const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
+    train_fwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(x, tgt, B, Bp, pk, params, ws, grad, 0, err);
+    train_bwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err);
+    const int nks = (int)(((Bp >> 6) + kDwSlice - 1) / kDwSlice);
+    train_dw_kernel<<<(unsigned)(kMlpLayers * 2 * nks), kTrThreads, sizeof(DwSmem), st>>>(Bp, nks, ws, grad, err);
+    if (lr > 0.0f) {
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+        adam_kernel<<<(unsigned)std::min<int64_t>((kMlpParams + 255) / 256, 4096), 256, 0, st>>>(
+            params, grad, adam_m, adam_v, kMlpParams, lr, b1, b2, 1e-8f, c1, c2);
+        if ((e = mlp_pack(params, packed, st)) != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// Input gradient gx[B][19] = (dy/dx)^T wy (wy [B][6]): the forward's
+// silu'(z), then the backward chain down to the inputs.
+cudaError_t mlp_input_grad(const float* x, const float* wy, int64_t B, const float* params, const void* packed,
+                           float* gx, void* work, int* err, cudaStream_t st) {
+    cudaError_t e = train_attrs();
+    if (e != cudaSuccess) return e;
+    const int64_t Bp = train_bp(B);
+    const TrainWS ws = train_carve(work, B);
+    const unsigned tiles = (unsigned)(Bp / 128);
+    const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
+    train_fwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(x, nullptr, B, Bp, pk, params, ws, nullptr, 1, err);
+    train_bwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(wy, 6, B, Bp, pk, ws, nullptr, gx, 1, err);
+    return cudaGetLastError();
+}
+
+}  // namespace srp
