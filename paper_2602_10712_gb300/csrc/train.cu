@@ -5,8 +5,9 @@
 //
 // One step is four kernels:
 //   train_fwd_kernel  one CTA per 128-row tile: the five layers in turn
-//                     (weights by bulk copy, one thread issues the MMAs, the
-//                     four warps' epilogue reads its TMEM lane quarter);
+//                     (weights by bulk copy, one thread issues the MMAs, 16
+//                     epilogue warps, four per TMEM lane quarter, each on
+//                     64 of the 256 columns);
 //                     the epilogue adds the bias, applies SiLU, writes the
 //                     next layer's BF16 A operand into shared memory, and
 //                     keeps for the backward pass silu'(z) (FP32) and the
@@ -113,7 +114,10 @@ __device__ __forceinline__ float warp_colsum32(float (&t)[32], int lane) {
     return t[0];
 }
 
-constexpr int kTrThreads = 128;
+// 16 warps: warp w reads TMEM lane quarter w % 4 (32 rows of the tile) and,
+// in 256-wide layers, the 64 columns 64 (w / 4) ... of them.
+constexpr int kTrThreads = 512;
+constexpr int kDwThreads = 128;
 
 struct TrainSmem {
     alignas(1024) unsigned char act[128 * 256 * 2];   // A operand: the tile's 128 rows (64 KB)
@@ -213,14 +217,16 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, part = warp >> 2, r = 32 * quarter + lane;
     const MlpLayout L = mlp_layout();
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
-    const int64_t row0 = (int64_t)blockIdx.x * 128, row = row0 + tid;
+    const int64_t row0 = (int64_t)blockIdx.x * 128, row = row0 + r;
     if (tid == 0) load_w(sm, pb + 2 * L.p_off[0], (uint32_t)(mlp_N(0) * mlp_K(0) * 2));
-    // the tile's inputs: BF16 A operand (K = 32, zero padded) and x^T
-    {
+    // the tile's inputs (warps 0-3, one row each): BF16 A operand (K = 32,
+    // zero padded) and x^T
+    if (part == 0) {
         float v[19];
 #pragma unroll
         for (int j = 0; j < 19; ++j) v[j] = row < B ? __ldg(x + row * 19 + j) : 0.0f;
@@ -232,7 +238,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
                 const int k = 8 * q + 2 * j;
                 u[j] = bf16x2(k < 19 ? v[k] : 0.0f, k + 1 < 19 ? v[k + 1] : 0.0f);
             }
-            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 8 * q, 32)) = make_uint4(u[0], u[1], u[2], u[3]);
+            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 8 * q, 32)) = make_uint4(u[0], u[1], u[2], u[3]);
         }
         if (mode == 0) {
 #pragma unroll
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
     uint32_t ph_w = 0, ph_m = 0;
     int failed = 0;
     const int nl = mode == 0 ? kMlpLayers : kMlpLayers - 1;
-    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+    const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
     for (int l = 0; l < nl; ++l) {
         failed = run_layer(sm, tbase, mlp_N(l), mlp_K(l), mlp_KC(l), ph_w, ph_m);
         if (failed) break;
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
             const float* bias = params + L.b_off[l];
             float* S = ws.S[l] + row * 256;
 #pragma unroll 1
-            for (int cc = 0; cc < 8; ++cc) {
+            for (int cc = 2 * part; cc < 2 * part + 2; ++cc) {
                 float v[32];
                 tc::tmem_ld32(taddr + 32u * (uint32_t)cc, v);
                 uint32_t pk[16];
@@ -277,7 +283,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
                     reinterpret_cast<float4*>(S + 32 * cc)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 32 * cc + 8 * q, 256)) =
+                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 32 * cc + 8 * q, 256)) =
                         make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                 if (mode == 0) {
                     unsigned char* ht = reinterpret_cast<unsigned char*>(ws.HT[l + 1]);
@@ -288,8 +294,9 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
                     }
                 }
             }
-        } else {
-            // output layer: loss, dL/dy, its transposed BF16 copy, output bias gradient
+        } else if (part == 0) {
+            // output layer (warps 0-3): loss, dL/dy, its transposed BF16 copy,
+            // output bias gradient
             float v[16];
             tc::tmem_ld16(taddr, v);
             const float invB = 1.0f / (float)B;
@@ -339,20 +346,21 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, part = warp >> 2, r = 32 * quarter + lane;
     const MlpLayout L = mlp_layout();
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
-    const int64_t row0 = (int64_t)blockIdx.x * 128, row = row0 + tid;
+    const int64_t row0 = (int64_t)blockIdx.x * 128, row = row0 + r;
     const int top = kMlpLayers - 1, lmin = mode == 0 ? 1 : 0;
     if (tid == 0) load_w(sm, pb + 2 * mlp_pT_off(top), (uint32_t)(mlp_NT(top) * mlp_KT(top) * 2));
-    {
+    if (part == 0) {
         float a[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) a[j] = (j < 6 && row < B) ? __ldg(dy + row * ld + j) : 0.0f;
 #pragma unroll
         for (int q = 0; q < 2; ++q)
-            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 8 * q, 16)) =
+            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 8 * q, 16)) =
                 make_uint4(bf16x2(a[8 * q], a[8 * q + 1]), bf16x2(a[8 * q + 2], a[8 * q + 3]),
                            bf16x2(a[8 * q + 4], a[8 * q + 5]), bf16x2(a[8 * q + 6], a[8 * q + 7]));
     }
@@ -360,7 +368,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
     __syncthreads();
     uint32_t ph_w = 0, ph_m = 0;
     int failed = 0;
-    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+    const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
     for (int l = top; l >= lmin; --l) {
         failed = run_layer(sm, tbase, mlp_NT(l), mlp_KT(l), mlp_KCT(l), ph_w, ph_m);
         if (failed) break;
@@ -369,7 +377,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
             // dL/dz_{l-1} = (dL/dz_l W_l) * silu'(z_{l-1})
             const float* S = ws.S[l - 1] + row * 256;
 #pragma unroll 1
-            for (int cc = 0; cc < 8; ++cc) {
+            for (int cc = 2 * part; cc < 2 * part + 2; ++cc) {
                 float v[32];
                 tc::tmem_ld32(taddr + 32u * (uint32_t)cc, v);
 #pragma unroll
@@ -382,7 +390,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
                 for (int j = 0; j < 16; ++j) pk[j] = bf16x2(v[2 * j], v[2 * j + 1]);
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(tid, 32 * cc + 8 * q, 256)) =
+                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 32 * cc + 8 * q, 256)) =
                         make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                 if (mode == 0) {
                     unsigned char* dz = reinterpret_cast<unsigned char*>(ws.DZT[l - 1]);
@@ -403,8 +411,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
                     sm.colsum[c] = 0.0f;
                 }
             }
-        } else {
-            // input gradient: gx = dL/dz_0 W_0 (19 of the 32 columns)
+        } else if (part == 0) {
+            // input gradient (warps 0-3): gx = dL/dz_0 W_0 (19 of the 32 columns)
             float v[32];
             tc::tmem_ld32(taddr, v);
             if (row < B) {
@@ -458,7 +466,7 @@ __device__ __forceinline__ DwItem dw_item(const TrainWS& ws, int l) {
     return it;
 }
 
-__global__ void __launch_bounds__(kTrThreads, 1) train_dw_kernel(int64_t Bp, int nks, TrainWS ws,
+__global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int nks, TrainWS ws,
                                                                 float* __restrict__ grad, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     DwSmem& sm = *reinterpret_cast<DwSmem*>(smem_raw);
@@ -607,7 +615,7 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     train_fwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(x, tgt, B, Bp, pk, params, ws, grad, 0, err);
     train_bwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err);
     const int nks = (int)(((Bp >> 6) + kDwSlice - 1) / kDwSlice);
-    train_dw_kernel<<<(unsigned)(kMlpLayers * 2 * nks), kTrThreads, sizeof(DwSmem), st>>>(Bp, nks, ws, grad, err);
+    train_dw_kernel<<<(unsigned)(kMlpLayers * 2 * nks), kDwThreads, sizeof(DwSmem), st>>>(Bp, nks, ws, grad, err);
     if (lr > 0.0f) {
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
