@@ -3,7 +3,7 @@
 // with Adam; Sec. 3.4 differentiates it inside the design loop) on the
 // tcgen05 tensor cores, BF16 operands and FP32 accumulators in TMEM.
 //
-// One step is four kernels:
+// One step is four kernels (three without the Adam update):
 //   train_fwd_kernel  one CTA per 128-row tile: the five layers in turn
 //                     (weights by bulk copy, one thread issues the MMAs, 16
 //                     epilogue warps, four per TMEM lane quarter, each on
@@ -22,7 +22,8 @@
 //   train_dw_kernel   the weight gradients dW_l = (dL/dz_l)^T h_l, batch
 //                     along K split over CTAs, bulk-copied double-buffered
 //                     K tiles, FP32 vector atomics into the gradient;
-//   adam_kernel + the weight packing (mlp.cu) when lr > 0.
+//   adam_pack_kernel  Adam, and the updated weights into both BF16 packed
+//                     layouts, when lr > 0.
 // Rounding points (what the oracle's round_act / round_grad reproduce):
 // every product consumes BF16 operands -- weights, inputs, activations,
 // back-propagated dL/dz -- and accumulates in FP32; silu'(z), the bias
@@ -271,9 +272,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
                     for (int e = 0; e < 2; ++e) {
                         const int col = 32 * cc + j + e;
                         const float z = v[j + e] + __ldg(bias + col);
-                        const float ez = 1.0f + expf(-z);
-                        const float s = 1.0f / ez;
-                        h[e] = z / ez;
+                        // sigmoid by the hardware exp2 and reciprocal (about
+                        // 2^-21 relative each, for every z: no cancellation)
+                        const float s = __fdividef(1.0f, 1.0f + __expf(-z));
+                        h[e] = z * s;
                         v[j + e] = s * (1.0f + z * (1.0f - s));   // silu'(z)
                     }
                     pk[j / 2] = bf16x2(h[0], h[1]);
@@ -573,20 +575,32 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
     if (tid < 32) tc::tmem_dealloc(tbase, 256);
 }
 
-// Adam (Kingma & Ba): bias-corrected moments, in place.
-__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
+// Adam (Kingma & Ba): bias-corrected moments, in place; every updated
+// weight is also written, rounded to BF16, into both packed layouts (the
+// padding of the packed buffers is zero from their creation).
+__global__ void adam_pack_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                                 float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                                 float c2, __nv_bfloat16* __restrict__ packed) {
+    const MlpLayout L = mlp_layout();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const float gg = g[e];
         const float mm = b1 * m[e] + (1.0f - b1) * gg;
         const float vv = b2 * v[e] + (1.0f - b2) * gg * gg;
         m[e] = mm;
         v[e] = vv;
-        p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+        const float pv = p[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+        p[e] = pv;
+        int l = 0;
+        while (l + 1 < kMlpLayers && e >= L.w_off[l + 1]) ++l;
+        const int64_t q = e - L.w_off[l];
+        if (q < (int64_t)mlp_in(l) * mlp_out(l)) {   // a weight, not a bias
+            const int o = (int)(q / mlp_in(l)), i = (int)(q - (int64_t)o * mlp_in(l));
+            const __nv_bfloat16 b = __float2bfloat16_rn(pv);
+            packed[L.p_off[l] + mlp_packed_off(l, o, i) / 2] = b;
+            packed[mlp_pT_off(l) + mlp_packedT_off(l, i, o) / 2] = b;
+        }
     }
 }
-
-cudaError_t mlp_pack(const float* params, void* packed, cudaStream_t st);
 
 static cudaError_t train_attrs() {
     static bool done = false;
@@ -619,9 +633,8 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     if (lr > 0.0f) {
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-        adam_kernel<<<(unsigned)std::min<int64_t>((kMlpParams + 255) / 256, 4096), 256, 0, st>>>(
-            params, grad, adam_m, adam_v, kMlpParams, lr, b1, b2, 1e-8f, c1, c2);
-        if ((e = mlp_pack(params, packed, st)) != cudaSuccess) return e;
+        adam_pack_kernel<<<(unsigned)((kMlpParams + 255) / 256), 256, 0, st>>>(
+            params, grad, adam_m, adam_v, kMlpParams, lr, b1, b2, 1e-8f, c1, c2, (__nv_bfloat16*)packed);
     }
     return cudaGetLastError();
 }
