@@ -449,6 +449,28 @@ def extra_legs(srp, ctx, dev, peaks, l2_gbs, sm_mhz, n_sm):
     t_nn = e0.elapsed_time(e1) / 1e3 / reps
     flops = 2.0 * (19 * 256 + 3 * 256 * 256 + 256 * 6) * nq
     nn_rate = nq / t_nn
+    # the training step alone, device time (CUDA events), on a copy of the
+    # trained network: one fused forward, backward, weight-gradient and
+    # Adam+pack pass per step (3 x 406 kFLOP per sample)
+    step_dev = {}
+    tnet = srp.MLP(ctx, sur.net.params())
+    for bsz in (8192, 65536):
+        xs = torch.randn((bsz, 19), device=dev)
+        ts = torch.randn((bsz, 6), device=dev)
+        for _ in range(5):
+            tnet.train_step(xs, ts, 1e-5, want_loss=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_it = 100
+        e0.record()
+        for _ in range(n_it):
+            tnet.train_step(xs, ts, 1e-5, want_loss=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_step = e0.elapsed_time(e1) / n_it
+        step_dev[str(bsz)] = {"ms_per_step": ms_step,
+                              "tflops": 3 * 2.0 * 203264 * bsz / (ms_step * 1e-3) / 1e12}
+    tnet.close()
     # tracer: one design, 4096 suns x 256^2 rays, K <= 3 (the training accuracy)
     th = S.sample_designs(1, 8)
     v = srp.srp_design_instantiate(mesh.verts, mesh.vhinge, mesh.hinges, th[0, 14:])
@@ -469,10 +491,13 @@ def extra_legs(srp, ctx, dev, peaks, l2_gbs, sm_mhz, n_sm):
                  "data_s": info["data_s"], "train_s": info["train_s"],
                  "train_samples_per_s": info["steps"] * 8192 / info["train_s"],
                  "train_tflops": 3 * 2.0 * 203264 * 8192 * info["steps"] / info["train_s"] / 1e12,
+                 "train_step_device": step_dev,
+                 "train_step_frac_of_bf16_peak": step_dev["8192"]["tflops"] / peak,
                  "mlp_tflops": flops / t_nn / 1e12, "mlp_frac_of_bf16_peak": flops / t_nn / 1e12 / peak,
                  "batch": nq, "note": "19-256x4-6 SiLU, BF16 tcgen05, FP32 accumulation; error vs 1024^2-ray MC; "
-                                      "training: batches of 8192 (fwd + bwd = 3 x 406 kFLOP per sample), wall clock "
-                                      "of the Python step loop"}
+                                      "training: batches of 8192 (fwd + bwd = 3 x 406 kFLOP per sample); train_tflops "
+                                      "is the wall clock of the Python step loop (batch gathers included), "
+                                      "train_step_device the step's kernels alone (CUDA events)"}
     # gradients: box-wing (64 groups, 2 hinges), K = 1, 1024^2 rays, 64 suns per call
     m1 = W.box_wing()
     ang = np.array([0.3, -0.5])

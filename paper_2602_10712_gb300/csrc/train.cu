@@ -99,6 +99,29 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
     return p;
 }
 
+// The warp's 32 rows (lanes) x 32 features (pk: BF16 pairs of the lane's
+// row) into the tile-blocked transposed store: through the warp's shared
+// scratch, so that each lane writes whole 16-byte runs (8 consecutive batch
+// rows of one feature) instead of 32 scattered 2-byte values.  Scratch slot
+// of (feature f, row r): f * 32 + (r ^ (((f >> 1) & 3) << 3)), which keeps
+// both the 2-byte writes (a feature's 32 rows) and the 16-byte reads (eight
+// features' row group q) free of bank conflicts.  f0: first feature, r0:
+// first batch row of the warp (a multiple of 32).
+__device__ __forceinline__ void store_transposed32(uint16_t* sc, const uint32_t (&pk)[16], int lane,
+                                                   unsigned char* dst, int f0, int64_t r0, int64_t Bp) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        sc[j * 32 + (lane ^ (((j >> 1) & 3) << 3))] = (uint16_t)(pk[j / 2] >> (16 * (j & 1)));
+    __syncwarp();
+    const int f = lane;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 v = *reinterpret_cast<const uint4*>(sc + f * 32 + ((q ^ ((f >> 1) & 3)) << 3));
+        *reinterpret_cast<uint4*>(dst + tb_off(f0 + f, r0 + 8 * q, 128, Bp)) = v;
+    }
+    __syncwarp();
+}
+
 // Warp transpose-reduction: lane c ends with the sum over the warp's 32
 // lanes of their t[c] (recursive halving: 31 shuffles for 32 columns).
 __device__ __forceinline__ float warp_colsum32(float (&t)[32], int lane) {
@@ -123,6 +146,7 @@ constexpr int kDwThreads = 128;
 struct TrainSmem {
     alignas(1024) unsigned char act[128 * 256 * 2];   // A operand: the tile's 128 rows (64 KB)
     alignas(1024) unsigned char w[256 * 256 * 2];     // B operand: one layer's packed weights (128 KB)
+    alignas(16) uint16_t scratch[kTrThreads / 32][32 * 32];   // per warp: a 32 x 32 BF16 block being transposed
     float colsum[256];                                 // bias-gradient sums of the tile
     alignas(8) uint64_t bar_w;
     alignas(8) uint64_t bar_mma;
@@ -288,12 +312,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
                     *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 32 * cc + 8 * q, 256)) =
                         make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                 if (mode == 0) {
-                    unsigned char* ht = reinterpret_cast<unsigned char*>(ws.HT[l + 1]);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const uint16_t hb = (uint16_t)(pk[j / 2] >> (16 * (j & 1)));
-                        *reinterpret_cast<uint16_t*>(ht + tb_off(32 * cc + j, row, 128, Bp)) = hb;
-                    }
+                    store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.HT[l + 1]),
+                                       32 * cc, row0 + 32 * quarter, Bp);
                 }
             }
         } else if (part == 0) {
@@ -395,12 +415,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
                     *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 32 * cc + 8 * q, 256)) =
                         make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                 if (mode == 0) {
-                    unsigned char* dz = reinterpret_cast<unsigned char*>(ws.DZT[l - 1]);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const uint16_t hb = (uint16_t)(pk[j / 2] >> (16 * (j & 1)));
-                        *reinterpret_cast<uint16_t*>(dz + tb_off(32 * cc + j, row, 128, Bp)) = hb;
-                    }
+                    store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.DZT[l - 1]),
+                                       32 * cc, row0 + 32 * quarter, Bp);
                     // bias gradient of layer l-1: this warp's 32 rows, column 32 cc + lane
                     const float cs = warp_colsum32(v, lane);
                     atomicAdd(&sm.colsum[32 * cc + lane], cs);
