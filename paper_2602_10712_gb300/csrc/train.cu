@@ -392,6 +392,13 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
     int failed = 0;
     const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
     for (int l = top; l >= lmin; --l) {
+        if (l >= 1) {
+            // this thread's silu'(z_{l-1}) (two 128-byte lines) toward L1
+            // while the tensor core works
+            const float* S = ws.S[l - 1] + row * 256 + 64 * part;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(S));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(S + 32));
+        }
         failed = run_layer(sm, tbase, mlp_NT(l), mlp_KT(l), mlp_KCT(l), ph_w, ph_m);
         if (failed) break;
         if (tid == 0 && l - 1 >= lmin) load_w(sm, pb + 2 * mlp_pT_off(l - 1), (uint32_t)(mlp_NT(l - 1) * mlp_KT(l - 1) * 2));
