@@ -86,7 +86,7 @@ typedef struct srp_trace_opts {
     int32_t sun_per_design;   /* 1: sun_dir is [D][S][3], 0: [S][3] [0]     */
     int32_t block_threads;    /* 0 or 128 (threads per block)               */
     int32_t chunks_per_item;  /* 0 = automatic; else ray chunks per item    */
-    int32_t kernel_variant;   /* min resident blocks/SM: 0 = default (6), 4, 5, 6, 7, 8 */
+    int32_t kernel_variant;   /* min resident blocks/SM: 0 = default (7), 4, 5, 6, 7, 8 */
     int32_t reserved;         /* must be 0                                  */
 } srp_trace_opts;
 

@@ -415,7 +415,7 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
                std::vector<DesignDev>* designs, TraceParams* p, int* width, int* block, int* grid_cap) {
     if (o && o->kernel_variant != 0 && (o->kernel_variant < 4 || o->kernel_variant > 8))
         return fail(SRP_EINVAL, "srp_force: kernel_variant must be 0, 4, 5, 6, 7 or 8");
-    const int variant = (o && o->kernel_variant) ? o->kernel_variant : 6;
+    const int variant = (o && o->kernel_variant) ? o->kernel_variant : 7;
     if (!c || !o) return fail(SRP_EINVAL, "srp_force: NULL ctx/opts");
     if (D < 0 || S < 0) return fail(SRP_EINVAL, "srp_force: negative D or S");
     if (G < 1 || G > kMaxGroups) return fail(SRP_EINVAL, "srp_force: G must be in 1..64");

@@ -117,8 +117,8 @@ int setup_device(int dev, DevState** out) {
         e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
         s.n_sm = v;
-        s.resident[0] = trace_resident_blocks(4, 128, 6);
-        s.resident[1] = trace_resident_blocks(8, 128, 6);
+        s.resident[0] = trace_resident_blocks(4, 128, 7);
+        s.resident[1] = trace_resident_blocks(8, 128, 7);
         s.ready = true;
     }
     *out = &s;
@@ -225,7 +225,7 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     p.part = ds->part;          // every unit overwrites its 12 partials: no clearing needed
     p.err = ds->err;
     p.stats = nullptr;
-    p.variant = 6;
+    p.variant = 7;
     p.queue = ds->queue;
     p.designs = ds->table;
     // the design table: written into the fixed array by small kernels that

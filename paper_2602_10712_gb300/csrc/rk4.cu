@@ -193,10 +193,23 @@ __device__ void model_fwd(const OrbitDev& o, OrbitSmem& s) {
     __syncthreads();
     for (int l = 1; l < 4; ++l) {
         const float* hin = s.h[(l - 1) & 1];
-        float a = o.b[l][t];
         const float* Wt = o.Wt[l];
-#pragma unroll 8
-        for (int i = 0; i < 256; ++i) a = fmaf(Wt[i * 256 + t], hin[i], a);
+        // 32 weight loads in flight per thread and four partial sums: the
+        // loop is bound by the latency of the weight stream from L2
+        float a0 = o.b[l][t], a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        for (int i = 0; i < 256; i += 32) {
+            float w[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) w[u] = __ldg(Wt + (i + u) * 256 + t);
+#pragma unroll
+            for (int u = 0; u < 32; u += 4) {
+                a0 = fmaf(w[u], hin[i + u], a0);
+                a1 = fmaf(w[u + 1], hin[i + u + 1], a1);
+                a2 = fmaf(w[u + 2], hin[i + u + 2], a2);
+                a3 = fmaf(w[u + 3], hin[i + u + 3], a3);
+            }
+        }
+        const float a = (a0 + a1) + (a2 + a3);
         s.zpre[l][t] = a;
         s.h[l & 1][t] = silu_f(a);
         __syncthreads();
@@ -242,9 +255,20 @@ __device__ void model_vjp(const OrbitDev& o, OrbitSmem& s) {
     for (int l = 3; l >= 1; --l) {  // dh_l[i] = sum_o W_l[o][i] dz_l[o]; dz_{l-1} = dh_l * silu'(z_{l-1})
         const float* gin = s.g[cur];
         const float* W = o.W[l];
-        float a = 0.0f;
-#pragma unroll 8
-        for (int oo = 0; oo < 256; ++oo) a = fmaf(W[oo * 256 + t], gin[oo], a);
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        for (int oo = 0; oo < 256; oo += 32) {
+            float w[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) w[u] = __ldg(W + (oo + u) * 256 + t);
+#pragma unroll
+            for (int u = 0; u < 32; u += 4) {
+                a0 = fmaf(w[u], gin[oo + u], a0);
+                a1 = fmaf(w[u + 1], gin[oo + u + 1], a1);
+                a2 = fmaf(w[u + 2], gin[oo + u + 2], a2);
+                a3 = fmaf(w[u + 3], gin[oo + u + 3], a3);
+            }
+        }
+        const float a = (a0 + a1) + (a2 + a3);
         s.g[cur ^ 1][t] = a * dsilu_f(s.zpre[l - 1][t]);
         __syncthreads();
         cur ^= 1;

@@ -22,7 +22,7 @@ from . import srp_build_bvh, srp_force
 
 
 def autotune(ctx, meshes, rho, sun_dir, com, *, rays_x, rays_y=None, max_bounces=1, sample_rays=None,
-             sample_suns=16, widths=(4, 8), variants=(4, 5, 6), rays_per_unit=(0, 1024, 4096, 16384), repeats=2,
+             sample_suns=16, widths=(4, 8), variants=(5, 6, 7), rays_per_unit=(0, 1024, 4096, 16384), repeats=2,
              **opts):
     """Returns (best dict(width, kernel_variant, chunks_per_item), table of
     timings in rays/s); chunks_per_item = 0 is the library's own plan.  `meshes` are workloads.Mesh-like (verts, tris, group);

@@ -104,6 +104,6 @@ def test_kernel_variants_and_autotuner(srp):
     best, table = tune.autotune(ctx, [m], torch.from_numpy(rho[None].copy()).to(dev), torch.from_numpy(sun).to(dev),
                                 torch.from_numpy(com[None].copy()).to(dev), rays_x=512, max_bounces=3,
                                 sample_rays=16384, sample_suns=4)
-    assert len(table) == 24 and best["width"] in (4, 8) and best["kernel_variant"] in (4, 5, 6)
+    assert len(table) == 24 and best["width"] in (4, 8) and best["kernel_variant"] in (5, 6, 7)
     assert best["chunks_per_item"] >= 0
     assert all(r["rays_per_s"] > 0 for r in table)
