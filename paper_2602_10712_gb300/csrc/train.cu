@@ -138,33 +138,85 @@ __device__ __forceinline__ float warp_colsum32(float (&t)[32], int lane) {
     return t[0];
 }
 
-// 16 warps: warp w reads TMEM lane quarter w % 4 (32 rows of the tile) and,
-// in 256-wide layers, the 64 columns 64 (w / 4) ... of them.
+// A tile's 128 rows are processed by a cluster of two CTAs (one SM each):
+// in every 256-wide layer CTA rank c computes the output features
+// [128 c, 128 c + 128) -- half the MMA N and half the epilogue -- and writes
+// its half of the next layer's BF16 A operand into both CTAs' shared memory
+// (distributed shared memory); each then tells the other, on an mbarrier of
+// the receiving CTA, that its half has landed.  The A operand is double
+// buffered (layer l reads act[l & 1], its epilogue writes act[(l + 1) & 1]),
+// so a CTA never writes into a buffer its partner's tensor core may still
+// read.  The narrow layers (the 6 outputs, the 19 input gradients) run on
+// rank 0 alone.  16 warps per CTA: warp w reads TMEM lane quarter w % 4 (32
+// rows) and the 32 columns 32 (w / 4) ... of the CTA's 128.
 constexpr int kTrThreads = 512;
 constexpr int kDwThreads = 128;
+constexpr int kHalf = 128;   // output features of a layer per CTA of the pair
 
 struct TrainSmem {
-    alignas(1024) unsigned char act[128 * 256 * 2];   // A operand: the tile's 128 rows (64 KB)
-    alignas(1024) unsigned char w[256 * 256 * 2];     // B operand: one layer's packed weights (128 KB)
+    alignas(1024) unsigned char act[2][128 * 256 * 2];   // A operands (2 x 64 KB)
+    alignas(1024) unsigned char w[256 * 128 * 2];        // B operand: this CTA's half of a layer (64 KB)
     alignas(16) uint16_t scratch[kTrThreads / 32][32 * 32];   // per warp: a 32 x 32 BF16 block being transposed
-    float colsum[256];                                 // bias-gradient sums of the tile
+    float colsum[kHalf];                                 // bias-gradient sums of the tile
     alignas(8) uint64_t bar_w;
     alignas(8) uint64_t bar_mma;
+    alignas(8) uint64_t bar_peer[2];                     // the partner's k-th half of an A operand landed (k & 1)
     uint32_t tmem_base;
     int fail;
 };
 
-// Thread 0: bring `bytes` of packed weights (multiple of 16) into sm.w.
-__device__ __forceinline__ void load_w(TrainSmem& sm, const unsigned char* src, uint32_t bytes) {
-    tc::mbar_expect_tx(&sm.bar_w, bytes);
-    for (uint32_t o = 0; o < bytes; o += 32768u)
-        tc::bulk_g2s(sm.w + o, src + o, min(32768u, bytes - o), &sm.bar_w);
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared variable in CTA `rank`
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t remote_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(tc::smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+// both CTAs of the pair (kernel start and end only: every thread reaches them)
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// Thread 0: D = A (act, K columns) x B^T (sm.w: N rows, chunks of KC), commit.
-__device__ __forceinline__ void issue_layer(TrainSmem& sm, uint32_t tbase, int N, int K, int KC) {
+// Thread 0: rows [r0, r0 + nr) of each of the K / KC chunks of a packed
+// layer (N x KC K-major tiles) into sm.w, one bulk copy per chunk.
+__device__ __forceinline__ void load_w_rows(TrainSmem& sm, const unsigned char* layer, int N, int K, int KC, int r0,
+                                            int nr) {
+    const uint32_t cb = (uint32_t)(nr * KC * 2);
+    tc::mbar_expect_tx(&sm.bar_w, cb * (uint32_t)(K / KC));
+    for (int c = 0; c < K / KC; ++c)
+        tc::bulk_g2s(sm.w + c * cb, layer + (size_t)c * N * KC * 2 + (size_t)r0 * KC * 2, cb, &sm.bar_w);
+}
+
+// Thread 0: D = A (act[buf], K columns) x B^T (sm.w: N rows, chunks of KC), commit.
+__device__ __forceinline__ void issue_layer(TrainSmem& sm, uint32_t tbase, int buf, int N, int K, int KC) {
     const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)N);
-    const uint32_t a0 = tc::smem_u32(sm.act), b0 = tc::smem_u32(sm.w);
+    const uint32_t a0 = tc::smem_u32(sm.act[buf]), b0 = tc::smem_u32(sm.w);
     const uint32_t sboA = (uint32_t)(K / 8) * 128u, sboB = (uint32_t)(KC / 8) * 128u;
     for (int kk = 0; kk < K / 16; ++kk) {
         const int c = kk / (KC / 16), j = kk - c * (KC / 16);
@@ -175,17 +227,28 @@ __device__ __forceinline__ void issue_layer(TrainSmem& sm, uint32_t tbase, int N
     tc::mma_commit(&sm.bar_mma);
 }
 
-// The per-layer handshake: thread 0 waits for the weights and issues the
-// MMAs; everyone waits for them.  Returns 0, or 1 (weights never landed) /
-// 2 (MMAs never completed) when a bounded wait gave up (block-uniform).
-__device__ __forceinline__ int run_layer(TrainSmem& sm, uint32_t tbase, int N, int K, int KC, uint32_t& ph_w,
-                                         uint32_t& ph_m) {
+// The partner's k-th signal (k = 0, 1, ...) arrives on bar_peer[k & 1] and
+// completes its phase k >> 1: the two barriers alternate, so a partner one
+// signal ahead (the most it can be) never advances the barrier being
+// waited on past the phase awaited.
+__device__ __forceinline__ bool wait_peer(TrainSmem& sm, int k) {
+    return mbar_wait_cluster_bounded(&sm.bar_peer[k & 1], (uint32_t)(k >> 1) & 1u, kWaitLimit);
+}
+
+// The per-layer handshake: thread 0 waits for the weights and, when
+// `peer_k` >= 0, for the partner's signal peer_k (its half of the A
+// operand), then issues the MMAs; everyone waits for them.  Returns 0, or 1
+// (weights or the partner never arrived) / 2 (MMAs never completed) when a
+// bounded wait gave up (block-uniform).
+__device__ __forceinline__ int run_layer(TrainSmem& sm, uint32_t tbase, int buf, int N, int K, int KC, int peer_k,
+                                         uint32_t& ph_w, uint32_t& ph_m) {
     if (threadIdx.x == 0) {
-        const bool ok = tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
+        bool ok = tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
+        if (ok && peer_k >= 0) ok = wait_peer(sm, peer_k);
         sm.fail = ok ? 0 : 1;
         if (ok) {
             tc::tc_fence_after();
-            issue_layer(sm, tbase, N, K, KC);
+            issue_layer(sm, tbase, buf, N, K, KC);
         }
     }
     __syncthreads();
@@ -202,31 +265,61 @@ __device__ __forceinline__ void train_setup(TrainSmem& sm) {
     if (threadIdx.x == 0) {
         tc::mbar_init(&sm.bar_w, 1);
         tc::mbar_init(&sm.bar_mma, 1);
+        tc::mbar_init(&sm.bar_peer[0], 1);
+        tc::mbar_init(&sm.bar_peer[1], 1);
         tc::fence_mbar_init();
     }
     if (threadIdx.x < 32) {
-        tc::tmem_alloc(&sm.tmem_base, 256);
+        tc::tmem_alloc(&sm.tmem_base, kHalf);
         tc::tmem_relinquish();
     }
-    for (int i = threadIdx.x; i < 256; i += kTrThreads) sm.colsum[i] = 0.0f;
+    for (int i = threadIdx.x; i < kHalf; i += kTrThreads) sm.colsum[i] = 0.0f;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
+    cluster_sync();   // the partner's barriers exist before anyone arrives on them
 }
 
-// After a failed wait: record it, let the copy or the MMAs in flight land
-// (bounded), free TMEM.  ph_w / ph_m are the parities still awaited.
+// After the epilogue: this CTA's writes (local and into the partner's A
+// buffer) visible to the tensor cores, then the partner gets signal k.
+__device__ __forceinline__ void signal_peer(TrainSmem& sm, uint32_t peer, int k) {
+    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+    tc::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_cluster(peer_addr(&sm.bar_peer[k & 1], peer));
+}
+
+// End of the kernel: record a failed wait, let the copy or the MMAs in
+// flight land (bounded), wait (bounded) for the partner's last signal so
+// that no write into this CTA's shared memory is still under way, free
+// TMEM, and leave together with the partner.
 __device__ __forceinline__ void train_teardown(TrainSmem& sm, uint32_t tbase, int failed, uint32_t ph_w,
-                                               uint32_t ph_m, int* err) {
-    if (failed && threadIdx.x == 0) {
-        atomicOr(err, kErrWaitTimeout);
-        if (failed == 1) tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
-        else tc::mbar_wait_bounded(&sm.bar_mma, ph_m ^ 1u, kWaitLimit);
+                                               uint32_t ph_m, int last_peer_k, int* err) {
+    if (threadIdx.x == 0) {
+        if (failed) {
+            atomicOr(err, kErrWaitTimeout);
+            if (failed == 1) tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
+            else tc::mbar_wait_bounded(&sm.bar_mma, ph_m ^ 1u, kWaitLimit);
+        }
+        if (last_peer_k >= 0 && !wait_peer(sm, last_peer_k)) atomicOr(err, kErrWaitTimeout);
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 256);
+    if (threadIdx.x < 32) tc::tmem_dealloc(tbase, kHalf);
+    cluster_sync();
+}
+
+// Writes the thread's 32 BF16 values (pk, features f0 .. f0 + 31 of row r)
+// into A buffer `dst` (K = 256 layout) of this CTA and of the partner.
+__device__ __forceinline__ void put_act(unsigned char* dst, const uint32_t (&pk)[16], int r, int f0, uint32_t peer) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        unsigned char* p = dst + tc::kmajor_off((uint32_t)r, (uint32_t)(f0 + 8 * q), 256u);
+        const uint4 v = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        *reinterpret_cast<uint4*>(p) = v;
+        st_cluster_v4(peer_addr(p, peer), v);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -234,23 +327,23 @@ __device__ __forceinline__ void train_teardown(TrainSmem& sm, uint32_t tbase, in
 // transposed inputs and activations for the weight gradients); mode 1: the
 // input gradient's forward (silu'(z) of the hidden layers only).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* __restrict__ x,
-                                                                 const float* __restrict__ tgt, int64_t B, int64_t Bp,
-                                                                 const __nv_bfloat16* __restrict__ packed,
-                                                                 const float* __restrict__ params, TrainWS ws,
-                                                                 float* __restrict__ grad, int mode, int* err) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrThreads, 1)
+    train_fwd_kernel(const float* __restrict__ x, const float* __restrict__ tgt, int64_t B, int64_t Bp,
+                     const __nv_bfloat16* __restrict__ packed, const float* __restrict__ params, TrainWS ws,
+                     float* __restrict__ grad, int mode, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, part = warp >> 2, r = 32 * quarter + lane;
+    const uint32_t rank = cluster_rank(), peer = rank ^ 1u;
     const MlpLayout L = mlp_layout();
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
-    const int64_t row0 = (int64_t)blockIdx.x * 128, row = row0 + r;
-    if (tid == 0) load_w(sm, pb + 2 * L.p_off[0], (uint32_t)(mlp_N(0) * mlp_K(0) * 2));
+    const int64_t row0 = (int64_t)(blockIdx.x >> 1) * 128, row = row0 + r;
+    if (tid == 0) load_w_rows(sm, pb + 2 * L.p_off[0], mlp_N(0), mlp_K(0), mlp_KC(0), kHalf * (int)rank, kHalf);
     // the tile's inputs (warps 0-3, one row each): BF16 A operand (K = 32,
-    // zero padded) and x^T
+    // zero padded) in both CTAs, x^T from rank 0
     if (part == 0) {
         float v[19];
 #pragma unroll
@@ -263,9 +356,9 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
                 const int k = 8 * q + 2 * j;
                 u[j] = bf16x2(k < 19 ? v[k] : 0.0f, k + 1 < 19 ? v[k + 1] : 0.0f);
             }
-            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 8 * q, 32)) = make_uint4(u[0], u[1], u[2], u[3]);
+            *reinterpret_cast<uint4*>(sm.act[0] + tc::kmajor_off(r, 8 * q, 32)) = make_uint4(u[0], u[1], u[2], u[3]);
         }
-        if (mode == 0) {
+        if (mode == 0 && rank == 0) {
 #pragma unroll
             for (int f = 0; f < 32; ++f) st_bf16(ws.HT[0], tb_off(f, row, 32, Bp), f < 19 ? v[f] : 0.0f);
         }
@@ -274,51 +367,57 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
     __syncthreads();
     uint32_t ph_w = 0, ph_m = 0;
     int failed = 0;
-    const int nl = mode == 0 ? kMlpLayers : kMlpLayers - 1;
     const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
-    for (int l = 0; l < nl; ++l) {
-        failed = run_layer(sm, tbase, mlp_N(l), mlp_K(l), mlp_KC(l), ph_w, ph_m);
+    const int f_loc = 32 * part, f_glob = kHalf * (int)rank + f_loc;   // this thread's 32 features
+    // hidden layers 0-3 on both CTAs, half the features each
+    for (int l = 0; l < kMlpLayers - 1; ++l) {
+        failed = run_layer(sm, tbase, l & 1, kHalf, mlp_K(l), mlp_KC(l), l - 1, ph_w, ph_m);
         if (failed) break;
         // the weights of layer l are consumed: bring the next layer's
-        if (tid == 0 && l + 1 < nl) load_w(sm, pb + 2 * L.p_off[l + 1], (uint32_t)(mlp_N(l + 1) * mlp_K(l + 1) * 2));
-        if (l < kMlpLayers - 1) {
-            const float* bias = params + L.b_off[l];
-            float* S = ws.S[l] + row * 256;
-#pragma unroll 1
-            for (int cc = 2 * part; cc < 2 * part + 2; ++cc) {
-                float v[32];
-                tc::tmem_ld32(taddr + 32u * (uint32_t)cc, v);
-                uint32_t pk[16];
+        if (tid == 0) {
+            if (l + 1 < kMlpLayers - 1)
+                load_w_rows(sm, pb + 2 * L.p_off[l + 1], mlp_N(l + 1), mlp_K(l + 1), mlp_KC(l + 1), kHalf * (int)rank,
+                            kHalf);
+            else if (mode == 0 && rank == 0)
+                load_w_rows(sm, pb + 2 * L.p_off[kMlpLayers - 1], mlp_N(kMlpLayers - 1), mlp_K(kMlpLayers - 1),
+                            mlp_KC(kMlpLayers - 1), 0, mlp_N(kMlpLayers - 1));
+        }
+        const float* bias = params + L.b_off[l] + f_glob;
+        float v[32];
+        tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
+        uint32_t pk[16];
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    float h[2];
+        for (int j = 0; j < 32; j += 2) {
+            float h[2];
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int col = 32 * cc + j + e;
-                        const float z = v[j + e] + __ldg(bias + col);
-                        // sigmoid by the hardware exp2 and reciprocal (about
-                        // 2^-21 relative each, for every z: no cancellation)
-                        const float s = __fdividef(1.0f, 1.0f + __expf(-z));
-                        h[e] = z * s;
-                        v[j + e] = s * (1.0f + z * (1.0f - s));   // silu'(z)
-                    }
-                    pk[j / 2] = bf16x2(h[0], h[1]);
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    reinterpret_cast<float4*>(S + 32 * cc)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 32 * cc + 8 * q, 256)) =
-                        make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-                if (mode == 0) {
-                    store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.HT[l + 1]),
-                                       32 * cc, row0 + 32 * quarter, Bp);
-                }
+            for (int e = 0; e < 2; ++e) {
+                const float z = v[j + e] + __ldg(bias + j + e);
+                // sigmoid by the hardware exp2 and reciprocal (about 2^-21
+                // relative each, for every z: no cancellation)
+                const float s = __fdividef(1.0f, 1.0f + __expf(-z));
+                h[e] = z * s;
+                v[j + e] = s * (1.0f + z * (1.0f - s));   // silu'(z)
             }
-        } else if (part == 0) {
-            // output layer (warps 0-3): loss, dL/dy, its transposed BF16 copy,
-            // output bias gradient
+            pk[j / 2] = bf16x2(h[0], h[1]);
+        }
+        float* S = ws.S[l] + row * 256 + f_glob;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            reinterpret_cast<float4*>(S)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        put_act(sm.act[(l + 1) & 1], pk, r, f_glob, peer);
+        if (mode == 0)
+            store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.HT[l + 1]), f_glob,
+                               row0 + 32 * quarter, Bp);
+        signal_peer(sm, peer, l);
+    }
+    int last_peer_k = failed ? -1 : kMlpLayers - 2;   // the partner's signal of layer 3
+    if (!failed && mode == 0 && rank == 0) {
+        // output layer on rank 0: loss, dL/dy, its transposed BF16 copy,
+        // output bias gradient
+        const int l = kMlpLayers - 1;
+        failed = run_layer(sm, tbase, l & 1, mlp_N(l), mlp_K(l), mlp_KC(l), l - 1, ph_w, ph_m);
+        last_peer_k = -1;   // already waited for before the MMAs (or failed)
+        if (!failed && part == 0) {
             float v[16];
             tc::tmem_ld16(taddr, v);
             const float invB = 1.0f / (float)B;
@@ -328,7 +427,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
             for (int j = 0; j < 8; ++j) {
                 dy[j] = 0.0f;
                 if (j < 6 && row < B) {
-                    const float d = v[j] + __ldg(params + L.b_off[4] + j) - __ldg(tgt + row * 6 + j);
+                    const float d = v[j] + __ldg(params + L.b_off[l] + j) - __ldg(tgt + row * 6 + j);
                     dy[j] = d > 0.0f ? invB : (d < 0.0f ? -invB : 0.0f);
                     lsum += fabsf(d);
                 }
@@ -342,47 +441,46 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_fwd_kernel(const float* _
                 float sdy = dy[j];
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) sdy += __shfl_xor_sync(0xffffffffu, sdy, off);
-                if (lane == 0 && sdy != 0.0f) atomicAdd(grad + L.b_off[4] + j, sdy);
+                if (lane == 0 && sdy != 0.0f) atomicAdd(grad + L.b_off[l] + j, sdy);
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
             if (lane == 0) atomicAdd(ws.loss, lsum * invB);
         }
-        tc::tc_fence_before();
-        tc::fence_async_smem();
-        __syncthreads();
     }
-    train_teardown(sm, tbase, failed, ph_w, ph_m, err);
+    train_teardown(sm, tbase, failed, ph_w, ph_m, last_peer_k, err);
 }
 
 // ---------------------------------------------------------------------------
 // Backward.  dy: dL/dy rows (ld floats per row; training: the forward's dY,
 // input gradient: the caller's weights wy).  mode 0: training (down to
 // dL/dz_0, transposed dL/dz and bias gradients); mode 1: the input gradient
-// gx = dL/dz_0 W_0 (FP32 [B][19]).
+// gx = dL/dz_0 W_0 (FP32 [B][19], on rank 0).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* __restrict__ dy, int ld, int64_t B,
-                                                                 int64_t Bp, const __nv_bfloat16* __restrict__ packed,
-                                                                 TrainWS ws, float* __restrict__ grad,
-                                                                 float* __restrict__ gx, int mode, int* err) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrThreads, 1)
+    train_bwd_kernel(const float* __restrict__ dy, int ld, int64_t B, int64_t Bp,
+                     const __nv_bfloat16* __restrict__ packed, TrainWS ws, float* __restrict__ grad,
+                     float* __restrict__ gx, int mode, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, part = warp >> 2, r = 32 * quarter + lane;
+    const uint32_t rank = cluster_rank(), peer = rank ^ 1u;
     const MlpLayout L = mlp_layout();
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
-    const int64_t row0 = (int64_t)blockIdx.x * 128, row = row0 + r;
-    const int top = kMlpLayers - 1, lmin = mode == 0 ? 1 : 0;
-    if (tid == 0) load_w(sm, pb + 2 * mlp_pT_off(top), (uint32_t)(mlp_NT(top) * mlp_KT(top) * 2));
+    const int64_t row0 = (int64_t)(blockIdx.x >> 1) * 128, row = row0 + r;
+    const int top = kMlpLayers - 1;
+    if (tid == 0)
+        load_w_rows(sm, pb + 2 * mlp_pT_off(top), mlp_NT(top), mlp_KT(top), mlp_KCT(top), kHalf * (int)rank, kHalf);
     if (part == 0) {
         float a[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) a[j] = (j < 6 && row < B) ? __ldg(dy + row * ld + j) : 0.0f;
 #pragma unroll
         for (int q = 0; q < 2; ++q)
-            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 8 * q, 16)) =
+            *reinterpret_cast<uint4*>(sm.act[0] + tc::kmajor_off(r, 8 * q, 16)) =
                 make_uint4(bf16x2(a[8 * q], a[8 * q + 1]), bf16x2(a[8 * q + 2], a[8 * q + 3]),
                            bf16x2(a[8 * q + 4], a[8 * q + 5]), bf16x2(a[8 * q + 6], a[8 * q + 7]));
     }
@@ -391,53 +489,58 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
     uint32_t ph_w = 0, ph_m = 0;
     int failed = 0;
     const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
-    for (int l = top; l >= lmin; --l) {
-        if (l >= 1) {
-            // this thread's silu'(z_{l-1}) (two 128-byte lines) toward L1
-            // while the tensor core works
-            const float* S = ws.S[l - 1] + row * 256 + 64 * part;
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(S));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(S + 32));
-        }
-        failed = run_layer(sm, tbase, mlp_NT(l), mlp_KT(l), mlp_KCT(l), ph_w, ph_m);
+    const int f_loc = 32 * part, f_glob = kHalf * (int)rank + f_loc;   // this thread's 32 features
+    int n_sig = 0;   // partner signals expected so far
+    // layers 4..1 on both CTAs, half the input features each
+    for (int l = top; l >= 1; --l) {
+        const int buf = (top - l) & 1;
+        // this thread's silu'(z_{l-1}) (one 128-byte line) toward L1 while
+        // the tensor core works
+        const float* S = ws.S[l - 1] + row * 256 + f_glob;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(S));
+        failed = run_layer(sm, tbase, buf, kHalf, mlp_KT(l), mlp_KCT(l), n_sig - 1, ph_w, ph_m);
         if (failed) break;
-        if (tid == 0 && l - 1 >= lmin) load_w(sm, pb + 2 * mlp_pT_off(l - 1), (uint32_t)(mlp_NT(l - 1) * mlp_KT(l - 1) * 2));
-        if (l >= 1) {
-            // dL/dz_{l-1} = (dL/dz_l W_l) * silu'(z_{l-1})
-            const float* S = ws.S[l - 1] + row * 256;
-#pragma unroll 1
-            for (int cc = 2 * part; cc < 2 * part + 2; ++cc) {
-                float v[32];
-                tc::tmem_ld32(taddr + 32u * (uint32_t)cc, v);
+        if (tid == 0) {
+            if (l - 1 >= 1)
+                load_w_rows(sm, pb + 2 * mlp_pT_off(l - 1), mlp_NT(l - 1), mlp_KT(l - 1), mlp_KCT(l - 1),
+                            kHalf * (int)rank, kHalf);
+            else if (mode == 1 && rank == 0)
+                load_w_rows(sm, pb + 2 * mlp_pT_off(0), mlp_NT(0), mlp_KT(0), mlp_KCT(0), 0, mlp_NT(0));
+        }
+        // dL/dz_{l-1} = (dL/dz_l W_l) * silu'(z_{l-1})
+        float v[32];
+        tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float4 s4 = __ldg(reinterpret_cast<const float4*>(S + 32 * cc) + q);
-                    v[4 * q] *= s4.x; v[4 * q + 1] *= s4.y; v[4 * q + 2] *= s4.z; v[4 * q + 3] *= s4.w;
-                }
-                uint32_t pk[16];
+        for (int q = 0; q < 8; ++q) {
+            const float4 s4 = __ldg(reinterpret_cast<const float4*>(S) + q);
+            v[4 * q] *= s4.x; v[4 * q + 1] *= s4.y; v[4 * q + 2] *= s4.z; v[4 * q + 3] *= s4.w;
+        }
+        uint32_t pk[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) pk[j] = bf16x2(v[2 * j], v[2 * j + 1]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, 32 * cc + 8 * q, 256)) =
-                        make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-                if (mode == 0) {
-                    store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.DZT[l - 1]),
-                                       32 * cc, row0 + 32 * quarter, Bp);
-                    // bias gradient of layer l-1: this warp's 32 rows, column 32 cc + lane
-                    const float cs = warp_colsum32(v, lane);
-                    atomicAdd(&sm.colsum[32 * cc + lane], cs);
-                }
+        for (int j = 0; j < 16; ++j) pk[j] = bf16x2(v[2 * j], v[2 * j + 1]);
+        put_act(sm.act[buf ^ 1], pk, r, f_glob, peer);
+        if (mode == 0) {
+            store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.DZT[l - 1]), f_glob,
+                               row0 + 32 * quarter, Bp);
+            // bias gradient of layer l-1: this warp's 32 rows, column f_loc + lane
+            const float cs = warp_colsum32(v, lane);
+            atomicAdd(&sm.colsum[f_loc + lane], cs);
+        }
+        signal_peer(sm, peer, n_sig);   // (its __syncthreads also orders the colsum adds)
+        ++n_sig;
+        if (mode == 0) {
+            for (int c = tid; c < kHalf; c += kTrThreads) {
+                atomicAdd(grad + L.b_off[l - 1] + kHalf * (int)rank + c, sm.colsum[c]);
+                sm.colsum[c] = 0.0f;
             }
-            if (mode == 0) {
-                __syncthreads();
-                for (int c = tid; c < 256; c += kTrThreads) {
-                    atomicAdd(grad + L.b_off[l - 1] + c, sm.colsum[c]);
-                    sm.colsum[c] = 0.0f;
-                }
-            }
-        } else if (part == 0) {
-            // input gradient (warps 0-3): gx = dL/dz_0 W_0 (19 of the 32 columns)
+        }
+    }
+    int last_peer_k = failed ? -1 : n_sig - 1;
+    if (!failed && mode == 1 && rank == 0) {
+        // input gradient on rank 0: gx = dL/dz_0 W_0 (19 of the 32 columns)
+        failed = run_layer(sm, tbase, (top - 0) & 1, mlp_NT(0), mlp_KT(0), mlp_KCT(0), n_sig - 1, ph_w, ph_m);
+        last_peer_k = -1;
+        if (!failed && part == 0) {
             float v[32];
             tc::tmem_ld32(taddr, v);
             if (row < B) {
@@ -445,11 +548,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_bwd_kernel(const float* _
                 for (int j = 0; j < 19; ++j) gx[row * 19 + j] = v[j];
             }
         }
-        tc::tc_fence_before();
-        tc::fence_async_smem();
-        __syncthreads();
     }
-    train_teardown(sm, tbase, failed, ph_w, ph_m, err);
+    train_teardown(sm, tbase, failed, ph_w, ph_m, last_peer_k, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -647,10 +747,10 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     const TrainWS ws = train_carve(work, B);
     if ((e = cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws.loss, 0, sizeof(float), st)) != cudaSuccess) return e;
-    const unsigned tiles = (unsigned)(Bp / 128);
+    const unsigned ctas = (unsigned)(2 * (Bp / 128));   // a cluster of two CTAs per 128-row tile
     const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
-    train_fwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(x, tgt, B, Bp, pk, params, ws, grad, 0, err);
-    train_bwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err);
+    train_fwd_kernel<<<ctas, kTrThreads, sizeof(TrainSmem), st>>>(x, tgt, B, Bp, pk, params, ws, grad, 0, err);
+    train_bwd_kernel<<<ctas, kTrThreads, sizeof(TrainSmem), st>>>(ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err);
     const int nks = (int)(((Bp >> 6) + kDwSlice - 1) / kDwSlice);
     train_dw_kernel<<<(unsigned)(kMlpLayers * 2 * nks), kDwThreads, sizeof(DwSmem), st>>>(Bp, nks, ws, grad, err);
     if (lr > 0.0f) {
@@ -670,10 +770,10 @@ cudaError_t mlp_input_grad(const float* x, const float* wy, int64_t B, const flo
     if (e != cudaSuccess) return e;
     const int64_t Bp = train_bp(B);
     const TrainWS ws = train_carve(work, B);
-    const unsigned tiles = (unsigned)(Bp / 128);
+    const unsigned ctas = (unsigned)(2 * (Bp / 128));
     const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
-    train_fwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(x, nullptr, B, Bp, pk, params, ws, nullptr, 1, err);
-    train_bwd_kernel<<<tiles, kTrThreads, sizeof(TrainSmem), st>>>(wy, 6, B, Bp, pk, ws, nullptr, gx, 1, err);
+    train_fwd_kernel<<<ctas, kTrThreads, sizeof(TrainSmem), st>>>(x, nullptr, B, Bp, pk, params, ws, nullptr, 1, err);
+    train_bwd_kernel<<<ctas, kTrThreads, sizeof(TrainSmem), st>>>(wy, 6, B, Bp, pk, ws, nullptr, gx, 1, err);
     return cudaGetLastError();
 }
 
