@@ -138,26 +138,28 @@ __device__ __forceinline__ float warp_colsum32(float (&t)[32], int lane) {
     return t[0];
 }
 
-// A tile's 128 rows are processed by a cluster of two CTAs (one SM each):
-// in every 256-wide layer CTA rank c computes the output features
-// [128 c, 128 c + 128) -- half the MMA N and half the epilogue -- and writes
-// its half of the next layer's BF16 A operand into both CTAs' shared memory
-// (distributed shared memory); each then tells the other, on an mbarrier of
-// the receiving CTA, that its half has landed.  The A operand is double
-// buffered (layer l reads act[l & 1], its epilogue writes act[(l + 1) & 1]),
-// so a CTA never writes into a buffer its partner's tensor core may still
-// read.  The narrow layers (the 6 outputs, the 19 input gradients) run on
-// rank 0 alone.  16 warps per CTA: warp w reads TMEM lane quarter w % 4 (32
-// rows) and the 32 columns 32 (w / 4) ... of the CTA's 128.
+// A tile's 128 rows are processed by one CTA (PAIR = 1) or, when the batch
+// has too few tiles to fill the GPU, by a cluster of two CTAs (PAIR = 2, one
+// SM each): in every 256-wide layer CTA rank c then computes the output
+// features [128 c, 128 c + 128) -- half the MMA N and half the epilogue --
+// and writes its half of the next layer's BF16 A operand into both CTAs'
+// shared memory (distributed shared memory); each then tells the other, on
+// an mbarrier of the receiving CTA, that its half has landed.  The pair's A
+// operand is double buffered (layer l reads act[l & 1], its epilogue writes
+// act[(l + 1) & 1]), so a CTA never writes into a buffer its partner's
+// tensor core may still read.  The narrow layers (the 6 outputs, the 19
+// input gradients) run on rank 0 alone.  16 warps per CTA: warp w reads
+// TMEM lane quarter w % 4 (32 rows) and a quarter of the CTA's columns.
 constexpr int kTrThreads = 512;
 constexpr int kDwThreads = 128;
-constexpr int kHalf = 128;   // output features of a layer per CTA of the pair
 
+template <int PAIR>
 struct TrainSmem {
-    alignas(1024) unsigned char act[2][128 * 256 * 2];   // A operands (2 x 64 KB)
-    alignas(1024) unsigned char w[256 * 128 * 2];        // B operand: this CTA's half of a layer (64 KB)
+    static constexpr int NH = 256 / PAIR;                // output features of a 256-wide layer per CTA
+    alignas(1024) unsigned char act[PAIR][128 * 256 * 2];   // A operand(s) (64 KB each)
+    alignas(1024) unsigned char w[256 * NH * 2];         // B operand: this CTA's share of a layer
     alignas(16) uint16_t scratch[kTrThreads / 32][32 * 32];   // per warp: a 32 x 32 BF16 block being transposed
-    float colsum[kHalf];                                 // bias-gradient sums of the tile
+    float colsum[NH];                                    // bias-gradient sums of the tile
     alignas(8) uint64_t bar_w;
     alignas(8) uint64_t bar_mma;
     alignas(8) uint64_t bar_peer[2];                     // the partner's k-th half of an A operand landed (k & 1)
@@ -205,7 +207,8 @@ __device__ __forceinline__ void cluster_sync() {
 
 // Thread 0: rows [r0, r0 + nr) of each of the K / KC chunks of a packed
 // layer (N x KC K-major tiles) into sm.w, one bulk copy per chunk.
-__device__ __forceinline__ void load_w_rows(TrainSmem& sm, const unsigned char* layer, int N, int K, int KC, int r0,
+template <int PAIR>
+__device__ __forceinline__ void load_w_rows(TrainSmem<PAIR>& sm, const unsigned char* layer, int N, int K, int KC, int r0,
                                             int nr) {
     const uint32_t cb = (uint32_t)(nr * KC * 2);
     tc::mbar_expect_tx(&sm.bar_w, cb * (uint32_t)(K / KC));
@@ -214,9 +217,10 @@ __device__ __forceinline__ void load_w_rows(TrainSmem& sm, const unsigned char* 
 }
 
 // Thread 0: D = A (act[buf], K columns) x B^T (sm.w: N rows, chunks of KC), commit.
-__device__ __forceinline__ void issue_layer(TrainSmem& sm, uint32_t tbase, int buf, int N, int K, int KC) {
+template <int PAIR>
+__device__ __forceinline__ void issue_layer(TrainSmem<PAIR>& sm, uint32_t tbase, int buf, int N, int K, int KC) {
     const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)N);
-    const uint32_t a0 = tc::smem_u32(sm.act[buf]), b0 = tc::smem_u32(sm.w);
+    const uint32_t a0 = tc::smem_u32(sm.act[buf % PAIR]), b0 = tc::smem_u32(sm.w);
     const uint32_t sboA = (uint32_t)(K / 8) * 128u, sboB = (uint32_t)(KC / 8) * 128u;
     for (int kk = 0; kk < K / 16; ++kk) {
         const int c = kk / (KC / 16), j = kk - c * (KC / 16);
@@ -231,7 +235,8 @@ __device__ __forceinline__ void issue_layer(TrainSmem& sm, uint32_t tbase, int b
 // completes its phase k >> 1: the two barriers alternate, so a partner one
 // signal ahead (the most it can be) never advances the barrier being
 // waited on past the phase awaited.
-__device__ __forceinline__ bool wait_peer(TrainSmem& sm, int k) {
+template <int PAIR>
+__device__ __forceinline__ bool wait_peer(TrainSmem<PAIR>& sm, int k) {
     return mbar_wait_cluster_bounded(&sm.bar_peer[k & 1], (uint32_t)(k >> 1) & 1u, kWaitLimit);
 }
 
@@ -240,7 +245,8 @@ __device__ __forceinline__ bool wait_peer(TrainSmem& sm, int k) {
 // operand), then issues the MMAs; everyone waits for them.  Returns 0, or 1
 // (weights or the partner never arrived) / 2 (MMAs never completed) when a
 // bounded wait gave up (block-uniform).
-__device__ __forceinline__ int run_layer(TrainSmem& sm, uint32_t tbase, int buf, int N, int K, int KC, int peer_k,
+template <int PAIR>
+__device__ __forceinline__ int run_layer(TrainSmem<PAIR>& sm, uint32_t tbase, int buf, int N, int K, int KC, int peer_k,
                                          uint32_t& ph_w, uint32_t& ph_m) {
     if (threadIdx.x == 0) {
         bool ok = tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
@@ -261,7 +267,8 @@ __device__ __forceinline__ int run_layer(TrainSmem& sm, uint32_t tbase, int buf,
     return 0;
 }
 
-__device__ __forceinline__ void train_setup(TrainSmem& sm) {
+template <int PAIR>
+__device__ __forceinline__ void train_setup(TrainSmem<PAIR>& sm) {
     if (threadIdx.x == 0) {
         tc::mbar_init(&sm.bar_w, 1);
         tc::mbar_init(&sm.bar_mma, 1);
@@ -270,30 +277,33 @@ __device__ __forceinline__ void train_setup(TrainSmem& sm) {
         tc::fence_mbar_init();
     }
     if (threadIdx.x < 32) {
-        tc::tmem_alloc(&sm.tmem_base, kHalf);
+        tc::tmem_alloc(&sm.tmem_base, TrainSmem<PAIR>::NH);
         tc::tmem_relinquish();
     }
-    for (int i = threadIdx.x; i < kHalf; i += kTrThreads) sm.colsum[i] = 0.0f;
+    for (int i = threadIdx.x; i < TrainSmem<PAIR>::NH; i += kTrThreads) sm.colsum[i] = 0.0f;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    cluster_sync();   // the partner's barriers exist before anyone arrives on them
+    if (PAIR == 2) cluster_sync();   // the partner's barriers exist before anyone arrives on them
 }
 
 // After the epilogue: this CTA's writes (local and into the partner's A
 // buffer) visible to the tensor cores, then the partner gets signal k.
-__device__ __forceinline__ void signal_peer(TrainSmem& sm, uint32_t peer, int k) {
-    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+template <int PAIR>
+__device__ __forceinline__ void signal_peer(TrainSmem<PAIR>& sm, uint32_t peer, int k) {
+    if (PAIR == 2) asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+    else tc::fence_async_smem();
     tc::tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0) mbar_arrive_cluster(peer_addr(&sm.bar_peer[k & 1], peer));
+    if (PAIR == 2 && threadIdx.x == 0) mbar_arrive_cluster(peer_addr(&sm.bar_peer[k & 1], peer));
 }
 
 // End of the kernel: record a failed wait, let the copy or the MMAs in
 // flight land (bounded), wait (bounded) for the partner's last signal so
 // that no write into this CTA's shared memory is still under way, free
 // TMEM, and leave together with the partner.
-__device__ __forceinline__ void train_teardown(TrainSmem& sm, uint32_t tbase, int failed, uint32_t ph_w,
+template <int PAIR>
+__device__ __forceinline__ void train_teardown(TrainSmem<PAIR>& sm, uint32_t tbase, int failed, uint32_t ph_w,
                                                uint32_t ph_m, int last_peer_k, int* err) {
     if (threadIdx.x == 0) {
         if (failed) {
@@ -306,19 +316,20 @@ __device__ __forceinline__ void train_teardown(TrainSmem& sm, uint32_t tbase, in
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    if (threadIdx.x < 32) tc::tmem_dealloc(tbase, kHalf);
-    cluster_sync();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tbase, TrainSmem<PAIR>::NH);
+    if (PAIR == 2) cluster_sync();
 }
 
 // Writes the thread's 32 BF16 values (pk, features f0 .. f0 + 31 of row r)
-// into A buffer `dst` (K = 256 layout) of this CTA and of the partner.
+// into A buffer `dst` (K = 256 layout) of this CTA and of the partner, if any.
+template <int PAIR>
 __device__ __forceinline__ void put_act(unsigned char* dst, const uint32_t (&pk)[16], int r, int f0, uint32_t peer) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         unsigned char* p = dst + tc::kmajor_off((uint32_t)r, (uint32_t)(f0 + 8 * q), 256u);
         const uint4 v = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         *reinterpret_cast<uint4*>(p) = v;
-        st_cluster_v4(peer_addr(p, peer), v);
+        if (PAIR == 2) st_cluster_v4(peer_addr(p, peer), v);
     }
 }
 
@@ -327,21 +338,24 @@ __device__ __forceinline__ void put_act(unsigned char* dst, const uint32_t (&pk)
 // transposed inputs and activations for the weight gradients); mode 1: the
 // input gradient's forward (silu'(z) of the hidden layers only).
 // ---------------------------------------------------------------------------
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrThreads, 1)
+template <int PAIR>
+__global__ void __launch_bounds__(kTrThreads, 1)
     train_fwd_kernel(const float* __restrict__ x, const float* __restrict__ tgt, int64_t B, int64_t Bp,
                      const __nv_bfloat16* __restrict__ packed, const float* __restrict__ params, TrainWS ws,
                      float* __restrict__ grad, int mode, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
+    using Smem = TrainSmem<PAIR>;
+    constexpr int NH = Smem::NH;
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, part = warp >> 2, r = 32 * quarter + lane;
-    const uint32_t rank = cluster_rank(), peer = rank ^ 1u;
+    const uint32_t rank = PAIR == 2 ? cluster_rank() : 0u, peer = rank ^ 1u;
     const MlpLayout L = mlp_layout();
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
-    const int64_t row0 = (int64_t)(blockIdx.x >> 1) * 128, row = row0 + r;
-    if (tid == 0) load_w_rows(sm, pb + 2 * L.p_off[0], mlp_N(0), mlp_K(0), mlp_KC(0), kHalf * (int)rank, kHalf);
+    const int64_t row0 = (int64_t)(blockIdx.x / PAIR) * 128, row = row0 + r;
+    if (tid == 0) load_w_rows(sm, pb + 2 * L.p_off[0], mlp_N(0), mlp_K(0), mlp_KC(0), NH * (int)rank, NH);
     // the tile's inputs (warps 0-3, one row each): BF16 A operand (K = 32,
     // zero padded) in both CTAs, x^T from rank 0
     if (part == 0) {
@@ -368,54 +382,56 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrThreads, 1)
     uint32_t ph_w = 0, ph_m = 0;
     int failed = 0;
     const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
-    const int f_loc = 32 * part, f_glob = kHalf * (int)rank + f_loc;   // this thread's 32 features
-    // hidden layers 0-3 on both CTAs, half the features each
+    // hidden layers 0-3: this CTA's NH features (all of them, or one half)
     for (int l = 0; l < kMlpLayers - 1; ++l) {
-        failed = run_layer(sm, tbase, l & 1, kHalf, mlp_K(l), mlp_KC(l), l - 1, ph_w, ph_m);
+        failed = run_layer(sm, tbase, l & 1, NH, mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m);
         if (failed) break;
         // the weights of layer l are consumed: bring the next layer's
         if (tid == 0) {
             if (l + 1 < kMlpLayers - 1)
-                load_w_rows(sm, pb + 2 * L.p_off[l + 1], mlp_N(l + 1), mlp_K(l + 1), mlp_KC(l + 1), kHalf * (int)rank,
-                            kHalf);
+                load_w_rows(sm, pb + 2 * L.p_off[l + 1], mlp_N(l + 1), mlp_K(l + 1), mlp_KC(l + 1), NH * (int)rank, NH);
             else if (mode == 0 && rank == 0)
                 load_w_rows(sm, pb + 2 * L.p_off[kMlpLayers - 1], mlp_N(kMlpLayers - 1), mlp_K(kMlpLayers - 1),
                             mlp_KC(kMlpLayers - 1), 0, mlp_N(kMlpLayers - 1));
         }
-        const float* bias = params + L.b_off[l] + f_glob;
-        float v[32];
-        tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
-        uint32_t pk[16];
+#pragma unroll 1
+        for (int cc = 0; cc < NH / 128; ++cc) {
+            const int f_loc = (NH / 4) * part + 32 * cc, f_glob = NH * (int)rank + f_loc;   // 32 features
+            const float* bias = params + L.b_off[l] + f_glob;
+            float v[32];
+            tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
+            uint32_t pk[16];
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-            float h[2];
+            for (int j = 0; j < 32; j += 2) {
+                float h[2];
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const float z = v[j + e] + __ldg(bias + j + e);
-                // sigmoid by the hardware exp2 and reciprocal (about 2^-21
-                // relative each, for every z: no cancellation)
-                const float s = __fdividef(1.0f, 1.0f + __expf(-z));
-                h[e] = z * s;
-                v[j + e] = s * (1.0f + z * (1.0f - s));   // silu'(z)
+                for (int e = 0; e < 2; ++e) {
+                    const float z = v[j + e] + __ldg(bias + j + e);
+                    // sigmoid by the hardware exp2 and reciprocal (about 2^-21
+                    // relative each, for every z: no cancellation)
+                    const float s = __fdividef(1.0f, 1.0f + __expf(-z));
+                    h[e] = z * s;
+                    v[j + e] = s * (1.0f + z * (1.0f - s));   // silu'(z)
+                }
+                pk[j / 2] = bf16x2(h[0], h[1]);
             }
-            pk[j / 2] = bf16x2(h[0], h[1]);
-        }
-        float* S = ws.S[l] + row * 256 + f_glob;
+            float* S = ws.S[l] + row * 256 + f_glob;
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            reinterpret_cast<float4*>(S)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        put_act(sm.act[(l + 1) & 1], pk, r, f_glob, peer);
-        if (mode == 0)
-            store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.HT[l + 1]), f_glob,
-                               row0 + 32 * quarter, Bp);
+            for (int q = 0; q < 8; ++q)
+                reinterpret_cast<float4*>(S)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            put_act<PAIR>(sm.act[((l + 1) & 1) % PAIR], pk, r, f_glob, peer);
+            if (mode == 0)
+                store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.HT[l + 1]), f_glob,
+                                   row0 + 32 * quarter, Bp);
+        }
         signal_peer(sm, peer, l);
     }
-    int last_peer_k = failed ? -1 : kMlpLayers - 2;   // the partner's signal of layer 3
+    int last_peer_k = (failed || PAIR == 1) ? -1 : kMlpLayers - 2;   // the partner's signal of layer 3
     if (!failed && mode == 0 && rank == 0) {
         // output layer on rank 0: loss, dL/dy, its transposed BF16 copy,
         // output bias gradient
         const int l = kMlpLayers - 1;
-        failed = run_layer(sm, tbase, l & 1, mlp_N(l), mlp_K(l), mlp_KC(l), l - 1, ph_w, ph_m);
+        failed = run_layer(sm, tbase, l & 1, mlp_N(l), mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m);
         last_peer_k = -1;   // already waited for before the MMAs (or failed)
         if (!failed && part == 0) {
             float v[16];
@@ -457,23 +473,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrThreads, 1)
 // dL/dz_0, transposed dL/dz and bias gradients); mode 1: the input gradient
 // gx = dL/dz_0 W_0 (FP32 [B][19], on rank 0).
 // ---------------------------------------------------------------------------
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrThreads, 1)
+template <int PAIR>
+__global__ void __launch_bounds__(kTrThreads, 1)
     train_bwd_kernel(const float* __restrict__ dy, int ld, int64_t B, int64_t Bp,
                      const __nv_bfloat16* __restrict__ packed, TrainWS ws, float* __restrict__ grad,
                      float* __restrict__ gx, int mode, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
+    using Smem = TrainSmem<PAIR>;
+    constexpr int NH = Smem::NH;
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, part = warp >> 2, r = 32 * quarter + lane;
-    const uint32_t rank = cluster_rank(), peer = rank ^ 1u;
+    const uint32_t rank = PAIR == 2 ? cluster_rank() : 0u, peer = rank ^ 1u;
     const MlpLayout L = mlp_layout();
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
-    const int64_t row0 = (int64_t)(blockIdx.x >> 1) * 128, row = row0 + r;
+    const int64_t row0 = (int64_t)(blockIdx.x / PAIR) * 128, row = row0 + r;
     const int top = kMlpLayers - 1;
     if (tid == 0)
-        load_w_rows(sm, pb + 2 * mlp_pT_off(top), mlp_NT(top), mlp_KT(top), mlp_KCT(top), kHalf * (int)rank, kHalf);
+        load_w_rows(sm, pb + 2 * mlp_pT_off(top), mlp_NT(top), mlp_KT(top), mlp_KCT(top), NH * (int)rank, NH);
     if (part == 0) {
         float a[16];
 #pragma unroll
@@ -489,56 +508,63 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrThreads, 1)
     uint32_t ph_w = 0, ph_m = 0;
     int failed = 0;
     const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
-    const int f_loc = 32 * part, f_glob = kHalf * (int)rank + f_loc;   // this thread's 32 features
     int n_sig = 0;   // partner signals expected so far
-    // layers 4..1 on both CTAs, half the input features each
+    // layers 4..1: this CTA's NH input features (all of them, or one half)
     for (int l = top; l >= 1; --l) {
         const int buf = (top - l) & 1;
-        // this thread's silu'(z_{l-1}) (one 128-byte line) toward L1 while
-        // the tensor core works
-        const float* S = ws.S[l - 1] + row * 256 + f_glob;
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(S));
-        failed = run_layer(sm, tbase, buf, kHalf, mlp_KT(l), mlp_KCT(l), n_sig - 1, ph_w, ph_m);
+        // this thread's silu'(z_{l-1}) lines toward L1 while the tensor core works
+        {
+            const float* S0 = ws.S[l - 1] + row * 256 + NH * (int)rank + (NH / 4) * part;
+#pragma unroll
+            for (int cc = 0; cc < NH / 128; ++cc) asm volatile("prefetch.global.L1 [%0];" ::"l"(S0 + 32 * cc));
+        }
+        failed = run_layer(sm, tbase, buf, NH, mlp_KT(l), mlp_KCT(l), PAIR == 2 ? n_sig - 1 : -1, ph_w, ph_m);
         if (failed) break;
         if (tid == 0) {
             if (l - 1 >= 1)
                 load_w_rows(sm, pb + 2 * mlp_pT_off(l - 1), mlp_NT(l - 1), mlp_KT(l - 1), mlp_KCT(l - 1),
-                            kHalf * (int)rank, kHalf);
+                            NH * (int)rank, NH);
             else if (mode == 1 && rank == 0)
                 load_w_rows(sm, pb + 2 * mlp_pT_off(0), mlp_NT(0), mlp_KT(0), mlp_KCT(0), 0, mlp_NT(0));
         }
-        // dL/dz_{l-1} = (dL/dz_l W_l) * silu'(z_{l-1})
-        float v[32];
-        tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
+#pragma unroll 1
+        for (int cc = 0; cc < NH / 128; ++cc) {
+            const int f_loc = (NH / 4) * part + 32 * cc, f_glob = NH * (int)rank + f_loc;   // 32 features
+            const float* S = ws.S[l - 1] + row * 256 + f_glob;
+            // dL/dz_{l-1} = (dL/dz_l W_l) * silu'(z_{l-1})
+            float v[32];
+            tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float4 s4 = __ldg(reinterpret_cast<const float4*>(S) + q);
-            v[4 * q] *= s4.x; v[4 * q + 1] *= s4.y; v[4 * q + 2] *= s4.z; v[4 * q + 3] *= s4.w;
-        }
-        uint32_t pk[16];
+            for (int q = 0; q < 8; ++q) {
+                const float4 s4 = __ldg(reinterpret_cast<const float4*>(S) + q);
+                v[4 * q] *= s4.x; v[4 * q + 1] *= s4.y; v[4 * q + 2] *= s4.z; v[4 * q + 3] *= s4.w;
+            }
+            uint32_t pk[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) pk[j] = bf16x2(v[2 * j], v[2 * j + 1]);
-        put_act(sm.act[buf ^ 1], pk, r, f_glob, peer);
-        if (mode == 0) {
-            store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.DZT[l - 1]), f_glob,
-                               row0 + 32 * quarter, Bp);
-            // bias gradient of layer l-1: this warp's 32 rows, column f_loc + lane
-            const float cs = warp_colsum32(v, lane);
-            atomicAdd(&sm.colsum[f_loc + lane], cs);
+            for (int j = 0; j < 16; ++j) pk[j] = bf16x2(v[2 * j], v[2 * j + 1]);
+            put_act<PAIR>(sm.act[(buf ^ 1) % PAIR], pk, r, f_glob, peer);
+            if (mode == 0) {
+                store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.DZT[l - 1]), f_glob,
+                                   row0 + 32 * quarter, Bp);
+                // bias gradient of layer l-1: this warp's 32 rows, column f_loc + lane
+                const float cs = warp_colsum32(v, lane);
+                atomicAdd(&sm.colsum[f_loc + lane], cs);
+            }
         }
         signal_peer(sm, peer, n_sig);   // (its __syncthreads also orders the colsum adds)
         ++n_sig;
         if (mode == 0) {
-            for (int c = tid; c < kHalf; c += kTrThreads) {
-                atomicAdd(grad + L.b_off[l - 1] + kHalf * (int)rank + c, sm.colsum[c]);
+            for (int c = tid; c < NH; c += kTrThreads) {
+                atomicAdd(grad + L.b_off[l - 1] + NH * (int)rank + c, sm.colsum[c]);
                 sm.colsum[c] = 0.0f;
             }
         }
     }
-    int last_peer_k = failed ? -1 : n_sig - 1;
+    int last_peer_k = (failed || PAIR == 1) ? -1 : n_sig - 1;
     if (!failed && mode == 1 && rank == 0) {
         // input gradient on rank 0: gx = dL/dz_0 W_0 (19 of the 32 columns)
-        failed = run_layer(sm, tbase, (top - 0) & 1, mlp_NT(0), mlp_KT(0), mlp_KCT(0), n_sig - 1, ph_w, ph_m);
+        failed = run_layer(sm, tbase, (top - 0) & 1, mlp_NT(0), mlp_KT(0), mlp_KCT(0), PAIR == 2 ? n_sig - 1 : -1, ph_w,
+                           ph_m);
         last_peer_k = -1;
         if (!failed && part == 0) {
             float v[32];
@@ -728,14 +754,62 @@ __global__ void adam_pack_kernel(float* __restrict__ p, const float* __restrict_
 static cudaError_t train_attrs() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(TrainSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
+    cudaError_t e = cudaSuccess;
+    const void* f[4] = {(const void*)train_fwd_kernel<1>, (const void*)train_bwd_kernel<1>,
+                        (const void*)train_fwd_kernel<2>, (const void*)train_bwd_kernel<2>};
+    const int sz[4] = {(int)sizeof(TrainSmem<1>), (int)sizeof(TrainSmem<1>), (int)sizeof(TrainSmem<2>),
+                       (int)sizeof(TrainSmem<2>)};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        e = cudaFuncSetAttribute(f[i], cudaFuncAttributeMaxDynamicSharedMemorySize, sz[i]);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(train_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DwSmem));
     if (e == cudaSuccess) done = true;
     return e;
+}
+
+// Pairs (two-CTA clusters) when the batch's tiles leave at least half the
+// SMs idle, one CTA per tile otherwise.
+static int train_pair(int64_t Bp) {
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return 2 * (Bp / 128) <= n_sm ? 2 : 1;
+}
+
+template <typename... Args>
+static cudaError_t launch_pairs(void (*kern)(Args...), unsigned tiles, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * tiles);
+    cfg.blockDim = dim3(kTrThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+static cudaError_t launch_fwd(int pair, unsigned tiles, cudaStream_t st, const float* x, const float* tgt, int64_t B,
+                              int64_t Bp, const __nv_bfloat16* pk, const float* params, const TrainWS& ws, float* grad,
+                              int mode, int* err) {
+    if (pair == 2)
+        return launch_pairs(train_fwd_kernel<2>, tiles, sizeof(TrainSmem<2>), st, x, tgt, B, Bp, pk, params, ws, grad,
+                            mode, err);
+    train_fwd_kernel<1><<<tiles, kTrThreads, sizeof(TrainSmem<1>), st>>>(x, tgt, B, Bp, pk, params, ws, grad, mode, err);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_bwd(int pair, unsigned tiles, cudaStream_t st, const float* dy, int ld, int64_t B, int64_t Bp,
+                              const __nv_bfloat16* pk, const TrainWS& ws, float* grad, float* gx, int mode, int* err) {
+    if (pair == 2)
+        return launch_pairs(train_bwd_kernel<2>, tiles, sizeof(TrainSmem<2>), st, dy, ld, B, Bp, pk, ws, grad, gx, mode,
+                            err);
+    train_bwd_kernel<1><<<tiles, kTrThreads, sizeof(TrainSmem<1>), st>>>(dy, ld, B, Bp, pk, ws, grad, gx, mode, err);
+    return cudaGetLastError();
 }
 
 // One optimisation step; grad receives dL/dparams; Adam applied when lr > 0.
@@ -747,10 +821,11 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     const TrainWS ws = train_carve(work, B);
     if ((e = cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws.loss, 0, sizeof(float), st)) != cudaSuccess) return e;
-    const unsigned ctas = (unsigned)(2 * (Bp / 128));   // a cluster of two CTAs per 128-row tile
+    const unsigned tiles = (unsigned)(Bp / 128);
+    const int pair = train_pair(Bp);
     const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
-    train_fwd_kernel<<<ctas, kTrThreads, sizeof(TrainSmem), st>>>(x, tgt, B, Bp, pk, params, ws, grad, 0, err);
-    train_bwd_kernel<<<ctas, kTrThreads, sizeof(TrainSmem), st>>>(ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err);
+    if ((e = launch_fwd(pair, tiles, st, x, tgt, B, Bp, pk, params, ws, grad, 0, err)) != cudaSuccess) return e;
+    if ((e = launch_bwd(pair, tiles, st, ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err)) != cudaSuccess) return e;
     const int nks = (int)(((Bp >> 6) + kDwSlice - 1) / kDwSlice);
     train_dw_kernel<<<(unsigned)(kMlpLayers * 2 * nks), kDwThreads, sizeof(DwSmem), st>>>(Bp, nks, ws, grad, err);
     if (lr > 0.0f) {
@@ -770,10 +845,11 @@ cudaError_t mlp_input_grad(const float* x, const float* wy, int64_t B, const flo
     if (e != cudaSuccess) return e;
     const int64_t Bp = train_bp(B);
     const TrainWS ws = train_carve(work, B);
-    const unsigned ctas = (unsigned)(2 * (Bp / 128));
+    const unsigned tiles = (unsigned)(Bp / 128);
+    const int pair = train_pair(Bp);
     const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
-    train_fwd_kernel<<<ctas, kTrThreads, sizeof(TrainSmem), st>>>(x, nullptr, B, Bp, pk, params, ws, nullptr, 1, err);
-    train_bwd_kernel<<<ctas, kTrThreads, sizeof(TrainSmem), st>>>(wy, 6, B, Bp, pk, ws, nullptr, gx, 1, err);
+    if ((e = launch_fwd(pair, tiles, st, x, nullptr, B, Bp, pk, params, ws, nullptr, 1, err)) != cudaSuccess) return e;
+    if ((e = launch_bwd(pair, tiles, st, wy, 6, B, Bp, pk, ws, nullptr, gx, 1, err)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -107,9 +107,12 @@ def _elementwise(g, go, what, el=1e-2, rm=1e-3):
     assert np.sqrt(np.mean(dev ** 2)) <= rm * scale, (what, "rms", np.sqrt(np.mean(dev ** 2)) / scale)
 
 
-def test_training_gradient_parity(srp):
-    """One L1 gradient on 1,000 samples (eight 128-row tiles, the last one
-    ragged) vs the FP64 oracle fed the same BF16 weights and inputs, with
+# 1,000 samples: eight 128-row tiles, the last one ragged, each on a pair of
+# CTAs (two-CTA clusters, half the features each); 12,000 samples: 94 tiles,
+# one CTA each
+@pytest.mark.parametrize("B", [1000, 12000])
+def test_training_gradient_parity(srp, B):
+    """One L1 gradient on B samples vs the FP64 oracle fed the same BF16 weights and inputs, with
     the hidden activations and every back-propagated dL/dz rounded to BF16
     where the kernel's GEMMs consume them (oracle round_act, round_grad).
     Targets sit 0.2-1.0 away from the oracle's outputs on either side, so
@@ -122,7 +125,6 @@ def test_training_gradient_parity(srp):
     p = omlp.init_params(seed=11)
     p = [(W, np.random.default_rng(40 + l).normal(size=b.shape) * 0.1) for l, (W, b) in enumerate(p)]
     net = srp.MLP(ctx, flat(p))
-    B = 1000
     x = inputs(B, seed=5)
     pb = [(omlp.bf16_round(W), b) for W, b in unflat(flat(p))]
     xb = omlp.bf16_round(x)
@@ -171,7 +173,8 @@ def test_training_reduces_loss(srp):
     assert l1 < l0 / 5, (l0, l1)
 
 
-def test_input_gradient_parity(srp):
+@pytest.mark.parametrize("B", [777, 10001])
+def test_input_gradient_parity(srp, B):
     """srp_mlp_grad_input vs the FP64 oracle's input gradient with the same
     BF16 weights and inputs, the hidden activations and each back-propagated
     vector (wy included) rounded to BF16 where the kernel's GEMMs consume
@@ -181,12 +184,13 @@ def test_input_gradient_parity(srp):
     training gradient's: a row's input gradient ends in one dot product per
     element over 256 terms of both signs, so rows whose result cancels to a
     small RMS carry the terms' FP32/BF16 rounding relatively larger (the
-    worst of 777 rows measured 1.1e-2)."""
+    worst of 777 rows measured 1.1e-2).  777 rows run on CTA pairs, 10,001
+    rows (79 tiles) on one CTA per tile."""
     ctx = srp.Context(0)
     p = omlp.init_params(seed=21)
     net = srp.MLP(ctx, flat(p))
-    x = inputs(777, seed=8)
-    wy = np.random.default_rng(3).normal(size=(777, 6)).astype(np.float32)
+    x = inputs(B, seed=8)
+    wy = np.random.default_rng(3).normal(size=(B, 6)).astype(np.float32)
     gx = net.grad_input(x, wy)
     pb = [(omlp.bf16_round(W), b) for W, b in unflat(flat(p))]
     go = omlp.input_grad(omlp.bf16_round(x), pb, wy.astype(np.float64), round_act=True, round_grad=True)
