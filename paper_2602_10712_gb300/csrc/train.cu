@@ -50,7 +50,7 @@ namespace srp {
 // gradient is one contiguous bulk copy.
 // ---------------------------------------------------------------------------
 struct TrainWS {
-    float* S[4];                 // silu'(z_l) [Bp][256] FP32, l = 0..3
+    float* S[4];                 // silu'(z_l), Bp x 256 FP32 in row groups (s_quad), l = 0..3
     __nv_bfloat16* HT[5];        // HT[0] = x^T (R = 32), HT[l] = h_l^T (R = 256)
     __nv_bfloat16* DZT[5];       // (dL/dz_l)^T: l = 0..3 R = 256, l = 4 R = 16 (dL/dy)
     float* dY;                   // dL/dy [Bp][8] FP32 (columns 6, 7 zero)
@@ -82,6 +82,16 @@ static TrainWS train_carve(void* base, int64_t B) {
 }
 
 float* train_loss_ptr(void* work, int64_t B) { return train_carve(work, B).loss; }
+
+// silu'(z) of one layer, Bp x 256 FP32, stored by groups of 32 rows and
+// quads of 4 features: element (row, f) at float
+// ((row / 32) * 64 + f / 4) * 128 + (row % 32) * 4 + f % 4.  The epilogue
+// thread of row r holds 32 consecutive features of its row, so the warp's
+// float4 store (or load) of one quad is 512 contiguous bytes rather than 32
+// lines 1 KB apart.  Returns the quad of (row, f), f a multiple of 4.
+__device__ __forceinline__ float4* s_quad(float* S, int64_t row, int f) {
+    return reinterpret_cast<float4*>(S + (((row >> 5) * 64 + (f >> 2)) * 128 + (row & 31) * 4));
+}
 
 // byte offset of element (row, col) of a tile-blocked X^T with RT-row tiles
 __device__ __forceinline__ size_t tb_off(int row, int64_t col, int RT, int64_t Bp) {
@@ -159,7 +169,7 @@ struct TrainSmem {
     alignas(1024) unsigned char act[PAIR][128 * 256 * 2];   // A operand(s) (64 KB each)
     alignas(1024) unsigned char w[256 * NH * 2];         // B operand: this CTA's share of a layer
     alignas(16) uint16_t scratch[kTrThreads / 32][32 * 32];   // per warp: a 32 x 32 BF16 block being transposed
-    float colsum[NH];                                    // bias-gradient sums of the tile
+    alignas(16) float colsum[NH];   // backward: bias-gradient sums of the tile; forward: this CTA's biases of the layer
     alignas(8) uint64_t bar_w;
     alignas(8) uint64_t bar_mma;
     alignas(8) uint64_t bar_peer[2];                     // the partner's k-th half of an A operand landed (k & 1)
@@ -384,6 +394,13 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     const uint32_t taddr = tbase + ((uint32_t)(32 * quarter) << 16);
     // hidden layers 0-3: this CTA's NH features (all of them, or one half)
     for (int l = 0; l < kMlpLayers - 1; ++l) {
+        // the layer's biases of this CTA's features into shared memory (the
+        // last NH threads; the previous epilogue's reads ended at its
+        // barrier, run_layer's barrier orders these writes before the reads)
+        if (tid >= kTrThreads - NH) {
+            const int c = tid - (kTrThreads - NH);
+            sm.colsum[c] = __ldg(params + L.b_off[l] + NH * (int)rank + c);
+        }
         failed = run_layer(sm, tbase, l & 1, NH, mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m);
         if (failed) break;
         // the weights of layer l are consumed: bring the next layer's
@@ -397,7 +414,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
 #pragma unroll 1
         for (int cc = 0; cc < NH / 128; ++cc) {
             const int f_loc = (NH / 4) * part + 32 * cc, f_glob = NH * (int)rank + f_loc;   // 32 features
-            const float* bias = params + L.b_off[l] + f_glob;
+            const float* bias = sm.colsum + f_loc;
             float v[32];
             tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
             uint32_t pk[16];
@@ -406,7 +423,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
                 float h[2];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const float z = v[j + e] + __ldg(bias + j + e);
+                    const float z = v[j + e] + bias[j + e];
                     // sigmoid by the hardware exp2 and reciprocal (about 2^-21
                     // relative each, for every z: no cancellation)
                     const float s = __fdividef(1.0f, 1.0f + __expf(-z));
@@ -415,10 +432,9 @@ __global__ void __launch_bounds__(kTrThreads, 1)
                 }
                 pk[j / 2] = bf16x2(h[0], h[1]);
             }
-            float* S = ws.S[l] + row * 256 + f_glob;
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                reinterpret_cast<float4*>(S)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                *s_quad(ws.S[l], row, f_glob + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             put_act<PAIR>(sm.act[((l + 1) & 1) % PAIR], pk, r, f_glob, peer);
             if (mode == 0)
                 store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.HT[l + 1]), f_glob,
@@ -512,11 +528,14 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     // layers 4..1: this CTA's NH input features (all of them, or one half)
     for (int l = top; l >= 1; --l) {
         const int buf = (top - l) & 1;
-        // this thread's silu'(z_{l-1}) lines toward L1 while the tensor core works
+        // this thread's silu'(z_{l-1}) of its first 32 features into
+        // registers while the tensor core works (the next 32, if any, load
+        // during the first chunk's stores)
+        float4 s4[8];
         {
-            const float* S0 = ws.S[l - 1] + row * 256 + NH * (int)rank + (NH / 4) * part;
+            const int f0 = NH * (int)rank + (NH / 4) * part;
 #pragma unroll
-            for (int cc = 0; cc < NH / 128; ++cc) asm volatile("prefetch.global.L1 [%0];" ::"l"(S0 + 32 * cc));
+            for (int q = 0; q < 8; ++q) s4[q] = __ldg(s_quad(ws.S[l - 1], row, f0 + 4 * q));
         }
         failed = run_layer(sm, tbase, buf, NH, mlp_KT(l), mlp_KCT(l), PAIR == 2 ? n_sig - 1 : -1, ph_w, ph_m);
         if (failed) break;
@@ -530,14 +549,16 @@ __global__ void __launch_bounds__(kTrThreads, 1)
 #pragma unroll 1
         for (int cc = 0; cc < NH / 128; ++cc) {
             const int f_loc = (NH / 4) * part + 32 * cc, f_glob = NH * (int)rank + f_loc;   // 32 features
-            const float* S = ws.S[l - 1] + row * 256 + f_glob;
             // dL/dz_{l-1} = (dL/dz_l W_l) * silu'(z_{l-1})
             float v[32];
             tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const float4 s4 = __ldg(reinterpret_cast<const float4*>(S) + q);
-                v[4 * q] *= s4.x; v[4 * q + 1] *= s4.y; v[4 * q + 2] *= s4.z; v[4 * q + 3] *= s4.w;
+                v[4 * q] *= s4[q].x; v[4 * q + 1] *= s4[q].y; v[4 * q + 2] *= s4[q].z; v[4 * q + 3] *= s4[q].w;
+            }
+            if (cc + 1 < NH / 128) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s4[q] = __ldg(s_quad(ws.S[l - 1], row, f_glob + 32 + 4 * q));
             }
             uint32_t pk[16];
 #pragma unroll
