@@ -70,6 +70,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// ---- 1-D bulk copy shared -> global (bulk-group completion) ---------------
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// this thread's committed shared -> global copies have read their source
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... and have completed
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // ---- TMEM -----------------------------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {  // one full warp
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
@@ -99,6 +111,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     d |= (uint64_t)1u << 46;  // descriptor version for tcgen05
     return d;                 // base offset 0, relative LBO, layout type 0 (no swizzle)
 }
+// The same descriptor read MN-major (instruction descriptor with
+// kMnMajorA / kMnMajorB): an operand of MN rows by K columns stored as core
+// matrices of 8 K rows x 8 MN elements (16 bytes per K row); element
+// (mn, k) at (mn / 8) * SBO + (k / 8) * LBO + (k % 8) * 16 + (mn % 8) * 2.
+// A K-major tile of R rows by F features, read MN-major with the features as
+// MN and the rows as K, is this with SBO = 128 and LBO = (F / 8) * 128.
+constexpr uint32_t kMnMajorA = 1u << 15;
+constexpr uint32_t kMnMajorB = 1u << 16;
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
     return (1u << 4)            // D format F32

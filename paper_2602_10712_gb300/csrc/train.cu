@@ -9,19 +9,22 @@
 //                     epilogue warps, four per TMEM lane quarter, each on
 //                     64 of the 256 columns);
 //                     the epilogue adds the bias, applies SiLU, writes the
-//                     next layer's BF16 A operand into shared memory, and
-//                     keeps for the backward pass silu'(z) (FP32) and the
-//                     BF16 activations transposed (batch along K); the last
+//                     next layer's BF16 A operand into shared memory and
+//                     keeps silu'(z) (FP32) for the backward pass; each
+//                     layer's A operand is bulk-copied out as it stands (a
+//                     tile image) for the weight gradients; the last
 //                     layer gives the L1 loss, dL/dy = sign(y - t)/B and the
 //                     output bias gradient;
 //   train_bwd_kernel  one CTA per tile: dL/dh = dL/dz W through the layers
 //                     from the top (transposed packed weights), the
 //                     epilogue multiplies by silu'(z), writes the BF16
-//                     operand of the next product, dL/dz transposed, and
-//                     sums the bias gradient over the tile's rows;
+//                     operand of the next product (copied out as a tile
+//                     image of dL/dz) and sums the bias gradient over the
+//                     tile's rows;
 //   train_dw_kernel   the weight gradients dW_l = (dL/dz_l)^T h_l, batch
-//                     along K split over CTAs, bulk-copied double-buffered
-//                     K tiles, FP32 vector atomics into the gradient;
+//                     along K split over CTAs, the tile images read as
+//                     MN-major operands (bulk-copied, double-buffered), FP32
+//                     vector atomics into the gradient;
 //   adam_pack_kernel  Adam, and the updated weights into both BF16 packed
 //                     layouts, when lr > 0.
 // Rounding points (what the oracle's round_act / round_grad reproduce):
@@ -42,17 +45,19 @@
 namespace srp {
 
 // ---------------------------------------------------------------------------
-// Workspace.  Bp = B rounded up to 128.  Transposed matrices X^T [R][Bp]
-// (R features, the batch along K) are stored "tile-blocked": tiles of
-// RT = min(R, 128) rows x 64 batch columns, each a K-major no-swizzle
-// core-matrix tile of RT * 128 bytes, tile (rt, kt) at byte
-// (rt * Bp/64 + kt) * RT * 128 -- so one K tile of an operand of the weight
-// gradient is one contiguous bulk copy.
+// Workspace.  Bp = B rounded up to 128.  The operands of the weight
+// gradients are kept as "tile images": per 128-row batch tile, the BF16
+// A operand of a layer exactly as it sat in shared memory (K-major core
+// matrices, the F features along K: element (r, f) of tile t at byte
+// t * 128 * F * 2 + kmajor_off(r, f, F)), bulk-copied out by the forward and
+// backward kernels.  Rows 64 h .. 64 h + 63 of a tile are one contiguous run
+// of 64 * F * 2 bytes, and the weight-gradient kernel reads such a run MN-major
+// (features along M or N, batch rows along K) -- no transposition anywhere.
 // ---------------------------------------------------------------------------
 struct TrainWS {
     float* S[4];                 // silu'(z_l), Bp x 256 FP32 in row groups (s_quad), l = 0..3
-    __nv_bfloat16* HT[5];        // HT[0] = x^T (R = 32), HT[l] = h_l^T (R = 256)
-    __nv_bfloat16* DZT[5];       // (dL/dz_l)^T: l = 0..3 R = 256, l = 4 R = 16 (dL/dy)
+    __nv_bfloat16* Him[5];       // tile images of the layer inputs: Him[0] = x (F = 32), Him[l] = h_l (F = 256)
+    __nv_bfloat16* DZim[5];      // tile images of dL/dz_l (F = 256), DZim[4] = dL/dy (F = 16)
     float* dY;                   // dL/dy [Bp][8] FP32 (columns 6, 7 zero)
     float* loss;                 // [1]
 };
@@ -72,10 +77,10 @@ static TrainWS train_carve(void* base, int64_t B) {
     unsigned char* q = (unsigned char*)base;
     TrainWS w;
     for (int l = 0; l < 4; ++l) { w.S[l] = (float*)q; q += al1k(Bp * 256 * 4); }
-    w.HT[0] = (__nv_bfloat16*)q; q += al1k(32 * Bp * 2);
-    for (int l = 1; l < 5; ++l) { w.HT[l] = (__nv_bfloat16*)q; q += al1k(256 * Bp * 2); }
-    for (int l = 0; l < 4; ++l) { w.DZT[l] = (__nv_bfloat16*)q; q += al1k(256 * Bp * 2); }
-    w.DZT[4] = (__nv_bfloat16*)q; q += al1k(16 * Bp * 2);
+    w.Him[0] = (__nv_bfloat16*)q; q += al1k(32 * Bp * 2);
+    for (int l = 1; l < 5; ++l) { w.Him[l] = (__nv_bfloat16*)q; q += al1k(256 * Bp * 2); }
+    for (int l = 0; l < 4; ++l) { w.DZim[l] = (__nv_bfloat16*)q; q += al1k(256 * Bp * 2); }
+    w.DZim[4] = (__nv_bfloat16*)q; q += al1k(16 * Bp * 2);
     w.dY = (float*)q; q += al1k(Bp * 8 * 4);
     w.loss = (float*)q;
     return w;
@@ -93,43 +98,10 @@ __device__ __forceinline__ float4* s_quad(float* S, int64_t row, int f) {
     return reinterpret_cast<float4*>(S + (((row >> 5) * 64 + (f >> 2)) * 128 + (row & 31) * 4));
 }
 
-// byte offset of element (row, col) of a tile-blocked X^T with RT-row tiles
-__device__ __forceinline__ size_t tb_off(int row, int64_t col, int RT, int64_t Bp) {
-    const int rt = row / RT, r = row - rt * RT;
-    const int64_t kt = col >> 6;
-    return ((size_t)rt * (size_t)(Bp >> 6) + (size_t)kt) * (size_t)(RT * 128) +
-           tc::kmajor_off((uint32_t)r, (uint32_t)(col & 63), 64u);
-}
-__device__ __forceinline__ void st_bf16(__nv_bfloat16* base, size_t byte_off, float v) {
-    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(base) + byte_off) = __float2bfloat16_rn(v);
-}
 __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
     uint32_t p;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(hi), "f"(lo));
     return p;
-}
-
-// The warp's 32 rows (lanes) x 32 features (pk: BF16 pairs of the lane's
-// row) into the tile-blocked transposed store: through the warp's shared
-// scratch, so that each lane writes whole 16-byte runs (8 consecutive batch
-// rows of one feature) instead of 32 scattered 2-byte values.  Scratch slot
-// of (feature f, row r): f * 32 + (r ^ (((f >> 1) & 3) << 3)), which keeps
-// both the 2-byte writes (a feature's 32 rows) and the 16-byte reads (eight
-// features' row group q) free of bank conflicts.  f0: first feature, r0:
-// first batch row of the warp (a multiple of 32).
-__device__ __forceinline__ void store_transposed32(uint16_t* sc, const uint32_t (&pk)[16], int lane,
-                                                   unsigned char* dst, int f0, int64_t r0, int64_t Bp) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-        sc[j * 32 + (lane ^ (((j >> 1) & 3) << 3))] = (uint16_t)(pk[j / 2] >> (16 * (j & 1)));
-    __syncwarp();
-    const int f = lane;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint4 v = *reinterpret_cast<const uint4*>(sc + f * 32 + ((q ^ ((f >> 1) & 3)) << 3));
-        *reinterpret_cast<uint4*>(dst + tb_off(f0 + f, r0 + 8 * q, 128, Bp)) = v;
-    }
-    __syncwarp();
 }
 
 // Warp transpose-reduction: lane c ends with the sum over the warp's 32
@@ -160,6 +132,10 @@ __device__ __forceinline__ float warp_colsum32(float (&t)[32], int lane) {
 // tensor core may still read.  The narrow layers (the 6 outputs, the 19
 // input gradients) run on rank 0 alone.  16 warps per CTA: warp w reads
 // TMEM lane quarter w % 4 (32 rows) and a quarter of the CTA's columns.
+// Once a layer's MMAs are issued, the thread that issued them also copies
+// the A operand out to its tile image (rank c of a pair: rows 64 c ..
+// 64 c + 63), and waits for that copy to have read shared memory before the
+// epilogue may write into it again.
 constexpr int kTrThreads = 512;
 constexpr int kDwThreads = 128;
 
@@ -168,7 +144,6 @@ struct TrainSmem {
     static constexpr int NH = 256 / PAIR;                // output features of a 256-wide layer per CTA
     alignas(1024) unsigned char act[PAIR][128 * 256 * 2];   // A operand(s) (64 KB each)
     alignas(1024) unsigned char w[256 * NH * 2];         // B operand: this CTA's share of a layer
-    alignas(16) uint16_t scratch[kTrThreads / 32][32 * 32];   // per warp: a 32 x 32 BF16 block being transposed
     alignas(16) float colsum[NH];   // backward: bias-gradient sums of the tile; forward: this CTA's biases of the layer
     alignas(8) uint64_t bar_w;
     alignas(8) uint64_t bar_mma;
@@ -250,14 +225,32 @@ __device__ __forceinline__ bool wait_peer(TrainSmem<PAIR>& sm, int k) {
     return mbar_wait_cluster_bounded(&sm.bar_peer[k & 1], (uint32_t)(k >> 1) & 1u, kWaitLimit);
 }
 
+// Copy-out of an A operand into its tile image: `bytes` from byte `off` of
+// the buffer to img + off (img null: none).
+struct ImgCopy {
+    unsigned char* img;
+    uint32_t off, bytes;
+};
+
+// The copy-out of a tile's A operand (F features) into image `img`: the
+// whole tile, or (pairs) rank c's rows 64 c .. 64 c + 63.
+template <int PAIR>
+__device__ __forceinline__ ImgCopy img_copy(__nv_bfloat16* img, int64_t tile, int F, uint32_t rank, bool whole) {
+    unsigned char* base = reinterpret_cast<unsigned char*>(img) + (size_t)tile * 128 * F * 2;
+    const uint32_t half = 64u * (uint32_t)F * 2u;
+    if (PAIR == 1 || whole) return ImgCopy{base, 0u, 2u * half};
+    return ImgCopy{base, rank * half, half};
+}
+
 // The per-layer handshake: thread 0 waits for the weights and, when
 // `peer_k` >= 0, for the partner's signal peer_k (its half of the A
-// operand), then issues the MMAs; everyone waits for them.  Returns 0, or 1
-// (weights or the partner never arrived) / 2 (MMAs never completed) when a
+// operand), issues the MMAs and the copy-out `cp`; everyone waits for the
+// MMAs (thread 0 also for the copy to have read its source).  Returns 0, or
+// 1 (weights or the partner never arrived) / 2 (MMAs never completed) when a
 // bounded wait gave up (block-uniform).
 template <int PAIR>
 __device__ __forceinline__ int run_layer(TrainSmem<PAIR>& sm, uint32_t tbase, int buf, int N, int K, int KC, int peer_k,
-                                         uint32_t& ph_w, uint32_t& ph_m) {
+                                         uint32_t& ph_w, uint32_t& ph_m, ImgCopy cp = ImgCopy{nullptr, 0u, 0u}) {
     if (threadIdx.x == 0) {
         bool ok = tc::mbar_wait_bounded(&sm.bar_w, ph_w, kWaitLimit);
         if (ok && peer_k >= 0) ok = wait_peer(sm, peer_k);
@@ -265,12 +258,17 @@ __device__ __forceinline__ int run_layer(TrainSmem<PAIR>& sm, uint32_t tbase, in
         if (ok) {
             tc::tc_fence_after();
             issue_layer(sm, tbase, buf, N, K, KC);
+            if (cp.img) {
+                tc::bulk_s2g(cp.img + cp.off, sm.act[buf % PAIR] + cp.off, cp.bytes);
+                tc::bulk_commit();
+            }
         }
     }
     __syncthreads();
     if (sm.fail) return 1;
     ph_w ^= 1u;
     const bool ok = tc::mbar_wait_bounded(&sm.bar_mma, ph_m, kWaitLimit);
+    if (threadIdx.x == 0 && cp.img) tc::bulk_wait_read0();
     ph_m ^= 1u;
     if (__syncthreads_or(!ok)) return 2;
     tc::tc_fence_after();
@@ -322,6 +320,7 @@ __device__ __forceinline__ void train_teardown(TrainSmem<PAIR>& sm, uint32_t tba
             else tc::mbar_wait_bounded(&sm.bar_mma, ph_m ^ 1u, kWaitLimit);
         }
         if (last_peer_k >= 0 && !wait_peer(sm, last_peer_k)) atomicOr(err, kErrWaitTimeout);
+        tc::bulk_wait0();   // the tile-image copies have landed
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -345,8 +344,8 @@ __device__ __forceinline__ void put_act(unsigned char* dst, const uint32_t (&pk)
 
 // ---------------------------------------------------------------------------
 // Forward.  mode 0: training (targets t: loss, dL/dy, output bias gradient,
-// transposed inputs and activations for the weight gradients); mode 1: the
-// input gradient's forward (silu'(z) of the hidden layers only).
+// tile images of the inputs and activations for the weight gradients);
+// mode 1: the input gradient's forward (silu'(z) of the hidden layers only).
 // ---------------------------------------------------------------------------
 template <int PAIR>
 __global__ void __launch_bounds__(kTrThreads, 1)
@@ -364,10 +363,10 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
-    const int64_t row0 = (int64_t)(blockIdx.x / PAIR) * 128, row = row0 + r;
+    const int64_t tile = blockIdx.x / PAIR, row = tile * 128 + r;
     if (tid == 0) load_w_rows(sm, pb + 2 * L.p_off[0], mlp_N(0), mlp_K(0), mlp_KC(0), NH * (int)rank, NH);
     // the tile's inputs (warps 0-3, one row each): BF16 A operand (K = 32,
-    // zero padded) in both CTAs, x^T from rank 0
+    // zero padded) in both CTAs
     if (part == 0) {
         float v[19];
 #pragma unroll
@@ -381,10 +380,6 @@ __global__ void __launch_bounds__(kTrThreads, 1)
                 u[j] = bf16x2(k < 19 ? v[k] : 0.0f, k + 1 < 19 ? v[k + 1] : 0.0f);
             }
             *reinterpret_cast<uint4*>(sm.act[0] + tc::kmajor_off(r, 8 * q, 32)) = make_uint4(u[0], u[1], u[2], u[3]);
-        }
-        if (mode == 0 && rank == 0) {
-#pragma unroll
-            for (int f = 0; f < 32; ++f) st_bf16(ws.HT[0], tb_off(f, row, 32, Bp), f < 19 ? v[f] : 0.0f);
         }
     }
     tc::fence_async_smem();
@@ -401,7 +396,8 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             const int c = tid - (kTrThreads - NH);
             sm.colsum[c] = __ldg(params + L.b_off[l] + NH * (int)rank + c);
         }
-        failed = run_layer(sm, tbase, l & 1, NH, mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m);
+        const ImgCopy cp = mode == 0 ? img_copy<PAIR>(ws.Him[l], tile, mlp_K(l), rank, false) : ImgCopy{nullptr, 0u, 0u};
+        failed = run_layer(sm, tbase, l & 1, NH, mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m, cp);
         if (failed) break;
         // the weights of layer l are consumed: bring the next layer's
         if (tid == 0) {
@@ -436,18 +432,16 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             for (int q = 0; q < 8; ++q)
                 *s_quad(ws.S[l], row, f_glob + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             put_act<PAIR>(sm.act[((l + 1) & 1) % PAIR], pk, r, f_glob, peer);
-            if (mode == 0)
-                store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.HT[l + 1]), f_glob,
-                                   row0 + 32 * quarter, Bp);
         }
         signal_peer(sm, peer, l);
     }
     int last_peer_k = (failed || PAIR == 1) ? -1 : kMlpLayers - 2;   // the partner's signal of layer 3
     if (!failed && mode == 0 && rank == 0) {
-        // output layer on rank 0: loss, dL/dy, its transposed BF16 copy,
-        // output bias gradient
+        // output layer on rank 0 (the image of its whole input tile too):
+        // loss, dL/dy, output bias gradient
         const int l = kMlpLayers - 1;
-        failed = run_layer(sm, tbase, l & 1, mlp_N(l), mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m);
+        failed = run_layer(sm, tbase, l & 1, mlp_N(l), mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m,
+                           img_copy<PAIR>(ws.Him[l], tile, mlp_K(l), rank, true));
         last_peer_k = -1;   // already waited for before the MMAs (or failed)
         if (!failed && part == 0) {
             float v[16];
@@ -467,8 +461,6 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             reinterpret_cast<float4*>(ws.dY + row * 8)[0] = make_float4(dy[0], dy[1], dy[2], dy[3]);
             reinterpret_cast<float4*>(ws.dY + row * 8)[1] = make_float4(dy[4], dy[5], dy[6], dy[7]);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) st_bf16(ws.DZT[4], tb_off(j, row, 16, Bp), j < 6 ? dy[j] : 0.0f);
-#pragma unroll
             for (int j = 0; j < 6; ++j) {
                 float sdy = dy[j];
 #pragma unroll
@@ -486,7 +478,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
 // ---------------------------------------------------------------------------
 // Backward.  dy: dL/dy rows (ld floats per row; training: the forward's dY,
 // input gradient: the caller's weights wy).  mode 0: training (down to
-// dL/dz_0, transposed dL/dz and bias gradients); mode 1: the input gradient
+// dL/dz_0, tile images of dL/dz and bias gradients); mode 1: the input gradient
 // gx = dL/dz_0 W_0 (FP32 [B][19], on rank 0).
 // ---------------------------------------------------------------------------
 template <int PAIR>
@@ -505,7 +497,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
-    const int64_t row0 = (int64_t)(blockIdx.x / PAIR) * 128, row = row0 + r;
+    const int64_t tile = blockIdx.x / PAIR, row = tile * 128 + r;
     const int top = kMlpLayers - 1;
     if (tid == 0)
         load_w_rows(sm, pb + 2 * mlp_pT_off(top), mlp_NT(top), mlp_KT(top), mlp_KCT(top), NH * (int)rank, NH);
@@ -537,7 +529,8 @@ __global__ void __launch_bounds__(kTrThreads, 1)
 #pragma unroll
             for (int q = 0; q < 8; ++q) s4[q] = __ldg(s_quad(ws.S[l - 1], row, f0 + 4 * q));
         }
-        failed = run_layer(sm, tbase, buf, NH, mlp_KT(l), mlp_KCT(l), PAIR == 2 ? n_sig - 1 : -1, ph_w, ph_m);
+        const ImgCopy cp = mode == 0 ? img_copy<PAIR>(ws.DZim[l], tile, mlp_KT(l), rank, false) : ImgCopy{nullptr, 0u, 0u};
+        failed = run_layer(sm, tbase, buf, NH, mlp_KT(l), mlp_KCT(l), PAIR == 2 ? n_sig - 1 : -1, ph_w, ph_m, cp);
         if (failed) break;
         if (tid == 0) {
             if (l - 1 >= 1)
@@ -565,8 +558,6 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             for (int j = 0; j < 16; ++j) pk[j] = bf16x2(v[2 * j], v[2 * j + 1]);
             put_act<PAIR>(sm.act[(buf ^ 1) % PAIR], pk, r, f_glob, peer);
             if (mode == 0) {
-                store_transposed32(sm.scratch[warp], pk, lane, reinterpret_cast<unsigned char*>(ws.DZT[l - 1]), f_glob,
-                                   row0 + 32 * quarter, Bp);
                 // bias gradient of layer l-1: this warp's 32 rows, column f_loc + lane
                 const float cs = warp_colsum32(v, lane);
                 atomicAdd(&sm.colsum[f_loc + lane], cs);
@@ -582,6 +573,20 @@ __global__ void __launch_bounds__(kTrThreads, 1)
         }
     }
     int last_peer_k = (failed || PAIR == 1) ? -1 : n_sig - 1;
+    if (!failed && mode == 0) {
+        // the image of dL/dz_0 (no MMA consumes it here): once the
+        // partner's half has landed, thread 0 copies it out
+        if (tid == 0) {
+            const bool ok = PAIR == 1 || wait_peer(sm, n_sig - 1);
+            if (!ok) atomicOr(err, kErrWaitTimeout);
+            if (ok) {
+                const ImgCopy cp = img_copy<PAIR>(ws.DZim[0], tile, 256, rank, false);
+                tc::bulk_s2g(cp.img + cp.off, sm.act[(top & 1) % PAIR] + cp.off, cp.bytes);
+                tc::bulk_commit();
+            }
+        }
+        last_peer_k = -1;
+    }
     if (!failed && mode == 1 && rank == 0) {
         // input gradient on rank 0: gx = dL/dz_0 W_0 (19 of the 32 columns)
         failed = run_layer(sm, tbase, (top - 0) & 1, mlp_NT(0), mlp_KT(0), mlp_KCT(0), PAIR == 2 ? n_sig - 1 : -1, ph_w,
@@ -600,11 +605,17 @@ __global__ void __launch_bounds__(kTrThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradients.  Work item (layer l, M tile mt, K slice ks):
-//   l = 0..3: dW_l[o][i] += sum_r dZT_l[o][r] HT_l[i][r]   (M = o, N = i)
-//   l = 4:    dW_4[o][i] += sum_r HT_4[i][r] DZT_4[o][r]    (M = i, N = o:
+// Weight gradients.  Work item (layer l, M tile mt, K slice ks), the batch
+// rows as the K of the product, both operands read MN-major from the tile
+// images (features along M or N):
+//   l = 0..3: dW_l[o][i] += sum_r dZ_l[r][o] H_l[r][i]    (M = o, N = i)
+//   l = 4:    dW_4[o][i] += sum_r H_4[r][i] dY[r][o]      (M = i, N = o:
 //             the 6 outputs fit an N = 16 tile; stored transposed)
-// over the batch columns of K slice ks (kDwSlice tiles of 64).
+// over the rows of K slice ks (kDwSlice chunks of 64 rows).  One chunk of
+// an image (64 rows x F features) is 8 row groups of F * 16 bytes; the A
+// operand takes the 2 KB of features [128 mt, 128 mt + 128) from each
+// (8 bulk copies, SBO 128, LBO 2 KB in shared memory), the B operand the
+// whole chunk (one copy, SBO 128, LBO F * 16).
 // ---------------------------------------------------------------------------
 constexpr int kDwSlice = 8;
 
@@ -618,23 +629,22 @@ struct DwSmem {
 };
 
 struct DwItem {
-    const unsigned char* A;   // tile-blocked, RT = 128
-    const unsigned char* Bm;  // tile-blocked, RT = min(N, 128)
-    int N, RTb;
+    const unsigned char* A;   // image, F = 256
+    const unsigned char* Bm;  // image, F = N
+    int N;
 };
 
 __device__ __forceinline__ DwItem dw_item(const TrainWS& ws, int l) {
     DwItem it;
     if (l < 4) {
-        it.A = reinterpret_cast<const unsigned char*>(ws.DZT[l]);
-        it.Bm = reinterpret_cast<const unsigned char*>(ws.HT[l]);
+        it.A = reinterpret_cast<const unsigned char*>(ws.DZim[l]);
+        it.Bm = reinterpret_cast<const unsigned char*>(ws.Him[l]);
         it.N = l == 0 ? 32 : 256;
     } else {
-        it.A = reinterpret_cast<const unsigned char*>(ws.HT[4]);
-        it.Bm = reinterpret_cast<const unsigned char*>(ws.DZT[4]);
+        it.A = reinterpret_cast<const unsigned char*>(ws.Him[4]);
+        it.Bm = reinterpret_cast<const unsigned char*>(ws.DZim[4]);
         it.N = 16;
     }
-    it.RTb = it.N < 128 ? it.N : 128;
     return it;
 }
 
@@ -662,19 +672,19 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = sm.tmem_base;
-    const uint32_t abytes = 128u * 128u, bbytes = (uint32_t)it.RTb * 128u;
-    const int nbt = it.N / it.RTb;   // B row tiles (2 for N = 256)
+    const uint32_t a_chunk = 64u * 256u * 2u, b_chunk = 64u * (uint32_t)it.N * 2u;   // image bytes per 64 rows
+    const uint32_t a_lbo = 2048u, b_lbo = (uint32_t)it.N * 16u;
     auto issue = [&](int i) {
         const int s = i & 1;
         const int64_t kt = kt0 + i;
-        tc::mbar_expect_tx(&sm.full[s], abytes + bbytes * (uint32_t)nbt);
-        tc::bulk_g2s(sm.a[s], it.A + ((size_t)mt * nkt_all + kt) * abytes, abytes, &sm.full[s]);
-        for (int bt = 0; bt < nbt; ++bt)
-            tc::bulk_g2s(sm.b[s] + bt * bbytes, it.Bm + ((size_t)bt * nkt_all + kt) * bbytes, bbytes, &sm.full[s]);
+        tc::mbar_expect_tx(&sm.full[s], 8u * 2048u + b_chunk);
+        const unsigned char* as = it.A + (size_t)kt * a_chunk + (size_t)mt * 2048u;
+        for (int g = 0; g < 8; ++g) tc::bulk_g2s(sm.a[s] + g * 2048, as + (size_t)g * 4096u, 2048u, &sm.full[s]);
+        tc::bulk_g2s(sm.b[s], it.Bm + (size_t)kt * b_chunk, b_chunk, &sm.full[s]);
     };
     int failed = 0;
     if (tid == 0 && nk > 0) {
-        const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)it.N);
+        const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)it.N) | tc::kMnMajorA | tc::kMnMajorB;
         issue(0);
         if (nk > 1) issue(1);
         for (int i = 0; i < nk; ++i) {
@@ -684,9 +694,9 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
             tc::tc_fence_after();
             const uint32_t a0 = tc::smem_u32(sm.a[s]), b0 = tc::smem_u32(sm.b[s]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                tc::mma_bf16(tbase, tc::sdesc(a0 + 256u * j, 128u, 1024u), tc::sdesc(b0 + 256u * j, 128u, 1024u), idesc,
-                             (i > 0 || j > 0) ? 1u : 0u);
+            for (int j = 0; j < 4; ++j)   // 16 rows (two K groups) per MMA
+                tc::mma_bf16(tbase, tc::sdesc(a0 + 2u * a_lbo * j, a_lbo, 128u),
+                             tc::sdesc(b0 + 2u * b_lbo * j, b_lbo, 128u), idesc, (i > 0 || j > 0) ? 1u : 0u);
             tc::mma_commit(&sm.mma[s]);
             if (i + 2 < nk) {
                 // the buffer is refilled once its MMAs are done
