@@ -98,6 +98,32 @@ __device__ __forceinline__ float4* s_quad(float* S, int64_t row, int f) {
     return reinterpret_cast<float4*>(S + (((row >> 5) * 64 + (f >> 2)) * 128 + (row & 31) * 4));
 }
 
+// Offsets (elements) of every layer's FP32 weights and biases in the flat
+// parameter vector and of its two BF16 packed layouts, in constant memory:
+// the kernels index them by a runtime layer number without a local-memory
+// copy of the table.
+struct TrainOffsets {
+    int64_t w[kMlpLayers], b[kMlpLayers], p[kMlpLayers], pT[kMlpLayers];
+};
+__host__ __device__ constexpr TrainOffsets train_offsets() {
+    TrainOffsets t{};
+    int64_t o = 0, q = 0;
+    for (int l = 0; l < kMlpLayers; ++l) {
+        t.w[l] = o;
+        o += (int64_t)mlp_in(l) * mlp_out(l);
+        t.b[l] = o;
+        o += mlp_out(l);
+        t.p[l] = q;
+        q += (int64_t)mlp_N(l) * mlp_K(l);
+    }
+    for (int l = 0; l < kMlpLayers; ++l) {
+        t.pT[l] = q;
+        q += (int64_t)mlp_NT(l) * mlp_KT(l);
+    }
+    return t;
+}
+static __constant__ TrainOffsets c_off = train_offsets();
+
 __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
     uint32_t p;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(hi), "f"(lo));
@@ -359,12 +385,11 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, part = warp >> 2, r = 32 * quarter + lane;
     const uint32_t rank = PAIR == 2 ? cluster_rank() : 0u, peer = rank ^ 1u;
-    const MlpLayout L = mlp_layout();
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
     const int64_t tile = blockIdx.x / PAIR, row = tile * 128 + r;
-    if (tid == 0) load_w_rows(sm, pb + 2 * L.p_off[0], mlp_N(0), mlp_K(0), mlp_KC(0), NH * (int)rank, NH);
+    if (tid == 0) load_w_rows(sm, pb + 2 * c_off.p[0], mlp_N(0), mlp_K(0), mlp_KC(0), NH * (int)rank, NH);
     // the tile's inputs (warps 0-3, one row each): BF16 A operand (K = 32,
     // zero padded) in both CTAs
     if (part == 0) {
@@ -394,7 +419,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
         // barrier, run_layer's barrier orders these writes before the reads)
         if (tid >= kTrThreads - NH) {
             const int c = tid - (kTrThreads - NH);
-            sm.colsum[c] = __ldg(params + L.b_off[l] + NH * (int)rank + c);
+            sm.colsum[c] = __ldg(params + c_off.b[l] + NH * (int)rank + c);
         }
         const ImgCopy cp = mode == 0 ? img_copy<PAIR>(ws.Him[l], tile, mlp_K(l), rank, false) : ImgCopy{nullptr, 0u, 0u};
         failed = run_layer(sm, tbase, l & 1, NH, mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m, cp);
@@ -402,16 +427,20 @@ __global__ void __launch_bounds__(kTrThreads, 1)
         // the weights of layer l are consumed: bring the next layer's
         if (tid == 0) {
             if (l + 1 < kMlpLayers - 1)
-                load_w_rows(sm, pb + 2 * L.p_off[l + 1], mlp_N(l + 1), mlp_K(l + 1), mlp_KC(l + 1), NH * (int)rank, NH);
+                load_w_rows(sm, pb + 2 * c_off.p[l + 1], mlp_N(l + 1), mlp_K(l + 1), mlp_KC(l + 1), NH * (int)rank, NH);
             else if (mode == 0 && rank == 0)
-                load_w_rows(sm, pb + 2 * L.p_off[kMlpLayers - 1], mlp_N(kMlpLayers - 1), mlp_K(kMlpLayers - 1),
+                load_w_rows(sm, pb + 2 * c_off.p[kMlpLayers - 1], mlp_N(kMlpLayers - 1), mlp_K(kMlpLayers - 1),
                             mlp_KC(kMlpLayers - 1), 0, mlp_N(kMlpLayers - 1));
         }
+        // silu' of the last 32-feature chunk is stored after the hand-off to
+        // the partner, so that the proxy fence before it does not wait for
+        // these global stores
+        float v[32];
+        int f_last = 0;
 #pragma unroll 1
         for (int cc = 0; cc < NH / 128; ++cc) {
             const int f_loc = (NH / 4) * part + 32 * cc, f_glob = NH * (int)rank + f_loc;   // 32 features
             const float* bias = sm.colsum + f_loc;
-            float v[32];
             tc::tmem_ld32(taddr + (uint32_t)f_loc, v);
             uint32_t pk[16];
 #pragma unroll
@@ -428,12 +457,18 @@ __global__ void __launch_bounds__(kTrThreads, 1)
                 }
                 pk[j / 2] = bf16x2(h[0], h[1]);
             }
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                *s_quad(ws.S[l], row, f_glob + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             put_act<PAIR>(sm.act[((l + 1) & 1) % PAIR], pk, r, f_glob, peer);
+            if (cc + 1 < NH / 128) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    *s_quad(ws.S[l], row, f_glob + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+            f_last = f_glob;
         }
         signal_peer(sm, peer, l);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            *s_quad(ws.S[l], row, f_last + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
     int last_peer_k = (failed || PAIR == 1) ? -1 : kMlpLayers - 2;   // the partner's signal of layer 3
     if (!failed && mode == 0 && rank == 0) {
@@ -453,7 +488,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             for (int j = 0; j < 8; ++j) {
                 dy[j] = 0.0f;
                 if (j < 6 && row < B) {
-                    const float d = v[j] + __ldg(params + L.b_off[l] + j) - __ldg(tgt + row * 6 + j);
+                    const float d = v[j] + __ldg(params + c_off.b[l] + j) - __ldg(tgt + row * 6 + j);
                     dy[j] = d > 0.0f ? invB : (d < 0.0f ? -invB : 0.0f);
                     lsum += fabsf(d);
                 }
@@ -465,7 +500,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
                 float sdy = dy[j];
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) sdy += __shfl_xor_sync(0xffffffffu, sdy, off);
-                if (lane == 0 && sdy != 0.0f) atomicAdd(grad + L.b_off[l] + j, sdy);
+                if (lane == 0 && sdy != 0.0f) atomicAdd(grad + c_off.b[l] + j, sdy);
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
@@ -493,14 +528,13 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, part = warp >> 2, r = 32 * quarter + lane;
     const uint32_t rank = PAIR == 2 ? cluster_rank() : 0u, peer = rank ^ 1u;
-    const MlpLayout L = mlp_layout();
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
     const int64_t tile = blockIdx.x / PAIR, row = tile * 128 + r;
     const int top = kMlpLayers - 1;
     if (tid == 0)
-        load_w_rows(sm, pb + 2 * mlp_pT_off(top), mlp_NT(top), mlp_KT(top), mlp_KCT(top), NH * (int)rank, NH);
+        load_w_rows(sm, pb + 2 * c_off.pT[top], mlp_NT(top), mlp_KT(top), mlp_KCT(top), NH * (int)rank, NH);
     if (part == 0) {
         float a[16];
 #pragma unroll
@@ -534,10 +568,10 @@ __global__ void __launch_bounds__(kTrThreads, 1)
         if (failed) break;
         if (tid == 0) {
             if (l - 1 >= 1)
-                load_w_rows(sm, pb + 2 * mlp_pT_off(l - 1), mlp_NT(l - 1), mlp_KT(l - 1), mlp_KCT(l - 1),
+                load_w_rows(sm, pb + 2 * c_off.pT[l - 1], mlp_NT(l - 1), mlp_KT(l - 1), mlp_KCT(l - 1),
                             NH * (int)rank, NH);
             else if (mode == 1 && rank == 0)
-                load_w_rows(sm, pb + 2 * mlp_pT_off(0), mlp_NT(0), mlp_KT(0), mlp_KCT(0), 0, mlp_NT(0));
+                load_w_rows(sm, pb + 2 * c_off.pT[0], mlp_NT(0), mlp_KT(0), mlp_KCT(0), 0, mlp_NT(0));
         }
 #pragma unroll 1
         for (int cc = 0; cc < NH / 128; ++cc) {
@@ -567,7 +601,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
         ++n_sig;
         if (mode == 0) {
             for (int c = tid; c < NH; c += kTrThreads) {
-                atomicAdd(grad + L.b_off[l - 1] + NH * (int)rank + c, sm.colsum[c]);
+                atomicAdd(grad + c_off.b[l - 1] + NH * (int)rank + c, sm.colsum[c]);
                 sm.colsum[c] = 0.0f;
             }
         }
@@ -653,7 +687,6 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     DwSmem& sm = *reinterpret_cast<DwSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const MlpLayout L = mlp_layout();
     const int ks = blockIdx.x % nks, mt = (blockIdx.x / nks) % 2, l = blockIdx.x / (2 * nks);
     const DwItem it = dw_item(ws, l);
     const int64_t nkt_all = Bp >> 6;
@@ -731,14 +764,14 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
             float v[16];
             tc::tmem_ld16(taddr, v);
 #pragma unroll
-            for (int o = 0; o < 6; ++o) atomicAdd(grad + L.w_off[4] + o * 256 + m, v[o]);
+            for (int o = 0; o < 6; ++o) atomicAdd(grad + c_off.w[4] + o * 256 + m, v[o]);
         } else if (l == 0) {
             float v[32];
             tc::tmem_ld32(taddr, v);
 #pragma unroll
-            for (int i = 0; i < 19; ++i) atomicAdd(grad + L.w_off[0] + (int64_t)m * 19 + i, v[i]);
+            for (int i = 0; i < 19; ++i) atomicAdd(grad + c_off.w[0] + (int64_t)m * 19 + i, v[i]);
         } else {
-            float4* dst = reinterpret_cast<float4*>(grad + L.w_off[l] + (int64_t)m * 256);
+            float4* dst = reinterpret_cast<float4*>(grad + c_off.w[l] + (int64_t)m * 256);
 #pragma unroll 1
             for (int cc = 0; cc < 8; ++cc) {
                 float v[32];
@@ -755,29 +788,40 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
     if (tid < 32) tc::tmem_dealloc(tbase, 256);
 }
 
-// Adam (Kingma & Ba): bias-corrected moments, in place; every updated
+// Adam (Kingma & Ba): bias-corrected moments, in place (ic1, ic2: the
+// reciprocals of the bias corrections 1 - b1^t, 1 - b2^t); every updated
 // weight is also written, rounded to BF16, into both packed layouts (the
-// padding of the packed buffers is zero from their creation).
+// padding of the packed buffers is zero from their creation).  The layer of
+// element e and its packed offsets come from shifts and compares: the K
+// chunk of the forward layout is 32 (layer 0) or 64 columns, of the
+// transposed one 16 (layer 4) or 64.
 __global__ void adam_pack_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                                 float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
-                                 float c2, __nv_bfloat16* __restrict__ packed) {
-    const MlpLayout L = mlp_layout();
+                                 float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float ic1,
+                                 float ic2, __nv_bfloat16* __restrict__ packed) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const float gg = g[e];
         const float mm = b1 * m[e] + (1.0f - b1) * gg;
         const float vv = b2 * v[e] + (1.0f - b2) * gg * gg;
         m[e] = mm;
         v[e] = vv;
-        const float pv = p[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+        const float pv = p[e] - lr * (mm * ic1) / (sqrtf(vv * ic2) + eps);
         p[e] = pv;
-        int l = 0;
-        while (l + 1 < kMlpLayers && e >= L.w_off[l + 1]) ++l;
-        const int64_t q = e - L.w_off[l];
-        if (q < (int64_t)mlp_in(l) * mlp_out(l)) {   // a weight, not a bias
-            const int o = (int)(q / mlp_in(l)), i = (int)(q - (int64_t)o * mlp_in(l));
-            const __nv_bfloat16 b = __float2bfloat16_rn(pv);
-            packed[L.p_off[l] + mlp_packed_off(l, o, i) / 2] = b;
-            packed[mlp_pT_off(l) + mlp_packedT_off(l, i, o) / 2] = b;
+        const int l = (int)(e >= c_off.w[1]) + (int)(e >= c_off.w[2]) + (int)(e >= c_off.w[3]) + (int)(e >= c_off.w[4]);
+        const int64_t q = e - c_off.w[l];
+        if (q < c_off.b[l] - c_off.w[l]) {   // a weight W_l[o][i], not a bias
+            const int o = l == 0 ? (int)(q / 19) : (int)(q >> 8);
+            const int i = (int)(q - (int64_t)o * (l == 0 ? 19 : 256));
+            const __nv_bfloat16 bv = __float2bfloat16_rn(pv);
+            // forward layout: N (= out, padded) rows x K (= in, padded) in chunks of KC columns
+            const int kcs = l == 0 ? 5 : 6, N = l == 4 ? 16 : 256;
+            const int c = i >> kcs, k = i & ((1 << kcs) - 1);
+            const uint32_t fo = (uint32_t)c * (uint32_t)(N << kcs) * 2u + tc::kmajor_off((uint32_t)o, (uint32_t)k, 1u << kcs);
+            packed[c_off.p[l] + fo / 2] = bv;
+            // transposed layout: NT (= in, padded) rows x KT (= out, padded) in chunks of KCT columns
+            const int kts = l == 4 ? 4 : 6, NT = l == 0 ? 32 : 256;
+            const int ct = o >> kts, kt = o & ((1 << kts) - 1);
+            const uint32_t to = (uint32_t)ct * (uint32_t)(NT << kts) * 2u + tc::kmajor_off((uint32_t)i, (uint32_t)kt, 1u << kts);
+            packed[c_off.pT[l] + to / 2] = bv;
         }
     }
 }
@@ -863,7 +907,7 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
         adam_pack_kernel<<<(unsigned)((kMlpParams + 255) / 256), 256, 0, st>>>(
-            params, grad, adam_m, adam_v, kMlpParams, lr, b1, b2, 1e-8f, c1, c2, (__nv_bfloat16*)packed);
+            params, grad, adam_m, adam_v, kMlpParams, lr, b1, b2, 1e-8f, 1.0f / c1, 1.0f / c2, (__nv_bfloat16*)packed);
     }
     return cudaGetLastError();
 }

@@ -157,6 +157,23 @@ def test_adam_step_parity(srp):
     assert np.allclose(v1, vo, rtol=1e-5, atol=1e-7)
 
 
+def test_adam_repacks_both_layouts(srp):
+    """The Adam kernel writes each updated weight, rounded to BF16, into the
+    forward and the transposed packed layouts: after three steps the network
+    infers and back-propagates bit for bit like a fresh network packed from
+    its updated parameters."""
+    ctx = srp.Context(0)
+    net = srp.MLP(ctx, flat(omlp.init_params(seed=13)))
+    x = inputs(3000, seed=9)
+    t = np.random.default_rng(4).normal(size=(3000, 6)).astype(np.float32)
+    for _ in range(3):
+        net.train_step(x, t, lr=1e-2, want_loss=False)
+    fresh = srp.MLP(ctx, net.params())
+    assert np.array_equal(net.infer(x), fresh.infer(x))
+    wy = np.random.default_rng(5).normal(size=(3000, 6)).astype(np.float32)
+    assert np.array_equal(net.grad_input(x, wy), fresh.grad_input(x, wy))
+
+
 def test_training_reduces_loss(srp):
     """Fit a smooth synthetic map (a fixed random 19->6 linear map + tanh):
     200 Adam steps reduce the L1 loss at least 5x."""
