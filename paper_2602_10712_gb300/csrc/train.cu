@@ -59,7 +59,8 @@ struct TrainWS {
     __nv_bfloat16* Him[5];       // tile images of the layer inputs: Him[0] = x (F = 32), Him[l] = h_l (F = 256)
     __nv_bfloat16* DZim[5];      // tile images of dL/dz_l (F = 256), DZim[4] = dL/dy (F = 16)
     float* dY;                   // dL/dy [Bp][8] FP32 (columns 6, 7 zero)
-    float* loss;                 // [1]
+    float* lossp;                // [Bp / 32]: the L1 loss of each 32-row warp of the forward's output layer
+    float* loss;                 // [1]: their sum, by the weight-gradient kernel
 };
 
 __host__ __device__ inline int64_t train_bp(int64_t B) { return (B + 127) / 128 * 128; }
@@ -69,7 +70,7 @@ static size_t al1k(size_t x) { return (x + 1023) / 1024 * 1024; }
 size_t train_bytes(int64_t B) {
     const size_t Bp = (size_t)train_bp(B);
     return 4 * al1k(Bp * 256 * 4) + al1k(32 * Bp * 2) + 4 * al1k(256 * Bp * 2) + 4 * al1k(256 * Bp * 2) +
-           al1k(16 * Bp * 2) + al1k(Bp * 8 * 4) + 1024;
+           al1k(16 * Bp * 2) + al1k(Bp * 8 * 4) + al1k(Bp / 32 * 4) + 1024;
 }
 
 static TrainWS train_carve(void* base, int64_t B) {
@@ -82,6 +83,7 @@ static TrainWS train_carve(void* base, int64_t B) {
     for (int l = 0; l < 4; ++l) { w.DZim[l] = (__nv_bfloat16*)q; q += al1k(256 * Bp * 2); }
     w.DZim[4] = (__nv_bfloat16*)q; q += al1k(16 * Bp * 2);
     w.dY = (float*)q; q += al1k(Bp * 8 * 4);
+    w.lossp = (float*)q; q += al1k(Bp / 32 * 4);
     w.loss = (float*)q;
     return w;
 }
@@ -215,6 +217,15 @@ __device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+
+// Programmatic dependent launch.  The backward, weight-gradient and Adam
+// kernels are launched with programmatic stream serialisation: they may
+// start while their predecessor in the stream still runs, do their set-up
+// (barriers, TMEM, weights that no kernel of the step writes), and wait
+// here before reading anything the predecessor wrote.  Each kernel lets its
+// dependent be scheduled once all of its own CTAs are resident.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Thread 0: rows [r0, r0 + nr) of each of the K / KC chunks of a packed
 // layer (N x KC K-major tiles) into sm.w, one bulk copy per chunk.
@@ -388,8 +399,14 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
+    grid_dep_launch();
     const int64_t tile = blockIdx.x / PAIR, row = tile * 128 + r;
     if (tid == 0) load_w_rows(sm, pb + 2 * c_off.p[0], mlp_N(0), mlp_K(0), mlp_KC(0), NH * (int)rank, NH);
+    // training: the gradient starts from zero (the backward and weight-
+    // gradient kernels accumulate into it once this grid has completed)
+    if (mode == 0)
+        for (int64_t e = (int64_t)blockIdx.x * kTrThreads + tid; e < kMlpParams; e += (int64_t)gridDim.x * kTrThreads)
+            grad[e] = 0.0f;
     // the tile's inputs (warps 0-3, one row each): BF16 A operand (K = 32,
     // zero padded) in both CTAs
     if (part == 0) {
@@ -473,7 +490,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     int last_peer_k = (failed || PAIR == 1) ? -1 : kMlpLayers - 2;   // the partner's signal of layer 3
     if (!failed && mode == 0 && rank == 0) {
         // output layer on rank 0 (the image of its whole input tile too):
-        // loss, dL/dy, output bias gradient
+        // the loss of each warp's 32 rows and dL/dy
         const int l = kMlpLayers - 1;
         failed = run_layer(sm, tbase, l & 1, mlp_N(l), mlp_K(l), mlp_KC(l), PAIR == 2 ? l - 1 : -1, ph_w, ph_m,
                            img_copy<PAIR>(ws.Him[l], tile, mlp_K(l), rank, true));
@@ -496,15 +513,8 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             reinterpret_cast<float4*>(ws.dY + row * 8)[0] = make_float4(dy[0], dy[1], dy[2], dy[3]);
             reinterpret_cast<float4*>(ws.dY + row * 8)[1] = make_float4(dy[4], dy[5], dy[6], dy[7]);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                float sdy = dy[j];
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) sdy += __shfl_xor_sync(0xffffffffu, sdy, off);
-                if (lane == 0 && sdy != 0.0f) atomicAdd(grad + c_off.b[l] + j, sdy);
-            }
-#pragma unroll
             for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-            if (lane == 0) atomicAdd(ws.loss, lsum * invB);
+            if (lane == 0) ws.lossp[tile * 4 + quarter] = lsum * invB;
         }
     }
     train_teardown(sm, tbase, failed, ph_w, ph_m, last_peer_k, err);
@@ -531,10 +541,12 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     const unsigned char* pb = reinterpret_cast<const unsigned char*>(packed);
     train_setup(sm);
     const uint32_t tbase = sm.tmem_base;
+    grid_dep_launch();
     const int64_t tile = blockIdx.x / PAIR, row = tile * 128 + r;
     const int top = kMlpLayers - 1;
     if (tid == 0)
         load_w_rows(sm, pb + 2 * c_off.pT[top], mlp_NT(top), mlp_KT(top), mlp_KCT(top), NH * (int)rank, NH);
+    grid_dep_wait();   // dy (training: the forward's dL/dy) and silu'(z) are the forward's
     if (part == 0) {
         float a[16];
 #pragma unroll
@@ -544,6 +556,16 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             *reinterpret_cast<uint4*>(sm.act[0] + tc::kmajor_off(r, 8 * q, 16)) =
                 make_uint4(bf16x2(a[8 * q], a[8 * q + 1]), bf16x2(a[8 * q + 2], a[8 * q + 3]),
                            bf16x2(a[8 * q + 4], a[8 * q + 5]), bf16x2(a[8 * q + 6], a[8 * q + 7]));
+        if (mode == 0 && rank == 0) {
+            // output bias gradient: the column sums of dL/dy over the warp's rows
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                float sdy = a[j];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sdy += __shfl_xor_sync(0xffffffffu, sdy, off);
+                if (lane == 0 && sdy != 0.0f) atomicAdd(grad + c_off.b[top] + j, sdy);
+            }
+        }
     }
     tc::fence_async_smem();
     __syncthreads();
@@ -658,6 +680,7 @@ struct DwSmem {
     alignas(1024) unsigned char b[2][256 * 64 * 2];
     alignas(8) uint64_t full[2];
     alignas(8) uint64_t mma[2];
+    float red[kDwThreads];
     uint32_t tmem_base;
     int fail;
 };
@@ -705,6 +728,21 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = sm.tmem_base;
+    grid_dep_launch();
+    grid_dep_wait();   // the tile images and loss partials are the forward's and backward's
+    if (blockIdx.x == 0) {
+        // the step's loss: the forward's per-warp partial sums, strided over
+        // the threads, then the threads' sums in order
+        float acc = 0.0f;
+        for (int64_t i = tid; i < (Bp >> 5); i += kDwThreads) acc += ws.lossp[i];
+        sm.red[tid] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            float tot = 0.0f;
+            for (int i = 0; i < kDwThreads; ++i) tot += sm.red[i];
+            ws.loss[0] = tot;
+        }
+    }
     const uint32_t a_chunk = 64u * 256u * 2u, b_chunk = 64u * (uint32_t)it.N * 2u;   // image bytes per 64 rows
     const uint32_t a_lbo = 2048u, b_lbo = (uint32_t)it.N * 16u;
     auto issue = [&](int i) {
@@ -798,6 +836,7 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
 __global__ void adam_pack_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                                  float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float ic1,
                                  float ic2, __nv_bfloat16* __restrict__ packed) {
+    grid_dep_wait();   // the gradient is the weight-gradient kernel's
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const float gg = g[e];
         const float mm = b1 * m[e] + (1.0f - b1) * gg;
@@ -851,20 +890,33 @@ static int train_pair(int64_t Bp) {
     return 2 * (Bp / 128) <= n_sm ? 2 : 1;
 }
 
+// Launch with cudaLaunchKernelEx: clusters of `cluster` CTAs (1: none);
+// `pdl`: programmatic stream serialisation (the kernel may start while its
+// predecessor still runs and waits for it in grid_dep_wait).
 template <typename... Args>
-static cudaError_t launch_pairs(void (*kern)(Args...), unsigned tiles, size_t smem, cudaStream_t st, Args... args) {
+static cudaError_t launch_ex(void (*kern)(Args...), unsigned grid, unsigned block, size_t smem, int cluster, bool pdl,
+                             cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * tiles);
-    cfg.blockDim = dim3(kTrThreads);
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute at[2];
+    unsigned na = 0;
+    if (cluster > 1) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = (unsigned)cluster;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
@@ -872,19 +924,19 @@ static cudaError_t launch_fwd(int pair, unsigned tiles, cudaStream_t st, const f
                               int64_t Bp, const __nv_bfloat16* pk, const float* params, const TrainWS& ws, float* grad,
                               int mode, int* err) {
     if (pair == 2)
-        return launch_pairs(train_fwd_kernel<2>, tiles, sizeof(TrainSmem<2>), st, x, tgt, B, Bp, pk, params, ws, grad,
-                            mode, err);
-    train_fwd_kernel<1><<<tiles, kTrThreads, sizeof(TrainSmem<1>), st>>>(x, tgt, B, Bp, pk, params, ws, grad, mode, err);
-    return cudaGetLastError();
+        return launch_ex(train_fwd_kernel<2>, 2 * tiles, kTrThreads, sizeof(TrainSmem<2>), 2, false, st, x, tgt, B, Bp,
+                         pk, params, ws, grad, mode, err);
+    return launch_ex(train_fwd_kernel<1>, tiles, kTrThreads, sizeof(TrainSmem<1>), 1, false, st, x, tgt, B, Bp, pk,
+                     params, ws, grad, mode, err);
 }
 
 static cudaError_t launch_bwd(int pair, unsigned tiles, cudaStream_t st, const float* dy, int ld, int64_t B, int64_t Bp,
                               const __nv_bfloat16* pk, const TrainWS& ws, float* grad, float* gx, int mode, int* err) {
     if (pair == 2)
-        return launch_pairs(train_bwd_kernel<2>, tiles, sizeof(TrainSmem<2>), st, dy, ld, B, Bp, pk, ws, grad, gx, mode,
-                            err);
-    train_bwd_kernel<1><<<tiles, kTrThreads, sizeof(TrainSmem<1>), st>>>(dy, ld, B, Bp, pk, ws, grad, gx, mode, err);
-    return cudaGetLastError();
+        return launch_ex(train_bwd_kernel<2>, 2 * tiles, kTrThreads, sizeof(TrainSmem<2>), 2, true, st, dy, ld, B, Bp,
+                         pk, ws, grad, gx, mode, err);
+    return launch_ex(train_bwd_kernel<1>, tiles, kTrThreads, sizeof(TrainSmem<1>), 1, true, st, dy, ld, B, Bp, pk, ws,
+                     grad, gx, mode, err);
 }
 
 // One optimisation step; grad receives dL/dparams; Adam applied when lr > 0.
@@ -894,22 +946,23 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     if (e != cudaSuccess) return e;
     const int64_t Bp = train_bp(B);
     const TrainWS ws = train_carve(work, B);
-    if ((e = cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ws.loss, 0, sizeof(float), st)) != cudaSuccess) return e;
     const unsigned tiles = (unsigned)(Bp / 128);
     const int pair = train_pair(Bp);
     const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
     if ((e = launch_fwd(pair, tiles, st, x, tgt, B, Bp, pk, params, ws, grad, 0, err)) != cudaSuccess) return e;
     if ((e = launch_bwd(pair, tiles, st, ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err)) != cudaSuccess) return e;
     const int nks = (int)(((Bp >> 6) + kDwSlice - 1) / kDwSlice);
-    train_dw_kernel<<<(unsigned)(kMlpLayers * 2 * nks), kDwThreads, sizeof(DwSmem), st>>>(Bp, nks, ws, grad, err);
+    if ((e = launch_ex(train_dw_kernel, (unsigned)(kMlpLayers * 2 * nks), kDwThreads, sizeof(DwSmem), 1, true, st, Bp,
+                       nks, ws, grad, err)) != cudaSuccess)
+        return e;
     if (lr > 0.0f) {
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-        adam_pack_kernel<<<(unsigned)((kMlpParams + 255) / 256), 256, 0, st>>>(
-            params, grad, adam_m, adam_v, kMlpParams, lr, b1, b2, 1e-8f, 1.0f / c1, 1.0f / c2, (__nv_bfloat16*)packed);
+        e = launch_ex(adam_pack_kernel, (unsigned)((kMlpParams + 255) / 256), 256u, 0, 1, true, st, params,
+                      (const float*)grad, adam_m, adam_v, (int64_t)kMlpParams, lr, b1, b2, 1e-8f, 1.0f / c1, 1.0f / c2,
+                      (__nv_bfloat16*)packed);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 // Input gradient gx[B][19] = (dy/dx)^T wy (wy [B][6]): the forward's
