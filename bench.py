@@ -1007,7 +1007,9 @@ def run_profile_case(case):
     mlp   -- proxy inference on 262,144 queries;
     train -- three proxy training steps of 8,192 samples;
     grad  -- srp_force_grad on the box-wing, 64 suns x 1024^2 rays, K = 1;
-    probe -- the L2 read probe over 64 MiB (3 launches of one pass)."""
+    probe -- the L2 read probe over 64 MiB (3 launches of one pass);
+    orbit -- srp_integrate under the neural proxy with the adjoint, 64
+             trajectories x 38 steps (one checkpoint segment)."""
     import torch
 
     import paper_2602_10712_gb300 as srp
@@ -1057,6 +1059,14 @@ def run_profile_case(case):
         ha = torch.from_numpy(m1.hinges).to(dev)
         for _ in range(3):
             srp.srp_force_grad(ctx, b1, rho1, sun1, com1, up, th1, ha, rays_x=1024, max_bounces=1)
+    elif case == "orbit":
+        _, _, o, th, net = _orbit_cases(srp, ctx)[1]
+        o = srp.orbit_opts(model=srp.SRP_FM_PROXY, n_theta=16, pressure=4.56e-6, mass=1000.0, sun=ORBIT_SUN, dt=60.0,
+                           n_steps=ORBIT_CKPT, ckpt_every=ORBIT_CKPT)
+        z0 = W.orbit_states(64, seed=7)
+        wN = np.random.default_rng(1).normal(size=(64, 13))
+        for _ in range(3):
+            srp.srp_integrate(ctx, o, z0, th[:64].copy(), proxy=net, dL_dzN=wN)
     elif case == "probe":
         # the L2 read probe over 64 MiB (one pass per launch, 3 launches)
         srp.srp_probe_read_bandwidth(ctx, 64 << 20, passes=1, reps=2)
@@ -1074,7 +1084,7 @@ def main():
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
-    ap.add_argument("--profile", choices=["trace", "trace_k1", "area", "mlp", "train", "grad", "probe"], default=None,
+    ap.add_argument("--profile", choices=["trace", "trace_k1", "area", "mlp", "train", "grad", "probe", "orbit"], default=None,
                     help="run a small ncu capture case and exit")
     args = ap.parse_args()
     if args.profile:
