@@ -586,8 +586,9 @@ def orbit_leg(srp, ctx):
                      "rk4_steps_per_s_with_adjoint": n * ORBIT_STEPS / t_a}
         check.append({"name": name, "z0": z0[0].copy(), "theta": th[0].copy(), "zN": r["zN"][0].copy(),
                       "params": net.params() if net is not None else None})
-    out["note"] = ("srp_integrate (one CTA per trajectory), one day at dt = 60 s, two-body + J2 + SRP with attitude "
-                   "dynamics; wall clock of one host-memory call; FP64 and latency-bound (no roofline claim)")
+    out["note"] = ("srp_integrate (T = 1, 2, 4 or 8 trajectories per CTA so that the CTAs about fill the SMs: 2 for "
+                   "256, 8 for 1024), one day at dt = 60 s, two-body + J2 + SRP with attitude dynamics; wall clock of "
+                   "one host-memory call; FP64 and latency-bound (no roofline claim)")
     return out, check
 
 

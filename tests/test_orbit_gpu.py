@@ -109,6 +109,36 @@ def test_batched_trajectories_independent(srp):
     assert np.array_equal(r2["zN"][0], r0["zN"][0]) and np.array_equal(r2["zN"][1], r1["zN"][0])
 
 
+@pytest.mark.parametrize("per_sm", [2, 3, 9])
+def test_trajectories_per_cta_bitwise(srp, per_sm):
+    """A CTA integrates 1, 2, 4 or 8 trajectories, chosen from their count
+    and the SM count; the per-trajectory arithmetic is the same for every
+    batch, so trajectories (and their adjoint gradients) integrated in a
+    batch of per_sm x SMs, with a ragged last CTA, equal bit for bit the
+    same trajectories integrated one at a time.  Proxy model, 14 steps with
+    checkpoints every 5."""
+    ctx = srp.Context(0)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    n = per_sm * n_sm - 1
+    net = srp.MLP(ctx, seed=5)
+    o = srp.orbit_opts(model=srp.SRP_FM_PROXY, pressure=4.56e-5, mass=800.0, sun=SUN, dt=60.0, n_steps=14,
+                       n_theta=16, ckpt_every=5)
+    rng = np.random.default_rng(per_sm)
+    z0 = np.stack([O.circular_state(rng.uniform(7e6, 4e7), rng.uniform(0, 1.5), rng.uniform(0, 6), rng.uniform(0, 6))
+                   for _ in range(n)])
+    q = rng.normal(size=(n, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
+    z0[:, 6:10] = q
+    z0[:, 10:13] = rng.normal(size=(n, 3)) * 1e-4
+    th = rng.uniform(0, 0.5, size=(n, 16))
+    wN = rng.normal(size=(n, 13))
+    r = srp.srp_integrate(ctx, o, z0, th, proxy=net, dL_dzN=wN)
+    for i in (0, n // 2, n - 1):
+        ri = srp.srp_integrate(ctx, o, z0[i:i + 1], th[i:i + 1], proxy=net, dL_dzN=wN[i:i + 1])
+        assert np.array_equal(r["zN"][i], ri["zN"][0]), i
+        assert np.array_equal(r["dL_dtheta"][i], ri["dL_dtheta"][0]), i
+        assert np.array_equal(r["dL_dz0"][i], ri["dL_dz0"][0]), i
+
+
 def test_design_optimisation_loop(srp):
     """Alg. 1's optimisation: recover the cannonball parameter that produced
     a reference end position (2 h arc) from a start 40% off, with bounds."""
