@@ -152,9 +152,10 @@ __device__ __forceinline__ float warp_colsum32(float (&t)[32], int lane) {
 // has too few tiles to fill the GPU, by a cluster of two CTAs (PAIR = 2, one
 // SM each): in every 256-wide layer CTA rank c then computes the output
 // features [128 c, 128 c + 128) -- half the MMA N and half the epilogue --
-// and writes its half of the next layer's BF16 A operand into both CTAs'
-// shared memory (distributed shared memory); each then tells the other, on
-// an mbarrier of the receiving CTA, that its half has landed.  The pair's A
+// and writes its half of the next layer's BF16 A operand into its own
+// shared memory; one thread then bulk-copies that half into the partner's
+// (distributed shared memory, 16 runs of 2 KB, completing on an mbarrier of
+// the receiving CTA, which expects the 32 KB before it waits).  The pair's A
 // operand is double buffered (layer l reads act[l & 1], its epilogue writes
 // act[(l + 1) & 1]), so a CTA never writes into a buffer its partner's
 // tensor core may still read.  The narrow layers (the 6 outputs, the 19
@@ -191,14 +192,15 @@ __device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_u32(p)), "r"(rank));
     return r;
 }
-__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint4 v) {
-    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
-                 "r"(v.w)
+// bulk copy of `bytes` from this CTA's shared memory to shared::cluster
+// address `dst`, completing (complete_tx) on the mbarrier at `bar`
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst),
+                 "r"(tc::smem_u32(src)), "r"(bytes), "r"(bar)
                  : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t remote_bar) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
-}
+constexpr uint32_t kPeerHalfBytes = 128u * 128u * 2u;   // a partner's half of a K = 256 A operand
 __device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
     for (uint32_t it = 0; it < limit; ++it) {
         uint32_t ok;
@@ -257,8 +259,11 @@ __device__ __forceinline__ void issue_layer(TrainSmem<PAIR>& sm, uint32_t tbase,
 // completes its phase k >> 1: the two barriers alternate, so a partner one
 // signal ahead (the most it can be) never advances the barrier being
 // waited on past the phase awaited.
+// Thread 0 arms the phase with the 32 KB it expects (the partner's copy may
+// land before or after) and waits for it.
 template <int PAIR>
 __device__ __forceinline__ bool wait_peer(TrainSmem<PAIR>& sm, int k) {
+    tc::mbar_expect_tx(&sm.bar_peer[k & 1], kPeerHalfBytes);
     return mbar_wait_cluster_bounded(&sm.bar_peer[k & 1], (uint32_t)(k >> 1) & 1u, kWaitLimit);
 }
 
@@ -332,15 +337,23 @@ __device__ __forceinline__ void train_setup(TrainSmem<PAIR>& sm) {
     if (PAIR == 2) cluster_sync();   // the partner's barriers exist before anyone arrives on them
 }
 
-// After the epilogue: this CTA's writes (local and into the partner's A
-// buffer) visible to the tensor cores, then the partner gets signal k.
+// After the epilogue: this CTA's writes into A buffer `buf` visible to the
+// async proxy (its tensor core and bulk copies), then thread 0 copies this
+// CTA's half (features 128 c .. 128 c + 127: 2 KB in each of the 16 8-row
+// groups) into the partner's `buf`, as signal k.
 template <int PAIR>
-__device__ __forceinline__ void signal_peer(TrainSmem<PAIR>& sm, uint32_t peer, int k) {
-    if (PAIR == 2) asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
-    else tc::fence_async_smem();
+__device__ __forceinline__ void signal_peer(TrainSmem<PAIR>& sm, uint32_t peer, int k, const unsigned char* buf) {
+    tc::fence_async_smem();
     tc::tc_fence_before();
     __syncthreads();
-    if (PAIR == 2 && threadIdx.x == 0) mbar_arrive_cluster(peer_addr(&sm.bar_peer[k & 1], peer));
+    if (PAIR == 2 && threadIdx.x == 0) {
+        const uint32_t bar = peer_addr(&sm.bar_peer[k & 1], peer);
+        const uint32_t half = (peer ^ 1u) * 2048u;
+        for (int g = 0; g < 16; ++g) {
+            const unsigned char* src = buf + g * 4096 + half;
+            bulk_s2peer(peer_addr(src, peer), src, 2048u, bar);
+        }
+    }
 }
 
 // End of the kernel: record a failed wait, let the copy or the MMAs in
@@ -367,15 +380,12 @@ __device__ __forceinline__ void train_teardown(TrainSmem<PAIR>& sm, uint32_t tba
 }
 
 // Writes the thread's 32 BF16 values (pk, features f0 .. f0 + 31 of row r)
-// into A buffer `dst` (K = 256 layout) of this CTA and of the partner, if any.
-template <int PAIR>
-__device__ __forceinline__ void put_act(unsigned char* dst, const uint32_t (&pk)[16], int r, int f0, uint32_t peer) {
+// into A buffer `dst` (K = 256 layout) of this CTA.
+__device__ __forceinline__ void put_act(unsigned char* dst, const uint32_t (&pk)[16], int r, int f0) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         unsigned char* p = dst + tc::kmajor_off((uint32_t)r, (uint32_t)(f0 + 8 * q), 256u);
-        const uint4 v = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-        *reinterpret_cast<uint4*>(p) = v;
-        if (PAIR == 2) st_cluster_v4(peer_addr(p, peer), v);
+        *reinterpret_cast<uint4*>(p) = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
     }
 }
 
@@ -474,7 +484,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
                 }
                 pk[j / 2] = bf16x2(h[0], h[1]);
             }
-            put_act<PAIR>(sm.act[((l + 1) & 1) % PAIR], pk, r, f_glob, peer);
+            put_act(sm.act[((l + 1) & 1) % PAIR], pk, r, f_glob);
             if (cc + 1 < NH / 128) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
@@ -482,7 +492,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             }
             f_last = f_glob;
         }
-        signal_peer(sm, peer, l);
+        signal_peer(sm, peer, l, sm.act[((l + 1) & 1) % PAIR]);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
             *s_quad(ws.S[l], row, f_last + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
@@ -612,14 +622,14 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             uint32_t pk[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) pk[j] = bf16x2(v[2 * j], v[2 * j + 1]);
-            put_act<PAIR>(sm.act[(buf ^ 1) % PAIR], pk, r, f_glob, peer);
+            put_act(sm.act[(buf ^ 1) % PAIR], pk, r, f_glob);
             if (mode == 0) {
                 // bias gradient of layer l-1: this warp's 32 rows, column f_loc + lane
                 const float cs = warp_colsum32(v, lane);
                 atomicAdd(&sm.colsum[f_loc + lane], cs);
             }
         }
-        signal_peer(sm, peer, n_sig);   // (its __syncthreads also orders the colsum adds)
+        signal_peer(sm, peer, n_sig, sm.act[(buf ^ 1) % PAIR]);   // (its __syncthreads also orders the colsum adds)
         ++n_sig;
         if (mode == 0) {
             for (int c = tid; c < NH; c += kTrThreads) {
@@ -661,62 +671,86 @@ __global__ void __launch_bounds__(kTrThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradients.  Work item (layer l, M tile mt, K slice ks), the batch
-// rows as the K of the product, both operands read MN-major from the tile
-// images (features along M or N):
+// Weight gradients.  The batch rows are the K of the products, both operands
+// read MN-major from the tile images (features along M or N):
 //   l = 0..3: dW_l[o][i] += sum_r dZ_l[r][o] H_l[r][i]    (M = o, N = i)
 //   l = 4:    dW_4[o][i] += sum_r H_4[r][i] dY[r][o]      (M = i, N = o:
 //             the 6 outputs fit an N = 16 tile; stored transposed)
-// over the rows of K slice ks (kDwSlice chunks of 64 rows).  One chunk of
-// an image (64 rows x F features) is 8 row groups of F * 16 bytes; the A
-// operand takes the 2 KB of features [128 mt, 128 mt + 128) from each
-// (8 bulk copies, SBO 128, LBO 2 KB in shared memory), the B operand the
-// whole chunk (one copy, SBO 128, LBO F * 16).
+// Work items: "heavy" (l = 1..3, M tile mt, K slice ks) and "light" (mt,
+// ks) covering layers 0 and 4 together (two accumulators), 8 x nks items,
+// nks chosen on the host so that they about fill the SMs in one wave; a
+// slice is `slice` chunks of 64 rows.  One chunk of an image (64 rows x F
+// features) is 8 row groups of F * 16 bytes; an A operand takes the 2 KB of
+// features [128 mt, 128 mt + 128) from each (8 bulk copies, SBO 128 and
+// LBO 2 KB in shared memory), a B operand the whole chunk (one copy, SBO
+// 128, LBO F * 16).  Four stages of up to 48 KB keep 192 KB of operands in
+// flight per SM; the issuing thread refills the stage of chunk i - 1 with
+// chunk i + 3 right after queueing chunk i's MMAs, so the tensor core never
+// waits for the refill.  The epilogue transposes each warp's 32 x 32 FP32
+// block through shared memory so that each red.global.add.v4 covers 4 rows
+// x 128 bytes, not 32 scattered rows.
 // ---------------------------------------------------------------------------
-constexpr int kDwSlice = 8;
+constexpr int kDwStages = 4;
+constexpr uint32_t kDwA = 16384u, kDwB = 32768u;   // stage bytes of the A and B regions
 
 struct DwSmem {
-    alignas(1024) unsigned char a[2][128 * 64 * 2];
-    alignas(1024) unsigned char b[2][256 * 64 * 2];
-    alignas(8) uint64_t full[2];
-    alignas(8) uint64_t mma[2];
+    alignas(1024) unsigned char a[kDwStages][kDwA];
+    alignas(1024) unsigned char b[kDwStages][kDwB];
+    alignas(8) uint64_t full[kDwStages];
+    alignas(8) uint64_t mma[kDwStages];
     float red[kDwThreads];
     uint32_t tmem_base;
     int fail;
 };
 
-struct DwItem {
-    const unsigned char* A;   // image, F = 256
+// One product of a work item: operand images, where a chunk of each lands
+// in a stage, N and the accumulator's first TMEM column.
+struct DwJob {
+    const unsigned char* A;   // image, F = 256 (features [128 mt, 128 mt + 128) taken)
     const unsigned char* Bm;  // image, F = N
-    int N;
+    uint32_t a_off, b_off;    // stage offsets: a_off in the A region (< kDwA) or, | 0x80000000, in the B region
+    int N, col;
 };
 
-__device__ __forceinline__ DwItem dw_item(const TrainWS& ws, int l) {
-    DwItem it;
-    if (l < 4) {
-        it.A = reinterpret_cast<const unsigned char*>(ws.DZim[l]);
-        it.Bm = reinterpret_cast<const unsigned char*>(ws.Him[l]);
-        it.N = l == 0 ? 32 : 256;
-    } else {
-        it.A = reinterpret_cast<const unsigned char*>(ws.Him[4]);
-        it.Bm = reinterpret_cast<const unsigned char*>(ws.DZim[4]);
-        it.N = 16;
+__device__ __forceinline__ int dw_jobs(const TrainWS& ws, int idx, int nks, DwJob (&jb)[2], int& mt, int& ks, int& l) {
+    if (idx < 6 * nks) {
+        l = 1 + idx / (2 * nks);
+        mt = (idx / nks) & 1;
+        ks = idx % nks;
+        jb[0] = DwJob{reinterpret_cast<const unsigned char*>(ws.DZim[l]), reinterpret_cast<const unsigned char*>(ws.Him[l]),
+                      0u, 0u, 256, 0};
+        return 1;
     }
-    return it;
+    const int j = idx - 6 * nks;
+    l = 0;
+    mt = j / nks;
+    ks = j % nks;
+    // layer 0: A in the A region, B (x, 4 KB) at 16 KB of the B region;
+    // layer 4: A at 0 of the B region, B (dL/dy, 2 KB) at 20 KB
+    jb[0] = DwJob{reinterpret_cast<const unsigned char*>(ws.DZim[0]), reinterpret_cast<const unsigned char*>(ws.Him[0]),
+                  0u, 16384u, 32, 0};
+    jb[1] = DwJob{reinterpret_cast<const unsigned char*>(ws.Him[4]), reinterpret_cast<const unsigned char*>(ws.DZim[4]),
+                  0x80000000u, 20480u, 16, 32};
+    return 2;
 }
 
-__global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int nks, TrainWS ws,
+__device__ __forceinline__ unsigned char* dw_a_dst(DwSmem& sm, int s, uint32_t a_off) {
+    return (a_off & 0x80000000u) ? sm.b[s] + (a_off & 0x7fffffffu) : sm.a[s] + a_off;
+}
+
+__global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int nks, int slice, TrainWS ws,
                                                                 float* __restrict__ grad, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     DwSmem& sm = *reinterpret_cast<DwSmem*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int ks = blockIdx.x % nks, mt = (blockIdx.x / nks) % 2, l = blockIdx.x / (2 * nks);
-    const DwItem it = dw_item(ws, l);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    DwJob jb[2];
+    int mt = 0, ks = 0, l = 0;
+    const int nj = dw_jobs(ws, blockIdx.x, nks, jb, mt, ks, l);
     const int64_t nkt_all = Bp >> 6;
-    const int kt0 = ks * kDwSlice;
-    const int nk = (int)min((int64_t)kDwSlice, nkt_all - kt0);
+    const int64_t kt0 = (int64_t)ks * slice;
+    const int nk = (int)max((int64_t)0, min((int64_t)slice, nkt_all - kt0));
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) { tc::mbar_init(&sm.full[s], 1); tc::mbar_init(&sm.mma[s], 1); }
+        for (int s = 0; s < kDwStages; ++s) { tc::mbar_init(&sm.full[s], 1); tc::mbar_init(&sm.mma[s], 1); }
         tc::fence_mbar_init();
         sm.fail = 0;
     }
@@ -743,36 +777,44 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
             ws.loss[0] = tot;
         }
     }
-    const uint32_t a_chunk = 64u * 256u * 2u, b_chunk = 64u * (uint32_t)it.N * 2u;   // image bytes per 64 rows
-    const uint32_t a_lbo = 2048u, b_lbo = (uint32_t)it.N * 16u;
     auto issue = [&](int i) {
-        const int s = i & 1;
+        const int s = i % kDwStages;
         const int64_t kt = kt0 + i;
-        tc::mbar_expect_tx(&sm.full[s], 8u * 2048u + b_chunk);
-        const unsigned char* as = it.A + (size_t)kt * a_chunk + (size_t)mt * 2048u;
-        for (int g = 0; g < 8; ++g) tc::bulk_g2s(sm.a[s] + g * 2048, as + (size_t)g * 4096u, 2048u, &sm.full[s]);
-        tc::bulk_g2s(sm.b[s], it.Bm + (size_t)kt * b_chunk, b_chunk, &sm.full[s]);
+        uint32_t bytes = 0;
+        for (int q = 0; q < nj; ++q) bytes += 8u * 2048u + 64u * (uint32_t)jb[q].N * 2u;
+        tc::mbar_expect_tx(&sm.full[s], bytes);
+        for (int q = 0; q < nj; ++q) {
+            const unsigned char* as = jb[q].A + (size_t)kt * (64u * 256u * 2u) + (size_t)mt * 2048u;
+            unsigned char* ad = dw_a_dst(sm, s, jb[q].a_off);
+            for (int g = 0; g < 8; ++g) tc::bulk_g2s(ad + g * 2048, as + (size_t)g * 4096u, 2048u, &sm.full[s]);
+            const uint32_t bc = 64u * (uint32_t)jb[q].N * 2u;
+            tc::bulk_g2s(sm.b[s] + jb[q].b_off, jb[q].Bm + (size_t)kt * bc, bc, &sm.full[s]);
+        }
     };
     int failed = 0;
     if (tid == 0 && nk > 0) {
-        const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)it.N) | tc::kMnMajorA | tc::kMnMajorB;
-        issue(0);
-        if (nk > 1) issue(1);
+        for (int i = 0; i < kDwStages && i < nk; ++i) issue(i);
         for (int i = 0; i < nk; ++i) {
-            const int s = i & 1;
-            const uint32_t par = (uint32_t)(i >> 1) & 1u;
-            if (!tc::mbar_wait_bounded(&sm.full[s], par, kWaitLimit)) { failed = 1; break; }
+            const int s = i % kDwStages;
+            if (!tc::mbar_wait_bounded(&sm.full[s], (uint32_t)(i / kDwStages) & 1u, kWaitLimit)) { failed = 1; break; }
             tc::tc_fence_after();
-            const uint32_t a0 = tc::smem_u32(sm.a[s]), b0 = tc::smem_u32(sm.b[s]);
+            for (int q = 0; q < nj; ++q) {
+                const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)jb[q].N) | tc::kMnMajorA | tc::kMnMajorB;
+                const uint32_t a0 = tc::smem_u32(dw_a_dst(sm, s, jb[q].a_off)), b0 = tc::smem_u32(sm.b[s] + jb[q].b_off);
+                const uint32_t b_lbo = (uint32_t)jb[q].N * 16u;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)   // 16 rows (two K groups) per MMA
-                tc::mma_bf16(tbase, tc::sdesc(a0 + 2u * a_lbo * j, a_lbo, 128u),
-                             tc::sdesc(b0 + 2u * b_lbo * j, b_lbo, 128u), idesc, (i > 0 || j > 0) ? 1u : 0u);
+                for (int j = 0; j < 4; ++j)   // 16 rows (two K groups) per MMA
+                    tc::mma_bf16(tbase + (uint32_t)jb[q].col, tc::sdesc(a0 + 4096u * j, 2048u, 128u),
+                                 tc::sdesc(b0 + 2u * b_lbo * j, b_lbo, 128u), idesc, (i > 0 || j > 0) ? 1u : 0u);
+            }
             tc::mma_commit(&sm.mma[s]);
-            if (i + 2 < nk) {
-                // the buffer is refilled once its MMAs are done
-                if (!tc::mbar_wait_bounded(&sm.mma[s], par, kWaitLimit)) { failed = 2; break; }
-                issue(i + 2);
+            // refill the previous chunk's stage once its MMAs are done (this
+            // chunk's are queued behind them)
+            const int ip = i - 1;
+            if (ip >= 0 && ip + kDwStages < nk) {
+                const int sp = ip % kDwStages;
+                if (!tc::mbar_wait_bounded(&sm.mma[sp], (uint32_t)(ip / kDwStages) & 1u, kWaitLimit)) { failed = 2; break; }
+                issue(ip + kDwStages);
             }
         }
         sm.fail = failed;
@@ -781,43 +823,58 @@ __global__ void __launch_bounds__(kDwThreads, 1) train_dw_kernel(int64_t Bp, int
     failed = sm.fail;
     if (!failed && nk > 0) {
         const int last = nk - 1;
-        const bool ok = tc::mbar_wait_bounded(&sm.mma[last & 1], (uint32_t)(last >> 1) & 1u, kWaitLimit);
+        const bool ok = tc::mbar_wait_bounded(&sm.mma[last % kDwStages], (uint32_t)(last / kDwStages) & 1u, kWaitLimit);
         if (__syncthreads_or(!ok)) failed = 2;
     }
     if (failed) {
         if (tid == 0) {
             atomicOr(err, kErrWaitTimeout);
             // copies and MMAs in flight land before the CTA leaves
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < kDwStages; ++s) {
                 tc::mbar_wait_bounded(&sm.full[s], 0u, 1u << 16);
                 tc::mbar_wait_bounded(&sm.mma[s], 0u, 1u << 16);
             }
         }
     } else if (nk > 0) {
         tc::tc_fence_after();
-        const int r = 32 * warp + (tid & 31);   // M row of the tile
-        const int m = 128 * mt + r;
+        const int m0 = 128 * mt + 32 * warp;   // first M row of the warp (TMEM lane quarter)
         const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
-        if (l == 4) {
-            float v[16];
-            tc::tmem_ld16(taddr, v);
-#pragma unroll
-            for (int o = 0; o < 6; ++o) atomicAdd(grad + c_off.w[4] + o * 256 + m, v[o]);
-        } else if (l == 0) {
-            float v[32];
-            tc::tmem_ld32(taddr, v);
-#pragma unroll
-            for (int i = 0; i < 19; ++i) atomicAdd(grad + c_off.w[0] + (int64_t)m * 19 + i, v[i]);
-        } else {
-            float4* dst = reinterpret_cast<float4*>(grad + c_off.w[l] + (int64_t)m * 256);
+        // per-warp 32 x 32 FP32 transpose block (rows 36 floats apart) in the
+        // stage buffers, free once the last MMA has completed
+        float* sc = reinterpret_cast<float*>(sm.a[0]) + warp * (32 * 36);
+        if (l > 0) {
+            float4* dst = reinterpret_cast<float4*>(grad + c_off.w[l]);
 #pragma unroll 1
             for (int cc = 0; cc < 8; ++cc) {
                 float v[32];
                 tc::tmem_ld32(taddr + 32u * (uint32_t)cc, v);
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    atomicAdd(dst + 8 * cc + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+                    *reinterpret_cast<float4*>(sc + lane * 36 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                __syncwarp();
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) {
+                    const int r = 4 * rr + (lane >> 3), c4 = lane & 7;   // row r, columns 4 c4 .. 4 c4 + 3
+                    const float4 x = *reinterpret_cast<const float4*>(sc + r * 36 + 4 * c4);
+                    atomicAdd(dst + (int64_t)(m0 + r) * 64 + 8 * cc + c4, x);
+                }
+                __syncwarp();
             }
+        } else {
+            // layer 0: dW_0[o][i], o = M row, i < 19 (rows of 19 floats)
+            float v[32];
+            tc::tmem_ld32(taddr, v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<float4*>(sc + lane * 36 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            __syncwarp();
+            if (lane < 19)
+                for (int r = 0; r < 32; ++r) atomicAdd(grad + c_off.w[0] + (int64_t)(m0 + r) * 19 + lane, sc[r * 36 + lane]);
+            // layer 4: dW_4[o][i], i = M row (consecutive over the warp), o < 6
+            float u[16];
+            tc::tmem_ld16(taddr + 32u, u);
+#pragma unroll
+            for (int o = 0; o < 6; ++o) atomicAdd(grad + c_off.w[4] + o * 256 + m0 + lane, u[o]);
         }
     }
     tc::tc_fence_before();
@@ -951,9 +1008,16 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
     if ((e = launch_fwd(pair, tiles, st, x, tgt, B, Bp, pk, params, ws, grad, 0, err)) != cudaSuccess) return e;
     if ((e = launch_bwd(pair, tiles, st, ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err)) != cudaSuccess) return e;
-    const int nks = (int)(((Bp >> 6) + kDwSlice - 1) / kDwSlice);
-    if ((e = launch_ex(train_dw_kernel, (unsigned)(kMlpLayers * 2 * nks), kDwThreads, sizeof(DwSmem), 1, true, st, Bp,
-                       nks, ws, grad, err)) != cudaSuccess)
+    // K slices: 8 work items per slice (6 heavy, 2 light), about one per SM
+    int n_sm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        n_sm = 8;
+    const int64_t chunks = Bp >> 6;
+    const int want = std::max(1, n_sm / 8);
+    const int slice = (int)((chunks + want - 1) / want);
+    const int nks = (int)((chunks + slice - 1) / slice);
+    if ((e = launch_ex(train_dw_kernel, (unsigned)(8 * nks), kDwThreads, sizeof(DwSmem), 1, true, st, Bp, nks, slice,
+                       ws, grad, err)) != cudaSuccess)
         return e;
     if (lr > 0.0f) {
         const float b1 = 0.9f, b2 = 0.999f;
