@@ -13,9 +13,11 @@
 //    in the rotation angle a (d n = axis x n, d x = axis x (x - p)); the
 //    visibility of each ray is held fixed (the estimate's boundary terms,
 //    where a shadow edge or silhouette moves, are not included).
-// Accumulation: per-warp FP32 shared-memory sums over <= 128 rays, flushed
-// into per-warp FP64, written as per-unit FP64 partials, summed in unit
-// order by grad_reduce_kernel.
+// Accumulation: per-warp FP32 shared-memory sums over <= 512 rays, flushed
+// into per-warp FP64 (an FP64 warp instruction is expensive on this GPU,
+// so the flushes are kept rare), written as per-unit FP64 partials, summed
+// by grad_reduce_kernel in a fixed order (one block per entry: strided
+// thread sums, then a tree).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(128) grad_kernel(const DesignDev dz, const Tra
                 }
             }
             __syncwarp();
-            if ((batch & 3) == 3 || kb + 32 >= k1) {   // flush FP32 sums (<= 128 rays) to FP64
+            if ((batch & 15) == 15 || kb + 32 >= k1) {   // flush FP32 sums (<= 512 rays) to FP64
                 for (int e = lane; e < g.ng; e += 32) { ws.d[e] += (double)ws.f[e]; ws.f[e] = 0.0f; }
                 __syncwarp();
             }
@@ -160,14 +162,26 @@ __global__ void __launch_bounds__(128) grad_kernel(const DesignDev dz, const Tra
     }
 }
 
-__global__ void grad_reduce_kernel(const double* __restrict__ gpart, int64_t units, int ng, int G, double* d_rho,
-                                   double* d_hinge) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ng) return;
-    double t = 0.0;
-    for (int64_t u = 0; u < units; ++u) t += gpart[(size_t)u * ng + e];
-    if (e < 2 * G) d_rho[e] = t;
-    else if (d_hinge) d_hinge[e - 2 * G] = t;
+constexpr int kGradReduceThreads = 256;
+
+// Entry e = blockIdx.x: thread t sums units t, t + 256, ...; then a fixed
+// tree over the threads (deterministic).
+__global__ void __launch_bounds__(kGradReduceThreads) grad_reduce_kernel(const double* __restrict__ gpart, int64_t units,
+                                                                         int ng, int G, double* d_rho, double* d_hinge) {
+    __shared__ double red[kGradReduceThreads];
+    const int e = blockIdx.x, t = threadIdx.x;
+    double a = 0.0;
+    for (int64_t u = t; u < units; u += kGradReduceThreads) a += gpart[(size_t)u * ng + e];
+    red[t] = a;
+    __syncthreads();
+    for (int h = kGradReduceThreads / 2; h > 0; h >>= 1) {
+        if (t < h) red[t] += red[t + h];
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (e < 2 * G) d_rho[e] = red[0];
+        else if (d_hinge) d_hinge[e - 2 * G] = red[0];
+    }
 }
 
 cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double* up, const int32_t* thinge,
@@ -183,7 +197,7 @@ cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double*
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    grad_reduce_kernel<<<(g.ng + 127) / 128, 128, 0, st>>>(gpart, units, g.ng, p.G, d_rho, d_hinge);
+    grad_reduce_kernel<<<g.ng, kGradReduceThreads, 0, st>>>(gpart, units, g.ng, p.G, d_rho, d_hinge);
     return cudaGetLastError();
 }
 
