@@ -164,6 +164,27 @@ int srp_bvh_get_info(const srp_bvh* bvh, srp_bvh_info* info);
  * SRP_EDEVICE_LIMIT. */
 int srp_bvh_set_nodes(srp_ctx* ctx, srp_bvh* bvh, const float* node_data, int64_t n_floats);
 
+/* Refit `bvh` to moved vertices of the same mesh (Sec. 3.4: each step of a
+ * design optimisation re-instantiates the design at new hinge angles):
+ * the topology is kept and, on the device, the leaf-order triangle records
+ * take the new vertex positions and every node's child bounds are
+ * recomputed bottom up (a leaf slot: its triangles' AABB; an inner slot:
+ * the union of its child's slots), padded outward as srp_build_bvh pads;
+ * the grid centre c, radius R and surface area are recomputed (FP64, host)
+ * exactly as srp_build_bvh computes them.  Host arrays as srp_build_bvh:
+ * verts [V][3] float32, tris [T][3] int32 with T equal to the BVH's (the
+ * triangle list must be the one the BVH was built from; group ids are
+ * kept).  Forces traced through a refitted BVH equal those through a fresh
+ * build up to the grouping of sums (closest hits do not depend on the
+ * boxes); traversal cost grows as the boxes drift from the topology.
+ * Stream-ordered on the context's stream and synchronous (returns after
+ * the refit has completed).  SRP_EINVAL: NULL, T mismatch, vertex index
+ * out of range or non-finite coordinate (nothing is changed);
+ * SRP_EUNSUPPORTED: the node array was replaced (srp_bvh_set_nodes) by one
+ * not numbered breadth first.  Calls using `bvh` on other streams must not
+ * overlap the refit. */
+int srp_bvh_refit(srp_ctx* ctx, srp_bvh* bvh, const float* verts, int V, const int32_t* tris, int T);
+
 /* Host-only build of the same wide BVH, for inspection and serialisation
  * (no device, no context).  Two-call pattern: with node_data == NULL it
  * stores the sizes in *n_node_floats and *n_nodes and returns.  Otherwise

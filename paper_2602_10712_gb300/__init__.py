@@ -19,7 +19,7 @@ from . import _build
 
 __all__ = ["SRPError", "load", "srp_ctx_create", "srp_ctx_destroy", "srp_sync", "srp_build_bvh",
            "srp_bvh_destroy", "srp_bvh_get_info", "srp_force", "srp_design_instantiate", "TraceOpts",
-           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_force_noalloc", "srp_force_area", "srp_force_thermal", "srp_trace_samples", "srp_force_grad", "SRPForce", "MLP",
+           "srp_build_bvh_host", "srp_trace_rays", "srp_bvh_set_nodes", "srp_bvh_refit", "srp_force_noalloc", "srp_force_area", "srp_force_thermal", "srp_trace_samples", "srp_force_grad", "SRPForce", "MLP",
            "mlp_param_count", "srp_integrate", "orbit_opts", "OrbitOpts", "ForceGraph",
            "Context", "SRP_MEM_HOST", "SRP_MEM_DEVICE"]
 
@@ -93,6 +93,7 @@ def _load_locked(build_if_needed: bool):
     lib.srp_collect_stats.argtypes = [_P, i32, _P]
     lib.srp_probe_read_bandwidth.argtypes = [_P, i64, i32, i32, C.POINTER(C.c_double)]
     lib.srp_bvh_set_nodes.argtypes = [_P, _P, _P, i64]
+    lib.srp_bvh_refit.argtypes = [_P, _P, _P, i32, _P, i32]
     lib.srp_force_grad.argtypes = [_P, _P, _P, i32, _P, i32, _P, _P, _P, i32, C.POINTER(TraceOpts), _P, _P, _P]
     lib.srp_mlp_param_count.argtypes = [C.POINTER(C.c_int64)]
     lib.srp_mlp_create.argtypes = [_P, _P, C.c_uint64, C.POINTER(_P)]
@@ -294,6 +295,15 @@ def srp_bvh_get_info(b: BVH) -> dict:
 def srp_bvh_set_nodes(ctx: Context, b: BVH, node_data):
     nd = _np(node_data, np.float32).reshape(-1)
     _check(load().srp_bvh_set_nodes(ctx.handle, b.handle, _ptr(nd), nd.shape[0]))
+
+
+def srp_bvh_refit(ctx: Context, b: BVH, verts, tris):
+    """Refit b to moved vertices of the mesh it was built from (same tris):
+    the topology is kept, triangle records and node bounds are recomputed on
+    the device, and the grid centre / radius as srp_build_bvh computes them."""
+    v = _np(verts, np.float32).reshape(-1, 3)
+    t = _np(tris, np.int32).reshape(-1, 3)
+    _check(load().srp_bvh_refit(ctx.handle, b.handle, _ptr(v), v.shape[0], _ptr(t), t.shape[0]))
 
 
 def srp_build_bvh_host(verts, tris, width: int = 4):

@@ -27,6 +27,8 @@ cudaError_t launch_area(const AreaParams& p, int width, int variant, int t_max, 
 cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double* up, const int32_t* thinge,
                         const double* hax, int H, double* gpart, double* d_rho, double* d_hinge, int n_sm,
                         cudaStream_t st);
+cudaError_t launch_refit(srp_bvh* h, const float* verts, const int32_t* tris, float pad_abs, cudaStream_t st);
+
 }  // namespace srp
 
 using namespace srp;
@@ -286,6 +288,7 @@ int srp_build_bvh(srp_ctx* c, const float* verts, int V, const int32_t* tris, co
     h->max_group = -1;
     for (int t = 0; t < T; ++t) h->max_group = std::max(h->max_group, (int)group[t]);
     h->n_nodes = b.n_nodes; h->n_leaves = b.n_leaves; h->depth = b.depth;
+    h->level_start = b.level_start;
     h->build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     for (int j = 0; j < 3; ++j) h->c[j] = cen[j];
     h->R = std::sqrt(R2);
@@ -364,6 +367,98 @@ int srp_bvh_set_nodes(srp_ctx* c, srp_bvh* h, const float* node_data, int64_t n_
     CU(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     CU(cudaMemcpy(h->d_nodes, node_data, sizeof(float) * n_floats, cudaMemcpyHostToDevice), "H2D nodes");
     c->last_tab.clear();  // force a fresh design-table upload
+    // breadth-first levels of the new tree, if its numbering is breadth
+    // first (srp_bvh_refit needs that); otherwise none
+    h->level_start.clear();
+    {
+        std::vector<int32_t> depth(h->n_nodes, -1);
+        std::vector<int32_t> queue = {0};
+        depth[0] = 0;
+        bool ok = true;
+        for (size_t qi = 0; qi < queue.size() && ok; ++qi) {
+            const int32_t n = queue[qi];
+            const int32_t* ch = reinterpret_cast<const int32_t*>(node_data + (int64_t)n * nf + 6 * W);
+            for (int k = 0; k < W; ++k) {
+                if (!(node_data[(int64_t)n * nf + k] <= node_data[(int64_t)n * nf + W + k]) || ch[k] < 0) continue;
+                if (depth[ch[k]] >= 0) { ok = false; break; }   // shared child or cycle
+                depth[ch[k]] = depth[n] + 1;
+                queue.push_back(ch[k]);
+            }
+        }
+        for (int32_t n = 1; n < h->n_nodes && ok; ++n)
+            if (depth[n] < depth[n - 1]) ok = false;   // unreachable (-1) or not breadth first
+        if (ok) {
+            for (int32_t n = 0; n < h->n_nodes; ++n)
+                if (n == 0 || depth[n] != depth[n - 1]) h->level_start.push_back(n);
+            h->level_start.push_back(h->n_nodes);
+        }
+    }
+    return SRP_OK;
+}
+
+int srp_bvh_refit(srp_ctx* c, srp_bvh* h, const float* verts, int V, const int32_t* tris, int T) {
+    if (!c || !h) return fail(SRP_EINVAL, "srp_bvh_refit: NULL ctx/bvh");
+    if (V < 0 || T != h->T) return fail(SRP_EINVAL, "srp_bvh_refit: T differs from the BVH's (or V < 0)");
+    if (T > 0 && (!verts || !tris)) return fail(SRP_EINVAL, "srp_bvh_refit: NULL arrays");
+    if (h->level_start.size() < 2)
+        return fail(SRP_EUNSUPPORTED, "srp_bvh_refit: the node array was replaced by one not numbered breadth first");
+    // the builder's checks and its padding scale (over the triangles' vertices)
+    float scale = 0.0f;
+    for (int t = 0; t < T; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const int v = tris[3 * (size_t)t + k];
+            if (v < 0 || v >= V) return fail(SRP_EINVAL, "srp_bvh_refit: triangle vertex index out of range");
+            for (int j = 0; j < 3; ++j) {
+                const float x = verts[3 * (size_t)v + j];
+                if (!std::isfinite(x)) return fail(SRP_EINVAL, "srp_bvh_refit: non-finite vertex coordinate");
+                scale = std::max(scale, std::fabs(x));
+            }
+        }
+    const float pad_abs = 1e-6f * (scale + 1e-3f);
+    // grid centre and radius over all vertices, surface area (FP64), as srp_build_bvh
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < V; ++v)
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = std::min(lo[j], (double)verts[3 * (size_t)v + j]);
+            hi[j] = std::max(hi[j], (double)verts[3 * (size_t)v + j]);
+        }
+    double cen[3] = {0, 0, 0}, R2 = 0.0;
+    if (V > 0) {
+        for (int j = 0; j < 3; ++j) cen[j] = 0.5 * (lo[j] + hi[j]);
+        for (int v = 0; v < V; ++v) {
+            double r2 = 0;
+            for (int j = 0; j < 3; ++j) { const double q = verts[3 * (size_t)v + j] - cen[j]; r2 += q * q; }
+            R2 = std::max(R2, r2);
+        }
+    }
+    double area = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const float* a = verts + 3 * (size_t)tris[3 * t];
+        const float* b = verts + 3 * (size_t)tris[3 * t + 1];
+        const float* q = verts + 3 * (size_t)tris[3 * t + 2];
+        const double e1[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+        const double e2[3] = {(double)q[0] - a[0], (double)q[1] - a[1], (double)q[2] - a[2]};
+        const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                     cz = e1[0] * e2[1] - e1[1] * e2[0];
+        area += 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
+    CU(cudaSetDevice(h->device), "cudaSetDevice");
+    float* d_v = nullptr;
+    int32_t* d_t = nullptr;
+    const size_t vb = sizeof(float) * 3 * (size_t)std::max(V, 1), tb = sizeof(int32_t) * 3 * (size_t)std::max(T, 1);
+    cudaError_t e = cudaMallocAsync((void**)&d_v, vb, c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_t, tb, c->stream);
+    if (e == cudaSuccess && V > 0) e = cudaMemcpyAsync(d_v, verts, sizeof(float) * 3 * (size_t)V, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && T > 0) e = cudaMemcpyAsync(d_t, tris, sizeof(int32_t) * 3 * (size_t)T, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_refit(h, d_v, d_t, pad_abs, c->stream);
+    if (d_v) cudaFreeAsync(d_v, c->stream);
+    if (d_t) cudaFreeAsync(d_t, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "srp_bvh_refit");
+    for (int j = 0; j < 3; ++j) h->c[j] = cen[j];
+    h->R = std::sqrt(R2);
+    h->area = area;
+    c->last_tab.clear();  // the design table carries c and R
     return SRP_OK;
 }
 

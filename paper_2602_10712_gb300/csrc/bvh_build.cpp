@@ -197,6 +197,7 @@ int build_wide_bvh(const float* verts, int V, const int32_t* tris, int T, int wi
     };
 
     out->n_leaves = 0; out->depth = 0;
+    out->level_start = {0, 1};
     int root_w = new_node();
     (void)root_w;
     if (T == 0) { out->n_nodes = 1; out->depth = 1; return SRP_OK; }
@@ -248,6 +249,12 @@ int build_wide_bvh(const float* verts, int V, const int32_t* tris, int T, int wi
         }
     }
     out->n_nodes = (int)(nd.size() / node_floats);
+    // work[i] describes wide node i (nodes are created in work-list order),
+    // and the list is breadth first: depths never decrease along it
+    out->level_start.clear();
+    for (int i = 0; i < (int)work.size(); ++i)
+        if (i == 0 || work[i].depth != work[i - 1].depth) out->level_start.push_back(i);
+    out->level_start.push_back(out->n_nodes);
     return SRP_OK;
 }
 

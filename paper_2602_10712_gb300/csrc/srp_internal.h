@@ -41,6 +41,9 @@ struct BuiltBVH {                  // host result of the builder
     std::vector<float> node_data;  // W-wide nodes, packed as described above
     std::vector<int32_t> tri_order;  // leaf order -> original triangle index
     int n_nodes = 0, n_leaves = 0, depth = 0;
+    // nodes are numbered breadth first: level d (root = 0) is the index range
+    // [level_start[d], level_start[d + 1]); depth + 1 entries
+    std::vector<int32_t> level_start;
 };
 
 // Binned-SAH binary build, collapsed to `width` (4 or 8) children.
@@ -121,4 +124,5 @@ struct srp_bvh {
     int64_t bytes;
     double area;    // total surface area (FP64, from the build's vertices)
     int max_group;  // largest material group id of the mesh (-1 when empty)
+    std::vector<int32_t> level_start;   // breadth-first level ranges of the nodes (srp_bvh_refit)
 };

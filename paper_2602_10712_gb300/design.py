@@ -48,17 +48,19 @@ def _project_rho(rho):
 
 
 def optimize_tracer(ctx, mesh, rho0, angles0, sun_dir, com, target_ft, *, steps=100, lr=0.01, hinge_lo=-np.pi / 2,
-                    hinge_hi=np.pi / 2, b1=0.9, b2=0.999, eps=1e-12, **trace_opts):
+                    hinge_hi=np.pi / 2, b1=0.9, b2=0.999, eps=1e-12, refit=True, **trace_opts):
     """Design optimisation through the tracer itself: Adam on the group
     reflectances (rho [G,2]) and the hinge angles of one design to bring its
     force and torque at the given suns (target_ft [S,6]) to the target,
     L = sum_s |(F,tau)_s - target_s|^2, with the reflectances projected into
     their admissible set and the angles clipped after every step.  Each step
-    instantiates the design, builds its BVH and calls srp_force and
-    srp_force_grad (upstream 2 (ft - target)); the hinge gradient holds the
-    visibility fixed (it is exact while no shadow boundary moves).
+    instantiates the design, brings its BVH up to date (refit=True: the
+    first step builds it on the host, later steps refit it on the device to
+    the moved vertices; False: a host build every step) and calls srp_force
+    and srp_force_grad (upstream 2 (ft - target)); the hinge gradient holds
+    the visibility fixed (it is exact while no shadow boundary moves).
     Returns (rho, angles, losses [steps+1])."""
-    from . import srp_build_bvh, srp_design_instantiate, srp_force, srp_force_grad
+    from . import srp_build_bvh, srp_bvh_refit, srp_design_instantiate, srp_force, srp_force_grad
     rho = _project_rho(np.array(rho0, dtype=np.float64))
     ang = np.array(angles0, dtype=np.float64)
     tri_hinge = np.asarray(mesh.vhinge)[np.asarray(mesh.tris)[:, 0]].astype(np.int32)
@@ -67,9 +69,15 @@ def optimize_tracer(ctx, mesh, rho0, angles0, sun_dir, com, target_ft, *, steps=
     v = np.zeros_like(p)
     losses = []
     tgt = np.asarray(target_ft, np.float64)
+    b = None
     for it in range(steps + 1):
         verts = srp_design_instantiate(mesh.verts, mesh.vhinge, mesh.hinges, ang)
-        b = srp_build_bvh(ctx, verts, mesh.tris, mesh.group, 4)
+        if b is not None and refit:
+            srp_bvh_refit(ctx, b, verts, mesh.tris)
+        else:
+            if b is not None:
+                b.close()
+            b = srp_build_bvh(ctx, verts, mesh.tris, mesh.group, 4)
         ft = srp_force(ctx, [b], rho.astype(np.float32)[None], sun_dir, com[None], **trace_opts)[0]
         d = ft - tgt
         losses.append(float(np.sum(d * d)))
@@ -78,7 +86,6 @@ def optimize_tracer(ctx, mesh, rho0, angles0, sun_dir, com, target_ft, *, steps=
             break
         d_rho, d_h = srp_force_grad(ctx, b, rho.astype(np.float32), sun_dir, com, 2.0 * d, tri_hinge=tri_hinge,
                                     hinge_axes=mesh.hinges, **trace_opts)
-        b.close()
         g = np.concatenate([np.asarray(d_rho).ravel(), np.asarray(d_h)])
         m = b1 * m + (1 - b1) * g
         v = b2 * v + (1 - b2) * g * g

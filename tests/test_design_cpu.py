@@ -24,6 +24,8 @@ def test_optimize_tracer_recovers_an_affine_model(monkeypatch):
 
     monkeypatch.setattr(srp, "srp_design_instantiate", lambda v, vh, hg, ang: state.__setitem__("ang", np.array(ang)))
     monkeypatch.setattr(srp, "srp_build_bvh", lambda ctx, v, t, g, w: types.SimpleNamespace(close=lambda: None))
+    refits = []
+    monkeypatch.setattr(srp, "srp_bvh_refit", lambda ctx, b, v, t: refits.append(1))
     monkeypatch.setattr(srp, "srp_force", lambda ctx, bvhs, rho, sun, com, **kw: forces(rho[0], state["ang"])[None])
 
     def grad(ctx, b, rho, sun, com, up, tri_hinge=None, hinge_axes=None, **kw):
@@ -42,6 +44,7 @@ def test_optimize_tracer_recovers_an_affine_model(monkeypatch):
 
     # the generating design inside the admissible set: recovered
     rho, ang, losses = run(-1.0, 1.0)
+    assert len(refits) == 600   # one host build, then a device refit per step
     assert losses[-1] < 1e-4 * losses[0]
     assert np.abs(rho - rho_true).max() < 0.02 and np.abs(ang - ang_true).max() < 0.02
     # a hinge range that excludes the first true angle (0.3): clipped to its bound
