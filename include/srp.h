@@ -323,13 +323,17 @@ int srp_trace_samples(srp_ctx* ctx, const float* verts, int V, const int32_t* vh
  *   d_rho   [G][2] float64   dL/d(rho_s, rho_d) per material group (exact
  *                            along the fixed paths: the bounce branch
  *                            probability does not depend on rho)
- *   d_hinge [H]    float64   dL/d(hinge angle) (K = 1 only; H = 0 skips it):
- *                            each ray's hit point is carried rigidly by its
- *                            facet as the hinge turns, visibility fixed
+ *   d_hinge [H]    float64   dL/d(hinge angle) (H = 0 skips it), visibility
+ *                            fixed: each path keeps its facets, branch
+ *                            choices and random draws; its primary hit point
+ *                            is carried rigidly by its facet as the hinge
+ *                            turns, later hits are re-intersected with their
+ *                            (turning or fixed) facets' planes, outgoing
+ *                            directions follow the turned normals
  * tri_hinge [T] int32 (by original triangle index; -1 = not on a hinge) and
  * hinge_axes [H][6] (point, unit axis; the axes the design was instantiated
  * with, srp_design_instantiate) describe the hinges; H <= 8.  The COM is
- * held fixed.  Memory per opts->mem; SRP_EUNSUPPORTED for H > 0 with K > 1.
+ * held fixed.  Memory per opts->mem.
  * Results are reproducible to FP32 rounding (per-warp FP32 atomics). */
 int srp_force_grad(srp_ctx* ctx, const srp_bvh* bvh, const float* rho, int G,
                    const double* sun_dir, int S, const double* com,

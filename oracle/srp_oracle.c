@@ -195,6 +195,7 @@ typedef struct {
     double n[8][3];     /* facing normal                                 */
     double cs[8];       /* cos = -n.d                                    */
     double dout[8][3];  /* outgoing direction (k < K)                    */
+    double us[8][3];    /* diffuse branch: the uniform unit-sphere point */
 } path_t;
 
 static void grid_ray(const scene_t* sc, const double e[3], uint64_t i, uint32_t s,
@@ -271,6 +272,7 @@ static void trace_path(const scene_t* sc, const double e[3], uint64_t i, uint32_
             for (int j = 0; j < 3; ++j) dout[j] = L > 0.0 ? v[j] / L : n[j];
             wout = 2.0 * w * rd;
             pth->br[h] = 1;
+            pth->us[h][0] = rr * cos(phi); pth->us[h][1] = rr * sin(phi); pth->us[h][2] = z;
         }
         for (int j = 0; j < 3; ++j) { dp[j] = w * d[j] - wout * dout[j]; pth->dout[h][j] = dout[j]; }
         cross3(arm, dp, tq);
@@ -321,6 +323,90 @@ static void path_grad(const scene_t* sc, const path_t* p, const double gF[3], co
         wbar_next = wbar;
     }
 }
+
+/* Rotation of v about the unit axis a by angle ang (Rodrigues). */
+static void rotate(const double a[3], double ang, const double v[3], double o[3])
+{
+    double c = cos(ang), s = sin(ang), axv[3];
+    cross3(a, v, axv);
+    double ad = dot3(a, v);
+    for (int j = 0; j < 3; ++j) o[j] = v[j] * c + axv[j] * s + a[j] * ad * (1.0 - c);
+}
+
+/* Value of a recorded path's contribution L = sum_k q_k . dp_k with hinge
+ * hh turned by `ang`, in the fixed-visibility reading of the hinge
+ * derivative: the path keeps its facets, its branch choices and its random
+ * draws, and the facets on hinge hh turn with it.  The primary hit point is
+ * carried by its facet (as at K = 1: weight w c(ang) / c0); every later hit
+ * is the intersection of the outgoing ray with the plane of the same facet
+ * (its recorded facing normal, turned if the facet turns); the outgoing
+ * direction follows the turned normal (specular: d + 2 c n; diffuse: the
+ * same uniform sphere point u, direction (n + u) / |n + u|).  At ang = 0 it
+ * reproduces the path's own deposits. */
+static double path_value_hinge(const scene_t* sc, const path_t* p, const double gF[3], const double gT[3],
+                               const int32_t* thinge, int hh, const double ap[3], const double aa[3], double ang)
+{
+    double x[3], n[3], d[3], rel[3], o[3];
+    const int f0 = p->f[0];
+    for (int j = 0; j < 3; ++j) { x[j] = p->x[0][j]; n[j] = p->n[0][j]; d[j] = p->d[0][j]; }
+    if (thinge[f0] == hh) {
+        for (int j = 0; j < 3; ++j) rel[j] = x[j] - ap[j];
+        rotate(aa, ang, rel, o);
+        for (int j = 0; j < 3; ++j) x[j] = o[j] + ap[j];
+        rotate(aa, ang, p->n[0], n);
+    }
+    double c = -dot3(n, d);
+    double w = p->w[0] * c / p->cs[0];
+    double L = 0.0;
+    for (int k = 0; k < p->m; ++k) {
+        const int g = sc->group[p->f[k]];
+        const double rs = sc->rho[2 * g], rd = sc->rho[2 * g + 1];
+        double arm[3], q[3], dp[3];
+        for (int j = 0; j < 3; ++j) arm[j] = x[j] - sc->com[j];
+        cross3(gT, arm, q);
+        for (int j = 0; j < 3; ++j) q[j] += gF[j];
+        if (k + 1 == sc->K) {
+            const double cn = 2.0 * rs * c + (2.0 / 3.0) * rd;
+            for (int j = 0; j < 3; ++j) dp[j] = w * ((1.0 - rs) * d[j] - cn * n[j]);
+            L += dot3(q, dp);
+            break;
+        }
+        double dout[3], wout;
+        if (p->br[k] == 0) {
+            for (int j = 0; j < 3; ++j) dout[j] = d[j] + 2.0 * c * n[j];
+            wout = 2.0 * w * rs;
+        } else {
+            double v[3];
+            for (int j = 0; j < 3; ++j) v[j] = n[j] + p->us[k][j];
+            const double Ln = sqrt(dot3(v, v));
+            for (int j = 0; j < 3; ++j) dout[j] = Ln > 0.0 ? v[j] / Ln : n[j];
+            wout = 2.0 * w * rd;
+        }
+        for (int j = 0; j < 3; ++j) dp[j] = w * d[j] - wout * dout[j];
+        L += dot3(q, dp);
+        if (k + 1 >= p->m) break;   /* the outgoing ray left the craft */
+        const int f1 = p->f[k + 1];
+        double v0[3], n1[3];
+        for (int j = 0; j < 3; ++j) { v0[j] = sc->tv[9 * (size_t)f1 + j]; n1[j] = p->n[k + 1][j]; }
+        if (thinge[f1] == hh) {
+            for (int j = 0; j < 3; ++j) rel[j] = v0[j] - ap[j];
+            rotate(aa, ang, rel, o);
+            for (int j = 0; j < 3; ++j) v0[j] = o[j] + ap[j];
+            double nt[3];
+            rotate(aa, ang, n1, nt);
+            for (int j = 0; j < 3; ++j) n1[j] = nt[j];
+        }
+        for (int j = 0; j < 3; ++j) rel[j] = v0[j] - x[j];
+        const double t = dot3(n1, rel) / dot3(n1, dout);
+        for (int j = 0; j < 3; ++j) { x[j] += t * dout[j]; n[j] = n1[j]; d[j] = dout[j]; }
+        c = -dot3(n, d);
+        w = wout;
+    }
+    return L;
+}
+
+/* Step of the central difference of path_value_hinge (radians). */
+#define OR_HINGE_STEP 1e-6
 
 /* Hinge derivative of a K=1 hit: the ray's surface element is carried
  * rigidly by the facet, so the ray's contribution is (w/c0) c(a) q.G(n(a)). */
@@ -400,6 +486,20 @@ static void* worker(void* arg)
                     int hh = wk->thinge[p.f[0]];
                     if (hh >= 0)
                         wk->grad_h[hh] += hinge_term(sc, &p, g6, g6 + 3, wk->hp + 6 * hh, wk->hp + 6 * hh + 3);
+                } else if (wk->H > 0 && sc->K > 1) {
+                    /* every hinge that turns a facet of the path: central
+                     * difference of the fixed-visibility path value */
+                    for (int k = 0; k < p.m; ++k) {
+                        const int hh = wk->thinge[p.f[k]];
+                        if (hh < 0 || hh >= wk->H) continue;
+                        int dup = 0;
+                        for (int k2 = 0; k2 < k; ++k2) dup |= wk->thinge[p.f[k2]] == hh;
+                        if (dup) continue;
+                        const double* ap = wk->hp + 6 * hh;
+                        const double vp = path_value_hinge(sc, &p, g6, g6 + 3, wk->thinge, hh, ap, ap + 3, OR_HINGE_STEP);
+                        const double vm = path_value_hinge(sc, &p, g6, g6 + 3, wk->thinge, hh, ap, ap + 3, -OR_HINGE_STEP);
+                        wk->grad_h[hh] += (vp - vm) / (2.0 * OR_HINGE_STEP);
+                    }
                 }
             }
         }
@@ -461,7 +561,9 @@ void or_grid(const float* verts, int V, double c_out[3], double* R_out)
  *   (n = 0: the full grid, off = 0, stride = 1).
  *   out_ft [S][6] (F, tau), out_sigma [S][6] or NULL.
  *   Gradient (optional, up != NULL): upstream dL/d(F,tau) [S][6];
- *   d_rho [G][2] and d_hinge [H] are ADDED to.  Hinges need K == 1.
+ *   d_rho [G][2] and d_hinge [H] are ADDED to.  Hinges: K = 1 the
+ *   analytic derivative of hinge_term; K > 1 the central difference of
+ *   path_value_hinge (fixed visibility) per path.
  */
 int or_force(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
              const double* rho, int G, const double* sun, int S, const double* com,
@@ -527,13 +629,6 @@ int or_force(const float* verts, int V, const int32_t* tris, const int32_t* grou
  * re-tracing.  Returns the central difference of L = sum_s up_s.(F_s,tau_s)
  * in d_hinge[H].  Single-threaded; for small test cases.
  */
-static void rotate(const double a[3], double ang, const double v[3], double o[3])
-{
-    double c = cos(ang), s = sin(ang), axv[3];
-    cross3(a, v, axv);
-    double ad = dot3(a, v);
-    for (int j = 0; j < 3; ++j) o[j] = v[j] * c + axv[j] * s + a[j] * ad * (1.0 - c);
-}
 
 int or_hinge_fd_fixed_hits(const float* verts, int V, const int32_t* tris, const int32_t* group, int T,
                            const double* rho, int G, const double* sun, int S, const double* com,

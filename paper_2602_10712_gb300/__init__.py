@@ -679,7 +679,7 @@ class SRPForce:
                 th = torch.from_numpy(np.asarray(d["vhinge"])[np.asarray(d["tris"])[:, 0]].astype(np.int32)).to(rho.device)
                 ha = torch.from_numpy(np.asarray(d["hinges"], np.float64)).to(rho.device)
                 o = dict(fctx.opts)
-                use_h = H > 0 and o.get("max_bounces", 1) == 1
+                use_h = H > 0
                 dr, dh = srp_force_grad(fctx.srp_ctx, fctx.bvh, rho.detach().reshape(-1, 2).contiguous().float(),
                                         sun_dir.detach().contiguous().double(), com.detach().reshape(3).contiguous().double(),
                                         g.contiguous().double(), th if use_h else None, ha if use_h else None, **o)

@@ -743,8 +743,6 @@ extern "C" int srp_force_grad(srp_ctx* c, const srp_bvh* bvh, const float* rho, 
                               const srp_trace_opts* o, const double* upstream, double* d_rho, double* d_hinge) {
     if (!o) return fail(SRP_EINVAL, "srp_force_grad: NULL opts");
     if (H < 0 || H > 8) return fail(SRP_EINVAL, "srp_force_grad: H must be in 0..8");
-    if (H > 0 && o->max_bounces != 1)
-        return fail(SRP_EUNSUPPORTED, "srp_force_grad: hinge gradients are defined for max_bounces == 1");
     if (H > 0 && (!tri_hinge || !hinge_axes || !d_hinge)) return fail(SRP_EINVAL, "srp_force_grad: NULL hinge arrays");
     srp_trace_opts oo = *o;
     oo.sun_per_design = 0;

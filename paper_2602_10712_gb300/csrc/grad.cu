@@ -1,18 +1,20 @@
 // grad.cu -- reverse-mode gradient of the SRP ray-grid estimate.
 //
 // For upstream weights g_s = dL/d(F_s, tau_s) (6 per sun direction) the
-// kernel returns dL/d(rho_s, rho_d) per material group and, for K = 1,
-// dL/d(hinge angle) per hinge.  It replays exactly the forward's rays (same
+// kernel returns dL/d(rho_s, rho_d) per material group and dL/d(hinge
+// angle) per hinge.  It replays exactly the forward's rays (same
 // Philox counters, same traversal and shading helpers), so the gradient is
 // that of the very estimate srp_force returns:
 //  * reflectances: the branch choice has a fixed probability, so every path
 //    is fixed and its deposits are polynomials in rho (exact derivative);
 //    reverse sweep over the recorded hits, last hit first;
-//  * hinges (K = 1): each ray's surface element is carried rigidly by its
-//    facet, so its contribution (w / cos0) cos(a) q.G(n(a)) is differentiated
-//    in the rotation angle a (d n = axis x n, d x = axis x (x - p)); the
-//    visibility of each ray is held fixed (the estimate's boundary terms,
-//    where a shadow edge or silhouette moves, are not included).
+//  * hinges: each ray's primary surface element is carried rigidly by its
+//    facet, so at K = 1 its contribution (w / cos0) cos(a) q.G(n(a)) is
+//    differentiated in the rotation angle a (d n = axis x n, d x = axis x
+//    (x - p)); at K > 1 the tangents run along the recorded path
+//    (hinge_path_tangent).  The visibility of each ray is held fixed (the
+//    estimate's boundary terms, where a shadow edge or silhouette moves,
+//    are not included).
 // Accumulation: per-warp FP32 shared-memory sums over <= 512 rays, flushed
 // into per-warp FP64 (an FP64 warp instruction is expensive on this GPU,
 // so the flushes are kept rare), written as per-unit FP64 partials, summed
@@ -42,6 +44,66 @@ struct GradWarpSmem {
     float f[kMaxGradEntries];
     double d[kMaxGradEntries];
 };
+
+// d/da of one recorded path's L = sum_k q_k . dp_k for hinge `hh` (point
+// ap, unit axis aa) in the fixed-visibility reading: the path keeps its
+// facets, branch choices and random draws, facets on the hinge turn with
+// it (d x = aa x (x - ap), d v = aa x v).  The primary hit point is carried
+// by its facet (weight w c(a) / c0, as for K = 1); each later hit is the
+// intersection of the outgoing ray with its facet's plane; the outgoing
+// direction follows the turned normal (specular d + 2 c n; diffuse
+// (n + u) / |n + u| with the sphere point u = l dout - n, l = 2 dout . n,
+// held).  Forward-mode tangents along the path, base values as recorded.
+__device__ float hinge_path_tangent(const DesignDev& dz, int hh, float3 ap, float3 aa, int m, int K, const int* hid,
+                                    const int* fr, const int* br, const float3* xr, const float3* nr, const float3* dr,
+                                    const float3* dout_r, const float* csr, const float* wr, const float* rsr,
+                                    const float* rdr, float3 com, float3 gF, float3 gT) {
+    const float3 zero = f3(0.0f, 0.0f, 0.0f);
+    float3 dx = hid[0] == hh ? cross(aa, xr[0] - ap) : zero;
+    float3 dn = hid[0] == hh ? cross(aa, nr[0]) : zero;
+    float3 dd = zero;
+    float dc = -dot(dn, dr[0]);
+    float dw = wr[0] * dc / csr[0];
+    float dL = 0.0f;
+    for (int k = 0; k < m; ++k) {
+        const float3 x = xr[k], n = nr[k], d = dr[k];
+        const float c = csr[k], w = wr[k], rs = rsr[k], rd = rdr[k];
+        const float3 q = gF + cross(gT, x - com), dq = cross(gT, dx);
+        if (k + 1 == K) {
+            const float cn = 2.0f * rs * c + (2.0f / 3.0f) * rd, dcn = 2.0f * rs * dc;
+            const float3 G = (1.0f - rs) * d - cn * n;
+            const float3 dG = (1.0f - rs) * dd - dcn * n - cn * dn;
+            dL += w * dot(dq, G) + dot(q, dw * G + w * dG);
+            break;
+        }
+        const float3 o = dout_r[k];
+        float3 dO;
+        float w2, dw2;
+        if (br[k] == 0) {
+            dO = dd + (2.0f * dc) * n + (2.0f * c) * dn;
+            w2 = 2.0f * w * rs; dw2 = 2.0f * dw * rs;
+        } else {
+            const float l = 2.0f * dot(o, n);
+            dO = (1.0f / l) * (dn - dot(o, dn) * o);
+            w2 = 2.0f * w * rd; dw2 = 2.0f * dw * rd;
+        }
+        dL += dot(dq, w * d - w2 * o) + dot(q, dw * d + w * dd - dw2 * o - w2 * dO);
+        if (k + 1 >= m) break;   // the outgoing ray left the craft
+        const float4 v4 = __ldg(dz.tri + 3 * (size_t)fr[k + 1]);
+        const float3 v0 = f3(v4.x, v4.y, v4.z), n1 = nr[k + 1];
+        const float3 dv0 = hid[k + 1] == hh ? cross(aa, v0 - ap) : zero;
+        const float3 dn1 = hid[k + 1] == hh ? cross(aa, n1) : zero;
+        const float den = dot(n1, o);
+        const float t = dot(n1, v0 - x) / den;
+        const float dt = (dot(dn1, v0 - x) + dot(n1, dv0 - dx) - t * (dot(dn1, o) + dot(n1, dO))) / den;
+        dx = dx + dt * o + t * dO;
+        dn = dn1;
+        dd = dO;
+        dc = -(dot(dn, o) + dot(n1, dd));
+        dw = dw2;
+    }
+    return dL;
+}
 
 template <int W>
 __global__ void __launch_bounds__(128) grad_kernel(const DesignDev dz, const TraceParams p, const GradParams g) {
@@ -116,6 +178,24 @@ __global__ void __launch_bounds__(128) grad_kernel(const DesignDev dz, const Tra
                         wbar += wbar_out * 2.0f * rb;
                     }
                     wbar_next = wbar;
+                }
+                // ---- hinge angles, K > 1: tangents along the recorded path
+                if (g.H > 0 && p.K > 1 && m > 0 && g.thinge) {
+                    int hid[kMaxBounces];
+                    for (int q = 0; q < m; ++q)
+                        hid[q] = __ldg(g.thinge + __float_as_uint(__ldg(dz.tri + 3 * (size_t)fr[q]).w));
+                    for (int q = 0; q < m; ++q) {
+                        const int hh = hid[q];
+                        bool dup = hh < 0 || hh >= g.H;
+                        for (int q2 = 0; q2 < q; ++q2) dup = dup || hid[q2] == hh;
+                        if (dup) continue;
+                        const double* hp = g.hax + 6 * hh;
+                        const float3 ap = f3((float)hp[0], (float)hp[1], (float)hp[2]);
+                        const float3 aa = f3((float)hp[3], (float)hp[4], (float)hp[5]);
+                        const float dL = hinge_path_tangent(dz, hh, ap, aa, m, p.K, hid, fr, br, xr, nr, dr, dout_r, csr,
+                                                            wr, rsr, rdr, ic.com, gF, gT);
+                        atomicAdd(&ws.f[2 * p.G + hh], dL);
+                    }
                 }
                 // ---- hinge angle (K = 1): surface element carried by its facet
                 if (g.H > 0 && p.K == 1 && m == 1) {
