@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
 // ---------------------------------------------------------------------------
 // Span pre-pass (full-grid launches): which batches of 32 neighbouring
 // pixels can meet the scene.  One block per (design, sun) item projects the
-// BVH boxes three levels below the root (W = 4: up to 64; W = 8: two
+// BVH boxes four levels below the root (W = 4: up to 256; W = 8: two
 // levels, up to 64) onto the grid plane as pixel rectangles widened by 2 pixels
 // (FP32 rounding of the ray origins is ~1e-4 pixel); a ray outside every
 // rectangle misses every box, so it cannot hit a triangle and deposits
@@ -383,20 +383,25 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
 // rectangle, count = batches up to the last one that does; rowoff = the
 // exclusive prefix of the counts (rowoff[ny] = the item's live batches).
 // ---------------------------------------------------------------------------
-constexpr int kTopBoxes = 64;   // box slots of the span pre-pass
+// Box slots of the span pre-pass: W = 4 -- the nodes four levels below the
+// root (256; on the benchmark's satellite four levels leave 16 % fewer live
+// batches than three), W = 8 -- two levels (64).
+template <int W>
+__host__ __device__ constexpr int top_boxes() { return W == 4 ? 256 : 64; }
+constexpr int kMaxTopBoxes = 256;
 
-// Pixel rectangle of box slot bi (0..63): W = 4 -- the node three levels
-// below the root along child digits (bi>>4, (bi>>2)&3, bi&3); W = 8 -- two
+// Pixel rectangle of box slot bi: W = 4 -- the node four levels below the
+// root along child digits (bi>>6, (bi>>4)&3, (bi>>2)&3, bi&3); W = 8 -- two
 // levels (bi>>3, bi&7).  A leaf on the way stands for its whole subtree (the
 // slot whose remaining digits are 0 carries it, the others are empty).
 template <int W>
 __device__ __forceinline__ float4 top_rect(const DesignDev& dz, const ItemConst& ic, int bi) {
     const float* nd0 = reinterpret_cast<const float*>(dz.nodes);
     constexpr int NFL = W == 4 ? 32 : 64;   // floats per node
-    constexpr int levels = W == 4 ? 3 : 2;
-    int digit[3];
-    if (W == 4) { digit[0] = bi >> 4; digit[1] = (bi >> 2) & 3; digit[2] = bi & 3; }
-    else { digit[0] = bi >> 3; digit[1] = bi & 7; digit[2] = 0; }
+    constexpr int levels = W == 4 ? 4 : 2;
+    int digit[4];
+    if (W == 4) { digit[0] = bi >> 6; digit[1] = (bi >> 4) & 3; digit[2] = (bi >> 2) & 3; digit[3] = bi & 3; }
+    else { digit[0] = bi >> 3; digit[1] = bi & 7; digit[2] = 0; digit[3] = 0; }
     const float* nd = nd0;
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     bool ok = false;
@@ -429,7 +434,8 @@ __device__ __forceinline__ float4 top_rect(const DesignDev& dz, const ItemConst&
 
 template <int W>
 __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
-    __shared__ float4 rect[kTopBoxes];
+    constexpr int kTopBoxes = top_boxes<W>();
+    __shared__ float4 rect[kMaxTopBoxes];
     __shared__ int wtot[4];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int64_t items = (int64_t)p.D * p.S;
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
         ItemConst ic;
         item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s)),
                    p.com + 3 * dl, p.rho + (size_t)dl * p.G * 2, p.design_base + dl, p.sun_base + s);
-        if (t < kTopBoxes) rect[t] = top_rect<W>(dz, ic, t);
+        for (int bi = t; bi < kTopBoxes; bi += blockDim.x) rect[bi] = top_rect<W>(dz, ic, bi);
         __syncthreads();
         const int nbx = p.nx / 32, ny = p.ny;
         int32_t* ro = p.rowoff + (size_t)item * (ny + 1);

@@ -1,7 +1,11 @@
 """srp_bvh_refit: a BVH built at one set of hinge angles and refitted on the
 device to the vertices of another traces the same forces as a fresh host
-build at the new angles (closest hits do not depend on the boxes; only the
-grouping of sums may differ), with the same grid centre and radius."""
+build at the new angles (closest hits do not depend on the boxes), with the
+same grid centre and radius.  Only the grouping of sums may differ: the
+span pre-pass projects the trees' boxes four levels down, so the two trees
+split the live batches into tiles differently and the FP32 tile sums round
+differently (about 1e-9 of |F|); the bound is 1e-7 of |F|, far below one
+ray's deposit at 256^2 rays (about 5e-5)."""
 import numpy as np
 import pytest
 
@@ -42,12 +46,12 @@ def test_refit_matches_fresh_build(srp, case, width):
         fr = _forces(srp, ctx, b, rho, sun, K)
         ff = _forces(srp, ctx, fresh, rho, sun, K)
         scale = np.abs(ff[:, :3]).max()
-        assert np.max(np.abs(fr - ff)) <= 1e-9 * scale + 1e-300, (K, np.max(np.abs(fr - ff)), scale)
+        assert np.max(np.abs(fr - ff)) <= 1e-7 * scale + 1e-300, (K, np.max(np.abs(fr - ff)), scale)
     # refitting back to the build's vertices restores its forces
     srp.srp_bvh_refit(ctx, b, v0, m.tris)
     b0 = srp.srp_build_bvh(ctx, v0, m.tris, m.group, width)
     f0, g0 = _forces(srp, ctx, b, rho, sun, 3), _forces(srp, ctx, b0, rho, sun, 3)
-    assert np.max(np.abs(f0 - g0)) <= 1e-9 * np.abs(g0[:, :3]).max()
+    assert np.max(np.abs(f0 - g0)) <= 1e-7 * np.abs(g0[:, :3]).max()
     b.close(); fresh.close(); b0.close()
 
 
