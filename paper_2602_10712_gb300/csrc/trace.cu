@@ -450,7 +450,32 @@ __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
         ItemConst ic;
         item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s)),
                    p.com + 3 * dl, p.rho + (size_t)dl * p.G * 2, p.design_base + dl, p.sun_base + s);
-        for (int bi = t; bi < kTopBoxes; bi += blockDim.x) rect[bi] = top_rect<W>(dz, ic, bi);
+        // the non-empty rectangles, compacted (a small tree fills few of
+        // the slots): per thread its slots t, t + 128, ..., then a block scan
+        // of the counts gives each thread its output range
+        constexpr int kPer = (kTopBoxes + 127) / 128;
+        float4 mine[kPer];
+        int nv = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int bi = t + 128 * k;
+            mine[k] = bi < kTopBoxes ? top_rect<W>(dz, ic, bi) : make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+            nv += mine[k].x <= mine[k].y ? 1 : 0;
+        }
+        int incl = nv;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane == 31) wtot[w] = incl;
+        __syncthreads();
+        int pos = incl - nv;
+        for (int k = 0; k < w; ++k) pos += wtot[k];
+        const int nrect = wtot[0] + wtot[1] + wtot[2] + wtot[3];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k)
+            if (mine[k].x <= mine[k].y) rect[pos++] = mine[k];
         __syncthreads();
         const int nbx = p.nx / 32, ny = p.ny;
         int32_t* ro = p.rowoff + (size_t)item * (ny + 1);
@@ -461,7 +486,7 @@ __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
             int cnt = 0;
             if (y < ny) {
                 float xmin = INFINITY, xmax = -INFINITY;
-                for (int j = 0; j < kTopBoxes; ++j) {
+                for (int j = 0; j < nrect; ++j) {
                     const float4 r = rect[j];
                     if (r.z < (float)(y + 1) && r.w > (float)y) { xmin = fminf(xmin, r.x); xmax = fmaxf(xmax, r.y); }
                 }
