@@ -106,7 +106,10 @@ __device__ float hinge_path_tangent(const DesignDev& dz, int hh, float3 ap, floa
 }
 
 template <int W>
-__global__ void __launch_bounds__(128) grad_kernel(const DesignDev dz, const TraceParams p, const GradParams g) {
+// Six resident blocks per SM (<= 80 registers, a few spills): 24 warps hide
+// the traversal's load latency better than 16 warps at 128 registers
+// (+10 % at K = 1, +7 % at K = 3 on the box-wing, bit-identical).
+__global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const TraceParams p, const GradParams g) {
     __shared__ GradWarpSmem sm[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     GradWarpSmem& ws = sm[warp];
@@ -271,7 +274,7 @@ cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double*
     g.up = up; g.thinge = thinge; g.hax = hax; g.H = H; g.ng = 2 * p.G + H; g.gpart = gpart;
     const int64_t units = (int64_t)p.S * p.cpb;
     if (units > 0 && p.n > 0) {
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + 3) / 4, (int64_t)n_sm * 8));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + 3) / 4, (int64_t)n_sm * 12));
         if (dz.width == 8) grad_kernel<8><<<grid, 128, 0, st>>>(dz, p, g);
         else grad_kernel<4><<<grid, 128, 0, st>>>(dz, p, g);
         cudaError_t e = cudaGetLastError();

@@ -108,6 +108,17 @@ __device__ __forceinline__ float tanh_approx(float x) {
     return y;
 }
 
+// (r0, r1) = (a0, a1) * (b0, b1) + (c0, c1) by one packed FP32 FMA
+// (fma.rn.f32x2: the rounding of two fmaf, one instruction).
+__device__ __forceinline__ void fma_x2(float a0, float a1, float b0, float b1, float c0, float c1, float& r0,
+                                       float& r1) {
+    asm("{\n .reg .b64 a, b, c, r;\n"
+        " mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n mov.b64 c, {%6, %7};\n"
+        " fma.rn.f32x2 r, a, b, c;\n mov.b64 {%0, %1}, r;\n}"
+        : "=f"(r0), "=f"(r1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
+
 // Two floats -> BF16 (round to nearest even), a in the low half.
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     const __nv_bfloat162_raw h = __floats2bfloat162_rn(a, b);
@@ -152,7 +163,8 @@ __device__ __forceinline__ void store_inputs(MlpFwdSmem& sm, const float (&v)[19
 // Epilogue of one 16-feature piece of chunk c for row r: accumulator words
 // u (TMEM), hb = half the bias (smem).  h = z/2 = fma(0.5, acc, b/2) equals
 // 0.5 (acc + b) exactly (scaling by 2 commutes with rounding); silu =
-// h + h tanh(h); BF16 pairs by one cvt each; into the A buffer; then signal
+// h + h tanh(h), two activations per packed FMA; BF16 pairs by one cvt
+// each; into the A buffer; then signal
 // chunk c.  Only the last chunk's signal carries the tcgen05 fence: the
 // next layer writes the other accumulator, and this one is rewritten only
 // after chunk 3 has been signalled.
@@ -165,9 +177,10 @@ __device__ __forceinline__ void epi_chunk(MlpFwdSmem& sm, const uint32_t (&u)[16
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int k = 8 * q + 2 * j;
-            const float h0 = fmaf(0.5f, __uint_as_float(u[k]), hb[c0 + k]);
-            const float h1 = fmaf(0.5f, __uint_as_float(u[k + 1]), hb[c0 + k + 1]);
-            const float s0 = fmaf(h0, tanh_approx(h0), h0), s1 = fmaf(h1, tanh_approx(h1), h1);
+            const float2 b2 = *reinterpret_cast<const float2*>(hb + c0 + k);
+            float h0, h1, s0, s1;
+            fma_x2(0.5f, 0.5f, __uint_as_float(u[k]), __uint_as_float(u[k + 1]), b2.x, b2.y, h0, h1);
+            fma_x2(h0, h1, tanh_approx(h0), tanh_approx(h1), h0, h1, s0, s1);
             asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p[j]) : "f"(s1), "f"(s0));   // s0 in the low half
         }
         *reinterpret_cast<uint4*>(sm.act + tc::kmajor_off(r, c0 + 8 * q, 256)) = make_uint4(p[0], p[1], p[2], p[3]);
