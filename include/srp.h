@@ -364,6 +364,21 @@ int srp_mlp_infer(srp_ctx* ctx, const srp_mlp* mlp, const float* x, int64_t B, f
  * grad_out (host [P], may be NULL) the gradient.  1 <= B <= 2^24. */
 int srp_mlp_train_step(srp_ctx* ctx, srp_mlp* mlp, const float* x, const float* t, int64_t B, float lr,
                        float* loss_out, float* grad_out, int mem);
+/* n_steps Adam steps (the optimisation loop of Sec. 3.3) on batches
+ * gathered from a data set resident on the device: x [n][19] and t [n][6]
+ * (device float32), idx [n_steps][batch] (device int32, row numbers of the
+ * data set: step s trains on rows idx[s*batch .. s*batch + batch - 1]),
+ * lr [n_steps] (host float32, each finite and > 0).  Each step computes
+ * the arithmetic of srp_mlp_train_step on the gathered (x, t) with lr[s];
+ * the gather is part of the first kernel's loads, and the steps are queued
+ * from this call without host round trips.  Asynchronous on the context's
+ * stream (idx and the data must stay valid until it has run); the caller
+ * reads the loss with srp_mlp_train_step (lr = 0) or the parameters with
+ * srp_mlp_get_params.  1 <= n <= 2^31, 1 <= batch <= 2^24, n_steps >= 0.
+ * An index outside 0..n-1 reads a zero row and is reported by the next
+ * srp_sync as SRP_EDEVICE_LIMIT. */
+int srp_mlp_train_epoch(srp_ctx* ctx, srp_mlp* mlp, const float* x, const float* t, int64_t n,
+                        const int32_t* idx, int64_t batch, int64_t n_steps, const float* lr);
 /* Input gradient of the proxy (what Alg. 1 back-propagates from the orbit
  * loss into the design): gx [B][19] = (dy/dx)^T wy for wy [B][6], per row;
  * BF16 GEMMs with FP32 accumulation as in training.  mem = srp_mem of x, wy

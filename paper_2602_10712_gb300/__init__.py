@@ -109,6 +109,7 @@ def _load_locked(build_if_needed: bool):
     lib.srp_integrate.argtypes = [_P, _P, _P, i32, _P, _P, _P, _P, _P, _P, _P, i32]
     lib.srp_mlp_train_step.argtypes = [_P, _P, _P, _P, i64, C.c_float, _P, _P, i32]
     lib.srp_mlp_grad_input.argtypes = [_P, _P, _P, _P, i64, _P, i32]
+    lib.srp_mlp_train_epoch.argtypes = [_P, _P, _P, _P, i64, _P, i64, i64, _P]
     lib.srp_mlp_save.argtypes = [_P, _P, C.c_char_p]
     lib.srp_mlp_load.argtypes = [_P, _P, C.c_char_p]
     lib.srp_mlp_save_state.argtypes = [_P, _P, C.c_char_p]
@@ -768,6 +769,23 @@ class MLP:
         _check(load().srp_mlp_train_step(self.ctx.handle, self.handle, _ptr(x), _ptr(t), x.shape[0], float(lr),
                                          _ptr(loss), _ptr(grad), SRP_MEM_HOST if host else SRP_MEM_DEVICE))
         return (float(loss[0]) if want_loss else None), grad
+
+    def train_epoch(self, x, t, idx, batch: int, lr):
+        """len(lr) Adam steps on batches gathered on the device: step s
+        trains on rows idx[s*batch:(s+1)*batch] of x [n,19] and t [n,6]
+        (CUDA float32 tensors) with learning rate lr[s]; idx is a CUDA int32
+        tensor of len(lr)*batch row numbers.  Asynchronous (queued on the
+        context's stream)."""
+        lr = _np(lr, np.float32).reshape(-1)
+        n_steps = lr.size
+        n = x.shape[0]
+        _need("x", x, n * 19, np.float32, True, self.ctx.device)
+        _need("t", t, n * 6, np.float32, True, self.ctx.device)
+        _need("idx", idx, n_steps * batch, np.int32, True, self.ctx.device)
+        if t.shape[0] != n:
+            raise ValueError("t must have the rows of x")
+        _check(load().srp_mlp_train_epoch(self.ctx.handle, self.handle, _ptr(x), _ptr(t), n, _ptr(idx), int(batch),
+                                          n_steps, lr.ctypes.data_as(_P)))
 
     def grad_input(self, x, wy, gx=None):
         """gx [B,19] = (dy/dx)^T wy for wy [B,6]; numpy -> host mode."""

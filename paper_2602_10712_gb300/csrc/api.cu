@@ -174,6 +174,7 @@ int srp_sync(srp_ctx* c) {
         if (flag & kErrVisitCap) what += " node-visit cap reached (corrupt BVH?);";
         if (flag & kErrAreaCount) what += " area-estimator sample count above its planned bound;";
         if (flag & kErrTriIndex) what += " triangle index outside the mesh (corrupt triangle table?);";
+        if (flag & kErrRowIndex) what += " training batch index outside the data set (its rows read as zero);";
         if (flag & kErrWaitTimeout) what += " a bounded wait of a tensor-core kernel gave up;";
         // a wait that gave up alone is a timeout; any traversal or table limit takes precedence
         const int code = flag == kErrWaitTimeout ? SRP_ETIMEOUT : SRP_EDEVICE_LIMIT;

@@ -374,8 +374,9 @@ cudaError_t mlp_forward(const float* x, int64_t B, const void* packed, const flo
 // Training and the input gradient run on the fused kernels of train.cu.
 size_t train_bytes(int64_t B);
 float* train_loss_ptr(void* work, int64_t B);
-cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params, float* grad, float* adam_m,
-                      float* adam_v, int64_t step, float lr, void* work, void* packed, int* err, cudaStream_t st);
+cudaError_t mlp_train(const float* x, const float* tgt, const int32_t* idx, int64_t n_src, int64_t B, float* params,
+                      float* grad, float* adam_m, float* adam_v, int64_t step, float lr, void* work, void* packed,
+                      int* err, cudaStream_t st);
 cudaError_t mlp_input_grad(const float* x, const float* wy, int64_t B, const float* params, const void* packed,
                            float* gx, void* work, int* err, cudaStream_t st);
 
@@ -576,11 +577,42 @@ extern "C" int srp_mlp_train_step(srp_ctx* c, srp_mlp* m, const float* x, const 
         return mfail(SRP_EINVAL, "srp_mlp_train_step: bad mem");
     }
     if (lr > 0.0f) m->step += 1;
-    MCU(mlp_train(dx, dt, B, m->params, m->grad, m->adam_m, m->adam_v, m->step, lr, m->work, m->packed, ctx_err(c), st),
+    MCU(mlp_train(dx, dt, nullptr, B, B, m->params, m->grad, m->adam_m, m->adam_v, m->step, lr, m->work, m->packed,
+                  ctx_err(c), st),
         "training launch");
     if (grad_out) MCU(cudaMemcpyAsync(grad_out, m->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, st), "D2H grad");
     if (loss_out) MCU(cudaMemcpyAsync(loss_out, train_loss_ptr(m->work, B), sizeof(float), cudaMemcpyDeviceToHost, st), "D2H loss");
     if (grad_out || loss_out || mem == SRP_MEM_HOST) return srp_sync(c);
+    return SRP_OK;
+}
+
+extern "C" int srp_mlp_train_epoch(srp_ctx* c, srp_mlp* m, const float* x, const float* t, int64_t n,
+                                   const int32_t* idx, int64_t batch, int64_t n_steps, const float* lr) {
+    if (!c || !m) return mfail(SRP_EINVAL, "srp_mlp_train_epoch: NULL ctx/mlp");
+    if (n < 1) return mfail(SRP_EINVAL, "srp_mlp_train_epoch: the data set needs at least one row");
+    if (batch < 1 || batch > (1 << 24)) return mfail(SRP_EINVAL, "srp_mlp_train_epoch: batch must be in 1..2^24");
+    if (n_steps < 0) return mfail(SRP_EINVAL, "srp_mlp_train_epoch: negative step count");
+    if (n_steps == 0) return SRP_OK;
+    if (!x || !t || !idx || !lr) return mfail(SRP_EINVAL, "srp_mlp_train_epoch: NULL x/t/idx/lr");
+    if (n > ((int64_t)1 << 31)) return mfail(SRP_EINVAL, "srp_mlp_train_epoch: more rows than int32 indices address");
+    for (int64_t s = 0; s < n_steps; ++s)
+        if (!(lr[s] > 0.0f) || !std::isfinite(lr[s]))
+            return mfail(SRP_EINVAL, "srp_mlp_train_epoch: every learning rate must be finite and > 0");
+    MCU(cudaSetDevice(m->device), "cudaSetDevice");
+    cudaStream_t st = ctx_stream(c);
+    const size_t need = train_bytes(batch);
+    if (m->work_bytes < need) {
+        if (m->work) cudaFree(m->work);
+        m->work = nullptr; m->work_bytes = 0;
+        if (cudaMalloc(&m->work, need) != cudaSuccess) return mfail(SRP_ENOMEM, "srp_mlp_train_epoch: workspace");
+        m->work_bytes = need;
+    }
+    for (int64_t s = 0; s < n_steps; ++s) {
+        m->step += 1;
+        MCU(mlp_train(x, t, idx + s * batch, n, batch, m->params, m->grad, m->adam_m, m->adam_v, m->step, lr[s],
+                      m->work, m->packed, ctx_err(c), st),
+            "training launch");
+    }
     return SRP_OK;
 }
 

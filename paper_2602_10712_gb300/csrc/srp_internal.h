@@ -35,6 +35,7 @@ constexpr int kErrVisitCap = 2;
 constexpr int kErrWaitTimeout = 4;      // a bounded mbarrier wait of a tensor-core kernel gave up
 constexpr int kErrAreaCount = 8;        // area estimator: sample counts above the planned bound
 constexpr int kErrTriIndex = 16;        // triangle table holds an index outside 0..T-1
+constexpr int kErrRowIndex = 32;        // training batch index outside the data set's rows
 
 struct BuiltBVH {                  // host result of the builder
     int width = 4;

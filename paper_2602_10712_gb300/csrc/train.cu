@@ -393,12 +393,15 @@ __device__ __forceinline__ void put_act(unsigned char* dst, const uint32_t (&pk)
 // Forward.  mode 0: training (targets t: loss, dL/dy, output bias gradient,
 // tile images of the inputs and activations for the weight gradients);
 // mode 1: the input gradient's forward (silu'(z) of the hidden layers only).
+// idx (may be NULL): batch row r reads row idx[r] of x and tgt, which hold
+// n_src rows (the batch gather of a training epoch, fused into the loads);
+// an index outside 0..n_src-1 sets kErrRowIndex and reads zeros.
 // ---------------------------------------------------------------------------
 template <int PAIR>
 __global__ void __launch_bounds__(kTrThreads, 1)
-    train_fwd_kernel(const float* __restrict__ x, const float* __restrict__ tgt, int64_t B, int64_t Bp,
-                     const __nv_bfloat16* __restrict__ packed, const float* __restrict__ params, TrainWS ws,
-                     float* __restrict__ grad, int mode, int* err) {
+    train_fwd_kernel(const float* __restrict__ x, const float* __restrict__ tgt, const int32_t* __restrict__ idx,
+                     int64_t n_src, int64_t B, int64_t Bp, const __nv_bfloat16* __restrict__ packed,
+                     const float* __restrict__ params, TrainWS ws, float* __restrict__ grad, int mode, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     using Smem = TrainSmem<PAIR>;
     constexpr int NH = Smem::NH;
@@ -411,6 +414,16 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     const uint32_t tbase = sm.tmem_base;
     grid_dep_launch();
     const int64_t tile = blockIdx.x / PAIR, row = tile * 128 + r;
+    // the data-set row of this batch row (warps 0-3 read x and tgt)
+    bool in_rows = row < B;
+    int64_t src = row;
+    if (idx != nullptr && part == 0 && in_rows) {
+        src = (int64_t)__ldg(idx + row);
+        if (src < 0 || src >= n_src) {
+            if (rank == 0) atomicOr(err, kErrRowIndex);
+            in_rows = false;
+        }
+    }
     if (tid == 0) load_w_rows(sm, pb + 2 * c_off.p[0], mlp_N(0), mlp_K(0), mlp_KC(0), NH * (int)rank, NH);
     // training: the gradient starts from zero (the backward and weight-
     // gradient kernels accumulate into it once this grid has completed)
@@ -422,7 +435,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
     if (part == 0) {
         float v[19];
 #pragma unroll
-        for (int j = 0; j < 19; ++j) v[j] = row < B ? __ldg(x + row * 19 + j) : 0.0f;
+        for (int j = 0; j < 19; ++j) v[j] = in_rows ? __ldg(x + src * 19 + j) : 0.0f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t u[4];
@@ -515,7 +528,7 @@ __global__ void __launch_bounds__(kTrThreads, 1)
             for (int j = 0; j < 8; ++j) {
                 dy[j] = 0.0f;
                 if (j < 6 && row < B) {
-                    const float d = v[j] + __ldg(params + c_off.b[l] + j) - __ldg(tgt + row * 6 + j);
+                    const float d = v[j] + __ldg(params + c_off.b[l] + j) - (in_rows ? __ldg(tgt + src * 6 + j) : 0.0f);
                     dy[j] = d > 0.0f ? invB : (d < 0.0f ? -invB : 0.0f);
                     lsum += fabsf(d);
                 }
@@ -977,14 +990,14 @@ static cudaError_t launch_ex(void (*kern)(Args...), unsigned grid, unsigned bloc
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-static cudaError_t launch_fwd(int pair, unsigned tiles, cudaStream_t st, const float* x, const float* tgt, int64_t B,
-                              int64_t Bp, const __nv_bfloat16* pk, const float* params, const TrainWS& ws, float* grad,
-                              int mode, int* err) {
+static cudaError_t launch_fwd(int pair, unsigned tiles, cudaStream_t st, const float* x, const float* tgt,
+                              const int32_t* idx, int64_t n_src, int64_t B, int64_t Bp, const __nv_bfloat16* pk,
+                              const float* params, const TrainWS& ws, float* grad, int mode, int* err) {
     if (pair == 2)
-        return launch_ex(train_fwd_kernel<2>, 2 * tiles, kTrThreads, sizeof(TrainSmem<2>), 2, false, st, x, tgt, B, Bp,
-                         pk, params, ws, grad, mode, err);
-    return launch_ex(train_fwd_kernel<1>, tiles, kTrThreads, sizeof(TrainSmem<1>), 1, false, st, x, tgt, B, Bp, pk,
-                     params, ws, grad, mode, err);
+        return launch_ex(train_fwd_kernel<2>, 2 * tiles, kTrThreads, sizeof(TrainSmem<2>), 2, false, st, x, tgt, idx,
+                         n_src, B, Bp, pk, params, ws, grad, mode, err);
+    return launch_ex(train_fwd_kernel<1>, tiles, kTrThreads, sizeof(TrainSmem<1>), 1, false, st, x, tgt, idx, n_src, B,
+                     Bp, pk, params, ws, grad, mode, err);
 }
 
 static cudaError_t launch_bwd(int pair, unsigned tiles, cudaStream_t st, const float* dy, int ld, int64_t B, int64_t Bp,
@@ -997,8 +1010,10 @@ static cudaError_t launch_bwd(int pair, unsigned tiles, cudaStream_t st, const f
 }
 
 // One optimisation step; grad receives dL/dparams; Adam applied when lr > 0.
-cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params, float* grad, float* adam_m,
-                      float* adam_v, int64_t step, float lr, void* work, void* packed, int* err, cudaStream_t st) {
+// idx (may be NULL): the batch's rows of x and tgt (n_src rows each).
+cudaError_t mlp_train(const float* x, const float* tgt, const int32_t* idx, int64_t n_src, int64_t B, float* params,
+                      float* grad, float* adam_m, float* adam_v, int64_t step, float lr, void* work, void* packed,
+                      int* err, cudaStream_t st) {
     cudaError_t e = train_attrs();
     if (e != cudaSuccess) return e;
     const int64_t Bp = train_bp(B);
@@ -1006,7 +1021,8 @@ cudaError_t mlp_train(const float* x, const float* tgt, int64_t B, float* params
     const unsigned tiles = (unsigned)(Bp / 128);
     const int pair = train_pair(Bp);
     const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
-    if ((e = launch_fwd(pair, tiles, st, x, tgt, B, Bp, pk, params, ws, grad, 0, err)) != cudaSuccess) return e;
+    if ((e = launch_fwd(pair, tiles, st, x, tgt, idx, n_src, B, Bp, pk, params, ws, grad, 0, err)) != cudaSuccess)
+        return e;
     if ((e = launch_bwd(pair, tiles, st, ws.dY, 8, B, Bp, pk, ws, grad, nullptr, 0, err)) != cudaSuccess) return e;
     // K slices: 8 work items per slice (6 heavy, 2 light), about one per SM
     int n_sm = 0, dev = 0;
@@ -1040,7 +1056,8 @@ cudaError_t mlp_input_grad(const float* x, const float* wy, int64_t B, const flo
     const unsigned tiles = (unsigned)(Bp / 128);
     const int pair = train_pair(Bp);
     const __nv_bfloat16* pk = (const __nv_bfloat16*)packed;
-    if ((e = launch_fwd(pair, tiles, st, x, nullptr, B, Bp, pk, params, ws, nullptr, 1, err)) != cudaSuccess) return e;
+    if ((e = launch_fwd(pair, tiles, st, x, nullptr, nullptr, B, B, Bp, pk, params, ws, nullptr, 1, err)) != cudaSuccess)
+        return e;
     if ((e = launch_bwd(pair, tiles, st, wy, 6, B, Bp, pk, ws, nullptr, gx, 1, err)) != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -127,7 +127,10 @@ def fit(ctx: Context, mesh, n_designs=4096, suns_per_design=256, rays=256, bounc
     exist: the data set is traced again from the same seeds (the tracer is
     deterministic), the finished epochs are skipped and the learning-rate
     schedule and batch order continue where they stopped.  device: where
-    the training batches live (default: the context's GPU)."""
+    the training batches live (default: the context's GPU).  On a GPU each
+    epoch is one srp_mlp_train_epoch call over a batch order drawn on the
+    device from (seed, epoch); elsewhere (a stand-in network) one
+    train_step per batch over a host permutation."""
     import json
     import os
 
@@ -157,15 +160,25 @@ def fit(ctx: Context, mesh, n_designs=4096, suns_per_design=256, rays=256, bounc
     dev = torch.device(device) if device is not None else torch.device("cuda", ctx.device)
     xt = torch.from_numpy(x).to(dev)
     yt = torch.from_numpy(yn).to(dev)
+    nb = n // batch
     for ep in range(ep0, epochs):
-        perm = torch.from_numpy(rng.permutation(n)).to(dev)
-        for b0 in range(0, n - batch + 1, batch):
-            idx = perm[b0:b0 + batch]
-            xb = xt.index_select(0, idx).contiguous()
-            yb = yt.index_select(0, idx).contiguous()
-            lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * step / steps)) + 1e-5
-            net.train_step(xb, yb, lr_t, want_loss=False)
-            step += 1
+        lrs = [lr * 0.5 * (1.0 + math.cos(math.pi * (step + k) / steps)) + 1e-5 for k in range(nb)]
+        if dev.type == "cuda":
+            # the epoch's batch order is drawn on the device from (seed,
+            # epoch) alone, so a resumed run repeats it; the batches are
+            # gathered inside the training kernels and the steps queued by
+            # one library call (no host round trip per step)
+            g = torch.Generator(device=dev)
+            g.manual_seed((seed + 7) * 1000003 + ep)
+            perm = torch.randperm(n, generator=g, device=dev)[:nb * batch].to(torch.int32)
+            net.train_epoch(xt, yt, perm, batch, np.array(lrs, np.float32))
+        else:
+            pt = torch.from_numpy(rng.permutation(n)).to(dev)
+            for k in range(nb):
+                idx = pt[k * batch:(k + 1) * batch]
+                net.train_step(xt.index_select(0, idx).contiguous(), yt.index_select(0, idx).contiguous(), lrs[k],
+                               want_loss=False)
+        step += nb
         if log is not None:
             l, _ = net.train_step(xt[:batch].contiguous(), yt[:batch].contiguous(), 0.0)
             log(f"epoch {ep} loss {l:.4f}")

@@ -174,6 +174,65 @@ def test_adam_repacks_both_layouts(srp):
     assert np.array_equal(net.grad_input(x, wy), fresh.grad_input(x, wy))
 
 
+def test_train_epoch_matches_gathered_steps(srp):
+    """srp_mlp_train_epoch (each batch gathered by row number inside the
+    training forward, the steps queued by one call) against
+    srp_mlp_train_step on the same batches gathered on the host, from the
+    same parameters, with the same learning rates: batches of 1,000 rows
+    (eight tiles, the last ragged) drawn with repeats from 5,000.  The two
+    differ only in the order of the weight gradient's FP32 atomic sums, so
+    after three Adam steps (each moving a weight by about lr) almost every
+    parameter agrees to 1e-2 lr and the losses to 1e-5; a batch gathered
+    from the wrong rows moves most parameters by O(lr)."""
+    ctx = srp.Context(0)
+    n, batch, steps = 5000, 1000, 3
+    rng = np.random.default_rng(31)
+    x = inputs(n, seed=21)
+    t = rng.normal(size=(n, 6)).astype(np.float32)
+    idx = rng.integers(0, n, size=steps * batch).astype(np.int32)
+    lrs = np.array([1e-3, 7e-4, 4e-4], np.float32)
+    p0 = flat(omlp.init_params(seed=14))
+    a, b = srp.MLP(ctx, p0), srp.MLP(ctx, p0)
+    dev = torch.device("cuda", 0)
+    a.train_epoch(torch.from_numpy(x).to(dev), torch.from_numpy(t).to(dev), torch.from_numpy(idx).to(dev), batch, lrs)
+    for s in range(steps):
+        rows = idx[s * batch:(s + 1) * batch]
+        b.train_step(x[rows], t[rows], float(lrs[s]), want_loss=False)
+    pa, pb = a.params(), b.params()
+    d = np.abs(pa - pb)
+    assert np.mean(d > 1e-2 * lrs[0]) < 1e-3, np.mean(d > 1e-2 * lrs[0])
+    assert d.max() <= 2.0 * lrs.sum(), d.max()
+    assert np.mean(np.abs(pa - p0) > 0.1 * lrs[0]) > 0.5   # the steps did move the weights
+    la, _ = a.train_step(x[:2000], t[:2000], 0.0)
+    lb, _ = b.train_step(x[:2000], t[:2000], 0.0)
+    assert abs(la - lb) <= 1e-5 * lb, (la, lb)
+
+
+def test_train_epoch_rejects_rows_outside_the_data_set(srp):
+    """A row number outside 0..n-1 is not read: the forward reads a zero row
+    in its place and flags it, the next synchronisation reports
+    SRP_EDEVICE_LIMIT, and the context trains normally afterwards."""
+    ctx = srp.Context(0)
+    n, batch = 600, 256
+    x = inputs(n, seed=22)
+    t = np.random.default_rng(3).normal(size=(n, 6)).astype(np.float32)
+    dev = torch.device("cuda", 0)
+    xd, td = torch.from_numpy(x).to(dev), torch.from_numpy(t).to(dev)
+    net = srp.MLP(ctx, seed=2)
+    for bad in (n, -1):
+        idx = np.arange(batch, dtype=np.int32)
+        idx[77] = bad
+        net.train_epoch(xd, td, torch.from_numpy(idx).to(dev), batch, np.array([1e-3], np.float32))
+        with pytest.raises(srp.SRPError) as e:
+            srp.srp_sync(ctx)
+        assert e.value.code == srp.SRP_EDEVICE_LIMIT and "training batch index" in str(e.value)
+    net.train_epoch(xd, td, torch.arange(batch, dtype=torch.int32, device=dev), batch, np.array([1e-3], np.float32))
+    srp.srp_sync(ctx)
+    with pytest.raises(srp.SRPError, match="SRP_EINVAL"):
+        net.train_epoch(xd, td, torch.arange(batch, dtype=torch.int32, device=dev), batch,
+                        np.array([0.0], np.float32))
+
+
 def test_training_reduces_loss(srp):
     """Fit a smooth synthetic map (a fixed random 19->6 linear map + tanh):
     200 Adam steps reduce the L1 loss at least 5x."""

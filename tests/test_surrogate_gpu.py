@@ -47,3 +47,47 @@ def test_surrogate_fits_and_beats_tracer():
     torch.cuda.synchronize()
     mc_rate = 4096 / (time.perf_counter() - t0)
     assert nn_rate >= 100 * mc_rate, (nn_rate, mc_rate)
+
+
+def test_fit_resumes_on_the_gpu(tmp_path, monkeypatch):
+    """fit's GPU path (one srp_mlp_train_epoch call per epoch over a batch
+    order drawn on the device from (seed, epoch)) interrupted in its third
+    epoch and resumed from its checkpoint ends where an uninterrupted run
+    ends: same step count, parameters equal up to the FP32 order of the
+    weight gradient's atomic sums.  Under the L1 loss that order can flip
+    the sign of a near-zero residual, so the two runs drift apart a little
+    over the last steps: the median parameter difference must stay below a
+    tenth of the median distance the training moved them (a resumed run
+    that replayed another batch order or restarted the learning-rate
+    schedule differs by a sizeable fraction of that distance)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_10712_gb300 as srp
+    from paper_2602_10712_gb300 import surrogate as S
+    ctx = srp.Context(0)
+    mesh = W.box_wing_7group()
+    kw = dict(n_designs=32, suns_per_design=16, rays=64, bounces=1, epochs=4, batch=128, lr=1e-2, seed=3)
+    ref, info = S.fit(ctx, mesh, **kw)
+    assert info["steps"] == 16
+    calls = {"n": 0}
+
+    class Crashing(srp.MLP):
+        def train_epoch(self, *a, **k):
+            calls["n"] += 1
+            if calls["n"] == 3:
+                raise RuntimeError("simulated crash")
+            return super().train_epoch(*a, **k)
+
+    prefix = str(tmp_path / "ckpt")
+    monkeypatch.setattr(S, "MLP", Crashing)
+    with pytest.raises(RuntimeError, match="simulated crash"):
+        S.fit(ctx, mesh, checkpoint=prefix, **kw)
+    monkeypatch.setattr(S, "MLP", srp.MLP)
+    meta = np.load(prefix + ".npz")
+    assert int(meta["epoch"]) == 2 and int(meta["step"]) == 8
+    res, info2 = S.fit(ctx, mesh, checkpoint=prefix, resume=True, **kw)
+    assert info2["steps"] == 16
+    d = np.abs(res.net.params() - ref.net.params())
+    moved = np.abs(ref.net.params() - S.MLP(ctx, seed=3).params())
+    assert np.median(moved) > 0.3 * kw["lr"], np.median(moved)
+    assert np.median(d) <= 0.1 * np.median(moved), (np.median(d), np.median(moved))
