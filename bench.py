@@ -498,7 +498,8 @@ def extra_legs(srp, ctx, dev, peaks, l2_gbs, sm_mhz, n_sm):
                  "mlp_tflops": flops / t_nn / 1e12, "mlp_frac_of_bf16_peak": flops / t_nn / 1e12 / peak,
                  "batch": nq, "note": "19-256x4-6 SiLU, BF16 tcgen05, FP32 accumulation; error vs 1024^2-ray MC; "
                                       "training: batches of 8192 (fwd + bwd = 3 x 406 kFLOP per sample); train_tflops "
-                                      "is the wall clock of the Python step loop (batch gathers included), "
+                                      "is the wall clock of fit's training loop (one srp_mlp_train_epoch call "
+                                      "per epoch, batches gathered inside the training forward), "
                                       "train_step_device the step's kernels alone (CUDA events)"}
     # gradients: box-wing (64 groups, 2 hinges), K = 1, 1024^2 rays, 64 suns per call
     m1 = W.box_wing()
