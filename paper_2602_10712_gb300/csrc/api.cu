@@ -764,6 +764,11 @@ extern "C" int srp_force_grad(srp_ctx* c, const srp_bvh* bvh, const float* rho, 
     if (S > 0 && (!rho || !sun_dir || !com || !upstream || !d_rho))
         return fail(SRP_EINVAL, "srp_force_grad: NULL array argument");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
+    if (p.rowoff) {   // the span pre-pass reads the design from the device table
+        rc = upload_designs(c, designs);
+        if (rc != SRP_OK) return rc;
+        p.designs = (const DesignDev*)c->dtab.p;
+    }
     const int ng = 2 * G + H;
     const int64_t units = (int64_t)S * p.cpb;
     if (c->gpart.ensure(sizeof(double) * ng * (size_t)std::max<int64_t>(units, 1)) != cudaSuccess)

@@ -15,6 +15,8 @@
 //    (hinge_path_tangent).  The visibility of each ray is held fixed (the
 //    estimate's boundary terms, where a shadow edge or silhouette moves,
 //    are not included).
+// Full grids of whole 32-pixel batches trace only the batches that can meet
+// the scene (the forward's span pre-pass; the rest contribute nothing).
 // Accumulation: per-warp FP32 shared-memory sums over <= 512 rays, flushed
 // into per-warp FP64 (an FP64 warp instruction is expensive on this GPU,
 // so the flushes are kept rare), written as per-unit FP64 partials, summed
@@ -127,13 +129,46 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
         const double* up = g.up + 6 * (size_t)s;
         const float3 gF = f3((float)up[0], (float)up[1], (float)up[2]);
         const float3 gT = f3((float)up[3], (float)up[4], (float)up[5]);
-        const int64_t k0 = cidx * p.chunk;
-        const int64_t k1 = min(k0 + p.chunk, p.n);
+        // span mode (full grids of whole 32-pixel batches, as in the
+        // forward): the unit's share of the item's batches that can meet
+        // the scene -- a ray of any other batch misses every box, so its
+        // path and its gradient contribution are empty; otherwise the
+        // contiguous slots [k0, k1) of the ray subset
+        const bool span = p.rowoff != nullptr;
+        const int32_t* rowoff = nullptr;
+        const int32_t* rowfirst = nullptr;
+        int64_t k0, k1;
+        int row = 0;
+        if (span) {
+            rowoff = p.rowoff + (size_t)s * (p.ny + 1);
+            rowfirst = p.rowfirst + (size_t)s * p.ny;
+            const int64_t L = __ldg(rowoff + p.ny);
+            k0 = cidx * L / p.cpb;
+            k1 = (cidx + 1) * L / p.cpb;
+            int lo = 0, hi = p.ny;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if ((int64_t)__ldg(rowoff + mid) <= k0) lo = mid; else hi = mid;
+            }
+            row = lo;
+        } else {
+            k0 = cidx * p.chunk;
+            k1 = min(k0 + p.chunk, p.n);
+        }
         int batch = 0;
-        for (int64_t kb = k0; kb < k1; kb += 32, ++batch) {
-            const int64_t k = kb + lane;
+        for (int64_t kb = k0; kb < k1; kb += span ? 1 : 32, ++batch) {
+            int64_t k;
+            uint64_t i;
+            if (span) {
+                while ((int64_t)__ldg(rowoff + row + 1) <= kb) ++row;
+                i = (uint64_t)((int64_t)row * p.nx + 32 * ((int64_t)__ldg(rowfirst + row) + (kb - __ldg(rowoff + row))) +
+                               lane);
+                k = kb;
+            } else {
+                k = kb + lane;
+                i = (uint64_t)(p.off + k * p.stride);
+            }
             if (k < k1) {
-                const uint64_t i = (uint64_t)(p.off + k * p.stride);
                 Seg s0 = primary_seg(ic, p, i);
                 // ---- forward replay with the path recorded
                 int m = 0;
@@ -224,7 +259,7 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
                 }
             }
             __syncwarp();
-            if ((batch & 15) == 15 || kb + 32 >= k1) {   // flush FP32 sums (<= 512 rays) to FP64
+            if ((batch & 15) == 15 || kb + (span ? 1 : 32) >= k1) {   // flush FP32 sums (<= 512 rays) to FP64
                 for (int e = lane; e < g.ng; e += 32) { ws.d[e] += (double)ws.f[e]; ws.f[e] = 0.0f; }
                 __syncwarp();
             }
@@ -267,9 +302,15 @@ __global__ void __launch_bounds__(kGradReduceThreads) grad_reduce_kernel(const d
     }
 }
 
+cudaError_t launch_span(const TraceParams& p, int width, cudaStream_t st);
+
 cudaError_t launch_grad(const DesignDev& dz, const TraceParams& p, const double* up, const int32_t* thinge,
                         const double* hax, int H, double* gpart, double* d_rho, double* d_hinge, int n_sm,
                         cudaStream_t st) {
+    if (p.rowoff && (int64_t)p.S * p.cpb > 0 && p.n > 0) {
+        const cudaError_t e = launch_span(p, dz.width, st);
+        if (e != cudaSuccess) return e;
+    }
     GradParams g;
     g.up = up; g.thinge = thinge; g.hax = hax; g.H = H; g.ng = 2 * p.G + H; g.gpart = gpart;
     const int64_t units = (int64_t)p.S * p.cpb;
