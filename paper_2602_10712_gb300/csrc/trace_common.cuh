@@ -122,6 +122,16 @@ __device__ __forceinline__ void slab4(const float4 x, unsigned long long s2, uns
         : "f"(x.x), "f"(x.y), "f"(x.z), "f"(x.w), "l"(s2), "l"(c2));
 }
 
+// Compare-exchange of entries a < b of a sorting network on (key, child):
+// the smaller key first; a child of -1 (key +inf) sorts last.
+__device__ __forceinline__ void sort_cx(float (&k)[4], int (&c)[4], int a, int b) {
+    const bool sw = k[b] < k[a];
+    const float ka = k[a], kb = k[b];
+    const int ca = c[a], cb = c[b];
+    k[a] = sw ? kb : ka; k[b] = sw ? ka : kb;
+    c[a] = sw ? cb : ca; c[b] = sw ? ca : cb;
+}
+
 // ---------------------------------------------------------------------------
 // Closest hit through a W-wide BVH.  Returns the leaf-order triangle index
 // (or -1) and sets tb.  Ties on t go to the smaller original index.
@@ -195,19 +205,42 @@ __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& 
             }
         }
         int next = -1;
-        float tnext = INFINITY;
+        if (W == 4) {
+            // the inner children still in reach sorted by entry distance
+            // (five compare-exchanges), pushed farthest first so that the
+            // nearest remaining one is popped first; the nearest is next
+            float k[4];
+            int cc[4];
 #pragma unroll
-        for (int c = 0; c < W; ++c) {
-            if (hit[c] && child[c] >= 0 && tn[c] <= tb) {
-                if (tn[c] < tnext) {
-                    if (next >= 0) {
-                        if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
-                        stack[sp++] = make_int2(next, __float_as_int(tnext));
-                    }
-                    next = child[c]; tnext = tn[c];
-                } else {
+            for (int c = 0; c < 4; ++c) {
+                const bool in = hit[c] && child[c] >= 0 && tn[c] <= tb;
+                k[c] = in ? tn[c] : INFINITY;
+                cc[c] = in ? child[c] : -1;
+            }
+            sort_cx(k, cc, 0, 1); sort_cx(k, cc, 2, 3); sort_cx(k, cc, 0, 2); sort_cx(k, cc, 1, 3); sort_cx(k, cc, 1, 2);
+#pragma unroll
+            for (int c = 3; c >= 1; --c) {
+                if (cc[c] >= 0) {
                     if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
-                    stack[sp++] = make_int2(child[c], __float_as_int(tn[c]));
+                    stack[sp++] = make_int2(cc[c], __float_as_int(k[c]));
+                }
+            }
+            next = cc[0];
+        } else {
+            float tnext = INFINITY;
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                if (hit[c] && child[c] >= 0 && tn[c] <= tb) {
+                    if (tn[c] < tnext) {
+                        if (next >= 0) {
+                            if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
+                            stack[sp++] = make_int2(next, __float_as_int(tnext));
+                        }
+                        next = child[c]; tnext = tn[c];
+                    } else {
+                        if (sp >= kStackSize) { atomicOr(err, kErrStackOverflow); return -1; }
+                        stack[sp++] = make_int2(child[c], __float_as_int(tn[c]));
+                    }
                 }
             }
         }
