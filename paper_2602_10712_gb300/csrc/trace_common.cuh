@@ -183,24 +183,33 @@ __device__ __forceinline__ int closest_hit(const DesignDev& dz, const RaySetup& 
                 child[4 * h + q] = ch_[q];
             }
         }
-        // leaves first: they may shrink tb before inner children are queued
+        // leaves first: they may shrink tb before inner children are queued.
+        // The hit leaves of the node are taken one after another from a
+        // slot mask (ascending slots), so lanes whose leaves sit in
+        // different slots run their triangle tests in the same iterations
+        // instead of one masked pass per slot.
+        unsigned lm = 0u;
 #pragma unroll
-        for (int c = 0; c < W; ++c) {
-            if (hit[c] && child[c] < 0) {
-                const int code = ~child[c];
-                const int first = code >> 3, cnt = (code & 7) + 1;
-                ntest += cnt;
-                for (int q = 0; q < cnt; ++q) {
-                    const int f = first + q;
-                    if (f == skip) continue;
-                    const float4 a = __ldg(tri + 3 * (size_t)f);
-                    const float4 b = __ldg(tri + 3 * (size_t)f + 1);
-                    const float4 cc = __ldg(tri + 3 * (size_t)f + 2);
-                    const float t = hit_triangle(r, xyz(a), xyz(b), xyz(cc));
-                    if (t > tmin && t <= tb) {
-                        const uint32_t id = __float_as_uint(a.w);
-                        if (t < tb || id < best_id) { tb = t; best = f; best_id = id; }
-                    }
+        for (int c = 0; c < W; ++c) lm |= (hit[c] && child[c] < 0) ? (1u << c) : 0u;
+        while (lm != 0u) {
+            const int c = __ffs(lm) - 1;
+            lm &= lm - 1u;
+            int ch = child[0];
+#pragma unroll
+            for (int j = 1; j < W; ++j) ch = c == j ? child[j] : ch;
+            const int code = ~ch;
+            const int first = code >> 3, cnt = (code & 7) + 1;
+            ntest += cnt;
+            for (int q = 0; q < cnt; ++q) {
+                const int f = first + q;
+                if (f == skip) continue;
+                const float4 a = __ldg(tri + 3 * (size_t)f);
+                const float4 b = __ldg(tri + 3 * (size_t)f + 1);
+                const float4 cc = __ldg(tri + 3 * (size_t)f + 2);
+                const float t = hit_triangle(r, xyz(a), xyz(b), xyz(cc));
+                if (t > tmin && t <= tb) {
+                    const uint32_t id = __float_as_uint(a.w);
+                    if (t < tb || id < best_id) { tb = t; best = f; best_id = id; }
                 }
             }
         }
