@@ -312,20 +312,26 @@ __device__ __forceinline__ bool any_hit(const DesignDev& dz, const RaySetup& r, 
                 child[4 * h + q] = ch_[q];
             }
         }
+        // hit leaves from a slot mask, one loop (as in closest_hit)
+        unsigned lm = 0u;
 #pragma unroll
-        for (int c = 0; c < W; ++c) {
-            if (hit[c] && child[c] < 0) {
-                const int code = ~child[c];
-                const int first = code >> 3, cnt = (code & 7) + 1;
-                ntest += cnt;
-                for (int q = 0; q < cnt; ++q) {
-                    const int f = first + q;
-                    if (f == skip) continue;
-                    const float4 a = __ldg(tri + 3 * (size_t)f);
-                    const float4 b = __ldg(tri + 3 * (size_t)f + 1);
-                    const float4 cc = __ldg(tri + 3 * (size_t)f + 2);
-                    if (hit_triangle(r, xyz(a), xyz(b), xyz(cc)) > tmin) return true;
-                }
+        for (int c = 0; c < W; ++c) lm |= (hit[c] && child[c] < 0) ? (1u << c) : 0u;
+        while (lm != 0u) {
+            const int c = __ffs(lm) - 1;
+            lm &= lm - 1u;
+            int ch = child[0];
+#pragma unroll
+            for (int j = 1; j < W; ++j) ch = c == j ? child[j] : ch;
+            const int code = ~ch;
+            const int first = code >> 3, cnt = (code & 7) + 1;
+            ntest += cnt;
+            for (int q = 0; q < cnt; ++q) {
+                const int f = first + q;
+                if (f == skip) continue;
+                const float4 a = __ldg(tri + 3 * (size_t)f);
+                const float4 b = __ldg(tri + 3 * (size_t)f + 1);
+                const float4 cc = __ldg(tri + 3 * (size_t)f + 2);
+                if (hit_triangle(r, xyz(a), xyz(b), xyz(cc)) > tmin) return true;
             }
         }
         int next = -1;
