@@ -113,8 +113,19 @@ template <int W>
 // (+10 % at K = 1, +7 % at K = 3 on the box-wing, bit-identical).
 __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const TraceParams p, const GradParams g) {
     __shared__ GradWarpSmem sm[4];
+    // hinge points and axes in FP32, converted once per block (a per-ray
+    // FP64 load and conversion runs on the FP64 pipe, slow on this GPU)
+    __shared__ float hxf[8][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     GradWarpSmem& ws = sm[warp];
+    if (threadIdx.x < 6 * g.H) hxf[threadIdx.x / 6][threadIdx.x % 6] = (float)g.hax[threadIdx.x];
+    __syncthreads();
+    // each lane keeps the running sums of the last hit's group (rho_s and
+    // rho_d entries) and of its hinge in registers while they repeat, and
+    // adds them to the warp's shared sums when they change and before each
+    // flush (neighbouring rays mostly end on the same facet)
+    int cg = -1, chh = -1;
+    float cs0 = 0.0f, cs1 = 0.0f, chs = 0.0f;
     const int64_t units = (int64_t)p.S * p.cpb;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -205,8 +216,12 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
                     float wbar;
                     if (q + 1 == p.K) {
                         const float qd = dot(qv, dr[q]), qn = dot(qv, nr[q]);
-                        atomicAdd(&ws.f[2 * gr[q]], w * (-qd - 2.0f * csr[q] * qn));
-                        atomicAdd(&ws.f[2 * gr[q] + 1], w * (-(2.0f / 3.0f) * qn));
+                        if (gr[q] != cg) {
+                            if (cg >= 0) { atomicAdd(&ws.f[2 * cg], cs0); atomicAdd(&ws.f[2 * cg + 1], cs1); }
+                            cg = gr[q]; cs0 = 0.0f; cs1 = 0.0f;
+                        }
+                        cs0 += w * (-qd - 2.0f * csr[q] * qn);
+                        cs1 += w * (-(2.0f / 3.0f) * qn);
                         wbar = (1.0f - rsr[q]) * qd - (2.0f * rsr[q] * csr[q] + (2.0f / 3.0f) * rdr[q]) * qn;
                     } else {
                         const float wbar_out = wbar_next - dot(qv, dout_r[q]);
@@ -227,9 +242,9 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
                         bool dup = hh < 0 || hh >= g.H;
                         for (int q2 = 0; q2 < q; ++q2) dup = dup || hid[q2] == hh;
                         if (dup) continue;
-                        const double* hp = g.hax + 6 * hh;
-                        const float3 ap = f3((float)hp[0], (float)hp[1], (float)hp[2]);
-                        const float3 aa = f3((float)hp[3], (float)hp[4], (float)hp[5]);
+                        const float* hp = hxf[hh];
+                        const float3 ap = f3(hp[0], hp[1], hp[2]);
+                        const float3 aa = f3(hp[3], hp[4], hp[5]);
                         const float dL = hinge_path_tangent(dz, hh, ap, aa, m, p.K, hid, fr, br, xr, nr, dr, dout_r, csr,
                                                             wr, rsr, rdr, ic.com, gF, gT);
                         atomicAdd(&ws.f[2 * p.G + hh], dL);
@@ -240,9 +255,9 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
                     const uint32_t orig = __float_as_uint(__ldg(dz.tri + 3 * (size_t)fr[0]).w);
                     const int hh = g.thinge ? __ldg(g.thinge + orig) : -1;
                     if (hh >= 0 && hh < g.H) {
-                        const double* hp = g.hax + 6 * hh;
-                        const float3 ap = f3((float)hp[0], (float)hp[1], (float)hp[2]);
-                        const float3 aa = f3((float)hp[3], (float)hp[4], (float)hp[5]);
+                        const float* hp = hxf[hh];
+                        const float3 ap = f3(hp[0], hp[1], hp[2]);
+                        const float3 aa = f3(hp[3], hp[4], hp[5]);
                         const float3 x = xr[0], n = nr[0], d = dr[0];
                         const float c = csr[0], rs = rsr[0], rd = rdr[0];
                         const float3 qv = gF + cross(gT, x - ic.com);
@@ -254,12 +269,20 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
                         const float3 dq = cross(gT, dx);
                         const float3 dG = (-2.0f * rs * dc) * n - cn * dn;
                         const float dphi = dc * dot(qv, Gv) + c * (dot(dq, Gv) + dot(qv, dG));
-                        atomicAdd(&ws.f[2 * p.G + hh], (wr[0] / c) * dphi);
+                        if (hh != chh) {
+                            if (chh >= 0) atomicAdd(&ws.f[2 * p.G + chh], chs);
+                            chh = hh; chs = 0.0f;
+                        }
+                        chs += (wr[0] / c) * dphi;
                     }
                 }
             }
-            __syncwarp();
             if ((batch & 15) == 15 || kb + (span ? 1 : 32) >= k1) {   // flush FP32 sums (<= 512 rays) to FP64
+                if (cg >= 0) { atomicAdd(&ws.f[2 * cg], cs0); atomicAdd(&ws.f[2 * cg + 1], cs1); cg = -1; }
+                if (chh >= 0) { atomicAdd(&ws.f[2 * p.G + chh], chs); chh = -1; }
+            }
+            __syncwarp();
+            if ((batch & 15) == 15 || kb + (span ? 1 : 32) >= k1) {
                 for (int e = lane; e < g.ng; e += 32) { ws.d[e] += (double)ws.f[e]; ws.f[e] = 0.0f; }
                 __syncwarp();
             }
