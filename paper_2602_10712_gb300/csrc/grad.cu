@@ -45,6 +45,7 @@ constexpr int kMaxGradEntries = 2 * kMaxGroups + 8;
 struct GradWarpSmem {
     float f[kMaxGradEntries];
     double d[kMaxGradEntries];
+    float dirc[12];   // the unit's primary direction: 1/d and the shear rows
 };
 
 // d/da of one recorded path's L = sum_k q_k . dp_k for hinge `hh` (point
@@ -140,6 +141,18 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
         const double* up = g.up + 6 * (size_t)s;
         const float3 gF = f3((float)up[0], (float)up[1], (float)up[2]);
         const float3 gT = f3((float)up[3], (float)up[4], (float)up[5]);
+        // the direction-only part of the primary rays' set-up (1/d and the
+        // shear rows), shared by the unit's rays: once per unit, as the
+        // forward does per item (the same values as a per-ray setup_ray)
+        if (lane == 0) {
+            RaySetup rd;
+            setup_ray(rd, f3(0.0f, 0.0f, 0.0f), ic.dd);
+            ws.dirc[0] = rd.inv.x; ws.dirc[1] = rd.inv.y; ws.dirc[2] = rd.inv.z;
+            ws.dirc[3] = rd.mx.x; ws.dirc[4] = rd.mx.y; ws.dirc[5] = rd.mx.z;
+            ws.dirc[6] = rd.my.x; ws.dirc[7] = rd.my.y; ws.dirc[8] = rd.my.z;
+            ws.dirc[9] = rd.mz.x; ws.dirc[10] = rd.mz.y; ws.dirc[11] = rd.mz.z;
+        }
+        __syncwarp();
         // span mode (full grids of whole 32-pixel batches, as in the
         // forward): the unit's share of the item's batches that can meet
         // the scene -- a ray of any other batch misses every box, so its
@@ -191,7 +204,16 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
 #pragma unroll 1
                 for (int kk = 1; kk <= p.K; ++kk) {
                     RaySetup rs;
-                    setup_ray(rs, sg.o, sg.d);
+                    if (kk == 1) {
+                        rs.o = sg.o; rs.d = sg.d;
+                        rs.inv = f3(ws.dirc[0], ws.dirc[1], ws.dirc[2]);
+                        rs.oinv = f3(sg.o.x * rs.inv.x, sg.o.y * rs.inv.y, sg.o.z * rs.inv.z);
+                        rs.mx = f3(ws.dirc[3], ws.dirc[4], ws.dirc[5]);
+                        rs.my = f3(ws.dirc[6], ws.dirc[7], ws.dirc[8]);
+                        rs.mz = f3(ws.dirc[9], ws.dirc[10], ws.dirc[11]);
+                    } else {
+                        setup_ray(rs, sg.o, sg.d);
+                    }
                     float t;
                     const int f = closest_hit<W>(dz, rs, kk == 1 ? 0.0f : ic.tmin_b, sg.src, t, p.err, nvis, ntest);
                     if (f < 0) break;
