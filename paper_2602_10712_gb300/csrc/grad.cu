@@ -192,7 +192,56 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
                 k = kb + lane;
                 i = (uint64_t)(p.off + k * p.stride);
             }
-            if (k < k1) {
+            if (k < k1 && p.K == 1) {
+                // ---- one hit per path: the same arithmetic as the general
+                // replay below at K = 1, with nothing recorded (registers
+                // only, no per-ray arrays)
+                const Seg s0 = primary_seg(ic, p, i);
+                RaySetup rs;
+                rs.o = s0.o; rs.d = s0.d;
+                rs.inv = f3(ws.dirc[0], ws.dirc[1], ws.dirc[2]);
+                rs.oinv = f3(s0.o.x * rs.inv.x, s0.o.y * rs.inv.y, s0.o.z * rs.inv.z);
+                rs.mx = f3(ws.dirc[3], ws.dirc[4], ws.dirc[5]);
+                rs.my = f3(ws.dirc[6], ws.dirc[7], ws.dirc[8]);
+                rs.mz = f3(ws.dirc[9], ws.dirc[10], ws.dirc[11]);
+                float t;
+                const int f = closest_hit<W>(dz, rs, 0.0f, s0.src, t, p.err, nvis, ntest);
+                if (f >= 0) {
+                    const HitGeom h = hit_geom(dz, ic, f, t, s0);
+                    const float3 qv = gF + cross(gT, h.x - ic.com);
+                    const float qd = dot(qv, s0.d), qn = dot(qv, h.n);
+                    if (h.g != cg) {
+                        if (cg >= 0) { atomicAdd(&ws.f[2 * cg], cs0); atomicAdd(&ws.f[2 * cg + 1], cs1); }
+                        cg = h.g; cs0 = 0.0f; cs1 = 0.0f;
+                    }
+                    cs0 += s0.w * (-qd - 2.0f * h.cs * qn);
+                    cs1 += s0.w * (-(2.0f / 3.0f) * qn);
+                    if (g.H > 0) {
+                        const uint32_t orig = __float_as_uint(__ldg(dz.tri + 3 * (size_t)f).w);
+                        const int hh = g.thinge ? __ldg(g.thinge + orig) : -1;
+                        if (hh >= 0 && hh < g.H) {
+                            const float* hp = hxf[hh];
+                            const float3 ap = f3(hp[0], hp[1], hp[2]);
+                            const float3 aa = f3(hp[3], hp[4], hp[5]);
+                            const float3 x = h.x, n = h.n, d = s0.d;
+                            const float c = h.cs, rs_ = h.rs, rd = h.rd;
+                            const float cn = 2.0f * rs_ * c + (2.0f / 3.0f) * rd;
+                            const float3 Gv = (1.0f - rs_) * d - cn * n;
+                            const float3 dn = cross(aa, n);
+                            const float3 dx = cross(aa, x - ap);
+                            const float dc = -dot(dn, d);
+                            const float3 dq = cross(gT, dx);
+                            const float3 dG = (-2.0f * rs_ * dc) * n - cn * dn;
+                            const float dphi = dc * dot(qv, Gv) + c * (dot(dq, Gv) + dot(qv, dG));
+                            if (hh != chh) {
+                                if (chh >= 0) atomicAdd(&ws.f[2 * p.G + chh], chs);
+                                chh = hh; chs = 0.0f;
+                            }
+                            chs += (s0.w / c) * dphi;
+                        }
+                    }
+                }
+            } else if (k < k1) {
                 Seg s0 = primary_seg(ic, p, i);
                 // ---- forward replay with the path recorded
                 int m = 0;
