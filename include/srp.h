@@ -333,7 +333,9 @@ int srp_trace_samples(srp_ctx* ctx, const float* verts, int V, const int32_t* vh
  * tri_hinge [T] int32 (by original triangle index; -1 = not on a hinge) and
  * hinge_axes [H][6] (point, unit axis; the axes the design was instantiated
  * with, srp_design_instantiate) describe the hinges; H <= 8.  The COM is
- * held fixed.  Memory per opts->mem.
+ * held fixed.  Memory per opts->mem.  Full grids whose rays_x is a
+ * multiple of 32 replay only the 32-pixel batches that can meet the scene
+ * (srp_force's batch pre-pass; a ray of another batch has an empty path).
  * Results are reproducible to FP32 rounding (per-warp FP32 atomics). */
 int srp_force_grad(srp_ctx* ctx, const srp_bvh* bvh, const float* rho, int G,
                    const double* sun_dir, int S, const double* com,
