@@ -549,12 +549,17 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
     if (cpb < 0) return fail(SRP_EINVAL, "srp_force: negative chunks_per_item");
     if (cpb == 0) {
         // Enough chunks per item that the resident warps (which take units in
-        // order) all work on the same (design, sun) item at a time: rays of one
-        // direction share BVH nodes in L1; a mix of directions per SM thrashed
-        // it (2x slower).  At least ~40k units for balance; at most 16M units
-        // of partials (1.5 GB); chunks of at least 256 rays.
+        // order) work on a few (design, sun) items at a time: rays of one
+        // direction share BVH nodes in L1 (a mix of many directions per SM
+        // thrashed it, 2x slower), while longer units spend less on their
+        // set-up (item constants, the span row search, partials).  One unit
+        // per four resident warps measured fastest on the satellite (1,024
+        // units per item: +1.9 % rays/s at K <= 3 and +4.3 % at K = 1 over
+        // one per warp; 512 the same; 8,192 -2 % / -7 %).  At least ~40k
+        // units for balance; at most 16M units of partials (1.5 GB); chunks
+        // of at least 256 rays.
         const int64_t warps = (int64_t)c->n_sm * trace_resident_blocks(w ? w : 4, bt, variant) * (bt / 32);
-        cpb = items > 0 ? std::max<int64_t>((40960 + items - 1) / items, warps) : 1;
+        cpb = items > 0 ? std::max<int64_t>((40960 + items - 1) / items, warps / 4) : 1;
         if (items > 0) cpb = std::min<int64_t>(cpb, std::max<int64_t>(1, (int64_t)16777216 / items));
         cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
     }

@@ -177,14 +177,15 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     int rc = setup_device(dev, &ds);
     if (rc != SRP_OK) return rc;
     // chunks per item: the automatic rule of srp_force (at least ~40k units
-    // in all, and at least one unit per resident warp per item so that the
-    // warps resident at a time share one (design, sun) item's BVH nodes in
-    // L1; chunks of at least 256 rays), then capped by the fixed scratch
+    // in all, and at least one unit per four resident warps per item so that
+    // the warps resident at a time share a few (design, sun) items' BVH
+    // nodes in L1; chunks of at least 256 rays), then capped by the fixed
+    // scratch
     int64_t cpb = o->chunks_per_item;
     if (cpb < 0) return fail(SRP_EINVAL, "srp_force_noalloc: negative chunks_per_item");
     if (cpb == 0) {
         const int64_t warps = (int64_t)ds->n_sm * ds->resident[width == 8 ? 1 : 0] * 4;
-        cpb = items > 0 ? std::max<int64_t>((40960 + items - 1) / items, warps) : 1;
+        cpb = items > 0 ? std::max<int64_t>((40960 + items - 1) / items, warps / 4) : 1;
         cpb = std::max<int64_t>(1, std::min<int64_t>(cpb, (n + 255) / 256));
     }
     int64_t chunk = (n + cpb - 1) / cpb;
