@@ -583,11 +583,13 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
     // (up to 4 GiB: 256 designs x 1024 suns x 1024 rows take 2.1 GB)
     p->rowfirst = nullptr;
     p->rowoff = nullptr;
-    const size_t span_bytes = sizeof(int32_t) * (size_t)items * (2 * (size_t)o->rays_y + 1);
+    const size_t row_bytes = (sizeof(int32_t) * (size_t)items * (2 * (size_t)o->rays_y + 1) + 255) / 256 * 256;
+    const size_t span_bytes = row_bytes + 8 * sizeof(float4) * (size_t)items;
     if (items > 0 && off == 0 && stride == 1 && n == grid_n && o->rays_x % 32 == 0 && span_bytes <= ((size_t)4 << 30)) {
         if (c->span.ensure(span_bytes) != cudaSuccess) return fail(SRP_ENOMEM, "srp_force: cannot allocate the span tables");
         p->rowfirst = (int32_t*)c->span.p;
         p->rowoff = p->rowfirst + (size_t)items * o->rays_y;
+        p->itab = (float4*)((char*)c->span.p + row_bytes);
     }
     return SRP_OK;
 }

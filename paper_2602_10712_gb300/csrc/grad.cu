@@ -136,21 +136,20 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
     for (int64_t u = gw; u < units; u += nw) {
         const int s = (int)(u / p.cpb);
         const int64_t cidx = u % p.cpb;
-        ItemConst ic;
-        item_setup(ic, dz, p, p.sun + 3 * (size_t)s, p.com, p.rho, p.design_base, p.sun_base + s);
         const double* up = g.up + 6 * (size_t)s;
         const float3 gF = f3((float)up[0], (float)up[1], (float)up[2]);
         const float3 gT = f3((float)up[3], (float)up[4], (float)up[5]);
-        // the direction-only part of the primary rays' set-up (1/d and the
-        // shear rows), shared by the unit's rays: once per unit, as the
-        // forward does per item (the same values as a per-ray setup_ray)
-        if (lane == 0) {
-            RaySetup rd;
-            setup_ray(rd, f3(0.0f, 0.0f, 0.0f), ic.dd);
-            ws.dirc[0] = rd.inv.x; ws.dirc[1] = rd.inv.y; ws.dirc[2] = rd.inv.z;
-            ws.dirc[3] = rd.mx.x; ws.dirc[4] = rd.mx.y; ws.dirc[5] = rd.mx.z;
-            ws.dirc[6] = rd.my.x; ws.dirc[7] = rd.my.y; ws.dirc[8] = rd.my.z;
-            ws.dirc[9] = rd.mz.x; ws.dirc[10] = rd.mz.y; ws.dirc[11] = rd.mz.z;
+        // the item's grid constants and the direction-only part of the
+        // primary rays' set-up (1/d and the shear rows), shared by the
+        // unit's rays: from the span pre-pass's table on full grids, else
+        // computed once per unit (the same values as a per-ray setup_ray)
+        ItemConst ic;
+        if (p.rowoff != nullptr) {
+            item_load(ic, p.itab + 8 * (size_t)s, p.rho, p.design_base, p.sun_base + s);
+            if (lane < 12) ws.dirc[lane] = __ldg(reinterpret_cast<const float*>(p.itab + 8 * (size_t)s + 5) + lane);
+        } else {
+            item_setup(ic, dz, p, p.sun + 3 * (size_t)s, p.com, p.rho, p.design_base, p.sun_base + s);
+            if (lane == 0) item_dirc(ic, ws.dirc);
         }
         __syncwarp();
         // span mode (full grids of whole 32-pixel batches, as in the
@@ -169,10 +168,15 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
             const int64_t L = __ldg(rowoff + p.ny);
             k0 = cidx * L / p.cpb;
             k1 = (cidx + 1) * L / p.cpb;
+            // the last row whose prefix is <= k0, 32 rows per round
             int lo = 0, hi = p.ny;
             while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if ((int64_t)__ldg(rowoff + mid) <= k0) lo = mid; else hi = mid;
+                const int step = (hi - lo + 31) / 32;
+                const int r = lo + lane * step;
+                const bool ok = r < hi && (int64_t)__ldg(rowoff + r) <= k0;
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                lo += (31 - __clz(m)) * step;
+                hi = min(hi, lo + step);
             }
             row = lo;
         } else {

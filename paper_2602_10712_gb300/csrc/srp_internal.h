@@ -83,6 +83,11 @@ struct TraceParams {
     // null: every ray of the subset is traced
     int32_t* rowfirst;         // [D*S][ny]
     int32_t* rowoff;           // [D*S][ny + 1]
+    // full-grid launches: per item the FP32 constants of its ray grid (the
+    // FP64 item set-up done once by span_kernel for the tracer's units):
+    // (ob, fdx), (bu, fdy), (bv, w0), (dd, tmin_b), (com, 0), then the 12
+    // direction-only values of the primary rays' set-up (1/d, shear rows)
+    float4* itab;              // [D*S][8]
 };
 
 // Parameters of the area-sampling estimator (area.cu).

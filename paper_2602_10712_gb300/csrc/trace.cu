@@ -236,25 +236,24 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
         const int dl = (int)(item_l / p.S), s = (int)(item_l % p.S);
         const int dg = dl;
         const DesignDev dz = p.designs[dl];
+        const bool span = p.rowoff != nullptr;
         ItemConst ic;
-        item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dg * p.S + s : s)), p.com + 3 * dg,
-                   p.rho + (size_t)dg * p.G * 2, p.design_base + dg, p.sun_base + s);
-        if (lane < 12) ws.dacc[lane] = 0.0;
-        if (lane == 0) {
-            RaySetup rd;
-            setup_ray(rd, f3(0.0f, 0.0f, 0.0f), ic.dd);
-            ws.dirc[0] = rd.inv.x; ws.dirc[1] = rd.inv.y; ws.dirc[2] = rd.inv.z;
-            ws.dirc[3] = rd.mx.x; ws.dirc[4] = rd.mx.y; ws.dirc[5] = rd.mx.z;
-            ws.dirc[6] = rd.my.x; ws.dirc[7] = rd.my.y; ws.dirc[8] = rd.my.z;
-            ws.dirc[9] = rd.mz.x; ws.dirc[10] = rd.mz.y; ws.dirc[11] = rd.mz.z;
+        if (span) {   // the item's constants as span_kernel computed them
+            item_load(ic, p.itab + 8 * (size_t)item_l, p.rho + (size_t)dg * p.G * 2, p.design_base + dg,
+                      p.sun_base + s);
+            if (lane < 12) ws.dirc[lane] = __ldg(reinterpret_cast<const float*>(p.itab + 8 * (size_t)item_l + 5) + lane);
+        } else {
+            item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dg * p.S + s : s)),
+                       p.com + 3 * dg, p.rho + (size_t)dg * p.G * 2, p.design_base + dg, p.sun_base + s);
+            if (lane == 0) item_dirc(ic, ws.dirc);
         }
+        if (lane < 12) ws.dacc[lane] = 0.0;
         __syncwarp();
         // The unit's rays come in batches of 32 (a tile holds kBatches of them):
         // span mode -- the unit's share of the item's live batches (batches of
         // 32 neighbouring pixels that can meet the scene, in grid order; the
         // others cannot hit anything and deposit nothing); otherwise -- the
         // contiguous slots [k0, k1) of the ray subset.
-        const bool span = p.rowoff != nullptr;
         const int64_t bstride = span ? 1 : p.stride;
         int64_t t0, t1;           // this unit's batches (span) or slots
         int row = 0;
@@ -266,11 +265,17 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
             const int64_t L = __ldg(rowoff + p.ny);
             t0 = cidx * L / p.cpb;
             t1 = (cidx + 1) * L / p.cpb;
-            // first row with batches at or after t0
+            // first row with batches at or after t0: the last row whose
+            // prefix is <= t0, searched 32 rows at a time (one load per lane
+            // and a ballot per round; the prefix is non-decreasing)
             int lo = 0, hi = p.ny;
             while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if ((int64_t)__ldg(rowoff + mid) <= t0) lo = mid; else hi = mid;
+                const int step = (hi - lo + 31) / 32;
+                const int r = lo + lane * step;
+                const bool ok = r < hi && (int64_t)__ldg(rowoff + r) <= t0;
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                lo += (31 - __clz(m)) * step;
+                hi = min(hi, lo + step);
             }
             row = lo;
         } else {
@@ -450,6 +455,7 @@ __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
         ItemConst ic;
         item_setup(ic, dz, p, p.sun + 3 * ((size_t)(p.sun_per_design ? (int64_t)dl * p.S + s : s)),
                    p.com + 3 * dl, p.rho + (size_t)dl * p.G * 2, p.design_base + dl, p.sun_base + s);
+        if (t == 0) item_store(ic, p.itab + 8 * (size_t)item);
         // the non-empty rectangles, compacted (a small tree fills few of
         // the slots): per thread its slots t, t + 128, ..., then a block scan
         // of the counts gives each thread its output range

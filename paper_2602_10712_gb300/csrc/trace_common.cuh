@@ -400,6 +400,42 @@ __device__ __forceinline__ void item_setup(ItemConst& ic, const DesignDev& dz, c
     ic.dglob = dglob; ic.sglob = sglob;
 }
 
+// The direction-only part of the primary rays' set-up (1/d and the shear
+// rows of setup_ray), shared by every ray of an item.
+__device__ __forceinline__ void item_dirc(const ItemConst& ic, float* dirc) {
+    RaySetup rd;
+    setup_ray(rd, f3(0.0f, 0.0f, 0.0f), ic.dd);
+    dirc[0] = rd.inv.x; dirc[1] = rd.inv.y; dirc[2] = rd.inv.z;
+    dirc[3] = rd.mx.x; dirc[4] = rd.mx.y; dirc[5] = rd.mx.z;
+    dirc[6] = rd.my.x; dirc[7] = rd.my.y; dirc[8] = rd.my.z;
+    dirc[9] = rd.mz.x; dirc[10] = rd.mz.y; dirc[11] = rd.mz.z;
+}
+
+// An item's FP32 grid constants and primary direction set-up as one
+// 8 x float4 record (TraceParams::itab), and back.
+__device__ __forceinline__ void item_store(const ItemConst& ic, float4* rec) {
+    rec[0] = make_float4(ic.ob.x, ic.ob.y, ic.ob.z, ic.fdx);
+    rec[1] = make_float4(ic.bu.x, ic.bu.y, ic.bu.z, ic.fdy);
+    rec[2] = make_float4(ic.bv.x, ic.bv.y, ic.bv.z, ic.w0);
+    rec[3] = make_float4(ic.dd.x, ic.dd.y, ic.dd.z, ic.tmin_b);
+    rec[4] = make_float4(ic.com.x, ic.com.y, ic.com.z, 0.0f);
+    float dc[12];
+    item_dirc(ic, dc);
+    rec[5] = make_float4(dc[0], dc[1], dc[2], dc[3]);
+    rec[6] = make_float4(dc[4], dc[5], dc[6], dc[7]);
+    rec[7] = make_float4(dc[8], dc[9], dc[10], dc[11]);
+}
+__device__ __forceinline__ void item_load(ItemConst& ic, const float4* rec, const float* rho, int dglob, int sglob) {
+    const float4 a = __ldg(rec), b = __ldg(rec + 1), c = __ldg(rec + 2), d = __ldg(rec + 3), e = __ldg(rec + 4);
+    ic.ob = f3(a.x, a.y, a.z); ic.fdx = a.w;
+    ic.bu = f3(b.x, b.y, b.z); ic.fdy = b.w;
+    ic.bv = f3(c.x, c.y, c.z); ic.w0 = c.w;
+    ic.dd = f3(d.x, d.y, d.z); ic.tmin_b = d.w;
+    ic.com = f3(e.x, e.y, e.z);
+    ic.rho = rho;
+    ic.dglob = dglob; ic.sglob = sglob;
+}
+
 // Primary segment of grid ray i (jittered pixel origin, travel direction d).
 __device__ __forceinline__ Seg primary_seg(const ItemConst& ic, const TraceParams& p, uint64_t i) {
     // i < nx * ny < 2^32 (checked on the host): 32-bit division
