@@ -475,19 +475,22 @@ int srp_integrate(srp_ctx* ctx, const srp_orbit_opts* opts, const srp_mlp* proxy
  * D*S*chunks_per_item the same when given), and the design table in a
  * fixed array of 4,096 entries (D <= 4,096); larger requests fail with
  * SRP_EINVAL.  Every fixed array (the partials, the design table, the
- * error word and the work-queue counter) is shared by every call on a
+ * pre-pass tables, the error word and the work-queue counter) is shared by every call on a
  * device and keeps the last call's contents: calls whose work overlaps on
  * the GPU (unordered streams) race on all of them and must not be issued --
  * besides corrupting the sums, one call can rewrite the design table while
  * the other's kernel reads it and then read out of bounds.  The first call
  * on each device looks up the arrays' addresses with that device current;
- * make it before any stream capture begins.  Unlike srp_force it traces
- * every ray of the grid: the batch pre-pass that lets srp_force skip the
- * 32-pixel batches that cannot meet the scene (full grids whose rays_x is a
- * multiple of 32) needs per-row tables this variant does not keep, so on
- * such grids it is slower and groups its sums differently (results equal up
- * to the rounding of that grouping).  With chunks_per_item = 0 it picks
- * chunks as srp_force does, capped so that D*S*chunks fits the array.
+ * make it before any stream capture begins.  On full grids whose rays_x
+ * is a multiple of 32 it runs srp_force's batch pre-pass (the 32-pixel
+ * batches that cannot meet the scene are not traced), with its per-row
+ * tables and per-item constants in a second fixed array of 16 MiB (shared
+ * like the others): D*S*(8*rays_y + 4) + 128*D*S bytes must fit, about
+ * 2,000 (design, sun) items at rays_y = 1024; larger calls, ray subsets and
+ * other widths trace every ray (slower on such grids, sums grouped
+ * differently: equal up to the rounding of that grouping).  With
+ * chunks_per_item = 0 it picks chunks as srp_force does, capped so that
+ * D*S*chunks fits the array.
  * d_status (device int32, may be NULL) receives the device-limit flags of
  * the call (0 = none; see SRP_EDEVICE_LIMIT).  Asynchronous; calls no
  * cudaMalloc/cudaFree or other allocating routine, and takes no host heap

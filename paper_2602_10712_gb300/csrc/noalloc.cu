@@ -22,11 +22,12 @@
 //    them: besides wrong sums, one call may rewrite the design table while
 //    the other's kernel reads it, pairing one design's triangles with
 //    another's nodes, which can read out of bounds;
-//  - it traces every ray of the grid: the batch pre-pass of srp_force,
-//    which skips 32-pixel batches that cannot meet the scene on full grids
-//    whose width is a multiple of 32, needs per-row tables this variant does
-//    not hold, so on such grids it is slower than srp_force and its sums are
-//    grouped differently (equal up to FP64 rounding of the grouping);
+//  - on full grids whose width is a multiple of 32 it runs srp_force's
+//    batch pre-pass (only the 32-pixel batches that can meet the scene are
+//    traced) with its per-row tables and per-item constants in a second
+//    fixed array of kSpanBytes (16 MiB): items * (8 ny + 4) + 128 items
+//    bytes must fit (about 2,000 items at ny = 1024); larger calls, ray
+//    subsets and other widths trace every ray;
 //  - the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
 //    before any stream capture begins;
@@ -46,6 +47,7 @@ namespace srp {
 void set_last_error(const std::string& msg);
 int trace_resident_blocks(int width, int block, int variant);
 cudaError_t launch_trace(const TraceParams& p, int width, int grid_cap, int block, cudaStream_t st);
+cudaError_t launch_span(const TraceParams& p, int width, cudaStream_t st);
 cudaError_t launch_reduce(const double* part, int64_t items, int cpb, double* out_ft, double* out_sigma,
                           cudaStream_t st);
 }  // namespace srp
@@ -55,6 +57,7 @@ using namespace srp;
 namespace {
 
 constexpr size_t kScratchBytes = 8u << 20;                       // 8 MiB
+constexpr size_t kSpanBytes = 16u << 20;                         // 16 MiB
 constexpr int64_t kScratchUnits = (int64_t)(kScratchBytes / (12 * sizeof(double)));
 constexpr int kMaxDevices = 64;
 constexpr int kNoAllocDesigns = 4096;
@@ -65,6 +68,8 @@ static __device__ __align__(256) double g_scratch[kScratchBytes / sizeof(double)
 static __device__ __align__(256) int g_err_word;
 static __device__ __align__(256) unsigned long long g_queue_word;
 static __device__ __align__(256) DesignDev g_design_table[kNoAllocDesigns];
+// the batch pre-pass's tables (row starts, row prefix, item constants)
+static __device__ __align__(256) int32_t g_span[kSpanBytes / sizeof(int32_t)];
 
 struct DevState {
     bool ready = false;
@@ -72,6 +77,7 @@ struct DevState {
     int* err = nullptr;      // device address of g_err_word on this device
     unsigned long long* queue = nullptr;  // device address of g_queue_word
     DesignDev* table = nullptr;           // device address of g_design_table
+    int32_t* span = nullptr;              // device address of g_span
     int n_sm = 0;
     int resident[2] = {0, 0};  // resident blocks per SM for widths 4 and 8
 };
@@ -113,6 +119,9 @@ int setup_device(int dev, DevState** out) {
         e = cudaGetSymbolAddress(&ptr, g_design_table);
         if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetSymbolAddress(designs): ") + cudaGetErrorString(e));
         s.table = static_cast<DesignDev*>(ptr);
+        e = cudaGetSymbolAddress(&ptr, g_span);
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaGetSymbolAddress(span tables): ") + cudaGetErrorString(e));
+        s.span = static_cast<int32_t*>(ptr);
         int v = 0;
         e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
@@ -229,6 +238,16 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     p.variant = 7;
     p.queue = ds->queue;
     p.designs = ds->table;
+    // full grids of whole 32-pixel batches: the batch pre-pass of srp_force,
+    // its tables in the fixed array when they fit (span_kernel rewrites every
+    // entry on each call)
+    const size_t row_bytes = (sizeof(int32_t) * (size_t)items * (2 * (size_t)o->rays_y + 1) + 255) / 256 * 256;
+    if (off == 0 && stride == 1 && n == grid_n && o->rays_x % 32 == 0 &&
+        row_bytes + 8 * sizeof(float4) * (size_t)items <= kSpanBytes) {
+        p.rowfirst = ds->span;
+        p.rowoff = ds->span + (size_t)items * o->rays_y;
+        p.itab = (float4*)((char*)ds->span + row_bytes);
+    }
     // the design table: written into the fixed array by small kernels that
     // carry 64 entries each in their parameters (stream-ordered, no host
     // buffer outlives the call)
@@ -252,6 +271,10 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
     if (e == cudaSuccess) e = cudaMemsetAsync(ds->queue, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const int grid_cap = ds->n_sm * ds->resident[width == 8 ? 1 : 0];
+    if (p.rowoff) {
+        e = launch_span(p, width, st);
+        if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("span_kernel launch: ") + cudaGetErrorString(e));
+    }
     e = launch_trace(p, width, grid_cap, 128, st);
     if (e != cudaSuccess) return fail(SRP_ECUDA, std::string("trace_kernel launch: ") + cudaGetErrorString(e));
     e = launch_reduce(ds->part, items, p.cpb, out_ft, out_sigma, st);

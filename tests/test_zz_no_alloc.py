@@ -66,8 +66,9 @@ def test_noalloc_matches_srp_force_twice():
 
 
 def test_noalloc_full_grid_multiple_of_32():
-    """rays_x % 32 == 0 over the whole grid: srp_force runs its batch
-    pre-pass, the variant traces every batch; the sums agree."""
+    """rays_x % 32 == 0 over the whole grid: both entry points run the
+    batch pre-pass (the variant with its tables in its fixed array); the
+    sums agree, on two calls in a row."""
     _need_gpu()
     import paper_2602_10712_gb300 as srp
     dev = torch.device("cuda:0")
@@ -83,6 +84,32 @@ def test_noalloc_full_grid_multiple_of_32():
     torch.cuda.synchronize()
     for call in range(2):
         out, sig = _run_noalloc(srp, [b], r_t, s_t, c_t, 1, 5, dev, **kw)
+        assert _close(out, ref[0].cpu().numpy()), call
+        assert np.allclose(sig, ref[1].cpu().numpy(), rtol=1e-5, atol=1e-12), call
+
+
+def test_noalloc_full_grid_beyond_the_prepass_array():
+    """A full 32-aligned grid whose pre-pass tables would not fit the fixed
+    16 MiB array (520 suns x 4096 rows: 17 MB): the variant traces every
+    ray instead, srp_force skips the empty batches; the sums agree to the
+    suite's tolerance, on two calls in a row."""
+    _need_gpu()
+    import paper_2602_10712_gb300 as srp
+    dev = torch.device("cuda:0")
+    ctx = srp.Context(0)
+    m, rho, _, com = W.config1()
+    S = 520
+    sun = W.fibonacci_directions(S)
+    b = srp.srp_build_bvh(ctx, m.verts, m.tris, m.group, 4)
+    r_t = torch.from_numpy(rho[None].copy()).to(dev)
+    s_t = torch.from_numpy(sun.copy()).to(dev)
+    c_t = torch.from_numpy(com[None].copy()).to(dev)
+    kw = dict(rays_x=32, rays_y=4096, max_bounces=1, seed=8)
+    assert S * (8 * 4096 + 4) + 128 * S > (16 << 20)
+    ref = srp.srp_force(ctx, [b], r_t, s_t, c_t, out_sigma=True, **kw)
+    torch.cuda.synchronize()
+    for call in range(2):
+        out, sig = _run_noalloc(srp, [b], r_t, s_t, c_t, 1, S, dev, **kw)
         assert _close(out, ref[0].cpu().numpy()), call
         assert np.allclose(sig, ref[1].cpu().numpy(), rtol=1e-5, atol=1e-12), call
 
