@@ -213,8 +213,10 @@ int srp_build_bvh_host(const float* verts, int V, const int32_t* tris, int T, in
  * asynchronous; the scratch they use belongs to the context, so calls on
  * one context must not overlap on different streams.  Validation of rho
  * and sun_dir values happens only for host-mem calls.  Whole grids
- * (ray_count 0) with rays_x a multiple of 32 first find, per grid row, the
- * batches of 32 pixels whose rays can meet the design (the BVH's top boxes
+ * (ray_count 0) with rays_x a multiple of 32 first find, per band of grid
+ * rows, the batches of 32 pixels (blocks of 8 x 4 when rays_y is a multiple
+ * of 4, 16 x 2 when it is even, else 32 x 1) whose rays can meet the design
+ * (the BVH's top boxes
  * projected onto the grid) and trace only those: the others deposit
  * exactly nothing, so the estimate is the whole grid's, its sums grouped
  * over the traced batches. */

@@ -590,6 +590,7 @@ int force_plan(srp_ctx* c, const srp_bvh* const* bvhs, int D, int G, int S, cons
         p->rowfirst = (int32_t*)c->span.p;
         p->rowoff = p->rowfirst + (size_t)items * o->rays_y;
         p->itab = (float4*)((char*)c->span.p + row_bytes);
+        p->bh = span_batch_rows(o->rays_y);
     }
     return SRP_OK;
 }

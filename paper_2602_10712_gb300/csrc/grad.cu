@@ -15,7 +15,8 @@
 //    (hinge_path_tangent).  The visibility of each ray is held fixed (the
 //    estimate's boundary terms, where a shadow edge or silhouette moves,
 //    are not included).
-// Full grids of whole 32-pixel batches trace only the batches that can meet
+// Full grids of whole 32-pixel batches (8 x 4 blocks where the rows allow)
+// trace only the batches that can meet
 // the scene (the forward's span pre-pass; the rest contribute nothing).
 // Accumulation: per-warp FP32 shared-memory sums over <= 512 rays, flushed
 // into per-warp FP64 (an FP64 warp instruction is expensive on this GPU,
@@ -163,13 +164,14 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
         int64_t k0, k1;
         int row = 0;
         if (span) {
-            rowoff = p.rowoff + (size_t)s * (p.ny + 1);
-            rowfirst = p.rowfirst + (size_t)s * p.ny;
-            const int64_t L = __ldg(rowoff + p.ny);
+            const int nband = p.ny / p.bh;
+            rowoff = p.rowoff + (size_t)s * (nband + 1);
+            rowfirst = p.rowfirst + (size_t)s * nband;
+            const int64_t L = __ldg(rowoff + nband);
             k0 = cidx * L / p.cpb;
             k1 = (cidx + 1) * L / p.cpb;
             // the last row whose prefix is <= k0, 32 rows per round
-            int lo = 0, hi = p.ny;
+            int lo = 0, hi = nband;
             while (hi - lo > 1) {
                 const int step = (hi - lo + 31) / 32;
                 const int r = lo + lane * step;
@@ -189,8 +191,9 @@ __global__ void __launch_bounds__(128, 6) grad_kernel(const DesignDev dz, const 
             uint64_t i;
             if (span) {
                 while ((int64_t)__ldg(rowoff + row + 1) <= kb) ++row;
-                i = (uint64_t)((int64_t)row * p.nx + 32 * ((int64_t)__ldg(rowfirst + row) + (kb - __ldg(rowoff + row))) +
-                               lane);
+                i = span_ray((int64_t)row * p.bh * p.nx +
+                                 (32 / p.bh) * ((int64_t)__ldg(rowfirst + row) + (kb - __ldg(rowoff + row))),
+                             lane, p.bh, p.nx);
                 k = kb;
             } else {
                 k = kb + lane;

@@ -247,6 +247,7 @@ extern "C" int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float*
         p.rowfirst = ds->span;
         p.rowoff = ds->span + (size_t)items * o->rays_y;
         p.itab = (float4*)((char*)ds->span + row_bytes);
+        p.bh = span_batch_rows(o->rays_y);
     }
     // the design table: written into the fixed array by small kernels that
     // carry 64 entries each in their parameters (stream-ordered, no host

@@ -78,17 +78,31 @@ struct TraceParams {
     const DesignDev* designs;  // [D] device-side design table
     unsigned long long* queue; // work-queue counter (zeroed before each launch)
     int32_t variant;           // register budget: minimum resident blocks 4 or 5
-    // full-grid launches: per item and grid row, the first batch of 32 pixels
-    // that can meet the scene and the prefix of such batches (span_kernel);
-    // null: every ray of the subset is traced
-    int32_t* rowfirst;         // [D*S][ny]
-    int32_t* rowoff;           // [D*S][ny + 1]
+    // full-grid launches: a batch is a block of 32 / bh x bh pixels (bh = 1,
+    // 2 or 4 rows, the tallest that divides ny); per item and band of bh
+    // grid rows, the first batch that can meet the scene and the prefix of
+    // such batches (span_kernel); null: every ray of the subset is traced
+    int32_t* rowfirst;         // [D*S][ny / bh]
+    int32_t* rowoff;           // [D*S][ny / bh + 1]
+    int32_t bh;
     // full-grid launches: per item the FP32 constants of its ray grid (the
     // FP64 item set-up done once by span_kernel for the tracer's units):
     // (ob, fdx), (bu, fdy), (bv, w0), (dd, tmin_b), (com, 0), then the 12
     // direction-only values of the primary rays' set-up (1/d, shear rows)
     float4* itab;              // [D*S][8]
 };
+
+// Rows of a span-mode batch for a grid of ny rows: the tallest of 4, 2, 1
+// that divides ny (the block is 32 / rows pixels wide).  Compact blocks keep
+// a warp's parallel rays closer together than a 32-pixel strip.
+#ifndef SRP_SPAN_ROWS_MAX
+#define SRP_SPAN_ROWS_MAX 4
+#endif
+inline int span_batch_rows(int ny) {
+    if (SRP_SPAN_ROWS_MAX >= 4 && ny % 4 == 0) return 4;
+    if (SRP_SPAN_ROWS_MAX >= 2 && ny % 2 == 0) return 2;
+    return 1;
+}
 
 // Parameters of the area-sampling estimator (area.cu).
 struct AreaParams {

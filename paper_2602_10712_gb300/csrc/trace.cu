@@ -15,7 +15,8 @@
 // Work decomposition: an item's n rays are split into `cpb` chunks of
 // `chunk` rays (a multiple of 64); one block processes one chunk at a time,
 // thread t handling rays k = start + t + j*blockDim, so a warp traces 32
-// neighbouring pixels of one grid row (coherent parallel rays share BVH
+// neighbouring pixels of one grid row, or on full grids (span mode) a
+// block of 8 x 4 pixels (coherent parallel rays share BVH
 // nodes through L1).  Blocks loop over chunks with a static stride.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -136,6 +137,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // looping over units (item, chunk) with a static stride; a unit's rays are
 // processed in tiles of 32*kBatches rays:
 //   primary batches  the warp traces 32 neighbouring pixels at a time
+//                    (span mode: an 8 x 4 block, 16 x 2 or 32 x 1 when the
+//                    grid's rows do not divide by 4)
 //                    (coherent parallel rays share node fetches); each
 //                    ray's deposit goes to its slot in shared memory and
 //                    paths that continue are pushed on the warp's queue;
@@ -205,7 +208,8 @@ __device__ __forceinline__ void q_batch(WarpSmem& ws, int& qcount, int nb, const
                                           __float_as_int(Bv.w), nullptr, p.err);
         nvis += h.nvis; ntest += h.ntest;
         if (h.f >= 0) {
-            const uint64_t i = (uint64_t)(ws.bbase[slot >> 5] + (int64_t)(slot & 31) * bstride);
+            const uint64_t i = p.rowoff ? span_ray(ws.bbase[slot >> 5], slot & 31, p.bh, p.nx)
+                                        : (uint64_t)(ws.bbase[slot >> 5] + (int64_t)(slot & 31) * bstride);
             const ShadeOut so = shade_segment(dz.tri, ic.rho, ic.com.x, ic.com.y, ic.com.z, p.K, p.seed, ic.sglob,
                                               ic.dglob, (uint32_t)i, kb, h.f, h.t, A.x, A.y, A.z, Bv.x, Bv.y, Bv.z,
                                               A.w, &ws.ys[0][slot], kTile);
@@ -251,7 +255,8 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
         __syncwarp();
         // The unit's rays come in batches of 32 (a tile holds kBatches of them):
         // span mode -- the unit's share of the item's live batches (batches of
-        // 32 neighbouring pixels that can meet the scene, in grid order; the
+        // 32 neighbouring pixels (a block of 32 / bh x bh) that can meet the
+        // scene, in grid order; the
         // others cannot hit anything and deposit nothing); otherwise -- the
         // contiguous slots [k0, k1) of the ray subset.
         const int64_t bstride = span ? 1 : p.stride;
@@ -259,16 +264,17 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
         int row = 0;
         const int32_t* rowoff = nullptr;
         const int32_t* rowfirst = nullptr;
+        const int nband = span ? p.ny / p.bh : 0;
         if (span) {
-            rowoff = p.rowoff + (size_t)item_l * (p.ny + 1);
-            rowfirst = p.rowfirst + (size_t)item_l * p.ny;
-            const int64_t L = __ldg(rowoff + p.ny);
+            rowoff = p.rowoff + (size_t)item_l * (nband + 1);
+            rowfirst = p.rowfirst + (size_t)item_l * nband;
+            const int64_t L = __ldg(rowoff + nband);
             t0 = cidx * L / p.cpb;
             t1 = (cidx + 1) * L / p.cpb;
-            // first row with batches at or after t0: the last row whose
-            // prefix is <= t0, searched 32 rows at a time (one load per lane
+            // first band with batches at or after t0: the last band whose
+            // prefix is <= t0, searched 32 bands at a time (one load per lane
             // and a ballot per round; the prefix is non-decreasing)
-            int lo = 0, hi = p.ny;
+            int lo = 0, hi = nband;
             while (hi - lo > 1) {
                 const int step = (hi - lo + 31) / 32;
                 const int r = lo + lane * step;
@@ -292,7 +298,8 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
                         if (32 * j < nslots) {
                             const int64_t lb = ts + j;
                             while ((int64_t)__ldg(rowoff + row + 1) <= lb) ++row;
-                            b = (int64_t)row * p.nx + 32 * ((int64_t)__ldg(rowfirst + row) + (lb - __ldg(rowoff + row)));
+                            b = (int64_t)row * p.bh * p.nx +
+                                (32 / p.bh) * ((int64_t)__ldg(rowfirst + row) + (lb - __ldg(rowoff + row)));
                         }
                     } else {
                         b = p.off + (ts + 32 * j) * p.stride;
@@ -312,7 +319,8 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
                 Seg nx;
                 bool cont = false;
                 if (slot < nslots) {
-                    const uint64_t i = (uint64_t)(ws.bbase[j] + (int64_t)lane * bstride);
+                    const uint64_t i = span ? span_ray(ws.bbase[j], lane, p.bh, p.nx)
+                                            : (uint64_t)(ws.bbase[j] + (int64_t)lane * bstride);
                     const Seg sg = primary_seg(ic, p, i);
                     ++nseg;
                     const HitOut h = trace_segment<W>(dz.nodes, dz.tri, sg.o.x, sg.o.y, sg.o.z, sg.d.x, sg.d.y,
@@ -379,14 +387,16 @@ __global__ void __launch_bounds__(128, MINB) trace_kernel(const TraceParams p) {
 
 // ---------------------------------------------------------------------------
 // Span pre-pass (full-grid launches): which batches of 32 neighbouring
-// pixels can meet the scene.  One block per (design, sun) item projects the
+// pixels (blocks of 32 / bh x bh, bh = TraceParams::bh) can meet the scene.
+// One block per (design, sun) item projects the
 // BVH boxes five levels below the root (W = 4: up to 1024; W = 8: two
 // levels, up to 64) onto the grid plane as pixel rectangles widened by 2 pixels
 // (FP32 rounding of the ray origins is ~1e-4 pixel); a ray outside every
 // rectangle misses every box, so it cannot hit a triangle and deposits
-// nothing.  Per row y: rowfirst[y] = first batch of the row that meets a
-// rectangle, count = batches up to the last one that does; rowoff = the
-// exclusive prefix of the counts (rowoff[ny] = the item's live batches).
+// nothing.  Per band y of bh grid rows: rowfirst[y] = first batch of the
+// band that meets a rectangle, count = batches up to the last one that
+// does; rowoff = the exclusive prefix of the counts (rowoff[ny / bh] = the
+// item's live batches).
 // ---------------------------------------------------------------------------
 // Box slots of the span pre-pass: W = 4 -- the nodes five levels below the
 // root (1024 slots; on the benchmark's satellite, over 32 sun directions,
@@ -483,23 +493,28 @@ __global__ void __launch_bounds__(128) span_kernel(const TraceParams p) {
         for (int k = 0; k < kPer; ++k)
             if (mine[k].x <= mine[k].y) rect[pos++] = mine[k];
         __syncthreads();
-        const int nbx = p.nx / 32, ny = p.ny;
+        const int bh = p.bh, bw = 32 / bh;
+        const int nbx = p.nx / bw, ny = p.ny / bh;   // batches per band, bands
+        const float inv_bw = 1.0f / (float)bw;      // exact: bw is a power of two
         int32_t* ro = p.rowoff + (size_t)item * (ny + 1);
         int32_t* rf = p.rowfirst + (size_t)item * ny;
         int carry = 0;
         for (int y0 = 0; y0 < ny; y0 += 128) {
-            const int y = y0 + t;
+            const int y = y0 + t;   // band: grid rows bh y .. bh y + bh - 1
             int cnt = 0;
             if (y < ny) {
                 float xmin = INFINITY, xmax = -INFINITY;
                 for (int j = 0; j < nrect; ++j) {
                     const float4 r = rect[j];
-                    if (r.z < (float)(y + 1) && r.w > (float)y) { xmin = fminf(xmin, r.x); xmax = fmaxf(xmax, r.y); }
+                    if (r.z < (float)(bh * y + bh) && r.w > (float)(bh * y)) {
+                        xmin = fminf(xmin, r.x);
+                        xmax = fmaxf(xmax, r.y);
+                    }
                 }
                 int bf = 0;
                 if (xmin < xmax) {
-                    const int b0 = (int)floorf(fminf(fmaxf(xmin * (1.0f / 32.0f), 0.0f), (float)nbx));
-                    const int b1 = (int)ceilf(fminf(fmaxf(xmax * (1.0f / 32.0f), 0.0f), (float)nbx));
+                    const int b0 = (int)floorf(fminf(fmaxf(xmin * inv_bw, 0.0f), (float)nbx));
+                    const int b1 = (int)ceilf(fminf(fmaxf(xmax * inv_bw, 0.0f), (float)nbx));
                     if (b1 > b0) { bf = b0; cnt = b1 - b0; }
                 }
                 rf[y] = bf;

@@ -436,6 +436,15 @@ __device__ __forceinline__ void item_load(ItemConst& ic, const float4* rec, cons
     ic.dglob = dglob; ic.sglob = sglob;
 }
 
+// Span mode: the grid ray of lane l in the batch whose top-left pixel has
+// grid index b; a batch is a block of 32 / bh columns x bh rows (bh = 1, 2
+// or 4), lanes along its rows, so lanes 2c and 2c + 1 hold horizontally
+// neighbouring pixels (the pairs of the collapsed-strata variance).
+__device__ __forceinline__ uint64_t span_ray(int64_t b, int l, int bh, int nx) {
+    const int sh = bh == 4 ? 3 : (bh == 2 ? 4 : 5);   // log2 of the block width
+    return (uint64_t)(b + (int64_t)(l >> sh) * nx + (l & ((1 << sh) - 1)));
+}
+
 // Primary segment of grid ray i (jittered pixel origin, travel direction d).
 __device__ __forceinline__ Seg primary_seg(const ItemConst& ic, const TraceParams& p, uint64_t i) {
     // i < nx * ny < 2^32 (checked on the host): 32-bit division
