@@ -37,11 +37,12 @@ NX = 2048
 K_BOUNCE = 3
 WORKLOAD = "procedural satellite 49,776 tris, 64 groups, 4096 Fibonacci suns x 2048^2 rays, K<=3"
 # dram__bytes_read.sum + dram__bytes_write.sum of trace_kernel<4,7> (packed
-# FP32 slab test, span pre-pass five BVH levels deep, sorted inner children,
-# slot-mask leaf loop) from the ncu capture of 16 of the 4096 suns (the
+# FP32 slab test, span pre-pass five BVH levels deep over 8 x 4 pixel
+# batches, sorted inner children, slot-mask leaf loop, per-item constants
+# from the pre-pass) from the ncu capture of 16 of the 4096 suns (the
 # launch-list summary of the 2048^2 satellite workload under profiles/),
 # scaled by the units processed (x256) to one benchmark launch
-TRACE_DRAM_BYTES_PER_LAUNCH = (28.428544e6 + 247.446016e6) * 256
+TRACE_DRAM_BYTES_PER_LAUNCH = (20.376320e6 + 136.071680e6) * 256
 
 
 def _peaks():
