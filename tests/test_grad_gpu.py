@@ -124,13 +124,15 @@ def test_autograd_function(srp, ctx):
     assert _rel(g_ang, dho) <= 1e-4, (g_ang, dho)
 
 
-@pytest.mark.parametrize("K", [1, 3])
-def test_grad_span_prepass_equals_ray_subsets(srp, ctx, K):
+@pytest.mark.parametrize("K,ny", [(1, 256), (3, 256), (1, 258), (1, 257)])
+def test_grad_span_prepass_equals_ray_subsets(srp, ctx, K, ny):
     """A full grid of whole 32-pixel batches traces only the batches that can
     meet the scene (the forward's pre-pass); the same grid given as two ray
     subsets traces every ray.  Both give the gradient of the same estimate:
     reflectance and hinge gradients agree to the FP32 grouping of the
-    per-warp sums (1e-5, the suite's bound), on the box-wing with hinges, 4 suns, 256^2 rays."""
+    per-warp sums (1e-5, the suite's bound), on the box-wing with hinges, 4
+    suns, 256 columns; 256, 258 and 257 rows give batches of 8 x 4, 16 x 2
+    and 32 x 1 pixels."""
     m, rho, _, com = W.config1()
     ang = np.array([0.3, -0.5])
     v = srp.srp_design_instantiate(m.verts, m.vhinge, m.hinges, ang)
@@ -138,9 +140,9 @@ def test_grad_span_prepass_equals_ray_subsets(srp, ctx, K):
     sun = W.fibonacci_directions(4)
     up = np.random.default_rng(12).normal(size=(4, 6))
     b = srp.srp_build_bvh(ctx, v, m.tris, m.group, 4)
-    kw = dict(tri_hinge=th, hinge_axes=m.hinges, rays_x=256, max_bounces=K, seed=6)
+    kw = dict(tri_hinge=th, hinge_axes=m.hinges, rays_x=256, rays_y=ny, max_bounces=K, seed=6)
     dr, dh = srp.srp_force_grad(ctx, b, rho, sun, com, up, **kw)
-    n = 256 * 256
+    n = 256 * ny
     a_r, a_h = srp.srp_force_grad(ctx, b, rho, sun, com, up, ray_offset=0, ray_count=n // 2, **kw)
     b_r, b_h = srp.srp_force_grad(ctx, b, rho, sun, com, up, ray_offset=n // 2, ray_count=n // 2, **kw)
     assert np.any(dr != 0.0) and np.all(np.abs(dh) > 0.0)

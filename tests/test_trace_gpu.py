@@ -384,21 +384,23 @@ def test_corrupted_bvh_reports_device_limit(srp, ctx):
     _assert_parity(ft[0], fo, b.info()["radius"])
 
 
-@pytest.mark.parametrize("width", [4, 8])
-def test_skipped_batches_deposit_nothing(srp, ctx, width):
+@pytest.mark.parametrize("width,ny", [(4, 256), (8, 256), (4, 258), (4, 257)])
+def test_skipped_batches_deposit_nothing(srp, ctx, width, ny):
     """On a full grid of whole 32-pixel batches only the batches that can
     meet the scene are traced; the rest must deposit nothing.  The same grid
     without its last ray is traced ray by ray (a ray subset): full =
-    subset + last ray, to rounding, on the satellite with K = 3."""
+    subset + last ray, to rounding, on the satellite with K = 3.  256 rows
+    make the batches 8 x 4 pixel blocks, 258 rows 16 x 2, 257 rows 32 x 1:
+    each shape must cover every ray of the grid exactly once."""
     m, rho, sun, com = W.config2(8)
     b = _bvh(srp, ctx, m, width=width)
     nx = 256
-    full = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=nx, max_bounces=3, seed=3)
-    sub = srp.srp_force(ctx, [b], rho[None], sun, com[None], rays_x=nx, max_bounces=3, seed=3, ray_offset=0,
-                        ray_stride=1, ray_count=nx * nx - 1)
+    kw = dict(rays_x=nx, rays_y=ny, max_bounces=3, seed=3)
+    full = srp.srp_force(ctx, [b], rho[None], sun, com[None], **kw)
+    sub = srp.srp_force(ctx, [b], rho[None], sun, com[None], ray_offset=0, ray_stride=1, ray_count=nx * ny - 1,
+                        **kw)
     for s in range(sun.shape[0]):
-        y, _ = srp.srp_trace_rays(ctx, b, rho, sun[s], com, np.array([nx * nx - 1]), sun_index=s, rays_x=nx,
-                                  max_bounces=3, seed=3)
+        y, _ = srp.srp_trace_rays(ctx, b, rho, sun[s], com, np.array([nx * ny - 1]), sun_index=s, **kw)
         want = sub[0, s] + y[0]
         scale = np.linalg.norm(full[0, s, :3])
         assert np.all(np.abs(full[0, s] - want) <= 1e-6 * scale * np.array([1, 1, 1, 10, 10, 10])), (s, full[0, s], want)
