@@ -56,6 +56,13 @@ struct OrbitDev {
 
 constexpr int kMaxCkptSeg = 64;
 constexpr int kOrbitThreads = 256;
+// proxy weight loads in flight per thread in the hidden layers (a multiple
+// of 4: the partial sums take inputs i = 4m + r in order, whatever the
+// chunk, so results do not depend on it)
+#ifndef SRP_RK4_WLOADS
+#define SRP_RK4_WLOADS 128
+#endif
+constexpr int kWLoads = SRP_RK4_WLOADS;
 
 // ---- dual numbers ------------------------------------------------------------
 struct Dual {
@@ -243,18 +250,20 @@ __device__ void model_fwd(const OrbitDev& o, OrbitSmem<T>& s) {
     for (int l = 1; l < 4; ++l) {
         const float* hin = &s.h[(l - 1) & 1][0][0];
         const float* Wt = o.Wt[l];
-        // 32 weight loads in flight per thread and four partial sums: the
-        // loop is bound by the latency of the weight stream from L2
+        // kWLoads weight loads in flight per thread and four partial sums:
+        // the loop is bound by the latency of the weight stream from L2, so
+        // the bytes in flight per SM set its rate (one CTA per SM leaves the
+        // registers for them)
         float a[4][T];
         const float bl = o.b[l][t];
 #pragma unroll
         for (int j = 0; j < T; ++j) { a[0][j] = bl; a[1][j] = 0.0f; a[2][j] = 0.0f; a[3][j] = 0.0f; }
-        for (int i = 0; i < 256; i += 32) {
-            float w[32];
+        for (int i = 0; i < 256; i += kWLoads) {
+            float w[kWLoads];
 #pragma unroll
-            for (int u = 0; u < 32; ++u) w[u] = __ldg(Wt + (i + u) * 256 + t);
+            for (int u = 0; u < kWLoads; ++u) w[u] = __ldg(Wt + (i + u) * 256 + t);
 #pragma unroll
-            for (int u = 0; u < 32; ++u) {
+            for (int u = 0; u < kWLoads; ++u) {
                 float hv[T];
                 ld_t<T>(hin + (i + u) * T, hv);
 #pragma unroll
@@ -333,12 +342,12 @@ __device__ void model_vjp(const OrbitDev& o, OrbitSmem<T>& s) {
         float a[4][T];
 #pragma unroll
         for (int j = 0; j < T; ++j) { a[0][j] = 0.0f; a[1][j] = 0.0f; a[2][j] = 0.0f; a[3][j] = 0.0f; }
-        for (int oo = 0; oo < 256; oo += 32) {
-            float w[32];
+        for (int oo = 0; oo < 256; oo += kWLoads) {
+            float w[kWLoads];
 #pragma unroll
-            for (int u = 0; u < 32; ++u) w[u] = __ldg(W + (oo + u) * 256 + t);
+            for (int u = 0; u < kWLoads; ++u) w[u] = __ldg(W + (oo + u) * 256 + t);
 #pragma unroll
-            for (int u = 0; u < 32; ++u) {
+            for (int u = 0; u < kWLoads; ++u) {
                 float gv[T];
                 ld_t<T>(gin + (oo + u) * T, gv);
 #pragma unroll
