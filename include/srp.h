@@ -509,8 +509,14 @@ int srp_force_noalloc(const srp_bvh* const* bvhs, int D, const float* rho, int G
  * persistent trace launch over every (design, sun, chunk) unit, reduction)
  * on the context's stream, reading
  * rho/sun_dir/com and writing out_ft/out_sigma at the captured addresses.
- * The graph uses the context's scratch: no other srp_force or graph of the
- * same context may run concurrently. */
+ * The graph uses the context's scratch (partial sums, pre-pass tables) at
+ * the addresses it had when the graph was captured: no other srp_force or
+ * graph of the same context may run concurrently, and a later call on the
+ * same context that needs more scratch than the graph's evaluation (more
+ * (design, sun) items or chunks, more grid rows) grows the scratch by
+ * reallocating it, after which the graph must not be launched again --
+ * create graphs after the context's largest call, or give each graph a
+ * context of its own. */
 typedef struct srp_graph srp_graph;
 int srp_force_graph_create(srp_ctx* ctx, const srp_bvh* const* bvhs, int D, const float* rho, int G,
                            const double* sun_dir, int S, const double* com, const srp_trace_opts* opts,
